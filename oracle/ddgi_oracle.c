@@ -427,6 +427,12 @@ void or_query(const or_volume* v, const uint8_t* states, const double* irr, cons
     for (int64_t q = 0; q < n; ++q) {
         const double* x = pos + 3*q;
         const double* nn = nrm + 3*q;
+        if (nn[0] == 0.0 && nn[1] == 0.0 && nn[2] == 0.0) {
+            /* no surface (a background pixel): no irradiance */
+            for (int k = 0; k < 3; ++k) out_E[3*q + k] = 0.0;
+            if (weights_out) for (int c = 0; c < 8; ++c) weights_out[8*q + c] = 0.0;
+            continue;
+        }
         double wo[3];
         sub3(camera, x, wo);
         double l = len3(wo);
