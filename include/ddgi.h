@@ -1,0 +1,255 @@
+/*
+ * ddgi.h -- C ABI of the GB300 probe-based irradiance field library.
+ *
+ * The library maintains the data structure of Majercik, Marrs, Spjut and
+ * McGuire, "Scaling Probe-Based Real-Time Dynamic Global Illumination for
+ * Production" (JCGT 2021): a 3D grid of probes storing octahedral irradiance
+ * and distance / squared-distance moments, which answers queries of the
+ * form irradiance(location, orientation) (Sec. 1) and is refreshed every
+ * frame by tracing rays from the probes (Sec. 2.3).
+ *
+ * Conventions shared by every call
+ *   - Every call returns a ddgi_status; DDGI_OK is 0.  On failure,
+ *     ddgi_last_error() returns a message for the calling thread, and no
+ *     output buffer has been written unless stated.
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller,
+ *     contiguous, 4-byte aligned (16-byte aligned where stated).  Pointers
+ *     without the suffix are host pointers; the library copies what it needs
+ *     before returning.
+ *   - Device work is enqueued asynchronously on the stream passed as
+ *     ddgi_stream (a cudaStream_t; NULL is the legacy default stream).  No
+ *     call synchronises the device unless its comment says so.
+ *   - The library owns scenes and volumes (opaque handles).  A handle may be
+ *     used from one host thread at a time.
+ *   - Vectors are float32 [n][3] arrays unless stated.  Triangles are wound
+ *     counter-clockwise seen from their front side.
+ *   - Stored irradiance is the cosine-weighted mean radiance M; queries
+ *     return irradiance E = pi * M.
+ */
+#ifndef DDGI_H
+#define DDGI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ddgi_scene_s*  ddgi_scene;
+typedef struct ddgi_volume_s* ddgi_volume;
+typedef void*                 ddgi_stream;   /* cudaStream_t */
+
+typedef enum {
+    DDGI_OK = 0,
+    DDGI_ERR_INVALID_ARG = 1,   /* bad pointer, size, alignment or descriptor */
+    DDGI_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    DDGI_ERR_OOM = 3,           /* device allocation failed */
+    DDGI_ERR_TIMEOUT = 4,       /* a bounded device wait gave up */
+    DDGI_ERR_NUMERIC = 5,       /* a kernel flagged a non-finite value */
+    DDGI_ERR_UNSUPPORTED = 6    /* option not built in */
+} ddgi_status;
+
+/* Probe states (Sec. 6, Fig. "probestates"); dynamic-object states are not used. */
+enum {
+    DDGI_STATE_UNINIT = 0,          /* not yet classified */
+    DDGI_STATE_OFF = 1,             /* inside static geometry: never traced (Sec. 6.1) */
+    DDGI_STATE_SLEEPING = 2,        /* no surface within probe spacing (Sec. 6.2) */
+    DDGI_STATE_NEWLY_VIGILANT = 3,  /* just classified; first update uses hysteresis 0 */
+    DDGI_STATE_VIGILANT = 4         /* traced and updated every frame */
+};
+
+/* Atlas storage formats (precision variants; the paper does not fix one). */
+enum {
+    DDGI_IRR_FP32 = 0,      /* rgb float32, 12 B / texel */
+    DDGI_IRR_FP16 = 1,      /* rgb float16 + pad, 8 B / texel */
+    DDGI_IRR_RGB9E5 = 2,    /* shared-exponent 9:9:9:5, 4 B / texel */
+    DDGI_DIST_FP32 = 0,     /* (mean, mean square) float32, 8 B / texel */
+    DDGI_DIST_FP16 = 1      /* (mean, mean square) float16, 4 B / texel */
+};
+
+/* Blend arithmetic (precision variants of the Eq. 1 contraction). */
+enum {
+    DDGI_BLEND_FP32 = 0,    /* SIMT float32 */
+    DDGI_BLEND_TF32 = 1,    /* tensor cores, TF32 operands, FP32 accumulate */
+    DDGI_BLEND_BF16 = 2     /* tensor cores, BF16 operands, FP32 accumulate */
+};
+
+const char* ddgi_last_error(void);
+int32_t     ddgi_version(void);
+
+/* ------------------------------------------------------------------ */
+/* Scenes                                                              */
+/* ------------------------------------------------------------------ */
+
+/* Register a triangle scene and build its bounding volume hierarchy on the
+ * host (binned SAH), then upload it.  The probe rays of Sec. 2.3 and the
+ * shadow rays of hit shading are traced against it.
+ *   verts            [n_verts][3] float, host
+ *   tris             [n_tris][3] int32 vertex indices, host, CCW = front
+ *   tri_object       [n_tris] int32 object index in [0, n_objects)
+ *   object_albedo    [n_objects][3] float diffuse albedo
+ *   object_flags     [n_objects] int32; bit 0: object casts shadows
+ *   tri_emitter      [n_tris] int32 emitter index in [0, n_emitters) or -1
+ *   emitter_radiance [n_emitters][3] float emitted radiance (front side only)
+ * Synchronises the device once (upload).  Errors: INVALID_ARG on a bad
+ * count or an index out of range (nothing allocated), OOM, CUDA. */
+ddgi_status ddgi_scene_create(const float* verts, int64_t n_verts,
+                              const int32_t* tris, int64_t n_tris,
+                              const int32_t* tri_object, int32_t n_objects,
+                              const float* object_albedo, const int32_t* object_flags,
+                              const int32_t* tri_emitter, int32_t n_emitters,
+                              const float* emitter_radiance, ddgi_scene* out);
+void ddgi_scene_destroy(ddgi_scene scene);
+
+/* Size of the uploaded hierarchy: node count, leaf count, triangle count. */
+ddgi_status ddgi_scene_info(ddgi_scene scene, int64_t* n_nodes, int64_t* n_leaves, int64_t* n_tris);
+
+/* Closest hit of n arbitrary rays, t in (0, inf) (the traversal used by the
+ * probe update, Sec. 2.3).  orig_dev, dir_dev: [n][3] float.  Outputs:
+ * t_dev [n] float (+inf on a miss), tri_dev [n] int32 original triangle
+ * index or -1, backface_dev [n] int32 (1 when dir . (e1 x e2) > 0) -- may be
+ * NULL.  Equal distances resolve to the lower triangle index. */
+ddgi_status ddgi_trace(ddgi_scene scene, const float* orig_dev, const float* dir_dev, int64_t n,
+                       float* t_dev, int32_t* tri_dev, int32_t* backface_dev, ddgi_stream stream);
+
+/* Pinhole-camera G-buffer of the scene (input generation for queries; the
+ * paper rasterises it, Sec. 7.4).  Pixel (x, y), row-major, looks along
+ * normalize(fwd + sx*tan(vfov/2)*aspect*right + sy*tan(vfov/2)*up) with
+ * sx = (x+0.5)/w*2-1, sy = 1-(y+0.5)/h*2.  Outputs pos_dev, nrm_dev
+ * [h*w][3]: first-hit position and unit geometric normal; misses give
+ * zero position and zero normal. */
+ddgi_status ddgi_raycast_gbuffer(ddgi_scene scene, const float cam_pos[3], const float cam_fwd[3],
+                                 const float cam_up[3], float vfov_deg, int32_t width, int32_t height,
+                                 float* pos_dev, float* nrm_dev, ddgi_stream stream);
+
+/* ------------------------------------------------------------------ */
+/* Lights                                                              */
+/* ------------------------------------------------------------------ */
+
+/* One directional light and a linear sky L(w) = sky_a + sky_b (w . sky_up)
+ * seen by rays that miss the scene. */
+typedef struct {
+    float sun_dir[3];           /* unit direction the light travels */
+    float sun_irradiance[3];    /* irradiance on a surface facing the sun */
+    float sky_a[3];
+    float sky_b[3];
+    float sky_up[3];
+} ddgi_lights;
+
+/* ------------------------------------------------------------------ */
+/* Volumes                                                             */
+/* ------------------------------------------------------------------ */
+
+/* Probe volume descriptor (Sec. 2.1 grid; Sec. 2.3 / 4 parameters). */
+typedef struct {
+    float   origin[3];          /* position of probe (0,0,0) */
+    float   spacing[3];         /* probe spacing per axis (> 0) */
+    int32_t counts[3];          /* probes per axis (>= 2) */
+    int32_t rays_per_probe;     /* R, 1..1024 */
+    int32_t irr_n;              /* interior irradiance texels per side (6 -> 8x8 tiles) */
+    int32_t dist_n;             /* interior distance texels per side (14 -> 16x16 tiles) */
+    float   hysteresis_irr;     /* alpha of Eq. 1 for irradiance */
+    float   hysteresis_vis;     /* alpha for distance moments */
+    float   gamma;              /* perceptual exponent of Sec. 4.2 (5; 1 = off) */
+    float   self_shadow_bias;   /* B of the self-shadow bias equation, Sec. 4.1 */
+    float   dist_cos_power;     /* exponent of the power-cosine distance weight */
+    float   t_max;              /* distance clamp for misses and far hits; <0: 2*|spacing| */
+    float   thr_low;            /* per-texel change thresholds of Sec. 4.3 (0.25) */
+    float   thr_high;           /* (0.8) */
+    float   thr_step;           /* hysteresis reduction on a large change (0.15) */
+    int32_t state_machine;      /* 1: classify probes (Sec. 6.3); 0: all probes vigilant */
+    int32_t irr_format;         /* DDGI_IRR_* */
+    int32_t dist_format;        /* DDGI_DIST_* */
+    int32_t reserved;
+    uint64_t seed;              /* seed of the per-frame random rotation */
+} ddgi_volume_desc;
+
+/* Allocate a volume: zeroed atlases (Tab. "algtable": uniform
+ * initialisation to 0), all probes UNINIT (VIGILANT when state_machine is
+ * 0), plus the per-frame ray buffer [P*R] of 16-byte records.  Synchronises
+ * the device once.  Errors: INVALID_ARG, OOM. */
+ddgi_status ddgi_volume_create(const ddgi_volume_desc* desc, ddgi_volume* out);
+void ddgi_volume_destroy(ddgi_volume volume);
+
+typedef struct {
+    int64_t n_probes;
+    int64_t irr_tile_texels;        /* (irr_n+2)^2 */
+    int64_t dist_tile_texels;       /* (dist_n+2)^2 */
+    int64_t irr_bytes;              /* atlas sizes in bytes */
+    int64_t dist_bytes;
+    int64_t irr_texel_bytes;
+    int64_t dist_texel_bytes;
+    float   t_max;                  /* resolved distance clamp */
+} ddgi_volume_info;
+ddgi_status ddgi_volume_get_info(ddgi_volume volume, ddgi_volume_info* info);
+
+/* Per-call update parameters. */
+typedef struct {
+    int64_t frame;              /* selects the random rotation of the ray pattern */
+    float   irr_hyst_scale;     /* scene-event scale on hysteresis_irr (Sec. 4.3), 1 = none */
+    float   vis_hyst_scale;     /* scene-event scale on hysteresis_vis */
+    int32_t blend_precision;    /* DDGI_BLEND_* */
+    int32_t reserved;
+} ddgi_update_params;
+
+/* One probe update frame (Sec. 2.3, Sec. 6.3 listing):
+ *   1. rays w_i = R_t * sf(i, R) for i < R, R_t a uniformly random rotation
+ *      drawn from (seed, frame), shared by every probe;
+ *   2. probes in UNINIT are classified by a distance-only trace: OFF when
+ *      more than 25% of rays hit back faces, NEWLY_VIGILANT when a front
+ *      face is closer than the minimum spacing, else SLEEPING;
+ *   3. rays of NEWLY_VIGILANT and VIGILANT probes are traced and shaded
+ *      (sun with shadow ray, emitters, previous-frame probes; back faces
+ *      give radiance 0 and 20% depth, Sec. 4.1);
+ *   4. texels blend the normalised cosine / power-cosine averages with
+ *      gamma encoding and per-texel hysteresis (Eq. 1, Sec. 4.2, 4.3),
+ *      NEWLY_VIGILANT probes with hysteresis 0; borders are copied
+ *      (Sec. 7.1); NEWLY_VIGILANT becomes VIGILANT.
+ * Errors: INVALID_ARG (nothing enqueued), CUDA. */
+ddgi_status ddgi_update(ddgi_volume volume, ddgi_scene scene, const ddgi_lights* lights,
+                        const ddgi_update_params* params, ddgi_stream stream);
+
+/* Irradiance query (Sec. 2.2) at n points: self-shadow bias
+ * (n*0.2 + w_o*0.8)*(0.75*D)*B with w_o towards camera_pos and D the minimum
+ * spacing (Sec. 4.1), then the 8-probe cage with trilinear, backface and
+ * Chebyshev visibility weights, gamma decode (Sec. 4.2).
+ *   pos_dev, nrm_dev [n][3] float (unit normals; a zero normal yields 0)
+ *   out_dev [n][3] float irradiance E.
+ * Errors: INVALID_ARG, CUDA. */
+ddgi_status ddgi_query(ddgi_volume volume, const float* pos_dev, const float* nrm_dev, int64_t n,
+                       const float camera_pos[3], float* out_dev, ddgi_stream stream);
+
+/* Copy out device state (asynchronous, device to device).
+ *   which 0: irradiance atlas, [P][(irr_n+2)^2] texels in irr_format
+ *   which 1: distance atlas,   [P][(dist_n+2)^2] texels in dist_format
+ *   which 2: probe states,     [P] uint8
+ * bytes must equal the buffer's size.  ddgi_set_buffer copies the other way
+ * (restoring a checkpoint or a shard exchanged between devices). */
+ddgi_status ddgi_get_buffer(ddgi_volume volume, int32_t which, void* dst_dev, size_t bytes,
+                            ddgi_stream stream);
+ddgi_status ddgi_set_buffer(ddgi_volume volume, int32_t which, const void* src_dev, size_t bytes,
+                            ddgi_stream stream);
+
+/* Ray records of the last update: records_dev [P*R][4] float (r, g, b, d)
+ * in active-list order, probe_ids_dev [P] int32 (the active list), and the
+ * active count written to *n_active (host; synchronises the stream). */
+ddgi_status ddgi_get_ray_records(ddgi_volume volume, float* records_dev, int32_t* probe_ids_dev,
+                                 int64_t* n_active, ddgi_stream stream);
+
+/* Kernel timing: when enabled, ddgi_update records CUDA events around its
+ * kernels on the update stream; ddgi_read_timings returns the summed
+ * milliseconds per stage since the last read (synchronises the stream):
+ * ms[0] classify, ms[1] lists, ms[2] trace+shade, ms[3] blend+border+states,
+ * ms[4] frame setup; counts[k] launches per stage. */
+ddgi_status ddgi_enable_timing(ddgi_volume volume, int32_t enable);
+ddgi_status ddgi_read_timings(ddgi_volume volume, float ms[5], int32_t counts[5]);
+
+/* Device status word: non-finite texel detected, or a bounded wait that
+ * gave up.  Reads and clears it (synchronises the stream). */
+ddgi_status ddgi_poll_status(ddgi_volume volume, ddgi_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDGI_H */

@@ -1,0 +1,241 @@
+"""Python front end of the C ABI (``include/ddgi.h``).
+
+Argument marshalling only: tensors are passed by device pointer, every step
+of the update and query runs in the CUDA library.  PyTorch provides device
+memory and streams.  Calls enqueue on the current torch stream unless a
+stream is given.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check, load
+
+__all__ = ["Scene", "Volume", "trace", "lights_struct"]
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t: torch.Tensor):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+def _f3(v):
+    return _lib.F3(*[float(x) for x in np.asarray(v, dtype=np.float64).reshape(3)])
+
+
+def lights_struct(lights) -> _lib.Lights:
+    """Any object with sun_dir, sun_irradiance, sky_a, sky_b, sky_up."""
+    return _lib.Lights(_f3(lights.sun_dir), _f3(lights.sun_irradiance), _f3(lights.sky_a),
+                       _f3(lights.sky_b), _f3(lights.sky_up))
+
+
+class Scene:
+    """A registered triangle scene (BVH built on the host, then uploaded)."""
+
+    def __init__(self, verts, tris, tri_object, object_albedo, object_flags, tri_emitter,
+                 emitter_radiance):
+        lib = load()
+        self._arrays = [
+            _np(verts, np.float32).reshape(-1, 3), _np(tris, np.int32).reshape(-1, 3),
+            _np(tri_object, np.int32), _np(object_albedo, np.float32).reshape(-1, 3),
+            _np(object_flags, np.int32), _np(tri_emitter, np.int32),
+            _np(emitter_radiance, np.float32).reshape(-1, 3)]
+        v, t, to, alb, fl, te, er = self._arrays
+        h = C.c_void_p()
+        check(lib.ddgi_scene_create(v.ctypes.data, len(v), t.ctypes.data, len(t), to.ctypes.data,
+                                    len(alb), alb.ctypes.data, fl.ctypes.data, te.ctypes.data,
+                                    len(er), er.ctypes.data if len(er) else None, C.byref(h)))
+        self.handle = h
+        self.n_tris = len(t)
+
+    @classmethod
+    def from_arrays(cls, sc):
+        """From any object with the scene fields (verts, tris, tri_object, ...)."""
+        return cls(sc.verts, sc.tris, sc.tri_object, sc.object_albedo, sc.object_flags,
+                   sc.tri_emitter, sc.emitter_radiance)
+
+    def info(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        check(load().ddgi_scene_info(self.handle, C.byref(a), C.byref(b), C.byref(c)))
+        return {"nodes": a.value, "leaves": b.value, "tris": c.value}
+
+    def trace(self, orig: torch.Tensor, dirs: torch.Tensor, stream=None):
+        n = orig.shape[0]
+        t = torch.empty(n, dtype=torch.float32, device=orig.device)
+        tri = torch.empty(n, dtype=torch.int32, device=orig.device)
+        bf = torch.empty(n, dtype=torch.int32, device=orig.device)
+        check(load().ddgi_trace(self.handle, _ptr(orig), _ptr(dirs), n, _ptr(t), _ptr(tri), _ptr(bf),
+                                _stream(stream)))
+        return t, tri, bf
+
+    def raycast_gbuffer(self, position, forward, up, vfov_deg, width, height, stream=None,
+                        device="cuda"):
+        pos = torch.empty((height * width, 3), dtype=torch.float32, device=device)
+        nrm = torch.empty((height * width, 3), dtype=torch.float32, device=device)
+        check(load().ddgi_raycast_gbuffer(self.handle, _f3(position), _f3(forward), _f3(up),
+                                          float(vfov_deg), int(width), int(height), _ptr(pos),
+                                          _ptr(nrm), _stream(stream)))
+        return pos, nrm
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ddgi_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def desc_struct(d) -> _lib.VolumeDesc:
+    """From any object with the volume fields (origin, spacing, counts, ...)."""
+    s = _lib.VolumeDesc()
+    s.origin = _f3(d.origin)
+    s.spacing = _f3(d.spacing)
+    s.counts = (C.c_int32 * 3)(*[int(x) for x in d.counts])
+    s.rays_per_probe = int(d.rays_per_probe)
+    s.irr_n = int(getattr(d, "irr_n", 6))
+    s.dist_n = int(getattr(d, "dist_n", 14))
+    s.hysteresis_irr = float(d.hysteresis_irr)
+    s.hysteresis_vis = float(d.hysteresis_vis)
+    s.gamma = float(getattr(d, "gamma", 5.0))
+    s.self_shadow_bias = float(getattr(d, "self_shadow_bias", 0.3))
+    s.dist_cos_power = float(getattr(d, "dist_cos_power", 50.0))
+    s.t_max = float(getattr(d, "t_max", -1.0))
+    s.thr_low = float(getattr(d, "thr_low", 0.25))
+    s.thr_high = float(getattr(d, "thr_high", 0.8))
+    s.thr_step = float(getattr(d, "thr_step", 0.15))
+    s.state_machine = int(getattr(d, "state_machine", 1))
+    s.irr_format = int(getattr(d, "irr_format", _lib.IRR_FP32))
+    s.dist_format = int(getattr(d, "dist_format", _lib.DIST_FP32))
+    s.seed = int(getattr(d, "seed", 0))
+    return s
+
+
+class Volume:
+    """A probe volume: atlases, states and the per-frame ray buffer on the device."""
+
+    def __init__(self, desc, irr_format=None, dist_format=None):
+        s = desc_struct(desc)
+        if irr_format is not None:
+            s.irr_format = irr_format
+        if dist_format is not None:
+            s.dist_format = dist_format
+        self.desc = s
+        h = C.c_void_p()
+        check(load().ddgi_volume_create(C.byref(s), C.byref(h)))
+        self.handle = h
+        info = _lib.VolumeInfo()
+        check(load().ddgi_volume_get_info(h, C.byref(info)))
+        self.info = info
+        self.n_probes = info.n_probes
+        self.R = s.rays_per_probe
+
+    def update(self, scene: Scene, lights, frame: int, irr_scale=1.0, vis_scale=1.0,
+               precision=_lib.BLEND_FP32, stream=None):
+        p = _lib.UpdateParams(int(frame), float(irr_scale), float(vis_scale), int(precision), 0)
+        L = lights if isinstance(lights, _lib.Lights) else lights_struct(lights)
+        check(load().ddgi_update(self.handle, scene.handle, C.byref(L), C.byref(p), _stream(stream)))
+
+    def query(self, pos: torch.Tensor, nrm: torch.Tensor, camera, out: torch.Tensor = None,
+              stream=None) -> torch.Tensor:
+        n = pos.shape[0]
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+        check(load().ddgi_query(self.handle, _ptr(pos), _ptr(nrm), n, _f3(camera), _ptr(out),
+                                _stream(stream)))
+        return out
+
+    def _get(self, which, nbytes, stream=None, device="cuda"):
+        buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        check(load().ddgi_get_buffer(self.handle, which, _ptr(buf), nbytes, _stream(stream)))
+        return buf
+
+    def states(self, stream=None) -> torch.Tensor:
+        return self._get(2, self.n_probes, stream)
+
+    def irr_raw(self, stream=None) -> torch.Tensor:
+        return self._get(0, self.info.irr_bytes, stream)
+
+    def dist_raw(self, stream=None) -> torch.Tensor:
+        return self._get(1, self.info.dist_bytes, stream)
+
+    def irr_atlas(self, stream=None) -> torch.Tensor:
+        """Encoded irradiance as float32 [P, n+2, n+2, 3] (FP32 storage only)."""
+        n = self.desc.irr_n + 2
+        raw = self.irr_raw(stream)
+        if self.desc.irr_format == _lib.IRR_FP32:
+            return raw.view(torch.float32).view(self.n_probes, n, n, 3)
+        if self.desc.irr_format == _lib.IRR_FP16:
+            return raw.view(torch.float16).view(self.n_probes, n, n, 4)[..., :3].float()
+        return raw.view(torch.int32).view(self.n_probes, n, n)
+
+    def dist_atlas(self, stream=None) -> torch.Tensor:
+        n = self.desc.dist_n + 2
+        raw = self.dist_raw(stream)
+        if self.desc.dist_format == _lib.DIST_FP32:
+            return raw.view(torch.float32).view(self.n_probes, n, n, 2)
+        return raw.view(torch.float16).view(self.n_probes, n, n, 2).float()
+
+    def set_buffer(self, which: int, src: torch.Tensor, stream=None):
+        check(load().ddgi_set_buffer(self.handle, which, _ptr(src), src.numel() * src.element_size(),
+                                     _stream(stream)))
+
+    def ray_records(self, stream=None):
+        """(records [n_active, R, 4], probe ids [n_active]) of the last update."""
+        rec = torch.empty((self.n_probes * self.R, 4), dtype=torch.float32, device="cuda")
+        ids = torch.empty(self.n_probes, dtype=torch.int32, device="cuda")
+        n = C.c_int64()
+        check(load().ddgi_get_ray_records(self.handle, _ptr(rec), _ptr(ids), C.byref(n),
+                                          _stream(stream)))
+        k = n.value
+        return rec[: k * self.R].view(k, self.R, 4), ids[:k]
+
+    def enable_timing(self, on=True):
+        check(load().ddgi_enable_timing(self.handle, int(bool(on))))
+
+    def read_timings(self):
+        ms = (C.c_float * 5)()
+        cnt = (C.c_int32 * 5)()
+        check(load().ddgi_read_timings(self.handle, ms, cnt))
+        names = ["classify", "lists", "trace_shade", "blend", "frame_setup"]
+        return {n: (ms[i], cnt[i]) for i, n in enumerate(names)}
+
+    def poll_status(self, stream=None):
+        check(load().ddgi_poll_status(self.handle, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ddgi_volume_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def trace(scene: Scene, orig, dirs, stream=None):
+    return scene.trace(orig, dirs, stream)

@@ -1,0 +1,112 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ddgi.h"
+
+namespace ddgi {
+
+// ---------------------------------------------------------------------------
+// Scene on the device.
+//   nodes: 4 float4 per BVH2 node:
+//     [0] child0 (lo.x, hi.x, lo.y, hi.y)  [1] child1 (lo.x, hi.x, lo.y, hi.y)
+//     [2] (c0 lo.z, c0 hi.z, c1 lo.z, c1 hi.z)
+//     [3] int bits (child0, child1, count0, count1); child >= 0 is an inner
+//         node, child < 0 a leaf whose triangles start at ~child.
+//   tris: 3 float4 per triangle in BVH order:
+//     v0 (w = original index bits), v1 (w = flags bits: bit0 casts shadow), v2.
+//   attr: per original triangle (object, emitter).
+// ---------------------------------------------------------------------------
+struct DevScene {
+    const float4* nodes;
+    const float4* tris;
+    const int2*   attr;
+    const float4* albedo;    // per object (r, g, b, flags bits)
+    const float4* emit;      // per emitter (r, g, b, 0)
+    int32_t n_nodes;
+    int32_t n_tris;
+};
+
+struct Lights {
+    float3 sun_dir, sun_irr, sky_a, sky_b, sky_up;
+    int32_t sun_on;
+};
+
+// Volume view passed by value to kernels.
+struct VolView {
+    float3 origin;
+    float3 spacing;
+    float3 inv_spacing;
+    int3   counts;
+    int3   shift;
+    float  min_spacing;
+    float  bias;            // self-shadow bias B
+    float  gamma;
+    float  inv_gamma;
+    float  half_gamma;
+    float  t_max;
+    int32_t irr_n, dist_n;
+    int32_t irr_tile, dist_tile;   // texels per bordered tile
+    int32_t n_probes;
+    int32_t irr_format, dist_format;
+    uint8_t* states;
+    void*    irr;
+    void*    dist;
+};
+
+struct BlendParams {
+    float hyst_irr, hyst_vis;      // already scaled and clamped
+    float thr_low, thr_high, thr_step;
+    int32_t R;
+};
+
+struct FrameRot { double m[9]; };
+
+// Host-side BVH build result.
+struct BvhHost {
+    std::vector<float4> nodes;   // 4 per node
+    std::vector<float4> tris;    // 3 per triangle
+    int64_t n_leaves = 0;
+    int32_t max_depth = 0;
+};
+
+// bvh_build.cpp
+bool build_bvh(const float* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris,
+               const int32_t* tri_flags, BvhHost& out, std::string& err);
+
+// Host rotation generator: SplitMix64 stream for (seed, frame), Shoemake quaternion.
+FrameRot frame_rotation(uint64_t seed, int64_t frame);
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (k_*.cu)
+// ---------------------------------------------------------------------------
+cudaError_t launch_frame_setup(const FrameRot& rot, int R, int irr_n, int dist_n, float cos_power,
+                               float4* dirs, float* w_irr, float* inv_s_irr, float* w_dist,
+                               float* inv_s_dist, cudaStream_t st);
+cudaError_t launch_build_list(const uint8_t* states, int P, int which, int32_t* list,
+                              int32_t* count, cudaStream_t st);
+cudaError_t launch_classify(const DevScene& s, const VolView& v, const float4* dirs, int R,
+                            const int32_t* list, const int32_t* count, int grid, cudaStream_t st);
+cudaError_t launch_trace_shade(const DevScene& s, const VolView& v, const Lights& L,
+                               const float4* dirs, int R, const int32_t* active,
+                               const int32_t* count, float4* records, int grid, cudaStream_t st);
+cudaError_t launch_blend(const VolView& v, const BlendParams& bp, const float* w_irr,
+                         const float* inv_s_irr, const float* w_dist, const float* inv_s_dist,
+                         const float4* records, const int32_t* active, const int32_t* count,
+                         uint32_t* status, int grid, cudaStream_t st);
+cudaError_t launch_query(const VolView& v, const float* pos, const float* nrm, int64_t n,
+                         float3 camera, float* out, cudaStream_t st);
+cudaError_t launch_trace_rays(const DevScene& s, const float* orig, const float* dir, int64_t n,
+                              float* t, int32_t* tri, int32_t* backface, cudaStream_t st);
+cudaError_t launch_gbuffer(const DevScene& s, float3 pos, float3 fwd, float3 right, float3 up,
+                           float tan_half, float aspect, int w, int h, float* out_pos,
+                           float* out_nrm, cudaStream_t st);
+
+int sm_count();
+
+}  // namespace ddgi

@@ -1,0 +1,233 @@
+// Per-frame ray pattern and the probe blend (Sec. 2.3 Eq. 1, Sec. 4.2, 4.3, 7.1).
+//
+// k_frame_setup computes, once per frame and shared by every probe, the ray
+// directions w_i = R_t sf(i, R) and the texel weight matrices
+//   W_irr[t][i]  = max(0, n_t . w_i)              (cosine weight)
+//   W_dist[t][i] = max(0, n_t . w_i)^p            (power-cosine weight)
+// with 1 / sum_i W per texel, in double precision, rounded once to float.
+//
+// k_blend_simt is the plain FP32 blend.  A CTA owns a group of kProbes
+// active probes: their ray records are staged in shared memory (padded
+// stride, conflict-free across probes), each thread computes (texel, probe)
+// dot products over the R rays, and the epilogue normalises, gamma-encodes,
+// applies the per-texel hysteresis thresholds, lerps with the old texel and
+// writes the texel plus the border texels that copy it (the octahedral
+// border copy of Sec. 7.1 fused into the blend).  The probe's state advances
+// Newly Vigilant -> Vigilant after its texels are written.
+#include "probe_math.cuh"
+
+namespace ddgi {
+
+namespace {
+
+__device__ double sf_component(int i, int n, int axis) {
+    const double inv_phi = 0.61803398874989484820;
+    double a = (double)i * inv_phi;
+    double phi = 6.283185307179586477 * (a - floor(a));
+    double z = 1.0 - (2.0 * i + 1.0) / (double)n;
+    double r = sqrt(fmax(0.0, 1.0 - z * z));
+    return axis == 0 ? cos(phi) * r : (axis == 1 ? sin(phi) * r : z);
+}
+
+__device__ void frame_dir(const FrameRot& rot, int i, int n, double out[3]) {
+    double s0 = sf_component(i, n, 0), s1 = sf_component(i, n, 1), s2 = sf_component(i, n, 2);
+    for (int a = 0; a < 3; ++a) out[a] = rot.m[3 * a] * s0 + rot.m[3 * a + 1] * s1 + rot.m[3 * a + 2] * s2;
+}
+
+__device__ void texel_dir(int t, int n, double v[3]) {
+    int i = t % n, j = t / n;
+    double ux = 2.0 * (i + 0.5) / n - 1.0, uy = 2.0 * (j + 0.5) / n - 1.0;
+    double x = ux, y = uy, z = 1.0 - fabs(ux) - fabs(uy);
+    if (z < 0.0) {
+        x = (1.0 - fabs(uy)) * (ux >= 0.0 ? 1.0 : -1.0);
+        y = (1.0 - fabs(ux)) * (uy >= 0.0 ? 1.0 : -1.0);
+    }
+    double l = sqrt(x * x + y * y + z * z);
+    v[0] = x / l;
+    v[1] = y / l;
+    v[2] = z / l;
+}
+
+}  // namespace
+
+// grid: irr_n^2 + dist_n^2 + 1 blocks; block b < irr_n^2 handles irradiance
+// texel b, the next dist_n^2 blocks distance texels, the last one the rays.
+__global__ void __launch_bounds__(256) k_frame_setup(FrameRot rot, int R, int irr_n, int dist_n,
+                                                     double cos_power, float4* dirs, float* w_irr,
+                                                     float* inv_s_irr, float* w_dist,
+                                                     float* inv_s_dist) {
+    __shared__ double red[256];
+    int b = blockIdx.x;
+    int ti = irr_n * irr_n, td = dist_n * dist_n;
+    if (b == ti + td) {
+        for (int i = threadIdx.x; i < R; i += blockDim.x) {
+            double w[3];
+            frame_dir(rot, i, R, w);
+            dirs[i] = make_float4((float)w[0], (float)w[1], (float)w[2], 0.0f);
+        }
+        return;
+    }
+    bool is_irr = b < ti;
+    int t = is_irr ? b : b - ti;
+    double nt[3];
+    texel_dir(t, is_irr ? irr_n : dist_n, nt);
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < R; i += blockDim.x) {
+        double w[3];
+        frame_dir(rot, i, R, w);
+        double c = fmax(0.0, nt[0] * w[0] + nt[1] * w[1] + nt[2] * w[2]);
+        double wt = is_irr ? c : pow(c, cos_power);
+        acc += wt;
+        if (is_irr) w_irr[(int64_t)t * R + i] = (float)wt;
+        else w_dist[(int64_t)t * R + i] = (float)wt;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        float inv = red[0] > 0.0 ? (float)(1.0 / red[0]) : -1.0f;   // -1: no ray in reach
+        if (is_irr) inv_s_irr[t] = inv;
+        else inv_s_dist[t] = inv;
+    }
+}
+
+// Border texels that copy interior texel (x, y) of a bordered tile (tile
+// coordinates, interior spans 1..n): the mirrored neighbour across each seam
+// edge it touches and, for the four interior corners, the opposite outer corner.
+template <typename F>
+__device__ __forceinline__ void for_border_copies(int x, int y, int n, F&& f) {
+    if (x == 1) f(0, n + 1 - y);
+    if (x == n) f(n + 1, n + 1 - y);
+    if (y == 1) f(n + 1 - x, 0);
+    if (y == n) f(n + 1 - x, n + 1);
+    if (x == n && y == n) f(0, 0);
+    if (x == 1 && y == n) f(n + 1, 0);
+    if (x == n && y == 1) f(0, n + 1);
+    if (x == 1 && y == 1) f(n + 1, n + 1);
+}
+
+constexpr int kProbes = 8;
+
+__global__ void __launch_bounds__(256) k_blend_simt(VolView v, BlendParams bp,
+                                                    const float* __restrict__ w_irr,
+                                                    const float* __restrict__ inv_s_irr,
+                                                    const float* __restrict__ w_dist,
+                                                    const float* __restrict__ inv_s_dist,
+                                                    const float4* __restrict__ records,
+                                                    const int32_t* __restrict__ active,
+                                                    const int32_t* __restrict__ count,
+                                                    uint32_t* status) {
+    extern __shared__ float4 srec[];   // kProbes x (R + 1) records
+    __shared__ int s_probe[kProbes];
+    __shared__ int s_newly[kProbes];
+    const int R = bp.R;
+    const int stride = R + 1;
+    const int n_act = *count;
+    const int ni = v.irr_n, nd = v.dist_n;
+    const int ti = ni * ni, td = nd * nd;
+    for (int g0 = blockIdx.x * kProbes; g0 < n_act; g0 += gridDim.x * kProbes) {
+        const int np = min(kProbes, n_act - g0);
+        if (threadIdx.x < np) {
+            int p = active[g0 + threadIdx.x];
+            s_probe[threadIdx.x] = p;
+            s_newly[threadIdx.x] = v.states[p] == DDGI_STATE_NEWLY_VIGILANT;
+        }
+        for (int k = threadIdx.x; k < np * R; k += blockDim.x) {
+            int pp = k / R, i = k - pp * R;
+            srec[pp * stride + i] = records[(int64_t)(g0 + pp) * R + i];
+        }
+        __syncthreads();
+        // irradiance texels: cosine-weighted average, gamma encode, thresholds, lerp
+        for (int q = threadIdx.x; q < ti * np; q += blockDim.x) {
+            int t = q / np, pp = q - t * np;
+            const float* wr = w_irr + (int64_t)t * R;
+            const float4* rr = srec + pp * stride;
+            float ar = 0.0f, ag = 0.0f, ab = 0.0f;
+            for (int i = 0; i < R; ++i) {
+                float w = __ldg(wr + i);
+                float4 L = rr[i];
+                ar = fmaf(w, L.x, ar);
+                ag = fmaf(w, L.y, ag);
+                ab = fmaf(w, L.z, ab);
+            }
+            float inv = __ldg(inv_s_irr + t);
+            int p = s_probe[pp];
+            int x = 1 + t % ni, y = 1 + t / ni;
+            float3 old = load_irr<false>(v, p, x, y);
+            float3 e = old;
+            if (inv >= 0.0f) {
+                float3 en = f3(powf(ar * inv, v.inv_gamma), powf(ag * inv, v.inv_gamma),
+                               powf(ab * inv, v.inv_gamma));
+                float delta = fmaxf(fabsf(en.x - old.x), fmaxf(fabsf(en.y - old.y), fabsf(en.z - old.z)));
+                float a = s_newly[pp] ? 0.0f : bp.hyst_irr;
+                if (delta > bp.thr_low) a = fmaxf(0.0f, a - bp.thr_step);
+                if (delta > bp.thr_high) a = 0.0f;
+                e = f3((1.0f - a) * en.x + a * old.x, (1.0f - a) * en.y + a * old.y,
+                       (1.0f - a) * en.z + a * old.z);
+                if (!(isfinite(e.x) && isfinite(e.y) && isfinite(e.z))) atomicOr(status, 1u);
+            }
+            store_irr(v, p, x, y, e);
+            for_border_copies(x, y, ni, [&](int bx, int by) { store_irr(v, p, bx, by, e); });
+        }
+        // distance texels: power-cosine weighted mean distance and mean squared distance
+        for (int q = threadIdx.x; q < td * np; q += blockDim.x) {
+            int t = q / np, pp = q - t * np;
+            const float* wr = w_dist + (int64_t)t * R;
+            const float4* rr = srec + pp * stride;
+            float m1 = 0.0f, m2 = 0.0f;
+            for (int i = 0; i < R; ++i) {
+                float w = __ldg(wr + i);
+                float d = rr[i].w;
+                float wd = w * d;
+                m1 += wd;
+                m2 = fmaf(wd, d, m2);
+            }
+            float inv = __ldg(inv_s_dist + t);
+            int p = s_probe[pp];
+            int x = 1 + t % nd, y = 1 + t / nd;
+            float2 old = load_dist<false>(v, p, x, y);
+            float2 e = old;
+            if (inv >= 0.0f) {
+                float a = s_newly[pp] ? 0.0f : bp.hyst_vis;
+                e = make_float2((1.0f - a) * (m1 * inv) + a * old.x, (1.0f - a) * (m2 * inv) + a * old.y);
+                if (!(isfinite(e.x) && isfinite(e.y))) atomicOr(status, 1u);
+            }
+            store_dist(v, p, x, y, e);
+            for_border_copies(x, y, nd, [&](int bx, int by) { store_dist(v, p, bx, by, e); });
+        }
+        __syncthreads();
+        if (threadIdx.x < np && s_newly[threadIdx.x]) v.states[s_probe[threadIdx.x]] = DDGI_STATE_VIGILANT;
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_frame_setup(const FrameRot& rot, int R, int irr_n, int dist_n, float cos_power,
+                               float4* dirs, float* w_irr, float* inv_s_irr, float* w_dist,
+                               float* inv_s_dist, cudaStream_t st) {
+    int blocks = irr_n * irr_n + dist_n * dist_n + 1;
+    k_frame_setup<<<blocks, 256, 0, st>>>(rot, R, irr_n, dist_n, (double)cos_power, dirs, w_irr,
+                                          inv_s_irr, w_dist, inv_s_dist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blend(const VolView& v, const BlendParams& bp, const float* w_irr, const float* inv_s_irr,
+                         const float* w_dist, const float* inv_s_dist, const float4* records,
+                         const int32_t* active, const int32_t* count, uint32_t* status, int grid,
+                         cudaStream_t st) {
+    size_t smem = (size_t)kProbes * (bp.R + 1) * sizeof(float4);
+    static int configured_smem = 0;
+    if ((int)smem > configured_smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_blend_simt, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured_smem = (int)smem;
+    }
+    k_blend_simt<<<grid, 256, smem, st>>>(v, bp, w_irr, inv_s_irr, w_dist, inv_s_dist, records, active,
+                                         count, status);
+    return cudaGetLastError();
+}
+
+}  // namespace ddgi

@@ -1,0 +1,272 @@
+// Device math of the probe data structure: octahedral map, bilinear texel
+// filtering of bordered tiles, probe addressing and the biased 8-probe query.
+// Used by the query kernel and by hit shading in the update (the previous
+// frame's probes give the indirect term).
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "ddgi_internal.h"
+
+namespace ddgi {
+
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float length(float3 a) { return sqrtf(dot(a, a)); }
+__device__ __forceinline__ float sgnnz(float x) { return x >= 0.0f ? 1.0f : -1.0f; }
+
+// Octahedral encode (Cigolle et al. 2014): v / |v|_1, lower hemisphere folded.
+__device__ __forceinline__ float2 oct_encode(float3 v) {
+    float l1 = fabsf(v.x) + fabsf(v.y) + fabsf(v.z);
+    float px = v.x / l1, py = v.y / l1;
+    if (v.z < 0.0f) {
+        float qx = (1.0f - fabsf(py)) * sgnnz(px);
+        float qy = (1.0f - fabsf(px)) * sgnnz(py);
+        px = qx;
+        py = qy;
+    }
+    return make_float2(px, py);
+}
+
+// Probe grid addressing: logical (i,j,k) of the window is stored at
+// ((i+shift) mod count, ...); the tracking window moves `shift`.
+__device__ __forceinline__ int wrap(int a, int m) { int r = a % m; return r < 0 ? r + m : r; }
+
+__device__ __forceinline__ int probe_phys(const VolView& v, int i, int j, int k) {
+    int a = wrap(i + v.shift.x, v.counts.x);
+    int b = wrap(j + v.shift.y, v.counts.y);
+    int c = wrap(k + v.shift.z, v.counts.z);
+    return a + v.counts.x * (b + v.counts.y * c);
+}
+
+__device__ __forceinline__ float3 probe_pos_logical(const VolView& v, int i, int j, int k) {
+    return f3(v.origin.x + (float)i * v.spacing.x, v.origin.y + (float)j * v.spacing.y,
+              v.origin.z + (float)k * v.spacing.z);
+}
+
+__device__ __forceinline__ float3 probe_pos_phys(const VolView& v, int p) {
+    int a = p % v.counts.x;
+    int b = (p / v.counts.x) % v.counts.y;
+    int c = p / (v.counts.x * v.counts.y);
+    return probe_pos_logical(v, wrap(a - v.shift.x, v.counts.x), wrap(b - v.shift.y, v.counts.y),
+                             wrap(c - v.shift.z, v.counts.z));
+}
+
+__device__ __forceinline__ bool state_active(uint8_t s) {
+    return s == DDGI_STATE_NEWLY_VIGILANT || s == DDGI_STATE_VIGILANT;
+}
+
+// Bilinear footprint in a bordered tile of n interior texels: the octahedral
+// coordinate [-1,1] spans texel positions [1, n+1]; texel k has its centre at k+0.5.
+struct Footprint {
+    int x0, y0;
+    float tx, ty;
+};
+
+__device__ __forceinline__ Footprint footprint(float2 u, int n) {
+    float sx = 1.0f + (u.x + 1.0f) * 0.5f * (float)n - 0.5f;
+    float sy = 1.0f + (u.y + 1.0f) * 0.5f * (float)n - 0.5f;
+    float fx = floorf(sx), fy = floorf(sy);
+    int x0 = (int)fx, y0 = (int)fy;
+    x0 = min(max(x0, 0), n);
+    y0 = min(max(y0, 0), n);
+    Footprint f;
+    f.x0 = x0;
+    f.y0 = y0;
+    f.tx = sx - (float)x0;
+    f.ty = sy - (float)y0;
+    return f;
+}
+
+// ---- texel storage formats -------------------------------------------------
+// Irradiance FP32: 3 floats per texel.  FP16: 4 halves (rgb + pad).
+// RGB9E5: one 32-bit word, 9-bit mantissas with a shared 5-bit exponent
+// (bias 15), as in the OpenGL EXT_texture_shared_exponent specification.
+
+__device__ __forceinline__ float3 rgb9e5_decode(uint32_t w) {
+    int e = (int)(w >> 27) - 15 - 9;
+    float s = ldexpf(1.0f, e);
+    return f3((float)(w & 511u) * s, (float)((w >> 9) & 511u) * s, (float)((w >> 18) & 511u) * s);
+}
+
+__device__ __forceinline__ uint32_t rgb9e5_encode(float3 c) {
+    const float kMax = 65408.0f;   // (511/512) * 2^16
+    float r = fminf(fmaxf(c.x, 0.0f), kMax);
+    float g = fminf(fmaxf(c.y, 0.0f), kMax);
+    float b = fminf(fmaxf(c.z, 0.0f), kMax);
+    float mx = fmaxf(r, fmaxf(g, b));
+    if (!(mx > 0.0f)) return 0u;
+    // exponent such that mx / 2^(e-15-9) < 512, e >= 0
+    int ex;
+    frexpf(mx, &ex);                       // mx = m * 2^ex, m in [0.5, 1)
+    int e = max(-16, ex - 1) + 1 + 15;     // shared exponent (biased)
+    if (e < 0) e = 0;
+    float s = ldexpf(1.0f, -(e - 15 - 9));
+    int mmax = (int)floorf(mx * s + 0.5f);
+    if (mmax == 512) { e += 1; s *= 0.5f; }
+    if (e > 31) e = 31;
+    uint32_t ir = (uint32_t)min(511, (int)floorf(r * s + 0.5f));
+    uint32_t ig = (uint32_t)min(511, (int)floorf(g * s + 0.5f));
+    uint32_t ib = (uint32_t)min(511, (int)floorf(b * s + 0.5f));
+    return ir | (ig << 9) | (ib << 18) | ((uint32_t)e << 27);
+}
+
+// NC = true reads through the non-coherent (read-only) path: only for
+// kernels that do not write the atlas.
+template <bool NC>
+__device__ __forceinline__ float ld(const float* p) { if (NC) return __ldg(p); else return *p; }
+template <bool NC>
+__device__ __forceinline__ uint32_t ld(const uint32_t* p) { if (NC) return __ldg(p); else return *p; }
+template <bool NC>
+__device__ __forceinline__ uint2 ld(const uint2* p) { if (NC) return __ldg(p); else return *p; }
+template <bool NC>
+__device__ __forceinline__ float2 ld(const float2* p) { if (NC) return __ldg(p); else return *p; }
+
+template <bool NC = true>
+__device__ __forceinline__ float3 load_irr(const VolView& v, int p, int x, int y) {
+    int64_t t = (int64_t)p * v.irr_tile + (int64_t)y * (v.irr_n + 2) + x;
+    if (v.irr_format == DDGI_IRR_FP32) {
+        const float* a = (const float*)v.irr + 3 * t;
+        return f3(ld<NC>(a), ld<NC>(a + 1), ld<NC>(a + 2));
+    } else if (v.irr_format == DDGI_IRR_FP16) {
+        uint2 w = ld<NC>((const uint2*)v.irr + t);
+        __half2 h0 = *reinterpret_cast<__half2*>(&w.x);
+        __half2 h1 = *reinterpret_cast<__half2*>(&w.y);
+        float2 a = __half22float2(h0);
+        return f3(a.x, a.y, __low2float(h1));
+    } else {
+        return rgb9e5_decode(ld<NC>((const uint32_t*)v.irr + t));
+    }
+}
+
+__device__ __forceinline__ void store_irr(const VolView& v, int p, int x, int y, float3 c) {
+    int64_t t = (int64_t)p * v.irr_tile + (int64_t)y * (v.irr_n + 2) + x;
+    if (v.irr_format == DDGI_IRR_FP32) {
+        float* a = (float*)v.irr + 3 * t;
+        a[0] = c.x; a[1] = c.y; a[2] = c.z;
+    } else if (v.irr_format == DDGI_IRR_FP16) {
+        __half2 h0 = __floats2half2_rn(c.x, c.y);
+        __half2 h1 = __floats2half2_rn(c.z, 0.0f);
+        uint2 w;
+        w.x = *reinterpret_cast<uint32_t*>(&h0);
+        w.y = *reinterpret_cast<uint32_t*>(&h1);
+        ((uint2*)v.irr)[t] = w;
+    } else {
+        ((uint32_t*)v.irr)[t] = rgb9e5_encode(c);
+    }
+}
+
+template <bool NC = true>
+__device__ __forceinline__ float2 load_dist(const VolView& v, int p, int x, int y) {
+    int64_t t = (int64_t)p * v.dist_tile + (int64_t)y * (v.dist_n + 2) + x;
+    if (v.dist_format == DDGI_DIST_FP32) {
+        return ld<NC>((const float2*)v.dist + t);
+    } else {
+        uint32_t w = ld<NC>((const uint32_t*)v.dist + t);
+        return __half22float2(*reinterpret_cast<__half2*>(&w));
+    }
+}
+
+__device__ __forceinline__ void store_dist(const VolView& v, int p, int x, int y, float2 m) {
+    int64_t t = (int64_t)p * v.dist_tile + (int64_t)y * (v.dist_n + 2) + x;
+    if (v.dist_format == DDGI_DIST_FP32) {
+        ((float2*)v.dist)[t] = m;
+    } else {
+        __half2 h = __floats2half2_rn(m.x, m.y);
+        ((uint32_t*)v.dist)[t] = *reinterpret_cast<uint32_t*>(&h);
+    }
+}
+
+__device__ __forceinline__ float3 sample_irr(const VolView& v, int p, float3 dir) {
+    Footprint f = footprint(oct_encode(dir), v.irr_n);
+    float3 a = load_irr(v, p, f.x0, f.y0), b = load_irr(v, p, f.x0 + 1, f.y0);
+    float3 c = load_irr(v, p, f.x0, f.y0 + 1), d = load_irr(v, p, f.x0 + 1, f.y0 + 1);
+    float w00 = (1.0f - f.tx) * (1.0f - f.ty), w10 = f.tx * (1.0f - f.ty);
+    float w01 = (1.0f - f.tx) * f.ty, w11 = f.tx * f.ty;
+    return f3(w00 * a.x + w10 * b.x + w01 * c.x + w11 * d.x,
+              w00 * a.y + w10 * b.y + w01 * c.y + w11 * d.y,
+              w00 * a.z + w10 * b.z + w01 * c.z + w11 * d.z);
+}
+
+__device__ __forceinline__ float2 sample_dist(const VolView& v, int p, float3 dir) {
+    Footprint f = footprint(oct_encode(dir), v.dist_n);
+    float2 a = load_dist(v, p, f.x0, f.y0), b = load_dist(v, p, f.x0 + 1, f.y0);
+    float2 c = load_dist(v, p, f.x0, f.y0 + 1), d = load_dist(v, p, f.x0 + 1, f.y0 + 1);
+    float w00 = (1.0f - f.tx) * (1.0f - f.ty), w10 = f.tx * (1.0f - f.ty);
+    float w01 = (1.0f - f.tx) * f.ty, w11 = f.tx * f.ty;
+    return make_float2(w00 * a.x + w10 * b.x + w01 * c.x + w11 * d.x,
+                       w00 * a.y + w10 * b.y + w01 * c.y + w11 * d.y);
+}
+
+// x^(gamma/2) on the gamma-encoded value; gamma = 5 uses x^2 sqrt(x).
+__device__ __forceinline__ float gamma_decode_half(float e, float half_gamma) {
+    e = fmaxf(e, 0.0f);
+    if (half_gamma == 2.5f) return e * e * sqrtf(e);
+    if (half_gamma == 0.5f) return sqrtf(e);
+    return powf(e, half_gamma);
+}
+
+// Cosine-weighted mean radiance M at x with normal n, the self-shadow bias
+// using w_o (Sec. 4.1 equation), the 8-probe cage (Sec. 2.2): trilinear,
+// backface ((1 + n.w_p)/2)^2 + 0.2, Chebyshev visibility, weight floor
+// 1e-6 * w_t * w_b, gamma decode (Sec. 4.2) normalised before squaring.
+__device__ __forceinline__ float3 query_M(const VolView& v, float3 x, float3 n, float3 wo) {
+    float k = 0.75f * v.min_spacing * v.bias;
+    float3 xb = f3(x.x + (0.2f * n.x + 0.8f * wo.x) * k, x.y + (0.2f * n.y + 0.8f * wo.y) * k,
+                   x.z + (0.2f * n.z + 0.8f * wo.z) * k);
+    float g[3] = {(xb.x - v.origin.x) / v.spacing.x, (xb.y - v.origin.y) / v.spacing.y,
+                  (xb.z - v.origin.z) / v.spacing.z};
+    int cnt[3] = {v.counts.x, v.counts.y, v.counts.z};
+    int base[3];
+    float fr[3];
+    for (int a = 0; a < 3; ++a) {
+        float b = floorf(g[a]);
+        b = fminf(fmaxf(b, 0.0f), (float)(cnt[a] - 2));
+        base[a] = (int)b;
+        fr[a] = fminf(fmaxf(g[a] - b, 0.0f), 1.0f);
+    }
+    float sumw = 0.0f;
+    float3 acc = f3(0.0f, 0.0f, 0.0f);
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+        int o0 = c & 1, o1 = (c >> 1) & 1, o2 = (c >> 2) & 1;
+        int p = probe_phys(v, base[0] + o0, base[1] + o1, base[2] + o2);
+        if (!state_active(v.states[p])) continue;
+        float3 xp = probe_pos_logical(v, base[0] + o0, base[1] + o1, base[2] + o2);
+        float wt = (o0 ? fr[0] : 1.0f - fr[0]) * (o1 ? fr[1] : 1.0f - fr[1]) * (o2 ? fr[2] : 1.0f - fr[2]);
+        float3 dp = xp - x;
+        float ldp = length(dp);
+        float cw = ldp > 0.0f ? dot(n, dp) / ldp : 1.0f;
+        float hb = (1.0f + cw) * 0.5f;
+        float wb = hb * hb + 0.2f;
+        float3 pv = xb - xp;
+        float r = length(pv);
+        float wc = 1.0f;
+        if (r > 0.0f) {
+            float2 mom = sample_dist(v, p, (1.0f / r) * pv);
+            if (r > mom.x) {
+                float var = fmaxf(mom.y - mom.x * mom.x, 0.0f);
+                float dr = r - mom.x;
+                wc = var / (var + dr * dr);
+            }
+        }
+        float w = wt * wb * fmaxf(wc, 1e-6f);
+        float3 e = sample_irr(v, p, n);
+        acc.x += w * gamma_decode_half(e.x, v.half_gamma);
+        acc.y += w * gamma_decode_half(e.y, v.half_gamma);
+        acc.z += w * gamma_decode_half(e.z, v.half_gamma);
+        sumw += w;
+    }
+    if (!(sumw > 0.0f)) return f3(0.0f, 0.0f, 0.0f);
+    float inv = 1.0f / sumw;
+    float3 a = inv * acc;
+    return f3(a.x * a.x, a.y * a.y, a.z * a.z);
+}
+
+}  // namespace ddgi

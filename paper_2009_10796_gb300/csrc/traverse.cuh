@@ -1,0 +1,157 @@
+// BVH2 traversal with the watertight ray/triangle test of Woop, Benthin and
+// Wald ("Watertight Ray/Triangle Intersection", JCGT 2013).  The edge
+// functions are evaluated with explicitly rounded products and differences
+// (no fused multiply-add), so a shared edge gives bitwise-negated values in
+// its two triangles and rays cannot slip between them.  Box tests are made
+// conservative by widening the exit distance by a few ulps (Ize, "Robust
+// BVH Ray Traversal", JCGT 2013).
+#pragma once
+
+#include <cfloat>
+
+#include "probe_math.cuh"
+
+namespace ddgi {
+
+constexpr int kStackSize = 64;
+
+struct RayPre {
+    float3 o, d, idir;
+    int kx, ky, kz;
+    float Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+__device__ __forceinline__ RayPre ray_pre(float3 o, float3 d) {
+    RayPre r;
+    r.o = o;
+    r.d = d;
+    float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    int kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    float dz = comp(d, kz);
+    if (dz < 0.0f) { int t = kx; kx = ky; ky = t; }
+    r.kx = kx;
+    r.ky = ky;
+    r.kz = kz;
+    r.Sx = comp(d, kx) / dz;
+    r.Sy = comp(d, ky) / dz;
+    r.Sz = 1.0f / dz;
+    const float eps = 1e-20f;
+    r.idir = f3(1.0f / (fabsf(d.x) > eps ? d.x : copysignf(eps, d.x)),
+                1.0f / (fabsf(d.y) > eps ? d.y : copysignf(eps, d.y)),
+                1.0f / (fabsf(d.z) > eps ? d.z : copysignf(eps, d.z)));
+    return r;
+}
+
+// Returns t of a hit in (0, inf) or -1.
+__device__ __forceinline__ float tri_hit(const RayPre& r, float4 p0, float4 p1, float4 p2) {
+    float3 A = f3(p0.x - r.o.x, p0.y - r.o.y, p0.z - r.o.z);
+    float3 B = f3(p1.x - r.o.x, p1.y - r.o.y, p1.z - r.o.z);
+    float3 C = f3(p2.x - r.o.x, p2.y - r.o.y, p2.z - r.o.z);
+    float Akz = comp(A, r.kz), Bkz = comp(B, r.kz), Ckz = comp(C, r.kz);
+    float Ax = __fsub_rn(comp(A, r.kx), __fmul_rn(r.Sx, Akz));
+    float Ay = __fsub_rn(comp(A, r.ky), __fmul_rn(r.Sy, Akz));
+    float Bx = __fsub_rn(comp(B, r.kx), __fmul_rn(r.Sx, Bkz));
+    float By = __fsub_rn(comp(B, r.ky), __fmul_rn(r.Sy, Bkz));
+    float Cx = __fsub_rn(comp(C, r.kx), __fmul_rn(r.Sx, Ckz));
+    float Cy = __fsub_rn(comp(C, r.ky), __fmul_rn(r.Sy, Ckz));
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        // exact edge case: re-evaluate the edge functions in double precision
+        U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+        V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+        W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return -1.0f;
+    float det = U + V + W;
+    if (det == 0.0f) return -1.0f;
+    float T = U * (r.Sz * Akz) + V * (r.Sz * Bkz) + W * (r.Sz * Ckz);
+    float t = T / det;
+    return t > 0.0f ? t : -1.0f;
+}
+
+struct Hit {
+    float t;
+    int32_t orig;   // original triangle index, -1 = miss
+    int32_t k;      // BVH-order triangle index
+};
+
+// Slab test of one child box; returns entry distance or +inf when missed.
+__device__ __forceinline__ float box_enter(const RayPre& r, float lx, float hx, float ly, float hy,
+                                           float lz, float hz, float tmax) {
+    float t0x = (lx - r.o.x) * r.idir.x, t1x = (hx - r.o.x) * r.idir.x;
+    float t0y = (ly - r.o.y) * r.idir.y, t1y = (hy - r.o.y) * r.idir.y;
+    float t0z = (lz - r.o.z) * r.idir.z, t1z = (hz - r.o.z) * r.idir.z;
+    float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.0f));
+    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tmax));
+    return tn <= tf * 1.0000005f ? tn : INFINITY;
+}
+
+// Closest hit (ANY = false) or any hit among shadow casters (ANY = true).
+template <bool ANY>
+__device__ __forceinline__ Hit traverse(const DevScene& s, const RayPre& r) {
+    Hit h;
+    h.t = INFINITY;
+    h.orig = -1;
+    h.k = -1;
+    if (s.n_nodes == 0) return h;
+    int stack[kStackSize];
+    int sp = 0;
+    int node = 0;
+    while (true) {
+        const float4* N = s.nodes + 4 * (int64_t)node;
+        float4 a = __ldg(N), b = __ldg(N + 1), z = __ldg(N + 2);
+        int4 m = __ldg(reinterpret_cast<const int4*>(N + 3));
+        float e0 = box_enter(r, a.x, a.y, a.z, a.w, z.x, z.y, h.t);
+        float e1 = box_enter(r, b.x, b.y, b.z, b.w, z.z, z.w, h.t);
+        bool h0 = e0 != INFINITY, h1 = e1 != INFINITY;
+#pragma unroll 1
+        for (int c = 0; c < 2; ++c) {
+            int child = c == 0 ? m.x : m.y;
+            bool hitc = c == 0 ? h0 : h1;
+            if (!hitc || child >= 0) continue;
+            int first = ~child, cnt = c == 0 ? m.z : m.w;
+            for (int k = first; k < first + cnt; ++k) {
+                const float4* T = s.tris + 3 * (int64_t)k;
+                float4 p0 = __ldg(T), p1 = __ldg(T + 1), p2 = __ldg(T + 2);
+                if (ANY && !(__float_as_int(p1.w) & 1)) continue;
+                float t = tri_hit(r, p0, p1, p2);
+                if (t < 0.0f) continue;
+                int orig = __float_as_int(p0.w);
+                if (ANY) {
+                    h.t = t;
+                    h.orig = orig;
+                    h.k = k;
+                    return h;
+                }
+                if (t < h.t || (t == h.t && orig < h.orig)) {
+                    h.t = t;
+                    h.orig = orig;
+                    h.k = k;
+                }
+            }
+            if (c == 0) h0 = false; else h1 = false;
+        }
+        if (h0 && h1) {
+            bool first0 = e0 <= e1;
+            int nearc = first0 ? m.x : m.y, farc = first0 ? m.y : m.x;
+            if (sp < kStackSize) stack[sp++] = farc;
+            node = nearc;
+        } else if (h0) {
+            node = m.x;
+        } else if (h1) {
+            node = m.y;
+        } else {
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+    }
+    return h;
+}
+
+}  // namespace ddgi

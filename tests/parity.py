@@ -1,0 +1,90 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path and the oracle on
+the same seeded inputs and compare them element by element.
+
+Tolerances (FP32 device arithmetic against the FP64 oracle):
+  * states and hit/miss: bit-exact, except rays whose FP32 and FP64 results
+    legitimately differ (grazing a triangle edge or silhouette within float
+    rounding); those are counted, reported and must stay rare.
+  * texels and query outputs: |gpu - oracle| <= 1e-4 * max(|oracle|, 1e-3 * max|oracle|);
+    texels touched with weight > 1e-3 of their row by a flagged ray are
+    listed and excluded.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle
+import synth
+
+REL = 1e-4
+
+
+def rel_err(got, ref, floor_frac=1e-3):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = np.maximum(np.abs(ref), floor_frac * max(np.abs(ref).max(), 1e-30))
+    return np.abs(got - ref) / scale
+
+
+def to_dev(a, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def gpu_rays_by_probe(vol):
+    rec, ids = vol.ray_records()
+    return rec.cpu().numpy().astype(np.float64), ids.cpu().numpy().astype(np.int64)
+
+
+def compare_rays(gpu_rec, gpu_ids, or_rays, rtol=1e-4):
+    """Per-ray comparison.  Returns (bad mask [n_active, R], probe ids)."""
+    ref = or_rays[gpu_ids]                                  # [n, R, 4]
+    assert not np.isnan(ref).any(), "GPU traced a probe the oracle did not"
+    scale = np.maximum(np.abs(ref), 1e-3 * np.maximum(np.abs(ref).max(axis=(0, 1)), 1e-30))
+    err = np.abs(gpu_rec - ref) / scale
+    bad = (err > rtol).any(axis=-1)
+    return bad, err
+
+
+def texel_weights(desc, seed, frame):
+    """Weights used by each texel (for masking texels touched by flagged rays)."""
+    dirs = oracle.frame_dirs(seed, frame, desc.rays_per_probe)
+    ti = oracle.texel_dirs(desc.irr_n).reshape(-1, 3)
+    td = oracle.texel_dirs(desc.dist_n).reshape(-1, 3)
+    wi = np.maximum(0.0, ti @ dirs.T)
+    wd = np.maximum(0.0, td @ dirs.T) ** desc.dist_cos_power
+    wi = wi / np.maximum(wi.sum(1, keepdims=True), 1e-300)
+    wd = wd / np.maximum(wd.sum(1, keepdims=True), 1e-300)
+    return wi, wd
+
+
+def border_sources(n):
+    """For each bordered-tile texel, the interior texel index (row-major over n x n) it holds."""
+    N = n + 2
+    tile = np.zeros((N, N, 1))
+    tile[1:-1, 1:-1, 0] = np.arange(n * n).reshape(n, n)
+    tile = oracle.border_copy(tile, n)
+    return tile[..., 0].astype(np.int64)
+
+
+def masked_texels(desc, seed, frame, bad, ids):
+    """Boolean masks [P, N, N] of texels influenced (> 1e-3 of their weight) by flagged rays."""
+    P = desc.n_probes
+    wi, wd = texel_weights(desc, seed, frame)
+    mi = np.zeros((P, desc.irr_n ** 2), dtype=bool)
+    md = np.zeros((P, desc.dist_n ** 2), dtype=bool)
+    for k in np.nonzero(bad.any(axis=1))[0]:
+        rays = np.nonzero(bad[k])[0]
+        mi[ids[k]] |= wi[:, rays].sum(1) > 1e-3
+        md[ids[k]] |= wd[:, rays].sum(1) > 1e-3
+    si, sd = border_sources(desc.irr_n), border_sources(desc.dist_n)
+    return mi[:, si], md[:, sd]
+
+
+def run_oracle(sc, lights, desc, frames, subset=None):
+    h = oracle.SceneHandle(sc)
+    st, irr, dist = oracle.new_state(desc)
+    rays = []
+    for f in frames:
+        rays.append(oracle.update(h, lights, desc, f, st, irr, dist, subset=subset, want_rays=True))
+    return st, irr, dist, rays
