@@ -1,0 +1,379 @@
+"""Benchmark: probe update + 1080p query on the procedural-city workload.
+
+One step = one full pass of the hot path over one frame: per-frame ray
+pattern, classification of uninitialised probes, active-probe compaction,
+trace + shade of every active probe's rays, blend with border copy and state
+advance, then the irradiance query of every pixel of a 1920x1080 G-buffer.
+
+Workload: 32x16x32 probes (16,384) at 2 m over a seeded city of 16,384 box
+buildings (196,610 triangles), 256 rays per probe, hysteresis 0.97, per-frame
+random rotation, multi-bounce, probe state machine on; the G-buffer comes
+from a seeded pinhole camera raycast into the same scene.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload instead (the CPU baseline arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "probe-update ms/frame & Grays/s at 16k probes; query ms at 1080p vs FP32 plain"
+WORKLOAD = ("city 32x16x32 probes @ 2 m, 196,610 tris, 256 rays/probe, hysteresis 0.97, "
+            "multi-bounce, state machine on, 1920x1080 G-buffer query")
+# FP32 lane operations counted per unit of work of the trace + shade kernel
+# (see the design notes: slab tests, watertight triangle test, hit shading).
+OPS_PER_NODE = 50
+OPS_PER_TRI = 30
+OPS_PER_QUERY = 700
+OPS_PER_RAY = 60
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        if self.file is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def make_workload():
+    sc = synth.city_scene()
+    return sc, synth.city_volume(), synth.city_lights(), synth.city_camera()
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# ----------------------------------------------------------------------------
+
+def oracle_step_estimate(sc, desc, L, n_active, R, n_pixels, subset, n_query_sample, frame=5):
+    """Time the oracle's update of the active probes in `subset` and its query
+    of `n_query_sample` surface points; extrapolate to one full step."""
+    import oracle
+    h = oracle.SceneHandle(sc)
+    st, irr, dist = oracle.new_state(desc)
+    st[:] = oracle.VIGILANT       # steady-state frame: every sampled probe traces
+    n_probe_sample = len(subset)
+    t0 = time.perf_counter()
+    oracle.update(h, L, desc, frame, st, irr, dist, subset=subset)
+    t_upd = time.perf_counter() - t0
+    pts, nrm = synth.surface_points(sc, n_query_sample, seed=3002)
+    t0 = time.perf_counter()
+    oracle.query(desc, st, irr, dist, pts, nrm, np.array([0.0, 12.0, -28.0]))
+    t_q = time.perf_counter() - t0
+    t_step = t_upd * (n_active / n_probe_sample) + t_q * (n_pixels / n_query_sample)
+    return t_step, t_upd, t_q
+
+
+def oracle_active_count(sc, desc, n_sample=128, seed=11):
+    """The oracle's own estimate of the active-probe count: classify a random
+    probe sample at frame 0 and scale the newly-vigilant fraction.  Returns the
+    estimate and the sampled probes found active."""
+    import oracle
+    st = np.zeros(desc.n_probes, dtype=np.uint8)
+    ids = np.sort(np.random.default_rng(seed).choice(desc.n_probes, n_sample, replace=False))
+    oracle.classify(oracle.SceneHandle(sc), desc, 0, ids, st)
+    act = ids[st[ids] == oracle.NEWLY_VIGILANT]
+    return max(1, int(round(len(act) / n_sample * desc.n_probes))), act
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, timed on the host cores on a
+    bounded sample per step, extrapolated to the same metric and unit."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc, desc, L, cam = make_workload()
+    n_active, act = oracle_active_count(sc, desc)
+    R = desc.rays_per_probe
+    n_pix = cam.width * cam.height
+    n_qs = 4096
+    n_ps = min(len(act), 16)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t_step, _, _ = oracle_step_estimate(sc, desc, L, n_active, R, n_pix, act[:n_ps], n_qs,
+                                            frame=k)
+        if k >= args.warmup:
+            times.append(t_step)
+    ms = 1e3 * float(np.mean(times))
+    value = n_active * R / (ms * 1e-3) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Grays/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "cpu"},
+        "cpu_baseline": {"value": value, "unit": "Grays/s", "cores": cores(), "kind": "oracle",
+                         "sample": f"{n_ps} active probes (one update) + {n_qs} query points per "
+                                   f"step, extrapolated to {n_active} active probes (oracle's own "
+                                   f"estimate from 128 classified probes) x {R} rays + {n_pix} pixels"},
+        "e2e": {"value": value, "unit": "Grays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2009_10796_gb300 as g
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    sc, desc, L, cam = make_workload()
+    scene = g.Scene.from_arrays(sc)
+    vol = g.Volume(desc)
+    pos, nrm = scene.raycast_gbuffer(cam.position, cam.forward, cam.up, cam.vfov_deg, cam.width,
+                                     cam.height, device=dev)
+    n_pix = pos.shape[0]
+    out = torch.empty_like(pos)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    camera = cam.position
+
+    def step(frame):
+        vol.update(scene, L, frame, stream=stream)
+        vol.query(pos, nrm, camera, out, stream=stream)
+
+    frame = 0
+    for _ in range(args.warmup):
+        step(frame)
+        frame += 1
+    torch.cuda.synchronize()
+    vol.poll_status()
+    n_active = int((vol.states() == g.STATE_VIGILANT).sum().item())
+    R = desc.rays_per_probe
+    stats = vol.trace_stats(scene, L)
+    vol.read_timings()
+    vol.enable_timing(True)
+
+    # device-timed steps; L2 flushed between steps outside the events
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    qev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            vol.update(scene, L, frame, stream=stream)
+            qev[k][0].record(stream)
+            vol.query(pos, nrm, camera, out, stream=stream)
+            qev[k][1].record(stream)
+            evs[k][1].record(stream)
+            frame += 1
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    query_ms = [a.elapsed_time(b) for a, b in qev]
+    timings = vol.read_timings()
+    vol.enable_timing(False)
+    ms = float(np.mean(step_ms))
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    rays_per_step = n_active * R
+    value = world * rays_per_step / (ms_max * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers: pinned G-buffer in,
+    # irradiance out, every step
+    pos_h = pos.cpu().pin_memory()
+    nrm_h = nrm.cpu().pin_memory()
+    out_h = torch.empty_like(pos_h).pin_memory()
+    pos_d = torch.empty_like(pos)
+    nrm_d = torch.empty_like(nrm)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        pos_d.copy_(pos_h, non_blocking=True)
+        nrm_d.copy_(nrm_h, non_blocking=True)
+        vol.update(scene, L, frame, stream=stream)
+        vol.query(pos_d, nrm_d, camera, out, stream=stream)
+        out_h.copy_(out, non_blocking=True)
+        frame += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([e2e_ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * rays_per_step / (float(t.item()) * 1e-3) / 1e9
+    vol.poll_status()
+
+    # roofline of the dominant kernel (trace + shade): counted FP32 lane ops
+    # per launch / its event-timed duration; peak = lanes x max SM clock
+    pk, pk_kind = peaks()
+    trace_ms, trace_n = timings["trace_shade"]
+    trace_ms_avg = trace_ms / max(trace_n, 1)
+    ops = (OPS_PER_NODE * (stats["nodes"] + stats["shadow_nodes"])
+           + OPS_PER_TRI * (stats["tris"] + stats["shadow_tris"])
+           + OPS_PER_QUERY * stats["queries"] + OPS_PER_RAY * stats["rays"])
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tops = sm_count * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = ops / (trace_ms_avg * 1e-3) / 1e12
+    blend_ms = timings["blend"][0] / max(timings["blend"][1], 1)
+    blend_bytes = n_active * (R * 16 + 2000 + 2816)      # records in, old interior in, tiles out
+    q_ms = float(np.mean(query_ms))
+    q_bytes = n_pix * 36                                  # positions + normals in, irradiance out
+    hbm = pk.get("hbm_gbs", 6800.0)
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        n_act_cpu, act = oracle_active_count(sc, desc)
+        t_step, t_upd, t_q = oracle_step_estimate(sc, desc, L, n_act_cpu, R, n_pix, act, 16384)
+        cpu = {"value": n_act_cpu * R / t_step / 1e9, "unit": "Grays/s", "cores": cores(),
+               "kind": "oracle",
+               "sample": f"{len(act)} active probes x {R} rays (one update, {t_upd:.1f} s) + 16384 "
+                         f"query points "
+                         f"({t_q:.2f} s), extrapolated to {n_act_cpu} active probes (oracle's own "
+                         f"estimate) + {n_pix} pixels"}
+    launches_per_step = 7   # frame setup, 2 list builds, classify, trace+shade, blend, query
+    line = {
+        "metric": METRIC, "value": value, "unit": "Grays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "probes": desc.n_probes, "active_probes": n_active,
+                   "rays_per_probe": R, "query_pixels": n_pix,
+                   "l2": "flushed between timed steps (256 MiB write outside the events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "update_ms_per_frame": ms - q_ms, "query_ms_1080p": q_ms,
+        "trace_grays_per_s": rays_per_step / (trace_ms_avg * 1e-3) / 1e9,
+        "stage_ms": {k: v[0] / max(v[1], 1) for k, v in timings.items()},
+        "wall_ms_per_step": 1e3 * wall / args.steps,
+        "trace_work_per_ray": {"nodes": stats["nodes"] / max(stats["rays"], 1),
+                               "tris": stats["tris"] / max(stats["rays"], 1),
+                               "shadow_rays": stats["shadow_rays"] / max(stats["rays"], 1),
+                               "queries": stats["queries"] / max(stats["rays"], 1)},
+        "roofline": {"bound": "alu", "kernel": "k_trace_shade", "achieved": achieved,
+                     "peak": peak_tops, "unit": "TFLOP/s", "frac": achieved / peak_tops,
+                     "traffic": None, "peak_kind": f"FP32 lanes x max SM clock ({pk_kind} clock)"},
+        "roofline_blend": {"bound": "hbm", "achieved": blend_bytes / (blend_ms * 1e-3) / 1e9,
+                           "peak": hbm, "unit": "GB/s",
+                           "frac": blend_bytes / (blend_ms * 1e-3) / 1e9 / hbm},
+        "roofline_query": {"bound": "hbm", "achieved": q_bytes / (q_ms * 1e-3) / 1e9, "peak": hbm,
+                           "unit": "GB/s", "frac": q_bytes / (q_ms * 1e-3) / 1e9 / hbm},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "Grays/s", "h2d_bytes_per_step": 2 * n_pix * 12,
+                "d2h_bytes_per_step": n_pix * 12},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -245,6 +245,16 @@ ddgi_status ddgi_get_ray_records(ddgi_volume volume, float* records_dev, int32_t
 ddgi_status ddgi_enable_timing(ddgi_volume volume, int32_t enable);
 ddgi_status ddgi_read_timings(ddgi_volume volume, float ms[5], int32_t counts[5]);
 
+/* Work counters of the last update's trace (measurement only; the update
+ * itself runs uninstrumented).  Re-traces the last update's rays of its
+ * active probes with a counting variant of the trace + shade kernel and
+ * writes, summed over rays: stats[0] primary rays, [1] primary node visits,
+ * [2] primary triangle tests, [3] shadow rays, [4] shadow node visits,
+ * [5] shadow triangle tests, [6] probe queries at hits.  Synchronises the
+ * stream.  Errors: INVALID_ARG (no update yet), CUDA. */
+ddgi_status ddgi_trace_stats(ddgi_volume volume, ddgi_scene scene, const ddgi_lights* lights,
+                             uint64_t stats[7], ddgi_stream stream);
+
 /* Device status word: non-finite texel detected, or a bounded wait that
  * gave up.  Reads and clears it (synchronises the stream). */
 ddgi_status ddgi_poll_status(ddgi_volume volume, ddgi_stream stream);

@@ -212,6 +212,14 @@ class Volume:
         k = n.value
         return rec[: k * self.R].view(k, self.R, 4), ids[:k]
 
+    def trace_stats(self, scene: Scene, lights, stream=None):
+        """Work counters of the last update's trace (instrumented re-trace)."""
+        st = (C.c_uint64 * 7)()
+        L = lights if isinstance(lights, _lib.Lights) else lights_struct(lights)
+        check(load().ddgi_trace_stats(self.handle, scene.handle, C.byref(L), st, _stream(stream)))
+        keys = ["rays", "nodes", "tris", "shadow_rays", "shadow_nodes", "shadow_tris", "queries"]
+        return {k: int(st[i]) for i, k in enumerate(keys)}
+
     def enable_timing(self, on=True):
         check(load().ddgi_enable_timing(self.handle, int(bool(on))))
 

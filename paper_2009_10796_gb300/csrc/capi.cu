@@ -97,6 +97,8 @@ struct ddgi_volume_s {
     float* inv_s_irr = nullptr;
     float* w_dist = nullptr;       // [dist_n^2][R]
     float* inv_s_dist = nullptr;
+    unsigned long long* stats = nullptr;   // [8] trace work counters
+    int64_t updates = 0;
     int3 shift{0, 0, 0};
     bool timing = false;
     TimedStage stages[5];
@@ -292,7 +294,7 @@ void ddgi_volume_destroy(ddgi_volume v) {
     if (!v) return;
     cudaFree(v->states); cudaFree(v->irr); cudaFree(v->dist); cudaFree(v->lists); cudaFree(v->counts);
     cudaFree(v->status); cudaFree(v->records); cudaFree(v->dirs); cudaFree(v->w_irr);
-    cudaFree(v->inv_s_irr); cudaFree(v->w_dist); cudaFree(v->inv_s_dist);
+    cudaFree(v->inv_s_irr); cudaFree(v->w_dist); cudaFree(v->inv_s_dist); cudaFree(v->stats);
     for (auto& st : v->stages)
         for (auto& pr : st.pending) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     delete v;
@@ -335,6 +337,7 @@ ddgi_status ddgi_volume_create(const ddgi_volume_desc* desc, ddgi_volume* out) {
     A((void**)&v->inv_s_irr, sizeof(float) * desc->irr_n * desc->irr_n);
     A((void**)&v->w_dist, sizeof(float) * desc->dist_n * desc->dist_n * (size_t)v->R);
     A((void**)&v->inv_s_dist, sizeof(float) * desc->dist_n * desc->dist_n);
+    A((void**)&v->stats, sizeof(unsigned long long) * 8);
     if (e == cudaSuccess) e = cudaMemset(v->states, desc->state_machine ? DDGI_STATE_UNINIT : DDGI_STATE_VIGILANT, (size_t)v->P);
     if (e == cudaSuccess) e = cudaMemset(v->irr, 0, v->irr_bytes);
     if (e == cudaSuccess) e = cudaMemset(v->dist, 0, v->dist_bytes);
@@ -440,6 +443,22 @@ ddgi_status ddgi_update(ddgi_volume v, ddgi_scene s, const ddgi_lights* lights,
         DDGI_CK(launch_blend(view, bp, v->w_irr, v->inv_s_irr, v->w_dist, v->inv_s_dist, v->records,
                              v->lists + v->P, v->counts + 1, v->status, sms * 4, st));
     }
+    v->updates++;
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_trace_stats(ddgi_volume v, ddgi_scene s, const ddgi_lights* lights, uint64_t stats[7],
+                             ddgi_stream stream) {
+    if (!v || !s || !lights || !stats) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (v->updates == 0) return fail(DDGI_ERR_INVALID_ARG, "no update has run on this volume");
+    cudaStream_t st = (cudaStream_t)stream;
+    DDGI_CK(cudaMemsetAsync(v->stats, 0, sizeof(unsigned long long) * 8, st));
+    DDGI_CK(launch_trace_shade_count(s->dev, make_view(v), make_lights(lights), v->dirs, v->R,
+                                     v->lists + v->P, v->counts + 1, v->stats, sm_count() * 16, st));
+    unsigned long long h[8];
+    DDGI_CK(cudaMemcpyAsync(h, v->stats, sizeof(h), cudaMemcpyDeviceToHost, st));
+    DDGI_CK(cudaStreamSynchronize(st));
+    for (int k = 0; k < 7; ++k) stats[k] = h[k];
     return DDGI_OK;
 }
 

@@ -95,6 +95,10 @@ cudaError_t launch_classify(const DevScene& s, const VolView& v, const float4* d
 cudaError_t launch_trace_shade(const DevScene& s, const VolView& v, const Lights& L,
                                const float4* dirs, int R, const int32_t* active,
                                const int32_t* count, float4* records, int grid, cudaStream_t st);
+cudaError_t launch_trace_shade_count(const DevScene& s, const VolView& v, const Lights& L,
+                                     const float4* dirs, int R, const int32_t* active,
+                                     const int32_t* count, unsigned long long* stats, int grid,
+                                     cudaStream_t st);
 cudaError_t launch_blend(const VolView& v, const BlendParams& bp, const float* w_irr,
                          const float* inv_s_irr, const float* w_dist, const float* inv_s_dist,
                          const float4* records, const int32_t* active, const int32_t* count,

@@ -52,11 +52,19 @@ __global__ void __launch_bounds__(256) k_classify(DevScene s, VolView v, const f
     }
 }
 
+// COUNT = true is the instrumented measurement variant: it writes no records
+// and accumulates per-ray work counters instead (stats[0..6]: primary rays,
+// primary node visits, primary triangle tests, shadow rays, shadow node
+// visits, shadow triangle tests, probe queries at hits).
+template <bool COUNT>
 __global__ void __launch_bounds__(128) k_trace_shade(DevScene s, VolView v, Lights L,
                                                      const float4* __restrict__ dirs, int R,
                                                      const int32_t* __restrict__ active,
                                                      const int32_t* __restrict__ count,
-                                                     float4* __restrict__ records) {
+                                                     float4* __restrict__ records,
+                                                     unsigned long long* stats) {
+    TraceCount cp, cs;
+    uint32_t n_rays = 0, n_shadow = 0, n_query = 0;
     const int64_t total = (int64_t)(*count) * R;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
@@ -67,7 +75,8 @@ __global__ void __launch_bounds__(128) k_trace_shade(DevScene s, VolView v, Ligh
         float4 d4 = __ldg(dirs + i);
         float3 d = f3(d4.x, d4.y, d4.z);
         RayPre r = ray_pre(o, d);
-        Hit h = traverse<false>(s, r);
+        Hit h = traverse<false, COUNT>(s, r, &cp);
+        if (COUNT) n_rays++;
         float4 rec;
         if (h.orig < 0) {
             float c = dot(d, L.sky_up);
@@ -97,18 +106,29 @@ __global__ void __launch_bounds__(128) k_trace_shade(DevScene s, VolView v, Ligh
                 if (L.sun_on && cosl > 0.0f) {
                     float off = 1e-4f * (1.0f + length(x));
                     RayPre sr = ray_pre(x + off * n, tol);
-                    Hit sh = traverse<true>(s, sr);
+                    Hit sh = traverse<true, COUNT>(s, sr, &cs);
+                    if (COUNT) n_shadow++;
                     if (sh.orig < 0) {
                         float k = cosl * 0.318309886183790672f;   // 1/pi
                         direct = f3(L.sun_irr.x * k, L.sun_irr.y * k, L.sun_irr.z * k);
                     }
                 }
                 float3 M = query_M(v, x, n, f3(-d.x, -d.y, -d.z));
+                if (COUNT) n_query++;
                 rec = make_float4(Le.x + rho.x * (direct.x + M.x), Le.y + rho.y * (direct.y + M.y),
                                   Le.z + rho.z * (direct.z + M.z), fminf(h.t, v.t_max));
             }
         }
-        records[idx] = rec;
+        if (!COUNT) records[idx] = rec;
+    }
+    if (COUNT) {
+        atomicAdd(stats + 0, (unsigned long long)n_rays);
+        atomicAdd(stats + 1, (unsigned long long)cp.nodes);
+        atomicAdd(stats + 2, (unsigned long long)cp.tris);
+        atomicAdd(stats + 3, (unsigned long long)n_shadow);
+        atomicAdd(stats + 4, (unsigned long long)cs.nodes);
+        atomicAdd(stats + 5, (unsigned long long)cs.tris);
+        atomicAdd(stats + 6, (unsigned long long)n_query);
     }
 }
 
@@ -171,7 +191,15 @@ cudaError_t launch_classify(const DevScene& s, const VolView& v, const float4* d
 cudaError_t launch_trace_shade(const DevScene& s, const VolView& v, const Lights& L, const float4* dirs,
                                int R, const int32_t* active, const int32_t* count, float4* records,
                                int grid, cudaStream_t st) {
-    k_trace_shade<<<grid, 128, 0, st>>>(s, v, L, dirs, R, active, count, records);
+    k_trace_shade<false><<<grid, 128, 0, st>>>(s, v, L, dirs, R, active, count, records, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_shade_count(const DevScene& s, const VolView& v, const Lights& L,
+                                     const float4* dirs, int R, const int32_t* active,
+                                     const int32_t* count, unsigned long long* stats, int grid,
+                                     cudaStream_t st) {
+    k_trace_shade<true><<<grid, 128, 0, st>>>(s, v, L, dirs, R, active, count, nullptr, stats);
     return cudaGetLastError();
 }
 

@@ -92,9 +92,17 @@ __device__ __forceinline__ float box_enter(const RayPre& r, float lx, float hx, 
     return tn <= tf * 1.0000005f ? tn : INFINITY;
 }
 
+// Work counters of the instrumented (measurement-only) traversal.
+struct TraceCount {
+    uint32_t nodes = 0;   // node visits (two child-box tests each)
+    uint32_t tris = 0;    // triangle tests
+};
+
 // Closest hit (ANY = false) or any hit among shadow casters (ANY = true).
-template <bool ANY>
-__device__ __forceinline__ Hit traverse(const DevScene& s, const RayPre& r) {
+// COUNT adds node-visit and triangle-test counters; the product kernels use
+// COUNT = false.
+template <bool ANY, bool COUNT = false>
+__device__ __forceinline__ Hit traverse(const DevScene& s, const RayPre& r, TraceCount* cnt_out = nullptr) {
     Hit h;
     h.t = INFINITY;
     h.orig = -1;
@@ -104,6 +112,7 @@ __device__ __forceinline__ Hit traverse(const DevScene& s, const RayPre& r) {
     int sp = 0;
     int node = 0;
     while (true) {
+        if (COUNT) cnt_out->nodes++;
         const float4* N = s.nodes + 4 * (int64_t)node;
         float4 a = __ldg(N), b = __ldg(N + 1), z = __ldg(N + 2);
         int4 m = __ldg(reinterpret_cast<const int4*>(N + 3));
@@ -120,6 +129,7 @@ __device__ __forceinline__ Hit traverse(const DevScene& s, const RayPre& r) {
                 const float4* T = s.tris + 3 * (int64_t)k;
                 float4 p0 = __ldg(T), p1 = __ldg(T + 1), p2 = __ldg(T + 2);
                 if (ANY && !(__float_as_int(p1.w) & 1)) continue;
+                if (COUNT) cnt_out->tris++;
                 float t = tri_hit(r, p0, p1, p2);
                 if (t < 0.0f) continue;
                 int orig = __float_as_int(p0.w);
