@@ -259,6 +259,39 @@ ddgi_status ddgi_trace_stats(ddgi_volume volume, ddgi_scene scene, const ddgi_li
  * gave up.  Reads and clears it (synchronises the stream). */
 ddgi_status ddgi_poll_status(ddgi_volume volume, ddgi_stream stream);
 
+/* ------------------------------------------------------------------ */
+/* Allocation-free update                                              */
+/* ------------------------------------------------------------------ */
+
+/* The paper has no counterpart to this call; it exists for callers that may
+ * not allocate device memory while they run, such as a renderer that plans
+ * all of its GPU memory at start-up and forbids cudaMalloc in its frame loop
+ * (an allocation can synchronise the device and breaks the memory plan), or a
+ * plug-in whose host application owns every device buffer.
+ *
+ * One update frame, the same steps and results as ddgi_update, for a volume
+ * whose state the caller owns: states_dev [P] uint8, irr_dev and dist_dev the
+ * atlases in the layout and formats of `desc` (what ddgi_get_buffer returns
+ * for a volume made from the same descriptor; start from zeroed atlases and
+ * states UNINIT, or VIGILANT with the state machine off).  The call allocates
+ * nothing: its scratch (ray pattern, weight tables, probe lists, counters,
+ * ray records) lives in fixed arrays of the library, about 17 MiB that every
+ * GPU loading the library holds until the process exits.
+ *
+ * Limits (INVALID_ARG beyond them): at most 32768 probes, 512 rays per
+ * probe and 1048576 probes x rays; irr_n <= 8, dist_n <= 16; FP32 blend only
+ * (UNSUPPORTED otherwise).
+ *
+ * The first call on a device looks up the arrays' device addresses with
+ * that device current; make that first call before any stream capture.
+ * Every call shares the arrays and overwrites the previous call's contents
+ * (the counters it needs zeroed are cleared by each call), so calls whose
+ * work overlaps on the GPU, on any streams, race: serialise them. */
+ddgi_status ddgi_update_noalloc(ddgi_scene scene, const ddgi_volume_desc* desc,
+                                const ddgi_lights* lights, const ddgi_update_params* params,
+                                uint8_t* states_dev, void* irr_dev, void* dist_dev,
+                                ddgi_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

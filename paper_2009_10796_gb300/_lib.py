@@ -76,6 +76,8 @@ SIGNATURES = {
     "ddgi_read_timings": (C.c_int, [_vp, C.c_float * 5, C.c_int32 * 5]),
     "ddgi_poll_status": (C.c_int, [_vp, _vp]),
     "ddgi_trace_stats": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.c_uint64 * 7, _vp]),
+    "ddgi_update_noalloc": (C.c_int, [_vp, C.POINTER(VolumeDesc), C.POINTER(Lights),
+                                      C.POINTER(UpdateParams), _vp, _vp, _vp, _vp]),
 }
 
 

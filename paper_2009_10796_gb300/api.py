@@ -15,7 +15,7 @@ import torch
 from . import _lib
 from ._lib import check, load
 
-__all__ = ["Scene", "Volume", "trace", "lights_struct"]
+__all__ = ["Scene", "Volume", "trace", "lights_struct", "update_noalloc"]
 
 
 def _stream(stream):
@@ -247,3 +247,16 @@ class Volume:
 
 def trace(scene: Scene, orig, dirs, stream=None):
     return scene.trace(orig, dirs, stream)
+
+
+def update_noalloc(scene: Scene, desc, lights, frame: int, states: torch.Tensor,
+                   irr: torch.Tensor, dist: torch.Tensor, irr_scale=1.0, vis_scale=1.0,
+                   stream=None):
+    """One update frame on caller-owned state, allocating no device memory
+    (ddgi_update_noalloc): `states`, `irr` and `dist` are the volume's state
+    buffers, owned and kept by the caller between frames."""
+    d = desc if isinstance(desc, _lib.VolumeDesc) else desc_struct(desc)
+    p = _lib.UpdateParams(int(frame), float(irr_scale), float(vis_scale), _lib.BLEND_FP32, 0)
+    L = lights if isinstance(lights, _lib.Lights) else lights_struct(lights)
+    check(load().ddgi_update_noalloc(scene.handle, C.byref(d), C.byref(L), C.byref(p), _ptr(states),
+                                     _ptr(irr), _ptr(dist), _stream(stream)))

@@ -17,6 +17,9 @@ static ddgi_status fail(ddgi_status s, const std::string& msg) {
     return s;
 }
 
+// Lets other translation units report through ddgi_last_error().
+ddgi_status set_error(ddgi_status s, const std::string& msg) { return fail(s, msg); }
+
 #define DDGI_CK(expr)                                                                         \
     do {                                                                                      \
         cudaError_t e_ = (expr);                                                              \
@@ -217,6 +220,15 @@ void ddgi_scene_destroy(ddgi_scene s) {
     cudaFree(s->nodes); cudaFree(s->tris); cudaFree(s->attr); cudaFree(s->albedo); cudaFree(s->emit);
     delete s;
 }
+
+}  // extern "C"
+
+namespace ddgi {
+// Device view of a registered scene, for other translation units.
+const DevScene* scene_device_view(ddgi_scene s) { return s ? &s->dev : nullptr; }
+}  // namespace ddgi
+
+extern "C" {
 
 ddgi_status ddgi_scene_info(ddgi_scene s, int64_t* n_nodes, int64_t* n_leaves, int64_t* n_tris) {
     if (!s) return fail(DDGI_ERR_INVALID_ARG, "scene is NULL");

@@ -113,4 +113,10 @@ cudaError_t launch_gbuffer(const DevScene& s, float3 pos, float3 fwd, float3 rig
 
 int sm_count();
 
+// Records an error message for ddgi_last_error() and returns the status.
+ddgi_status set_error(ddgi_status s, const std::string& msg);
+
+// Device view of a registered scene (NULL for a NULL handle).
+const DevScene* scene_device_view(ddgi_scene s);
+
 }  // namespace ddgi
