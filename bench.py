@@ -229,36 +229,43 @@ def run_gpu(args):
     n_active = int((vol.states() == g.STATE_VIGILANT).sum().item())
     R = desc.rays_per_probe
     stats = vol.trace_stats(scene, L)
-    vol.read_timings()
-    vol.enable_timing(True)
 
-    # device-timed steps; L2 flushed between steps outside the events
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    qev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    def timed_steps(precision):
+        # device-timed steps; L2 flushed between steps outside the events
+        nonlocal frame
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        qev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        vol.read_timings()
+        vol.enable_timing(True)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
         wall0 = time.perf_counter()
         for k in range(args.steps):
             flush.fill_(float(k))
             evs[k][0].record(stream)
-            vol.update(scene, L, frame, stream=stream)
+            vol.update(scene, L, frame, precision=precision, stream=stream)
             qev[k][0].record(stream)
             vol.query(pos, nrm, camera, out, stream=stream)
             qev[k][1].record(stream)
             evs[k][1].record(stream)
             frame += 1
         torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
-    if world > 1:
-        dist.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    query_ms = [a.elapsed_time(b) for a, b in qev]
-    timings = vol.read_timings()
-    vol.enable_timing(False)
+        wall_s = time.perf_counter() - wall0
+        if world > 1:
+            dist.barrier()
+        tm = vol.read_timings()
+        vol.enable_timing(False)
+        return ([a.elapsed_time(b) for a, b in evs], [a.elapsed_time(b) for a, b in qev], tm, wall_s)
+
+    with ClockSampler(local) as clk:
+        step_ms, query_ms, timings, wall = timed_steps(g.BLEND_FP32)
+        mixed = None
+        if not args.no_mixed:
+            m_step, m_query, m_tm, _ = timed_steps(g.BLEND_BF16)
+            mixed = (m_step, m_query, m_tm)
     ms = float(np.mean(step_ms))
     t = torch.tensor([ms], device=dev)
     if world > 1:
@@ -309,6 +316,7 @@ def run_gpu(args):
     achieved = ops / (trace_ms_avg * 1e-3) / 1e12
     blend_ms = timings["blend"][0] / max(timings["blend"][1], 1)
     blend_bytes = n_active * (R * 16 + 2000 + 2816)      # records in, old interior in, tiles out
+    blend_flops = n_active * 2 * R * (36 * 3 + 196 * 2)    # the contraction of Eq. 1 (irr + distance moments)
     q_ms = float(np.mean(query_ms))
     q_bytes = n_pix * 36                                  # positions + normals in, irradiance out
     hbm = pk.get("hbm_gbs", 6800.0)
@@ -350,6 +358,16 @@ def run_gpu(args):
                            "frac": blend_bytes / (blend_ms * 1e-3) / 1e9 / hbm},
         "roofline_query": {"bound": "hbm", "achieved": q_bytes / (q_ms * 1e-3) / 1e9, "peak": hbm,
                            "unit": "GB/s", "frac": q_bytes / (q_ms * 1e-3) / 1e9 / hbm},
+        "mixed_bf16": None if mixed is None else {
+            "blend": "BF16 irradiance / FP32-accurate distance moments on tcgen05 tensor cores",
+            "ms_per_step": float(np.mean(mixed[0])),
+            "value": rays_per_step / (float(np.mean(mixed[0])) * 1e-3) / 1e9,
+            "blend_ms": mixed[2]["blend"][0] / max(mixed[2]["blend"][1], 1),
+            "blend_hbm_frac": blend_bytes / (mixed[2]["blend"][0] / max(mixed[2]["blend"][1], 1) * 1e-3)
+                              / 1e9 / hbm,
+            "blend_tensor_tflops": blend_flops / (mixed[2]["blend"][0] / max(mixed[2]["blend"][1], 1) * 1e-3)
+                                   / 1e12,
+            "frame_setup_ms": mixed[2]["frame_setup"][0] / max(mixed[2]["frame_setup"][1], 1)},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "Grays/s", "h2d_bytes_per_step": 2 * n_pix * 12,
                 "d2h_bytes_per_step": n_pix * 12},
@@ -366,6 +384,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the BF16 tensor-core blend timing")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

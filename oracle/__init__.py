@@ -127,6 +127,12 @@ def _declare(lib):
     lib.or_query_cascade.argtypes = [C.c_int64, C.POINTER(OrVolume), C.POINTER(_u8p),
                                      C.POINTER(_dp), C.POINTER(_dp), C.c_int64, _dp, _dp, _dp,
                                      _dp, _dp]
+    lib.or_tracking_scroll.argtypes = [C.POINTER(OrVolume), _dp, _u8p, _dp, _dp]
+    lib.or_tracking_scroll.restype = C.c_int64
+    lib.or_update_cascade.argtypes = [C.POINTER(OrScene), C.POINTER(OrLights), C.c_int64,
+                                      C.POINTER(OrVolume), C.c_int64, C.c_double, C.c_double,
+                                      C.POINTER(_u8p), C.POINTER(_dp), C.POINTER(_dp), _i64p,
+                                      C.POINTER(_i64p), C.POINTER(_dp)]
     return lib
 
 
@@ -361,3 +367,41 @@ def query_cascade(vol_structs, states_list, irr_list, dist_list, pos, nrm, camer
     lib().or_query_cascade(k, vols, sp, ip, dp, n, _ptr(pos, _dp), _ptr(nrm, _dp), _ptr(cam, _dp),
                            _ptr(out, _dp), _ptr(w, _dp))
     return (out, w) if want_weights else out
+
+
+def tracking_scroll(vol: OrVolume, camera, states, irr, dist) -> int:
+    """Scroll a tracking window to the camera (Sec. 7.2); updates vol's origin
+    and shift in place and resets the planes that leapfrog."""
+    cam = _f64(camera, (3,))
+    return int(lib().or_tracking_scroll(C.byref(vol), _ptr(cam, _dp), _ptr(states, _u8p),
+                                        _ptr(irr, _dp), _ptr(dist, _dp)))
+
+
+def update_cascade(scene_h, lights, vol_structs, frame, states_list, irr_list, dist_list,
+                   subsets=None, irr_scale=1.0, vis_scale=1.0, want_rays=False):
+    """One cascade update frame in place; hit shading samples the whole cascade."""
+    k = len(vol_structs)
+    vols = (OrVolume * k)(*vol_structs)
+    sp = (_u8p * k)(*[_ptr(a, _u8p) for a in states_list])
+    ip = (_dp * k)(*[_ptr(a, _dp) for a in irr_list])
+    dp = (_dp * k)(*[_ptr(a, _dp) for a in dist_list])
+    nsub = None
+    subp = None
+    keep = []
+    if subsets is not None:
+        arrs = [np.ascontiguousarray(x, dtype=np.int64) for x in subsets]
+        keep += arrs
+        nsub = np.array([len(a) for a in arrs], dtype=np.int64)
+        subp = (_i64p * k)(*[_ptr(a, _i64p) for a in arrs])
+    rays = None
+    rp = None
+    if want_rays:
+        R = vol_structs[0].rays
+        rays = []
+        for j in range(k):
+            n = len(subsets[j]) if subsets is not None else int(np.prod(list(vol_structs[j].counts)))
+            rays.append(np.full((n, R, 4), np.nan))
+        rp = (_dp * k)(*[_ptr(a, _dp) for a in rays])
+    lib().or_update_cascade(C.byref(scene_h.s), C.byref(make_lights(lights)), k, vols, frame,
+                            irr_scale, vis_scale, sp, ip, dp, _ptr(nsub, _i64p), subp, rp)
+    return rays

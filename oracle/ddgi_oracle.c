@@ -455,6 +455,32 @@ static double volume_weight(const or_volume* v, const double x[3]) {
     return w;
 }
 
+/* Cascade value M at x (Sec. 7.3): volumes densest first, each weighted by its
+ * fall-off box, accumulation stops once the weights reach 1; the weighted
+ * values are normalised by the weight sum (0 when no volume covers x). */
+static void cascade_M(int64_t n_vol, const or_volume* vols, const uint8_t* const* states,
+                      const double* const* irr, const double* const* dist,
+                      const double x[3], const double n[3], const double wo[3], double M[3],
+                      double* vol_weights) {
+    double sum = 0.0, acc[3] = {0.0, 0.0, 0.0};
+    for (int64_t k = 0; k < n_vol; ++k) {
+        double vw = volume_weight(&vols[k], x);
+        double take = fmin(vw, 1.0 - sum);
+        if (vol_weights) vol_weights[k] = take > 0.0 ? take : 0.0;
+        if (take <= 0.0) continue;
+        double Mk[3];
+        query_M(&vols[k], states[k], irr[k], dist[k], x, n, wo, Mk, NULL);
+        for (int c = 0; c < 3; ++c) acc[c] += take * Mk[c];
+        sum += take;
+        if (sum >= 1.0) {
+            for (int64_t j = k + 1; j < n_vol; ++j)
+                if (vol_weights) vol_weights[j] = 0.0;
+            break;
+        }
+    }
+    for (int c = 0; c < 3; ++c) M[c] = sum > 0.0 ? acc[c] / sum : 0.0;
+}
+
 void or_query_cascade(int64_t n_vol, const or_volume* vols, const uint8_t* const* states,
                       const double* const* irr, const double* const* dist,
                       int64_t n, const double* pos, const double* nrm, const double camera[3],
@@ -468,31 +494,29 @@ void or_query_cascade(int64_t n_vol, const or_volume* vols, const uint8_t* const
         double l = len3(wo);
         if (l < 1e-6) { wo[0] = nn[0]; wo[1] = nn[1]; wo[2] = nn[2]; }
         else { wo[0] /= l; wo[1] /= l; wo[2] /= l; }
-        double sum = 0.0, acc[3] = {0.0, 0.0, 0.0};
-        for (int64_t k = 0; k < n_vol; ++k) {
-            double vw = volume_weight(&vols[k], x);
-            double take = fmin(vw, 1.0 - sum);
-            if (vol_weights_out) vol_weights_out[q * n_vol + k] = take > 0.0 ? take : 0.0;
-            if (take <= 0.0) continue;
-            double M[3];
-            query_M(&vols[k], states[k], irr[k], dist[k], x, nn, wo, M, NULL);
-            for (int c = 0; c < 3; ++c) acc[c] += take * M_PI * M[c];
-            sum += take;
-            if (sum >= 1.0) {
-                for (int64_t j = k + 1; j < n_vol; ++j)
-                    if (vol_weights_out) vol_weights_out[q * n_vol + j] = 0.0;
-                break;
-            }
+        if (nn[0] == 0.0 && nn[1] == 0.0 && nn[2] == 0.0) {
+            for (int c = 0; c < 3; ++c) out_E[3*q + c] = 0.0;
+            if (vol_weights_out) for (int64_t k = 0; k < n_vol; ++k) vol_weights_out[q * n_vol + k] = 0.0;
+            continue;
         }
-        for (int c = 0; c < 3; ++c) out_E[3*q + c] = sum > 0.0 ? acc[c] / sum : 0.0;
+        double M[3];
+        cascade_M(n_vol, vols, states, irr, dist, x, nn, wo, M, vol_weights_out ? vol_weights_out + q * n_vol : NULL);
+        for (int c = 0; c < 3; ++c) out_E[3*q + c] = M_PI * M[c];
     }
 }
 
 /* ------------------------------------------------------------------ */
 /* Shading one probe ray (Sec. 2.3, Sec. 4.1 backface rule)             */
 /* ------------------------------------------------------------------ */
-static void shade_ray(const or_scene* s, const or_lights* L, const or_volume* v,
-                      const uint8_t* st, const double* irr, const double* dist,
+typedef struct {
+    int64_t n_vol;
+    const or_volume* vols;
+    const uint8_t* const* states;
+    const double* const* irr;
+    const double* const* dist;
+} or_prev;   /* the previous frame's probes that hit shading samples */
+
+static void shade_ray(const or_scene* s, const or_lights* L, const or_volume* v, const or_prev* prev,
                       const double o[3], const double d[3], double out[4]) {
     double t;
     int64_t tri;
@@ -530,7 +554,10 @@ static void shade_ray(const or_scene* s, const or_lights* L, const or_volume* v,
     /* indirect: the previous frame's probes queried at the hit, looking back at the probe */
     double wo[3] = { -d[0], -d[1], -d[2] };
     double M[3];
-    query_M(v, st, irr, dist, x, n, wo, M, NULL);
+    if (prev->n_vol == 1)
+        query_M(&prev->vols[0], prev->states[0], prev->irr[0], prev->dist[0], x, n, wo, M, NULL);
+    else
+        cascade_M(prev->n_vol, prev->vols, prev->states, prev->irr, prev->dist, x, n, wo, M, NULL);
     for (int k = 0; k < 3; ++k) out[k] = Le[k] + rho[k] * (direct[k] + M[k]);
     out[3] = fmin(t, v->t_max);
 }
@@ -615,6 +642,10 @@ void or_update(const or_scene* s, const or_lights* L, const or_volume* v, int64_
     double* dirs = (double*)malloc(sizeof(double) * 3 * (size_t)R);
     or_frame_dirs(v->seed, frame, R, dirs);
     double* rays = (double*)calloc((size_t)(n > 0 ? n : 1) * (size_t)R * 4, sizeof(double));
+    const uint8_t* st1[1] = { states };
+    const double* ir1[1] = { irr };
+    const double* di1[1] = { dist };
+    or_prev prev = { 1, v, st1, ir1, di1 };
     #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t q = 0; q < n; ++q) {
         int64_t p = list[q];
@@ -622,7 +653,7 @@ void or_update(const or_scene* s, const or_lights* L, const or_volume* v, int64_
         double x[3];
         probe_pos_phys(v, p, x);
         for (int64_t r = 0; r < R; ++r)
-            shade_ray(s, L, v, states, irr, dist, x, dirs + 3*r, rays + (q * R + r) * 4);
+            shade_ray(s, L, v, &prev, x, dirs + 3*r, rays + (q * R + r) * 4);
     }
     /* 3. blend into the atlases, copy borders */
     int64_t tsi = irr_tile_size(v), tsd = dist_tile_size(v);
@@ -644,4 +675,112 @@ void or_update(const or_scene* s, const or_lights* L, const or_volume* v, int64_
     free(rays);
     free(dirs);
     free(list);
+}
+
+/* ------------------------------------------------------------------ */
+/* Cascades (Sec. 7.3) and the camera tracking window (Sec. 7.2)       */
+/* ------------------------------------------------------------------ */
+
+static void reset_probe(const or_volume* v, int64_t p, uint8_t* states, double* irr, double* dist) {
+    states[p] = OR_UNINIT;
+    memset(irr + p * irr_tile_size(v), 0, sizeof(double) * (size_t)irr_tile_size(v));
+    memset(dist + p * dist_tile_size(v), 0, sizeof(double) * (size_t)dist_tile_size(v));
+}
+
+/* Moves the window by whole probe planes until the camera lies within one
+ * spacing of its centre on every axis.  Each move shifts the logical grid by
+ * one plane: the plane behind the camera leapfrogs to the front, keeping its
+ * storage (circular buffer), and is reset to zero texels and UNINIT so it is
+ * classified and converged again.  Returns the number of planes moved. */
+int64_t or_tracking_scroll(or_volume* v, const double camera[3], uint8_t* states, double* irr, double* dist) {
+    int64_t moved = 0;
+    for (int a = 0; a < 3; ++a) {
+        for (;;) {
+            double centre = v->origin[a] + 0.5 * (double)(v->counts[a] - 1) * v->spacing[a];
+            int dir = 0;
+            if (camera[a] - centre > v->spacing[a]) dir = 1;
+            else if (centre - camera[a] > v->spacing[a]) dir = -1;
+            if (!dir) break;
+            v->origin[a] += dir * v->spacing[a];
+            v->shift[a] += dir;
+            int64_t fresh = dir > 0 ? v->counts[a] - 1 : 0;   /* logical index of the new plane */
+            int b = (a + 1) % 3, c = (a + 2) % 3;
+            for (int64_t j = 0; j < v->counts[b]; ++j)
+                for (int64_t k = 0; k < v->counts[c]; ++k) {
+                    int64_t ijk[3];
+                    ijk[a] = fresh; ijk[b] = j; ijk[c] = k;
+                    reset_probe(v, or_probe_phys(v, ijk[0], ijk[1], ijk[2]), states, irr, dist);
+                }
+            moved++;
+        }
+    }
+    return moved;
+}
+
+/* One update frame of a cascade: every volume's probes trace the same ray
+ * pattern (the first volume's seed), hit shading samples the whole cascade
+ * of the previous frame, and each volume blends its own probes. */
+void or_update_cascade(const or_scene* s, const or_lights* L, int64_t n_vol, const or_volume* vols,
+                       int64_t frame, double irr_scale, double vis_scale,
+                       uint8_t* const* states, double* const* irr, double* const* dist,
+                       const int64_t* n_subset, const int64_t* const* subsets, double* const* rays_out) {
+    int64_t R = vols[0].rays;
+    int64_t** lists = (int64_t**)malloc(sizeof(int64_t*) * (size_t)n_vol);
+    int64_t* nl = (int64_t*)malloc(sizeof(int64_t) * (size_t)n_vol);
+    for (int64_t k = 0; k < n_vol; ++k) {
+        const or_volume* v = &vols[k];
+        int64_t P = v->counts[0] * v->counts[1] * v->counts[2];
+        nl[k] = (subsets && subsets[k]) ? n_subset[k] : P;
+        lists[k] = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nl[k] > 0 ? nl[k] : 1));
+        for (int64_t q = 0; q < nl[k]; ++q) lists[k][q] = (subsets && subsets[k]) ? subsets[k][q] : q;
+        if (v->state_machine) {
+            or_volume vk = *v;
+            vk.seed = vols[0].seed;
+            int64_t nu = 0;
+            int64_t* un = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nl[k] > 0 ? nl[k] : 1));
+            for (int64_t q = 0; q < nl[k]; ++q) if (states[k][lists[k][q]] == OR_UNINIT) un[nu++] = lists[k][q];
+            if (nu) or_classify(s, &vk, frame, nu, un, states[k], NULL, NULL);
+            free(un);
+        }
+    }
+    double* dirs = (double*)malloc(sizeof(double) * 3 * (size_t)R);
+    or_frame_dirs(vols[0].seed, frame, R, dirs);
+    or_prev prev = { n_vol, vols, (const uint8_t* const*)states, (const double* const*)irr,
+                     (const double* const*)dist };
+    double** rays = (double**)malloc(sizeof(double*) * (size_t)n_vol);
+    for (int64_t k = 0; k < n_vol; ++k) {
+        rays[k] = (double*)calloc((size_t)(nl[k] > 0 ? nl[k] : 1) * (size_t)R * 4, sizeof(double));
+        const or_volume* v = &vols[k];
+        #pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t q = 0; q < nl[k]; ++q) {
+            int64_t p = lists[k][q];
+            if (!is_active(states[k][p])) continue;
+            double x[3];
+            probe_pos_phys(v, p, x);
+            for (int64_t r = 0; r < R; ++r)
+                shade_ray(s, L, v, &prev, x, dirs + 3*r, rays[k] + (q * R + r) * 4);
+        }
+    }
+    for (int64_t k = 0; k < n_vol; ++k) {
+        const or_volume* v = &vols[k];
+        #pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t q = 0; q < nl[k]; ++q) {
+            int64_t p = lists[k][q];
+            if (!is_active(states[k][p])) continue;
+            blend_probe(v, dirs, rays[k] + q * R * 4, states[k][p] == OR_NEWLY_VIGILANT, irr_scale, vis_scale,
+                        irr[k] + p * irr_tile_size(v), dist[k] + p * dist_tile_size(v));
+        }
+        if (rays_out && rays_out[k])
+            for (int64_t q = 0; q < nl[k]; ++q)
+                if (is_active(states[k][lists[k][q]]))
+                    memcpy(rays_out[k] + q * R * 4, rays[k] + q * R * 4, sizeof(double) * 4 * (size_t)R);
+        for (int64_t q = 0; q < nl[k]; ++q)
+            if (states[k][lists[k][q]] == OR_NEWLY_VIGILANT) states[k][lists[k][q]] = OR_VIGILANT;
+        free(rays[k]);
+        free(lists[k]);
+    }
+    free(rays);
+    free(lists);
+    free(nl);
+    free(dirs);
 }

@@ -102,6 +102,12 @@ void or_query_cascade(int64_t n_vol, const or_volume* vols, const uint8_t* const
                       int64_t n, const double* pos, const double* nrm, const double camera[3],
                       double* out_E, double* vol_weights_out);
 
+int64_t or_tracking_scroll(or_volume* v, const double camera[3], uint8_t* states, double* irr, double* dist);
+void or_update_cascade(const or_scene* s, const or_lights* L, int64_t n_vol, const or_volume* vols,
+                       int64_t frame, double irr_scale, double vis_scale,
+                       uint8_t* const* states, double* const* irr, double* const* dist,
+                       const int64_t* n_subset, const int64_t* const* subsets, double* const* rays_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,63 @@
+// Blend epilogue shared by the SIMT and tensor-core blends (Sec. 2.3 Eq. 1,
+// Sec. 4.2 gamma encoding, Sec. 4.3 per-texel thresholds, Sec. 7.1 border copy).
+#pragma once
+
+#include "probe_math.cuh"
+
+namespace ddgi {
+
+// Border texels that copy interior texel (x, y) of a bordered tile (tile
+// coordinates, interior spans 1..n): the mirrored neighbour across each seam
+// edge it touches and, for the four interior corners, the opposite outer corner.
+template <typename F>
+__device__ __forceinline__ void for_border_copies(int x, int y, int n, F&& f) {
+    if (x == 1) f(0, n + 1 - y);
+    if (x == n) f(n + 1, n + 1 - y);
+    if (y == 1) f(n + 1 - x, 0);
+    if (y == n) f(n + 1 - x, n + 1);
+    if (x == n && y == n) f(0, 0);
+    if (x == 1 && y == n) f(n + 1, 0);
+    if (x == n && y == 1) f(0, n + 1);
+    if (x == 1 && y == 1) f(n + 1, n + 1);
+}
+
+// Epilogues shared by the SIMT and tensor-core blends: one (texel, probe)
+// pair from its weighted sums.  inv < 0 marks a texel no ray reaches: it
+// keeps its old value.
+__device__ __forceinline__ void blend_irr_texel(const VolView& v, const BlendParams& bp, int p, int t,
+                                                float ar, float ag, float ab, float inv, bool newly,
+                                                uint32_t* status) {
+    const int ni = v.irr_n;
+    int x = 1 + t % ni, y = 1 + t / ni;
+    float3 old = load_irr<false>(v, p, x, y);
+    float3 e = old;
+    if (inv >= 0.0f) {
+        float3 en = f3(powf(ar * inv, v.inv_gamma), powf(ag * inv, v.inv_gamma), powf(ab * inv, v.inv_gamma));
+        float delta = fmaxf(fabsf(en.x - old.x), fmaxf(fabsf(en.y - old.y), fabsf(en.z - old.z)));
+        float a = newly ? 0.0f : bp.hyst_irr;
+        if (delta > bp.thr_low) a = fmaxf(0.0f, a - bp.thr_step);
+        if (delta > bp.thr_high) a = 0.0f;
+        e = f3((1.0f - a) * en.x + a * old.x, (1.0f - a) * en.y + a * old.y, (1.0f - a) * en.z + a * old.z);
+        if (!(isfinite(e.x) && isfinite(e.y) && isfinite(e.z))) atomicOr(status, 1u);
+    }
+    store_irr(v, p, x, y, e);
+    for_border_copies(x, y, ni, [&](int bx, int by) { store_irr(v, p, bx, by, e); });
+}
+
+__device__ __forceinline__ void blend_dist_texel(const VolView& v, const BlendParams& bp, int p, int t,
+                                                 float m1, float m2, float inv, bool newly,
+                                                 uint32_t* status) {
+    const int nd = v.dist_n;
+    int x = 1 + t % nd, y = 1 + t / nd;
+    float2 old = load_dist<false>(v, p, x, y);
+    float2 e = old;
+    if (inv >= 0.0f) {
+        float a = newly ? 0.0f : bp.hyst_vis;
+        e = make_float2((1.0f - a) * (m1 * inv) + a * old.x, (1.0f - a) * (m2 * inv) + a * old.y);
+        if (!(isfinite(e.x) && isfinite(e.y))) atomicOr(status, 1u);
+    }
+    store_dist(v, p, x, y, e);
+    for_border_copies(x, y, nd, [&](int bx, int by) { store_dist(v, p, bx, by, e); });
+}
+
+}  // namespace ddgi

@@ -101,6 +101,12 @@ struct ddgi_volume_s {
     float* w_dist = nullptr;       // [dist_n^2][R]
     float* inv_s_dist = nullptr;
     unsigned long long* stats = nullptr;   // [8] trace work counters
+    int32_t* shadow_list = nullptr;        // [P * R] rays needing a shadow ray
+    int32_t* shadow_count = nullptr;
+    uint8_t* pack_irr = nullptr;           // tensor-core blend: weight tiles in operand layout
+    uint8_t* pack_dist = nullptr;
+    float* inv_irr_r = nullptr;            // 1 / sum of the rounded weights
+    float* inv_dist_r = nullptr;
     int64_t updates = 0;
     int3 shift{0, 0, 0};
     bool timing = false;
@@ -307,6 +313,8 @@ void ddgi_volume_destroy(ddgi_volume v) {
     cudaFree(v->states); cudaFree(v->irr); cudaFree(v->dist); cudaFree(v->lists); cudaFree(v->counts);
     cudaFree(v->status); cudaFree(v->records); cudaFree(v->dirs); cudaFree(v->w_irr);
     cudaFree(v->inv_s_irr); cudaFree(v->w_dist); cudaFree(v->inv_s_dist); cudaFree(v->stats);
+    cudaFree(v->shadow_list); cudaFree(v->shadow_count);
+    cudaFree(v->pack_irr); cudaFree(v->pack_dist); cudaFree(v->inv_irr_r); cudaFree(v->inv_dist_r);
     for (auto& st : v->stages)
         for (auto& pr : st.pending) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     delete v;
@@ -350,6 +358,12 @@ ddgi_status ddgi_volume_create(const ddgi_volume_desc* desc, ddgi_volume* out) {
     A((void**)&v->w_dist, sizeof(float) * desc->dist_n * desc->dist_n * (size_t)v->R);
     A((void**)&v->inv_s_dist, sizeof(float) * desc->dist_n * desc->dist_n);
     A((void**)&v->stats, sizeof(unsigned long long) * 8);
+    A((void**)&v->shadow_list, sizeof(int32_t) * (size_t)v->P * v->R);
+    A((void**)&v->shadow_count, sizeof(int32_t) * 4);
+    A((void**)&v->pack_irr, tc_pack_irr_bytes(v->R));
+    A((void**)&v->pack_dist, tc_pack_dist_bytes(v->R));
+    A((void**)&v->inv_irr_r, sizeof(float) * 128);
+    A((void**)&v->inv_dist_r, sizeof(float) * 256);
     if (e == cudaSuccess) e = cudaMemset(v->states, desc->state_machine ? DDGI_STATE_UNINIT : DDGI_STATE_VIGILANT, (size_t)v->P);
     if (e == cudaSuccess) e = cudaMemset(v->irr, 0, v->irr_bytes);
     if (e == cudaSuccess) e = cudaMemset(v->dist, 0, v->dist_bytes);
@@ -413,8 +427,11 @@ ddgi_status ddgi_update(ddgi_volume v, ddgi_scene s, const ddgi_lights* lights,
     if (!v || !s || !lights || !params) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
     if (!(params->irr_hyst_scale >= 0.0f) || !(params->vis_hyst_scale >= 0.0f))
         return fail(DDGI_ERR_INVALID_ARG, "negative hysteresis scale");
-    if (params->blend_precision != DDGI_BLEND_FP32)
-        return fail(DDGI_ERR_UNSUPPORTED, "blend precision not available in this build");
+    if (params->blend_precision < DDGI_BLEND_FP32 || params->blend_precision > DDGI_BLEND_BF16)
+        return fail(DDGI_ERR_INVALID_ARG, "unknown blend precision");
+    const bool tensor = params->blend_precision != DDGI_BLEND_FP32;
+    if (tensor && !tc_blend_supported(v->desc.irr_n, v->desc.dist_n))
+        return fail(DDGI_ERR_UNSUPPORTED, "tensor-core blend needs irr_n^2 <= 128 and dist_n^2 <= 256");
     cudaStream_t st = (cudaStream_t)stream;
     const ddgi_volume_desc& d = v->desc;
     VolView view = make_view(v);
@@ -424,6 +441,10 @@ ddgi_status ddgi_update(ddgi_volume v, ddgi_scene s, const ddgi_lights* lights,
         StageTimer tm(v, 4, st);
         DDGI_CK(launch_frame_setup(rot, v->R, d.irr_n, d.dist_n, d.dist_cos_power, v->dirs, v->w_irr,
                                    v->inv_s_irr, v->w_dist, v->inv_s_dist, st));
+        if (tensor)
+            DDGI_CK(launch_pack_weights(v->w_irr, v->w_dist, v->R, d.irr_n, d.dist_n,
+                                        params->blend_precision == DDGI_BLEND_BF16, v->pack_irr, v->pack_dist,
+                                        v->inv_irr_r, v->inv_dist_r, st));
     }
     DDGI_CK(cudaMemsetAsync(v->counts, 0, sizeof(int32_t) * 2, st));
     if (d.state_machine) {
@@ -440,8 +461,9 @@ ddgi_status ddgi_update(ddgi_volume v, ddgi_scene s, const ddgi_lights* lights,
     }
     {
         StageTimer tm(v, 2, st);
-        DDGI_CK(launch_trace_shade(s->dev, view, make_lights(lights), v->dirs, v->R, v->lists + v->P,
-                                   v->counts + 1, v->records, sms * 16, st));
+        DDGI_CK(launch_trace_wavefront(s->dev, view, make_lights(lights), v->dirs, v->R, v->lists + v->P,
+                                       v->counts + 1, v->records, v->shadow_list, v->shadow_count, sms * 8,
+                                       st));
     }
     BlendParams bp{};
     bp.hyst_irr = std::fmin(1.0f, std::fmax(0.0f, d.hysteresis_irr * params->irr_hyst_scale));
@@ -452,8 +474,13 @@ ddgi_status ddgi_update(ddgi_volume v, ddgi_scene s, const ddgi_lights* lights,
     bp.R = v->R;
     {
         StageTimer tm(v, 3, st);
-        DDGI_CK(launch_blend(view, bp, v->w_irr, v->inv_s_irr, v->w_dist, v->inv_s_dist, v->records,
-                             v->lists + v->P, v->counts + 1, v->status, sms * 4, st));
+        if (tensor)
+            DDGI_CK(launch_blend_tc(view, bp, params->blend_precision == DDGI_BLEND_BF16, v->pack_irr, v->pack_dist,
+                                    v->inv_irr_r, v->inv_dist_r, v->records, v->lists + v->P, v->counts + 1,
+                                    v->status, sms, st));
+        else
+            DDGI_CK(launch_blend(view, bp, v->w_irr, v->inv_s_irr, v->w_dist, v->inv_s_dist, v->records,
+                                 v->lists + v->P, v->counts + 1, v->status, sms * 4, st));
     }
     v->updates++;
     return DDGI_OK;

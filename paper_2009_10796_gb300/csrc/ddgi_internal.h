@@ -95,6 +95,9 @@ cudaError_t launch_classify(const DevScene& s, const VolView& v, const float4* d
 cudaError_t launch_trace_shade(const DevScene& s, const VolView& v, const Lights& L,
                                const float4* dirs, int R, const int32_t* active,
                                const int32_t* count, float4* records, int grid, cudaStream_t st);
+cudaError_t launch_trace_wavefront(const DevScene& s, const VolView& v, const Lights& L, const float4* dirs,
+                                   int R, const int32_t* active, const int32_t* count, float4* records,
+                                   int32_t* shadow_list, int32_t* shadow_count, int grid, cudaStream_t st);
 cudaError_t launch_trace_shade_count(const DevScene& s, const VolView& v, const Lights& L,
                                      const float4* dirs, int R, const int32_t* active,
                                      const int32_t* count, unsigned long long* stats, int grid,
@@ -103,6 +106,17 @@ cudaError_t launch_blend(const VolView& v, const BlendParams& bp, const float* w
                          const float* inv_s_irr, const float* w_dist, const float* inv_s_dist,
                          const float4* records, const int32_t* active, const int32_t* count,
                          uint32_t* status, int grid, cudaStream_t st);
+// tensor-core blend (k_blend_tc.cu)
+int tc_blend_chunks(int R);
+size_t tc_pack_irr_bytes(int R);
+size_t tc_pack_dist_bytes(int R);
+bool tc_blend_supported(int irr_n, int dist_n);
+cudaError_t launch_pack_weights(const float* w_irr, const float* w_dist, int R, int irr_n, int dist_n, int irr_bf16,
+                                uint8_t* a_irr, uint8_t* a_dist, float* inv_irr, float* inv_dist, cudaStream_t st);
+cudaError_t launch_blend_tc(const VolView& v, const BlendParams& bp, int bf16, const uint8_t* a_irr,
+                            const uint8_t* a_dist, const float* inv_irr, const float* inv_dist,
+                            const float4* records, const int32_t* active, const int32_t* count, uint32_t* status,
+                            int grid, cudaStream_t st);
 cudaError_t launch_query(const VolView& v, const float* pos, const float* nrm, int64_t n,
                          float3 camera, float* out, cudaStream_t st);
 cudaError_t launch_trace_rays(const DevScene& s, const float* orig, const float* dir, int64_t n,

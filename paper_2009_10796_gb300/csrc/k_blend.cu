@@ -14,7 +14,7 @@
 // writes the texel plus the border texels that copy it (the octahedral
 // border copy of Sec. 7.1 fused into the blend).  The probe's state advances
 // Newly Vigilant -> Vigilant after its texels are written.
-#include "probe_math.cuh"
+#include "blend_epilogue.cuh"
 
 namespace ddgi {
 
@@ -94,21 +94,6 @@ __global__ void __launch_bounds__(256) k_frame_setup(FrameRot rot, int R, int ir
     }
 }
 
-// Border texels that copy interior texel (x, y) of a bordered tile (tile
-// coordinates, interior spans 1..n): the mirrored neighbour across each seam
-// edge it touches and, for the four interior corners, the opposite outer corner.
-template <typename F>
-__device__ __forceinline__ void for_border_copies(int x, int y, int n, F&& f) {
-    if (x == 1) f(0, n + 1 - y);
-    if (x == n) f(n + 1, n + 1 - y);
-    if (y == 1) f(n + 1 - x, 0);
-    if (y == n) f(n + 1 - x, n + 1);
-    if (x == n && y == n) f(0, 0);
-    if (x == 1 && y == n) f(n + 1, 0);
-    if (x == n && y == 1) f(0, n + 1);
-    if (x == 1 && y == 1) f(n + 1, n + 1);
-}
-
 constexpr int kProbes = 8;
 
 __global__ void __launch_bounds__(256) k_blend_simt(VolView v, BlendParams bp,
@@ -153,24 +138,8 @@ __global__ void __launch_bounds__(256) k_blend_simt(VolView v, BlendParams bp,
                 ag = fmaf(w, L.y, ag);
                 ab = fmaf(w, L.z, ab);
             }
-            float inv = __ldg(inv_s_irr + t);
-            int p = s_probe[pp];
-            int x = 1 + t % ni, y = 1 + t / ni;
-            float3 old = load_irr<false>(v, p, x, y);
-            float3 e = old;
-            if (inv >= 0.0f) {
-                float3 en = f3(powf(ar * inv, v.inv_gamma), powf(ag * inv, v.inv_gamma),
-                               powf(ab * inv, v.inv_gamma));
-                float delta = fmaxf(fabsf(en.x - old.x), fmaxf(fabsf(en.y - old.y), fabsf(en.z - old.z)));
-                float a = s_newly[pp] ? 0.0f : bp.hyst_irr;
-                if (delta > bp.thr_low) a = fmaxf(0.0f, a - bp.thr_step);
-                if (delta > bp.thr_high) a = 0.0f;
-                e = f3((1.0f - a) * en.x + a * old.x, (1.0f - a) * en.y + a * old.y,
-                       (1.0f - a) * en.z + a * old.z);
-                if (!(isfinite(e.x) && isfinite(e.y) && isfinite(e.z))) atomicOr(status, 1u);
-            }
-            store_irr(v, p, x, y, e);
-            for_border_copies(x, y, ni, [&](int bx, int by) { store_irr(v, p, bx, by, e); });
+            blend_irr_texel(v, bp, s_probe[pp], t, ar, ag, ab, __ldg(inv_s_irr + t), s_newly[pp] != 0,
+                            status);
         }
         // distance texels: power-cosine weighted mean distance and mean squared distance
         for (int q = threadIdx.x; q < td * np; q += blockDim.x) {
@@ -185,18 +154,7 @@ __global__ void __launch_bounds__(256) k_blend_simt(VolView v, BlendParams bp,
                 m1 += wd;
                 m2 = fmaf(wd, d, m2);
             }
-            float inv = __ldg(inv_s_dist + t);
-            int p = s_probe[pp];
-            int x = 1 + t % nd, y = 1 + t / nd;
-            float2 old = load_dist<false>(v, p, x, y);
-            float2 e = old;
-            if (inv >= 0.0f) {
-                float a = s_newly[pp] ? 0.0f : bp.hyst_vis;
-                e = make_float2((1.0f - a) * (m1 * inv) + a * old.x, (1.0f - a) * (m2 * inv) + a * old.y);
-                if (!(isfinite(e.x) && isfinite(e.y))) atomicOr(status, 1u);
-            }
-            store_dist(v, p, x, y, e);
-            for_border_copies(x, y, nd, [&](int bx, int by) { store_dist(v, p, bx, by, e); });
+            blend_dist_texel(v, bp, s_probe[pp], t, m1, m2, __ldg(inv_s_dist + t), s_newly[pp] != 0, status);
         }
         __syncthreads();
         if (threadIdx.x < np && s_newly[threadIdx.x]) v.states[s_probe[threadIdx.x]] = DDGI_STATE_VIGILANT;

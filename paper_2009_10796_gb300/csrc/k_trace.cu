@@ -132,6 +132,148 @@ __global__ void __launch_bounds__(128) k_trace_shade(DevScene s, VolView v, Ligh
     }
 }
 
+// ---------------------------------------------------------------------------
+// Wavefront form of trace + shade: three coherent passes over the same rays.
+//   k_trace_primary  closest hit of every ray; stores (t, BVH triangle index,
+//                    sun visibility, 0) in the ray's record slot and appends
+//                    the rays that need a shadow ray (front-face hits facing
+//                    the sun) to a compact list
+//   k_trace_shadow   any-hit shadow rays over that list; sets the visibility
+//   k_shade          shading and the previous-frame query at each hit; writes
+//                    the final (r, g, b, d) record over the hit record
+// Each pass keeps its lanes on one kind of work, where the fused kernel ran
+// traversal, shadow rays and queries divergently in the same warp.  The
+// arithmetic of every value is the fused kernel's, in the same order.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void hit_frame(const DevScene& s, int k, float3& ng) {
+    const float4* T = s.tris + 3 * (int64_t)k;
+    float4 p0 = __ldg(T), p1 = __ldg(T + 1), p2 = __ldg(T + 2);
+    ng = cross(f3(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z), f3(p2.x - p0.x, p2.y - p0.y, p2.z - p0.z));
+}
+
+__global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolView v, Lights L,
+                                                       const float4* __restrict__ dirs, int R,
+                                                       const int32_t* __restrict__ active,
+                                                       const int32_t* __restrict__ count,
+                                                       float4* __restrict__ hits,
+                                                       int32_t* __restrict__ shadow_list,
+                                                       int32_t* shadow_count) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = (int64_t)(*count) * R;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // warp-uniform trip count so every lane takes part in the list append
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
+        int64_t idx = base + lane;
+        bool need = false;
+        if (idx < total) {
+            int slot = (int)(idx / R);
+            int i = (int)(idx - (int64_t)slot * R);
+            int p = __ldg(active + slot);
+            float3 o = probe_pos_phys(v, p);
+            float4 d4 = __ldg(dirs + i);
+            float3 d = f3(d4.x, d4.y, d4.z);
+            Hit h = traverse<false>(s, ray_pre(o, d));
+            if (h.orig >= 0 && L.sun_on) {
+                float3 ng;
+                hit_frame(s, h.k, ng);
+                if (!(dot(d, ng) > 0.0f)) {
+                    float3 n = (1.0f / length(ng)) * ng;
+                    float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
+                    need = dot(n, tol) > 0.0f;
+                }
+            }
+            hits[idx] = make_float4(h.t, __int_as_float(h.orig >= 0 ? h.k : -1), 0.0f, 0.0f);
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, need);
+        if (mask) {
+            int leader = __ffs(mask) - 1;
+            int off = 0;
+            if (lane == leader) off = atomicAdd(shadow_count, __popc(mask));
+            off = __shfl_sync(0xffffffffu, off, leader);
+            if (need) shadow_list[off + __popc(mask & ((1u << lane) - 1u))] = (int32_t)idx;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolView v, Lights L,
+                                                      const float4* __restrict__ dirs, int R,
+                                                      const int32_t* __restrict__ active,
+                                                      float4* __restrict__ hits,
+                                                      const int32_t* __restrict__ shadow_list,
+                                                      const int32_t* __restrict__ shadow_count) {
+    const int n = *shadow_count;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        int64_t idx = __ldg(shadow_list + q);
+        int slot = (int)(idx / R);
+        int i = (int)(idx - (int64_t)slot * R);
+        int p = __ldg(active + slot);
+        float3 o = probe_pos_phys(v, p);
+        float4 d4 = __ldg(dirs + i);
+        float3 d = f3(d4.x, d4.y, d4.z);
+        float4 hr = hits[idx];
+        float3 ng;
+        hit_frame(s, __float_as_int(hr.y), ng);
+        float3 n = (1.0f / length(ng)) * ng;
+        float3 x = o + hr.x * d;
+        float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
+        float off = 1e-4f * (1.0f + length(x));
+        Hit sh = traverse<true>(s, ray_pre(x + off * n, tol));
+        if (sh.orig < 0) reinterpret_cast<float*>(hits)[4 * idx + 2] = 1.0f;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_shade(DevScene s, VolView v, Lights L, const float4* __restrict__ dirs,
+                                               int R, const int32_t* __restrict__ active,
+                                               const int32_t* __restrict__ count, float4* records) {
+    const int64_t total = (int64_t)(*count) * R;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+        int slot = (int)(idx / R);
+        int i = (int)(idx - (int64_t)slot * R);
+        float4 d4 = __ldg(dirs + i);
+        float3 d = f3(d4.x, d4.y, d4.z);
+        float4 hr = records[idx];
+        int k = __float_as_int(hr.y);
+        float4 rec;
+        if (k < 0) {
+            float c = dot(d, L.sky_up);
+            rec = make_float4(L.sky_a.x + L.sky_b.x * c, L.sky_a.y + L.sky_b.y * c,
+                              L.sky_a.z + L.sky_b.z * c, v.t_max);
+        } else {
+            float3 ng;
+            hit_frame(s, k, ng);
+            float t = hr.x;
+            if (dot(d, ng) > 0.0f) {
+                rec = make_float4(0.0f, 0.0f, 0.0f, fminf(0.2f * t, v.t_max));
+            } else {
+                int p = __ldg(active + slot);
+                float3 o = probe_pos_phys(v, p);
+                float3 n = (1.0f / length(ng)) * ng;
+                float3 x = o + t * d;
+                int orig = __float_as_int(__ldg(&s.tris[3 * (int64_t)k].w));
+                int2 at = __ldg(s.attr + orig);
+                float4 rho = __ldg(s.albedo + at.x);
+                float3 Le = f3(0.0f, 0.0f, 0.0f);
+                if (at.y >= 0) {
+                    float4 e = __ldg(s.emit + at.y);
+                    Le = f3(e.x, e.y, e.z);
+                }
+                float3 direct = f3(0.0f, 0.0f, 0.0f);
+                if (hr.z != 0.0f) {
+                    float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
+                    float kk = dot(n, tol) * 0.318309886183790672f;   // 1/pi
+                    direct = f3(L.sun_irr.x * kk, L.sun_irr.y * kk, L.sun_irr.z * kk);
+                }
+                float3 M = query_M(v, x, n, f3(-d.x, -d.y, -d.z));
+                rec = make_float4(Le.x + rho.x * (direct.x + M.x), Le.y + rho.y * (direct.y + M.y),
+                                  Le.z + rho.z * (direct.z + M.z), fminf(t, v.t_max));
+            }
+        }
+        records[idx] = rec;
+    }
+}
+
 __global__ void k_trace_rays(DevScene s, const float* __restrict__ orig, const float* __restrict__ dir,
                              int64_t n, float* __restrict__ t_out, int32_t* __restrict__ tri_out,
                              int32_t* __restrict__ bf_out) {
@@ -192,6 +334,19 @@ cudaError_t launch_trace_shade(const DevScene& s, const VolView& v, const Lights
                                int R, const int32_t* active, const int32_t* count, float4* records,
                                int grid, cudaStream_t st) {
     k_trace_shade<false><<<grid, 128, 0, st>>>(s, v, L, dirs, R, active, count, records, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_wavefront(const DevScene& s, const VolView& v, const Lights& L, const float4* dirs,
+                                   int R, const int32_t* active, const int32_t* count, float4* records,
+                                   int32_t* shadow_list, int32_t* shadow_count, int grid, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(shadow_count, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    k_trace_primary<<<grid, 256, 0, st>>>(s, v, L, dirs, R, active, count, records, shadow_list, shadow_count);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_trace_shadow<<<grid, 256, 0, st>>>(s, v, L, dirs, R, active, records, shadow_list, shadow_count);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_shade<<<grid, 256, 0, st>>>(s, v, L, dirs, R, active, count, records);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,165 @@
+"""Reduced-precision atlas storage against the FP64 oracle.
+
+Tolerances come from the formats: FP16 rounds to nearest with 11 significant
+bits (relative error <= 2^-11); RGB9E5 shares one exponent chosen from the
+largest channel, so each channel's error is <= 2^-9 of the texel's largest
+channel.  Both add the FP32 parity tolerance of the arithmetic itself.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from parity import REL, rel_err, run_oracle, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_2009_10796_gb300 as pkg
+    pkg.load()
+    torch.cuda.set_device(0)
+    return pkg
+
+
+def _decode_rgb9e5(words):
+    w = words.astype(np.int64) & 0xFFFFFFFF
+    e = (w >> 27) - 15 - 9
+    s = np.ldexp(1.0, e)
+    return np.stack([(w & 511) * s, ((w >> 9) & 511) * s, ((w >> 18) & 511) * s], axis=-1)
+
+
+def _room(g, irr_format, dist_format):
+    sc = synth.room_scene()
+    L = synth.room_lights()
+    desc = synth.room_volume()
+    st, irr, dist, _ = run_oracle(sc, L, desc, [0])
+    V = g.Volume(desc, irr_format=irr_format, dist_format=dist_format)
+    V.update(g.Scene.from_arrays(sc), L, 0)
+    torch.cuda.synchronize()
+    assert np.array_equal(V.states().cpu().numpy(), st)
+    return desc, st, irr, dist, V
+
+
+def test_fp16_irradiance_and_distance_storage(g):
+    desc, st, irr, dist, V = _room(g, g.IRR_FP16, g.DIST_FP16)
+    gi = V.irr_atlas().cpu().numpy().astype(np.float64)
+    gd = V.dist_atlas().cpu().numpy().astype(np.float64)
+    tol = 2.0 ** -11 + REL
+    ei = rel_err(gi, irr)
+    ed = rel_err(gd, dist)
+    print(f"[precision] fp16 irr max rel {ei.max():.2e}, dist max rel {ed.max():.2e}")
+    assert ei.max() <= tol and ed.max() <= tol
+    # the stored value is the FP16 rounding of an FP32 result: never worse than half an ulp + FP32 error
+    pos, nrm, cam = synth.room_queries()
+    E_ref = oracle.query(desc, st, irr, dist, pos, nrm, cam)
+    E = V.query(to_dev(pos), to_dev(nrm), cam).cpu().numpy()
+    eq = rel_err(E, E_ref).max(-1)
+    # decode raises the encoded value to the 5th power: relative error x5
+    print(f"[precision] fp16 query max rel {eq.max():.2e}, median {np.median(eq):.2e}")
+    assert np.median(eq) <= 5 * 2.0 ** -11 and np.mean(eq <= 1e-2) >= 0.999
+
+
+def test_rgb9e5_irradiance_storage(g):
+    desc, st, irr, dist, V = _room(g, g.IRR_RGB9E5, g.DIST_FP32)
+    words = V.irr_raw().view(torch.int32).cpu().numpy().reshape(irr.shape[:-1])
+    gi = _decode_rgb9e5(words)
+    mx = np.abs(irr).max(-1, keepdims=True)
+    err = np.abs(gi - irr)
+    bound = 2.0 ** -9 * mx + REL * np.maximum(mx, 1e-3 * np.abs(irr).max())
+    print(f"[precision] rgb9e5 max err / bound {np.max(err / np.maximum(bound, 1e-30)):.3f}")
+    assert np.all(err <= bound)
+    # the distance atlas stays FP32
+    assert rel_err(V.dist_atlas().cpu().numpy(), dist).max() <= REL
+    pos, nrm, cam = synth.room_queries()
+    E_ref = oracle.query(desc, st, irr, dist, pos, nrm, cam)
+    E = V.query(to_dev(pos), to_dev(nrm), cam).cpu().numpy()
+    eq = rel_err(E, E_ref).max(-1)
+    print(f"[precision] rgb9e5 query max rel {eq.max():.2e}, median {np.median(eq):.2e}")
+    assert np.median(eq) <= 5 * 2.0 ** -9 and np.mean(eq <= 5e-2) >= 0.999
+
+
+# ------------------------------------------------------ tensor-core blend
+
+def _threshold_straddlers(sc, L, desc, tol):
+    """Texels whose frame-1 change (encoded domain) lies within `tol` of a
+    per-texel threshold: reduced precision may legitimately take the other
+    branch there.  The change is the oracle's: frame 1 rerun with hysteresis 0
+    gives the new value each texel blends in."""
+    h = oracle.SceneHandle(sc)
+    st, irr0, dist0 = oracle.new_state(desc)
+    oracle.update(h, L, desc, 0, st, irr0, dist0)
+    d0 = synth.VolumeDesc(**{**desc.__dict__, "hysteresis_irr": 0.0, "hysteresis_vis": 0.0})
+    st1, irr1, dist1 = st.copy(), irr0.copy(), dist0.copy()
+    oracle.update(h, L, d0, 1, st1, irr1, dist1)
+    delta = np.abs(irr1 - irr0).max(-1)
+    near = (np.abs(delta - desc.thr_low) < tol) | (np.abs(delta - desc.thr_high) < tol)
+    return np.broadcast_to(near[..., None], irr0.shape)
+
+
+@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+@pytest.mark.parametrize("hysteresis", [0.0, 0.9])
+def test_tensor_core_blend_against_oracle(g, mode, hysteresis):
+    """Irradiance in TF32 / BF16 and FP32-accurate distance moments: texels
+    within 1e-3 relative of the FP64 oracle in the stored domain, over two
+    frames (multi-bounce).  With hysteresis, texels whose change sits within
+    the format's error of a threshold are excluded and counted."""
+    prec = g.BLEND_TF32 if mode == "tf32" else g.BLEND_BF16
+    sc = synth.room_scene()
+    L = synth.room_lights()
+    desc = synth.room_volume(hysteresis_irr=hysteresis, hysteresis_vis=0.8 * hysteresis)
+    st, irr, dist, _ = run_oracle(sc, L, desc, [0, 1])
+    V = g.Volume(desc)
+    S = g.Scene.from_arrays(sc)
+    V.update(S, L, 0, precision=prec)
+    V.update(S, L, 1, precision=prec)
+    torch.cuda.synchronize()
+    V.poll_status()
+    assert np.array_equal(V.states().cpu().numpy(), st)
+    gi = V.irr_atlas().cpu().numpy().astype(np.float64)
+    gd = V.dist_atlas().cpu().numpy().astype(np.float64)
+    ei = rel_err(gi, irr)
+    ed = rel_err(gd, dist)
+    skip = np.zeros_like(ei, dtype=bool)
+    if hysteresis > 0:
+        skip = _threshold_straddlers(sc, L, desc, tol=1e-2 if mode == "bf16" else 2e-3)
+    print(f"[precision] {mode} blend (hysteresis {hysteresis}): irr max rel {ei[~skip].max():.2e} "
+          f"(median {np.median(ei):.2e}), dist max rel {ed.max():.2e} (median {np.median(ed):.2e}), "
+          f"threshold-straddling texels excluded: {int(skip[..., 0].sum())} of {skip[..., 0].size}")
+    assert ei[~skip].max() <= 1e-3 and ed.max() <= 1e-3
+    assert skip[..., 0].mean() < 0.01
+    # moments of one weighted distribution: the variance stays non-negative
+    mu, mu2 = gd[..., 0], gd[..., 1]
+    assert np.all(mu2 >= mu * mu * (1 - 1e-6) - 1e-9)
+    pos, nrm, cam = synth.room_queries()
+    E_ref = oracle.query(desc, st, irr, dist, pos, nrm, cam)
+    E = V.query(to_dev(pos), to_dev(nrm), cam).cpu().numpy()
+    eq = rel_err(E, E_ref).max(-1)
+    print(f"[precision] {mode} blend query max rel {eq.max():.2e}, median {np.median(eq):.2e}")
+    assert np.median(eq) <= 1e-3
+
+
+def test_tensor_core_blend_matches_fp32_at_scale(g):
+    """City workload, same rays: the BF16 tensor-core blend against the FP32
+    SIMT blend, every active probe."""
+    sc = synth.city_scene()
+    L = synth.city_lights()
+    desc = synth.city_volume()
+    S = g.Scene.from_arrays(sc)
+    A = g.Volume(desc)
+    B = g.Volume(desc)
+    A.update(S, L, 0)
+    B.update(S, L, 0, precision=g.BLEND_BF16)
+    torch.cuda.synchronize()
+    assert torch.equal(A.states(), B.states())
+    act = (A.states() == g.STATE_VIGILANT).cpu().numpy()
+    ia = A.irr_atlas().cpu().numpy()[act]
+    ib = B.irr_atlas().cpu().numpy()[act]
+    da = A.dist_atlas().cpu().numpy()[act]
+    db = B.dist_atlas().cpu().numpy()[act]
+    ei = rel_err(ib, ia)
+    ed = rel_err(db, da)
+    print(f"[precision] city bf16 vs fp32: irr max {ei.max():.2e}, dist max {ed.max():.2e}, probes {act.sum()}")
+    assert ei.max() <= 1e-3 and ed.max() <= 1e-3
