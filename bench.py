@@ -264,7 +264,7 @@ def run_gpu(args):
         step_ms, query_ms, timings, wall = timed_steps(g.BLEND_FP32)
         mixed = None
         if not args.no_mixed:
-            m_step, m_query, m_tm, _ = timed_steps(g.BLEND_BF16)
+            m_step, m_query, m_tm, _ = timed_steps(g.BLEND_TF32)
             mixed = (m_step, m_query, m_tm)
     ms = float(np.mean(step_ms))
     t = torch.tensor([ms], device=dev)
@@ -321,6 +321,9 @@ def run_gpu(args):
     q_bytes = n_pix * 36                                  # positions + normals in, irradiance out
     hbm = pk.get("hbm_gbs", 6800.0)
 
+    cascade = None if args.no_cascade else run_cascade(args, g, torch, stream)
+    diff = None if args.no_diff else run_diff(args, g, torch, stream)
+
     if rank != 0:
         return
     cpu = None
@@ -333,7 +336,7 @@ def run_gpu(args):
                          f"query points "
                          f"({t_q:.2f} s), extrapolated to {n_act_cpu} active probes (oracle's own "
                          f"estimate) + {n_pix} pixels"}
-    launches_per_step = 7   # frame setup, 2 list builds, classify, trace+shade, blend, query
+    launches_per_step = 9   # frame setup, 2 list builds, classify, 3 trace passes, blend, query
     line = {
         "metric": METRIC, "value": value, "unit": "Grays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -358,8 +361,8 @@ def run_gpu(args):
                            "frac": blend_bytes / (blend_ms * 1e-3) / 1e9 / hbm},
         "roofline_query": {"bound": "hbm", "achieved": q_bytes / (q_ms * 1e-3) / 1e9, "peak": hbm,
                            "unit": "GB/s", "frac": q_bytes / (q_ms * 1e-3) / 1e9 / hbm},
-        "mixed_bf16": None if mixed is None else {
-            "blend": "BF16 irradiance / FP32-accurate distance moments on tcgen05 tensor cores",
+        "mixed_tf32": None if mixed is None else {
+            "blend": "TF32 irradiance / FP32-accurate distance moments on tcgen05 tensor cores",
             "ms_per_step": float(np.mean(mixed[0])),
             "value": rays_per_step / (float(np.mean(mixed[0])) * 1e-3) / 1e9,
             "blend_ms": mixed[2]["blend"][0] / max(mixed[2]["blend"][1], 1),
@@ -368,6 +371,8 @@ def run_gpu(args):
             "blend_tensor_tflops": blend_flops / (mixed[2]["blend"][0] / max(mixed[2]["blend"][1], 1) * 1e-3)
                                    / 1e12,
             "frame_setup_ms": mixed[2]["frame_setup"][0] / max(mixed[2]["frame_setup"][1], 1)},
+        "cascade_batched": cascade,
+        "differentiation": diff,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "Grays/s", "h2d_bytes_per_step": 2 * n_pix * 12,
                 "d2h_bytes_per_step": n_pix * 12},
@@ -377,6 +382,89 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
 
 
+def run_cascade(args, g, torch, stream):
+    """Batched cascades: 4 tracking volumes of 32^3 probes at 1/2/4/8 m over a
+    1M-triangle terrain with buildings, 288 rays per probe, the camera moving
+    0.6 m per frame; every frame is one captured launch sequence over all
+    volumes (CUDA graph), launch shapes from the autotuner."""
+    sc = synth.terrain_scene()
+    L = synth.city_lights()
+    descs = synth.terrain_cascades()
+    scene = g.Scene.from_arrays(sc)
+    C = g.Cascade(descs)
+    cache = os.path.join(ROOT, "_build", "autotune.json")
+    os.makedirs(os.path.dirname(cache), exist_ok=True)
+    from_cache = C.autotune(scene, L, 0, synth.terrain_camera_path(0), cache_path=cache)
+    frame = 1
+    for _ in range(args.warmup):
+        C.update(scene, L, frame, synth.terrain_camera_path(frame), use_graph=True, stream=stream)
+        frame += 1
+    torch.cuda.synchronize()
+    active = [int((C.states(k) == g.STATE_VIGILANT).sum().item()) for k in range(C.n)]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        C.update(scene, L, frame, synth.terrain_camera_path(frame), use_graph=True, stream=stream)
+        frame += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    C.poll_status()
+    ms = e0.elapsed_time(e1) / args.steps
+    rays = sum(active) * descs[0].rays_per_probe
+    return {"workload": "terrain + buildings, 1,048,568 tris; 4 tracking cascades of 32^3 probes at 1/2/4/8 m; "
+                        "288 rays/probe; camera 0.6 m/frame",
+            "ms_per_frame": ms, "grays_per_s": rays / (ms * 1e-3) / 1e9, "active_probes": active,
+            "graph": True, "tuning": {"trace_blocks_per_sm": C.tuning()[0], "blend_probes_per_cta": C.tuning()[1],
+                                      "from_cache": from_cache}}
+
+
+def run_diff(args, g, torch, stream):
+    """Differentiation: 16x8x16 probes (2,048, 128 rays) in a 192k-triangle
+    interior with 64 emissive quads and 257 objects; two frames from a zero
+    atlas (direct + one bounce, gamma 1) queried at 1M surface points; Adam
+    (lr 0.02) on emitter radiance and albedo toward hidden seeded targets."""
+    sc, truth_alb, truth_em = synth.interior_scene()
+    L = synth.Lights()
+    desc = synth.interior_volume()
+    scene = g.Scene.from_arrays(sc)
+    vol = g.Volume(desc)
+    pts, nrm = synth.surface_points(sc, 1_000_000, seed=3005)
+    P = torch.tensor(pts, dtype=torch.float32, device="cuda")
+    N_ = torch.tensor(nrm, dtype=torch.float32, device="cuda")
+    cam = np.array([0.0, 10.0, 0.0])
+    ta = torch.tensor(truth_alb, dtype=torch.float32, device="cuda")
+    te = torch.tensor(truth_em, dtype=torch.float32, device="cuda")
+    with torch.no_grad():
+        target = g.IrradianceField.apply(ta, te, vol, scene, L, P, N_, cam, 0, 2).clone()
+    rng = synth.Rng(4005)
+    albedo = torch.full_like(ta, 0.5).requires_grad_(True)
+    emit = torch.tensor(np.repeat(rng.uniform(len(truth_em), 0.1, 2.0)[:, None], 3, axis=1), dtype=torch.float32,
+                        device="cuda").requires_grad_(True)
+    opt = torch.optim.Adam([albedo, emit], lr=0.02)
+    losses = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    steps = 200
+    e0.record(stream)
+    for _ in range(steps):
+        opt.zero_grad()
+        E = g.IrradianceField.apply(albedo, emit, vol, scene, L, P, N_, cam, 0, 2)
+        loss = ((E - target) ** 2).mean()
+        loss.backward()
+        opt.step()
+        losses.append(loss.detach())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    losses = [float(x) for x in losses]
+    return {"workload": "interior 192,140 tris, 257 objects, 64 emitters; 2,048 probes x 128 rays; 2 frames; "
+                        "1M query points; Adam lr 0.02",
+            "adam_steps": steps, "ms_per_step": ms, "loss_first": losses[0], "loss_last": losses[-1],
+            "emitter_max_abs_err": float((emit.detach() - te).abs().max()),
+            "emitter_mean_abs_err": float((emit.detach() - te).abs().mean())}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,7 +472,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the BF16 tensor-core blend timing")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the TF32 tensor-core blend timing")
+    ap.add_argument("--no-cascade", action="store_true", help="skip the batched cascade workload")
+    ap.add_argument("--no-diff", action="store_true", help="skip the differentiation workload")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

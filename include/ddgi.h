@@ -36,8 +36,9 @@
 extern "C" {
 #endif
 
-typedef struct ddgi_scene_s*  ddgi_scene;
-typedef struct ddgi_volume_s* ddgi_volume;
+typedef struct ddgi_scene_s*   ddgi_scene;
+typedef struct ddgi_volume_s*  ddgi_volume;
+typedef struct ddgi_cascade_s* ddgi_cascade;
 typedef void*                 ddgi_stream;   /* cudaStream_t */
 
 typedef enum {
@@ -161,7 +162,7 @@ typedef struct {
     int32_t state_machine;      /* 1: classify probes (Sec. 6.3); 0: all probes vigilant */
     int32_t irr_format;         /* DDGI_IRR_* */
     int32_t dist_format;        /* DDGI_DIST_* */
-    int32_t reserved;
+    int32_t tracking;           /* cascades: 1 = camera-tracking window (Sec. 7.2) */
     uint64_t seed;              /* seed of the per-frame random rotation */
 } ddgi_volume_desc;
 
@@ -209,6 +210,15 @@ typedef struct {
  * Errors: INVALID_ARG (nothing enqueued), CUDA. */
 ddgi_status ddgi_update(ddgi_volume volume, ddgi_scene scene, const ddgi_lights* lights,
                         const ddgi_update_params* params, ddgi_stream stream);
+
+/* ddgi_update restricted to probes [probe_begin, probe_end) (a shard): only
+ * those probes are classified, traced, blended and advanced; hit shading still
+ * samples every probe of the volume's current atlas.  Running the shards of a
+ * frame on copies of the same state and exchanging the updated ranges gives
+ * the same atlas as one ddgi_update.  Errors: INVALID_ARG on a bad range. */
+ddgi_status ddgi_update_range(ddgi_volume volume, ddgi_scene scene, const ddgi_lights* lights,
+                              const ddgi_update_params* params, int64_t probe_begin, int64_t probe_end,
+                              ddgi_stream stream);
 
 /* Irradiance query (Sec. 2.2) at n points: self-shadow bias
  * (n*0.2 + w_o*0.8)*(0.75*D)*B with w_o towards camera_pos and D the minimum
@@ -258,6 +268,102 @@ ddgi_status ddgi_trace_stats(ddgi_volume volume, ddgi_scene scene, const ddgi_li
 /* Device status word: non-finite texel detected, or a bounded wait that
  * gave up.  Reads and clears it (synchronises the stream). */
 ddgi_status ddgi_poll_status(ddgi_volume volume, ddgi_stream stream);
+
+/* ------------------------------------------------------------------ */
+/* Cascades of volumes with tracking windows                           */
+/* ------------------------------------------------------------------ */
+
+/* Nested volumes at different spacings (Sec. 7.3), densest first, each
+ * optionally a camera-tracking window (desc.tracking = 1, Sec. 7.2): when the
+ * camera is more than one spacing from a window's centre along an axis, the
+ * plane behind it leapfrogs to the front (a circular buffer of planes) and is
+ * reset to zero texels and UNINIT.  Volumes must share rays_per_probe, tile
+ * sizes, formats, gamma, hysteresis and thresholds; they share one ray
+ * pattern per frame (the first descriptor's seed).  n in [1, 8].
+ * Synchronises the device once.  Errors: INVALID_ARG, OOM. */
+ddgi_status ddgi_cascade_create(const ddgi_volume_desc* descs, int32_t n, ddgi_cascade* out);
+void ddgi_cascade_destroy(ddgi_cascade cascade);
+
+typedef struct {
+    int64_t frame;
+    float   camera_pos[3];      /* moves tracking windows; centres their fall-off boxes */
+    float   irr_hyst_scale;
+    float   vis_hyst_scale;
+    int32_t blend_precision;    /* DDGI_BLEND_* */
+    int32_t use_graph;          /* 1: replay the frame's launches as a CUDA graph */
+} ddgi_cascade_params;
+
+/* One update frame of every volume in one batched launch sequence: the
+ * windows scroll, leapfrogged planes reset, then classification, trace and
+ * shade, blend and state advance run over all volumes' probes together; hit
+ * shading samples the whole cascade of the previous frame (Sec. 7.3
+ * weights).  Per-frame parameters go through device memory, so with
+ * use_graph the sequence is captured once (per precision, lights,
+ * hysteresis scales and tuning) and replayed.  Blocks the host only while an
+ * earlier frame still reads the pinned parameter slot this frame reuses
+ * (two slots).  Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+ddgi_status ddgi_cascade_update(ddgi_cascade cascade, ddgi_scene scene, const ddgi_lights* lights,
+                                const ddgi_cascade_params* params, ddgi_stream stream);
+
+/* Cascade query (Sec. 2.2 per volume, Sec. 7.3 blending): volumes densest
+ * first, weight = product over axes of a linear fall-off over the last cell
+ * of the volume's box (for tracking windows a box tightened by one cell and
+ * centred on the last update's camera), accumulated until the weights reach
+ * 1, normalised by the weights taken.  Same buffers as ddgi_query. */
+ddgi_status ddgi_cascade_query(ddgi_cascade cascade, const float* pos_dev, const float* nrm_dev, int64_t n,
+                               const float camera_pos[3], float* out_dev, ddgi_stream stream);
+
+/* Buffers of volume `vol` as in ddgi_get_buffer, and its current window:
+ * origin (world position of logical probe (0,0,0)) and the circular shift
+ * (logical (i,j,k) is stored at (i+shift) mod count). */
+ddgi_status ddgi_cascade_get_buffer(ddgi_cascade cascade, int32_t vol, int32_t which, void* dst_dev,
+                                    size_t bytes, ddgi_stream stream);
+ddgi_status ddgi_cascade_get_window(ddgi_cascade cascade, int32_t vol, double origin[3], int32_t shift[3]);
+
+/* Launch shapes: trace kernels' blocks per SM (1..32) and the SIMT blend's
+ * probes per CTA (4, 8 or 16).  ddgi_cascade_autotune times the update under
+ * each candidate and keeps the fastest, caching the choice in a JSON file at
+ * cache_path (keyed by GPU name and workload); *from_cache = 1 when the cache
+ * answered.  Timing advances the volumes by the frames it runs. */
+ddgi_status ddgi_cascade_set_tuning(ddgi_cascade cascade, int32_t trace_blocks_per_sm,
+                                    int32_t blend_probes_per_cta);
+ddgi_status ddgi_cascade_get_tuning(ddgi_cascade cascade, int32_t* trace_blocks_per_sm,
+                                    int32_t* blend_probes_per_cta);
+ddgi_status ddgi_cascade_autotune(ddgi_cascade cascade, ddgi_scene scene, const ddgi_lights* lights,
+                                  const ddgi_cascade_params* params, const char* cache_path,
+                                  int32_t* from_cache, ddgi_stream stream);
+ddgi_status ddgi_cascade_poll_status(ddgi_cascade cascade, ddgi_stream stream);
+
+/* ------------------------------------------------------------------ */
+/* Differentiation                                                     */
+/* ------------------------------------------------------------------ */
+
+/* Replace the scene's materials from device arrays: albedo [n_objects][3],
+ * emitter radiance [n_emitters][3] (either may be NULL to keep it). */
+ddgi_status ddgi_scene_set_materials(ddgi_scene scene, const float* albedo_dev, const float* emit_dev,
+                                     ddgi_stream stream);
+
+/* Differentiable forward: resets the volume to a zero atlas with every probe
+ * VIGILANT, runs n_frames (1..8) updates from first_frame (hysteresis 0,
+ * so frame f holds direct light plus f bounces through the probes), keeps
+ * the atlas after each frame, then queries E at the points (as ddgi_query).
+ * The volume needs hysteresis 0, the state machine off and FP32 atlases
+ * (UNSUPPORTED otherwise). */
+ddgi_status ddgi_diff_forward(ddgi_volume volume, ddgi_scene scene, const ddgi_lights* lights, int64_t first_frame,
+                              int32_t n_frames, const float* pos_dev, const float* nrm_dev, int64_t n,
+                              const float camera_pos[3], float* out_dev, ddgi_stream stream);
+
+/* Reverse pass of the last ddgi_diff_forward: given dE_dev [n][3] = dLoss/dE,
+ * writes dLoss/d(albedo) [n_objects][3] and dLoss/d(emitter radiance)
+ * [n_emitters][3].  The query's weights, hits and distances are constants of
+ * the fixed geometry; rays are traced again rather than stored; texel
+ * gradients flow back through the gamma encoding, the normalised cosine
+ * blend, the border copy and each frame's hit shading into the previous
+ * frame's atlas. */
+ddgi_status ddgi_diff_backward(ddgi_volume volume, ddgi_scene scene, const ddgi_lights* lights,
+                               int64_t first_frame, int32_t n_frames, const float* pos_dev, const float* nrm_dev,
+                               int64_t n, const float camera_pos[3], const float* dE_dev, float* d_albedo_dev,
+                               float* d_emit_dev, ddgi_stream stream);
 
 /* ------------------------------------------------------------------ */
 /* Allocation-free update                                              */

@@ -127,6 +127,8 @@ def _declare(lib):
     lib.or_query_cascade.argtypes = [C.c_int64, C.POINTER(OrVolume), C.POINTER(_u8p),
                                      C.POINTER(_dp), C.POINTER(_dp), C.c_int64, _dp, _dp, _dp,
                                      _dp, _dp]
+    lib.or_diff.argtypes = [C.POINTER(OrScene), C.POINTER(OrLights), C.POINTER(OrVolume), C.c_int64,
+                            C.c_int64, C.c_int64, _dp, _dp, _dp, _dp, _dp, _dp, _dp, C.c_int64, C.c_int64]
     lib.or_tracking_scroll.argtypes = [C.POINTER(OrVolume), _dp, _u8p, _dp, _dp]
     lib.or_tracking_scroll.restype = C.c_int64
     lib.or_update_cascade.argtypes = [C.POINTER(OrScene), C.POINTER(OrLights), C.c_int64,
@@ -405,3 +407,24 @@ def update_cascade(scene_h, lights, vol_structs, frame, states_list, irr_list, d
     lib().or_update_cascade(C.byref(scene_h.s), C.byref(make_lights(lights)), k, vols, frame,
                             irr_scale, vis_scale, sp, ip, dp, _ptr(nsub, _i64p), subp, rp)
     return rays
+
+
+def diff(scene_h, lights, desc, pos, nrm, camera, dE, first_frame=0, n_frames=2):
+    """Forward E and the reverse-mode gradient of sum(dE * E) with respect to
+    emitter radiance [E,3] and object albedo [O,3] (hysteresis 0, every probe
+    tracing, n_frames updates from a zero atlas)."""
+    pos = _f64(pos, (-1, 3))
+    nrm = _f64(nrm, (-1, 3))
+    dE = _f64(dE, (-1, 3))
+    cam = _f64(camera, (3,))
+    n = len(pos)
+    E = np.zeros((n, 3))
+    ne = len(scene_h.emitter_radiance) if scene_h.tri_emitter.max(initial=-1) >= 0 else 0
+    no = len(scene_h.object_albedo)
+    g_em = np.zeros((max(ne, 1), 3))
+    g_al = np.zeros((no, 3))
+    v = make_volume(desc)
+    lib().or_diff(C.byref(scene_h.s), C.byref(make_lights(lights)), C.byref(v), first_frame, n_frames, n,
+                  _ptr(pos, _dp), _ptr(nrm, _dp), _ptr(cam, _dp), _ptr(dE, _dp), _ptr(E, _dp),
+                  _ptr(g_em, _dp), _ptr(g_al, _dp), ne, no)
+    return E, g_em[:ne], g_al

@@ -784,3 +784,207 @@ void or_update_cascade(const or_scene* s, const or_lights* L, int64_t n_vol, con
     free(nl);
     free(dirs);
 }
+
+/* ------------------------------------------------------------------ */
+/* Differentiation: reverse mode through n_frames updates from a zero   */
+/* atlas with hysteresis 0, followed by the query (Sec. 2.2-2.3, 4.2).  */
+/* Parameters are the emitters' radiance and the objects' albedo;       */
+/* geometry (hits, distances, Chebyshev and backface weights) is fixed. */
+/* ------------------------------------------------------------------ */
+
+/* Query adjoint: accumulates dM into texel gradients g_irr (bordered tiles
+ * of the atlas `irr`).  M_c = A_c^2, A_c = sum_p w_p a_pc / sum_p w_p,
+ * a_pc = b_pc^(gamma/2) with b_pc the bilinear sample; d a / d b is 0 where
+ * b <= 0. */
+static void query_M_adjoint(const or_volume* v, const uint8_t* st, const double* irr, const double* dist,
+                            const double x[3], const double n[3], const double wo[3], const double dM[3],
+                            double* g_irr) {
+    double wts[8];
+    double M[3];
+    query_M(v, st, irr, dist, x, n, wo, M, wts);
+    double D = min_spacing(v);
+    double xb[3];
+    for (int a = 0; a < 3; ++a) xb[a] = x[a] + (0.2 * n[a] + 0.8 * wo[a]) * (0.75 * D) * v->bias_B;
+    int64_t base[3];
+    for (int a = 0; a < 3; ++a) {
+        double g = (xb[a] - v->origin[a]) / v->spacing[a];
+        double b = floor(g);
+        double bmax = (double)(v->counts[a] - 2);
+        if (b > bmax) b = bmax;
+        if (b < 0.0) b = 0.0;
+        base[a] = (int64_t)b;
+    }
+    double W = 0.0;
+    for (int c = 0; c < 8; ++c) W += wts[c];
+    if (!(W > 0.0)) return;
+    int64_t tsi = irr_tile_size(v), N = v->irr_n + 2, ni = v->irr_n;
+    double A[3];
+    for (int k = 0; k < 3; ++k) A[k] = sqrt(fmax(M[k], 0.0));
+    /* the tile footprint of direction n */
+    double u[2];
+    or_oct_encode(n, u);
+    double sx = 1.0 + (u[0] + 1.0) * 0.5 * (double)ni - 0.5, sy = 1.0 + (u[1] + 1.0) * 0.5 * (double)ni - 0.5;
+    int64_t x0 = (int64_t)floor(sx), y0 = (int64_t)floor(sy);
+    if (x0 > N - 2) x0 = N - 2;
+    if (y0 > N - 2) y0 = N - 2;
+    if (x0 < 0) x0 = 0;
+    if (y0 < 0) y0 = 0;
+    double tx = sx - (double)x0, ty = sy - (double)y0;
+    double bw[4] = { (1 - tx) * (1 - ty), tx * (1 - ty), (1 - tx) * ty, tx * ty };
+    int64_t bx[4] = { x0, x0 + 1, x0, x0 + 1 }, by[4] = { y0, y0, y0 + 1, y0 + 1 };
+    for (int c = 0; c < 8; ++c) {
+        if (!(wts[c] > 0.0)) continue;
+        int o[3] = { c & 1, (c >> 1) & 1, (c >> 2) & 1 };
+        int64_t p = or_probe_phys(v, base[0] + o[0], base[1] + o[1], base[2] + o[2]);
+        double b[3];
+        or_sample_bilinear(irr + p * tsi, ni, 3, n, b);
+        for (int k = 0; k < 3; ++k) {
+            if (!(b[k] > 0.0)) continue;
+            double dA = dM[k] * 2.0 * A[k];                                  /* dM/dA */
+            double da = dA * wts[c] / W;                                     /* dA/da_p */
+            double db = da * 0.5 * v->gamma * pow(b[k], 0.5 * v->gamma - 1.0);  /* da/db */
+            for (int j = 0; j < 4; ++j) g_irr[p * tsi + (by[j] * N + bx[j]) * 3 + k] += db * bw[j];
+        }
+    }
+}
+
+/* Folds border-texel gradients into the interior texels they copy. */
+static void border_fold(double* g_tile, int64_t n, int64_t C) {
+    int64_t N = n + 2;
+    /* same source map as or_border_copy, transposed */
+    for (int64_t k = 1; k <= n; ++k)
+        for (int64_t c = 0; c < C; ++c) {
+            TILE(g_tile, N, C, 1, n + 1 - k)[c] += TILE(g_tile, N, C, 0, k)[c];
+            TILE(g_tile, N, C, n, n + 1 - k)[c] += TILE(g_tile, N, C, n + 1, k)[c];
+            TILE(g_tile, N, C, n + 1 - k, 1)[c] += TILE(g_tile, N, C, k, 0)[c];
+            TILE(g_tile, N, C, n + 1 - k, n)[c] += TILE(g_tile, N, C, k, n + 1)[c];
+        }
+    for (int64_t c = 0; c < C; ++c) {
+        TILE(g_tile, N, C, n, n)[c] += TILE(g_tile, N, C, 0, 0)[c];
+        TILE(g_tile, N, C, 1, n)[c] += TILE(g_tile, N, C, n + 1, 0)[c];
+        TILE(g_tile, N, C, n, 1)[c] += TILE(g_tile, N, C, 0, n + 1)[c];
+        TILE(g_tile, N, C, 1, 1)[c] += TILE(g_tile, N, C, n + 1, n + 1)[c];
+    }
+    for (int64_t y = 0; y < N; ++y)
+        for (int64_t x = 0; x < N; ++x)
+            if (x == 0 || y == 0 || x == N - 1 || y == N - 1)
+                for (int64_t c = 0; c < C; ++c) TILE(g_tile, N, C, x, y)[c] = 0.0;
+}
+
+/* Forward: n_frames updates (state machine off: every probe traces) from a
+ * zero atlas with hysteresis 0, then E at the query points.  Backward: the
+ * gradient of sum(dE * E) with respect to emitter radiance [n_em][3] and
+ * object albedo [n_obj][3].  E_out may be NULL. */
+void or_diff(const or_scene* s, const or_lights* L, const or_volume* v, int64_t first_frame, int64_t n_frames,
+             int64_t n, const double* pos, const double* nrm, const double camera[3], const double* dE,
+             double* E_out, double* d_emit, double* d_albedo, int64_t n_emitters, int64_t n_objects) {
+    int64_t P = v->counts[0] * v->counts[1] * v->counts[2], R = v->rays;
+    int64_t tsi = irr_tile_size(v), tsd = dist_tile_size(v);
+    or_volume vv = *v;
+    vv.hyst_irr = 0.0;
+    vv.hyst_vis = 0.0;
+    vv.state_machine = 0;
+    /* atlases per frame: [f] is the atlas after frame f; index -1 is zero */
+    double** irr = (double**)malloc(sizeof(double*) * (size_t)(n_frames + 1));
+    double** dist = (double**)malloc(sizeof(double*) * (size_t)(n_frames + 1));
+    uint8_t* st = (uint8_t*)malloc((size_t)P);
+    memset(st, OR_VIGILANT, (size_t)P);
+    for (int64_t f = 0; f <= n_frames; ++f) {
+        irr[f] = (double*)calloc((size_t)(P * tsi), sizeof(double));
+        dist[f] = (double*)calloc((size_t)(P * tsd), sizeof(double));
+    }
+    for (int64_t f = 0; f < n_frames; ++f) {
+        memcpy(irr[f + 1], irr[f], sizeof(double) * (size_t)(P * tsi));
+        memcpy(dist[f + 1], dist[f], sizeof(double) * (size_t)(P * tsd));
+        or_update(s, L, &vv, first_frame + f, 1.0, 1.0, st, irr[f + 1], dist[f + 1], 0, NULL, NULL);
+    }
+    /* query of the last atlas */
+    double* g = (double*)calloc((size_t)(P * tsi), sizeof(double));
+    for (int64_t q = 0; q < n; ++q) {
+        const double* x = pos + 3 * q;
+        const double* nn = nrm + 3 * q;
+        if (nn[0] == 0.0 && nn[1] == 0.0 && nn[2] == 0.0) {
+            if (E_out) for (int k = 0; k < 3; ++k) E_out[3 * q + k] = 0.0;
+            continue;
+        }
+        double wo[3];
+        sub3(camera, x, wo);
+        double l = len3(wo);
+        if (l < 1e-6) { wo[0] = nn[0]; wo[1] = nn[1]; wo[2] = nn[2]; }
+        else { wo[0] /= l; wo[1] /= l; wo[2] /= l; }
+        double M[3], dM[3];
+        query_M(&vv, st, irr[n_frames], dist[n_frames], x, nn, wo, M, NULL);
+        for (int k = 0; k < 3; ++k) {
+            if (E_out) E_out[3 * q + k] = M_PI * M[k];
+            dM[k] = M_PI * dE[3 * q + k];
+        }
+        query_M_adjoint(&vv, st, irr[n_frames], dist[n_frames], x, nn, wo, dM, g);
+    }
+    for (int64_t k = 0; k < 3 * n_emitters; ++k) d_emit[k] = 0.0;
+    for (int64_t k = 0; k < 3 * n_objects; ++k) d_albedo[k] = 0.0;
+    double* dirs = (double*)malloc(sizeof(double) * 3 * (size_t)R);
+    double* gp = (double*)calloc((size_t)(P * tsi), sizeof(double));
+    for (int64_t f = n_frames - 1; f >= 0; --f) {
+        /* gradients of the texels written by frame f -> ray radiance -> parameters and frame f-1 */
+        or_frame_dirs(vv.seed, first_frame + f, R, dirs);
+        memset(gp, 0, sizeof(double) * (size_t)(P * tsi));
+        for (int64_t p = 0; p < P; ++p) {
+            double* gt = g + p * tsi;
+            border_fold(gt, v->irr_n, 3);
+            double xp[3];
+            probe_pos_phys(&vv, p, xp);
+            for (int64_t r = 0; r < R; ++r) {
+                const double* d = dirs + 3 * r;
+                /* dL_r = sum_t W_tr / s_t * dm_t, dm = de * (1/gamma) m^(1/gamma - 1) */
+                double gL[3] = {0.0, 0.0, 0.0};
+                for (int64_t j = 0; j < v->irr_n; ++j)
+                    for (int64_t i = 0; i < v->irr_n; ++i) {
+                        double nt[3];
+                        or_texel_dir(i, j, v->irr_n, nt);
+                        double sw = 0.0;
+                        for (int64_t rr = 0; rr < R; ++rr) sw += fmax(0.0, dot3(nt, dirs + 3 * rr));
+                        if (!(sw > 0.0)) continue;
+                        double w = fmax(0.0, dot3(nt, d)) / sw;
+                        const double* e = irr[f + 1] + p * tsi + ((j + 1) * (v->irr_n + 2) + (i + 1)) * 3;
+                        const double* gg = gt + ((j + 1) * (v->irr_n + 2) + (i + 1)) * 3;
+                        for (int k = 0; k < 3; ++k) {
+                            double m = pow(e[k], vv.gamma);
+                            double dedm = m > 0.0 ? pow(m, 1.0 / vv.gamma - 1.0) / vv.gamma : (vv.gamma == 1.0 ? 1.0 : 0.0);
+                            gL[k] += w * gg[k] * dedm;
+                        }
+                    }
+                if (gL[0] == 0.0 && gL[1] == 0.0 && gL[2] == 0.0) continue;
+                /* shading adjoint of this ray (re-traced) */
+                double t;
+                int64_t tri;
+                int back;
+                if (!or_closest_hit(s, xp, d, &t, &tri, &back) || back) continue;
+                double x[3] = { xp[0] + t * d[0], xp[1] + t * d[1], xp[2] + t * d[2] };
+                double nn[3];
+                tri_unit_normal(s, tri, nn);
+                int32_t obj = s->tri_object[tri], em = s->tri_emitter[tri];
+                if (em >= 0) for (int k = 0; k < 3; ++k) d_emit[3 * em + k] += gL[k];
+                double tol[3] = { -L->sun_dir[0], -L->sun_dir[1], -L->sun_dir[2] };
+                double cosl = dot3(nn, tol), direct[3] = {0.0, 0.0, 0.0};
+                if (cosl > 0.0 && (L->sun_irradiance[0] > 0.0 || L->sun_irradiance[1] > 0.0 || L->sun_irradiance[2] > 0.0)) {
+                    double off = 1e-4 * (1.0 + len3(x));
+                    double so[3] = { x[0] + off * nn[0], x[1] + off * nn[1], x[2] + off * nn[2] };
+                    if (!or_any_hit_shadow(s, so, tol))
+                        for (int k = 0; k < 3; ++k) direct[k] = L->sun_irradiance[k] * cosl / M_PI;
+                }
+                double wo[3] = { -d[0], -d[1], -d[2] }, Mp[3];
+                query_M(&vv, st, irr[f], dist[f], x, nn, wo, Mp, NULL);
+                const double* rho = s->object_albedo + 3 * (int64_t)obj;
+                double dMp[3];
+                for (int k = 0; k < 3; ++k) {
+                    d_albedo[3 * obj + k] += gL[k] * (direct[k] + Mp[k]);
+                    dMp[k] = gL[k] * rho[k];
+                }
+                if (f > 0) query_M_adjoint(&vv, st, irr[f], dist[f], x, nn, wo, dMp, gp);
+            }
+        }
+        double* tmp = g; g = gp; gp = tmp;
+    }
+    for (int64_t f = 0; f <= n_frames; ++f) { free(irr[f]); free(dist[f]); }
+    free(irr); free(dist); free(st); free(g); free(gp); free(dirs);
+}

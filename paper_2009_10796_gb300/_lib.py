@@ -36,7 +36,7 @@ class VolumeDesc(C.Structure):
                 ("self_shadow_bias", C.c_float), ("dist_cos_power", C.c_float), ("t_max", C.c_float),
                 ("thr_low", C.c_float), ("thr_high", C.c_float), ("thr_step", C.c_float),
                 ("state_machine", C.c_int32), ("irr_format", C.c_int32), ("dist_format", C.c_int32),
-                ("reserved", C.c_int32), ("seed", C.c_uint64)]
+                ("tracking", C.c_int32), ("seed", C.c_uint64)]
 
 
 class VolumeInfo(C.Structure):
@@ -48,6 +48,11 @@ class VolumeInfo(C.Structure):
 class UpdateParams(C.Structure):
     _fields_ = [("frame", C.c_int64), ("irr_hyst_scale", C.c_float), ("vis_hyst_scale", C.c_float),
                 ("blend_precision", C.c_int32), ("reserved", C.c_int32)]
+
+
+class CascadeParams(C.Structure):
+    _fields_ = [("frame", C.c_int64), ("camera_pos", F3), ("irr_hyst_scale", C.c_float),
+                ("vis_hyst_scale", C.c_float), ("blend_precision", C.c_int32), ("use_graph", C.c_int32)]
 
 
 _vp = C.c_void_p
@@ -69,6 +74,8 @@ SIGNATURES = {
     "ddgi_volume_get_info": (C.c_int, [_vp, C.POINTER(VolumeInfo)]),
     "ddgi_update": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.POINTER(UpdateParams), _vp]),
     "ddgi_query": (C.c_int, [_vp, _vp, _vp, C.c_int64, F3, _vp, _vp]),
+    "ddgi_update_range": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.POINTER(UpdateParams), C.c_int64, C.c_int64,
+                                    _vp]),
     "ddgi_get_buffer": (C.c_int, [_vp, C.c_int32, _vp, C.c_size_t, _vp]),
     "ddgi_set_buffer": (C.c_int, [_vp, C.c_int32, _vp, C.c_size_t, _vp]),
     "ddgi_get_ray_records": (C.c_int, [_vp, _vp, _vp, C.POINTER(C.c_int64), _vp]),
@@ -78,6 +85,22 @@ SIGNATURES = {
     "ddgi_trace_stats": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.c_uint64 * 7, _vp]),
     "ddgi_update_noalloc": (C.c_int, [_vp, C.POINTER(VolumeDesc), C.POINTER(Lights),
                                       C.POINTER(UpdateParams), _vp, _vp, _vp, _vp]),
+    "ddgi_cascade_create": (C.c_int, [C.POINTER(VolumeDesc), C.c_int32, C.POINTER(_vp)]),
+    "ddgi_cascade_destroy": (None, [_vp]),
+    "ddgi_cascade_update": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.POINTER(CascadeParams), _vp]),
+    "ddgi_cascade_query": (C.c_int, [_vp, _vp, _vp, C.c_int64, F3, _vp, _vp]),
+    "ddgi_cascade_get_buffer": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.c_size_t, _vp]),
+    "ddgi_cascade_get_window": (C.c_int, [_vp, C.c_int32, C.c_double * 3, C.c_int32 * 3]),
+    "ddgi_cascade_set_tuning": (C.c_int, [_vp, C.c_int32, C.c_int32]),
+    "ddgi_cascade_get_tuning": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "ddgi_cascade_autotune": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.POINTER(CascadeParams), C.c_char_p,
+                                        C.POINTER(C.c_int32), _vp]),
+    "ddgi_cascade_poll_status": (C.c_int, [_vp, _vp]),
+    "ddgi_scene_set_materials": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "ddgi_diff_forward": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.c_int64, C.c_int32, _vp, _vp, C.c_int64, F3,
+                                    _vp, _vp]),
+    "ddgi_diff_backward": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.c_int64, C.c_int32, _vp, _vp, C.c_int64, F3,
+                                     _vp, _vp, _vp, _vp]),
 }
 
 

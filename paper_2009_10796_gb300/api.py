@@ -15,7 +15,7 @@ import torch
 from . import _lib
 from ._lib import check, load
 
-__all__ = ["Scene", "Volume", "trace", "lights_struct", "update_noalloc"]
+__all__ = ["Scene", "Volume", "Cascade", "IrradianceField", "trace", "lights_struct", "update_noalloc"]
 
 
 def _stream(stream):
@@ -87,6 +87,12 @@ class Scene:
                                 _stream(stream)))
         return t, tri, bf
 
+    def set_materials(self, albedo: torch.Tensor = None, emit: torch.Tensor = None, stream=None):
+        """Object albedo [O,3] and emitter radiance [E,3] from device tensors."""
+        a = albedo.detach().float().contiguous() if albedo is not None else None
+        e = emit.detach().float().contiguous() if emit is not None else None
+        check(load().ddgi_scene_set_materials(self.handle, _ptr(a), _ptr(e), _stream(stream)))
+
     def raycast_gbuffer(self, position, forward, up, vfov_deg, width, height, stream=None,
                         device="cuda"):
         pos = torch.empty((height * width, 3), dtype=torch.float32, device=device)
@@ -129,6 +135,7 @@ def desc_struct(d) -> _lib.VolumeDesc:
     s.state_machine = int(getattr(d, "state_machine", 1))
     s.irr_format = int(getattr(d, "irr_format", _lib.IRR_FP32))
     s.dist_format = int(getattr(d, "dist_format", _lib.DIST_FP32))
+    s.tracking = int(getattr(d, "tracking", 0))
     s.seed = int(getattr(d, "seed", 0))
     return s
 
@@ -157,6 +164,14 @@ class Volume:
         p = _lib.UpdateParams(int(frame), float(irr_scale), float(vis_scale), int(precision), 0)
         L = lights if isinstance(lights, _lib.Lights) else lights_struct(lights)
         check(load().ddgi_update(self.handle, scene.handle, C.byref(L), C.byref(p), _stream(stream)))
+
+    def update_range(self, scene: Scene, lights, frame: int, probe_begin: int, probe_end: int, irr_scale=1.0,
+                     vis_scale=1.0, precision=_lib.BLEND_FP32, stream=None):
+        """Update only probes [probe_begin, probe_end) (one shard of the grid)."""
+        p = _lib.UpdateParams(int(frame), float(irr_scale), float(vis_scale), int(precision), 0)
+        L = lights if isinstance(lights, _lib.Lights) else lights_struct(lights)
+        check(load().ddgi_update_range(self.handle, scene.handle, C.byref(L), C.byref(p), int(probe_begin),
+                                       int(probe_end), _stream(stream)))
 
     def query(self, pos: torch.Tensor, nrm: torch.Tensor, camera, out: torch.Tensor = None,
               stream=None) -> torch.Tensor:
@@ -220,6 +235,25 @@ class Volume:
         keys = ["rays", "nodes", "tris", "shadow_rays", "shadow_nodes", "shadow_tris", "queries"]
         return {k: int(st[i]) for i, k in enumerate(keys)}
 
+    def diff_forward(self, scene: Scene, lights, pos, nrm, camera, first_frame=0, n_frames=2, stream=None):
+        out = torch.empty((pos.shape[0], 3), dtype=torch.float32, device=pos.device)
+        L = lights if isinstance(lights, _lib.Lights) else lights_struct(lights)
+        check(load().ddgi_diff_forward(self.handle, scene.handle, C.byref(L), int(first_frame), int(n_frames),
+                                       _ptr(pos), _ptr(nrm), pos.shape[0], _f3(camera), _ptr(out),
+                                       _stream(stream)))
+        return out
+
+    def diff_backward(self, scene: Scene, lights, pos, nrm, camera, dE, n_objects, n_emitters, first_frame=0,
+                      n_frames=2, stream=None):
+        d_alb = torch.empty((n_objects, 3), dtype=torch.float32, device=pos.device)
+        d_em = torch.empty((max(n_emitters, 1), 3), dtype=torch.float32, device=pos.device)
+        L = lights if isinstance(lights, _lib.Lights) else lights_struct(lights)
+        dE = dE.float().contiguous()
+        check(load().ddgi_diff_backward(self.handle, scene.handle, C.byref(L), int(first_frame), int(n_frames),
+                                        _ptr(pos), _ptr(nrm), pos.shape[0], _f3(camera), _ptr(dE), _ptr(d_alb),
+                                        _ptr(d_em), _stream(stream)))
+        return d_alb, d_em[:n_emitters]
+
     def enable_timing(self, on=True):
         check(load().ddgi_enable_timing(self.handle, int(bool(on))))
 
@@ -260,3 +294,126 @@ def update_noalloc(scene: Scene, desc, lights, frame: int, states: torch.Tensor,
     L = lights if isinstance(lights, _lib.Lights) else lights_struct(lights)
     check(load().ddgi_update_noalloc(scene.handle, C.byref(d), C.byref(L), C.byref(p), _ptr(states),
                                      _ptr(irr), _ptr(dist), _stream(stream)))
+
+
+class Cascade:
+    """Nested probe volumes updated together (densest first), optionally
+    camera-tracking windows; see ddgi_cascade_* in include/ddgi.h."""
+
+    def __init__(self, descs):
+        arr = (_lib.VolumeDesc * len(descs))(*[d if isinstance(d, _lib.VolumeDesc) else desc_struct(d)
+                                               for d in descs])
+        self.descs = list(arr)
+        h = C.c_void_p()
+        check(load().ddgi_cascade_create(arr, len(descs), C.byref(h)))
+        self.handle = h
+        self.n = len(descs)
+
+    def _params(self, frame, camera, irr_scale, vis_scale, precision, use_graph):
+        return _lib.CascadeParams(int(frame), _f3(camera), float(irr_scale), float(vis_scale),
+                                  int(precision), int(bool(use_graph)))
+
+    def update(self, scene: Scene, lights, frame: int, camera, irr_scale=1.0, vis_scale=1.0,
+               precision=_lib.BLEND_FP32, use_graph=False, stream=None):
+        p = self._params(frame, camera, irr_scale, vis_scale, precision, use_graph)
+        L = lights if isinstance(lights, _lib.Lights) else lights_struct(lights)
+        check(load().ddgi_cascade_update(self.handle, scene.handle, C.byref(L), C.byref(p), _stream(stream)))
+
+    def query(self, pos: torch.Tensor, nrm: torch.Tensor, camera, out: torch.Tensor = None, stream=None):
+        n = pos.shape[0]
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+        check(load().ddgi_cascade_query(self.handle, _ptr(pos), _ptr(nrm), n, _f3(camera), _ptr(out),
+                                        _stream(stream)))
+        return out
+
+    def _sizes(self, k):
+        d = self.descs[k]
+        P = d.counts[0] * d.counts[1] * d.counts[2]
+        tb = {0: 12, 1: 8, 2: 4}[d.irr_format]
+        db = {0: 8, 1: 4}[d.dist_format]
+        return P, P * (d.irr_n + 2) ** 2 * tb, P * (d.dist_n + 2) ** 2 * db
+
+    def buffer(self, k, which, stream=None):
+        P, bi, bd = self._sizes(k)
+        nb = {0: bi, 1: bd, 2: P}[which]
+        buf = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        check(load().ddgi_cascade_get_buffer(self.handle, k, which, _ptr(buf), nb, _stream(stream)))
+        return buf
+
+    def states(self, k):
+        return self.buffer(k, 2)
+
+    def irr_atlas(self, k):
+        d = self.descs[k]
+        n = d.irr_n + 2
+        return self.buffer(k, 0).view(torch.float32).view(-1, n, n, 3)
+
+    def dist_atlas(self, k):
+        d = self.descs[k]
+        n = d.dist_n + 2
+        return self.buffer(k, 1).view(torch.float32).view(-1, n, n, 2)
+
+    def window(self, k):
+        o = (C.c_double * 3)()
+        sh = (C.c_int32 * 3)()
+        check(load().ddgi_cascade_get_window(self.handle, k, o, sh))
+        return list(o), list(sh)
+
+    def set_tuning(self, trace_blocks_per_sm, blend_probes_per_cta):
+        check(load().ddgi_cascade_set_tuning(self.handle, int(trace_blocks_per_sm), int(blend_probes_per_cta)))
+
+    def tuning(self):
+        a, b = C.c_int32(), C.c_int32()
+        check(load().ddgi_cascade_get_tuning(self.handle, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def autotune(self, scene: Scene, lights, frame, camera, cache_path=None, precision=_lib.BLEND_FP32,
+                 stream=None):
+        p = self._params(frame, camera, 1.0, 1.0, precision, False)
+        L = lights if isinstance(lights, _lib.Lights) else lights_struct(lights)
+        fc = C.c_int32(0)
+        check(load().ddgi_cascade_autotune(self.handle, scene.handle, C.byref(L), C.byref(p),
+                                           cache_path.encode() if cache_path else None, C.byref(fc),
+                                           _stream(stream)))
+        return bool(fc.value)
+
+    def poll_status(self, stream=None):
+        check(load().ddgi_cascade_poll_status(self.handle, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ddgi_cascade_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class IrradianceField(torch.autograd.Function):
+    """E = field(albedo, emit): the probe update (n_frames from a zero atlas,
+    hysteresis 0) and the query at fixed points, differentiable with respect
+    to per-object albedo [O,3] and per-emitter radiance [E,3].  The backward
+    pass is the library's adjoint (ddgi_diff_backward); rays are re-traced.
+
+    Usage: IrradianceField.apply(albedo, emit, volume, scene, lights, pos, nrm,
+    camera, first_frame, n_frames)."""
+
+    @staticmethod
+    def forward(ctx, albedo, emit, volume, scene, lights, pos, nrm, camera, first_frame=0, n_frames=2):
+        scene.set_materials(albedo, emit)
+        E = volume.diff_forward(scene, lights, pos, nrm, camera, first_frame, n_frames)
+        ctx.save_for_backward(albedo, emit)
+        ctx.args = (volume, scene, lights, pos, nrm, camera, first_frame, n_frames)
+        return E
+
+    @staticmethod
+    def backward(ctx, dE):
+        albedo, emit = ctx.saved_tensors
+        volume, scene, lights, pos, nrm, camera, first_frame, n_frames = ctx.args
+        d_alb, d_em = volume.diff_backward(scene, lights, pos, nrm, camera, dE, albedo.shape[0], emit.shape[0],
+                                           first_frame, n_frames)
+        return d_alb, d_em, None, None, None, None, None, None, None, None

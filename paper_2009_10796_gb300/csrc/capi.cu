@@ -1,5 +1,6 @@
 // C ABI and host runtime: scene registration (BVH build + upload), volume
 // allocation, the per-frame launch sequence, queries, buffer access, timing.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -61,6 +62,41 @@ FrameRot frame_rotation(uint64_t seed, int64_t frame) {
     return r;
 }
 
+std::vector<int32_t> ray_order_morton(int R) {
+    auto spread = [](uint32_t v) {
+        v &= 0x3FFu;
+        v = (v | (v << 16)) & 0x030000FFu;
+        v = (v | (v << 8)) & 0x0300F00Fu;
+        v = (v | (v << 4)) & 0x030C30C3u;
+        v = (v | (v << 2)) & 0x09249249u;
+        return v;
+    };
+    std::vector<std::pair<uint32_t, int32_t>> keys((size_t)R);
+    const double inv_phi = 0.61803398874989484820, two_pi = 6.283185307179586477;
+    for (int i = 0; i < R; ++i) {
+        double a = (double)i * inv_phi;
+        double phi = two_pi * (a - std::floor(a));
+        double z = 1.0 - (2.0 * i + 1.0) / (double)R;
+        double r = std::sqrt(std::fmax(0.0, 1.0 - z * z));
+        double x = std::cos(phi) * r, y = std::sin(phi) * r;
+        double l1 = std::fabs(x) + std::fabs(y) + std::fabs(z);
+        double px = x / l1, py = y / l1;
+        if (z < 0.0) {
+            double qx = (1.0 - std::fabs(py)) * (px >= 0.0 ? 1.0 : -1.0);
+            double qy = (1.0 - std::fabs(px)) * (py >= 0.0 ? 1.0 : -1.0);
+            px = qx;
+            py = qy;
+        }
+        uint32_t ux = (uint32_t)std::fmin(1023.0, (px + 1.0) * 512.0);
+        uint32_t uy = (uint32_t)std::fmin(1023.0, (py + 1.0) * 512.0);
+        keys[i] = {spread(ux) | (spread(uy) << 1), i};
+    }
+    std::sort(keys.begin(), keys.end());
+    std::vector<int32_t> perm((size_t)R);
+    for (int i = 0; i < R; ++i) perm[i] = keys[i].second;
+    return perm;
+}
+
 }  // namespace ddgi
 
 using namespace ddgi;
@@ -73,6 +109,7 @@ struct ddgi_scene_s {
     float4* albedo = nullptr;
     float4* emit = nullptr;
     int64_t n_nodes = 0, n_leaves = 0, n_tris = 0;
+    int32_t n_objects = 0, n_emitters = 0;
 };
 
 struct TimedStage {
@@ -103,6 +140,10 @@ struct ddgi_volume_s {
     unsigned long long* stats = nullptr;   // [8] trace work counters
     int32_t* shadow_list = nullptr;        // [P * R] rays needing a shadow ray
     int32_t* shadow_count = nullptr;
+    int32_t* perm = nullptr;               // [R] ray order within a probe's warps
+    std::vector<void*> snap_irr, snap_dist;   // differentiable forward: atlas after each frame
+    float* g_irr = nullptr;                // adjoint: texel gradients of two frames
+    float* g_prev = nullptr;
     uint8_t* pack_irr = nullptr;           // tensor-core blend: weight tiles in operand layout
     uint8_t* pack_dist = nullptr;
     float* inv_irr_r = nullptr;            // 1 / sum of the rounded weights
@@ -217,6 +258,8 @@ ddgi_status ddgi_scene_create(const float* verts, int64_t n_verts, const int32_t
     s->dev.emit = s->emit;
     s->dev.n_nodes = (int32_t)s->n_nodes;
     s->dev.n_tris = (int32_t)n_tris;
+    s->n_objects = n_objects;
+    s->n_emitters = n_emitters;
     *out = s;
     return DDGI_OK;
 }
@@ -313,7 +356,10 @@ void ddgi_volume_destroy(ddgi_volume v) {
     cudaFree(v->states); cudaFree(v->irr); cudaFree(v->dist); cudaFree(v->lists); cudaFree(v->counts);
     cudaFree(v->status); cudaFree(v->records); cudaFree(v->dirs); cudaFree(v->w_irr);
     cudaFree(v->inv_s_irr); cudaFree(v->w_dist); cudaFree(v->inv_s_dist); cudaFree(v->stats);
-    cudaFree(v->shadow_list); cudaFree(v->shadow_count);
+    cudaFree(v->shadow_list); cudaFree(v->shadow_count); cudaFree(v->perm);
+    for (void* p : v->snap_irr) cudaFree(p);
+    for (void* p : v->snap_dist) cudaFree(p);
+    cudaFree(v->g_irr); cudaFree(v->g_prev);
     cudaFree(v->pack_irr); cudaFree(v->pack_dist); cudaFree(v->inv_irr_r); cudaFree(v->inv_dist_r);
     for (auto& st : v->stages)
         for (auto& pr : st.pending) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
@@ -360,6 +406,11 @@ ddgi_status ddgi_volume_create(const ddgi_volume_desc* desc, ddgi_volume* out) {
     A((void**)&v->stats, sizeof(unsigned long long) * 8);
     A((void**)&v->shadow_list, sizeof(int32_t) * (size_t)v->P * v->R);
     A((void**)&v->shadow_count, sizeof(int32_t) * 4);
+    A((void**)&v->perm, sizeof(int32_t) * v->R);
+    if (e == cudaSuccess) {
+        std::vector<int32_t> perm = ray_order_morton(v->R);
+        e = cudaMemcpy(v->perm, perm.data(), sizeof(int32_t) * v->R, cudaMemcpyHostToDevice);
+    }
     A((void**)&v->pack_irr, tc_pack_irr_bytes(v->R));
     A((void**)&v->pack_dist, tc_pack_dist_bytes(v->R));
     A((void**)&v->inv_irr_r, sizeof(float) * 128);
@@ -422,8 +473,26 @@ struct StageTimer {
     }
 };
 
+static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* lights,
+                               const ddgi_update_params* params, int64_t begin, int64_t end, ddgi_stream stream);
+
 ddgi_status ddgi_update(ddgi_volume v, ddgi_scene s, const ddgi_lights* lights,
                         const ddgi_update_params* params, ddgi_stream stream) {
+    if (!v) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    return update_impl(v, s, lights, params, 0, v->P, stream);
+}
+
+ddgi_status ddgi_update_range(ddgi_volume v, ddgi_scene s, const ddgi_lights* lights,
+                              const ddgi_update_params* params, int64_t probe_begin, int64_t probe_end,
+                              ddgi_stream stream) {
+    if (!v) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (probe_begin < 0 || probe_end > v->P || probe_begin > probe_end)
+        return fail(DDGI_ERR_INVALID_ARG, "probe range out of bounds");
+    return update_impl(v, s, lights, params, probe_begin, probe_end, stream);
+}
+
+static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* lights,
+                               const ddgi_update_params* params, int64_t begin, int64_t end, ddgi_stream stream) {
     if (!v || !s || !lights || !params) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
     if (!(params->irr_hyst_scale >= 0.0f) || !(params->vis_hyst_scale >= 0.0f))
         return fail(DDGI_ERR_INVALID_ARG, "negative hysteresis scale");
@@ -450,18 +519,18 @@ ddgi_status ddgi_update(ddgi_volume v, ddgi_scene s, const ddgi_lights* lights,
     if (d.state_machine) {
         {
             StageTimer tm(v, 1, st);
-            DDGI_CK(launch_build_list(v->states, (int)v->P, 0, v->lists, v->counts + 0, st));
+            DDGI_CK(launch_build_list_range(v->states, (int)begin, (int)end, 0, v->lists, v->counts + 0, st));
         }
         StageTimer tm(v, 0, st);
-        DDGI_CK(launch_classify(s->dev, view, v->dirs, v->R, v->lists, v->counts + 0, sms * 8, st));
+        DDGI_CK(launch_classify(s->dev, view, v->dirs, v->R, v->perm, v->lists, v->counts + 0, sms * 8, st));
     }
     {
         StageTimer tm(v, 1, st);
-        DDGI_CK(launch_build_list(v->states, (int)v->P, 1, v->lists + v->P, v->counts + 1, st));
+        DDGI_CK(launch_build_list_range(v->states, (int)begin, (int)end, 1, v->lists + v->P, v->counts + 1, st));
     }
     {
         StageTimer tm(v, 2, st);
-        DDGI_CK(launch_trace_wavefront(s->dev, view, make_lights(lights), v->dirs, v->R, v->lists + v->P,
+        DDGI_CK(launch_trace_wavefront(s->dev, view, make_lights(lights), v->dirs, v->R, v->perm, v->lists + v->P,
                                        v->counts + 1, v->records, v->shadow_list, v->shadow_count, sms * 8,
                                        st));
     }
@@ -597,6 +666,636 @@ ddgi_status ddgi_poll_status(ddgi_volume v, ddgi_stream stream) {
     DDGI_CK(cudaStreamSynchronize(st));
     if (w & 2u) return fail(DDGI_ERR_TIMEOUT, "a bounded device wait gave up");
     if (w & 1u) return fail(DDGI_ERR_NUMERIC, "non-finite texel value produced");
+    return DDGI_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Cascades (Sec. 7.3) with camera tracking windows (Sec. 7.2): one batched
+// launch sequence over every volume per frame, optionally replayed as a
+// CUDA graph, launch shapes from an autotuner.
+// ===========================================================================
+
+#include <fstream>
+#include <sstream>
+
+namespace {
+
+constexpr int kMaxPlanes = 256;
+
+struct FrameParams {
+    VolView views[kMaxVolumes];
+    FrameRot rot;
+    int4 planes[kMaxPlanes];
+    int32_t n_planes;
+    int32_t pad[3];
+};
+
+struct GraphKey {
+    int32_t precision = -1, trace_mult = 0, blend_probes = 0;
+    float irr_scale = 0.f, vis_scale = 0.f;
+    ddgi_lights lights{};
+    bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
+};
+
+}  // namespace
+
+struct ddgi_cascade_s {
+    int n = 0;
+    ddgi_volume_desc desc[kMaxVolumes]{};
+    int64_t P[kMaxVolumes]{};
+    int64_t total = 0;
+    int R = 0;
+    float t_max[kMaxVolumes]{};
+    size_t irr_bytes[kMaxVolumes]{}, dist_bytes[kMaxVolumes]{};
+    uint8_t* states[kMaxVolumes]{};
+    void* irr[kMaxVolumes]{};
+    void* dist[kMaxVolumes]{};
+    double origin[kMaxVolumes][3]{};
+    int shift[kMaxVolumes][3]{};
+    int32_t* lists = nullptr;
+    int32_t* counts = nullptr;
+    uint32_t* status = nullptr;
+    float4* records = nullptr;
+    int32_t* shadow_list = nullptr;
+    int32_t* shadow_count = nullptr;
+    int32_t* perm = nullptr;
+    float4* dirs = nullptr;
+    float *w_irr = nullptr, *inv_s_irr = nullptr, *w_dist = nullptr, *inv_s_dist = nullptr;
+    uint8_t *pack_irr = nullptr, *pack_dist = nullptr;
+    float *inv_irr_r = nullptr, *inv_dist_r = nullptr;
+    FrameParams* d_params = nullptr;
+    FrameParams* h_params[2]{};
+    cudaEvent_t slot_done[2]{};
+    bool slot_used[2]{};
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph[2]{};
+    GraphKey graph_key[2];
+    int64_t updates = 0;
+    int trace_mult = 8;
+    int blend_probes = 8;
+};
+
+namespace {
+
+void cascade_free(ddgi_cascade_s* c) {
+    for (int k = 0; k < c->n; ++k) { cudaFree(c->states[k]); cudaFree(c->irr[k]); cudaFree(c->dist[k]); }
+    cudaFree(c->lists); cudaFree(c->counts); cudaFree(c->status); cudaFree(c->records);
+    cudaFree(c->shadow_list); cudaFree(c->shadow_count); cudaFree(c->perm); cudaFree(c->dirs); cudaFree(c->w_irr);
+    cudaFree(c->inv_s_irr); cudaFree(c->w_dist); cudaFree(c->inv_s_dist); cudaFree(c->pack_irr);
+    cudaFree(c->pack_dist); cudaFree(c->inv_irr_r); cudaFree(c->inv_dist_r); cudaFree(c->d_params);
+    for (int s = 0; s < 2; ++s) {
+        if (c->h_params[s]) cudaFreeHost(c->h_params[s]);
+        if (c->slot_done[s]) cudaEventDestroy(c->slot_done[s]);
+        if (c->graph[s]) cudaGraphExecDestroy(c->graph[s]);
+    }
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    delete c;
+}
+
+// Host side of the tracking window (Sec. 7.2), the same rule as the oracle:
+// move by whole planes until the camera is within one spacing of the centre
+// on every axis; each move records the physical plane that leapfrogs.
+void cascade_scroll(ddgi_cascade_s* c, int k, const float cam[3], FrameParams* fp) {
+    const ddgi_volume_desc& d = c->desc[k];
+    for (int a = 0; a < 3; ++a) {
+        int moves = 0;
+        for (;;) {
+            double centre = c->origin[k][a] + 0.5 * (double)(d.counts[a] - 1) * (double)d.spacing[a];
+            int dir = 0;
+            if ((double)cam[a] - centre > (double)d.spacing[a]) dir = 1;
+            else if (centre - (double)cam[a] > (double)d.spacing[a]) dir = -1;
+            if (!dir) break;
+            c->origin[k][a] += dir * (double)d.spacing[a];
+            c->shift[k][a] += dir;
+            int fresh = dir > 0 ? d.counts[a] - 1 : 0;
+            int phys = ((fresh + c->shift[k][a]) % d.counts[a] + d.counts[a]) % d.counts[a];
+            if (moves < d.counts[a] && fp->n_planes < kMaxPlanes) fp->planes[fp->n_planes++] = make_int4(k, a, phys, 0);
+            ++moves;
+        }
+    }
+}
+
+VolView cascade_view(const ddgi_cascade_s* c, int k, const float cam[3]) {
+    const ddgi_volume_desc& d = c->desc[k];
+    VolView w{};
+    w.origin = make_float3((float)c->origin[k][0], (float)c->origin[k][1], (float)c->origin[k][2]);
+    w.spacing = make_float3(d.spacing[0], d.spacing[1], d.spacing[2]);
+    w.inv_spacing = make_float3(1.0f / d.spacing[0], 1.0f / d.spacing[1], 1.0f / d.spacing[2]);
+    w.counts = make_int3(d.counts[0], d.counts[1], d.counts[2]);
+    w.shift = make_int3(c->shift[k][0], c->shift[k][1], c->shift[k][2]);
+    w.min_spacing = std::fmin(d.spacing[0], std::fmin(d.spacing[1], d.spacing[2]));
+    w.bias = d.self_shadow_bias;
+    w.gamma = d.gamma;
+    w.inv_gamma = 1.0f / d.gamma;
+    w.half_gamma = 0.5f * d.gamma;
+    w.t_max = c->t_max[k];
+    w.irr_n = d.irr_n;
+    w.dist_n = d.dist_n;
+    w.irr_tile = (d.irr_n + 2) * (d.irr_n + 2);
+    w.dist_tile = (d.dist_n + 2) * (d.dist_n + 2);
+    w.n_probes = (int32_t)c->P[k];
+    w.irr_format = d.irr_format;
+    w.dist_format = d.dist_format;
+    w.states = c->states[k];
+    w.irr = c->irr[k];
+    w.dist = c->dist[k];
+    float lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        if (d.tracking) {   // tracking: fall-off box tightened by one cell and centred on the camera
+            double h = (0.5 * (double)(d.counts[a] - 1) - 1.0) * (double)d.spacing[a];
+            lo[a] = (float)((double)cam[a] - h);
+            hi[a] = (float)((double)cam[a] + h);
+        } else {
+            lo[a] = (float)c->origin[k][a];
+            hi[a] = (float)(c->origin[k][a] + (double)(d.counts[a] - 1) * (double)d.spacing[a]);
+        }
+    }
+    w.blend_lo = make_float3(lo[0], lo[1], lo[2]);
+    w.blend_hi = make_float3(hi[0], hi[1], hi[2]);
+    return w;
+}
+
+ddgi_status cascade_enqueue(ddgi_cascade_s* c, const DevScene& sc, const Lights& L, const BlendParams& bp,
+                            int precision, int slot, cudaStream_t st) {
+    const ddgi_volume_desc& d0 = c->desc[0];
+    const bool tensor = precision != DDGI_BLEND_FP32;
+    int sms = sm_count();
+    VolSet vs{};
+    vs.table = c->d_params->views;
+    vs.n = c->n;
+    DDGI_CK(cudaMemcpyAsync(c->d_params, c->h_params[slot], sizeof(FrameParams), cudaMemcpyHostToDevice, st));
+    DDGI_CK(launch_reset_planes(vs, c->d_params->planes, &c->d_params->n_planes, kMaxPlanes, st));
+    DDGI_CK(launch_frame_setup_dev(&c->d_params->rot, c->R, d0.irr_n, d0.dist_n, d0.dist_cos_power, c->dirs,
+                                   c->w_irr, c->inv_s_irr, c->w_dist, c->inv_s_dist, st));
+    if (tensor)
+        DDGI_CK(launch_pack_weights(c->w_irr, c->w_dist, c->R, d0.irr_n, d0.dist_n, precision == DDGI_BLEND_BF16,
+                                    c->pack_irr, c->pack_dist, c->inv_irr_r, c->inv_dist_r, st));
+    DDGI_CK(cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 2, st));
+    DDGI_CK(launch_build_list_multi(vs, (int)c->total, 0, c->lists, c->counts + 0, st));
+    DDGI_CK(launch_classify_multi(sc, vs, c->dirs, c->R, c->perm, c->lists, c->counts + 0, sms * 8, st));
+    DDGI_CK(launch_build_list_multi(vs, (int)c->total, 1, c->lists + c->total, c->counts + 1, st));
+    DDGI_CK(launch_trace_wavefront_multi(sc, vs, L, c->dirs, c->R, c->perm, c->lists + c->total, c->counts + 1,
+                                         c->records, c->shadow_list, c->shadow_count, sms * c->trace_mult, st));
+    if (tensor)
+        DDGI_CK(launch_blend_tc_set(vs, true, bp, precision == DDGI_BLEND_BF16, c->pack_irr, c->pack_dist,
+                                    c->inv_irr_r, c->inv_dist_r, c->records, c->lists + c->total, c->counts + 1,
+                                    c->status, sms, st));
+    else
+        DDGI_CK(launch_blend_set(vs, true, bp, c->w_irr, c->inv_s_irr, c->w_dist, c->inv_s_dist, c->records,
+                                 c->lists + c->total, c->counts + 1, c->status, sms * 4, c->blend_probes, st));
+    return DDGI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ddgi_status ddgi_cascade_create(const ddgi_volume_desc* descs, int32_t n, ddgi_cascade* out) {
+    if (!out) return fail(DDGI_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!descs || n < 1 || n > kMaxVolumes) return fail(DDGI_ERR_INVALID_ARG, "need 1..8 volume descriptors");
+    for (int k = 0; k < n; ++k) {
+        ddgi_status s = check_desc(&descs[k]);
+        if (s != DDGI_OK) return s;
+        const ddgi_volume_desc &a = descs[0], &b = descs[k];
+        if (b.rays_per_probe != a.rays_per_probe || b.irr_n != a.irr_n || b.dist_n != a.dist_n ||
+            b.irr_format != a.irr_format || b.dist_format != a.dist_format || b.gamma != a.gamma ||
+            b.hysteresis_irr != a.hysteresis_irr || b.hysteresis_vis != a.hysteresis_vis ||
+            b.dist_cos_power != a.dist_cos_power || b.thr_low != a.thr_low || b.thr_high != a.thr_high ||
+            b.thr_step != a.thr_step)
+            return fail(DDGI_ERR_INVALID_ARG,
+                        "cascade volumes must share rays, tile sizes, formats, gamma, hysteresis and thresholds");
+    }
+    ddgi_cascade_s* c = new ddgi_cascade_s();
+    c->n = n;
+    c->R = descs[0].rays_per_probe;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes > 0 ? bytes : 16);
+    };
+    for (int k = 0; k < n; ++k) {
+        const ddgi_volume_desc& d = descs[k];
+        c->desc[k] = d;
+        c->P[k] = (int64_t)d.counts[0] * d.counts[1] * d.counts[2];
+        c->total += c->P[k];
+        double sx = d.spacing[0], sy = d.spacing[1], sz = d.spacing[2];
+        c->t_max[k] = d.t_max >= 0.0f ? d.t_max : (float)(2.0 * std::sqrt(sx * sx + sy * sy + sz * sz));
+        size_t tb = d.irr_format == DDGI_IRR_FP32 ? 12 : (d.irr_format == DDGI_IRR_FP16 ? 8 : 4);
+        size_t db = d.dist_format == DDGI_DIST_FP32 ? 8 : 4;
+        c->irr_bytes[k] = (size_t)c->P[k] * (d.irr_n + 2) * (d.irr_n + 2) * tb;
+        c->dist_bytes[k] = (size_t)c->P[k] * (d.dist_n + 2) * (d.dist_n + 2) * db;
+        for (int a = 0; a < 3; ++a) c->origin[k][a] = d.origin[a];
+        A((void**)&c->states[k], (size_t)c->P[k]);
+        A(&c->irr[k], c->irr_bytes[k]);
+        A(&c->dist[k], c->dist_bytes[k]);
+        if (e == cudaSuccess)
+            e = cudaMemset(c->states[k], d.state_machine ? DDGI_STATE_UNINIT : DDGI_STATE_VIGILANT, (size_t)c->P[k]);
+        if (e == cudaSuccess) e = cudaMemset(c->irr[k], 0, c->irr_bytes[k]);
+        if (e == cudaSuccess) e = cudaMemset(c->dist[k], 0, c->dist_bytes[k]);
+    }
+    if (c->total > (int64_t)kEntryMask) {
+        cascade_free(c);
+        return fail(DDGI_ERR_INVALID_ARG, "cascade has too many probes");
+    }
+    const ddgi_volume_desc& d0 = descs[0];
+    A((void**)&c->lists, sizeof(int32_t) * 2 * (size_t)c->total);
+    A((void**)&c->counts, sizeof(int32_t) * 4);
+    A((void**)&c->status, sizeof(uint32_t));
+    A((void**)&c->records, sizeof(float4) * (size_t)c->total * c->R);
+    A((void**)&c->shadow_list, sizeof(int32_t) * (size_t)c->total * c->R);
+    A((void**)&c->shadow_count, sizeof(int32_t) * 4);
+    A((void**)&c->dirs, sizeof(float4) * c->R);
+    A((void**)&c->perm, sizeof(int32_t) * c->R);
+    if (e == cudaSuccess) {
+        std::vector<int32_t> perm = ray_order_morton(c->R);
+        e = cudaMemcpy(c->perm, perm.data(), sizeof(int32_t) * c->R, cudaMemcpyHostToDevice);
+    }
+    A((void**)&c->w_irr, sizeof(float) * d0.irr_n * d0.irr_n * (size_t)c->R);
+    A((void**)&c->inv_s_irr, sizeof(float) * d0.irr_n * d0.irr_n);
+    A((void**)&c->w_dist, sizeof(float) * d0.dist_n * d0.dist_n * (size_t)c->R);
+    A((void**)&c->inv_s_dist, sizeof(float) * d0.dist_n * d0.dist_n);
+    A((void**)&c->pack_irr, tc_pack_irr_bytes(c->R));
+    A((void**)&c->pack_dist, tc_pack_dist_bytes(c->R));
+    A((void**)&c->inv_irr_r, sizeof(float) * 128);
+    A((void**)&c->inv_dist_r, sizeof(float) * 256);
+    A((void**)&c->d_params, sizeof(FrameParams));
+    for (int s = 0; s < 2 && e == cudaSuccess; ++s) {
+        e = cudaMallocHost((void**)&c->h_params[s], sizeof(FrameParams));
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->slot_done[s], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) e = prepare_blend_kernels(c->R);
+    if (e == cudaSuccess) e = prepare_blend_tc_kernels();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cascade_free(c);
+        return fail(e == cudaErrorMemoryAllocation ? DDGI_ERR_OOM : DDGI_ERR_CUDA,
+                    std::string("cascade allocation: ") + cudaGetErrorString(e));
+    }
+    *out = c;
+    return DDGI_OK;
+}
+
+void ddgi_cascade_destroy(ddgi_cascade c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    cascade_free(c);
+}
+
+ddgi_status ddgi_cascade_update(ddgi_cascade c, ddgi_scene s, const ddgi_lights* lights,
+                                const ddgi_cascade_params* params, ddgi_stream stream) {
+    if (!c || !s || !lights || !params) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (!(params->irr_hyst_scale >= 0.0f) || !(params->vis_hyst_scale >= 0.0f))
+        return fail(DDGI_ERR_INVALID_ARG, "negative hysteresis scale");
+    if (params->blend_precision < DDGI_BLEND_FP32 || params->blend_precision > DDGI_BLEND_BF16)
+        return fail(DDGI_ERR_INVALID_ARG, "unknown blend precision");
+    if (params->blend_precision != DDGI_BLEND_FP32 && !tc_blend_supported(c->desc[0].irr_n, c->desc[0].dist_n))
+        return fail(DDGI_ERR_UNSUPPORTED, "tensor-core blend needs irr_n^2 <= 128 and dist_n^2 <= 256");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(params->camera_pos[a])) return fail(DDGI_ERR_INVALID_ARG, "camera not finite");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int slot = (int)(params->frame & 1);
+    // the pinned slot may still be read by the copy of an earlier frame
+    if (c->slot_used[slot]) DDGI_CK(cudaEventSynchronize(c->slot_done[slot]));
+    FrameParams* fp = c->h_params[slot];
+    fp->n_planes = 0;
+    for (int k = 0; k < c->n; ++k)
+        if (c->desc[k].tracking) cascade_scroll(c, k, params->camera_pos, fp);
+    for (int k = 0; k < c->n; ++k) fp->views[k] = cascade_view(c, k, params->camera_pos);
+    fp->rot = frame_rotation(c->desc[0].seed, params->frame);
+
+    const ddgi_volume_desc& d0 = c->desc[0];
+    BlendParams bp{};
+    bp.hyst_irr = std::fmin(1.0f, std::fmax(0.0f, d0.hysteresis_irr * params->irr_hyst_scale));
+    bp.hyst_vis = std::fmin(1.0f, std::fmax(0.0f, d0.hysteresis_vis * params->vis_hyst_scale));
+    bp.thr_low = d0.thr_low;
+    bp.thr_high = d0.thr_high;
+    bp.thr_step = d0.thr_step;
+    bp.R = c->R;
+    Lights L = make_lights(lights);
+
+    if (params->use_graph) {
+        GraphKey key;
+        key.precision = params->blend_precision;
+        key.trace_mult = c->trace_mult;
+        key.blend_probes = c->blend_probes;
+        key.irr_scale = params->irr_hyst_scale;
+        key.vis_scale = params->vis_hyst_scale;
+        key.lights = *lights;
+        if (!c->graph[slot] || !(c->graph_key[slot] == key)) {
+            if (c->graph[slot]) {
+                cudaGraphExecDestroy(c->graph[slot]);
+                c->graph[slot] = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            DDGI_CK(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeRelaxed));
+            ddgi_status rs = cascade_enqueue(c, s->dev, L, bp, params->blend_precision, slot, c->capture_stream);
+            cudaError_t ce = cudaStreamEndCapture(c->capture_stream, &g);
+            if (rs != DDGI_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rs;
+            }
+            if (ce != cudaSuccess) return fail(DDGI_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&c->graph[slot], g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) return fail(DDGI_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+            c->graph_key[slot] = key;
+        }
+        DDGI_CK(cudaGraphLaunch(c->graph[slot], st));
+    } else {
+        ddgi_status rs = cascade_enqueue(c, s->dev, L, bp, params->blend_precision, slot, st);
+        if (rs != DDGI_OK) return rs;
+    }
+    DDGI_CK(cudaEventRecord(c->slot_done[slot], st));
+    c->slot_used[slot] = true;
+    c->updates++;
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_cascade_query(ddgi_cascade c, const float* pos_dev, const float* nrm_dev, int64_t n,
+                               const float camera_pos[3], float* out_dev, ddgi_stream stream) {
+    if (!c || !camera_pos) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (c->updates == 0) return fail(DDGI_ERR_INVALID_ARG, "no cascade update has run");
+    if (n < 0) return fail(DDGI_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return DDGI_OK;
+    if (!pos_dev || !nrm_dev || !out_dev || !aligned(pos_dev, 4) || !aligned(nrm_dev, 4) || !aligned(out_dev, 4))
+        return fail(DDGI_ERR_INVALID_ARG, "bad buffer");
+    VolSet vs{};
+    vs.table = c->d_params->views;
+    vs.n = c->n;
+    DDGI_CK(launch_query_cascade(vs, pos_dev, nrm_dev, n, make_float3(camera_pos[0], camera_pos[1], camera_pos[2]),
+                                 out_dev, (cudaStream_t)stream));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_cascade_get_buffer(ddgi_cascade c, int32_t vol, int32_t which, void* dst_dev, size_t bytes,
+                                    ddgi_stream stream) {
+    if (!c || !dst_dev) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (vol < 0 || vol >= c->n) return fail(DDGI_ERR_INVALID_ARG, "volume index out of range");
+    void* p;
+    size_t nb;
+    if (which == 0) { p = c->irr[vol]; nb = c->irr_bytes[vol]; }
+    else if (which == 1) { p = c->dist[vol]; nb = c->dist_bytes[vol]; }
+    else if (which == 2) { p = c->states[vol]; nb = (size_t)c->P[vol]; }
+    else return fail(DDGI_ERR_INVALID_ARG, "which must be 0, 1 or 2");
+    if (bytes != nb) return fail(DDGI_ERR_INVALID_ARG, "size mismatch: expected " + std::to_string(nb));
+    DDGI_CK(cudaMemcpyAsync(dst_dev, p, nb, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_cascade_get_window(ddgi_cascade c, int32_t vol, double origin[3], int32_t shift[3]) {
+    if (!c || !origin || !shift) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (vol < 0 || vol >= c->n) return fail(DDGI_ERR_INVALID_ARG, "volume index out of range");
+    for (int a = 0; a < 3; ++a) {
+        origin[a] = c->origin[vol][a];
+        shift[a] = c->shift[vol][a];
+    }
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_cascade_set_tuning(ddgi_cascade c, int32_t trace_blocks_per_sm, int32_t blend_probes_per_cta) {
+    if (!c) return fail(DDGI_ERR_INVALID_ARG, "cascade is NULL");
+    if (trace_blocks_per_sm < 1 || trace_blocks_per_sm > 32)
+        return fail(DDGI_ERR_INVALID_ARG, "trace_blocks_per_sm must be in [1, 32]");
+    if (blend_probes_per_cta != 4 && blend_probes_per_cta != 8 && blend_probes_per_cta != 16)
+        return fail(DDGI_ERR_INVALID_ARG, "blend_probes_per_cta must be 4, 8 or 16");
+    c->trace_mult = trace_blocks_per_sm;
+    c->blend_probes = blend_probes_per_cta;
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_cascade_get_tuning(ddgi_cascade c, int32_t* trace_blocks_per_sm, int32_t* blend_probes_per_cta) {
+    if (!c || !trace_blocks_per_sm || !blend_probes_per_cta) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    *trace_blocks_per_sm = c->trace_mult;
+    *blend_probes_per_cta = c->blend_probes;
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_cascade_poll_status(ddgi_cascade c, ddgi_stream stream) {
+    if (!c) return fail(DDGI_ERR_INVALID_ARG, "cascade is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t w = 0;
+    DDGI_CK(cudaMemcpyAsync(&w, c->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    DDGI_CK(cudaMemsetAsync(c->status, 0, sizeof(uint32_t), st));
+    DDGI_CK(cudaStreamSynchronize(st));
+    if (w & 2u) return fail(DDGI_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (w & 1u) return fail(DDGI_ERR_NUMERIC, "non-finite texel value produced");
+    return DDGI_OK;
+}
+
+// Autotuner: times the cascade update under each candidate launch shape
+// (trace blocks per SM x SIMT blend probes per CTA) and keeps the fastest.
+// Results are cached in a small JSON file keyed by GPU name and workload
+// signature; a cached entry is used without timing.  Timing advances the
+// volumes by the frames it runs (all with params->frame's ray pattern).
+ddgi_status ddgi_cascade_autotune(ddgi_cascade c, ddgi_scene s, const ddgi_lights* lights,
+                                  const ddgi_cascade_params* params, const char* cache_path, int32_t* from_cache,
+                                  ddgi_stream stream) {
+    if (!c || !s || !lights || !params) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    cudaDeviceProp prop{};
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&prop, dev);
+    std::ostringstream key;
+    key << prop.name << "|n=" << c->n << "|P=" << c->total << "|R=" << c->R << "|tris=" << s->n_tris
+        << "|prec=" << params->blend_precision;
+    std::string k = key.str();
+    std::string cache;
+    if (cache_path) {
+        std::ifstream f(cache_path);
+        if (f) { std::stringstream ss; ss << f.rdbuf(); cache = ss.str(); }
+        size_t at = cache.find("\"" + k + "\"");
+        if (at != std::string::npos) {
+            int tm = 0, bp = 0;
+            size_t a = cache.find("\"trace_blocks_per_sm\":", at), b = cache.find("\"blend_probes_per_cta\":", at);
+            if (a != std::string::npos && b != std::string::npos) {
+                tm = std::atoi(cache.c_str() + a + 22);
+                bp = std::atoi(cache.c_str() + b + 23);
+                if (ddgi_cascade_set_tuning(c, tm, bp) == DDGI_OK) {
+                    if (from_cache) *from_cache = 1;
+                    return DDGI_OK;
+                }
+            }
+        }
+    }
+    const int trace_opts[] = {2, 4, 8, 16};
+    const int blend_opts[] = {4, 8, 16};
+    ddgi_cascade_params p = *params;
+    p.use_graph = 0;
+    // one untimed frame: classification and first allocations of work
+    ddgi_status r = ddgi_cascade_update(c, s, lights, &p, stream);
+    if (r != DDGI_OK) return r;
+    cudaEvent_t e0, e1;
+    DDGI_CK(cudaEventCreate(&e0));
+    DDGI_CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_t = c->trace_mult, best_b = c->blend_probes;
+    for (int tmul : trace_opts) {
+        for (int bpp : blend_opts) {
+            if (params->blend_precision != DDGI_BLEND_FP32 && bpp != 8) continue;   // tensor blend: fixed tiles
+            c->trace_mult = tmul;
+            c->blend_probes = bpp;
+            float tot = 0.0f;
+            for (int rep = 0; rep < 2; ++rep) {
+                DDGI_CK(cudaEventRecord(e0, st));
+                r = ddgi_cascade_update(c, s, lights, &p, stream);
+                if (r != DDGI_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return r; }
+                DDGI_CK(cudaEventRecord(e1, st));
+                DDGI_CK(cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                DDGI_CK(cudaEventElapsedTime(&ms, e0, e1));
+                tot += ms;
+            }
+            if (tot < best) { best = tot; best_t = tmul; best_b = bpp; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->trace_mult = best_t;
+    c->blend_probes = best_b;
+    if (from_cache) *from_cache = 0;
+    if (cache_path) {
+        std::ostringstream entry;
+        entry << "\"" << k << "\": {\"trace_blocks_per_sm\": " << best_t << ", \"blend_probes_per_cta\": " << best_b
+              << ", \"ms\": " << best / 2.0f << "}";
+        std::string body;
+        size_t l = cache.find('{'), rb = cache.rfind('}');
+        if (l != std::string::npos && rb != std::string::npos && rb > l) {
+            std::string inner = cache.substr(l + 1, rb - l - 1);
+            bool empty = inner.find_first_not_of(" \n\t\r") == std::string::npos;
+            body = "{" + inner + (empty ? "" : ",\n ") + entry.str() + "}\n";
+        } else {
+            body = "{\n " + entry.str() + "}\n";
+        }
+        std::ofstream f(cache_path);
+        if (f) f << body;
+    }
+    return DDGI_OK;
+}
+
+}  // extern "C"
+
+
+// ===========================================================================
+// Differentiation: forward through n frames of the update from a zero atlas
+// (hysteresis 0, every probe tracing) and the query; reverse pass to the
+// emitters' radiance and the objects' albedo.  Geometry is fixed.
+// ===========================================================================
+
+namespace ddgi {
+cudaError_t launch_query_adjoint(const VolView& v, const float* pos, const float* nrm, int64_t n, float3 cam,
+                                 const float* dE, float* g_irr, cudaStream_t st);
+cudaError_t launch_border_fold(float* g_irr, int P, int n, cudaStream_t st);
+cudaError_t launch_blend_adjoint(const VolView& v_after, const float* w_irr, const float* inv_s, const float* g_irr,
+                                 int P, int R, float4* gL, cudaStream_t st);
+cudaError_t launch_shade_adjoint(const DevScene& s, const VolView& v_before, const Lights& L, const float4* dirs,
+                                 int P, int R, const float4* gL, float* d_emit, float* d_albedo, float* g_prev,
+                                 int with_prev, cudaStream_t st);
+cudaError_t launch_set_materials(float4* albedo, int n_obj, const float* alb, float4* emit, int n_em, const float* em,
+                                 cudaStream_t st);
+}  // namespace ddgi
+
+static ddgi_status diff_check(ddgi_volume v, int32_t n_frames) {
+    const ddgi_volume_desc& d = v->desc;
+    if (n_frames < 1 || n_frames > 8) return fail(DDGI_ERR_INVALID_ARG, "n_frames must be in [1, 8]");
+    if (d.hysteresis_irr != 0.0f || d.hysteresis_vis != 0.0f || d.state_machine != 0 ||
+        d.irr_format != DDGI_IRR_FP32 || d.dist_format != DDGI_DIST_FP32)
+        return fail(DDGI_ERR_UNSUPPORTED,
+                    "differentiation needs hysteresis 0, the state machine off and FP32 atlases");
+    return DDGI_OK;
+}
+
+extern "C" {
+
+ddgi_status ddgi_scene_set_materials(ddgi_scene s, const float* albedo_dev, const float* emit_dev,
+                                     ddgi_stream stream) {
+    if (!s) return fail(DDGI_ERR_INVALID_ARG, "scene is NULL");
+    if (!aligned(albedo_dev, 4) || !aligned(emit_dev, 4)) return fail(DDGI_ERR_INVALID_ARG, "misaligned buffer");
+    DDGI_CK(launch_set_materials(s->albedo, albedo_dev ? s->n_objects : 0, albedo_dev, s->emit,
+                                 emit_dev ? s->n_emitters : 0, emit_dev, (cudaStream_t)stream));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_diff_forward(ddgi_volume v, ddgi_scene s, const ddgi_lights* lights, int64_t first_frame,
+                              int32_t n_frames, const float* pos_dev, const float* nrm_dev, int64_t n,
+                              const float camera_pos[3], float* out_dev, ddgi_stream stream) {
+    if (!v || !s || !lights || !camera_pos) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    ddgi_status r = diff_check(v, n_frames);
+    if (r != DDGI_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    while ((int)v->snap_irr.size() < n_frames + 1) {
+        void *a = nullptr, *b = nullptr;
+        DDGI_CK(cudaMalloc(&a, v->irr_bytes));
+        DDGI_CK(cudaMalloc(&b, v->dist_bytes));
+        v->snap_irr.push_back(a);
+        v->snap_dist.push_back(b);
+    }
+    DDGI_CK(cudaMemsetAsync(v->irr, 0, v->irr_bytes, st));
+    DDGI_CK(cudaMemsetAsync(v->dist, 0, v->dist_bytes, st));
+    DDGI_CK(cudaMemsetAsync(v->states, DDGI_STATE_VIGILANT, (size_t)v->P, st));
+    DDGI_CK(cudaMemsetAsync(v->snap_irr[0], 0, v->irr_bytes, st));
+    DDGI_CK(cudaMemsetAsync(v->snap_dist[0], 0, v->dist_bytes, st));
+    for (int f = 0; f < n_frames; ++f) {
+        ddgi_update_params p{};
+        p.frame = first_frame + f;
+        p.irr_hyst_scale = 1.0f;
+        p.vis_hyst_scale = 1.0f;
+        p.blend_precision = DDGI_BLEND_FP32;
+        r = ddgi_update(v, s, lights, &p, stream);
+        if (r != DDGI_OK) return r;
+        DDGI_CK(cudaMemcpyAsync(v->snap_irr[f + 1], v->irr, v->irr_bytes, cudaMemcpyDeviceToDevice, st));
+        DDGI_CK(cudaMemcpyAsync(v->snap_dist[f + 1], v->dist, v->dist_bytes, cudaMemcpyDeviceToDevice, st));
+    }
+    return ddgi_query(v, pos_dev, nrm_dev, n, camera_pos, out_dev, stream);
+}
+
+ddgi_status ddgi_diff_backward(ddgi_volume v, ddgi_scene s, const ddgi_lights* lights, int64_t first_frame,
+                               int32_t n_frames, const float* pos_dev, const float* nrm_dev, int64_t n,
+                               const float camera_pos[3], const float* dE_dev, float* d_albedo_dev,
+                               float* d_emit_dev, ddgi_stream stream) {
+    if (!v || !s || !lights || !camera_pos || !d_albedo_dev) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (s->n_emitters > 0 && !d_emit_dev) return fail(DDGI_ERR_INVALID_ARG, "NULL emitter gradient");
+    if (n > 0 && (!pos_dev || !nrm_dev || !dE_dev)) return fail(DDGI_ERR_INVALID_ARG, "NULL buffer");
+    ddgi_status r = diff_check(v, n_frames);
+    if (r != DDGI_OK) return r;
+    if ((int)v->snap_irr.size() < n_frames + 1)
+        return fail(DDGI_ERR_INVALID_ARG, "ddgi_diff_forward with these frames has not run");
+    cudaStream_t st = (cudaStream_t)stream;
+    const ddgi_volume_desc& d = v->desc;
+    size_t gbytes = (size_t)v->P * (d.irr_n + 2) * (d.irr_n + 2) * 3 * sizeof(float);
+    if (!v->g_irr) DDGI_CK(cudaMalloc((void**)&v->g_irr, gbytes));
+    if (!v->g_prev) DDGI_CK(cudaMalloc((void**)&v->g_prev, gbytes));
+    DDGI_CK(cudaMemsetAsync(v->g_irr, 0, gbytes, st));
+    DDGI_CK(cudaMemsetAsync(d_albedo_dev, 0, sizeof(float) * 3 * (size_t)s->n_objects, st));
+    if (s->n_emitters > 0) DDGI_CK(cudaMemsetAsync(d_emit_dev, 0, sizeof(float) * 3 * (size_t)s->n_emitters, st));
+    auto snap_view = [&](int k) {
+        VolView w = make_view(v);
+        w.irr = v->snap_irr[k];
+        w.dist = v->snap_dist[k];
+        return w;
+    };
+    Lights L = make_lights(lights);
+    float3 cam = make_float3(camera_pos[0], camera_pos[1], camera_pos[2]);
+    DDGI_CK(launch_query_adjoint(snap_view(n_frames), pos_dev, nrm_dev, n, cam, dE_dev, v->g_irr, st));
+    float* g = v->g_irr;
+    float* gp = v->g_prev;
+    for (int f = n_frames - 1; f >= 0; --f) {
+        DDGI_CK(launch_border_fold(g, (int)v->P, d.irr_n, st));
+        FrameRot rot = frame_rotation(d.seed, first_frame + f);
+        DDGI_CK(launch_frame_setup(rot, v->R, d.irr_n, d.dist_n, d.dist_cos_power, v->dirs, v->w_irr, v->inv_s_irr,
+                                   v->w_dist, v->inv_s_dist, st));
+        DDGI_CK(launch_blend_adjoint(snap_view(f + 1), v->w_irr, v->inv_s_irr, g, (int)v->P, v->R, v->records, st));
+        DDGI_CK(cudaMemsetAsync(gp, 0, gbytes, st));
+        DDGI_CK(launch_shade_adjoint(s->dev, snap_view(f), L, v->dirs, (int)v->P, v->R, v->records, d_emit_dev,
+                                     d_albedo_dev, gp, f > 0, st));
+        float* t = g;
+        g = gp;
+        gp = t;
+    }
     return DDGI_OK;
 }
 

@@ -57,7 +57,36 @@ struct VolView {
     uint8_t* states;
     void*    irr;
     void*    dist;
+    float3   blend_lo;      // cascade fall-off box (Sec. 7.3): outermost planes, or
+    float3   blend_hi;      // camera-centred for a tracking window
 };
+
+// Volumes a kernel works on: one view by value (a single volume) or a device
+// table of up to kMaxVolumes views (a cascade).  Probe lists hold entries
+// (volume << 24) | probe, so a single volume's entries are its probe indices.
+constexpr int kMaxVolumes = 8;
+constexpr int kEntryShift = 24;
+constexpr int32_t kEntryMask = (1 << kEntryShift) - 1;
+
+struct VolSet {
+    VolView single;           // the volume when table == nullptr
+    const VolView* table;     // device array [n] for cascades
+    int32_t n;
+};
+
+template <bool MULTI>
+__device__ __forceinline__ const VolView& vol_of(const VolSet& s, int k) {
+    if (MULTI) return s.table[k];
+    return s.single;
+}
+
+inline VolSet single_set(const VolView& v) {
+    VolSet s{};
+    s.single = v;
+    s.table = nullptr;
+    s.n = 1;
+    return s;
+}
 
 struct BlendParams {
     float hyst_irr, hyst_vis;      // already scaled and clamped
@@ -88,16 +117,37 @@ FrameRot frame_rotation(uint64_t seed, int64_t frame);
 cudaError_t launch_frame_setup(const FrameRot& rot, int R, int irr_n, int dist_n, float cos_power,
                                float4* dirs, float* w_irr, float* inv_s_irr, float* w_dist,
                                float* inv_s_dist, cudaStream_t st);
+cudaError_t launch_frame_setup_dev(const FrameRot* rot_dev, int R, int irr_n, int dist_n, float cos_power,
+                                   float4* dirs, float* w_irr, float* inv_s_irr, float* w_dist,
+                                   float* inv_s_dist, cudaStream_t st);
 cudaError_t launch_build_list(const uint8_t* states, int P, int which, int32_t* list,
                               int32_t* count, cudaStream_t st);
-cudaError_t launch_classify(const DevScene& s, const VolView& v, const float4* dirs, int R,
+// probes [begin, end) only (a shard of the grid)
+cudaError_t launch_build_list_range(const uint8_t* states, int begin, int end, int which, int32_t* list,
+                                    int32_t* count, cudaStream_t st);
+cudaError_t launch_build_list_multi(const VolSet& vs, int total, int which, int32_t* list, int32_t* count,
+                                    cudaStream_t st);
+// perm (may be NULL = identity): ray order of a probe's warps, a permutation
+// of [0, R) that groups nearby directions (ray_order_morton)
+cudaError_t launch_classify(const DevScene& s, const VolView& v, const float4* dirs, int R, const int32_t* perm,
                             const int32_t* list, const int32_t* count, int grid, cudaStream_t st);
+cudaError_t launch_classify_multi(const DevScene& s, const VolSet& vs, const float4* dirs, int R,
+                                  const int32_t* perm, const int32_t* list, const int32_t* count, int grid,
+                                  cudaStream_t st);
 cudaError_t launch_trace_shade(const DevScene& s, const VolView& v, const Lights& L,
                                const float4* dirs, int R, const int32_t* active,
                                const int32_t* count, float4* records, int grid, cudaStream_t st);
 cudaError_t launch_trace_wavefront(const DevScene& s, const VolView& v, const Lights& L, const float4* dirs,
-                                   int R, const int32_t* active, const int32_t* count, float4* records,
-                                   int32_t* shadow_list, int32_t* shadow_count, int grid, cudaStream_t st);
+                                   int R, const int32_t* perm, const int32_t* active, const int32_t* count,
+                                   float4* records, int32_t* shadow_list, int32_t* shadow_count, int grid,
+                                   cudaStream_t st);
+cudaError_t launch_trace_wavefront_multi(const DevScene& s, const VolSet& vs, const Lights& L,
+                                         const float4* dirs, int R, const int32_t* perm, const int32_t* active,
+                                         const int32_t* count, float4* records, int32_t* shadow_list,
+                                         int32_t* shadow_count, int grid, cudaStream_t st);
+// Morton order of the octahedral positions of the unrotated spherical-
+// Fibonacci directions (host; a rotation keeps neighbouring directions together)
+std::vector<int32_t> ray_order_morton(int R);
 cudaError_t launch_trace_shade_count(const DevScene& s, const VolView& v, const Lights& L,
                                      const float4* dirs, int R, const int32_t* active,
                                      const int32_t* count, unsigned long long* stats, int grid,
@@ -106,6 +156,12 @@ cudaError_t launch_blend(const VolView& v, const BlendParams& bp, const float* w
                          const float* inv_s_irr, const float* w_dist, const float* inv_s_dist,
                          const float4* records, const int32_t* active, const int32_t* count,
                          uint32_t* status, int grid, cudaStream_t st);
+// blend over a volume set; probes_per_cta in {4, 8, 16} (autotuned)
+cudaError_t launch_blend_set(const VolSet& vs, bool multi, const BlendParams& bp, const float* w_irr,
+                             const float* inv_s_irr, const float* w_dist, const float* inv_s_dist,
+                             const float4* records, const int32_t* active, const int32_t* count,
+                             uint32_t* status, int grid, int probes_per_cta, cudaStream_t st);
+cudaError_t prepare_blend_kernels(int R);
 // tensor-core blend (k_blend_tc.cu)
 int tc_blend_chunks(int R);
 size_t tc_pack_irr_bytes(int R);
@@ -117,8 +173,19 @@ cudaError_t launch_blend_tc(const VolView& v, const BlendParams& bp, int bf16, c
                             const uint8_t* a_dist, const float* inv_irr, const float* inv_dist,
                             const float4* records, const int32_t* active, const int32_t* count, uint32_t* status,
                             int grid, cudaStream_t st);
+cudaError_t launch_blend_tc_set(const VolSet& vs, bool multi, const BlendParams& bp, int bf16,
+                                const uint8_t* a_irr, const uint8_t* a_dist, const float* inv_irr,
+                                const float* inv_dist, const float4* records, const int32_t* active,
+                                const int32_t* count, uint32_t* status, int grid, cudaStream_t st);
+cudaError_t prepare_blend_tc_kernels();
 cudaError_t launch_query(const VolView& v, const float* pos, const float* nrm, int64_t n,
                          float3 camera, float* out, cudaStream_t st);
+cudaError_t launch_query_cascade(const VolSet& vs, const float* pos, const float* nrm, int64_t n, float3 camera,
+                                 float* out, cudaStream_t st);
+// Resets probe planes that a tracking window leapfrogged: planes[i] =
+// (volume, axis, physical plane index); count on the device.
+cudaError_t launch_reset_planes(const VolSet& vs, const int4* planes, const int32_t* count, int max_planes,
+                                cudaStream_t st);
 cudaError_t launch_trace_rays(const DevScene& s, const float* orig, const float* dir, int64_t n,
                               float* t, int32_t* tri, int32_t* backface, cudaStream_t st);
 cudaError_t launch_gbuffer(const DevScene& s, float3 pos, float3 fwd, float3 right, float3 up,

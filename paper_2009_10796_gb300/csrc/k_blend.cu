@@ -52,11 +52,15 @@ __device__ void texel_dir(int t, int n, double v[3]) {
 
 // grid: irr_n^2 + dist_n^2 + 1 blocks; block b < irr_n^2 handles irradiance
 // texel b, the next dist_n^2 blocks distance texels, the last one the rays.
-__global__ void __launch_bounds__(256) k_frame_setup(FrameRot rot, int R, int irr_n, int dist_n,
-                                                     double cos_power, float4* dirs, float* w_irr,
+template <bool ROT_DEV>
+__global__ void __launch_bounds__(256) k_frame_setup(FrameRot rot_arg, const FrameRot* rot_dev, int R, int irr_n,
+                                                     int dist_n, double cos_power, float4* dirs, float* w_irr,
                                                      float* inv_s_irr, float* w_dist,
                                                      float* inv_s_dist) {
     __shared__ double red[256];
+    // ROT_DEV: the rotation is read from device memory (per-frame parameters
+    // written before a captured graph replays)
+    const FrameRot rot = ROT_DEV ? *rot_dev : rot_arg;
     int b = blockIdx.x;
     int ti = irr_n * irr_n, td = dist_n * dist_n;
     if (b == ti + td) {
@@ -94,9 +98,8 @@ __global__ void __launch_bounds__(256) k_frame_setup(FrameRot rot, int R, int ir
     }
 }
 
-constexpr int kProbes = 8;
-
-__global__ void __launch_bounds__(256) k_blend_simt(VolView v, BlendParams bp,
+template <bool MULTI, int kProbes>
+__global__ void __launch_bounds__(256) k_blend_simt(VolSet vs, BlendParams bp,
                                                     const float* __restrict__ w_irr,
                                                     const float* __restrict__ inv_s_irr,
                                                     const float* __restrict__ w_dist,
@@ -111,14 +114,16 @@ __global__ void __launch_bounds__(256) k_blend_simt(VolView v, BlendParams bp,
     const int R = bp.R;
     const int stride = R + 1;
     const int n_act = *count;
-    const int ni = v.irr_n, nd = v.dist_n;
+    const VolView& v0 = vol_of<MULTI>(vs, 0);   // cascades share R and tile sizes
+    const int ni = v0.irr_n, nd = v0.dist_n;
     const int ti = ni * ni, td = nd * nd;
     for (int g0 = blockIdx.x * kProbes; g0 < n_act; g0 += gridDim.x * kProbes) {
         const int np = min(kProbes, n_act - g0);
         if (threadIdx.x < np) {
-            int p = active[g0 + threadIdx.x];
-            s_probe[threadIdx.x] = p;
-            s_newly[threadIdx.x] = v.states[p] == DDGI_STATE_NEWLY_VIGILANT;
+            int e = active[g0 + threadIdx.x];
+            s_probe[threadIdx.x] = e;
+            s_newly[threadIdx.x] =
+                vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask] == DDGI_STATE_NEWLY_VIGILANT;
         }
         for (int k = threadIdx.x; k < np * R; k += blockDim.x) {
             int pp = k / R, i = k - pp * R;
@@ -138,8 +143,9 @@ __global__ void __launch_bounds__(256) k_blend_simt(VolView v, BlendParams bp,
                 ag = fmaf(w, L.y, ag);
                 ab = fmaf(w, L.z, ab);
             }
-            blend_irr_texel(v, bp, s_probe[pp], t, ar, ag, ab, __ldg(inv_s_irr + t), s_newly[pp] != 0,
-                            status);
+            const int e = s_probe[pp];
+            blend_irr_texel(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, t, ar, ag, ab,
+                            __ldg(inv_s_irr + t), s_newly[pp] != 0, status);
         }
         // distance texels: power-cosine weighted mean distance and mean squared distance
         for (int q = threadIdx.x; q < td * np; q += blockDim.x) {
@@ -154,10 +160,15 @@ __global__ void __launch_bounds__(256) k_blend_simt(VolView v, BlendParams bp,
                 m1 += wd;
                 m2 = fmaf(wd, d, m2);
             }
-            blend_dist_texel(v, bp, s_probe[pp], t, m1, m2, __ldg(inv_s_dist + t), s_newly[pp] != 0, status);
+            const int e = s_probe[pp];
+            blend_dist_texel(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, t, m1, m2,
+                             __ldg(inv_s_dist + t), s_newly[pp] != 0, status);
         }
         __syncthreads();
-        if (threadIdx.x < np && s_newly[threadIdx.x]) v.states[s_probe[threadIdx.x]] = DDGI_STATE_VIGILANT;
+        if (threadIdx.x < np && s_newly[threadIdx.x]) {
+            const int e = s_probe[threadIdx.x];
+            vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask] = DDGI_STATE_VIGILANT;
+        }
         __syncthreads();
     }
 }
@@ -166,8 +177,35 @@ cudaError_t launch_frame_setup(const FrameRot& rot, int R, int irr_n, int dist_n
                                float4* dirs, float* w_irr, float* inv_s_irr, float* w_dist,
                                float* inv_s_dist, cudaStream_t st) {
     int blocks = irr_n * irr_n + dist_n * dist_n + 1;
-    k_frame_setup<<<blocks, 256, 0, st>>>(rot, R, irr_n, dist_n, (double)cos_power, dirs, w_irr,
-                                          inv_s_irr, w_dist, inv_s_dist);
+    k_frame_setup<false><<<blocks, 256, 0, st>>>(rot, nullptr, R, irr_n, dist_n, (double)cos_power, dirs, w_irr,
+                                                 inv_s_irr, w_dist, inv_s_dist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_frame_setup_dev(const FrameRot* rot_dev, int R, int irr_n, int dist_n, float cos_power,
+                                   float4* dirs, float* w_irr, float* inv_s_irr, float* w_dist,
+                                   float* inv_s_dist, cudaStream_t st) {
+    int blocks = irr_n * irr_n + dist_n * dist_n + 1;
+    k_frame_setup<true><<<blocks, 256, 0, st>>>(FrameRot{}, rot_dev, R, irr_n, dist_n, (double)cos_power, dirs,
+                                                w_irr, inv_s_irr, w_dist, inv_s_dist);
+    return cudaGetLastError();
+}
+
+template <bool MULTI, int PGS>
+static cudaError_t blend_simt(const VolSet& vs, const BlendParams& bp, const float* w_irr, const float* inv_s_irr,
+                              const float* w_dist, const float* inv_s_dist, const float4* records,
+                              const int32_t* active, const int32_t* count, uint32_t* status, int grid,
+                              cudaStream_t st) {
+    size_t smem = (size_t)PGS * (bp.R + 1) * sizeof(float4);
+    static int configured_smem = 0;
+    if ((int)smem > configured_smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_blend_simt<MULTI, PGS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured_smem = (int)smem;
+    }
+    k_blend_simt<MULTI, PGS><<<grid, 256, smem, st>>>(vs, bp, w_irr, inv_s_irr, w_dist, inv_s_dist, records,
+                                                      active, count, status);
     return cudaGetLastError();
 }
 
@@ -175,17 +213,46 @@ cudaError_t launch_blend(const VolView& v, const BlendParams& bp, const float* w
                          const float* w_dist, const float* inv_s_dist, const float4* records,
                          const int32_t* active, const int32_t* count, uint32_t* status, int grid,
                          cudaStream_t st) {
-    size_t smem = (size_t)kProbes * (bp.R + 1) * sizeof(float4);
-    static int configured_smem = 0;
-    if ((int)smem > configured_smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_blend_simt, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        configured_smem = (int)smem;
-    }
-    k_blend_simt<<<grid, 256, smem, st>>>(v, bp, w_irr, inv_s_irr, w_dist, inv_s_dist, records, active,
-                                         count, status);
-    return cudaGetLastError();
+    return blend_simt<false, 8>(single_set(v), bp, w_irr, inv_s_irr, w_dist, inv_s_dist, records, active, count,
+                                status, grid, st);
+}
+
+cudaError_t launch_blend_set(const VolSet& vs, bool multi, const BlendParams& bp, const float* w_irr,
+                             const float* inv_s_irr, const float* w_dist, const float* inv_s_dist,
+                             const float4* records, const int32_t* active, const int32_t* count,
+                             uint32_t* status, int grid, int probes_per_cta, cudaStream_t st) {
+#define DDGI_BLEND_CASE(M, P)                                                                                 \
+    if (multi == M && probes_per_cta == P)                                                                   \
+        return blend_simt<M, P>(vs, bp, w_irr, inv_s_irr, w_dist, inv_s_dist, records, active, count, status, \
+                                grid, st);
+    DDGI_BLEND_CASE(false, 4)
+    DDGI_BLEND_CASE(false, 8)
+    DDGI_BLEND_CASE(false, 16)
+    DDGI_BLEND_CASE(true, 4)
+    DDGI_BLEND_CASE(true, 8)
+    DDGI_BLEND_CASE(true, 16)
+#undef DDGI_BLEND_CASE
+    return cudaErrorInvalidValue;
+}
+
+// Sets the shared-memory opt-in of every SIMT blend instantiation for R rays
+// (outside any stream capture).
+cudaError_t prepare_blend_kernels(int R) {
+    cudaError_t e = cudaSuccess;
+#define DDGI_PREP(M, P)                                                                                   \
+    if (e == cudaSuccess)                                                                                \
+        e = cudaFuncSetAttribute(k_blend_simt<M, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                                 (int)((size_t)P * (R + 1) * sizeof(float4)) > 48 * 1024                    \
+                                     ? (int)((size_t)P * (R + 1) * sizeof(float4))                          \
+                                     : 48 * 1024);
+    DDGI_PREP(false, 4)
+    DDGI_PREP(false, 8)
+    DDGI_PREP(false, 16)
+    DDGI_PREP(true, 4)
+    DDGI_PREP(true, 8)
+    DDGI_PREP(true, 16)
+#undef DDGI_PREP
+    return e;
 }
 
 }  // namespace ddgi

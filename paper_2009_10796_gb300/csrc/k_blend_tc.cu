@@ -199,8 +199,8 @@ __global__ void __launch_bounds__(128) k_pack_weights(const float* __restrict__ 
     }
 }
 
-template <bool BF16>
-__global__ void __launch_bounds__(NT, 1) k_blend_tc(VolView v, BlendParams bp, const uint8_t* __restrict__ a_irr_pack,
+template <bool BF16, bool MULTI>
+__global__ void __launch_bounds__(NT, 1) k_blend_tc(VolSet vs, BlendParams bp, const uint8_t* __restrict__ a_irr_pack,
                                                     const uint8_t* __restrict__ a_dist_pack, int nchunks,
                                                     const float* __restrict__ inv_irr,
                                                     const float* __restrict__ inv_dist,
@@ -216,7 +216,8 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(VolView v, BlendParams bp, c
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int R = bp.R;
-    const int ti = v.irr_n * v.irr_n, td = v.dist_n * v.dist_n;
+    const VolView& v0 = vol_of<MULTI>(vs, 0);   // cascades share R and tile sizes
+    const int ti = v0.irr_n * v0.irr_n, td = v0.dist_n * v0.dist_n;
     constexpr uint32_t es_irr = BF16 ? 2u : 4u;
     constexpr uint32_t sbo_irr = KC * es_irr * 8;
     constexpr uint32_t sbo4 = KC * 4 * 8;
@@ -256,9 +257,10 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(VolView v, BlendParams bp, c
     for (int g0 = blockIdx.x * PG; g0 < n_act; g0 += gridDim.x * PG) {
         const int np = min(PG, n_act - g0);
         if (tid < PG) {
-            int p = tid < np ? active[g0 + tid] : 0;
-            s_probe[tid] = p;
-            s_newly[tid] = tid < np && v.states[p] == DDGI_STATE_NEWLY_VIGILANT;
+            int e = tid < np ? active[g0 + tid] : 0;
+            s_probe[tid] = e;
+            s_newly[tid] = tid < np &&
+                           vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask] == DDGI_STATE_NEWLY_VIGILANT;
         }
         for (int c = 0; c < nchunks; ++c) {
             const int s = c & 1;
@@ -396,18 +398,24 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(VolView v, BlendParams bp, c
         for (int q = tid; q < ti * np; q += NT) {
             int t = q / np, pp = q - t * np;
             const float* a = Dirr + t * IRR_N + 3 * pp;
-            blend_irr_texel(v, bp, s_probe[pp], t, a[0], a[1], a[2], __ldg(inv_irr + t), s_newly[pp] != 0, status);
+            const int e = s_probe[pp];
+            blend_irr_texel(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, t, a[0], a[1], a[2],
+                            __ldg(inv_irr + t), s_newly[pp] != 0, status);
         }
         for (int q = tid; q < td * np; q += NT) {
             int t = q / np, pp = q - t * np;
             const float* a = Ddist + t * DIST_N + 4 * pp;
-            blend_dist_texel(v, bp, s_probe[pp], t, a[0] + a[1], a[2] + a[3], __ldg(inv_dist + t),
-                             s_newly[pp] != 0, status);
+            const int e = s_probe[pp];
+            blend_dist_texel(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, t, a[0] + a[1], a[2] + a[3],
+                             __ldg(inv_dist + t), s_newly[pp] != 0, status);
         }
         // the next group's bulk copies (async proxy) overwrite what these reads used
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (tid < np && s_newly[tid]) v.states[s_probe[tid]] = DDGI_STATE_VIGILANT;
+        if (tid < np && s_newly[tid]) {
+            const int e = s_probe[tid];
+            vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask] = DDGI_STATE_VIGILANT;
+        }
         __syncthreads();
     }
     if (abort) {
@@ -439,25 +447,55 @@ cudaError_t launch_pack_weights(const float* w_irr, const float* w_dist, int R, 
     return cudaGetLastError();
 }
 
+template <bool BF16, bool MULTI>
+static cudaError_t blend_tc(const VolSet& vs, const BlendParams& bp, const uint8_t* a_irr, const uint8_t* a_dist,
+                            const float* inv_irr, const float* inv_dist, const float4* records,
+                            const int32_t* active, const int32_t* count, uint32_t* status, int grid,
+                            cudaStream_t st) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_blend_tc<BF16, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_blend_tc<BF16, MULTI><<<grid, NT, SMEM_BYTES, st>>>(vs, bp, a_irr, a_dist, tc_blend_chunks(bp.R), inv_irr,
+                                                          inv_dist, records, active, count, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blend_tc_set(const VolSet& vs, bool multi, const BlendParams& bp, int bf16,
+                                const uint8_t* a_irr, const uint8_t* a_dist, const float* inv_irr,
+                                const float* inv_dist, const float4* records, const int32_t* active,
+                                const int32_t* count, uint32_t* status, int grid, cudaStream_t st) {
+    if (bf16 && multi)
+        return blend_tc<true, true>(vs, bp, a_irr, a_dist, inv_irr, inv_dist, records, active, count, status, grid, st);
+    if (bf16)
+        return blend_tc<true, false>(vs, bp, a_irr, a_dist, inv_irr, inv_dist, records, active, count, status, grid, st);
+    if (multi)
+        return blend_tc<false, true>(vs, bp, a_irr, a_dist, inv_irr, inv_dist, records, active, count, status, grid, st);
+    return blend_tc<false, false>(vs, bp, a_irr, a_dist, inv_irr, inv_dist, records, active, count, status, grid, st);
+}
+
 cudaError_t launch_blend_tc(const VolView& v, const BlendParams& bp, int bf16, const uint8_t* a_irr,
                             const uint8_t* a_dist, const float* inv_irr, const float* inv_dist,
                             const float4* records, const int32_t* active, const int32_t* count, uint32_t* status,
                             int grid, cudaStream_t st) {
-    static bool configured[2] = {false, false};
-    cudaError_t e;
-    if (!configured[bf16 ? 1 : 0]) {
-        e = bf16 ? cudaFuncSetAttribute(k_blend_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES)
-                 : cudaFuncSetAttribute(k_blend_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        configured[bf16 ? 1 : 0] = true;
-    }
-    if (bf16)
-        k_blend_tc<true><<<grid, NT, SMEM_BYTES, st>>>(v, bp, a_irr, a_dist, tc_blend_chunks(bp.R), inv_irr, inv_dist,
-                                                       records, active, count, status);
-    else
-        k_blend_tc<false><<<grid, NT, SMEM_BYTES, st>>>(v, bp, a_irr, a_dist, tc_blend_chunks(bp.R), inv_irr, inv_dist,
-                                                        records, active, count, status);
-    return cudaGetLastError();
+    return launch_blend_tc_set(single_set(v), false, bp, bf16, a_irr, a_dist, inv_irr, inv_dist, records, active,
+                               count, status, grid, st);
+}
+
+// Shared-memory opt-in of every tensor-core blend instantiation (outside any stream capture).
+cudaError_t prepare_blend_tc_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(k_blend_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM_BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_blend_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_blend_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_blend_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    return e;
 }
 
 }  // namespace ddgi

@@ -31,13 +31,13 @@ __global__ void __launch_bounds__(256) k_query(VolView v, const float* __restric
 // NEWLY_VIGILANT or VIGILANT) into list[], count[0] += matches.  Warp-
 // aggregated atomics: one atomic per warp.  List order is not deterministic;
 // consumers carry the probe index with each entry.
-__global__ void k_build_list(const uint8_t* __restrict__ states, int P, int which, int32_t* list,
+__global__ void k_build_list(const uint8_t* __restrict__ states, int begin, int end, int which, int32_t* list,
                              int32_t* count) {
     const int lane = threadIdx.x & 31;
-    for (int base = blockIdx.x * blockDim.x; base < P; base += gridDim.x * blockDim.x) {
+    for (int base = begin + blockIdx.x * blockDim.x; base < end; base += gridDim.x * blockDim.x) {
         int p = base + threadIdx.x;
         bool pred = false;
-        if (p < P) {
+        if (p < end) {
             uint8_t s = states[p];
             pred = which == 0 ? s == DDGI_STATE_UNINIT : state_active(s);
         }
@@ -51,6 +51,106 @@ __global__ void k_build_list(const uint8_t* __restrict__ states, int P, int whic
     }
 }
 
+// Cascade query (Sec. 7.3): one thread per point, volumes densest first.
+__global__ void __launch_bounds__(256) k_query_cascade(VolSet vs, const float* __restrict__ pos,
+                                                       const float* __restrict__ nrm, int64_t n, float3 cam,
+                                                       float* __restrict__ out) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        float3 x = f3(__ldg(pos + 3 * q), __ldg(pos + 3 * q + 1), __ldg(pos + 3 * q + 2));
+        float3 nn = f3(__ldg(nrm + 3 * q), __ldg(nrm + 3 * q + 1), __ldg(nrm + 3 * q + 2));
+        float3 E = f3(0.0f, 0.0f, 0.0f);
+        if (nn.x != 0.0f || nn.y != 0.0f || nn.z != 0.0f) {
+            float3 wo = cam - x;
+            float l = length(wo);
+            wo = l < 1e-6f ? nn : (1.0f / l) * wo;
+            float3 M = cascade_M(vs.table, vs.n, x, nn, wo);
+            const float pi = 3.14159265358979323846f;
+            E = f3(pi * M.x, pi * M.y, pi * M.z);
+        }
+        out[3 * q] = E.x;
+        out[3 * q + 1] = E.y;
+        out[3 * q + 2] = E.z;
+    }
+}
+
+// List build over every volume of a set: global index g runs over the
+// volumes' probes in order; entries are (volume << 24) | probe.
+__global__ void k_build_list_multi(VolSet vs, int total, int which, int32_t* list, int32_t* count) {
+    const int lane = threadIdx.x & 31;
+    for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
+        int g = base + threadIdx.x;
+        bool pred = false;
+        int entry = 0;
+        if (g < total) {
+            int k = 0, off = 0;
+            while (k + 1 < vs.n && g >= off + vs.table[k].n_probes) {
+                off += vs.table[k].n_probes;
+                ++k;
+            }
+            int p = g - off;
+            uint8_t s = vs.table[k].states[p];
+            pred = which == 0 ? s == DDGI_STATE_UNINIT : state_active(s);
+            entry = (k << kEntryShift) | p;
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, pred);
+        if (mask == 0) continue;
+        int leader = __ffs(mask) - 1;
+        int o = 0;
+        if (lane == leader) o = atomicAdd(count, __popc(mask));
+        o = __shfl_sync(0xffffffffu, o, leader);
+        if (pred) list[o + __popc(mask & ((1u << lane) - 1u))] = entry;
+    }
+}
+
+// Tracking-window reset (Sec. 7.2): every probe of a leapfrogged plane gets
+// zero texels and state UNINIT.  One block per plane.
+__global__ void k_reset_planes(VolSet vs, const int4* __restrict__ planes, const int32_t* __restrict__ count) {
+    if ((int)blockIdx.x >= *count) return;
+    int4 pl = planes[blockIdx.x];          // (volume, axis, physical plane, 0)
+    const VolView& v = vs.table[pl.x];
+    int cnt[3] = {v.counts.x, v.counts.y, v.counts.z};
+    int a = pl.y, b = (a + 1) % 3, c = (a + 2) % 3;
+    int n_probes = cnt[b] * cnt[c];
+    int ti = v.irr_tile, td = v.dist_tile;
+    for (int q = threadIdx.x; q < n_probes; q += blockDim.x) {
+        int ijk[3];
+        ijk[a] = pl.z;
+        ijk[b] = q % cnt[b];
+        ijk[c] = q / cnt[b];
+        int p = ijk[0] + cnt[0] * (ijk[1] + cnt[1] * ijk[2]);
+        v.states[p] = DDGI_STATE_UNINIT;
+        for (int k = 0; k < ti; ++k) store_irr(v, p, k % (v.irr_n + 2), k / (v.irr_n + 2), f3(0.0f, 0.0f, 0.0f));
+        for (int k = 0; k < td; ++k)
+            store_dist(v, p, k % (v.dist_n + 2), k / (v.dist_n + 2), make_float2(0.0f, 0.0f));
+    }
+}
+
+cudaError_t launch_query_cascade(const VolSet& vs, const float* pos, const float* nrm, int64_t n, float3 camera,
+                                 float* out, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    int grid = (int)(blocks < 1048576 ? blocks : 1048576);
+    k_query_cascade<<<grid, 256, 0, st>>>(vs, pos, nrm, n, camera, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_list_multi(const VolSet& vs, int total, int which, int32_t* list, int32_t* count,
+                                    cudaStream_t st) {
+    int blocks = (total + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_build_list_multi<<<blocks, 256, 0, st>>>(vs, total, which, list, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_planes(const VolSet& vs, const int4* planes, const int32_t* count, int max_planes,
+                                cudaStream_t st) {
+    if (max_planes <= 0) return cudaSuccess;
+    k_reset_planes<<<max_planes, 256, 0, st>>>(vs, planes, count);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_query(const VolView& v, const float* pos, const float* nrm, int64_t n, float3 camera,
                          float* out, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
@@ -62,10 +162,15 @@ cudaError_t launch_query(const VolView& v, const float* pos, const float* nrm, i
 
 cudaError_t launch_build_list(const uint8_t* states, int P, int which, int32_t* list, int32_t* count,
                               cudaStream_t st) {
-    int blocks = (P + 255) / 256;
+    return launch_build_list_range(states, 0, P, which, list, count, st);
+}
+
+cudaError_t launch_build_list_range(const uint8_t* states, int begin, int end, int which, int32_t* list,
+                                    int32_t* count, cudaStream_t st) {
+    int blocks = (end - begin + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    k_build_list<<<blocks, 256, 0, st>>>(states, P, which, list, count);
+    k_build_list<<<blocks, 256, 0, st>>>(states, begin, end, which, list, count);
     return cudaGetLastError();
 }
 

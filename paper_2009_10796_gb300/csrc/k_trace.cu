@@ -12,19 +12,24 @@
 
 namespace ddgi {
 
-__global__ void __launch_bounds__(256) k_classify(DevScene s, VolView v, const float4* __restrict__ dirs,
-                                                  int R, const int32_t* __restrict__ list,
+template <bool MULTI>
+__global__ void __launch_bounds__(256) k_classify(DevScene s, VolSet vs, const float4* __restrict__ dirs,
+                                                  int R, const int32_t* __restrict__ perm,
+                                                  const int32_t* __restrict__ list,
                                                   const int32_t* __restrict__ count) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int n = *count;
     for (int q = warp; q < n; q += nwarps) {
-        int p = list[q];
+        int e = list[q];
+        const VolView& v = vol_of<MULTI>(vs, e >> kEntryShift);
+        int p = e & kEntryMask;
         float3 o = probe_pos_phys(v, p);
         int bf = 0;
         float dmin = INFINITY;
-        for (int i = lane; i < R; i += 32) {
+        for (int j = lane; j < R; j += 32) {
+            const int i = perm ? __ldg(perm + j) : j;
             float4 d4 = __ldg(dirs + i);
             float3 d = f3(d4.x, d4.y, d4.z);
             RayPre r = ray_pre(o, d);
@@ -152,8 +157,10 @@ __device__ __forceinline__ void hit_frame(const DevScene& s, int k, float3& ng) 
     ng = cross(f3(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z), f3(p2.x - p0.x, p2.y - p0.y, p2.z - p0.z));
 }
 
-__global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolView v, Lights L,
+template <bool MULTI>
+__global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Lights L,
                                                        const float4* __restrict__ dirs, int R,
+                                                       const int32_t* __restrict__ perm,
                                                        const int32_t* __restrict__ active,
                                                        const int32_t* __restrict__ count,
                                                        float4* __restrict__ hits,
@@ -167,10 +174,14 @@ __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolView v, Li
         int64_t idx = base + lane;
         bool need = false;
         if (idx < total) {
+            // work item -> (probe slot, ray): a warp takes a compact cone of
+            // directions; the record keeps its canonical ray index
             int slot = (int)(idx / R);
-            int i = (int)(idx - (int64_t)slot * R);
-            int p = __ldg(active + slot);
-            float3 o = probe_pos_phys(v, p);
+            int j = (int)(idx - (int64_t)slot * R);
+            int i = perm ? __ldg(perm + j) : j;
+            idx = (int64_t)slot * R + i;
+            int e = __ldg(active + slot);
+            float3 o = probe_pos_phys(vol_of<MULTI>(vs, e >> kEntryShift), e & kEntryMask);
             float4 d4 = __ldg(dirs + i);
             float3 d = f3(d4.x, d4.y, d4.z);
             Hit h = traverse<false>(s, ray_pre(o, d));
@@ -196,7 +207,8 @@ __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolView v, Li
     }
 }
 
-__global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolView v, Lights L,
+template <bool MULTI>
+__global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolSet vs, Lights L,
                                                       const float4* __restrict__ dirs, int R,
                                                       const int32_t* __restrict__ active,
                                                       float4* __restrict__ hits,
@@ -207,8 +219,8 @@ __global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolView v, Lig
         int64_t idx = __ldg(shadow_list + q);
         int slot = (int)(idx / R);
         int i = (int)(idx - (int64_t)slot * R);
-        int p = __ldg(active + slot);
-        float3 o = probe_pos_phys(v, p);
+        int e = __ldg(active + slot);
+        float3 o = probe_pos_phys(vol_of<MULTI>(vs, e >> kEntryShift), e & kEntryMask);
         float4 d4 = __ldg(dirs + i);
         float3 d = f3(d4.x, d4.y, d4.z);
         float4 hr = hits[idx];
@@ -223,18 +235,24 @@ __global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolView v, Lig
     }
 }
 
-__global__ void __launch_bounds__(256) k_shade(DevScene s, VolView v, Lights L, const float4* __restrict__ dirs,
-                                               int R, const int32_t* __restrict__ active,
+template <bool MULTI>
+__global__ void __launch_bounds__(256) k_shade(DevScene s, VolSet vs, Lights L, const float4* __restrict__ dirs,
+                                               int R, const int32_t* __restrict__ perm,
+                                               const int32_t* __restrict__ active,
                                                const int32_t* __restrict__ count, float4* records) {
     const int64_t total = (int64_t)(*count) * R;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
-        int slot = (int)(idx / R);
-        int i = (int)(idx - (int64_t)slot * R);
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += stride) {
+        int slot = (int)(w / R);
+        int j = (int)(w - (int64_t)slot * R);
+        int i = perm ? __ldg(perm + j) : j;
+        const int64_t idx = (int64_t)slot * R + i;
         float4 d4 = __ldg(dirs + i);
         float3 d = f3(d4.x, d4.y, d4.z);
         float4 hr = records[idx];
         int k = __float_as_int(hr.y);
+        const int e = __ldg(active + slot);
+        const VolView& v = vol_of<MULTI>(vs, e >> kEntryShift);
         float4 rec;
         if (k < 0) {
             float c = dot(d, L.sky_up);
@@ -247,8 +265,7 @@ __global__ void __launch_bounds__(256) k_shade(DevScene s, VolView v, Lights L, 
             if (dot(d, ng) > 0.0f) {
                 rec = make_float4(0.0f, 0.0f, 0.0f, fminf(0.2f * t, v.t_max));
             } else {
-                int p = __ldg(active + slot);
-                float3 o = probe_pos_phys(v, p);
+                float3 o = probe_pos_phys(v, e & kEntryMask);
                 float3 n = (1.0f / length(ng)) * ng;
                 float3 x = o + t * d;
                 int orig = __float_as_int(__ldg(&s.tris[3 * (int64_t)k].w));
@@ -265,7 +282,9 @@ __global__ void __launch_bounds__(256) k_shade(DevScene s, VolView v, Lights L, 
                     float kk = dot(n, tol) * 0.318309886183790672f;   // 1/pi
                     direct = f3(L.sun_irr.x * kk, L.sun_irr.y * kk, L.sun_irr.z * kk);
                 }
-                float3 M = query_M(v, x, n, f3(-d.x, -d.y, -d.z));
+                // the previous frame's probes at the hit: the volume itself, or the whole cascade
+                float3 M = MULTI ? cascade_M(vs.table, vs.n, x, n, f3(-d.x, -d.y, -d.z))
+                                 : query_M(v, x, n, f3(-d.x, -d.y, -d.z));
                 rec = make_float4(Le.x + rho.x * (direct.x + M.x), Le.y + rho.y * (direct.y + M.y),
                                   Le.z + rho.z * (direct.z + M.z), fminf(t, v.t_max));
             }
@@ -324,9 +343,16 @@ __global__ void k_gbuffer(DevScene s, float3 cpos, float3 fwd, float3 right, flo
     }
 }
 
-cudaError_t launch_classify(const DevScene& s, const VolView& v, const float4* dirs, int R,
+cudaError_t launch_classify(const DevScene& s, const VolView& v, const float4* dirs, int R, const int32_t* perm,
                             const int32_t* list, const int32_t* count, int grid, cudaStream_t st) {
-    k_classify<<<grid, 256, 0, st>>>(s, v, dirs, R, list, count);
+    k_classify<false><<<grid, 256, 0, st>>>(s, single_set(v), dirs, R, perm, list, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_classify_multi(const DevScene& s, const VolSet& vs, const float4* dirs, int R,
+                                  const int32_t* perm, const int32_t* list, const int32_t* count, int grid,
+                                  cudaStream_t st) {
+    k_classify<true><<<grid, 256, 0, st>>>(s, vs, dirs, R, perm, list, count);
     return cudaGetLastError();
 }
 
@@ -337,17 +363,36 @@ cudaError_t launch_trace_shade(const DevScene& s, const VolView& v, const Lights
     return cudaGetLastError();
 }
 
-cudaError_t launch_trace_wavefront(const DevScene& s, const VolView& v, const Lights& L, const float4* dirs,
-                                   int R, const int32_t* active, const int32_t* count, float4* records,
-                                   int32_t* shadow_list, int32_t* shadow_count, int grid, cudaStream_t st) {
+template <bool MULTI>
+static cudaError_t trace_wavefront(const DevScene& s, const VolSet& vs, const Lights& L, const float4* dirs, int R,
+                                   const int32_t* perm, const int32_t* active, const int32_t* count,
+                                   float4* records, int32_t* shadow_list, int32_t* shadow_count, int grid,
+                                   cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(shadow_count, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
-    k_trace_primary<<<grid, 256, 0, st>>>(s, v, L, dirs, R, active, count, records, shadow_list, shadow_count);
+    k_trace_primary<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, perm, active, count, records, shadow_list,
+                                                  shadow_count);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_trace_shadow<<<grid, 256, 0, st>>>(s, v, L, dirs, R, active, records, shadow_list, shadow_count);
+    k_trace_shadow<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, active, records, shadow_list, shadow_count);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_shade<<<grid, 256, 0, st>>>(s, v, L, dirs, R, active, count, records);
+    k_shade<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, perm, active, count, records);
     return cudaGetLastError();
+}
+
+cudaError_t launch_trace_wavefront(const DevScene& s, const VolView& v, const Lights& L, const float4* dirs,
+                                   int R, const int32_t* perm, const int32_t* active, const int32_t* count,
+                                   float4* records, int32_t* shadow_list, int32_t* shadow_count, int grid,
+                                   cudaStream_t st) {
+    return trace_wavefront<false>(s, single_set(v), L, dirs, R, perm, active, count, records, shadow_list,
+                                  shadow_count, grid, st);
+}
+
+cudaError_t launch_trace_wavefront_multi(const DevScene& s, const VolSet& vs, const Lights& L,
+                                         const float4* dirs, int R, const int32_t* perm, const int32_t* active,
+                                         const int32_t* count, float4* records, int32_t* shadow_list,
+                                         int32_t* shadow_count, int grid, cudaStream_t st) {
+    return trace_wavefront<true>(s, vs, L, dirs, R, perm, active, count, records, shadow_list, shadow_count, grid,
+                                 st);
 }
 
 cudaError_t launch_trace_shade_count(const DevScene& s, const VolView& v, const Lights& L,

@@ -269,4 +269,31 @@ __device__ __forceinline__ float3 query_M(const VolView& v, float3 x, float3 n, 
     return f3(a.x * a.x, a.y * a.y, a.z * a.z);
 }
 
+// Cascade value M at x (Sec. 7.3): volumes densest first; each volume's
+// weight is the product over axes of its linear fall-off over the last cell
+// of its blend box; accumulation stops once the weights reach 1; the sum is
+// normalised by the weights taken (0 when no volume covers x).
+__device__ __forceinline__ float volume_weight(const VolView& v, float3 x) {
+    float wx = fminf(fmaxf(fminf(x.x - v.blend_lo.x, v.blend_hi.x - x.x) / v.spacing.x, 0.0f), 1.0f);
+    float wy = fminf(fmaxf(fminf(x.y - v.blend_lo.y, v.blend_hi.y - x.y) / v.spacing.y, 0.0f), 1.0f);
+    float wz = fminf(fmaxf(fminf(x.z - v.blend_lo.z, v.blend_hi.z - x.z) / v.spacing.z, 0.0f), 1.0f);
+    return wx * wy * wz;
+}
+
+__device__ __forceinline__ float3 cascade_M(const VolView* vols, int n, float3 x, float3 nrm, float3 wo) {
+    float sum = 0.0f;
+    float3 acc = f3(0.0f, 0.0f, 0.0f);
+    for (int k = 0; k < n; ++k) {
+        const VolView& v = vols[k];
+        float take = fminf(volume_weight(v, x), 1.0f - sum);
+        if (!(take > 0.0f)) continue;
+        float3 M = query_M(v, x, nrm, wo);
+        acc = acc + take * M;
+        sum += take;
+        if (sum >= 1.0f) break;
+    }
+    if (!(sum > 0.0f)) return f3(0.0f, 0.0f, 0.0f);
+    return (1.0f / sum) * acc;
+}
+
 }  // namespace ddgi

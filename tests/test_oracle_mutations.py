@@ -38,11 +38,12 @@ BATTERY = [
 
 MUTATIONS = {
     "blend_unnormalised": ("enew[k] = pow(m[k] / sw, 1.0 / v->gamma);", "enew[k] = pow(m[k], 1.0 / v->gamma);"),
-    "bias_sign": ("(0.2 * n[a] + 0.8 * wo[a])", "(0.2 * n[a] - 0.8 * wo[a])"),
+    "bias_sign": ("    for (int a = 0; a < 3; ++a)\n        xb[a] = x[a] + (0.2 * n[a] + 0.8 * wo[a])",
+                  "    for (int a = 0; a < 3; ++a)\n        xb[a] = x[a] + (0.2 * n[a] - 0.8 * wo[a])"),
     "border_unmirrored": ("TILE(tile, N, C, 0,     k)[c] = TILE(tile, N, C, 1, n + 1 - k)[c];",
                           "TILE(tile, N, C, 0,     k)[c] = TILE(tile, N, C, 1, k)[c];"),
-    "bilinear_transposed": ("double tx = sx - (double)x0, ty = sy - (double)y0;",
-                            "double ty = sx - (double)x0, tx = sy - (double)y0;"),
+    "bilinear_transposed": ("double tx = sx - (double)x0, ty = sy - (double)y0;\n    for (int64_t c = 0;",
+                            "double ty = sx - (double)x0, tx = sy - (double)y0;\n    for (int64_t c = 0;"),
     "backface_depth": ("out[3] = fmin(0.2 * t, v->t_max);", "out[3] = fmin(t, v->t_max);"),
     "chebyshev_square": ("wc = var / (var + dr * dr);", "wc = var / (var + dr);"),
     "gamma_decode": ("pow(fmax(e[k], 0.0), 0.5 * v->gamma)", "pow(fmax(e[k], 0.0), v->gamma)"),
@@ -51,8 +52,8 @@ MUTATIONS = {
                   "double z = 1.0 - (2.0 * (double)i) / (double)n;"),
     "trilinear_flipped": ("for (int a = 0; a < 3; ++a) wt *= o[a] ? fr[a] : 1.0 - fr[a];",
                           "for (int a = 0; a < 3; ++a) wt *= o[a] ? 1.0 - fr[a] : fr[a];"),
-    "direct_no_pi": ("direct[k] = L->sun_irradiance[k] * cosl / M_PI;",
-                     "direct[k] = L->sun_irradiance[k] * cosl;"),
+    "direct_no_pi": ("direct[k] = L->sun_irradiance[k] * cosl / M_PI;\n    }\n    /* indirect",
+                     "direct[k] = L->sun_irradiance[k] * cosl;\n    }\n    /* indirect"),
     "lerp_swapped": ("for (int k = 0; k < 3; ++k) old[k] = (1.0 - a) * enew[k] + a * old[k];",
                      "for (int k = 0; k < 3; ++k) old[k] = a * enew[k] + (1.0 - a) * old[k];"),
     "indirect_dropped": ("out[k] = Le[k] + rho[k] * (direct[k] + M[k]);", "out[k] = Le[k] + rho[k] * direct[k];"),
