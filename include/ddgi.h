@@ -93,8 +93,10 @@ int32_t     ddgi_version(void);
  *   object_flags     [n_objects] int32; bit 0: object casts shadows
  *   tri_emitter      [n_tris] int32 emitter index in [0, n_emitters) or -1
  *   emitter_radiance [n_emitters][3] float emitted radiance (front side only)
- * Synchronises the device once (upload).  Errors: INVALID_ARG on a bad
- * count or an index out of range (nothing allocated), OOM, CUDA. */
+ * n_tris is at most DDGI_MAX_TRIS.  Synchronises the device once (upload).
+ * Errors: INVALID_ARG on a bad count or an index out of range (nothing
+ * allocated), OOM, CUDA. */
+#define DDGI_MAX_TRIS ((int64_t)1 << 28)
 ddgi_status ddgi_scene_create(const float* verts, int64_t n_verts,
                               const int32_t* tris, int64_t n_tris,
                               const int32_t* tri_object, int32_t n_objects,

@@ -197,6 +197,7 @@ ddgi_status ddgi_scene_create(const float* verts, int64_t n_verts, const int32_t
     *out = nullptr;
     if (n_verts < 0 || n_tris < 0 || n_objects < 1 || n_emitters < 0)
         return fail(DDGI_ERR_INVALID_ARG, "negative count or no objects");
+    if (n_tris > DDGI_MAX_TRIS) return fail(DDGI_ERR_INVALID_ARG, "more than DDGI_MAX_TRIS triangles");
     if (n_tris > 0 && (!verts || !tris || !tri_object || !tri_emitter))
         return fail(DDGI_ERR_INVALID_ARG, "NULL triangle arrays");
     if (!object_albedo || !object_flags) return fail(DDGI_ERR_INVALID_ARG, "NULL object arrays");

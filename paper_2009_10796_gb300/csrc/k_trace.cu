@@ -173,7 +173,9 @@ __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Li
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
         int64_t idx = base + lane;
         bool need = false;
-        if (idx < total) {
+        const bool valid = idx < total;
+        float3 o = f3(0.0f, 0.0f, 0.0f), d = f3(0.0f, 0.0f, 1.0f);
+        if (valid) {
             // work item -> (probe slot, ray): a warp takes a compact cone of
             // directions; the record keeps its canonical ray index
             int slot = (int)(idx / R);
@@ -181,10 +183,12 @@ __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Li
             int i = perm ? __ldg(perm + j) : j;
             idx = (int64_t)slot * R + i;
             int e = __ldg(active + slot);
-            float3 o = probe_pos_phys(vol_of<MULTI>(vs, e >> kEntryShift), e & kEntryMask);
+            o = probe_pos_phys(vol_of<MULTI>(vs, e >> kEntryShift), e & kEntryMask);
             float4 d4 = __ldg(dirs + i);
-            float3 d = f3(d4.x, d4.y, d4.z);
-            Hit h = traverse<false>(s, ray_pre(o, d));
+            d = f3(d4.x, d4.y, d4.z);
+        }
+        Hit h = traverse_ww<false>(s, ray_pre(o, d), valid);
+        if (valid) {
             if (h.orig >= 0 && L.sun_on) {
                 float3 ng;
                 hit_frame(s, h.k, ng);
@@ -215,23 +219,32 @@ __global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolSet vs, Lig
                                                       const int32_t* __restrict__ shadow_list,
                                                       const int32_t* __restrict__ shadow_count) {
     const int n = *shadow_count;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-        int64_t idx = __ldg(shadow_list + q);
-        int slot = (int)(idx / R);
-        int i = (int)(idx - (int64_t)slot * R);
-        int e = __ldg(active + slot);
-        float3 o = probe_pos_phys(vol_of<MULTI>(vs, e >> kEntryShift), e & kEntryMask);
-        float4 d4 = __ldg(dirs + i);
-        float3 d = f3(d4.x, d4.y, d4.z);
-        float4 hr = hits[idx];
-        float3 ng;
-        hit_frame(s, __float_as_int(hr.y), ng);
-        float3 n = (1.0f / length(ng)) * ng;
-        float3 x = o + hr.x * d;
-        float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
-        float off = 1e-4f * (1.0f + length(x));
-        Hit sh = traverse<true>(s, ray_pre(x + off * n, tol));
-        if (sh.orig < 0) reinterpret_cast<float*>(hits)[4 * idx + 2] = 1.0f;
+    const int stride = gridDim.x * blockDim.x;
+    const float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
+    // warp-uniform trip count: the traversal is warp-cooperative
+    for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const int q = base + (threadIdx.x & 31);
+        const bool valid = q < n;
+        int64_t idx = 0;
+        float3 so = f3(0.0f, 0.0f, 0.0f);
+        if (valid) {
+            idx = __ldg(shadow_list + q);
+            int slot = (int)(idx / R);
+            int i = (int)(idx - (int64_t)slot * R);
+            int e = __ldg(active + slot);
+            float3 o = probe_pos_phys(vol_of<MULTI>(vs, e >> kEntryShift), e & kEntryMask);
+            float4 d4 = __ldg(dirs + i);
+            float3 d = f3(d4.x, d4.y, d4.z);
+            float4 hr = hits[idx];
+            float3 ng;
+            hit_frame(s, __float_as_int(hr.y), ng);
+            float3 nn = (1.0f / length(ng)) * ng;
+            float3 x = o + hr.x * d;
+            float off = 1e-4f * (1.0f + length(x));
+            so = x + off * nn;
+        }
+        Hit sh = traverse_ww<true>(s, ray_pre(so, tol), valid);
+        if (valid && sh.orig < 0) reinterpret_cast<float*>(hits)[4 * idx + 2] = 1.0f;
     }
 }
 

@@ -164,4 +164,102 @@ __device__ __forceinline__ Hit traverse(const DevScene& s, const RayPre& r, Trac
     return h;
 }
 
+// Warp-cooperative traversal with postponed leaves ("while-while", Aila and
+// Laine, "Understanding the Efficiency of Ray Traversal on GPUs", HPG 2009).
+// A lane that reaches a leaf parks it and keeps descending internal nodes
+// until every lane of the warp holds a leaf; the parked leaves are then
+// tested together, so the triangle loop runs with most lanes busy instead
+// of once per node visit for whichever lane happened to reach a leaf.  The
+// closest hit (smallest t, ties to the smaller original index) does not
+// depend on the visiting order because box culling is conservative, so the
+// result equals traverse<false>'s; for ANY, occlusion is the same.
+// Every lane of the warp must call it (inactive lanes pass valid = false).
+// Stack entries are node indices (>= 0) or leaf codes
+// ~((first << 2) | (count - 1)) (leaves hold 1..4 triangles, first < 2^28).
+constexpr int kNoLeaf = 0;              // "no parked leaf" (leaf codes are < 0)
+constexpr int kDone = (int)0x80000000;  // empty-stack sentinel, below every leaf code
+
+__device__ __forceinline__ int leaf_code(int child, int cnt) { return ~(((~child) << 2) | (cnt - 1)); }
+
+template <bool ANY>
+__device__ __forceinline__ Hit traverse_ww(const DevScene& s, const RayPre& r, bool valid) {
+    Hit h;
+    h.t = INFINITY;
+    h.orig = -1;
+    h.k = -1;
+    int stack[kStackSize];
+    int sp = 0;
+    int node = (valid && s.n_nodes > 0) ? 0 : kDone;
+    int leaf = kNoLeaf;
+    while (true) {
+        // internal nodes, until no lane is still looking for a leaf
+        while (true) {
+            if (node >= 0) {
+                const float4* N = s.nodes + 4 * (int64_t)node;
+                float4 a = __ldg(N), b = __ldg(N + 1), z = __ldg(N + 2);
+                int4 m = __ldg(reinterpret_cast<const int4*>(N + 3));
+                float e0 = box_enter(r, a.x, a.y, a.z, a.w, z.x, z.y, h.t);
+                float e1 = box_enter(r, b.x, b.y, b.z, b.w, z.z, z.w, h.t);
+                int c0 = m.x >= 0 ? m.x : leaf_code(m.x, m.z);
+                int c1 = m.y >= 0 ? m.y : leaf_code(m.y, m.w);
+                // an empty slot (leaf of 0 triangles, inverted box) is never entered
+                bool h0 = e0 != INFINITY && (m.x >= 0 || m.z > 0);
+                bool h1 = e1 != INFINITY && (m.y >= 0 || m.w > 0);
+                if (h0 && h1) {
+                    bool first0 = e0 <= e1;
+                    if (sp < kStackSize) stack[sp++] = first0 ? c1 : c0;
+                    node = first0 ? c0 : c1;
+                } else if (h0) {
+                    node = c0;
+                } else if (h1) {
+                    node = c1;
+                } else {
+                    node = sp > 0 ? stack[--sp] : kDone;
+                }
+                if (node < 0 && node != kDone && leaf == kNoLeaf) {
+                    leaf = node;
+                    node = sp > 0 ? stack[--sp] : kDone;
+                }
+            }
+            if (__ballot_sync(0xffffffffu, node >= 0 && leaf == kNoLeaf) == 0) break;
+        }
+        // parked leaves (and leaves popped right after them)
+        while (leaf != kNoLeaf) {
+            int code = ~leaf;
+            int first = code >> 2, cnt = (code & 3) + 1;
+            for (int k = first; k < first + cnt; ++k) {
+                const float4* T = s.tris + 3 * (int64_t)k;
+                float4 p0 = __ldg(T), p1 = __ldg(T + 1), p2 = __ldg(T + 2);
+                if (ANY && !(__float_as_int(p1.w) & 1)) continue;
+                float t = tri_hit(r, p0, p1, p2);
+                if (t < 0.0f) continue;
+                int orig = __float_as_int(p0.w);
+                if (ANY) {
+                    h.t = t;
+                    h.orig = orig;
+                    h.k = k;
+                    break;
+                }
+                if (t < h.t || (t == h.t && orig < h.orig)) {
+                    h.t = t;
+                    h.orig = orig;
+                    h.k = k;
+                }
+            }
+            if (ANY && h.orig >= 0) {
+                node = kDone;
+                leaf = kNoLeaf;
+                break;
+            }
+            leaf = kNoLeaf;
+            if (node < 0 && node != kDone) {
+                leaf = node;
+                node = sp > 0 ? stack[--sp] : kDone;
+            }
+        }
+        if (__ballot_sync(0xffffffffu, node != kDone) == 0) break;
+    }
+    return h;
+}
+
 }  // namespace ddgi
