@@ -844,7 +844,8 @@ ddgi_status cascade_enqueue(ddgi_cascade_s* c, const DevScene& sc, const Lights&
                                     c->inv_irr_r, c->inv_dist_r, c->records, c->lists + c->total, c->counts + 1,
                                     c->status, sms, st));
     else
-        DDGI_CK(launch_blend_set(vs, true, bp, c->w_irr, c->inv_s_irr, c->w_dist, c->inv_s_dist, c->records,
+        DDGI_CK(launch_blend_set(vs, true, bp, d0.irr_n, d0.dist_n, c->w_irr, c->inv_s_irr, c->w_dist, c->inv_s_dist,
+                                 c->records,
                                  c->lists + c->total, c->counts + 1, c->status, sms * 4, c->blend_probes, st));
     return DDGI_OK;
 }

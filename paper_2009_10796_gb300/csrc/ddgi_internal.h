@@ -137,6 +137,9 @@ cudaError_t launch_classify_multi(const DevScene& s, const VolSet& vs, const flo
 cudaError_t launch_trace_shade(const DevScene& s, const VolView& v, const Lights& L,
                                const float4* dirs, int R, const int32_t* active,
                                const int32_t* count, float4* records, int grid, cudaStream_t st);
+// Wavefront trace: persistent primary pass (closest hits, shadow-ray list),
+// persistent shadow pass, then shading.  shadow_count is 4 int32 of device
+// scratch, 8-byte aligned (shadow-ray count, 64-bit work counter).
 cudaError_t launch_trace_wavefront(const DevScene& s, const VolView& v, const Lights& L, const float4* dirs,
                                    int R, const int32_t* perm, const int32_t* active, const int32_t* count,
                                    float4* records, int32_t* shadow_list, int32_t* shadow_count, int grid,
@@ -156,8 +159,10 @@ cudaError_t launch_blend(const VolView& v, const BlendParams& bp, const float* w
                          const float* inv_s_irr, const float* w_dist, const float* inv_s_dist,
                          const float4* records, const int32_t* active, const int32_t* count,
                          uint32_t* status, int grid, cudaStream_t st);
-// blend over a volume set; probes_per_cta in {4, 8, 16} (autotuned)
-cudaError_t launch_blend_set(const VolSet& vs, bool multi, const BlendParams& bp, const float* w_irr,
+// blend over a volume set sharing irr_n / dist_n; probes_per_cta in
+// {4, 8, 16} (autotuned)
+cudaError_t launch_blend_set(const VolSet& vs, bool multi, const BlendParams& bp, int irr_n, int dist_n,
+                             const float* w_irr,
                              const float* inv_s_irr, const float* w_dist, const float* inv_s_dist,
                              const float4* records, const int32_t* active, const int32_t* count,
                              uint32_t* status, int grid, int probes_per_cta, cudaStream_t st);

@@ -6,10 +6,17 @@
 //   W_dist[t][i] = max(0, n_t . w_i)^p            (power-cosine weight)
 // with 1 / sum_i W per texel, in double precision, rounded once to float.
 //
-// k_blend_simt is the plain FP32 blend.  A CTA owns a group of kProbes
-// active probes: their ray records are staged in shared memory (padded
-// stride, conflict-free across probes), each thread computes (texel, probe)
-// dot products over the R rays, and the epilogue normalises, gamma-encodes,
+// The plain FP32 blend is a product of the texel weight matrices with each
+// probe's ray records.  k_blend_tiled computes it register-tiled: a CTA owns
+// a group of PG active probes whose records sit in shared memory as four
+// channel planes (r, g, b, distance); the weight matrices stream through
+// shared memory in chunks of kTileKC rays; each thread accumulates a 4-texel
+// x 4-probe tile of distance moments (sum w d and sum w d^2, two FMAs per
+// ray and texel) or a 4-texel x 2-probe tile of irradiance, so every
+// shared-memory load feeds 8 to 16 FMAs.  k_blend_simt
+// (one thread per (texel, probe) pair) covers the shapes the tiled kernel
+// does not fit.  Both sum each texel's rays in ray order with the same
+// operations, so they give the same bits.  The epilogue normalises, gamma-encodes,
 // applies the per-texel hysteresis thresholds, lerps with the old texel and
 // writes the texel plus the border texels that copy it (the octahedral
 // border copy of Sec. 7.1 fused into the blend).  The probe's state advances
@@ -156,13 +163,273 @@ __global__ void __launch_bounds__(256) k_blend_simt(VolSet vs, BlendParams bp,
             for (int i = 0; i < R; ++i) {
                 float w = __ldg(wr + i);
                 float d = rr[i].w;
-                float wd = w * d;
-                m1 += wd;
-                m2 = fmaf(wd, d, m2);
+                m1 = fmaf(w, d, m1);
+                m2 = fmaf(w, d * d, m2);
             }
             const int e = s_probe[pp];
             blend_dist_texel(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, t, m1, m2,
                              __ldg(inv_s_dist + t), s_newly[pp] != 0, status);
+        }
+        __syncthreads();
+        if (threadIdx.x < np && s_newly[threadIdx.x]) {
+            const int e = s_probe[threadIdx.x];
+            vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask] = DDGI_STATE_VIGILANT;
+        }
+        __syncthreads();
+    }
+}
+
+constexpr int kTileKC = 16;   // rays per staged weight chunk
+constexpr int kTileWS = kTileKC + 4;   // weight row stride in floats: 16-byte rows, conflict-free columns
+constexpr int kTileMaxThreads = 320;   // with 2 CTAs per SM: up to 102 registers per thread
+constexpr int kRecBatch = 8;           // record loads in flight per thread while staging
+
+// Threads, shared memory and feasibility of k_blend_tiled for a tile shape.
+// Distance units fill whole warps first, so no warp runs both tile kinds.
+struct TiledShape {
+    int nqi, nqd;           // texel rows per register tile: ceil(texels / 4)
+    int dist_units, dist_threads, irr_units, threads;
+    size_t smem;
+};
+
+static TiledShape tiled_shape(int PG, int R, int irr_n, int dist_n) {
+    TiledShape t;
+    t.nqi = (irr_n * irr_n + 3) / 4;
+    t.nqd = (dist_n * dist_n + 3) / 4;
+    t.dist_units = t.nqd * (PG / 4);
+    t.dist_threads = (t.dist_units + 31) / 32 * 32;
+    t.irr_units = t.nqi * (PG / 2);
+    t.threads = t.dist_threads + (t.irr_units + 31) / 32 * 32;
+    t.smem = sizeof(float) * ((size_t)4 * PG * (R + 4) + (size_t)2 * 4 * (t.nqd + t.nqi) * kTileWS);
+    return t;
+}
+
+// 16-byte asynchronous global -> shared copy (zero-filled when !valid).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// grid-stride over groups of PG active probes; blockDim = TiledShape::threads.
+// Requires R % 4 == 0.  Thread u < dist_units owns distance texels
+// tq + a * nqd (a < 4) of probes 4 pq .. 4 pq + 3; thread dist_threads + u'
+// (u' < irr_units) owns irradiance texels tq + a * nqi of probes 2 pq,
+// 2 pq + 1.  Striding the texels by nqd (not 4) puts a warp's weight rows on
+// distinct banks.  The next weight chunk is in flight (asynchronous copy)
+// while the current one is summed; the old texel values are fetched all at
+// once before the blend.
+template <bool MULTI, int PG>
+__global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, BlendParams bp,
+                                                                    const float* __restrict__ w_irr,
+                                                                    const float* __restrict__ inv_s_irr,
+                                                                    const float* __restrict__ w_dist,
+                                                                    const float* __restrict__ inv_s_dist,
+                                                                    const float4* __restrict__ records,
+                                                                    const int32_t* __restrict__ active,
+                                                                    const int32_t* __restrict__ count,
+                                                                    uint32_t* status) {
+    static_assert(PG % 4 == 0, "probe groups come in quads");
+    extern __shared__ __align__(16) float sm[];
+    __shared__ int s_probe[PG];
+    __shared__ int s_newly[PG];
+    const int R = bp.R;
+    const int RS = R + 4;
+    const VolView& v0 = vol_of<MULTI>(vs, 0);   // cascades share R and tile sizes
+    const int ni = v0.irr_n, nd = v0.dist_n;
+    const int ti = ni * ni, td = nd * nd;
+    const int nqi = (ti + 3) / 4, nqd = (td + 3) / 4;
+    const int wrows = 4 * (nqd + nqi);          // distance rows, then irradiance rows
+    float* pr = sm;                              // [PG][RS] planes: radiance r, g, b and distance
+    float* pgc = pr + PG * RS;
+    float* pbc = pgc + PG * RS;
+    float* pdc = pbc + PG * RS;
+    float* wbuf = pdc + PG * RS;                 // 2 x [wrows][kTileWS] weight chunks
+    const int dist_units = nqd * (PG / 4), irr_units = nqi * (PG / 2);
+    const int dist_threads = (dist_units + 31) / 32 * 32;
+    const int u = threadIdx.x;
+    const bool is_dist = u < dist_units;
+    const bool is_irr = u >= dist_threads && u - dist_threads < irr_units;
+    const int ui = is_dist ? u : u - dist_threads;
+    const int tq = is_dist ? ui % nqd : (is_irr ? ui % nqi : 0);
+    const int pq = is_dist ? ui / nqd : (is_irr ? ui / nqi : 0);
+    const int n_chunks = (R + kTileKC - 1) / kTileKC;
+    const int n_act = *count;
+
+    auto issue_chunk = [&](int c) {
+        float* wb = wbuf + (c & 1) * wrows * kTileWS;
+        const int c0 = c * kTileKC;
+        for (int k = threadIdx.x; k < wrows * (kTileKC / 4); k += blockDim.x) {
+            int row = k / (kTileKC / 4), j = 4 * (k - row * (kTileKC / 4));
+            bool dist_row = row < 4 * nqd;
+            int t = dist_row ? row : row - 4 * nqd;
+            bool ok = c0 + j < R && t < (dist_row ? td : ti);
+            const float* src = (dist_row ? w_dist : w_irr) + (ok ? (int64_t)t * R + c0 + j : 0);
+            cp_async16(wb + row * kTileWS + j, src, ok);
+        }
+        cp_async_commit();
+    };
+
+    for (int g0 = blockIdx.x * PG; g0 < n_act; g0 += gridDim.x * PG) {
+        const int np = min(PG, n_act - g0);
+        issue_chunk(0);   // overlaps the record staging below
+        if (threadIdx.x < np) {
+            int e = active[g0 + threadIdx.x];
+            s_probe[threadIdx.x] = e;
+            s_newly[threadIdx.x] =
+                vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask] == DDGI_STATE_NEWLY_VIGILANT;
+        }
+        // records -> planes, kRecBatch independent loads in flight per thread
+        for (int k0 = threadIdx.x; k0 < PG * R; k0 += kRecBatch * blockDim.x) {
+            float4 rec[kRecBatch];
+#pragma unroll
+            for (int b = 0; b < kRecBatch; ++b) {
+                const int k = k0 + b * blockDim.x;
+                rec[b] = k < np * R ? records[(int64_t)g0 * R + k] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int b = 0; b < kRecBatch; ++b) {
+                const int k = k0 + b * blockDim.x;
+                if (k < PG * R) {
+                    const int pp = k / R, o = pp * RS + (k - pp * R);
+                    pr[o] = rec[b].x;
+                    pgc[o] = rec[b].y;
+                    pbc[o] = rec[b].z;
+                    pdc[o] = rec[b].w;
+                }
+            }
+        }
+        // distance tile: sum w d at acc[a*4+b], sum w d^2 at acc[16+a*4+b];
+        // irradiance tile: r, g, b at acc[{0, 8, 16} + a*2+b]
+        float acc[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) acc[k] = 0.0f;
+        for (int c = 0; c < n_chunks; ++c) {
+            if (c + 1 < n_chunks) {
+                issue_chunk(c + 1);
+                cp_async_wait_all_but_one();
+            } else {
+                cp_async_wait_all();
+            }
+            __syncthreads();   // chunk c (and, at c = 0, the planes) visible to all
+            const float* wb = wbuf + (c & 1) * wrows * kTileWS;
+            const int c0 = c * kTileKC, kc = min(kTileKC, R - c0);
+            if (is_dist) {
+                for (int j = 0; j < kc; j += 4) {
+                    float4 w[4], d[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+                        w[a] = *reinterpret_cast<const float4*>(wb + (tq + a * nqd) * kTileWS + j);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b)
+                        d[b] = *reinterpret_cast<const float4*>(pdc + (4 * pq + b) * RS + c0 + j);
+#pragma unroll
+                    for (int ii = 0; ii < 4; ++ii) {
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const float dv = ii == 0 ? d[b].x : ii == 1 ? d[b].y : ii == 2 ? d[b].z : d[b].w;
+                            const float d2 = dv * dv;
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) {
+                                const float wv = ii == 0 ? w[a].x : ii == 1 ? w[a].y : ii == 2 ? w[a].z : w[a].w;
+                                acc[a * 4 + b] = fmaf(wv, dv, acc[a * 4 + b]);
+                                acc[16 + a * 4 + b] = fmaf(wv, d2, acc[16 + a * 4 + b]);
+                            }
+                        }
+                    }
+                }
+            } else if (is_irr) {
+                const float* wsi = wb + 4 * nqd * kTileWS;
+                for (int j = 0; j < kc; j += 4) {
+                    float4 w[4], cr[2], cg[2], cb[2];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+                        w[a] = *reinterpret_cast<const float4*>(wsi + (tq + a * nqi) * kTileWS + j);
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        const int o = (2 * pq + b) * RS + c0 + j;
+                        cr[b] = *reinterpret_cast<const float4*>(pr + o);
+                        cg[b] = *reinterpret_cast<const float4*>(pgc + o);
+                        cb[b] = *reinterpret_cast<const float4*>(pbc + o);
+                    }
+#pragma unroll
+                    for (int ii = 0; ii < 4; ++ii) {
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            const float wv = ii == 0 ? w[a].x : ii == 1 ? w[a].y : ii == 2 ? w[a].z : w[a].w;
+#pragma unroll
+                            for (int b = 0; b < 2; ++b) {
+                                const float4 r4 = cr[b], g4 = cg[b], b4 = cb[b];
+                                const float lr = ii == 0 ? r4.x : ii == 1 ? r4.y : ii == 2 ? r4.z : r4.w;
+                                const float lg = ii == 0 ? g4.x : ii == 1 ? g4.y : ii == 2 ? g4.z : g4.w;
+                                const float lb = ii == 0 ? b4.x : ii == 1 ? b4.y : ii == 2 ? b4.z : b4.w;
+                                acc[a * 2 + b] = fmaf(wv, lr, acc[a * 2 + b]);
+                                acc[8 + a * 2 + b] = fmaf(wv, lg, acc[8 + a * 2 + b]);
+                                acc[16 + a * 2 + b] = fmaf(wv, lb, acc[16 + a * 2 + b]);
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();   // this chunk's buffer is refilled two chunks later
+        }
+        if (is_dist) {
+            float2 old[16];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int t = tq + a * nqd, pp = 4 * pq + b;
+                    old[a * 4 + b] = make_float2(0.0f, 0.0f);
+                    if (t < td && pp < np) {
+                        const int e = s_probe[pp];
+                        old[a * 4 + b] = dist_texel_old(vol_of<MULTI>(vs, e >> kEntryShift), e & kEntryMask, t);
+                    }
+                }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int t = tq + a * nqd;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int pp = 4 * pq + b;
+                    if (t < td && pp < np) {
+                        const int e = s_probe[pp];
+                        blend_dist_texel_from(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, t,
+                                              acc[a * 4 + b], acc[16 + a * 4 + b], __ldg(inv_s_dist + t),
+                                              s_newly[pp] != 0, status, old[a * 4 + b]);
+                    }
+                }
+            }
+        } else if (is_irr) {
+            float3 old[8];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const int t = tq + a * nqi, pp = 2 * pq + b;
+                    old[a * 2 + b] = f3(0.0f, 0.0f, 0.0f);
+                    if (t < ti && pp < np) {
+                        const int e = s_probe[pp];
+                        old[a * 2 + b] = irr_texel_old(vol_of<MULTI>(vs, e >> kEntryShift), e & kEntryMask, t);
+                    }
+                }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int t = tq + a * nqi;
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const int pp = 2 * pq + b;
+                    if (t < ti && pp < np) {
+                        const int e = s_probe[pp];
+                        blend_irr_texel_from(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, t,
+                                             acc[a * 2 + b], acc[8 + a * 2 + b], acc[16 + a * 2 + b],
+                                             __ldg(inv_s_irr + t), s_newly[pp] != 0, status, old[a * 2 + b]);
+                    }
+                }
+            }
         }
         __syncthreads();
         if (threadIdx.x < np && s_newly[threadIdx.x]) {
@@ -191,19 +458,59 @@ cudaError_t launch_frame_setup_dev(const FrameRot* rot_dev, int R, int irr_n, in
     return cudaGetLastError();
 }
 
-template <bool MULTI, int PGS>
-static cudaError_t blend_simt(const VolSet& vs, const BlendParams& bp, const float* w_irr, const float* inv_s_irr,
-                              const float* w_dist, const float* inv_s_dist, const float4* records,
-                              const int32_t* active, const int32_t* count, uint32_t* status, int grid,
-                              cudaStream_t st) {
-    size_t smem = (size_t)PGS * (bp.R + 1) * sizeof(float4);
-    static int configured_smem = 0;
-    if ((int)smem > configured_smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_blend_simt<MULTI, PGS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured_smem = (int)smem;
+// Sets the kernel's dynamic shared-memory cap to the device's opt-in maximum
+// less its static shared memory, once per process (host-side attribute; must
+// not run under stream capture).
+template <typename K>
+static cudaError_t allow_max_smem(K kernel, bool& done) {
+    if (done) return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+static int smem_optin() {
+    static int optin = 0;
+    if (optin == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            optin = 48 * 1024;
     }
+    return optin;
+}
+
+// Opts both blend kernels of one instantiation into the maximum dynamic
+// shared memory, once per process.
+template <bool MULTI, int PGS>
+static cudaError_t opt_in_blend() {
+    static bool tiled = false, rows = false;
+    cudaError_t e = allow_max_smem(k_blend_tiled<MULTI, PGS>, tiled);
+    if (e == cudaSuccess) e = allow_max_smem(k_blend_simt<MULTI, PGS>, rows);
+    return e;
+}
+
+template <bool MULTI, int PGS>
+static cudaError_t blend_simt(const VolSet& vs, const BlendParams& bp, int irr_n, int dist_n, const float* w_irr,
+                              const float* inv_s_irr, const float* w_dist, const float* inv_s_dist,
+                              const float4* records, const int32_t* active, const int32_t* count,
+                              uint32_t* status, int grid, cudaStream_t st) {
+    cudaError_t e = opt_in_blend<MULTI, PGS>();
+    if (e != cudaSuccess) return e;
+    const TiledShape ts = tiled_shape(PGS, bp.R, irr_n, dist_n);
+    if (bp.R % 4 == 0 && ts.threads <= kTileMaxThreads && ts.smem + 1024 <= (size_t)smem_optin()) {
+        k_blend_tiled<MULTI, PGS><<<grid, ts.threads, ts.smem, st>>>(vs, bp, w_irr, inv_s_irr, w_dist, inv_s_dist,
+                                                                     records, active, count, status);
+        return cudaGetLastError();
+    }
+    size_t smem = (size_t)PGS * (bp.R + 1) * sizeof(float4);
     k_blend_simt<MULTI, PGS><<<grid, 256, smem, st>>>(vs, bp, w_irr, inv_s_irr, w_dist, inv_s_dist, records,
                                                       active, count, status);
     return cudaGetLastError();
@@ -213,18 +520,19 @@ cudaError_t launch_blend(const VolView& v, const BlendParams& bp, const float* w
                          const float* w_dist, const float* inv_s_dist, const float4* records,
                          const int32_t* active, const int32_t* count, uint32_t* status, int grid,
                          cudaStream_t st) {
-    return blend_simt<false, 8>(single_set(v), bp, w_irr, inv_s_irr, w_dist, inv_s_dist, records, active, count,
-                                status, grid, st);
+    return blend_simt<false, 16>(single_set(v), bp, v.irr_n, v.dist_n, w_irr, inv_s_irr, w_dist, inv_s_dist,
+                                records, active, count, status, grid, st);
 }
 
-cudaError_t launch_blend_set(const VolSet& vs, bool multi, const BlendParams& bp, const float* w_irr,
+cudaError_t launch_blend_set(const VolSet& vs, bool multi, const BlendParams& bp, int irr_n, int dist_n,
+                             const float* w_irr,
                              const float* inv_s_irr, const float* w_dist, const float* inv_s_dist,
                              const float4* records, const int32_t* active, const int32_t* count,
                              uint32_t* status, int grid, int probes_per_cta, cudaStream_t st) {
 #define DDGI_BLEND_CASE(M, P)                                                                                 \
     if (multi == M && probes_per_cta == P)                                                                   \
-        return blend_simt<M, P>(vs, bp, w_irr, inv_s_irr, w_dist, inv_s_dist, records, active, count, status, \
-                                grid, st);
+        return blend_simt<M, P>(vs, bp, irr_n, dist_n, w_irr, inv_s_irr, w_dist, inv_s_dist, records, active,   \
+                                count, status, grid, st);
     DDGI_BLEND_CASE(false, 4)
     DDGI_BLEND_CASE(false, 8)
     DDGI_BLEND_CASE(false, 16)
@@ -235,23 +543,15 @@ cudaError_t launch_blend_set(const VolSet& vs, bool multi, const BlendParams& bp
     return cudaErrorInvalidValue;
 }
 
-// Sets the shared-memory opt-in of every SIMT blend instantiation for R rays
-// (outside any stream capture).
-cudaError_t prepare_blend_kernels(int R) {
-    cudaError_t e = cudaSuccess;
-#define DDGI_PREP(M, P)                                                                                   \
-    if (e == cudaSuccess)                                                                                \
-        e = cudaFuncSetAttribute(k_blend_simt<M, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
-                                 (int)((size_t)P * (R + 1) * sizeof(float4)) > 48 * 1024                    \
-                                     ? (int)((size_t)P * (R + 1) * sizeof(float4))                          \
-                                     : 48 * 1024);
-    DDGI_PREP(false, 4)
-    DDGI_PREP(false, 8)
-    DDGI_PREP(false, 16)
-    DDGI_PREP(true, 4)
-    DDGI_PREP(true, 8)
-    DDGI_PREP(true, 16)
-#undef DDGI_PREP
+// Sets the shared-memory opt-in of every SIMT blend instantiation (outside
+// any stream capture).
+cudaError_t prepare_blend_kernels(int) {
+    cudaError_t e = opt_in_blend<false, 4>();
+    if (e == cudaSuccess) e = opt_in_blend<false, 8>();
+    if (e == cudaSuccess) e = opt_in_blend<false, 16>();
+    if (e == cudaSuccess) e = opt_in_blend<true, 4>();
+    if (e == cudaSuccess) e = opt_in_blend<true, 8>();
+    if (e == cudaSuccess) e = opt_in_blend<true, 16>();
     return e;
 }
 

@@ -181,85 +181,104 @@ constexpr int kDone = (int)0x80000000;  // empty-stack sentinel, below every lea
 
 __device__ __forceinline__ int leaf_code(int child, int cnt) { return ~(((~child) << 2) | (cnt - 1)); }
 
-template <bool ANY>
-__device__ __forceinline__ Hit traverse_ww(const DevScene& s, const RayPre& r, bool valid) {
-    Hit h;
-    h.t = INFINITY;
-    h.orig = -1;
-    h.k = -1;
+// Per-lane state of the warp-cooperative walk.
+struct WwLane {
     int stack[kStackSize];
-    int sp = 0;
-    int node = (valid && s.n_nodes > 0) ? 0 : kDone;
-    int leaf = kNoLeaf;
+    int sp;
+    int node;   // next internal node, a leaf code taken from the stack, or kDone
+    int leaf;   // parked leaf code or kNoLeaf
+    Hit h;
+};
+
+__device__ __forceinline__ void ww_start(const DevScene& s, WwLane& w, bool valid) {
+    w.sp = 0;
+    w.node = (valid && s.n_nodes > 0) ? 0 : kDone;
+    w.leaf = kNoLeaf;
+    w.h.t = INFINITY;
+    w.h.orig = -1;
+    w.h.k = -1;
+}
+
+__device__ __forceinline__ int ww_pop(WwLane& w) { return w.sp > 0 ? w.stack[--w.sp] : kDone; }
+
+// One round: descend internal nodes until no lane is still looking for a
+// leaf, then test every parked leaf (and leaves popped right after it).  A
+// lane's walk is over when node == kDone after the round.  Warp-cooperative.
+template <bool ANY>
+__device__ __forceinline__ void ww_round(const DevScene& s, const RayPre& r, WwLane& w) {
     while (true) {
-        // internal nodes, until no lane is still looking for a leaf
-        while (true) {
-            if (node >= 0) {
-                const float4* N = s.nodes + 4 * (int64_t)node;
-                float4 a = __ldg(N), b = __ldg(N + 1), z = __ldg(N + 2);
-                int4 m = __ldg(reinterpret_cast<const int4*>(N + 3));
-                float e0 = box_enter(r, a.x, a.y, a.z, a.w, z.x, z.y, h.t);
-                float e1 = box_enter(r, b.x, b.y, b.z, b.w, z.z, z.w, h.t);
-                int c0 = m.x >= 0 ? m.x : leaf_code(m.x, m.z);
-                int c1 = m.y >= 0 ? m.y : leaf_code(m.y, m.w);
-                // an empty slot (leaf of 0 triangles, inverted box) is never entered
-                bool h0 = e0 != INFINITY && (m.x >= 0 || m.z > 0);
-                bool h1 = e1 != INFINITY && (m.y >= 0 || m.w > 0);
-                if (h0 && h1) {
-                    bool first0 = e0 <= e1;
-                    if (sp < kStackSize) stack[sp++] = first0 ? c1 : c0;
-                    node = first0 ? c0 : c1;
-                } else if (h0) {
-                    node = c0;
-                } else if (h1) {
-                    node = c1;
-                } else {
-                    node = sp > 0 ? stack[--sp] : kDone;
-                }
-                if (node < 0 && node != kDone && leaf == kNoLeaf) {
-                    leaf = node;
-                    node = sp > 0 ? stack[--sp] : kDone;
-                }
+        if (w.node >= 0) {
+            const float4* N = s.nodes + 4 * (int64_t)w.node;
+            float4 a = __ldg(N), b = __ldg(N + 1), z = __ldg(N + 2);
+            int4 m = __ldg(reinterpret_cast<const int4*>(N + 3));
+            float e0 = box_enter(r, a.x, a.y, a.z, a.w, z.x, z.y, w.h.t);
+            float e1 = box_enter(r, b.x, b.y, b.z, b.w, z.z, z.w, w.h.t);
+            int c0 = m.x >= 0 ? m.x : leaf_code(m.x, m.z);
+            int c1 = m.y >= 0 ? m.y : leaf_code(m.y, m.w);
+            // an empty slot (leaf of 0 triangles, inverted box) is never entered
+            bool h0 = e0 != INFINITY && (m.x >= 0 || m.z > 0);
+            bool h1 = e1 != INFINITY && (m.y >= 0 || m.w > 0);
+            if (h0 && h1) {
+                bool first0 = e0 <= e1;
+                if (w.sp < kStackSize) w.stack[w.sp++] = first0 ? c1 : c0;
+                w.node = first0 ? c0 : c1;
+            } else if (h0) {
+                w.node = c0;
+            } else if (h1) {
+                w.node = c1;
+            } else {
+                w.node = ww_pop(w);
             }
-            if (__ballot_sync(0xffffffffu, node >= 0 && leaf == kNoLeaf) == 0) break;
+            if (w.node < 0 && w.node != kDone && w.leaf == kNoLeaf) {
+                w.leaf = w.node;
+                w.node = ww_pop(w);
+            }
         }
-        // parked leaves (and leaves popped right after them)
-        while (leaf != kNoLeaf) {
-            int code = ~leaf;
-            int first = code >> 2, cnt = (code & 3) + 1;
-            for (int k = first; k < first + cnt; ++k) {
-                const float4* T = s.tris + 3 * (int64_t)k;
-                float4 p0 = __ldg(T), p1 = __ldg(T + 1), p2 = __ldg(T + 2);
-                if (ANY && !(__float_as_int(p1.w) & 1)) continue;
-                float t = tri_hit(r, p0, p1, p2);
-                if (t < 0.0f) continue;
-                int orig = __float_as_int(p0.w);
-                if (ANY) {
-                    h.t = t;
-                    h.orig = orig;
-                    h.k = k;
-                    break;
-                }
-                if (t < h.t || (t == h.t && orig < h.orig)) {
-                    h.t = t;
-                    h.orig = orig;
-                    h.k = k;
-                }
-            }
-            if (ANY && h.orig >= 0) {
-                node = kDone;
-                leaf = kNoLeaf;
+        if (__ballot_sync(0xffffffffu, w.node >= 0 && w.leaf == kNoLeaf) == 0) break;
+    }
+    while (w.leaf != kNoLeaf) {
+        int code = ~w.leaf;
+        int first = code >> 2, cnt = (code & 3) + 1;
+        for (int k = first; k < first + cnt; ++k) {
+            const float4* T = s.tris + 3 * (int64_t)k;
+            float4 p0 = __ldg(T), p1 = __ldg(T + 1), p2 = __ldg(T + 2);
+            if (ANY && !(__float_as_int(p1.w) & 1)) continue;
+            float t = tri_hit(r, p0, p1, p2);
+            if (t < 0.0f) continue;
+            int orig = __float_as_int(p0.w);
+            if (ANY) {
+                w.h.t = t;
+                w.h.orig = orig;
+                w.h.k = k;
                 break;
             }
-            leaf = kNoLeaf;
-            if (node < 0 && node != kDone) {
-                leaf = node;
-                node = sp > 0 ? stack[--sp] : kDone;
+            if (t < w.h.t || (t == w.h.t && orig < w.h.orig)) {
+                w.h.t = t;
+                w.h.orig = orig;
+                w.h.k = k;
             }
         }
-        if (__ballot_sync(0xffffffffu, node != kDone) == 0) break;
+        if (ANY && w.h.orig >= 0) {
+            w.node = kDone;
+            w.leaf = kNoLeaf;
+            break;
+        }
+        w.leaf = kNoLeaf;
+        if (w.node < 0 && w.node != kDone) {
+            w.leaf = w.node;
+            w.node = ww_pop(w);
+        }
     }
-    return h;
+}
+
+template <bool ANY>
+__device__ __forceinline__ Hit traverse_ww(const DevScene& s, const RayPre& r, bool valid) {
+    WwLane w;
+    ww_start(s, w, valid);
+    do {
+        ww_round<ANY>(s, r, w);
+    } while (__ballot_sync(0xffffffffu, w.node != kDone) != 0);
+    return w.h;
 }
 
 }  // namespace ddgi
