@@ -336,7 +336,7 @@ def run_gpu(args):
                          f"query points "
                          f"({t_q:.2f} s), extrapolated to {n_act_cpu} active probes (oracle's own "
                          f"estimate) + {n_pix} pixels"}
-    launches_per_step = 9   # frame setup, 2 list builds, classify, 3 trace passes, blend, query
+    launches_per_step = 10  # frame directions + weights, 2 list builds, classify, 3 trace passes, blend, query
     line = {
         "metric": METRIC, "value": value, "unit": "Grays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",

@@ -133,12 +133,14 @@ struct ddgi_volume_s {
     uint32_t* status = nullptr;
     float4* records = nullptr;     // [P * R]
     float4* dirs = nullptr;        // [R]
+    double* dirs64 = nullptr;      // [R][3] the same in double precision (weights)
     float* w_irr = nullptr;        // [irr_n^2][R]
     float* inv_s_irr = nullptr;
     float* w_dist = nullptr;       // [dist_n^2][R]
     float* inv_s_dist = nullptr;
     unsigned long long* stats = nullptr;   // [8] trace work counters
     int32_t* shadow_list = nullptr;        // [P * R] rays needing a shadow ray
+    int32_t* hit_list = nullptr;           // [P * R] rays with a front hit to shade
     int32_t* shadow_count = nullptr;
     int32_t* perm = nullptr;               // [R] ray order within a probe's warps
     std::vector<void*> snap_irr, snap_dist;   // differentiable forward: atlas after each frame
@@ -355,9 +357,9 @@ static ddgi_status check_desc(const ddgi_volume_desc* d) {
 void ddgi_volume_destroy(ddgi_volume v) {
     if (!v) return;
     cudaFree(v->states); cudaFree(v->irr); cudaFree(v->dist); cudaFree(v->lists); cudaFree(v->counts);
-    cudaFree(v->status); cudaFree(v->records); cudaFree(v->dirs); cudaFree(v->w_irr);
+    cudaFree(v->status); cudaFree(v->records); cudaFree(v->dirs); cudaFree(v->dirs64); cudaFree(v->w_irr);
     cudaFree(v->inv_s_irr); cudaFree(v->w_dist); cudaFree(v->inv_s_dist); cudaFree(v->stats);
-    cudaFree(v->shadow_list); cudaFree(v->shadow_count); cudaFree(v->perm);
+    cudaFree(v->shadow_list); cudaFree(v->hit_list); cudaFree(v->shadow_count); cudaFree(v->perm);
     for (void* p : v->snap_irr) cudaFree(p);
     for (void* p : v->snap_dist) cudaFree(p);
     cudaFree(v->g_irr); cudaFree(v->g_prev);
@@ -400,12 +402,14 @@ ddgi_status ddgi_volume_create(const ddgi_volume_desc* desc, ddgi_volume* out) {
     A((void**)&v->status, sizeof(uint32_t));
     A((void**)&v->records, sizeof(float4) * (size_t)v->P * v->R);
     A((void**)&v->dirs, sizeof(float4) * v->R);
+    A((void**)&v->dirs64, sizeof(double) * 3 * v->R);
     A((void**)&v->w_irr, sizeof(float) * desc->irr_n * desc->irr_n * (size_t)v->R);
     A((void**)&v->inv_s_irr, sizeof(float) * desc->irr_n * desc->irr_n);
     A((void**)&v->w_dist, sizeof(float) * desc->dist_n * desc->dist_n * (size_t)v->R);
     A((void**)&v->inv_s_dist, sizeof(float) * desc->dist_n * desc->dist_n);
     A((void**)&v->stats, sizeof(unsigned long long) * 8);
     A((void**)&v->shadow_list, sizeof(int32_t) * (size_t)v->P * v->R);
+    A((void**)&v->hit_list, sizeof(int32_t) * (size_t)v->P * v->R);
     A((void**)&v->shadow_count, sizeof(int32_t) * 4);
     A((void**)&v->perm, sizeof(int32_t) * v->R);
     if (e == cudaSuccess) {
@@ -509,7 +513,7 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
     FrameRot rot = frame_rotation(d.seed, params->frame);
     {
         StageTimer tm(v, 4, st);
-        DDGI_CK(launch_frame_setup(rot, v->R, d.irr_n, d.dist_n, d.dist_cos_power, v->dirs, v->w_irr,
+        DDGI_CK(launch_frame_setup(rot, v->R, d.irr_n, d.dist_n, d.dist_cos_power, v->dirs, v->dirs64, v->w_irr,
                                    v->inv_s_irr, v->w_dist, v->inv_s_dist, st));
         if (tensor)
             DDGI_CK(launch_pack_weights(v->w_irr, v->w_dist, v->R, d.irr_n, d.dist_n,
@@ -532,7 +536,7 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
     {
         StageTimer tm(v, 2, st);
         DDGI_CK(launch_trace_wavefront(s->dev, view, make_lights(lights), v->dirs, v->R, v->perm, v->lists + v->P,
-                                       v->counts + 1, v->records, v->shadow_list, v->shadow_count, sms * 8,
+                                       v->counts + 1, v->records, v->shadow_list, v->hit_list, v->shadow_count, sms * 8,
                                        st));
     }
     BlendParams bp{};
@@ -720,9 +724,11 @@ struct ddgi_cascade_s {
     uint32_t* status = nullptr;
     float4* records = nullptr;
     int32_t* shadow_list = nullptr;
+    int32_t* hit_list = nullptr;
     int32_t* shadow_count = nullptr;
     int32_t* perm = nullptr;
     float4* dirs = nullptr;
+    double* dirs64 = nullptr;
     float *w_irr = nullptr, *inv_s_irr = nullptr, *w_dist = nullptr, *inv_s_dist = nullptr;
     uint8_t *pack_irr = nullptr, *pack_dist = nullptr;
     float *inv_irr_r = nullptr, *inv_dist_r = nullptr;
@@ -743,7 +749,9 @@ namespace {
 void cascade_free(ddgi_cascade_s* c) {
     for (int k = 0; k < c->n; ++k) { cudaFree(c->states[k]); cudaFree(c->irr[k]); cudaFree(c->dist[k]); }
     cudaFree(c->lists); cudaFree(c->counts); cudaFree(c->status); cudaFree(c->records);
-    cudaFree(c->shadow_list); cudaFree(c->shadow_count); cudaFree(c->perm); cudaFree(c->dirs); cudaFree(c->w_irr);
+    cudaFree(c->shadow_list); cudaFree(c->hit_list); cudaFree(c->shadow_count); cudaFree(c->perm); cudaFree(c->dirs);
+    cudaFree(c->dirs64);
+    cudaFree(c->w_irr);
     cudaFree(c->inv_s_irr); cudaFree(c->w_dist); cudaFree(c->inv_s_dist); cudaFree(c->pack_irr);
     cudaFree(c->pack_dist); cudaFree(c->inv_irr_r); cudaFree(c->inv_dist_r); cudaFree(c->d_params);
     for (int s = 0; s < 2; ++s) {
@@ -785,7 +793,10 @@ VolView cascade_view(const ddgi_cascade_s* c, int k, const float cam[3]) {
     w.spacing = make_float3(d.spacing[0], d.spacing[1], d.spacing[2]);
     w.inv_spacing = make_float3(1.0f / d.spacing[0], 1.0f / d.spacing[1], 1.0f / d.spacing[2]);
     w.counts = make_int3(d.counts[0], d.counts[1], d.counts[2]);
-    w.shift = make_int3(c->shift[k][0], c->shift[k][1], c->shift[k][2]);
+    // reduced to [0, count): the device indexes with one conditional add / subtract
+    w.shift = make_int3(((c->shift[k][0] % d.counts[0]) + d.counts[0]) % d.counts[0],
+                        ((c->shift[k][1] % d.counts[1]) + d.counts[1]) % d.counts[1],
+                        ((c->shift[k][2] % d.counts[2]) + d.counts[2]) % d.counts[2]);
     w.min_spacing = std::fmin(d.spacing[0], std::fmin(d.spacing[1], d.spacing[2]));
     w.bias = d.self_shadow_bias;
     w.gamma = d.gamma;
@@ -828,7 +839,7 @@ ddgi_status cascade_enqueue(ddgi_cascade_s* c, const DevScene& sc, const Lights&
     vs.n = c->n;
     DDGI_CK(cudaMemcpyAsync(c->d_params, c->h_params[slot], sizeof(FrameParams), cudaMemcpyHostToDevice, st));
     DDGI_CK(launch_reset_planes(vs, c->d_params->planes, &c->d_params->n_planes, kMaxPlanes, st));
-    DDGI_CK(launch_frame_setup_dev(&c->d_params->rot, c->R, d0.irr_n, d0.dist_n, d0.dist_cos_power, c->dirs,
+    DDGI_CK(launch_frame_setup_dev(&c->d_params->rot, c->R, d0.irr_n, d0.dist_n, d0.dist_cos_power, c->dirs, c->dirs64,
                                    c->w_irr, c->inv_s_irr, c->w_dist, c->inv_s_dist, st));
     if (tensor)
         DDGI_CK(launch_pack_weights(c->w_irr, c->w_dist, c->R, d0.irr_n, d0.dist_n, precision == DDGI_BLEND_BF16,
@@ -838,7 +849,8 @@ ddgi_status cascade_enqueue(ddgi_cascade_s* c, const DevScene& sc, const Lights&
     DDGI_CK(launch_classify_multi(sc, vs, c->dirs, c->R, c->perm, c->lists, c->counts + 0, sms * 8, st));
     DDGI_CK(launch_build_list_multi(vs, (int)c->total, 1, c->lists + c->total, c->counts + 1, st));
     DDGI_CK(launch_trace_wavefront_multi(sc, vs, L, c->dirs, c->R, c->perm, c->lists + c->total, c->counts + 1,
-                                         c->records, c->shadow_list, c->shadow_count, sms * c->trace_mult, st));
+                                         c->records, c->shadow_list, c->hit_list, c->shadow_count, sms * c->trace_mult,
+                                         st));
     if (tensor)
         DDGI_CK(launch_blend_tc_set(vs, true, bp, precision == DDGI_BLEND_BF16, c->pack_irr, c->pack_dist,
                                     c->inv_irr_r, c->inv_dist_r, c->records, c->lists + c->total, c->counts + 1,
@@ -907,8 +919,10 @@ ddgi_status ddgi_cascade_create(const ddgi_volume_desc* descs, int32_t n, ddgi_c
     A((void**)&c->status, sizeof(uint32_t));
     A((void**)&c->records, sizeof(float4) * (size_t)c->total * c->R);
     A((void**)&c->shadow_list, sizeof(int32_t) * (size_t)c->total * c->R);
+    A((void**)&c->hit_list, sizeof(int32_t) * (size_t)c->total * c->R);
     A((void**)&c->shadow_count, sizeof(int32_t) * 4);
     A((void**)&c->dirs, sizeof(float4) * c->R);
+    A((void**)&c->dirs64, sizeof(double) * 3 * c->R);
     A((void**)&c->perm, sizeof(int32_t) * c->R);
     if (e == cudaSuccess) {
         std::vector<int32_t> perm = ray_order_morton(c->R);
@@ -1288,7 +1302,7 @@ ddgi_status ddgi_diff_backward(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
     for (int f = n_frames - 1; f >= 0; --f) {
         DDGI_CK(launch_border_fold(g, (int)v->P, d.irr_n, st));
         FrameRot rot = frame_rotation(d.seed, first_frame + f);
-        DDGI_CK(launch_frame_setup(rot, v->R, d.irr_n, d.dist_n, d.dist_cos_power, v->dirs, v->w_irr, v->inv_s_irr,
+        DDGI_CK(launch_frame_setup(rot, v->R, d.irr_n, d.dist_n, d.dist_cos_power, v->dirs, v->dirs64, v->w_irr, v->inv_s_irr,
                                    v->w_dist, v->inv_s_dist, st));
         DDGI_CK(launch_blend_adjoint(snap_view(f + 1), v->w_irr, v->inv_s_irr, g, (int)v->P, v->R, v->records, st));
         DDGI_CK(cudaMemsetAsync(gp, 0, gbytes, st));

@@ -43,7 +43,7 @@ struct VolView {
     float3 spacing;
     float3 inv_spacing;
     int3   counts;
-    int3   shift;
+    int3   shift;           // circular window shift, each component in [0, count)
     float  min_spacing;
     float  bias;            // self-shadow bias B
     float  gamma;
@@ -114,11 +114,12 @@ FrameRot frame_rotation(uint64_t seed, int64_t frame);
 // ---------------------------------------------------------------------------
 // Kernel launchers (k_*.cu)
 // ---------------------------------------------------------------------------
+// Frame ray pattern and texel weights; dirs64 is [R][3] double scratch.
 cudaError_t launch_frame_setup(const FrameRot& rot, int R, int irr_n, int dist_n, float cos_power,
-                               float4* dirs, float* w_irr, float* inv_s_irr, float* w_dist,
+                               float4* dirs, double* dirs64, float* w_irr, float* inv_s_irr, float* w_dist,
                                float* inv_s_dist, cudaStream_t st);
 cudaError_t launch_frame_setup_dev(const FrameRot* rot_dev, int R, int irr_n, int dist_n, float cos_power,
-                                   float4* dirs, float* w_irr, float* inv_s_irr, float* w_dist,
+                                   float4* dirs, double* dirs64, float* w_irr, float* inv_s_irr, float* w_dist,
                                    float* inv_s_dist, cudaStream_t st);
 cudaError_t launch_build_list(const uint8_t* states, int P, int which, int32_t* list,
                               int32_t* count, cudaStream_t st);
@@ -137,17 +138,19 @@ cudaError_t launch_classify_multi(const DevScene& s, const VolSet& vs, const flo
 cudaError_t launch_trace_shade(const DevScene& s, const VolView& v, const Lights& L,
                                const float4* dirs, int R, const int32_t* active,
                                const int32_t* count, float4* records, int grid, cudaStream_t st);
-// Wavefront trace: persistent primary pass (closest hits, shadow-ray list),
-// persistent shadow pass, then shading.  shadow_count is 4 int32 of device
-// scratch, 8-byte aligned (shadow-ray count, 64-bit work counter).
+// Wavefront trace: persistent primary pass (closest hits; final records of
+// misses and back faces; lists of shadow rays and of front hits), persistent
+// shadow pass, then shading of the front hits.  shadow_list and hit_list
+// hold one int32 per ray (active probes x R); shadow_count is 4 int32 of
+// device scratch, 8-byte aligned (shadow rays, front hits, 64-bit work counter).
 cudaError_t launch_trace_wavefront(const DevScene& s, const VolView& v, const Lights& L, const float4* dirs,
                                    int R, const int32_t* perm, const int32_t* active, const int32_t* count,
-                                   float4* records, int32_t* shadow_list, int32_t* shadow_count, int grid,
-                                   cudaStream_t st);
+                                   float4* records, int32_t* shadow_list, int32_t* hit_list, int32_t* shadow_count,
+                                   int grid, cudaStream_t st);
 cudaError_t launch_trace_wavefront_multi(const DevScene& s, const VolSet& vs, const Lights& L,
                                          const float4* dirs, int R, const int32_t* perm, const int32_t* active,
                                          const int32_t* count, float4* records, int32_t* shadow_list,
-                                         int32_t* shadow_count, int grid, cudaStream_t st);
+                                         int32_t* hit_list, int32_t* shadow_count, int grid, cudaStream_t st);
 // Morton order of the octahedral positions of the unrotated spherical-
 // Fibonacci directions (host; a rotation keeps neighbouring directions together)
 std::vector<int32_t> ray_order_morton(int R);

@@ -1,7 +1,8 @@
 // Per-frame ray pattern and the probe blend (Sec. 2.3 Eq. 1, Sec. 4.2, 4.3, 7.1).
 //
-// k_frame_setup computes, once per frame and shared by every probe, the ray
-// directions w_i = R_t sf(i, R) and the texel weight matrices
+// k_frame_dirs and k_frame_weights compute, once per frame and shared by
+// every probe, the ray directions w_i = R_t sf(i, R) and the texel weight
+// matrices
 //   W_irr[t][i]  = max(0, n_t . w_i)              (cosine weight)
 //   W_dist[t][i] = max(0, n_t . w_i)^p            (power-cosine weight)
 // with 1 / sum_i W per texel, in double precision, rounded once to float.
@@ -57,37 +58,56 @@ __device__ void texel_dir(int t, int n, double v[3]) {
 
 }  // namespace
 
-// grid: irr_n^2 + dist_n^2 + 1 blocks; block b < irr_n^2 handles irradiance
-// texel b, the next dist_n^2 blocks distance texels, the last one the rays.
+// The frame's ray directions, once per ray: w_i = R_t sf(i, R) in double
+// precision, rounded to float for the trace and kept in double for the
+// weights.  ROT_DEV: the rotation is read from device memory (per-frame
+// parameters written before a captured graph replays).
 template <bool ROT_DEV>
-__global__ void __launch_bounds__(256) k_frame_setup(FrameRot rot_arg, const FrameRot* rot_dev, int R, int irr_n,
-                                                     int dist_n, double cos_power, float4* dirs, float* w_irr,
-                                                     float* inv_s_irr, float* w_dist,
-                                                     float* inv_s_dist) {
-    __shared__ double red[256];
-    // ROT_DEV: the rotation is read from device memory (per-frame parameters
-    // written before a captured graph replays)
+__global__ void __launch_bounds__(64) k_frame_dirs(FrameRot rot_arg, const FrameRot* rot_dev, int R, float4* dirs,
+                                                   double* dirs64) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R) return;
     const FrameRot rot = ROT_DEV ? *rot_dev : rot_arg;
-    int b = blockIdx.x;
-    int ti = irr_n * irr_n, td = dist_n * dist_n;
-    if (b == ti + td) {
-        for (int i = threadIdx.x; i < R; i += blockDim.x) {
-            double w[3];
-            frame_dir(rot, i, R, w);
-            dirs[i] = make_float4((float)w[0], (float)w[1], (float)w[2], 0.0f);
+    double w[3];
+    frame_dir(rot, i, R, w);
+    dirs[i] = make_float4((float)w[0], (float)w[1], (float)w[2], 0.0f);
+    dirs64[3 * i] = w[0];
+    dirs64[3 * i + 1] = w[1];
+    dirs64[3 * i + 2] = w[2];
+}
+
+// c^p for c >= 0: repeated squaring when p is a small whole number (the
+// usual power-cosine exponent), pow otherwise.
+__device__ double cos_pow(double c, double p) {
+    if (p >= 0.0 && p <= 1024.0 && p == floor(p)) {
+        unsigned e = (unsigned)p;
+        double r = 1.0, b = c;
+        while (e) {
+            if (e & 1u) r *= b;
+            b *= b;
+            e >>= 1;
         }
-        return;
+        return r;
     }
-    bool is_irr = b < ti;
-    int t = is_irr ? b : b - ti;
+    return pow(c, p);
+}
+
+// grid: irr_n^2 + dist_n^2 blocks; block b < irr_n^2 handles irradiance
+// texel b, the others distance texels; rays strided over the block.
+__global__ void __launch_bounds__(256) k_frame_weights(int R, int irr_n, int dist_n, double cos_power,
+                                                       const double* __restrict__ dirs64, float* w_irr,
+                                                       float* inv_s_irr, float* w_dist, float* inv_s_dist) {
+    __shared__ double red[256];
+    const int b = blockIdx.x;
+    const int ti = irr_n * irr_n;
+    const bool is_irr = b < ti;
+    const int t = is_irr ? b : b - ti;
     double nt[3];
     texel_dir(t, is_irr ? irr_n : dist_n, nt);
     double acc = 0.0;
     for (int i = threadIdx.x; i < R; i += blockDim.x) {
-        double w[3];
-        frame_dir(rot, i, R, w);
-        double c = fmax(0.0, nt[0] * w[0] + nt[1] * w[1] + nt[2] * w[2]);
-        double wt = is_irr ? c : pow(c, cos_power);
+        double c = fmax(0.0, nt[0] * dirs64[3 * i] + nt[1] * dirs64[3 * i + 1] + nt[2] * dirs64[3 * i + 2]);
+        double wt = is_irr ? c : cos_pow(c, cos_power);
         acc += wt;
         if (is_irr) w_irr[(int64_t)t * R + i] = (float)wt;
         else w_dist[(int64_t)t * R + i] = (float)wt;
@@ -441,20 +461,24 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, B
 }
 
 cudaError_t launch_frame_setup(const FrameRot& rot, int R, int irr_n, int dist_n, float cos_power,
-                               float4* dirs, float* w_irr, float* inv_s_irr, float* w_dist,
+                               float4* dirs, double* dirs64, float* w_irr, float* inv_s_irr, float* w_dist,
                                float* inv_s_dist, cudaStream_t st) {
-    int blocks = irr_n * irr_n + dist_n * dist_n + 1;
-    k_frame_setup<false><<<blocks, 256, 0, st>>>(rot, nullptr, R, irr_n, dist_n, (double)cos_power, dirs, w_irr,
-                                                 inv_s_irr, w_dist, inv_s_dist);
+    k_frame_dirs<false><<<(R + 63) / 64, 64, 0, st>>>(rot, nullptr, R, dirs, dirs64);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_frame_weights<<<irr_n * irr_n + dist_n * dist_n, 256, 0, st>>>(R, irr_n, dist_n, (double)cos_power, dirs64,
+                                                                      w_irr, inv_s_irr, w_dist, inv_s_dist);
     return cudaGetLastError();
 }
 
 cudaError_t launch_frame_setup_dev(const FrameRot* rot_dev, int R, int irr_n, int dist_n, float cos_power,
-                                   float4* dirs, float* w_irr, float* inv_s_irr, float* w_dist,
+                                   float4* dirs, double* dirs64, float* w_irr, float* inv_s_irr, float* w_dist,
                                    float* inv_s_dist, cudaStream_t st) {
-    int blocks = irr_n * irr_n + dist_n * dist_n + 1;
-    k_frame_setup<true><<<blocks, 256, 0, st>>>(FrameRot{}, rot_dev, R, irr_n, dist_n, (double)cos_power, dirs,
-                                                w_irr, inv_s_irr, w_dist, inv_s_dist);
+    k_frame_dirs<true><<<(R + 63) / 64, 64, 0, st>>>(FrameRot{}, rot_dev, R, dirs, dirs64);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_frame_weights<<<irr_n * irr_n + dist_n * dist_n, 256, 0, st>>>(R, irr_n, dist_n, (double)cos_power, dirs64,
+                                                                      w_irr, inv_s_irr, w_dist, inv_s_dist);
     return cudaGetLastError();
 }
 

@@ -189,12 +189,14 @@ __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Li
                                                        const int32_t* __restrict__ count,
                                                        float4* __restrict__ hits,
                                                        int32_t* __restrict__ shadow_list,
+                                                       int32_t* __restrict__ hit_list,
                                                        int32_t* shadow_count,
                                                        unsigned long long* next) {
     const int lane = threadIdx.x & 31;
     const int64_t total = (int64_t)(*count) * R;
     const float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
     int64_t rec = -1;   // record index of the lane's ray, -1 when idle
+    int entry = 0;      // its probe's list entry
     bool exhausted = false;
     float3 d = f3(0.0f, 0.0f, 1.0f);
     RayPre r = ray_pre(f3(0.0f, 0.0f, 0.0f), d);
@@ -209,8 +211,8 @@ __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Li
             int j = (int)(item - (int64_t)slot * R);
             int i = perm ? __ldg(perm + j) : j;
             rec = (int64_t)slot * R + i;
-            int e = __ldg(active + slot);
-            float3 o = probe_pos_phys(vol_of<MULTI>(vs, e >> kEntryShift), e & kEntryMask);
+            entry = __ldg(active + slot);
+            float3 o = probe_pos_phys(vol_of<MULTI>(vs, entry >> kEntryShift), entry & kEntryMask);
             float4 d4 = __ldg(dirs + i);
             d = f3(d4.x, d4.y, d4.z);
             r = ray_pre(o, d);
@@ -218,19 +220,33 @@ __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Li
         }
         if (__ballot_sync(0xffffffffu, rec >= 0) == 0) break;
         ww_round<false>(s, r, w);
-        bool need = false;
+        bool need = false, front = false;
         int64_t done = -1;
         if (rec >= 0 && w.node == kDone) {
+            // misses and back faces get their final record here; front hits
+            // keep (t, triangle) for the shading pass
             const Hit& h = w.h;
-            if (h.orig >= 0 && L.sun_on) {
+            const float t_max = vol_of<MULTI>(vs, entry >> kEntryShift).t_max;
+            float4 out;
+            if (h.orig < 0) {
+                float c = dot(d, L.sky_up);
+                out = make_float4(L.sky_a.x + L.sky_b.x * c, L.sky_a.y + L.sky_b.y * c, L.sky_a.z + L.sky_b.z * c,
+                                  t_max);
+            } else {
                 float3 ng;
                 hit_frame(s, h.k, ng);
-                if (!(dot(d, ng) > 0.0f)) {
-                    float3 n = (1.0f / length(ng)) * ng;
-                    need = dot(n, tol) > 0.0f;
+                if (dot(d, ng) > 0.0f) {
+                    out = make_float4(0.0f, 0.0f, 0.0f, fminf(0.2f * h.t, t_max));
+                } else {
+                    front = true;
+                    if (L.sun_on) {
+                        float3 n = (1.0f / length(ng)) * ng;
+                        need = dot(n, tol) > 0.0f;
+                    }
+                    out = make_float4(h.t, __int_as_float(h.k), 0.0f, 0.0f);
                 }
             }
-            hits[rec] = make_float4(h.t, __int_as_float(h.orig >= 0 ? h.k : -1), 0.0f, 0.0f);
+            hits[rec] = out;
             done = rec;
             rec = -1;
         }
@@ -241,6 +257,14 @@ __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Li
             if (lane == leader) off = atomicAdd(shadow_count, __popc(mask));
             off = __shfl_sync(0xffffffffu, off, leader);
             if (need) shadow_list[off + __popc(mask & ((1u << lane) - 1u))] = (int32_t)done;
+        }
+        mask = __ballot_sync(0xffffffffu, front);
+        if (mask) {
+            int leader = __ffs(mask) - 1;
+            int off = 0;
+            if (lane == leader) off = atomicAdd(shadow_count + 1, __popc(mask));
+            off = __shfl_sync(0xffffffffu, off, leader);
+            if (front) hit_list[off + __popc(mask & ((1u << lane) - 1u))] = (int32_t)done;
         }
     }
 }
@@ -288,61 +312,49 @@ __global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolSet vs, Lig
     }
 }
 
+// Shading of the front hits (Sec. 2.3 ray radiance, multi-bounce through the
+// previous frame's probes), one thread per entry of the compacted hit list.
 template <bool MULTI>
-__global__ void __launch_bounds__(256) k_shade(DevScene s, VolSet vs, Lights L, const float4* __restrict__ dirs,
-                                               int R, const int32_t* __restrict__ perm,
-                                               const int32_t* __restrict__ active,
-                                               const int32_t* __restrict__ count, float4* records) {
-    const int64_t total = (int64_t)(*count) * R;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += stride) {
-        int slot = (int)(w / R);
-        int j = (int)(w - (int64_t)slot * R);
-        int i = perm ? __ldg(perm + j) : j;
-        const int64_t idx = (int64_t)slot * R + i;
+__global__ void __launch_bounds__(256, 4) k_shade(DevScene s, VolSet vs, Lights L, const float4* __restrict__ dirs,
+                                               int R, const int32_t* __restrict__ active,
+                                               const int32_t* __restrict__ hit_list,
+                                               const int32_t* __restrict__ hit_count, float4* records) {
+    const int n_hits = *hit_count;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_hits; q += gridDim.x * blockDim.x) {
+        const int64_t idx = __ldg(hit_list + q);
+        const int slot = (int)(idx / R);
+        const int i = (int)(idx - (int64_t)slot * R);
         float4 d4 = __ldg(dirs + i);
         float3 d = f3(d4.x, d4.y, d4.z);
         float4 hr = records[idx];
         int k = __float_as_int(hr.y);
         const int e = __ldg(active + slot);
         const VolView& v = vol_of<MULTI>(vs, e >> kEntryShift);
-        float4 rec;
-        if (k < 0) {
-            float c = dot(d, L.sky_up);
-            rec = make_float4(L.sky_a.x + L.sky_b.x * c, L.sky_a.y + L.sky_b.y * c,
-                              L.sky_a.z + L.sky_b.z * c, v.t_max);
-        } else {
-            float3 ng;
-            hit_frame(s, k, ng);
-            float t = hr.x;
-            if (dot(d, ng) > 0.0f) {
-                rec = make_float4(0.0f, 0.0f, 0.0f, fminf(0.2f * t, v.t_max));
-            } else {
-                float3 o = probe_pos_phys(v, e & kEntryMask);
-                float3 n = (1.0f / length(ng)) * ng;
-                float3 x = o + t * d;
-                int orig = __float_as_int(__ldg(&s.tris[3 * (int64_t)k].w));
-                int2 at = __ldg(s.attr + orig);
-                float4 rho = __ldg(s.albedo + at.x);
-                float3 Le = f3(0.0f, 0.0f, 0.0f);
-                if (at.y >= 0) {
-                    float4 e = __ldg(s.emit + at.y);
-                    Le = f3(e.x, e.y, e.z);
-                }
-                float3 direct = f3(0.0f, 0.0f, 0.0f);
-                if (hr.z != 0.0f) {
-                    float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
-                    float kk = dot(n, tol) * 0.318309886183790672f;   // 1/pi
-                    direct = f3(L.sun_irr.x * kk, L.sun_irr.y * kk, L.sun_irr.z * kk);
-                }
-                // the previous frame's probes at the hit: the volume itself, or the whole cascade
-                float3 M = MULTI ? cascade_M(vs.table, vs.n, x, n, f3(-d.x, -d.y, -d.z))
-                                 : query_M(v, x, n, f3(-d.x, -d.y, -d.z));
-                rec = make_float4(Le.x + rho.x * (direct.x + M.x), Le.y + rho.y * (direct.y + M.y),
-                                  Le.z + rho.z * (direct.z + M.z), fminf(t, v.t_max));
-            }
+        float3 ng;
+        hit_frame(s, k, ng);
+        float t = hr.x;
+        float3 o = probe_pos_phys(v, e & kEntryMask);
+        float3 n = (1.0f / length(ng)) * ng;
+        float3 x = o + t * d;
+        int orig = __float_as_int(__ldg(&s.tris[3 * (int64_t)k].w));
+        int2 at = __ldg(s.attr + orig);
+        float4 rho = __ldg(s.albedo + at.x);
+        float3 Le = f3(0.0f, 0.0f, 0.0f);
+        if (at.y >= 0) {
+            float4 em = __ldg(s.emit + at.y);
+            Le = f3(em.x, em.y, em.z);
         }
-        records[idx] = rec;
+        float3 direct = f3(0.0f, 0.0f, 0.0f);
+        if (hr.z != 0.0f) {
+            float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
+            float kk = dot(n, tol) * 0.318309886183790672f;   // 1/pi
+            direct = f3(L.sun_irr.x * kk, L.sun_irr.y * kk, L.sun_irr.z * kk);
+        }
+        // the previous frame's probes at the hit: the volume itself, or the whole cascade
+        float3 M = MULTI ? cascade_M(vs.table, vs.n, x, n, f3(-d.x, -d.y, -d.z))
+                         : query_M(v, x, n, f3(-d.x, -d.y, -d.z));
+        records[idx] = make_float4(Le.x + rho.x * (direct.x + M.x), Le.y + rho.y * (direct.y + M.y),
+                                   Le.z + rho.z * (direct.z + M.z), fminf(t, v.t_max));
     }
 }
 
@@ -419,38 +431,38 @@ cudaError_t launch_trace_shade(const DevScene& s, const VolView& v, const Lights
 template <bool MULTI>
 static cudaError_t trace_wavefront(const DevScene& s, const VolSet& vs, const Lights& L, const float4* dirs, int R,
                                    const int32_t* perm, const int32_t* active, const int32_t* count,
-                                   float4* records, int32_t* shadow_list, int32_t* shadow_count, int grid,
-                                   cudaStream_t st) {
-    // shadow_count[0]: shadow rays; shadow_count[2..3]: the 64-bit work counter
-    // of the persistent passes, zeroed before each
+                                   float4* records, int32_t* shadow_list, int32_t* hit_list, int32_t* shadow_count,
+                                   int grid, cudaStream_t st) {
+    // shadow_count[0]: shadow rays; [1]: front hits; [2..3]: the 64-bit work
+    // counter of the persistent passes, zeroed before each
     unsigned long long* next = reinterpret_cast<unsigned long long*>(shadow_count + 2);
     cudaError_t e = cudaMemsetAsync(shadow_count, 0, 4 * sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     k_trace_primary<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, perm, active, count, records, shadow_list,
-                                                  shadow_count, next);
+                                                  hit_list, shadow_count, next);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
     k_trace_shadow<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, active, records, shadow_list, shadow_count,
                                                  next);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_shade<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, perm, active, count, records);
+    k_shade<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, active, hit_list, shadow_count + 1, records);
     return cudaGetLastError();
 }
 
 cudaError_t launch_trace_wavefront(const DevScene& s, const VolView& v, const Lights& L, const float4* dirs,
                                    int R, const int32_t* perm, const int32_t* active, const int32_t* count,
-                                   float4* records, int32_t* shadow_list, int32_t* shadow_count, int grid,
-                                   cudaStream_t st) {
-    return trace_wavefront<false>(s, single_set(v), L, dirs, R, perm, active, count, records, shadow_list,
+                                   float4* records, int32_t* shadow_list, int32_t* hit_list, int32_t* shadow_count,
+                                   int grid, cudaStream_t st) {
+    return trace_wavefront<false>(s, single_set(v), L, dirs, R, perm, active, count, records, shadow_list, hit_list,
                                   shadow_count, grid, st);
 }
 
 cudaError_t launch_trace_wavefront_multi(const DevScene& s, const VolSet& vs, const Lights& L,
                                          const float4* dirs, int R, const int32_t* perm, const int32_t* active,
                                          const int32_t* count, float4* records, int32_t* shadow_list,
-                                         int32_t* shadow_count, int grid, cudaStream_t st) {
-    return trace_wavefront<true>(s, vs, L, dirs, R, perm, active, count, records, shadow_list, shadow_count, grid,
-                                 st);
+                                         int32_t* hit_list, int32_t* shadow_count, int grid, cudaStream_t st) {
+    return trace_wavefront<true>(s, vs, L, dirs, R, perm, active, count, records, shadow_list, hit_list,
+                                 shadow_count, grid, st);
 }
 
 cudaError_t launch_trace_shade_count(const DevScene& s, const VolView& v, const Lights& L,

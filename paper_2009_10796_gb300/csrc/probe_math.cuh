@@ -34,14 +34,33 @@ __device__ __forceinline__ float2 oct_encode(float3 v) {
     return make_float2(px, py);
 }
 
-// Probe grid addressing: logical (i,j,k) of the window is stored at
-// ((i+shift) mod count, ...); the tracking window moves `shift`.
-__device__ __forceinline__ int wrap(int a, int m) { int r = a % m; return r < 0 ? r + m : r; }
+// The same map with the hardware reciprocal (__fdividef, about 2 ulp) for
+// the per-probe lookups of the query, where IEEE division dominated.
+__device__ __forceinline__ float2 oct_encode_fast(float3 v) {
+    float inv = __fdividef(1.0f, fabsf(v.x) + fabsf(v.y) + fabsf(v.z));
+    float px = v.x * inv, py = v.y * inv;
+    if (v.z < 0.0f) {
+        float qx = (1.0f - fabsf(py)) * sgnnz(px);
+        float qy = (1.0f - fabsf(px)) * sgnnz(py);
+        px = qx;
+        py = qy;
+    }
+    return make_float2(px, py);
+}
 
+// Probe grid addressing: logical (i,j,k) of the window is stored at
+// ((i+shift) mod count, ...); the tracking window moves `shift`, which a
+// VolView holds reduced to [0, count).
+__device__ __forceinline__ int wrap(int a, int m) { int r = a % m; return r < 0 ? r + m : r; }
+// (a + s) mod m and (a - s) mod m for a, s in [0, m)
+__device__ __forceinline__ int wrap_add(int a, int s, int m) { int r = a + s; return r >= m ? r - m : r; }
+__device__ __forceinline__ int wrap_sub(int a, int s, int m) { int r = a - s; return r < 0 ? r + m : r; }
+
+// Logical (i, j, k) inside the grid -> physical probe index.
 __device__ __forceinline__ int probe_phys(const VolView& v, int i, int j, int k) {
-    int a = wrap(i + v.shift.x, v.counts.x);
-    int b = wrap(j + v.shift.y, v.counts.y);
-    int c = wrap(k + v.shift.z, v.counts.z);
+    int a = wrap_add(i, v.shift.x, v.counts.x);
+    int b = wrap_add(j, v.shift.y, v.counts.y);
+    int c = wrap_add(k, v.shift.z, v.counts.z);
     return a + v.counts.x * (b + v.counts.y * c);
 }
 
@@ -54,8 +73,8 @@ __device__ __forceinline__ float3 probe_pos_phys(const VolView& v, int p) {
     int a = p % v.counts.x;
     int b = (p / v.counts.x) % v.counts.y;
     int c = p / (v.counts.x * v.counts.y);
-    return probe_pos_logical(v, wrap(a - v.shift.x, v.counts.x), wrap(b - v.shift.y, v.counts.y),
-                             wrap(c - v.shift.z, v.counts.z));
+    return probe_pos_logical(v, wrap_sub(a, v.shift.x, v.counts.x), wrap_sub(b, v.shift.y, v.counts.y),
+                             wrap_sub(c, v.shift.z, v.counts.z));
 }
 
 __device__ __forceinline__ bool state_active(uint8_t s) {
@@ -183,10 +202,9 @@ __device__ __forceinline__ void store_dist(const VolView& v, int p, int x, int y
     }
 }
 
-__device__ __forceinline__ float3 sample_irr(const VolView& v, int p, float3 dir) {
-    Footprint f = footprint(oct_encode(dir), v.irr_n);
-    float3 a = load_irr(v, p, f.x0, f.y0), b = load_irr(v, p, f.x0 + 1, f.y0);
-    float3 c = load_irr(v, p, f.x0, f.y0 + 1), d = load_irr(v, p, f.x0 + 1, f.y0 + 1);
+// Bilinear samples at a footprint: one storage-format dispatch per sample,
+// then the four taps (rows y0, y0 + 1 of the bordered tile).
+__device__ __forceinline__ float3 bilerp3(const Footprint& f, float3 a, float3 b, float3 c, float3 d) {
     float w00 = (1.0f - f.tx) * (1.0f - f.ty), w10 = f.tx * (1.0f - f.ty);
     float w01 = (1.0f - f.tx) * f.ty, w11 = f.tx * f.ty;
     return f3(w00 * a.x + w10 * b.x + w01 * c.x + w11 * d.x,
@@ -194,14 +212,46 @@ __device__ __forceinline__ float3 sample_irr(const VolView& v, int p, float3 dir
               w00 * a.z + w10 * b.z + w01 * c.z + w11 * d.z);
 }
 
-__device__ __forceinline__ float2 sample_dist(const VolView& v, int p, float3 dir) {
-    Footprint f = footprint(oct_encode(dir), v.dist_n);
-    float2 a = load_dist(v, p, f.x0, f.y0), b = load_dist(v, p, f.x0 + 1, f.y0);
-    float2 c = load_dist(v, p, f.x0, f.y0 + 1), d = load_dist(v, p, f.x0 + 1, f.y0 + 1);
+__device__ __forceinline__ float3 sample_irr_at(const VolView& v, int p, const Footprint& f) {
+    const int row = v.irr_n + 2;
+    const int64_t t = (int64_t)p * v.irr_tile + (int64_t)f.y0 * row + f.x0;
+    if (v.irr_format == DDGI_IRR_FP32) {
+        const float* a = (const float*)v.irr + 3 * t;
+        const float* c = a + 3 * row;
+        return bilerp3(f, f3(__ldg(a), __ldg(a + 1), __ldg(a + 2)), f3(__ldg(a + 3), __ldg(a + 4), __ldg(a + 5)),
+                       f3(__ldg(c), __ldg(c + 1), __ldg(c + 2)), f3(__ldg(c + 3), __ldg(c + 4), __ldg(c + 5)));
+    }
+    return bilerp3(f, load_irr(v, p, f.x0, f.y0), load_irr(v, p, f.x0 + 1, f.y0), load_irr(v, p, f.x0, f.y0 + 1),
+                   load_irr(v, p, f.x0 + 1, f.y0 + 1));
+}
+
+__device__ __forceinline__ float2 sample_dist_at(const VolView& v, int p, const Footprint& f) {
+    const int row = v.dist_n + 2;
+    float2 a, b, c, d;
+    if (v.dist_format == DDGI_DIST_FP32) {
+        const float2* q = (const float2*)v.dist + (int64_t)p * v.dist_tile + (int64_t)f.y0 * row + f.x0;
+        a = __ldg(q);
+        b = __ldg(q + 1);
+        c = __ldg(q + row);
+        d = __ldg(q + row + 1);
+    } else {
+        a = load_dist(v, p, f.x0, f.y0);
+        b = load_dist(v, p, f.x0 + 1, f.y0);
+        c = load_dist(v, p, f.x0, f.y0 + 1);
+        d = load_dist(v, p, f.x0 + 1, f.y0 + 1);
+    }
     float w00 = (1.0f - f.tx) * (1.0f - f.ty), w10 = f.tx * (1.0f - f.ty);
     float w01 = (1.0f - f.tx) * f.ty, w11 = f.tx * f.ty;
     return make_float2(w00 * a.x + w10 * b.x + w01 * c.x + w11 * d.x,
                        w00 * a.y + w10 * b.y + w01 * c.y + w11 * d.y);
+}
+
+__device__ __forceinline__ float3 sample_irr(const VolView& v, int p, float3 dir) {
+    return sample_irr_at(v, p, footprint(oct_encode(dir), v.irr_n));
+}
+
+__device__ __forceinline__ float2 sample_dist(const VolView& v, int p, float3 dir) {
+    return sample_dist_at(v, p, footprint(oct_encode(dir), v.dist_n));
 }
 
 // x^(gamma/2) on the gamma-encoded value; gamma = 5 uses x^2 sqrt(x).
@@ -212,10 +262,22 @@ __device__ __forceinline__ float gamma_decode_half(float e, float half_gamma) {
     return powf(e, half_gamma);
 }
 
+// The same with sqrt(x) as x * rsqrt(x) (hardware reciprocal square root,
+// about 2 ulp), for the query's 8 probes x 3 channels.
+__device__ __forceinline__ float gamma_decode_half_fast(float e, float half_gamma) {
+    e = fmaxf(e, 0.0f);
+    const float sq = e > 0.0f ? e * rsqrtf(e) : 0.0f;
+    if (half_gamma == 2.5f) return e * e * sq;
+    if (half_gamma == 0.5f) return sq;
+    return powf(e, half_gamma);
+}
+
 // Cosine-weighted mean radiance M at x with normal n, the self-shadow bias
 // using w_o (Sec. 4.1 equation), the 8-probe cage (Sec. 2.2): trilinear,
 // backface ((1 + n.w_p)/2)^2 + 0.2, Chebyshev visibility, weight floor
 // 1e-6 * w_t * w_b, gamma decode (Sec. 4.2) normalised before squaring.
+// Per-probe normalisations, the Chebyshev ratio and the square roots of the
+// decode use the hardware reciprocal and reciprocal square root.
 __device__ __forceinline__ float3 query_M(const VolView& v, float3 x, float3 n, float3 wo) {
     float k = 0.75f * v.min_spacing * v.bias;
     float3 xb = f3(x.x + (0.2f * n.x + 0.8f * wo.x) * k, x.y + (0.2f * n.y + 0.8f * wo.y) * k,
@@ -233,6 +295,7 @@ __device__ __forceinline__ float3 query_M(const VolView& v, float3 x, float3 n, 
     }
     float sumw = 0.0f;
     float3 acc = f3(0.0f, 0.0f, 0.0f);
+    const Footprint fn = footprint(oct_encode(n), v.irr_n);   // irradiance lookup direction: n, every probe
 #pragma unroll 1
     for (int c = 0; c < 8; ++c) {
         int o0 = c & 1, o1 = (c >> 1) & 1, o2 = (c >> 2) & 1;
@@ -241,26 +304,28 @@ __device__ __forceinline__ float3 query_M(const VolView& v, float3 x, float3 n, 
         float3 xp = probe_pos_logical(v, base[0] + o0, base[1] + o1, base[2] + o2);
         float wt = (o0 ? fr[0] : 1.0f - fr[0]) * (o1 ? fr[1] : 1.0f - fr[1]) * (o2 ? fr[2] : 1.0f - fr[2]);
         float3 dp = xp - x;
-        float ldp = length(dp);
-        float cw = ldp > 0.0f ? dot(n, dp) / ldp : 1.0f;
+        float dd = dot(dp, dp);
+        float cw = dd > 0.0f ? dot(n, dp) * rsqrtf(dd) : 1.0f;
         float hb = (1.0f + cw) * 0.5f;
         float wb = hb * hb + 0.2f;
         float3 pv = xb - xp;
-        float r = length(pv);
+        float rr = dot(pv, pv);
         float wc = 1.0f;
-        if (r > 0.0f) {
-            float2 mom = sample_dist(v, p, (1.0f / r) * pv);
+        if (rr > 0.0f) {
+            float ir = rsqrtf(rr);
+            float r = rr * ir;
+            float2 mom = sample_dist_at(v, p, footprint(oct_encode_fast(ir * pv), v.dist_n));
             if (r > mom.x) {
                 float var = fmaxf(mom.y - mom.x * mom.x, 0.0f);
                 float dr = r - mom.x;
-                wc = var / (var + dr * dr);
+                wc = __fdividef(var, var + dr * dr);
             }
         }
         float w = wt * wb * fmaxf(wc, 1e-6f);
-        float3 e = sample_irr(v, p, n);
-        acc.x += w * gamma_decode_half(e.x, v.half_gamma);
-        acc.y += w * gamma_decode_half(e.y, v.half_gamma);
-        acc.z += w * gamma_decode_half(e.z, v.half_gamma);
+        float3 e = sample_irr_at(v, p, fn);
+        acc.x += w * gamma_decode_half_fast(e.x, v.half_gamma);
+        acc.y += w * gamma_decode_half_fast(e.y, v.half_gamma);
+        acc.z += w * gamma_decode_half_fast(e.z, v.half_gamma);
         sumw += w;
     }
     if (!(sumw > 0.0f)) return f3(0.0f, 0.0f, 0.0f);
