@@ -96,7 +96,7 @@ int32_t     ddgi_version(void);
  * n_tris is at most DDGI_MAX_TRIS.  Synchronises the device once (upload).
  * Errors: INVALID_ARG on a bad count or an index out of range (nothing
  * allocated), OOM, CUDA. */
-#define DDGI_MAX_TRIS ((int64_t)1 << 28)
+#define DDGI_MAX_TRIS ((int64_t)1 << 27)
 ddgi_status ddgi_scene_create(const float* verts, int64_t n_verts,
                               const int32_t* tris, int64_t n_tris,
                               const int32_t* tri_object, int32_t n_objects,

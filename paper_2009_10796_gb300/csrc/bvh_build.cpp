@@ -14,8 +14,9 @@ namespace ddgi {
 namespace {
 
 constexpr int kBins = 32;
-constexpr int kMaxLeaf = 4;
-constexpr int kMaxSahDepth = 30;   // + log2(2^30 / 4) median levels < 64 stack slots
+constexpr int kMaxLeaf = 4;   // at most kMaxLeafTris
+constexpr int kMaxSahDepth = 30;   // + log2(2^28 / 4) median levels < 64 stack slots
+static_assert(kMaxLeaf <= kMaxLeafTris, "leaf size beyond what the traversal encodes");
 constexpr float kTraversalCost = 1.0f;
 constexpr float kIntersectCost = 1.0f;
 
@@ -194,6 +195,98 @@ struct Builder {
     }
 };
 
+// One binary child: box, reference (node >= 0 or ~first), triangle count.
+struct Kid {
+    float lo[3], hi[3];
+    int32_t ref, cnt;
+    float area() const {
+        float dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+        return 2.0f * (dx * dy + dy * dz + dz * dx);
+    }
+};
+
+void binary_kids(const std::vector<float4>& n2, int32_t i, std::vector<Kid>& out) {
+    int32_t meta[4];
+    std::memcpy(meta, &n2[4 * (size_t)i + 3], sizeof(meta));
+    const float4 z = n2[4 * (size_t)i + 2];
+    for (int slot = 0; slot < 2; ++slot) {
+        if (meta[slot] < 0 && meta[2 + slot] == 0) continue;   // empty slot
+        const float4 xy = n2[4 * (size_t)i + slot];
+        Kid k;
+        k.lo[0] = xy.x; k.hi[0] = xy.y;
+        k.lo[1] = xy.z; k.hi[1] = xy.w;
+        k.lo[2] = slot ? z.z : z.x; k.hi[2] = slot ? z.w : z.y;
+        k.ref = meta[slot];
+        k.cnt = meta[2 + slot];
+        out.push_back(k);
+    }
+}
+
+// Collapse of the binary hierarchy into 4-wide nodes: a node starts from a
+// binary node's two children and repeatedly replaces its internal child of
+// largest surface area by that child's two children until it holds four
+// (two below kWideFullDepth).  Layout, 8 float4 per node: the children's
+// lo_x, hi_x, lo_y, hi_y, lo_z, hi_z (one float4 each, child c in lane c),
+// an int4 of child references, one float4 of padding.  An empty slot has
+// the box lo = hi = (+inf, +inf, +inf), which no ray enters, and reference
+// kRefDone.
+void collapse_wide(const std::vector<float4>& n2, std::vector<float4>& n4, int32_t& max_depth4) {
+    n4.clear();
+    max_depth4 = 0;
+    if (n2.empty()) return;
+    struct Job {
+        int32_t n2, n4, depth;
+    };
+    std::vector<Job> jobs{{0, 0, 1}};
+    n4.resize(8);
+    std::vector<Kid> kids, sub;
+    while (!jobs.empty()) {
+        Job j = jobs.back();
+        jobs.pop_back();
+        max_depth4 = std::max(max_depth4, j.depth);
+        kids.clear();
+        binary_kids(n2, j.n2, kids);
+        const size_t width = j.depth <= kWideFullDepth ? 4 : 2;
+        while (kids.size() < width) {
+            int best = -1;
+            float best_area = -1.0f;
+            for (size_t k = 0; k < kids.size(); ++k)
+                if (kids[k].ref >= 0 && kids[k].area() > best_area) { best_area = kids[k].area(); best = (int)k; }
+            if (best < 0) break;
+            sub.clear();
+            binary_kids(n2, kids[best].ref, sub);
+            kids.erase(kids.begin() + best);
+            kids.insert(kids.end(), sub.begin(), sub.end());
+        }
+        float lo[3][4], hi[3][4];
+        int32_t ref[4];
+        for (int c = 0; c < 4; ++c) {
+            if (c < (int)kids.size()) {
+                const Kid& k = kids[c];
+                for (int a = 0; a < 3; ++a) { lo[a][c] = k.lo[a]; hi[a][c] = k.hi[a]; }
+                if (k.ref >= 0) {
+                    int32_t id = (int32_t)(n4.size() / 8);
+                    n4.resize(n4.size() + 8);
+                    jobs.push_back({k.ref, id, j.depth + 1});
+                    ref[c] = id;
+                } else {
+                    ref[c] = ~(((~k.ref) << kLeafBits) | (k.cnt - 1));
+                }
+            } else {
+                for (int a = 0; a < 3; ++a) { lo[a][c] = INFINITY; hi[a][c] = INFINITY; }
+                ref[c] = kRefDone;
+            }
+        }
+        float4* N = &n4[8 * (size_t)j.n4];
+        for (int a = 0; a < 3; ++a) {
+            N[2 * a] = make_float4(lo[a][0], lo[a][1], lo[a][2], lo[a][3]);
+            N[2 * a + 1] = make_float4(hi[a][0], hi[a][1], hi[a][2], hi[a][3]);
+        }
+        std::memcpy(&N[6], ref, sizeof(ref));
+        N[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+}
+
 }  // namespace
 
 bool build_bvh(const float* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris,
@@ -233,6 +326,7 @@ bool build_bvh(const float* verts, int64_t n_verts, const int32_t* tris, int64_t
         out.tris[3 * k + 2] = make_float4(v[2][0], v[2][1], v[2][2], 0.0f);
     }
     if (out.max_depth > 62) { err = "BVH too deep"; return false; }
+    collapse_wide(out.nodes, out.nodes4, out.max_depth4);
     return true;
 }
 

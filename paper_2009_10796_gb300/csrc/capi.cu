@@ -104,6 +104,7 @@ using namespace ddgi;
 struct ddgi_scene_s {
     DevScene dev{};
     float4* nodes = nullptr;
+    float4* nodes4 = nullptr;
     float4* tris = nullptr;
     int2* attr = nullptr;
     float4* albedo = nullptr;
@@ -230,17 +231,20 @@ ddgi_status ddgi_scene_create(const float* verts, int64_t n_verts, const int32_t
     if (n_emitters == 0) em[0] = make_float4(0.f, 0.f, 0.f, 0.f);
     ddgi_scene_s* s = new ddgi_scene_s();
     auto cleanup = [&]() {
-        cudaFree(s->nodes); cudaFree(s->tris); cudaFree(s->attr); cudaFree(s->albedo); cudaFree(s->emit);
+        cudaFree(s->nodes); cudaFree(s->nodes4); cudaFree(s->tris); cudaFree(s->attr); cudaFree(s->albedo); cudaFree(s->emit);
         delete s;
     };
     size_t nb = bvh.nodes.size() * sizeof(float4), tb = bvh.tris.size() * sizeof(float4);
+    size_t nb4 = bvh.nodes4.size() * sizeof(float4);
     cudaError_t e = cudaSuccess;
     if (nb) e = cudaMalloc(&s->nodes, nb);
+    if (e == cudaSuccess && nb4) e = cudaMalloc(&s->nodes4, nb4);
     if (e == cudaSuccess && tb) e = cudaMalloc(&s->tris, tb);
     if (e == cudaSuccess && n_tris) e = cudaMalloc(&s->attr, attr.size() * sizeof(int2));
     if (e == cudaSuccess) e = cudaMalloc(&s->albedo, alb.size() * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&s->emit, em.size() * sizeof(float4));
     if (e == cudaSuccess && nb) e = cudaMemcpy(s->nodes, bvh.nodes.data(), nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nb4) e = cudaMemcpy(s->nodes4, bvh.nodes4.data(), nb4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && tb) e = cudaMemcpy(s->tris, bvh.tris.data(), tb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && n_tris)
         e = cudaMemcpy(s->attr, attr.data(), attr.size() * sizeof(int2), cudaMemcpyHostToDevice);
@@ -255,6 +259,8 @@ ddgi_status ddgi_scene_create(const float* verts, int64_t n_verts, const int32_t
     s->n_leaves = bvh.n_leaves;
     s->n_tris = n_tris;
     s->dev.nodes = s->nodes;
+    s->dev.nodes4 = s->nodes4;
+    s->dev.n_nodes4 = (int32_t)(bvh.nodes4.size() / 8);
     s->dev.tris = s->tris;
     s->dev.attr = s->attr;
     s->dev.albedo = s->albedo;
@@ -269,7 +275,7 @@ ddgi_status ddgi_scene_create(const float* verts, int64_t n_verts, const int32_t
 
 void ddgi_scene_destroy(ddgi_scene s) {
     if (!s) return;
-    cudaFree(s->nodes); cudaFree(s->tris); cudaFree(s->attr); cudaFree(s->albedo); cudaFree(s->emit);
+    cudaFree(s->nodes); cudaFree(s->nodes4); cudaFree(s->tris); cudaFree(s->attr); cudaFree(s->albedo); cudaFree(s->emit);
     delete s;
 }
 

@@ -23,12 +23,14 @@ namespace ddgi {
 //   attr: per original triangle (object, emitter).
 // ---------------------------------------------------------------------------
 struct DevScene {
-    const float4* nodes;
+    const float4* nodes;     // binary hierarchy, 4 float4 per node
+    const float4* nodes4;    // the same collapsed to 4-wide nodes, 8 float4 per node
     const float4* tris;
     const int2*   attr;
     const float4* albedo;    // per object (r, g, b, flags bits)
     const float4* emit;      // per emitter (r, g, b, 0)
     int32_t n_nodes;
+    int32_t n_nodes4;
     int32_t n_tris;
 };
 
@@ -60,6 +62,22 @@ struct VolView {
     float3   blend_lo;      // cascade fall-off box (Sec. 7.3): outermost planes, or
     float3   blend_hi;      // camera-centred for a tracking window
 };
+
+// Largest BVH leaf (triangles); the traversal packs a leaf's first triangle
+// and count - 1 into one int (kLeafBits bits of count), so scenes stay below
+// 2^(31 - kLeafBits) triangles.
+constexpr int kMaxLeafTris = 8;
+constexpr int kLeafBits = 3;
+static_assert(kMaxLeafTris <= (1 << kLeafBits), "leaf count must fit its bits");
+
+// Child references of 4-wide nodes: node index (>= 0), leaf code (< 0), or
+// kRefDone for an empty slot.  Nodes deeper than kWideFullDepth take two
+// children, so a traversal stack of kStackSize4 entries cannot overflow
+// (at most 3 pushes per level down to that depth, 1 below, 63 levels).
+constexpr int kRefDone = (int)0x80000000;
+constexpr int kWideFullDepth = 20;
+constexpr int kStackSize4 = 128;
+static_assert(3 * kWideFullDepth + 63 <= kStackSize4, "4-wide traversal stack bound");
 
 // Volumes a kernel works on: one view by value (a single volume) or a device
 // table of up to kMaxVolumes views (a cascade).  Probe lists hold entries
@@ -99,6 +117,8 @@ struct FrameRot { double m[9]; };
 // Host-side BVH build result.
 struct BvhHost {
     std::vector<float4> nodes;   // 4 per node
+    std::vector<float4> nodes4;  // 8 per 4-wide node
+    int32_t max_depth4 = 0;
     std::vector<float4> tris;    // 3 per triangle
     int64_t n_leaves = 0;
     int32_t max_depth = 0;

@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Li
     bool exhausted = false;
     float3 d = f3(0.0f, 0.0f, 1.0f);
     RayPre r = ray_pre(f3(0.0f, 0.0f, 0.0f), d);
-    WwLane w;
+    WwLane<kStackSize4> w;
     ww_start(s, w, false);
     while (true) {
         int64_t item = refill(next, total, rec < 0, exhausted);
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Li
             ww_start(s, w, true);
         }
         if (__ballot_sync(0xffffffffu, rec >= 0) == 0) break;
-        ww_round<false>(s, r, w);
+        ww4_round<false>(s, r, w);
         bool need = false, front = false;
         int64_t done = -1;
         if (rec >= 0 && w.node == kDone) {
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolSet vs, Lig
     int64_t rec = -1;
     bool exhausted = false;
     RayPre r = ray_pre(f3(0.0f, 0.0f, 0.0f), tol);
-    WwLane w;
+    WwLane<kStackSize4> w;
     ww_start(s, w, false);
     while (true) {
         int64_t item = refill(next, total, rec < 0, exhausted);
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolSet vs, Lig
             ww_start(s, w, true);
         }
         if (__ballot_sync(0xffffffffu, rec >= 0) == 0) break;
-        ww_round<true>(s, r, w);
+        ww4_round<true>(s, r, w);
         if (rec >= 0 && w.node == kDone) {
             if (w.h.orig < 0) reinterpret_cast<float*>(hits)[4 * rec + 2] = 1.0f;
             rec = -1;

@@ -175,22 +175,24 @@ __device__ __forceinline__ Hit traverse(const DevScene& s, const RayPre& r, Trac
 // result equals traverse<false>'s; for ANY, occlusion is the same.
 // Every lane of the warp must call it (inactive lanes pass valid = false).
 // Stack entries are node indices (>= 0) or leaf codes
-// ~((first << 2) | (count - 1)) (leaves hold 1..4 triangles, first < 2^28).
+// ~((first << kLeafBits) | (count - 1)) (1..kMaxLeafTris triangles).
 constexpr int kNoLeaf = 0;              // "no parked leaf" (leaf codes are < 0)
-constexpr int kDone = (int)0x80000000;  // empty-stack sentinel, below every leaf code
+constexpr int kDone = kRefDone;         // empty-stack sentinel, below every leaf code
 
-__device__ __forceinline__ int leaf_code(int child, int cnt) { return ~(((~child) << 2) | (cnt - 1)); }
+__device__ __forceinline__ int leaf_code(int child, int cnt) { return ~(((~child) << kLeafBits) | (cnt - 1)); }
 
 // Per-lane state of the warp-cooperative walk.
+template <int N = kStackSize>
 struct WwLane {
-    int stack[kStackSize];
+    int stack[N];
     int sp;
     int node;   // next internal node, a leaf code taken from the stack, or kDone
     int leaf;   // parked leaf code or kNoLeaf
     Hit h;
 };
 
-__device__ __forceinline__ void ww_start(const DevScene& s, WwLane& w, bool valid) {
+template <int N>
+__device__ __forceinline__ void ww_start(const DevScene& s, WwLane<N>& w, bool valid) {
     w.sp = 0;
     w.node = (valid && s.n_nodes > 0) ? 0 : kDone;
     w.leaf = kNoLeaf;
@@ -199,13 +201,17 @@ __device__ __forceinline__ void ww_start(const DevScene& s, WwLane& w, bool vali
     w.h.k = -1;
 }
 
-__device__ __forceinline__ int ww_pop(WwLane& w) { return w.sp > 0 ? w.stack[--w.sp] : kDone; }
+template <int N>
+__device__ __forceinline__ int ww_pop(WwLane<N>& w) { return w.sp > 0 ? w.stack[--w.sp] : kDone; }
+
+template <bool ANY, int N>
+__device__ __forceinline__ void ww_leaves(const DevScene& s, const RayPre& r, WwLane<N>& w);
 
 // One round: descend internal nodes until no lane is still looking for a
 // leaf, then test every parked leaf (and leaves popped right after it).  A
 // lane's walk is over when node == kDone after the round.  Warp-cooperative.
 template <bool ANY>
-__device__ __forceinline__ void ww_round(const DevScene& s, const RayPre& r, WwLane& w) {
+__device__ __forceinline__ void ww_round(const DevScene& s, const RayPre& r, WwLane<>& w) {
     while (true) {
         if (w.node >= 0) {
             const float4* N = s.nodes + 4 * (int64_t)w.node;
@@ -236,9 +242,16 @@ __device__ __forceinline__ void ww_round(const DevScene& s, const RayPre& r, WwL
         }
         if (__ballot_sync(0xffffffffu, w.node >= 0 && w.leaf == kNoLeaf) == 0) break;
     }
+    ww_leaves<ANY>(s, r, w);
+}
+
+// Leaf phase of a round: test the parked leaf and the leaves popped right
+// after it.
+template <bool ANY, int N>
+__device__ __forceinline__ void ww_leaves(const DevScene& s, const RayPre& r, WwLane<N>& w) {
     while (w.leaf != kNoLeaf) {
         int code = ~w.leaf;
-        int first = code >> 2, cnt = (code & 3) + 1;
+        int first = code >> kLeafBits, cnt = (code & ((1 << kLeafBits) - 1)) + 1;
         for (int k = first; k < first + cnt; ++k) {
             const float4* T = s.tris + 3 * (int64_t)k;
             float4 p0 = __ldg(T), p1 = __ldg(T + 1), p2 = __ldg(T + 2);
@@ -271,9 +284,59 @@ __device__ __forceinline__ void ww_round(const DevScene& s, const RayPre& r, WwL
     }
 }
 
+// Compare-exchange of (entry distance, reference) pairs, ascending.
+__device__ __forceinline__ void cx(float& ka, int& va, float& kb, int& vb) {
+    const bool sw = kb < ka;
+    const float k = sw ? kb : ka;
+    const int v = sw ? vb : va;
+    kb = sw ? ka : kb;
+    vb = sw ? va : vb;
+    ka = k;
+    va = v;
+}
+
+// The same round over the 4-wide hierarchy: a node tests its four child
+// boxes, descends into the nearest hit child and pushes the other hits
+// farthest first (closest-hit rays; shadow rays push in slot order, any hit
+// ends them).  Leaves found among the children are parked or pushed as leaf
+// codes exactly as in the binary walk.
+template <bool ANY>
+__device__ __forceinline__ void ww4_round(const DevScene& s, const RayPre& r, WwLane<kStackSize4>& w) {
+    while (true) {
+        if (w.node >= 0) {
+            const float4* N = s.nodes4 + 8 * (int64_t)w.node;
+            const float4 lx = __ldg(N), hx = __ldg(N + 1), ly = __ldg(N + 2), hy = __ldg(N + 3);
+            const float4 lz = __ldg(N + 4), hz = __ldg(N + 5);
+            const int4 ref = __ldg(reinterpret_cast<const int4*>(N + 6));
+            float k0 = box_enter(r, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, w.h.t);
+            float k1 = box_enter(r, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, w.h.t);
+            float k2 = box_enter(r, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, w.h.t);
+            float k3 = box_enter(r, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, w.h.t);
+            int v0 = ref.x, v1 = ref.y, v2 = ref.z, v3 = ref.w;
+            if (!ANY) {
+                cx(k0, v0, k1, v1);
+                cx(k2, v2, k3, v3);
+                cx(k0, v0, k2, v2);
+                cx(k1, v1, k3, v3);
+                cx(k1, v1, k2, v2);
+            }
+            if (k3 != INFINITY && w.sp < kStackSize4) w.stack[w.sp++] = v3;
+            if (k2 != INFINITY && w.sp < kStackSize4) w.stack[w.sp++] = v2;
+            if (k1 != INFINITY && w.sp < kStackSize4) w.stack[w.sp++] = v1;
+            w.node = k0 != INFINITY ? v0 : ww_pop(w);
+            if (w.node < 0 && w.node != kDone && w.leaf == kNoLeaf) {
+                w.leaf = w.node;
+                w.node = ww_pop(w);
+            }
+        }
+        if (__ballot_sync(0xffffffffu, w.node >= 0 && w.leaf == kNoLeaf) == 0) break;
+    }
+    ww_leaves<ANY>(s, r, w);
+}
+
 template <bool ANY>
 __device__ __forceinline__ Hit traverse_ww(const DevScene& s, const RayPre& r, bool valid) {
-    WwLane w;
+    WwLane<> w;
     ww_start(s, w, valid);
     do {
         ww_round<ANY>(s, r, w);
