@@ -35,13 +35,18 @@ import synth  # noqa: E402
 METRIC = "probe-update ms/frame & Grays/s at 16k probes; query ms at 1080p vs FP32 plain"
 WORKLOAD = ("city 32x16x32 probes @ 2 m, 196,610 tris, 256 rays/probe, hysteresis 0.97, "
             "multi-bounce, state machine on, 1920x1080 G-buffer query")
-# FP32 lane operations counted per unit of work of the trace + shade kernel
-# (see the design notes: slab tests, watertight triangle test, hit shading).
-OPS_PER_NODE = 50
+# FP32 lane operations counted per unit of work of the trace passes (see the
+# design notes): a child-box slab test is 25, a 4-wide node visit tests four
+# boxes and, for closest-hit rays, orders them with 5 compare-exchanges of 5
+# operations; a watertight triangle test is 30.
+OPS_PER_WIDE_NODE = 4 * 25 + 5 * 5
+OPS_PER_WIDE_NODE_ANY = 4 * 25
 OPS_PER_TRI = 30
-OPS_PER_QUERY = 700
-OPS_PER_RAY = 60
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) of one k_trace_primary launch on this workload,
+# from the ncu capture in profiles/trace_passes_city.md; set to None whenever
+# the kernel changes until it is captured again
+PRIMARY_TRAFFIC_BYTES = 2_724_352 + 910_080
 
 
 def peaks():
@@ -66,15 +71,31 @@ class ClockSampler:
         self.file = None
 
     def __enter__(self):
+        self.window = None
         try:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.file, stderr=subprocess.DEVNULL)
+            # the timed region starts only once the sampler is producing rows
+            t0 = time.perf_counter()
+            while self._rows() == 0 and time.perf_counter() - t0 < 10.0:
+                time.sleep(0.05)
         except Exception:
             self.proc = None
         return self
+
+    def _rows(self):
+        try:
+            with open(self.file.name) as f:
+                return sum(1 for _ in f)
+        except OSError:
+            return 0
+
+    def mark(self):
+        """Row count now: call at the start and at the end of the timed region."""
+        return self._rows()
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -96,6 +117,12 @@ class ClockSampler:
                 if len(parts) >= 9:
                     rows.append(parts)
         os.unlink(self.file.name)
+        where = "whole run"
+        if self.window is not None:
+            a, b = self.window
+            inside = rows[a:b]
+            # a timed region shorter than the sampling period: the first row after it
+            rows, where = (inside, "timed region") if inside else (rows[b:b + 1], "first sample after the timed region")
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -103,7 +130,8 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "window": where}
 
 
 def make_workload():
@@ -261,7 +289,10 @@ def run_gpu(args):
         return ([a.elapsed_time(b) for a, b in evs], [a.elapsed_time(b) for a, b in qev], tm, wall_s)
 
     with ClockSampler(local) as clk:
+        m0 = clk.mark()
         step_ms, query_ms, timings, wall = timed_steps(g.BLEND_FP32)
+        time.sleep(0.15)    # one sampling period, so a row taken during the region has landed
+        clk.window = (m0, clk.mark())
         mixed = None
         if not args.no_mixed:
             m_step, m_query, m_tm, _ = timed_steps(g.BLEND_TF32)
@@ -303,17 +334,20 @@ def run_gpu(args):
     e2e_value = world * rays_per_step / (float(t.item()) * 1e-3) / 1e9
     vol.poll_status()
 
-    # roofline of the dominant kernel (trace + shade): counted FP32 lane ops
-    # per launch / its event-timed duration; peak = lanes x max SM clock
+    # roofline of the dominant kernel, the primary trace pass: its counted FP32
+    # lane operations per launch / its event-timed duration on the update
+    # stream; peak = lanes x max SM clock (one operation per lane per clock)
     pk, pk_kind = peaks()
     trace_ms, trace_n = timings["trace_shade"]
     trace_ms_avg = trace_ms / max(trace_n, 1)
-    ops = (OPS_PER_NODE * (stats["nodes"] + stats["shadow_nodes"])
-           + OPS_PER_TRI * (stats["tris"] + stats["shadow_tris"])
-           + OPS_PER_QUERY * stats["queries"] + OPS_PER_RAY * stats["rays"])
+    prim_ms = timings["trace_primary"][0] / max(timings["trace_primary"][1], 1)
+    shadow_ms = timings["trace_shadow"][0] / max(timings["trace_shadow"][1], 1)
+    prim_ops = OPS_PER_WIDE_NODE * stats["nodes"] + OPS_PER_TRI * stats["tris"]
+    shadow_ops = OPS_PER_WIDE_NODE_ANY * stats["shadow_nodes"] + OPS_PER_TRI * stats["shadow_tris"]
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_tops = sm_count * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    achieved = ops / (trace_ms_avg * 1e-3) / 1e12
+    achieved = prim_ops / (prim_ms * 1e-3) / 1e12
+    shadow_achieved = shadow_ops / (shadow_ms * 1e-3) / 1e12
     blend_ms = timings["blend"][0] / max(timings["blend"][1], 1)
     blend_bytes = n_active * (R * 16 + 2000 + 2816)      # records in, old interior in, tiles out
     blend_flops = n_active * 2 * R * (36 * 3 + 196 * 2)    # the contraction of Eq. 1 (irr + distance moments)
@@ -349,13 +383,18 @@ def run_gpu(args):
         "trace_grays_per_s": rays_per_step / (trace_ms_avg * 1e-3) / 1e9,
         "stage_ms": {k: v[0] / max(v[1], 1) for k, v in timings.items()},
         "wall_ms_per_step": 1e3 * wall / args.steps,
-        "trace_work_per_ray": {"nodes": stats["nodes"] / max(stats["rays"], 1),
+        "trace_work_per_ray": {"wide_nodes": stats["nodes"] / max(stats["rays"], 1),
                                "tris": stats["tris"] / max(stats["rays"], 1),
                                "shadow_rays": stats["shadow_rays"] / max(stats["rays"], 1),
                                "queries": stats["queries"] / max(stats["rays"], 1)},
-        "roofline": {"bound": "alu", "kernel": "k_trace_shade", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": "k_trace_primary", "achieved": achieved,
                      "peak": peak_tops, "unit": "TFLOP/s", "frac": achieved / peak_tops,
-                     "traffic": None, "peak_kind": f"FP32 lanes x max SM clock ({pk_kind} clock)"},
+                     "traffic": PRIMARY_TRAFFIC_BYTES,
+                     "peak_kind": f"FP32 lanes x max SM clock ({pk_kind} clock)",
+                     "ops_per_launch": prim_ops, "launch_ms": prim_ms},
+        "roofline_shadow": {"bound": "alu", "kernel": "k_trace_shadow", "achieved": shadow_achieved,
+                            "peak": peak_tops, "unit": "TFLOP/s", "frac": shadow_achieved / peak_tops,
+                            "launch_ms": shadow_ms},
         "roofline_blend": {"bound": "hbm", "achieved": blend_bytes / (blend_ms * 1e-3) / 1e9,
                            "peak": hbm, "unit": "GB/s",
                            "frac": blend_bytes / (blend_ms * 1e-3) / 1e9 / hbm},
@@ -468,7 +507,7 @@ def run_diff(args, g, torch, stream):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -252,18 +252,23 @@ ddgi_status ddgi_get_ray_records(ddgi_volume volume, float* records_dev, int32_t
 /* Kernel timing: when enabled, ddgi_update records CUDA events around its
  * kernels on the update stream; ddgi_read_timings returns the summed
  * milliseconds per stage since the last read (synchronises the stream):
- * ms[0] classify, ms[1] lists, ms[2] trace+shade, ms[3] blend+border+states,
- * ms[4] frame setup; counts[k] launches per stage. */
+ * ms[0] classify, ms[1] lists, ms[2] trace+shade (the three passes below
+ * with their launch gaps), ms[3] blend+border+states, ms[4] frame setup,
+ * ms[5] primary pass, ms[6] shadow pass, ms[7] shading pass; counts[k]
+ * launches per stage. */
 ddgi_status ddgi_enable_timing(ddgi_volume volume, int32_t enable);
-ddgi_status ddgi_read_timings(ddgi_volume volume, float ms[5], int32_t counts[5]);
+ddgi_status ddgi_read_timings(ddgi_volume volume, float ms[8], int32_t counts[8]);
 
 /* Work counters of the last update's trace (measurement only; the update
  * itself runs uninstrumented).  Re-traces the last update's rays of its
- * active probes with a counting variant of the trace + shade kernel and
- * writes, summed over rays: stats[0] primary rays, [1] primary node visits,
- * [2] primary triangle tests, [3] shadow rays, [4] shadow node visits,
- * [5] shadow triangle tests, [6] probe queries at hits.  Synchronises the
- * stream.  Errors: INVALID_ARG (no update yet), CUDA. */
+ * active probes with counting builds of the primary and shadow passes
+ * (hit records go to a temporary buffer the call allocates and frees) and
+ * writes, summed over rays: stats[0] primary rays, [1] primary 4-wide node
+ * visits (four child-box tests each), [2] primary triangle tests, [3] shadow
+ * rays, [4] shadow node visits, [5] shadow triangle tests, [6] front hits
+ * (each shaded with one probe query).  The visiting order follows the warp
+ * schedule, so repeated calls can differ slightly.  Synchronises the stream.
+ * Errors: INVALID_ARG (no update yet), OOM, CUDA. */
 ddgi_status ddgi_trace_stats(ddgi_volume volume, ddgi_scene scene, const ddgi_lights* lights,
                              uint64_t stats[7], ddgi_stream stream);
 

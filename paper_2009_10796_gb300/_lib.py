@@ -80,7 +80,7 @@ SIGNATURES = {
     "ddgi_set_buffer": (C.c_int, [_vp, C.c_int32, _vp, C.c_size_t, _vp]),
     "ddgi_get_ray_records": (C.c_int, [_vp, _vp, _vp, C.POINTER(C.c_int64), _vp]),
     "ddgi_enable_timing": (C.c_int, [_vp, C.c_int32]),
-    "ddgi_read_timings": (C.c_int, [_vp, C.c_float * 5, C.c_int32 * 5]),
+    "ddgi_read_timings": (C.c_int, [_vp, C.c_float * 8, C.c_int32 * 8]),
     "ddgi_poll_status": (C.c_int, [_vp, _vp]),
     "ddgi_trace_stats": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.c_uint64 * 7, _vp]),
     "ddgi_update_noalloc": (C.c_int, [_vp, C.POINTER(VolumeDesc), C.POINTER(Lights),

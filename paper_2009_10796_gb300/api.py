@@ -258,10 +258,11 @@ class Volume:
         check(load().ddgi_enable_timing(self.handle, int(bool(on))))
 
     def read_timings(self):
-        ms = (C.c_float * 5)()
-        cnt = (C.c_int32 * 5)()
+        ms = (C.c_float * 8)()
+        cnt = (C.c_int32 * 8)()
         check(load().ddgi_read_timings(self.handle, ms, cnt))
-        names = ["classify", "lists", "trace_shade", "blend", "frame_setup"]
+        names = ["classify", "lists", "trace_shade", "blend", "frame_setup", "trace_primary", "trace_shadow",
+                 "shade"]
         return {n: (ms[i], cnt[i]) for i, n in enumerate(names)}
 
     def poll_status(self, stream=None):

@@ -154,7 +154,7 @@ struct ddgi_volume_s {
     int64_t updates = 0;
     int3 shift{0, 0, 0};
     bool timing = false;
-    TimedStage stages[5];
+    TimedStage stages[8];
 };
 
 static VolView make_view(const ddgi_volume_s* v) {
@@ -541,9 +541,18 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
     }
     {
         StageTimer tm(v, 2, st);
+        // per-pass events (stages 5, 6, 7) when timing is on
+        cudaEvent_t marks[4] = {nullptr, nullptr, nullptr, nullptr};
+        if (v->timing)
+            for (auto& m : marks) DDGI_CK(cudaEventCreate(&m));
         DDGI_CK(launch_trace_wavefront(s->dev, view, make_lights(lights), v->dirs, v->R, v->perm, v->lists + v->P,
                                        v->counts + 1, v->records, v->shadow_list, v->hit_list, v->shadow_count, sms * 8,
-                                       st));
+                                       st, v->timing ? marks : nullptr));
+        if (v->timing) {
+            v->stages[5].pending.emplace_back(marks[0], marks[1]);
+            v->stages[6].pending.emplace_back(marks[1], marks[2]);
+            v->stages[7].pending.emplace_back(marks[2], marks[3]);
+        }
     }
     BlendParams bp{};
     bp.hyst_irr = std::fmin(1.0f, std::fmax(0.0f, d.hysteresis_irr * params->irr_hyst_scale));
@@ -571,13 +580,30 @@ ddgi_status ddgi_trace_stats(ddgi_volume v, ddgi_scene s, const ddgi_lights* lig
     if (!v || !s || !lights || !stats) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
     if (v->updates == 0) return fail(DDGI_ERR_INVALID_ARG, "no update has run on this volume");
     cudaStream_t st = (cudaStream_t)stream;
+    // the counting passes write their hit records to scratch, leaving the
+    // update's records untouched
+    float4* scratch = nullptr;
+    DDGI_CK(cudaMalloc(&scratch, sizeof(float4) * (size_t)v->P * v->R));
     DDGI_CK(cudaMemsetAsync(v->stats, 0, sizeof(unsigned long long) * 8, st));
-    DDGI_CK(launch_trace_shade_count(s->dev, make_view(v), make_lights(lights), v->dirs, v->R,
-                                     v->lists + v->P, v->counts + 1, v->stats, sm_count() * 16, st));
+    cudaError_t e = launch_trace_count(s->dev, make_view(v), make_lights(lights), v->dirs, v->R, v->perm,
+                                       v->lists + v->P, v->counts + 1, scratch, v->shadow_list, v->hit_list,
+                                       v->shadow_count, v->stats, sm_count() * 8, st);
     unsigned long long h[8];
-    DDGI_CK(cudaMemcpyAsync(h, v->stats, sizeof(h), cudaMemcpyDeviceToHost, st));
-    DDGI_CK(cudaStreamSynchronize(st));
-    for (int k = 0; k < 7; ++k) stats[k] = h[k];
+    int32_t n[4] = {0, 0, 0, 0};
+    int32_t n_active = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, v->stats, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(n, v->shadow_count, sizeof(n), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&n_active, v->counts + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(scratch);
+    DDGI_CK(e);
+    stats[0] = (uint64_t)n_active * (uint64_t)v->R;
+    stats[1] = h[1];
+    stats[2] = h[2];
+    stats[3] = (uint64_t)n[0];
+    stats[4] = h[4];
+    stats[5] = h[5];
+    stats[6] = (uint64_t)n[1];
     return DDGI_OK;
 }
 
@@ -647,9 +673,9 @@ ddgi_status ddgi_enable_timing(ddgi_volume v, int32_t enable) {
     return DDGI_OK;
 }
 
-ddgi_status ddgi_read_timings(ddgi_volume v, float ms[5], int32_t counts[5]) {
+ddgi_status ddgi_read_timings(ddgi_volume v, float ms[8], int32_t counts[8]) {
     if (!v || !ms || !counts) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < 8; ++k) {
         float total = 0.0f;
         int32_t c = 0;
         for (auto& pr : v->stages[k].pending) {
@@ -658,8 +684,10 @@ ddgi_status ddgi_read_timings(ddgi_volume v, float ms[5], int32_t counts[5]) {
             DDGI_CK(cudaEventElapsedTime(&t, pr.first, pr.second));
             total += t;
             c++;
+            // the pass marks share events (stage 6 starts where stage 5 ends,
+            // 7 where 6 ends): each is destroyed once, as a pair's start
             cudaEventDestroy(pr.first);
-            cudaEventDestroy(pr.second);
+            if (k < 5 || k == 7) cudaEventDestroy(pr.second);
         }
         v->stages[k].pending.clear();
         ms[k] = total;

@@ -163,10 +163,18 @@ cudaError_t launch_trace_shade(const DevScene& s, const VolView& v, const Lights
 // shadow pass, then shading of the front hits.  shadow_list and hit_list
 // hold one int32 per ray (active probes x R); shadow_count is 4 int32 of
 // device scratch, 8-byte aligned (shadow rays, front hits, 64-bit work counter).
+// marks: 4 events recorded around the three passes, or nullptr.
 cudaError_t launch_trace_wavefront(const DevScene& s, const VolView& v, const Lights& L, const float4* dirs,
                                    int R, const int32_t* perm, const int32_t* active, const int32_t* count,
                                    float4* records, int32_t* shadow_list, int32_t* hit_list, int32_t* shadow_count,
-                                   int grid, cudaStream_t st);
+                                   int grid, cudaStream_t st, cudaEvent_t* marks);
+// Measurement build of the primary and shadow passes: adds 4-wide node
+// visits and triangle tests to stats[1], [2] (primary) and [4], [5] (shadow);
+// the shadow-ray and front-hit counts are left in shadow_count[0], [1].
+cudaError_t launch_trace_count(const DevScene& s, const VolView& v, const Lights& L, const float4* dirs, int R,
+                               const int32_t* perm, const int32_t* active, const int32_t* count, float4* records,
+                               int32_t* shadow_list, int32_t* hit_list, int32_t* shadow_count,
+                               unsigned long long* stats, int grid, cudaStream_t st);
 cudaError_t launch_trace_wavefront_multi(const DevScene& s, const VolSet& vs, const Lights& L,
                                          const float4* dirs, int R, const int32_t* perm, const int32_t* active,
                                          const int32_t* count, float4* records, int32_t* shadow_list,
@@ -174,10 +182,6 @@ cudaError_t launch_trace_wavefront_multi(const DevScene& s, const VolSet& vs, co
 // Morton order of the octahedral positions of the unrotated spherical-
 // Fibonacci directions (host; a rotation keeps neighbouring directions together)
 std::vector<int32_t> ray_order_morton(int R);
-cudaError_t launch_trace_shade_count(const DevScene& s, const VolView& v, const Lights& L,
-                                     const float4* dirs, int R, const int32_t* active,
-                                     const int32_t* count, unsigned long long* stats, int grid,
-                                     cudaStream_t st);
 cudaError_t launch_blend(const VolView& v, const BlendParams& bp, const float* w_irr,
                          const float* inv_s_irr, const float* w_dist, const float* inv_s_dist,
                          const float4* records, const int32_t* active, const int32_t* count,

@@ -57,19 +57,13 @@ __global__ void __launch_bounds__(256) k_classify(DevScene s, VolSet vs, const f
     }
 }
 
-// COUNT = true is the instrumented measurement variant: it writes no records
-// and accumulates per-ray work counters instead (stats[0..6]: primary rays,
-// primary node visits, primary triangle tests, shadow rays, shadow node
-// visits, shadow triangle tests, probe queries at hits).
-template <bool COUNT>
+// Fused trace + shade, one thread per probe ray (the allocation-free
+// update's path: it needs no shadow or hit lists).
 __global__ void __launch_bounds__(128) k_trace_shade(DevScene s, VolView v, Lights L,
                                                      const float4* __restrict__ dirs, int R,
                                                      const int32_t* __restrict__ active,
                                                      const int32_t* __restrict__ count,
-                                                     float4* __restrict__ records,
-                                                     unsigned long long* stats) {
-    TraceCount cp, cs;
-    uint32_t n_rays = 0, n_shadow = 0, n_query = 0;
+                                                     float4* __restrict__ records) {
     const int64_t total = (int64_t)(*count) * R;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
@@ -80,8 +74,7 @@ __global__ void __launch_bounds__(128) k_trace_shade(DevScene s, VolView v, Ligh
         float4 d4 = __ldg(dirs + i);
         float3 d = f3(d4.x, d4.y, d4.z);
         RayPre r = ray_pre(o, d);
-        Hit h = traverse<false, COUNT>(s, r, &cp);
-        if (COUNT) n_rays++;
+        Hit h = traverse<false>(s, r);
         float4 rec;
         if (h.orig < 0) {
             float c = dot(d, L.sky_up);
@@ -111,41 +104,31 @@ __global__ void __launch_bounds__(128) k_trace_shade(DevScene s, VolView v, Ligh
                 if (L.sun_on && cosl > 0.0f) {
                     float off = 1e-4f * (1.0f + length(x));
                     RayPre sr = ray_pre(x + off * n, tol);
-                    Hit sh = traverse<true, COUNT>(s, sr, &cs);
-                    if (COUNT) n_shadow++;
+                    Hit sh = traverse<true>(s, sr);
                     if (sh.orig < 0) {
                         float k = cosl * 0.318309886183790672f;   // 1/pi
                         direct = f3(L.sun_irr.x * k, L.sun_irr.y * k, L.sun_irr.z * k);
                     }
                 }
                 float3 M = query_M(v, x, n, f3(-d.x, -d.y, -d.z));
-                if (COUNT) n_query++;
                 rec = make_float4(Le.x + rho.x * (direct.x + M.x), Le.y + rho.y * (direct.y + M.y),
                                   Le.z + rho.z * (direct.z + M.z), fminf(h.t, v.t_max));
             }
         }
-        if (!COUNT) records[idx] = rec;
-    }
-    if (COUNT) {
-        atomicAdd(stats + 0, (unsigned long long)n_rays);
-        atomicAdd(stats + 1, (unsigned long long)cp.nodes);
-        atomicAdd(stats + 2, (unsigned long long)cp.tris);
-        atomicAdd(stats + 3, (unsigned long long)n_shadow);
-        atomicAdd(stats + 4, (unsigned long long)cs.nodes);
-        atomicAdd(stats + 5, (unsigned long long)cs.tris);
-        atomicAdd(stats + 6, (unsigned long long)n_query);
+        records[idx] = rec;
     }
 }
 
 // ---------------------------------------------------------------------------
 // Wavefront form of trace + shade: three coherent passes over the same rays.
-//   k_trace_primary  closest hit of every ray; stores (t, BVH triangle index,
-//                    sun visibility, 0) in the ray's record slot and appends
-//                    the rays that need a shadow ray (front-face hits facing
-//                    the sun) to a compact list
+//   k_trace_primary  closest hit of every ray over the 4-wide hierarchy;
+//                    writes the final record of misses (sky) and back faces,
+//                    stores (t, BVH triangle index, 0, 0) for front hits and
+//                    appends them to the hit list, and those facing the sun
+//                    to the shadow-ray list
 //   k_trace_shadow   any-hit shadow rays over that list; sets the visibility
-//   k_shade          shading and the previous-frame query at each hit; writes
-//                    the final (r, g, b, d) record over the hit record
+//   k_shade          shading and the previous-frame query at each front hit;
+//                    writes the final (r, g, b, d) record over the hit record
 // Each pass keeps its lanes on one kind of work, where the fused kernel ran
 // traversal, shadow rays and queries divergently in the same warp.  The
 // arithmetic of every value is the fused kernel's, in the same order.
@@ -181,7 +164,9 @@ __device__ __forceinline__ int64_t refill(unsigned long long* next, int64_t tota
     return w < total ? w : -1;
 }
 
-template <bool MULTI>
+// COUNT: measurement build that adds its 4-wide node visits and triangle
+// tests to stats[1], stats[2] (otherwise identical).
+template <bool MULTI, bool COUNT = false>
 __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Lights L,
                                                        const float4* __restrict__ dirs, int R,
                                                        const int32_t* __restrict__ perm,
@@ -191,9 +176,11 @@ __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Li
                                                        int32_t* __restrict__ shadow_list,
                                                        int32_t* __restrict__ hit_list,
                                                        int32_t* shadow_count,
-                                                       unsigned long long* next) {
+                                                       unsigned long long* next,
+                                                       unsigned long long* stats = nullptr) {
     const int lane = threadIdx.x & 31;
     const int64_t total = (int64_t)(*count) * R;
+    TraceCount tc;
     const float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
     int64_t rec = -1;   // record index of the lane's ray, -1 when idle
     int entry = 0;      // its probe's list entry
@@ -219,7 +206,7 @@ __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Li
             ww_start(s, w, true);
         }
         if (__ballot_sync(0xffffffffu, rec >= 0) == 0) break;
-        ww4_round<false>(s, r, w);
+        ww4_round<false, COUNT>(s, r, w, &tc);
         bool need = false, front = false;
         int64_t done = -1;
         if (rec >= 0 && w.node == kDone) {
@@ -267,17 +254,24 @@ __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Li
             if (front) hit_list[off + __popc(mask & ((1u << lane) - 1u))] = (int32_t)done;
         }
     }
+    if (COUNT) {
+        atomicAdd(stats + 1, (unsigned long long)tc.nodes);
+        atomicAdd(stats + 2, (unsigned long long)tc.tris);
+    }
 }
 
-template <bool MULTI>
+// COUNT: adds 4-wide node visits and triangle tests to stats[4], stats[5].
+template <bool MULTI, bool COUNT = false>
 __global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolSet vs, Lights L,
                                                       const float4* __restrict__ dirs, int R,
                                                       const int32_t* __restrict__ active,
                                                       float4* __restrict__ hits,
                                                       const int32_t* __restrict__ shadow_list,
                                                       const int32_t* __restrict__ shadow_count,
-                                                      unsigned long long* next) {
+                                                      unsigned long long* next,
+                                                      unsigned long long* stats = nullptr) {
     const int64_t total = *shadow_count;
+    TraceCount tc;
     const float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
     int64_t rec = -1;
     bool exhausted = false;
@@ -304,11 +298,15 @@ __global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolSet vs, Lig
             ww_start(s, w, true);
         }
         if (__ballot_sync(0xffffffffu, rec >= 0) == 0) break;
-        ww4_round<true>(s, r, w);
+        ww4_round<true, COUNT>(s, r, w, &tc);
         if (rec >= 0 && w.node == kDone) {
             if (w.h.orig < 0) reinterpret_cast<float*>(hits)[4 * rec + 2] = 1.0f;
             rec = -1;
         }
+    }
+    if (COUNT) {
+        atomicAdd(stats + 4, (unsigned long long)tc.nodes);
+        atomicAdd(stats + 5, (unsigned long long)tc.tris);
     }
 }
 
@@ -424,7 +422,7 @@ cudaError_t launch_classify_multi(const DevScene& s, const VolSet& vs, const flo
 cudaError_t launch_trace_shade(const DevScene& s, const VolView& v, const Lights& L, const float4* dirs,
                                int R, const int32_t* active, const int32_t* count, float4* records,
                                int grid, cudaStream_t st) {
-    k_trace_shade<false><<<grid, 128, 0, st>>>(s, v, L, dirs, R, active, count, records, nullptr);
+    k_trace_shade<<<grid, 128, 0, st>>>(s, v, L, dirs, R, active, count, records);
     return cudaGetLastError();
 }
 
@@ -432,29 +430,51 @@ template <bool MULTI>
 static cudaError_t trace_wavefront(const DevScene& s, const VolSet& vs, const Lights& L, const float4* dirs, int R,
                                    const int32_t* perm, const int32_t* active, const int32_t* count,
                                    float4* records, int32_t* shadow_list, int32_t* hit_list, int32_t* shadow_count,
-                                   int grid, cudaStream_t st) {
+                                   int grid, cudaStream_t st, cudaEvent_t* marks) {
     // shadow_count[0]: shadow rays; [1]: front hits; [2..3]: the 64-bit work
     // counter of the persistent passes, zeroed before each
     unsigned long long* next = reinterpret_cast<unsigned long long*>(shadow_count + 2);
     cudaError_t e = cudaMemsetAsync(shadow_count, 0, 4 * sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
+    if (marks && (e = cudaEventRecord(marks[0], st)) != cudaSuccess) return e;
     k_trace_primary<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, perm, active, count, records, shadow_list,
                                                   hit_list, shadow_count, next);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+    if (marks && (e = cudaEventRecord(marks[1], st)) != cudaSuccess) return e;
     k_trace_shadow<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, active, records, shadow_list, shadow_count,
                                                  next);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (marks && (e = cudaEventRecord(marks[2], st)) != cudaSuccess) return e;
     k_shade<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, active, hit_list, shadow_count + 1, records);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (marks && (e = cudaEventRecord(marks[3], st)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+cudaError_t launch_trace_count(const DevScene& s, const VolView& v, const Lights& L, const float4* dirs, int R,
+                               const int32_t* perm, const int32_t* active, const int32_t* count, float4* records,
+                               int32_t* shadow_list, int32_t* hit_list, int32_t* shadow_count,
+                               unsigned long long* stats, int grid, cudaStream_t st) {
+    const VolSet vs = single_set(v);
+    unsigned long long* next = reinterpret_cast<unsigned long long*>(shadow_count + 2);
+    cudaError_t e = cudaMemsetAsync(shadow_count, 0, 4 * sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    k_trace_primary<false, true><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, perm, active, count, records,
+                                                        shadow_list, hit_list, shadow_count, next, stats);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+    k_trace_shadow<false, true><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, active, records, shadow_list,
+                                                       shadow_count, next, stats);
     return cudaGetLastError();
 }
 
 cudaError_t launch_trace_wavefront(const DevScene& s, const VolView& v, const Lights& L, const float4* dirs,
                                    int R, const int32_t* perm, const int32_t* active, const int32_t* count,
                                    float4* records, int32_t* shadow_list, int32_t* hit_list, int32_t* shadow_count,
-                                   int grid, cudaStream_t st) {
+                                   int grid, cudaStream_t st, cudaEvent_t* marks) {
     return trace_wavefront<false>(s, single_set(v), L, dirs, R, perm, active, count, records, shadow_list, hit_list,
-                                  shadow_count, grid, st);
+                                  shadow_count, grid, st, marks);
 }
 
 cudaError_t launch_trace_wavefront_multi(const DevScene& s, const VolSet& vs, const Lights& L,
@@ -462,15 +482,7 @@ cudaError_t launch_trace_wavefront_multi(const DevScene& s, const VolSet& vs, co
                                          const int32_t* count, float4* records, int32_t* shadow_list,
                                          int32_t* hit_list, int32_t* shadow_count, int grid, cudaStream_t st) {
     return trace_wavefront<true>(s, vs, L, dirs, R, perm, active, count, records, shadow_list, hit_list,
-                                 shadow_count, grid, st);
-}
-
-cudaError_t launch_trace_shade_count(const DevScene& s, const VolView& v, const Lights& L,
-                                     const float4* dirs, int R, const int32_t* active,
-                                     const int32_t* count, unsigned long long* stats, int grid,
-                                     cudaStream_t st) {
-    k_trace_shade<true><<<grid, 128, 0, st>>>(s, v, L, dirs, R, active, count, nullptr, stats);
-    return cudaGetLastError();
+                                 shadow_count, grid, st, nullptr);
 }
 
 cudaError_t launch_trace_rays(const DevScene& s, const float* orig, const float* dir, int64_t n,

@@ -92,17 +92,16 @@ __device__ __forceinline__ float box_enter(const RayPre& r, float lx, float hx, 
     return tn <= tf * 1.0000005f ? tn : INFINITY;
 }
 
-// Work counters of the instrumented (measurement-only) traversal.
+// Work counters of the measurement builds of the 4-wide walk.
 struct TraceCount {
-    uint32_t nodes = 0;   // node visits (two child-box tests each)
+    uint32_t nodes = 0;   // 4-wide node visits (four child-box tests each)
     uint32_t tris = 0;    // triangle tests
 };
 
-// Closest hit (ANY = false) or any hit among shadow casters (ANY = true).
-// COUNT adds node-visit and triangle-test counters; the product kernels use
-// COUNT = false.
-template <bool ANY, bool COUNT = false>
-__device__ __forceinline__ Hit traverse(const DevScene& s, const RayPre& r, TraceCount* cnt_out = nullptr) {
+// Closest hit (ANY = false) or any hit among shadow casters (ANY = true)
+// over the binary hierarchy, one ray per thread.
+template <bool ANY>
+__device__ __forceinline__ Hit traverse(const DevScene& s, const RayPre& r) {
     Hit h;
     h.t = INFINITY;
     h.orig = -1;
@@ -112,7 +111,6 @@ __device__ __forceinline__ Hit traverse(const DevScene& s, const RayPre& r, Trac
     int sp = 0;
     int node = 0;
     while (true) {
-        if (COUNT) cnt_out->nodes++;
         const float4* N = s.nodes + 4 * (int64_t)node;
         float4 a = __ldg(N), b = __ldg(N + 1), z = __ldg(N + 2);
         int4 m = __ldg(reinterpret_cast<const int4*>(N + 3));
@@ -129,7 +127,6 @@ __device__ __forceinline__ Hit traverse(const DevScene& s, const RayPre& r, Trac
                 const float4* T = s.tris + 3 * (int64_t)k;
                 float4 p0 = __ldg(T), p1 = __ldg(T + 1), p2 = __ldg(T + 2);
                 if (ANY && !(__float_as_int(p1.w) & 1)) continue;
-                if (COUNT) cnt_out->tris++;
                 float t = tri_hit(r, p0, p1, p2);
                 if (t < 0.0f) continue;
                 int orig = __float_as_int(p0.w);
@@ -204,8 +201,9 @@ __device__ __forceinline__ void ww_start(const DevScene& s, WwLane<N>& w, bool v
 template <int N>
 __device__ __forceinline__ int ww_pop(WwLane<N>& w) { return w.sp > 0 ? w.stack[--w.sp] : kDone; }
 
-template <bool ANY, int N>
-__device__ __forceinline__ void ww_leaves(const DevScene& s, const RayPre& r, WwLane<N>& w);
+template <bool ANY, int N, bool COUNT = false>
+__device__ __forceinline__ void ww_leaves(const DevScene& s, const RayPre& r, WwLane<N>& w,
+                                          TraceCount* tc = nullptr);
 
 // One round: descend internal nodes until no lane is still looking for a
 // leaf, then test every parked leaf (and leaves popped right after it).  A
@@ -246,9 +244,9 @@ __device__ __forceinline__ void ww_round(const DevScene& s, const RayPre& r, WwL
 }
 
 // Leaf phase of a round: test the parked leaf and the leaves popped right
-// after it.
-template <bool ANY, int N>
-__device__ __forceinline__ void ww_leaves(const DevScene& s, const RayPre& r, WwLane<N>& w) {
+// after it.  COUNT adds triangle tests to *tc (measurement builds only).
+template <bool ANY, int N, bool COUNT>
+__device__ __forceinline__ void ww_leaves(const DevScene& s, const RayPre& r, WwLane<N>& w, TraceCount* tc) {
     while (w.leaf != kNoLeaf) {
         int code = ~w.leaf;
         int first = code >> kLeafBits, cnt = (code & ((1 << kLeafBits) - 1)) + 1;
@@ -256,6 +254,7 @@ __device__ __forceinline__ void ww_leaves(const DevScene& s, const RayPre& r, Ww
             const float4* T = s.tris + 3 * (int64_t)k;
             float4 p0 = __ldg(T), p1 = __ldg(T + 1), p2 = __ldg(T + 2);
             if (ANY && !(__float_as_int(p1.w) & 1)) continue;
+            if (COUNT) tc->tris++;
             float t = tri_hit(r, p0, p1, p2);
             if (t < 0.0f) continue;
             int orig = __float_as_int(p0.w);
@@ -300,10 +299,12 @@ __device__ __forceinline__ void cx(float& ka, int& va, float& kb, int& vb) {
 // farthest first (closest-hit rays; shadow rays push in slot order, any hit
 // ends them).  Leaves found among the children are parked or pushed as leaf
 // codes exactly as in the binary walk.
-template <bool ANY>
-__device__ __forceinline__ void ww4_round(const DevScene& s, const RayPre& r, WwLane<kStackSize4>& w) {
+template <bool ANY, bool COUNT = false>
+__device__ __forceinline__ void ww4_round(const DevScene& s, const RayPre& r, WwLane<kStackSize4>& w,
+                                          TraceCount* tc = nullptr) {
     while (true) {
         if (w.node >= 0) {
+            if (COUNT) tc->nodes++;
             const float4* N = s.nodes4 + 8 * (int64_t)w.node;
             const float4 lx = __ldg(N), hx = __ldg(N + 1), ly = __ldg(N + 2), hy = __ldg(N + 3);
             const float4 lz = __ldg(N + 4), hz = __ldg(N + 5);
@@ -331,7 +332,7 @@ __device__ __forceinline__ void ww4_round(const DevScene& s, const RayPre& r, Ww
         }
         if (__ballot_sync(0xffffffffu, w.node >= 0 && w.leaf == kNoLeaf) == 0) break;
     }
-    ww_leaves<ANY>(s, r, w);
+    ww_leaves<ANY, kStackSize4, COUNT>(s, r, w, tc);
 }
 
 template <bool ANY>

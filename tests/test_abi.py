@@ -37,6 +37,28 @@ def test_binding_covers_header():
     assert set(_lib.SIGNATURES) == set(declared_functions())
 
 
+def test_binding_array_lengths_match_header():
+    """Fixed-length array parameters (`float ms[8]`) have ctypes arrays of
+    the same length, in the same position."""
+    import ctypes as C
+    from paper_2009_10796_gb300 import _lib
+    src = open(os.path.join(ROOT, "include", "ddgi.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    checked = 0
+    for name, params in re.findall(r"\b(ddgi_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src):
+        if name not in _lib.SIGNATURES:
+            continue
+        argtypes = _lib.SIGNATURES[name][1]
+        for k, prm in enumerate(p.strip() for p in params.split(",")):
+            m = re.search(r"\[(\d+)\]\s*$", prm)
+            if not m:
+                continue
+            t = argtypes[k]
+            assert issubclass(t, C.Array) and t._length_ == int(m.group(1)), (name, k, prm, t)
+            checked += 1
+    assert checked >= 4
+
+
 def test_version_and_error_without_gpu(lib):
     import paper_2009_10796_gb300 as g
     L = g.load()
