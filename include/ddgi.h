@@ -62,7 +62,7 @@ enum {
 
 /* Atlas storage formats (precision variants; the paper does not fix one). */
 enum {
-    DDGI_IRR_FP32 = 0,      /* rgb float32, 12 B / texel */
+    DDGI_IRR_FP32 = 0,      /* rgb float32 + one unused float (0), 16 B / texel */
     DDGI_IRR_FP16 = 1,      /* rgb float16 + pad, 8 B / texel */
     DDGI_IRR_RGB9E5 = 2,    /* shared-exponent 9:9:9:5, 4 B / texel */
     DDGI_DIST_FP32 = 0,     /* (mean, mean square) float32, 8 B / texel */
@@ -78,6 +78,12 @@ enum {
 
 const char* ddgi_last_error(void);
 int32_t     ddgi_version(void);
+
+/* Bytes per texel of an atlas storage format: which 0 irradiance
+ * (DDGI_IRR_*), 1 distance (DDGI_DIST_*).  Returns 0 for an unknown
+ * combination.  Host only; needs no device.  Atlas sizes are
+ * probes x (n + 2)^2 texels of this size. */
+int32_t     ddgi_texel_bytes(int32_t which, int32_t format);
 
 /* ------------------------------------------------------------------ */
 /* Scenes                                                              */
@@ -386,7 +392,8 @@ ddgi_status ddgi_diff_backward(ddgi_volume volume, ddgi_scene scene, const ddgi_
  * whose state the caller owns: states_dev [P] uint8, irr_dev and dist_dev the
  * atlases in the layout and formats of `desc` (what ddgi_get_buffer returns
  * for a volume made from the same descriptor; start from zeroed atlases and
- * states UNINIT, or VIGILANT with the state machine off).  The call allocates
+ * states UNINIT, or VIGILANT with the state machine off); irr_dev 16-byte
+ * and dist_dev 8-byte aligned.  The call allocates
  * nothing: its scratch (ray pattern, weight tables, probe lists, counters,
  * ray records) lives in fixed arrays of the library, about 17 MiB that every
  * GPU loading the library holds until the process exits.

@@ -63,6 +63,7 @@ _ip = C.POINTER(C.c_int32)
 SIGNATURES = {
     "ddgi_last_error": (C.c_char_p, []),
     "ddgi_version": (C.c_int32, []),
+    "ddgi_texel_bytes": (C.c_int32, [C.c_int32, C.c_int32]),
     "ddgi_scene_create": (C.c_int, [_vp, C.c_int64, _vp, C.c_int64, _vp, C.c_int32, _vp, _vp, _vp,
                                     C.c_int32, _vp, C.POINTER(_vp)]),
     "ddgi_scene_destroy": (None, [_vp]),

@@ -201,7 +201,7 @@ class Volume:
         n = self.desc.irr_n + 2
         raw = self.irr_raw(stream)
         if self.desc.irr_format == _lib.IRR_FP32:
-            return raw.view(torch.float32).view(self.n_probes, n, n, 3)
+            return raw.view(torch.float32).view(self.n_probes, n, n, 4)[..., :3]
         if self.desc.irr_format == _lib.IRR_FP16:
             return raw.view(torch.float16).view(self.n_probes, n, n, 4)[..., :3].float()
         return raw.view(torch.int32).view(self.n_probes, n, n)
@@ -331,8 +331,8 @@ class Cascade:
     def _sizes(self, k):
         d = self.descs[k]
         P = d.counts[0] * d.counts[1] * d.counts[2]
-        tb = {0: 12, 1: 8, 2: 4}[d.irr_format]
-        db = {0: 8, 1: 4}[d.dist_format]
+        tb = load().ddgi_texel_bytes(0, int(d.irr_format))
+        db = load().ddgi_texel_bytes(1, int(d.dist_format))
         return P, P * (d.irr_n + 2) ** 2 * tb, P * (d.dist_n + 2) ** 2 * db
 
     def buffer(self, k, which, stream=None):
@@ -348,7 +348,7 @@ class Cascade:
     def irr_atlas(self, k):
         d = self.descs[k]
         n = d.irr_n + 2
-        return self.buffer(k, 0).view(torch.float32).view(-1, n, n, 3)
+        return self.buffer(k, 0).view(torch.float32).view(-1, n, n, 4)[..., :3]
 
     def dist_atlas(self, k):
         d = self.descs[k]

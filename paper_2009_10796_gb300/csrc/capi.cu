@@ -192,6 +192,18 @@ const char* ddgi_last_error(void) { return g_err.c_str(); }
 
 int32_t ddgi_version(void) { return 1; }
 
+int32_t ddgi_texel_bytes(int32_t which, int32_t format) {
+    if (which == 0) {
+        if (format == DDGI_IRR_FP32) return 16;
+        if (format == DDGI_IRR_FP16) return 8;
+        if (format == DDGI_IRR_RGB9E5) return 4;
+    } else if (which == 1) {
+        if (format == DDGI_DIST_FP32) return 8;
+        if (format == DDGI_DIST_FP16) return 4;
+    }
+    return 0;
+}
+
 ddgi_status ddgi_scene_create(const float* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris,
                               const int32_t* tri_object, int32_t n_objects, const float* object_albedo,
                               const int32_t* object_flags, const int32_t* tri_emitter, int32_t n_emitters,
@@ -390,8 +402,8 @@ ddgi_status ddgi_volume_create(const ddgi_volume_desc* desc, ddgi_volume* out) {
         double sx = desc->spacing[0], sy = desc->spacing[1], sz = desc->spacing[2];
         v->t_max = (float)(2.0 * std::sqrt(sx * sx + sy * sy + sz * sz));
     }
-    v->irr_texel_bytes = desc->irr_format == DDGI_IRR_FP32 ? 12 : (desc->irr_format == DDGI_IRR_FP16 ? 8 : 4);
-    v->dist_texel_bytes = desc->dist_format == DDGI_DIST_FP32 ? 8 : 4;
+    v->irr_texel_bytes = (size_t)ddgi_texel_bytes(0, desc->irr_format);
+    v->dist_texel_bytes = (size_t)ddgi_texel_bytes(1, desc->dist_format);
     int64_t ti = (int64_t)(desc->irr_n + 2) * (desc->irr_n + 2);
     int64_t td = (int64_t)(desc->dist_n + 2) * (desc->dist_n + 2);
     v->irr_bytes = (size_t)(v->P * ti) * v->irr_texel_bytes;
@@ -930,8 +942,8 @@ ddgi_status ddgi_cascade_create(const ddgi_volume_desc* descs, int32_t n, ddgi_c
         c->total += c->P[k];
         double sx = d.spacing[0], sy = d.spacing[1], sz = d.spacing[2];
         c->t_max[k] = d.t_max >= 0.0f ? d.t_max : (float)(2.0 * std::sqrt(sx * sx + sy * sy + sz * sz));
-        size_t tb = d.irr_format == DDGI_IRR_FP32 ? 12 : (d.irr_format == DDGI_IRR_FP16 ? 8 : 4);
-        size_t db = d.dist_format == DDGI_DIST_FP32 ? 8 : 4;
+        size_t tb = (size_t)ddgi_texel_bytes(0, d.irr_format);
+        size_t db = (size_t)ddgi_texel_bytes(1, d.dist_format);
         c->irr_bytes[k] = (size_t)c->P[k] * (d.irr_n + 2) * (d.irr_n + 2) * tb;
         c->dist_bytes[k] = (size_t)c->P[k] * (d.dist_n + 2) * (d.dist_n + 2) * db;
         for (int a = 0; a < 3; ++a) c->origin[k][a] = d.origin[a];

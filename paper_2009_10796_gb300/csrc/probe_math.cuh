@@ -104,7 +104,8 @@ __device__ __forceinline__ Footprint footprint(float2 u, int n) {
 }
 
 // ---- texel storage formats -------------------------------------------------
-// Irradiance FP32: 3 floats per texel.  FP16: 4 halves (rgb + pad).
+// Irradiance FP32: 4 floats per texel (rgb + an unused 0), one 16-byte load.
+// FP16: 4 halves (rgb + pad).
 // RGB9E5: one 32-bit word, 9-bit mantissas with a shared 5-bit exponent
 // (bias 15), as in the OpenGL EXT_texture_shared_exponent specification.
 
@@ -146,13 +147,15 @@ template <bool NC>
 __device__ __forceinline__ uint2 ld(const uint2* p) { if (NC) return __ldg(p); else return *p; }
 template <bool NC>
 __device__ __forceinline__ float2 ld(const float2* p) { if (NC) return __ldg(p); else return *p; }
+template <bool NC>
+__device__ __forceinline__ float4 ld(const float4* p) { if (NC) return __ldg(p); else return *p; }
 
 template <bool NC = true>
 __device__ __forceinline__ float3 load_irr(const VolView& v, int p, int x, int y) {
     int64_t t = (int64_t)p * v.irr_tile + (int64_t)y * (v.irr_n + 2) + x;
     if (v.irr_format == DDGI_IRR_FP32) {
-        const float* a = (const float*)v.irr + 3 * t;
-        return f3(ld<NC>(a), ld<NC>(a + 1), ld<NC>(a + 2));
+        const float4 a = ld<NC>((const float4*)v.irr + t);
+        return f3(a.x, a.y, a.z);
     } else if (v.irr_format == DDGI_IRR_FP16) {
         uint2 w = ld<NC>((const uint2*)v.irr + t);
         __half2 h0 = *reinterpret_cast<__half2*>(&w.x);
@@ -167,8 +170,7 @@ __device__ __forceinline__ float3 load_irr(const VolView& v, int p, int x, int y
 __device__ __forceinline__ void store_irr(const VolView& v, int p, int x, int y, float3 c) {
     int64_t t = (int64_t)p * v.irr_tile + (int64_t)y * (v.irr_n + 2) + x;
     if (v.irr_format == DDGI_IRR_FP32) {
-        float* a = (float*)v.irr + 3 * t;
-        a[0] = c.x; a[1] = c.y; a[2] = c.z;
+        ((float4*)v.irr)[t] = make_float4(c.x, c.y, c.z, 0.0f);
     } else if (v.irr_format == DDGI_IRR_FP16) {
         __half2 h0 = __floats2half2_rn(c.x, c.y);
         __half2 h1 = __floats2half2_rn(c.z, 0.0f);
@@ -216,10 +218,10 @@ __device__ __forceinline__ float3 sample_irr_at(const VolView& v, int p, const F
     const int row = v.irr_n + 2;
     const int64_t t = (int64_t)p * v.irr_tile + (int64_t)f.y0 * row + f.x0;
     if (v.irr_format == DDGI_IRR_FP32) {
-        const float* a = (const float*)v.irr + 3 * t;
-        const float* c = a + 3 * row;
-        return bilerp3(f, f3(__ldg(a), __ldg(a + 1), __ldg(a + 2)), f3(__ldg(a + 3), __ldg(a + 4), __ldg(a + 5)),
-                       f3(__ldg(c), __ldg(c + 1), __ldg(c + 2)), f3(__ldg(c + 3), __ldg(c + 4), __ldg(c + 5)));
+        const float4* a = (const float4*)v.irr + t;
+        const float4 q00 = __ldg(a), q10 = __ldg(a + 1), q01 = __ldg(a + row), q11 = __ldg(a + row + 1);
+        return bilerp3(f, f3(q00.x, q00.y, q00.z), f3(q10.x, q10.y, q10.z), f3(q01.x, q01.y, q01.z),
+                       f3(q11.x, q11.y, q11.z));
     }
     return bilerp3(f, load_irr(v, p, f.x0, f.y0), load_irr(v, p, f.x0 + 1, f.y0), load_irr(v, p, f.x0, f.y0 + 1),
                    load_irr(v, p, f.x0 + 1, f.y0 + 1));

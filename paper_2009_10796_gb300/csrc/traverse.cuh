@@ -19,6 +19,7 @@ struct RayPre {
     float3 o, d, idir;
     int kx, ky, kz;
     float Sx, Sy, Sz;
+    int oct;    // bit a set: axis a runs toward -inf (its near slab plane is the box's hi)
 };
 
 __device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
@@ -43,7 +44,20 @@ __device__ __forceinline__ RayPre ray_pre(float3 o, float3 d) {
     r.idir = f3(1.0f / (fabsf(d.x) > eps ? d.x : copysignf(eps, d.x)),
                 1.0f / (fabsf(d.y) > eps ? d.y : copysignf(eps, d.y)),
                 1.0f / (fabsf(d.z) > eps ? d.z : copysignf(eps, d.z)));
+    r.oct = (signbit(r.idir.x) ? 1 : 0) | (signbit(r.idir.y) ? 2 : 0) | (signbit(r.idir.z) ? 4 : 0);
     return r;
+}
+
+// Three-input minimum / maximum (one PTX instruction on sm_100 and later).
+__device__ __forceinline__ float fmin3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float fmax3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
 }
 
 // Returns t of a hit in (0, inf) or -1.
@@ -89,6 +103,17 @@ __device__ __forceinline__ float box_enter(const RayPre& r, float lx, float hx, 
     float t0z = (lz - r.o.z) * r.idir.z, t1z = (hz - r.o.z) * r.idir.z;
     float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.0f));
     float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tmax));
+    return tn <= tf * 1.0000005f ? tn : INFINITY;
+}
+
+// Slab test with the near and far planes already chosen by the ray's octant
+// (nx = the box's lo.x when the ray runs toward +x, its hi.x otherwise, and
+// so on): the same entry distance as box_enter, since per axis the near-plane
+// distance is exactly the smaller of the two, without the per-axis min/max.
+__device__ __forceinline__ float box_enter_oct(const RayPre& r, float nx, float fx, float ny, float fy, float nz,
+                                               float fz, float tmax) {
+    float tn = fmax3f((nx - r.o.x) * r.idir.x, (ny - r.o.y) * r.idir.y, fmaxf((nz - r.o.z) * r.idir.z, 0.0f));
+    float tf = fmin3f((fx - r.o.x) * r.idir.x, (fy - r.o.y) * r.idir.y, fminf((fz - r.o.z) * r.idir.z, tmax));
     return tn <= tf * 1.0000005f ? tn : INFINITY;
 }
 
@@ -306,13 +331,17 @@ __device__ __forceinline__ void ww4_round(const DevScene& s, const RayPre& r, Ww
         if (w.node >= 0) {
             if (COUNT) tc->nodes++;
             const float4* N = s.nodes4 + 8 * (int64_t)w.node;
-            const float4 lx = __ldg(N), hx = __ldg(N + 1), ly = __ldg(N + 2), hy = __ldg(N + 3);
-            const float4 lz = __ldg(N + 4), hz = __ldg(N + 5);
+            // near / far planes per axis by the ray's octant: lo and hi swap for
+            // an axis the ray runs down
+            const int ax = r.oct & 1, ay = (r.oct >> 1) & 1, az = (r.oct >> 2) & 1;
+            const float4 nx = __ldg(N + ax), fx = __ldg(N + (ax ^ 1));
+            const float4 ny = __ldg(N + 2 + ay), fy = __ldg(N + 2 + (ay ^ 1));
+            const float4 nz = __ldg(N + 4 + az), fz = __ldg(N + 4 + (az ^ 1));
             const int4 ref = __ldg(reinterpret_cast<const int4*>(N + 6));
-            float k0 = box_enter(r, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, w.h.t);
-            float k1 = box_enter(r, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, w.h.t);
-            float k2 = box_enter(r, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, w.h.t);
-            float k3 = box_enter(r, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, w.h.t);
+            float k0 = box_enter_oct(r, nx.x, fx.x, ny.x, fy.x, nz.x, fz.x, w.h.t);
+            float k1 = box_enter_oct(r, nx.y, fx.y, ny.y, fy.y, nz.y, fz.y, w.h.t);
+            float k2 = box_enter_oct(r, nx.z, fx.z, ny.z, fy.z, nz.z, fz.z, w.h.t);
+            float k3 = box_enter_oct(r, nx.w, fx.w, ny.w, fy.w, nz.w, fz.w, w.h.t);
             int v0 = ref.x, v1 = ref.y, v2 = ref.z, v3 = ref.w;
             if (!ANY) {
                 cx(k0, v0, k1, v1);

@@ -70,6 +70,14 @@ def test_version_and_error_without_gpu(lib):
     assert b"NULL" in L.ddgi_last_error()
 
 
+def test_texel_bytes_without_gpu(lib):
+    import paper_2009_10796_gb300 as g
+    L = g.load()
+    assert [L.ddgi_texel_bytes(0, f) for f in (g.IRR_FP32, g.IRR_FP16, g.IRR_RGB9E5)] == [16, 8, 4]
+    assert [L.ddgi_texel_bytes(1, f) for f in (g.DIST_FP32, g.DIST_FP16)] == [8, 4]
+    assert L.ddgi_texel_bytes(0, 7) == 0 and L.ddgi_texel_bytes(2, 0) == 0
+
+
 def test_struct_layouts_match_header(tmp_path):
     """ctypes structs mirror the C structs: compare with what gcc lays out."""
     import ctypes as C
