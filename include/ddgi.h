@@ -114,6 +114,20 @@ void ddgi_scene_destroy(ddgi_scene scene);
 /* Size of the uploaded hierarchy: node count, leaf count, triangle count. */
 ddgi_status ddgi_scene_info(ddgi_scene scene, int64_t* n_nodes, int64_t* n_leaves, int64_t* n_tris);
 
+/* Host-only check of the bounding volume hierarchy that ddgi_scene_create
+ * would build for these triangles (no counterpart in the paper; a
+ * diagnostic that needs no GPU).  Builds the binary SAH tree and its 4-wide
+ * collapse on the host and walks the 4-wide form, writing
+ *   stats[0] binary nodes, [1] 4-wide nodes, [2] leaves, [3] binary depth,
+ *   [4] 4-wide depth, [5] deepest stack a walk that pushes every child
+ *   needs, [6] empty child slots, [7] violations: a reference out of range,
+ *   a child box not inside its parent's, a triangle outside its leaf's box,
+ *   or a triangle reached other than exactly once, [8] triangles.
+ * verts [n_verts][3] float, tris [n_tris][3] int32 (host).  Errors:
+ * INVALID_ARG as in ddgi_scene_create. */
+ddgi_status ddgi_bvh_check(const float* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris,
+                           int64_t stats[9]);
+
 /* Closest hit of n arbitrary rays, t in (0, inf) (the traversal used by the
  * probe update, Sec. 2.3).  orig_dev, dir_dev: [n][3] float.  Outputs:
  * t_dev [n] float (+inf on a miss), tri_dev [n] int32 original triangle

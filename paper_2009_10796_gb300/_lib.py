@@ -68,6 +68,7 @@ SIGNATURES = {
                                     C.c_int32, _vp, C.POINTER(_vp)]),
     "ddgi_scene_destroy": (None, [_vp]),
     "ddgi_scene_info": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "ddgi_bvh_check": (C.c_int, [_vp, C.c_int64, _vp, C.c_int64, C.c_int64 * 9]),
     "ddgi_trace": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _vp, _vp, _vp]),
     "ddgi_raycast_gbuffer": (C.c_int, [_vp, F3, F3, F3, C.c_float, C.c_int32, C.c_int32, _vp, _vp, _vp]),
     "ddgi_volume_create": (C.c_int, [C.POINTER(VolumeDesc), C.POINTER(_vp)]),

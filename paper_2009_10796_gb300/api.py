@@ -15,7 +15,8 @@ import torch
 from . import _lib
 from ._lib import check, load
 
-__all__ = ["Scene", "Volume", "Cascade", "IrradianceField", "trace", "lights_struct", "update_noalloc"]
+__all__ = ["Scene", "Volume", "Cascade", "IrradianceField", "trace", "lights_struct", "update_noalloc",
+           "bvh_check"]
 
 
 def _stream(stream):
@@ -46,6 +47,18 @@ def lights_struct(lights) -> _lib.Lights:
     """Any object with sun_dir, sun_irradiance, sky_a, sky_b, sky_up."""
     return _lib.Lights(_f3(lights.sun_dir), _f3(lights.sun_irradiance), _f3(lights.sky_a),
                        _f3(lights.sky_b), _f3(lights.sky_up))
+
+
+def bvh_check(verts, tris) -> dict:
+    """Host-only check of the hierarchy a scene of these triangles gets
+    (``ddgi_bvh_check``): sizes, depths, stack bound and violations."""
+    v = _np(verts, np.float32).reshape(-1, 3)
+    t = _np(tris, np.int32).reshape(-1, 3)
+    st = (C.c_int64 * 9)()
+    check(load().ddgi_bvh_check(v.ctypes.data if len(v) else None, len(v), t.ctypes.data if len(t) else None,
+                                len(t), st))
+    keys = ["nodes", "nodes4", "leaves", "depth", "depth4", "max_stack", "empty_slots", "violations", "tris"]
+    return {k: int(st[i]) for i, k in enumerate(keys)}
 
 
 class Scene:

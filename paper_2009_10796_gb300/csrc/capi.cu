@@ -300,6 +300,77 @@ const DevScene* scene_device_view(ddgi_scene s) { return s ? &s->dev : nullptr; 
 
 extern "C" {
 
+ddgi_status ddgi_bvh_check(const float* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris,
+                           int64_t stats[9]) {
+    if (!stats) return fail(DDGI_ERR_INVALID_ARG, "stats is NULL");
+    if (n_verts < 0 || n_tris < 0 || n_tris > DDGI_MAX_TRIS) return fail(DDGI_ERR_INVALID_ARG, "bad count");
+    if (n_tris > 0 && (!verts || !tris)) return fail(DDGI_ERR_INVALID_ARG, "NULL triangle arrays");
+    BvhHost bvh;
+    std::string err;
+    if (!build_bvh(verts, n_verts, tris, n_tris, nullptr, bvh, err)) return fail(DDGI_ERR_INVALID_ARG, err);
+    for (int k = 0; k < 9; ++k) stats[k] = 0;
+    const int64_t n4 = (int64_t)(bvh.nodes4.size() / 8);
+    stats[0] = (int64_t)(bvh.nodes.size() / 4);
+    stats[1] = n4;
+    stats[2] = bvh.n_leaves;
+    stats[3] = bvh.max_depth;
+    stats[4] = bvh.max_depth4;
+    stats[8] = n_tris;
+    if (n4 == 0) return DDGI_OK;
+    struct Item {
+        int32_t ref;
+        float lo[3], hi[3];
+    };
+    std::vector<int32_t> seen((size_t)n_tris, 0);
+    std::vector<Item> stack;
+    stack.push_back({0, {-INFINITY, -INFINITY, -INFINITY}, {INFINITY, INFINITY, INFINITY}});
+    int64_t bad = 0, deepest = 0;
+    while (!stack.empty()) {
+        Item it = stack.back();
+        stack.pop_back();
+        if (it.ref >= 0) {
+            if (it.ref >= n4) { bad++; continue; }
+            const float4* N = &bvh.nodes4[8 * (size_t)it.ref];
+            int32_t ref[4];
+            std::memcpy(ref, &N[6], sizeof(ref));
+            const float* lo[3] = {&N[0].x, &N[2].x, &N[4].x};
+            const float* hi[3] = {&N[1].x, &N[3].x, &N[5].x};
+            for (int c = 0; c < 4; ++c) {
+                if (ref[c] == kRefDone) {
+                    stats[6]++;
+                    continue;
+                }
+                Item k;
+                k.ref = ref[c];
+                for (int a = 0; a < 3; ++a) {
+                    k.lo[a] = lo[a][c];
+                    k.hi[a] = hi[a][c];
+                    if (k.lo[a] < it.lo[a] || k.hi[a] > it.hi[a] || k.lo[a] > k.hi[a]) bad++;
+                }
+                stack.push_back(k);
+            }
+            deepest = std::max<int64_t>(deepest, (int64_t)stack.size());
+        } else {
+            const int code = ~it.ref;
+            const int first = code >> kLeafBits, cnt = (code & ((1 << kLeafBits) - 1)) + 1;
+            if (first < 0 || (int64_t)first + cnt > n_tris) { bad++; continue; }
+            for (int k = first; k < first + cnt; ++k) {
+                seen[(size_t)k]++;
+                const float* p[3] = {&bvh.tris[3 * (size_t)k].x, &bvh.tris[3 * (size_t)k + 1].x,
+                                     &bvh.tris[3 * (size_t)k + 2].x};
+                for (int q = 0; q < 3; ++q)
+                    for (int a = 0; a < 3; ++a)
+                        if (p[q][a] < it.lo[a] || p[q][a] > it.hi[a]) bad++;
+            }
+        }
+    }
+    for (int32_t c : seen)
+        if (c != 1) bad++;
+    stats[5] = deepest;
+    stats[7] = bad;
+    return DDGI_OK;
+}
+
 ddgi_status ddgi_scene_info(ddgi_scene s, int64_t* n_nodes, int64_t* n_leaves, int64_t* n_tris) {
     if (!s) return fail(DDGI_ERR_INVALID_ARG, "scene is NULL");
     if (n_nodes) *n_nodes = s->n_nodes;

@@ -28,18 +28,24 @@ namespace ddgi {
 
 namespace {
 
-__device__ double sf_component(int i, int n, int axis) {
+// All three components of sf(i, n) at once (one sincos, one square root).
+__device__ void sf_dir(int i, int n, double v[3]) {
     const double inv_phi = 0.61803398874989484820;
     double a = (double)i * inv_phi;
     double phi = 6.283185307179586477 * (a - floor(a));
     double z = 1.0 - (2.0 * i + 1.0) / (double)n;
     double r = sqrt(fmax(0.0, 1.0 - z * z));
-    return axis == 0 ? cos(phi) * r : (axis == 1 ? sin(phi) * r : z);
+    double sp, cp;
+    sincos(phi, &sp, &cp);
+    v[0] = cp * r;
+    v[1] = sp * r;
+    v[2] = z;
 }
 
 __device__ void frame_dir(const FrameRot& rot, int i, int n, double out[3]) {
-    double s0 = sf_component(i, n, 0), s1 = sf_component(i, n, 1), s2 = sf_component(i, n, 2);
-    for (int a = 0; a < 3; ++a) out[a] = rot.m[3 * a] * s0 + rot.m[3 * a + 1] * s1 + rot.m[3 * a + 2] * s2;
+    double sv[3];
+    sf_dir(i, n, sv);
+    for (int a = 0; a < 3; ++a) out[a] = rot.m[3 * a] * sv[0] + rot.m[3 * a + 1] * sv[1] + rot.m[3 * a + 2] * sv[2];
 }
 
 __device__ void texel_dir(int t, int n, double v[3]) {
@@ -63,7 +69,7 @@ __device__ void texel_dir(int t, int n, double v[3]) {
 // weights.  ROT_DEV: the rotation is read from device memory (per-frame
 // parameters written before a captured graph replays).
 template <bool ROT_DEV>
-__global__ void __launch_bounds__(64) k_frame_dirs(FrameRot rot_arg, const FrameRot* rot_dev, int R, float4* dirs,
+__global__ void __launch_bounds__(32) k_frame_dirs(FrameRot rot_arg, const FrameRot* rot_dev, int R, float4* dirs,
                                                    double* dirs64) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= R) return;
@@ -98,12 +104,14 @@ __global__ void __launch_bounds__(256) k_frame_weights(int R, int irr_n, int dis
                                                        const double* __restrict__ dirs64, float* w_irr,
                                                        float* inv_s_irr, float* w_dist, float* inv_s_dist) {
     __shared__ double red[256];
+    __shared__ double s_nt[3];
     const int b = blockIdx.x;
     const int ti = irr_n * irr_n;
     const bool is_irr = b < ti;
     const int t = is_irr ? b : b - ti;
-    double nt[3];
-    texel_dir(t, is_irr ? irr_n : dist_n, nt);
+    if (threadIdx.x == 0) texel_dir(t, is_irr ? irr_n : dist_n, s_nt);   // once per block: FP64 is slow here
+    __syncthreads();
+    const double nt[3] = {s_nt[0], s_nt[1], s_nt[2]};
     double acc = 0.0;
     for (int i = threadIdx.x; i < R; i += blockDim.x) {
         double c = fmax(0.0, nt[0] * dirs64[3 * i] + nt[1] * dirs64[3 * i + 1] + nt[2] * dirs64[3 * i + 2]);
@@ -463,7 +471,7 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, B
 cudaError_t launch_frame_setup(const FrameRot& rot, int R, int irr_n, int dist_n, float cos_power,
                                float4* dirs, double* dirs64, float* w_irr, float* inv_s_irr, float* w_dist,
                                float* inv_s_dist, cudaStream_t st) {
-    k_frame_dirs<false><<<(R + 63) / 64, 64, 0, st>>>(rot, nullptr, R, dirs, dirs64);
+    k_frame_dirs<false><<<(R + 31) / 32, 32, 0, st>>>(rot, nullptr, R, dirs, dirs64);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_frame_weights<<<irr_n * irr_n + dist_n * dist_n, 256, 0, st>>>(R, irr_n, dist_n, (double)cos_power, dirs64,
@@ -474,7 +482,7 @@ cudaError_t launch_frame_setup(const FrameRot& rot, int R, int irr_n, int dist_n
 cudaError_t launch_frame_setup_dev(const FrameRot* rot_dev, int R, int irr_n, int dist_n, float cos_power,
                                    float4* dirs, double* dirs64, float* w_irr, float* inv_s_irr, float* w_dist,
                                    float* inv_s_dist, cudaStream_t st) {
-    k_frame_dirs<true><<<(R + 63) / 64, 64, 0, st>>>(FrameRot{}, rot_dev, R, dirs, dirs64);
+    k_frame_dirs<true><<<(R + 31) / 32, 32, 0, st>>>(FrameRot{}, rot_dev, R, dirs, dirs64);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_frame_weights<<<irr_n * irr_n + dist_n * dist_n, 256, 0, st>>>(R, irr_n, dist_n, (double)cos_power, dirs64,
