@@ -229,6 +229,9 @@ static TiledShape tiled_shape(int PG, int R, int irr_n, int dist_n) {
     t.irr_units = t.nqi * (PG / 2);
     t.threads = t.dist_threads + (t.irr_units + 31) / 32 * 32;
     t.smem = sizeof(float) * ((size_t)4 * PG * (R + 4) + (size_t)2 * 4 * (t.nqd + t.nqi) * kTileWS);
+    // the epilogue reuses the same shared memory for the weighted sums
+    const size_t sums = sizeof(float) * (size_t)PG * (2 * dist_n * dist_n + 3 * irr_n * irr_n);
+    if (sums > t.smem) t.smem = sums;
     return t;
 }
 
@@ -248,8 +251,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // (u' < irr_units) owns irradiance texels tq + a * nqi of probes 2 pq,
 // 2 pq + 1.  Striding the texels by nqd (not 4) puts a warp's weight rows on
 // distinct banks.  The next weight chunk is in flight (asynchronous copy)
-// while the current one is summed; the old texel values are fetched all at
-// once before the blend.
+// while the current one is summed; the blend epilogue runs over the sums in
+// shared memory.
 template <bool MULTI, int PG>
 __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, BlendParams bp,
                                                                     const float* __restrict__ w_irr,
@@ -404,60 +407,52 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, B
             }
             __syncthreads();   // this chunk's buffer is refilled two chunks later
         }
+        // the sums go to shared memory (records and weights are consumed), then
+        // every thread blends texels in a short rolled loop, consecutive threads
+        // on consecutive texels of one probe: the blend code is fetched once per
+        // loop, not once per unrolled output
+        float* sum_d = sm;                    // [PG][td] x (m1, m2)
+        float* sum_i = sm + 2 * PG * td;      // [PG][ti] x (r, g, b)
         if (is_dist) {
-            float2 old[16];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int t = tq + a * nqd, pp = 4 * pq + b;
-                    old[a * 4 + b] = make_float2(0.0f, 0.0f);
-                    if (t < td && pp < np) {
-                        const int e = s_probe[pp];
-                        old[a * 4 + b] = dist_texel_old(vol_of<MULTI>(vs, e >> kEntryShift), e & kEntryMask, t);
-                    }
-                }
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 const int t = tq + a * nqd;
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int pp = 4 * pq + b;
-                    if (t < td && pp < np) {
-                        const int e = s_probe[pp];
-                        blend_dist_texel_from(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, t,
-                                              acc[a * 4 + b], acc[16 + a * 4 + b], __ldg(inv_s_dist + t),
-                                              s_newly[pp] != 0, status, old[a * 4 + b]);
+                for (int b = 0; b < 4; ++b)
+                    if (t < td) {
+                        const int o = (4 * pq + b) * td + t;
+                        sum_d[2 * o] = acc[a * 4 + b];
+                        sum_d[2 * o + 1] = acc[16 + a * 4 + b];
                     }
-                }
             }
         } else if (is_irr) {
-            float3 old[8];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const int t = tq + a * nqi, pp = 2 * pq + b;
-                    old[a * 2 + b] = f3(0.0f, 0.0f, 0.0f);
-                    if (t < ti && pp < np) {
-                        const int e = s_probe[pp];
-                        old[a * 2 + b] = irr_texel_old(vol_of<MULTI>(vs, e >> kEntryShift), e & kEntryMask, t);
-                    }
-                }
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 const int t = tq + a * nqi;
 #pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const int pp = 2 * pq + b;
-                    if (t < ti && pp < np) {
-                        const int e = s_probe[pp];
-                        blend_irr_texel_from(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, t,
-                                             acc[a * 2 + b], acc[8 + a * 2 + b], acc[16 + a * 2 + b],
-                                             __ldg(inv_s_irr + t), s_newly[pp] != 0, status, old[a * 2 + b]);
+                for (int b = 0; b < 2; ++b)
+                    if (t < ti) {
+                        const int o = (2 * pq + b) * ti + t;
+                        sum_i[3 * o] = acc[a * 2 + b];
+                        sum_i[3 * o + 1] = acc[8 + a * 2 + b];
+                        sum_i[3 * o + 2] = acc[16 + a * 2 + b];
                     }
-                }
             }
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int o = threadIdx.x; o < np * td; o += blockDim.x) {
+            const int pp = o / td, t = o - pp * td;
+            const int e = s_probe[pp];
+            blend_dist_texel(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, t, sum_d[2 * o],
+                             sum_d[2 * o + 1], __ldg(inv_s_dist + t), s_newly[pp] != 0, status);
+        }
+#pragma unroll 2
+        for (int o = threadIdx.x; o < np * ti; o += blockDim.x) {
+            const int pp = o / ti, t = o - pp * ti;
+            const int e = s_probe[pp];
+            blend_irr_texel(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, t, sum_i[3 * o],
+                            sum_i[3 * o + 1], sum_i[3 * o + 2], __ldg(inv_s_irr + t), s_newly[pp] != 0, status);
         }
         __syncthreads();
         if (threadIdx.x < np && s_newly[threadIdx.x]) {
