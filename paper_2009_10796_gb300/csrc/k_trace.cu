@@ -187,7 +187,9 @@ __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Li
     bool exhausted = false;
     float3 d = f3(0.0f, 0.0f, 1.0f);
     RayPre r = ray_pre(f3(0.0f, 0.0f, 0.0f), d);
+    int stack[kStackSize4];
     WwLane<kStackSize4> w;
+    w.stack = stack;
     ww_start(s, w, false);
     while (true) {
         int64_t item = refill(next, total, rec < 0, exhausted);
@@ -276,7 +278,9 @@ __global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolSet vs, Lig
     int64_t rec = -1;
     bool exhausted = false;
     RayPre r = ray_pre(f3(0.0f, 0.0f, 0.0f), tol);
+    int stack[kStackSize4];
     WwLane<kStackSize4> w;
+    w.stack = stack;
     ww_start(s, w, false);
     while (true) {
         int64_t item = refill(next, total, rec < 0, exhausted);

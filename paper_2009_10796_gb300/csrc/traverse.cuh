@@ -203,10 +203,12 @@ constexpr int kDone = kRefDone;         // empty-stack sentinel, below every lea
 
 __device__ __forceinline__ int leaf_code(int child, int cnt) { return ~(((~child) << kLeafBits) | (cnt - 1)); }
 
-// Per-lane state of the warp-cooperative walk.
+// Per-lane state of the warp-cooperative walk.  The stack array lives
+// apart from the scalar fields (a pointer to the caller's local array), so
+// the fields stay in registers while only the array goes to local memory.
 template <int N = kStackSize>
 struct WwLane {
-    int stack[N];
+    int* stack;   // N entries
     int sp;
     int node;   // next internal node, a leaf code taken from the stack, or kDone
     int leaf;   // parked leaf code or kNoLeaf
@@ -366,7 +368,9 @@ __device__ __forceinline__ void ww4_round(const DevScene& s, const RayPre& r, Ww
 
 template <bool ANY>
 __device__ __forceinline__ Hit traverse_ww(const DevScene& s, const RayPre& r, bool valid) {
+    int stack[kStackSize];
     WwLane<> w;
+    w.stack = stack;
     ww_start(s, w, valid);
     do {
         ww_round<ANY>(s, r, w);
