@@ -355,6 +355,24 @@ def run_gpu(args):
     q_bytes = n_pix * 36                                  # positions + normals in, irradiance out
     hbm = pk.get("hbm_gbs", 6800.0)
 
+    # second-order glossy lookups (Sec. 4.4) at the G-buffer points, the camera
+    # rays standing in for the reflection rays that reached them
+    gdirs = pos - torch.tensor(np.asarray(camera, np.float32), device=dev)
+    gdirs = gdirs / gdirs.norm(dim=1, keepdim=True).clamp_min(1e-12)
+    gout = torch.empty_like(pos)
+    for _ in range(args.warmup):
+        vol.query_glossy(pos, nrm, gdirs, gout, stream=stream)
+    gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        gev[k][0].record(stream)
+        vol.query_glossy(pos, nrm, gdirs, gout, stream=stream)
+        gev[k][1].record(stream)
+    torch.cuda.synchronize()
+    glossy_ms = float(np.mean([a.elapsed_time(b) for a, b in gev]))
+
+    paper_res = None if args.no_paper_res else run_paper_resolution(args, g, torch, stream, scene, L, pos, nrm,
+                                                                     camera, flush)
     cascade = None if args.no_cascade else run_cascade(args, g, torch, stream)
     diff = None if args.no_diff else run_diff(args, g, torch, stream)
 
@@ -379,7 +397,7 @@ def run_gpu(args):
                    "rays_per_probe": R, "query_pixels": n_pix,
                    "l2": "flushed between timed steps (256 MiB write outside the events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "update_ms_per_frame": ms - q_ms, "query_ms_1080p": q_ms,
+        "update_ms_per_frame": ms - q_ms, "query_ms_1080p": q_ms, "glossy_query_ms_1080p": glossy_ms,
         "trace_grays_per_s": rays_per_step / (trace_ms_avg * 1e-3) / 1e9,
         "stage_ms": {k: v[0] / max(v[1], 1) for k, v in timings.items()},
         "wall_ms_per_step": 1e3 * wall / args.steps,
@@ -410,6 +428,7 @@ def run_gpu(args):
             "blend_tensor_tflops": blend_flops / (mixed[2]["blend"][0] / max(mixed[2]["blend"][1], 1) * 1e-3)
                                    / 1e12,
             "frame_setup_ms": mixed[2]["frame_setup"][0] / max(mixed[2]["frame_setup"][1], 1)},
+        "paper_resolution": paper_res,
         "cascade_batched": cascade,
         "differentiation": diff,
         "cpu_baseline": cpu,
@@ -456,6 +475,39 @@ def run_cascade(args, g, torch, stream):
             "ms_per_frame": ms, "grays_per_s": rays / (ms * 1e-3) / 1e9, "active_probes": active,
             "graph": True, "tuning": {"trace_blocks_per_sm": C.tuning()[0], "blend_probes_per_cta": C.tuning()[1],
                                       "from_cache": from_cache}}
+
+
+def run_paper_resolution(args, g, torch, stream, scene, L, pos, nrm, camera, flush):
+    """The same city step with the paper's tile resolution: 8x8 irradiance and
+    16x16 visibility interiors (Sec. 7.1), FP32 blend."""
+    desc = synth.city_volume(irr_n=8, dist_n=16)
+    vol = g.Volume(desc)
+    out = torch.empty_like(pos)
+    frame = 0
+    for _ in range(args.warmup):
+        vol.update(scene, L, frame, stream=stream)
+        vol.query(pos, nrm, camera, out, stream=stream)
+        frame += 1
+    torch.cuda.synchronize()
+    n_active = int((vol.states() == g.STATE_VIGILANT).sum().item())
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    vol.read_timings()
+    vol.enable_timing(True)
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        evs[k][0].record(stream)
+        vol.update(scene, L, frame, stream=stream)
+        vol.query(pos, nrm, camera, out, stream=stream)
+        evs[k][1].record(stream)
+        frame += 1
+    torch.cuda.synchronize()
+    tm = vol.read_timings()
+    vol.enable_timing(False)
+    vol.poll_status()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    return {"workload": "city, 8x8 irradiance / 16x16 visibility interiors, FP32 blend",
+            "ms_per_step": ms, "grays_per_s": n_active * desc.rays_per_probe / (ms * 1e-3) / 1e9,
+            "blend_ms": tm["blend"][0] / max(tm["blend"][1], 1), "active_probes": n_active}
 
 
 def run_diff(args, g, torch, stream):
@@ -514,6 +566,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the TF32 tensor-core blend timing")
     ap.add_argument("--no-cascade", action="store_true", help="skip the batched cascade workload")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation workload")
+    ap.add_argument("--no-paper-res", action="store_true", help="skip the paper-resolution tile variant")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

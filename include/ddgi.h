@@ -252,6 +252,17 @@ ddgi_status ddgi_update_range(ddgi_volume volume, ddgi_scene scene, const ddgi_l
 ddgi_status ddgi_query(ddgi_volume volume, const float* pos_dev, const float* nrm_dev, int64_t n,
                        const float camera_pos[3], float* out_dev, ddgi_stream stream);
 
+/* Second-order glossy lookup (Sec. 4.4): the probes reused as prefiltered
+ * radiance at reflection-ray hits.  pos_dev, nrm_dev: [n][3] float hit
+ * points and unit normals; dir_dev: [n][3] float unit directions the hits
+ * were reached along (the reflection rays).  out_dev [n][3] float gets M,
+ * the cosine-weighted mean radiance read in the mirror direction
+ * r = d - 2 (d.n) n, in radiance units (ddgi_query returns pi M); the
+ * self-shadow bias uses n and -d.  A zero normal gives 0.  Errors as
+ * ddgi_query. */
+ddgi_status ddgi_query_glossy(ddgi_volume volume, const float* pos_dev, const float* nrm_dev,
+                              const float* dir_dev, int64_t n, float* out_dev, ddgi_stream stream);
+
 /* Copy out device state (asynchronous, device to device).
  *   which 0: irradiance atlas, [P][(irr_n+2)^2] texels in irr_format
  *   which 1: distance atlas,   [P][(dist_n+2)^2] texels in dist_format

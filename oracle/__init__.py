@@ -124,6 +124,7 @@ def _declare(lib):
                               C.c_int64, C.c_double, C.c_double, _u8p, _dp, _dp, C.c_int64,
                               _i64p, _dp]
     lib.or_query.argtypes = [C.POINTER(OrVolume), _u8p, _dp, _dp, C.c_int64, _dp, _dp, _dp, _dp, _dp]
+    lib.or_query_glossy.argtypes = [C.POINTER(OrVolume), _u8p, _dp, _dp, C.c_int64, _dp, _dp, _dp, _dp]
     lib.or_query_cascade.argtypes = [C.c_int64, C.POINTER(OrVolume), C.POINTER(_u8p),
                                      C.POINTER(_dp), C.POINTER(_dp), C.c_int64, _dp, _dp, _dp,
                                      _dp, _dp]
@@ -349,6 +350,21 @@ def query(desc, states, irr, dist, pos, nrm, camera, want_weights=False, shift=(
     lib().or_query(C.byref(v), _ptr(states, _u8p), _ptr(_f64(irr), _dp), _ptr(_f64(dist), _dp),
                    n, _ptr(pos, _dp), _ptr(nrm, _dp), _ptr(cam, _dp), _ptr(out, _dp), _ptr(w, _dp))
     return (out, w) if want_weights else out
+
+
+def query_glossy(desc, states, irr, dist, pos, nrm, dirs, shift=(0, 0, 0), origin=None):
+    """Second-order glossy lookup (Sec. 4.4): prefiltered radiance M [n, 3] at
+    reflection-ray hits `pos` (normals `nrm`) reached along unit `dirs`,
+    read in the mirror direction."""
+    pos = _f64(pos, (-1, 3))
+    nrm = _f64(nrm, (-1, 3))
+    dirs = _f64(dirs, (-1, 3))
+    n = len(pos)
+    out = np.zeros((n, 3))
+    v = make_volume(desc, shift, origin)
+    lib().or_query_glossy(C.byref(v), _ptr(states, _u8p), _ptr(_f64(irr), _dp), _ptr(_f64(dist), _dp),
+                          n, _ptr(pos, _dp), _ptr(nrm, _dp), _ptr(dirs, _dp), _ptr(out, _dp))
+    return out
 
 
 def query_cascade(vol_structs, states_list, irr_list, dist_list, pos, nrm, camera,

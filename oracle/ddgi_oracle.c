@@ -355,9 +355,12 @@ void or_classify(const or_scene* s, const or_volume* v, int64_t frame,
 /* Query (Sec. 2.2, self-shadow bias Eq. of Sec. 4.1, decode Sec. 4.2)  */
 /* Returns the cosine-weighted mean radiance M (E = pi * M).           */
 /* ------------------------------------------------------------------ */
-static void query_M(const or_volume* v, const uint8_t* st, const double* irr, const double* dist,
-                    const double x[3], const double n[3], const double wo[3],
-                    double M[3], double* wout) {
+/* `look` is the direction the irradiance tiles are read in: the normal n for
+ * the irradiance query, the mirror direction for a second-order glossy
+ * lookup (Sec. 4.4); bias and backface weights always use n. */
+static void query_M_look(const or_volume* v, const uint8_t* st, const double* irr, const double* dist,
+                         const double x[3], const double n[3], const double wo[3], const double look[3],
+                         double M[3], double* wout) {
     double D = min_spacing(v);
     double xb[3];
     for (int a = 0; a < 3; ++a)
@@ -408,15 +411,45 @@ static void query_M(const or_volume* v, const uint8_t* st, const double* irr, co
         }
         double w = wt * wb * fmax(wc, 1e-6);
         if (wout) wout[c] = w;
-        /* irradiance in the normal direction, gamma decoded to a gamma-2 curve */
+        /* irradiance in the lookup direction, gamma decoded to a gamma-2 curve */
         double e[3];
-        or_sample_bilinear(irr + p * tsi, v->irr_n, 3, n, e);
+        or_sample_bilinear(irr + p * tsi, v->irr_n, 3, look, e);
         for (int k = 0; k < 3; ++k) acc[k] += w * pow(fmax(e[k], 0.0), 0.5 * v->gamma);
         sumw += w;
     }
     for (int k = 0; k < 3; ++k) {
         double a = sumw > 0.0 ? acc[k] / sumw : 0.0;
         M[k] = a * a;
+    }
+}
+
+static void query_M(const or_volume* v, const uint8_t* st, const double* irr, const double* dist,
+                    const double x[3], const double n[3], const double wo[3],
+                    double M[3], double* wout) {
+    query_M_look(v, st, irr, dist, x, n, wo, n, M, wout);
+}
+
+/* Second-order glossy (Sec. 4.4): at a reflection-ray hit x with normal n,
+ * reached along the unit direction d, the probes are read in the mirror
+ * direction r = d - 2 (d.n) n and the result is the prefiltered radiance M
+ * (not pi M); the view direction of the self-shadow bias is -d. */
+void or_query_glossy(const or_volume* v, const uint8_t* states, const double* irr, const double* dist,
+                     int64_t n, const double* pos, const double* nrm, const double* dirs, double* out_M) {
+    #pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < n; ++q) {
+        const double* x = pos + 3*q;
+        const double* nn = nrm + 3*q;
+        const double* d = dirs + 3*q;
+        if (nn[0] == 0.0 && nn[1] == 0.0 && nn[2] == 0.0) {
+            for (int k = 0; k < 3; ++k) out_M[3*q + k] = 0.0;
+            continue;
+        }
+        double dn = dot3(d, nn);
+        double r[3] = { d[0] - 2.0 * dn * nn[0], d[1] - 2.0 * dn * nn[1], d[2] - 2.0 * dn * nn[2] };
+        double lr = len3(r);
+        if (lr > 0.0) { r[0] /= lr; r[1] /= lr; r[2] /= lr; }
+        double wo[3] = { -d[0], -d[1], -d[2] };
+        query_M_look(v, states, irr, dist, x, nn, wo, r, out_M + 3*q, NULL);
     }
 }
 

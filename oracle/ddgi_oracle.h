@@ -97,6 +97,8 @@ void or_update(const or_scene* s, const or_lights* L, const or_volume* v, int64_
 void or_query(const or_volume* v, const uint8_t* states, const double* irr, const double* dist,
               int64_t n, const double* pos, const double* nrm, const double camera[3],
               double* out_E, double* weights_out);
+void or_query_glossy(const or_volume* v, const uint8_t* states, const double* irr, const double* dist,
+                     int64_t n, const double* pos, const double* nrm, const double* dirs, double* out_M);
 void or_query_cascade(int64_t n_vol, const or_volume* vols, const uint8_t* const* states,
                       const double* const* irr, const double* const* dist,
                       int64_t n, const double* pos, const double* nrm, const double camera[3],

@@ -76,6 +76,7 @@ SIGNATURES = {
     "ddgi_volume_get_info": (C.c_int, [_vp, C.POINTER(VolumeInfo)]),
     "ddgi_update": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.POINTER(UpdateParams), _vp]),
     "ddgi_query": (C.c_int, [_vp, _vp, _vp, C.c_int64, F3, _vp, _vp]),
+    "ddgi_query_glossy": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, _vp, _vp]),
     "ddgi_update_range": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.POINTER(UpdateParams), C.c_int64, C.c_int64,
                                     _vp]),
     "ddgi_get_buffer": (C.c_int, [_vp, C.c_int32, _vp, C.c_size_t, _vp]),

@@ -195,6 +195,17 @@ class Volume:
                                 _stream(stream)))
         return out
 
+    def query_glossy(self, pos: torch.Tensor, nrm: torch.Tensor, dirs: torch.Tensor, out: torch.Tensor = None,
+                     stream=None) -> torch.Tensor:
+        """Prefiltered radiance M read in the mirror direction at reflection-ray
+        hits reached along `dirs` (second-order glossy, Sec. 4.4)."""
+        n = pos.shape[0]
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+        check(load().ddgi_query_glossy(self.handle, _ptr(pos), _ptr(nrm), _ptr(dirs), n, _ptr(out),
+                                       _stream(stream)))
+        return out
+
     def _get(self, which, nbytes, stream=None, device="cuda"):
         buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
         check(load().ddgi_get_buffer(self.handle, which, _ptr(buf), nbytes, _stream(stream)))

@@ -690,6 +690,18 @@ ddgi_status ddgi_trace_stats(ddgi_volume v, ddgi_scene s, const ddgi_lights* lig
     return DDGI_OK;
 }
 
+ddgi_status ddgi_query_glossy(ddgi_volume v, const float* pos_dev, const float* nrm_dev, const float* dir_dev,
+                              int64_t n, float* out_dev, ddgi_stream stream) {
+    if (!v) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (n < 0) return fail(DDGI_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return DDGI_OK;
+    if (!pos_dev || !nrm_dev || !dir_dev || !out_dev || !aligned(pos_dev, 4) || !aligned(nrm_dev, 4) ||
+        !aligned(dir_dev, 4) || !aligned(out_dev, 4))
+        return fail(DDGI_ERR_INVALID_ARG, "bad buffer");
+    DDGI_CK(launch_query_glossy(make_view(v), pos_dev, nrm_dev, dir_dev, n, out_dev, (cudaStream_t)stream));
+    return DDGI_OK;
+}
+
 ddgi_status ddgi_query(ddgi_volume v, const float* pos_dev, const float* nrm_dev, int64_t n,
                        const float camera_pos[3], float* out_dev, ddgi_stream stream) {
     if (!v || !camera_pos) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");

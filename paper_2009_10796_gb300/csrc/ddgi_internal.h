@@ -210,6 +210,8 @@ cudaError_t launch_blend_tc_set(const VolSet& vs, bool multi, const BlendParams&
                                 const float* inv_dist, const float4* records, const int32_t* active,
                                 const int32_t* count, uint32_t* status, int grid, cudaStream_t st);
 cudaError_t prepare_blend_tc_kernels();
+cudaError_t launch_query_glossy(const VolView& v, const float* pos, const float* nrm, const float* dirs, int64_t n,
+                                float* out, cudaStream_t st);
 cudaError_t launch_query(const VolView& v, const float* pos, const float* nrm, int64_t n,
                          float3 camera, float* out, cudaStream_t st);
 cudaError_t launch_query_cascade(const VolSet& vs, const float* pos, const float* nrm, int64_t n, float3 camera,

@@ -524,19 +524,45 @@ static cudaError_t opt_in_blend() {
     return e;
 }
 
+template <int PG>
+static bool tiled_fits(const BlendParams& bp, int irr_n, int dist_n) {
+    const TiledShape ts = tiled_shape(PG, bp.R, irr_n, dist_n);
+    return bp.R % 4 == 0 && ts.threads <= kTileMaxThreads && ts.smem + 1024 <= (size_t)smem_optin();
+}
+
+template <bool MULTI, int PG>
+static cudaError_t launch_tiled(const VolSet& vs, const BlendParams& bp, int irr_n, int dist_n, const float* w_irr,
+                                const float* inv_s_irr, const float* w_dist, const float* inv_s_dist,
+                                const float4* records, const int32_t* active, const int32_t* count,
+                                uint32_t* status, int grid, cudaStream_t st) {
+    cudaError_t e = opt_in_blend<MULTI, PG>();
+    if (e != cudaSuccess) return e;
+    const TiledShape ts = tiled_shape(PG, bp.R, irr_n, dist_n);
+    k_blend_tiled<MULTI, PG><<<grid, ts.threads, ts.smem, st>>>(vs, bp, w_irr, inv_s_irr, w_dist, inv_s_dist,
+                                                                records, active, count, status);
+    return cudaGetLastError();
+}
+
+// The tiled kernel with PGS probes per CTA, or with fewer when its tiles do
+// not fit (larger texel counts need more threads per probe group); the row
+// kernel when no group size fits.  The grid is scaled to keep the probes
+// per launch wave.
 template <bool MULTI, int PGS>
 static cudaError_t blend_simt(const VolSet& vs, const BlendParams& bp, int irr_n, int dist_n, const float* w_irr,
                               const float* inv_s_irr, const float* w_dist, const float* inv_s_dist,
                               const float4* records, const int32_t* active, const int32_t* count,
                               uint32_t* status, int grid, cudaStream_t st) {
+    if (PGS >= 16 && tiled_fits<16>(bp, irr_n, dist_n))
+        return launch_tiled<MULTI, 16>(vs, bp, irr_n, dist_n, w_irr, inv_s_irr, w_dist, inv_s_dist, records, active,
+                                       count, status, grid, st);
+    if (PGS >= 8 && tiled_fits<8>(bp, irr_n, dist_n))
+        return launch_tiled<MULTI, 8>(vs, bp, irr_n, dist_n, w_irr, inv_s_irr, w_dist, inv_s_dist, records, active,
+                                      count, status, grid * (PGS / 8), st);
+    if (tiled_fits<4>(bp, irr_n, dist_n))
+        return launch_tiled<MULTI, 4>(vs, bp, irr_n, dist_n, w_irr, inv_s_irr, w_dist, inv_s_dist, records, active,
+                                      count, status, grid * (PGS / 4), st);
     cudaError_t e = opt_in_blend<MULTI, PGS>();
     if (e != cudaSuccess) return e;
-    const TiledShape ts = tiled_shape(PGS, bp.R, irr_n, dist_n);
-    if (bp.R % 4 == 0 && ts.threads <= kTileMaxThreads && ts.smem + 1024 <= (size_t)smem_optin()) {
-        k_blend_tiled<MULTI, PGS><<<grid, ts.threads, ts.smem, st>>>(vs, bp, w_irr, inv_s_irr, w_dist, inv_s_dist,
-                                                                     records, active, count, status);
-        return cudaGetLastError();
-    }
     size_t smem = (size_t)PGS * (bp.R + 1) * sizeof(float4);
     k_blend_simt<MULTI, PGS><<<grid, 256, smem, st>>>(vs, bp, w_irr, inv_s_irr, w_dist, inv_s_dist, records,
                                                       active, count, status);

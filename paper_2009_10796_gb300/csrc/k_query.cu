@@ -27,6 +27,31 @@ __global__ void __launch_bounds__(256) k_query(VolView v, const float* __restric
     }
 }
 
+// Second-order glossy lookup (Sec. 4.4): one thread per reflection-ray hit;
+// dirs are the unit directions the hits were reached along.  Output is the
+// prefiltered radiance M read in the mirror direction (no factor pi).
+__global__ void __launch_bounds__(256) k_query_glossy(VolView v, const float* __restrict__ pos,
+                                                      const float* __restrict__ nrm, const float* __restrict__ dirs,
+                                                      int64_t n, float* __restrict__ out) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        float3 x = f3(__ldg(pos + 3 * q), __ldg(pos + 3 * q + 1), __ldg(pos + 3 * q + 2));
+        float3 nn = f3(__ldg(nrm + 3 * q), __ldg(nrm + 3 * q + 1), __ldg(nrm + 3 * q + 2));
+        float3 d = f3(__ldg(dirs + 3 * q), __ldg(dirs + 3 * q + 1), __ldg(dirs + 3 * q + 2));
+        float3 M = f3(0.0f, 0.0f, 0.0f);
+        if (nn.x != 0.0f || nn.y != 0.0f || nn.z != 0.0f) {
+            float dn = dot(d, nn);
+            float3 r = d - (2.0f * dn) * nn;
+            float lr = length(r);
+            if (lr > 0.0f) r = (1.0f / lr) * r;
+            M = query_M_look(v, x, nn, f3(-d.x, -d.y, -d.z), r);
+        }
+        out[3 * q] = M.x;
+        out[3 * q + 1] = M.y;
+        out[3 * q + 2] = M.z;
+    }
+}
+
 // Compacts probe indices whose state matches `which` (0: UNINIT, 1: active =
 // NEWLY_VIGILANT or VIGILANT) into list[], count[0] += matches.  Warp-
 // aggregated atomics: one atomic per warp.  List order is not deterministic;
@@ -157,6 +182,15 @@ cudaError_t launch_query(const VolView& v, const float* pos, const float* nrm, i
     int64_t blocks = (n + 255) / 256;
     int grid = (int)(blocks < 1048576 ? blocks : 1048576);
     k_query<<<grid, 256, 0, st>>>(v, pos, nrm, n, camera, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_query_glossy(const VolView& v, const float* pos, const float* nrm, const float* dirs, int64_t n,
+                                float* out, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    int grid = (int)(blocks < 1048576 ? blocks : 1048576);
+    k_query_glossy<<<grid, 256, 0, st>>>(v, pos, nrm, dirs, n, out);
     return cudaGetLastError();
 }
 

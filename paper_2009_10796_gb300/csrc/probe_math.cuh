@@ -280,7 +280,10 @@ __device__ __forceinline__ float gamma_decode_half_fast(float e, float half_gamm
 // 1e-6 * w_t * w_b, gamma decode (Sec. 4.2) normalised before squaring.
 // Per-probe normalisations, the Chebyshev ratio and the square roots of the
 // decode use the hardware reciprocal and reciprocal square root.
-__device__ __forceinline__ float3 query_M(const VolView& v, float3 x, float3 n, float3 wo) {
+// `look` is the direction the irradiance tiles are read in: n for the
+// irradiance query, the mirror direction for a second-order glossy lookup
+// (Sec. 4.4); the bias and the backface weights use n either way.
+__device__ __forceinline__ float3 query_M_look(const VolView& v, float3 x, float3 n, float3 wo, float3 look) {
     float k = 0.75f * v.min_spacing * v.bias;
     float3 xb = f3(x.x + (0.2f * n.x + 0.8f * wo.x) * k, x.y + (0.2f * n.y + 0.8f * wo.y) * k,
                    x.z + (0.2f * n.z + 0.8f * wo.z) * k);
@@ -297,7 +300,7 @@ __device__ __forceinline__ float3 query_M(const VolView& v, float3 x, float3 n, 
     }
     float sumw = 0.0f;
     float3 acc = f3(0.0f, 0.0f, 0.0f);
-    const Footprint fn = footprint(oct_encode(n), v.irr_n);   // irradiance lookup direction: n, every probe
+    const Footprint fn = footprint(oct_encode(look), v.irr_n);   // irradiance lookup, the same for every probe
 #pragma unroll 1
     for (int c = 0; c < 8; ++c) {
         int o0 = c & 1, o1 = (c >> 1) & 1, o2 = (c >> 2) & 1;
@@ -334,6 +337,10 @@ __device__ __forceinline__ float3 query_M(const VolView& v, float3 x, float3 n, 
     float inv = 1.0f / sumw;
     float3 a = inv * acc;
     return f3(a.x * a.x, a.y * a.y, a.z * a.z);
+}
+
+__device__ __forceinline__ float3 query_M(const VolView& v, float3 x, float3 n, float3 wo) {
+    return query_M_look(v, x, n, wo, n);
 }
 
 // Cascade value M at x (Sec. 7.3): volumes densest first; each volume's

@@ -482,6 +482,41 @@ def test_query_agreeing_probes_return_common_value():
     assert np.allclose(E, PI * s ** vol.gamma, rtol=1e-12)
 
 
+def test_glossy_lookup_reads_the_mirror_direction():
+    """Second-order glossy (Sec. 4.4): with every probe holding the same tiles
+    and no occlusion, the lookup is the tile's bilinear sample in the mirror
+    direction r = d - 2 (d.n) n, decoded, as radiance M (no factor pi)."""
+    vol = synth.VolumeDesc(origin=(0, 0, 0), spacing=(1.0, 1.0, 1.0), counts=(3, 3, 3),
+                           state_machine=0, gamma=5.0, self_shadow_bias=0.3)
+    st, irr, dist = oracle.new_state(vol)
+    rng = synth.Rng(33)
+    tile = rng.uniform(irr[0].size, 0.1, 1.0).reshape(irr[0].shape)
+    irr[:] = tile
+    dist[..., 0] = 10.0
+    dist[..., 1] = 100.0
+    st[:] = oracle.VIGILANT
+    n = 200
+    pos = synth.f32(rng.uniform(3 * n, 0.3, 1.7).reshape(n, 3))
+    nrm = rng.unit_vectors(n)
+    d = rng.unit_vectors(n)
+    M = oracle.query_glossy(vol, st, irr, dist, pos, nrm, d)
+    dn = np.sum(d * nrm, -1, keepdims=True)
+    r = d - 2 * dn * nrm
+    r /= np.linalg.norm(r, axis=1, keepdims=True)
+    assert np.allclose(M, oracle.sample_bilinear(tile, vol.irr_n, r) ** vol.gamma, rtol=1e-12)
+    # the mirror direction differs from the normal: a normal lookup would not match
+    assert not np.allclose(M, oracle.sample_bilinear(tile, vol.irr_n, nrm) ** vol.gamma, rtol=1e-3)
+    # head-on arrival (d = -n) mirrors back along n: E / pi of the irradiance
+    # query with the camera straight above
+    x = pos[:1]
+    nn = nrm[:1]
+    Mg = oracle.query_glossy(vol, st, irr, dist, x, nn, -nn)
+    E = oracle.query(vol, st, irr, dist, x, nn, x[0] + 4.0 * nn[0])
+    assert np.allclose(Mg, E / PI, rtol=1e-12)
+    # no surface: zero
+    assert np.all(oracle.query_glossy(vol, st, irr, dist, x, np.zeros((1, 3)), -nn) == 0)
+
+
 def test_query_chebyshev_and_backface_weights_by_hand():
     vol = _two_cube(B=0.0)
     st, irr, dist = oracle.new_state(vol)
