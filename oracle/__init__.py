@@ -54,7 +54,8 @@ class OrVolume(C.Structure):
                 ("bias_B", C.c_double), ("cos_power", C.c_double), ("t_max", C.c_double),
                 ("thr_low", C.c_double), ("thr_high", C.c_double), ("thr_step", C.c_double),
                 ("state_machine", C.c_int64), ("seed", C.c_uint64), ("shift", C.c_int64 * 3),
-                ("blend_lo", C.c_double * 3), ("blend_hi", C.c_double * 3)]
+                ("blend_lo", C.c_double * 3), ("blend_hi", C.c_double * 3),
+                ("offsets", C.POINTER(C.c_double)), ("opt_iters", C.c_int64), ("offset_limit", C.c_double)]
 
 
 def build(force: bool = False, extra_flags=()) -> str:
@@ -124,6 +125,7 @@ def _declare(lib):
                               C.c_int64, C.c_double, C.c_double, _u8p, _dp, _dp, C.c_int64,
                               _i64p, _dp]
     lib.or_query.argtypes = [C.POINTER(OrVolume), _u8p, _dp, _dp, C.c_int64, _dp, _dp, _dp, _dp, _dp]
+    lib.or_optimize.argtypes = [C.c_void_p, C.POINTER(OrVolume), C.c_int64, C.c_int64, _i64p]
     lib.or_query_glossy.argtypes = [C.POINTER(OrVolume), _u8p, _dp, _dp, C.c_int64, _dp, _dp, _dp, _dp]
     lib.or_query_cascade.argtypes = [C.c_int64, C.POINTER(OrVolume), C.POINTER(_u8p),
                                      C.POINTER(_dp), C.POINTER(_dp), C.c_int64, _dp, _dp, _dp,
@@ -186,8 +188,15 @@ def make_lights(lights) -> OrLights:
     return L
 
 
-def make_volume(desc, shift=(0, 0, 0), origin=None, blend_lo=None, blend_hi=None) -> OrVolume:
+def make_volume(desc, shift=(0, 0, 0), origin=None, blend_lo=None, blend_hi=None, offsets=None) -> OrVolume:
+    """`offsets`: float64 [P, 3] probe offsets (Sec. 5), written in place by the
+    position optimizer; the caller keeps it alive while the struct is used."""
     v = OrVolume()
+    if offsets is not None:
+        assert offsets.dtype == np.float64 and offsets.flags.c_contiguous and offsets.shape == (desc.n_probes, 3)
+        v.offsets = offsets.ctypes.data_as(C.POINTER(C.c_double))
+    v.opt_iters = int(getattr(desc, "optimizer_iters", 0))
+    v.offset_limit = float(getattr(desc, "offset_limit", 0.45))
     org = desc.origin if origin is None else origin
     v.origin[:] = [float(x) for x in org]
     v.spacing[:] = [float(x) for x in desc.spacing]
@@ -214,6 +223,11 @@ def make_volume(desc, shift=(0, 0, 0), origin=None, blend_lo=None, blend_hi=None
     v.blend_lo[:] = [float(x) for x in lo]
     v.blend_hi[:] = [float(x) for x in hi]
     return v
+
+
+def new_offsets(desc):
+    """Zero probe offsets [P, 3] (every probe on its grid point)."""
+    return np.zeros((desc.n_probes, 3), dtype=np.float64)
 
 
 def new_state(desc, initial=None):
@@ -310,24 +324,34 @@ def trace(scene_h: SceneHandle, o, d):
     return t, tri, bf
 
 
-def classify(scene_h, desc, frame, probe_ids, states, shift=(0, 0, 0), origin=None):
+def optimize(scene_h, desc, frame, probe_ids, offsets):
+    """desc.optimizer_iters iterations of the probe position optimizer (Sec. 5)
+    on the probes `probe_ids`, in place on `offsets` [P, 3]."""
+    ids = np.ascontiguousarray(probe_ids, dtype=np.int64)
+    v = make_volume(desc, offsets=offsets)
+    lib().or_optimize(C.byref(scene_h.s), C.byref(v), frame, len(ids), _ptr(ids, _i64p))
+    return offsets
+
+
+def classify(scene_h, desc, frame, probe_ids, states, shift=(0, 0, 0), origin=None, offsets=None):
     ids = np.ascontiguousarray(probe_ids, dtype=np.int64)
     bf = np.zeros(len(ids), dtype=np.int32)
     dmin = np.zeros(len(ids))
-    v = make_volume(desc, shift, origin)
+    v = make_volume(desc, shift, origin, offsets=offsets)
     lib().or_classify(C.byref(scene_h.s), C.byref(v), frame, len(ids), _ptr(ids, _i64p),
                       _ptr(states, _u8p), _ptr(bf, _i32p), _ptr(dmin, _dp))
     return bf, dmin
 
 
 def update(scene_h, lights, desc, frame, states, irr, dist, subset=None, irr_scale=1.0,
-           vis_scale=1.0, want_rays=False, shift=(0, 0, 0), origin=None):
-    """One update frame, in place on (states, irr, dist).  Returns per-ray
-    records [n_list, R, 4] (r, g, b, d) when want_rays (NaN for inactive probes)."""
+           vis_scale=1.0, want_rays=False, shift=(0, 0, 0), origin=None, offsets=None):
+    """One update frame, in place on (states, irr, dist) and, with the position
+    optimizer on, on `offsets` [P, 3].  Returns per-ray records [n_list, R, 4]
+    (r, g, b, d) when want_rays (NaN for inactive probes)."""
     assert states.dtype == np.uint8 and states.flags.c_contiguous
     assert irr.dtype == np.float64 and irr.flags.c_contiguous
     assert dist.dtype == np.float64 and dist.flags.c_contiguous
-    v = make_volume(desc, shift, origin)
+    v = make_volume(desc, shift, origin, offsets=offsets)
     L = make_lights(lights)
     sub = None if subset is None else np.ascontiguousarray(subset, dtype=np.int64)
     n_list = desc.n_probes if sub is None else len(sub)
@@ -339,20 +363,20 @@ def update(scene_h, lights, desc, frame, states, irr, dist, subset=None, irr_sca
 
 
 def query(desc, states, irr, dist, pos, nrm, camera, want_weights=False, shift=(0, 0, 0),
-          origin=None):
+          origin=None, offsets=None):
     pos = _f64(pos, (-1, 3))
     nrm = _f64(nrm, (-1, 3))
     cam = _f64(camera, (3,))
     n = len(pos)
     out = np.zeros((n, 3))
     w = np.zeros((n, 8)) if want_weights else None
-    v = make_volume(desc, shift, origin)
+    v = make_volume(desc, shift, origin, offsets=offsets)
     lib().or_query(C.byref(v), _ptr(states, _u8p), _ptr(_f64(irr), _dp), _ptr(_f64(dist), _dp),
                    n, _ptr(pos, _dp), _ptr(nrm, _dp), _ptr(cam, _dp), _ptr(out, _dp), _ptr(w, _dp))
     return (out, w) if want_weights else out
 
 
-def query_glossy(desc, states, irr, dist, pos, nrm, dirs, shift=(0, 0, 0), origin=None):
+def query_glossy(desc, states, irr, dist, pos, nrm, dirs, shift=(0, 0, 0), origin=None, offsets=None):
     """Second-order glossy lookup (Sec. 4.4): prefiltered radiance M [n, 3] at
     reflection-ray hits `pos` (normals `nrm`) reached along unit `dirs`,
     read in the mirror direction."""
@@ -361,7 +385,7 @@ def query_glossy(desc, states, irr, dist, pos, nrm, dirs, shift=(0, 0, 0), origi
     dirs = _f64(dirs, (-1, 3))
     n = len(pos)
     out = np.zeros((n, 3))
-    v = make_volume(desc, shift, origin)
+    v = make_volume(desc, shift, origin, offsets=offsets)
     lib().or_query_glossy(C.byref(v), _ptr(states, _u8p), _ptr(_f64(irr), _dp), _ptr(_f64(dist), _dp),
                           n, _ptr(pos, _dp), _ptr(nrm, _dp), _ptr(dirs, _dp), _ptr(out, _dp))
     return out

@@ -299,10 +299,13 @@ void or_probe_pos_logical(const or_volume* v, int64_t i, int64_t j, int64_t k, d
     x[2] = v->origin[2] + (double)k * v->spacing[2];
 }
 
+/* World position of a probe: its grid point plus its offset (Sec. 5). */
 static void probe_pos_phys(const or_volume* v, int64_t phys, double x[3]) {
     int64_t ijk[3];
     probe_logical(v, phys, ijk);
     or_probe_pos_logical(v, ijk[0], ijk[1], ijk[2], x);
+    if (v->offsets)
+        for (int a = 0; a < 3; ++a) x[a] += v->offsets[3 * phys + a];
 }
 
 static double min_spacing(const or_volume* v) {
@@ -313,6 +316,69 @@ static int is_active(uint8_t s) { return s == OR_NEWLY_VIGILANT || s == OR_VIGIL
 
 static int64_t irr_tile_size(const or_volume* v) { return (v->irr_n + 2) * (v->irr_n + 2) * 3; }
 static int64_t dist_tile_size(const or_volume* v) { return (v->dist_n + 2) * (v->dist_n + 2) * 2; }
+
+/* ------------------------------------------------------------------ */
+/* Probe position optimizer (Sec. 5 and its listing)                   */
+/* ------------------------------------------------------------------ */
+/* Iteration k traces the R rays of frame (frame + k) from each probe's
+ * current position, then moves its offset:
+ *   more than 25% backfaces: along the vector to the closest backface
+ *     (t * w) by the largest scale that keeps every component of the offset
+ *     within +-limit (less 1 mm); only if that scale exceeds 1, i.e. the move
+ *     goes through the backface;
+ *   otherwise, unless the farthest front face lies within 60 degrees of the
+ *     closest one (one visible surface): min(0.2, t) along the direction of
+ *     the farthest front face, each component clamped to +-limit.
+ * Closest picks the smallest t (ties: smaller ray index), farthest the
+ * largest t (ties: larger ray index); misses are neither. */
+void or_optimize(const or_scene* s, const or_volume* v, int64_t frame, int64_t n, const int64_t* phys_ids) {
+    int64_t R = v->rays;
+    if (!v->offsets || v->opt_iters <= 0 || n <= 0) return;
+    double* dirs = (double*)malloc(sizeof(double) * 3 * (size_t)R);
+    double lim[3];
+    for (int a = 0; a < 3; ++a) lim[a] = v->offset_limit * v->spacing[a];
+    for (int64_t k = 0; k < v->opt_iters; ++k) {
+        or_frame_dirs(v->seed, frame + k, R, dirs);
+        #pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t q = 0; q < n; ++q) {
+            int64_t p = phys_ids[q];
+            double x[3];
+            probe_pos_phys(v, p, x);
+            int64_t bf = 0, ib = -1, icf = -1, iff = -1;
+            double tb = INFINITY, tcf = INFINITY, tff = -INFINITY;
+            for (int64_t i = 0; i < R; ++i) {
+                double t;
+                int64_t tri;
+                int back;
+                if (!or_closest_hit(s, x, dirs + 3*i, &t, &tri, &back)) continue;
+                if (back) {
+                    bf++;
+                    if (t < tb) { tb = t; ib = i; }
+                } else {
+                    if (t < tcf) { tcf = t; icf = i; }
+                    if (t >= tff) { tff = t; iff = i; }
+                }
+            }
+            double* cur = v->offsets + 3 * p;
+            if (4 * bf > R) {
+                double vec[3], comb[3];
+                for (int a = 0; a < 3; ++a) {
+                    vec[a] = tb * dirs[3*ib + a];
+                    double pos = (lim[a] - cur[a]) / vec[a];
+                    double neg = (-lim[a] - cur[a]) / vec[a];
+                    comb[a] = fmax(pos, neg);
+                }
+                double scale = fmin(fmin(comb[0], comb[1]), comb[2]) - 1e-3;
+                if (scale > 1.0)
+                    for (int a = 0; a < 3; ++a) cur[a] += vec[a] * scale;
+            } else if (iff >= 0 && icf >= 0 && !(dot3(dirs + 3*iff, dirs + 3*icf) > 0.5)) {
+                double step = fmin(0.2, tff);
+                for (int a = 0; a < 3; ++a) cur[a] = clampd(cur[a] + step * dirs[3*iff + a], -lim[a], lim[a]);
+            }
+        }
+    }
+    free(dirs);
+}
 
 /* ------------------------------------------------------------------ */
 /* Classification (Sec. 6.3 and its state listing)                     */
@@ -385,6 +451,8 @@ static void query_M_look(const or_volume* v, const uint8_t* st, const double* ir
         if (!is_active(st[p])) continue;
         double xp[3];
         or_probe_pos_logical(v, base[0] + o[0], base[1] + o[1], base[2] + o[2], xp);
+        if (v->offsets)   /* the probe's own (moved) position; the cage stays on the grid */
+            for (int a = 0; a < 3; ++a) xp[a] += v->offsets[3 * p + a];
         /* trilinear weight */
         double wt = 1.0;
         for (int a = 0; a < 3; ++a) wt *= o[a] ? fr[a] : 1.0 - fr[a];
@@ -668,6 +736,7 @@ void or_update(const or_scene* s, const or_lights* L, const or_volume* v, int64_
         int64_t nu = 0;
         int64_t* un = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
         for (int64_t q = 0; q < n; ++q) if (states[list[q]] == OR_UNINIT) un[nu++] = list[q];
+        if (nu) or_optimize(s, v, frame, nu, un);   /* no-op unless the optimizer is on */
         if (nu) or_classify(s, v, frame, nu, un, states, NULL, NULL);
         free(un);
     }

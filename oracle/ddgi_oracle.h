@@ -60,6 +60,9 @@ typedef struct {
     int64_t shift[3];           /* tracking window: logical (i,j,k) stored at (i+shift) mod count */
     double  blend_lo[3];        /* cascade fall-off box (outermost planes, or camera-centred) */
     double  blend_hi[3];
+    double* offsets;            /* [P][3] probe offsets from the grid (Sec. 5), or NULL */
+    int64_t opt_iters;          /* position-optimizer iterations for uninitialised probes (0: off) */
+    double  offset_limit;       /* largest offset per axis, as a fraction of the spacing */
 } or_volume;
 
 enum { OR_UNINIT = 0, OR_OFF = 1, OR_SLEEPING = 2, OR_NEWLY_VIGILANT = 3, OR_VIGILANT = 4 };
@@ -87,6 +90,7 @@ int or_any_hit_shadow(const or_scene* s, const double o[3], const double d[3]);
 /* --- probes --- */
 int64_t or_probe_phys(const or_volume* v, int64_t i, int64_t j, int64_t k);
 void or_probe_pos_logical(const or_volume* v, int64_t i, int64_t j, int64_t k, double x[3]);
+void or_optimize(const or_scene* s, const or_volume* v, int64_t frame, int64_t n, const int64_t* phys_ids);
 void or_classify(const or_scene* s, const or_volume* v, int64_t frame,
                  int64_t n, const int64_t* phys_ids, uint8_t* states,
                  int32_t* backface_count, double* dmin_front);

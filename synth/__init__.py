@@ -124,6 +124,8 @@ class VolumeDesc:
     thr_high: float = 0.8
     thr_step: float = 0.15
     tracking: int = 0
+    optimizer_iters: int = 0  # position-optimizer iterations for new probes (Sec. 5; the paper uses 5)
+    offset_limit: float = 0.45  # largest probe offset per axis, fraction of the spacing
 
     def resolved_t_max(self) -> float:
         if self.t_max >= 0:
