@@ -373,6 +373,7 @@ def run_gpu(args):
 
     paper_res = None if args.no_paper_res else run_paper_resolution(args, g, torch, stream, scene, L, pos, nrm,
                                                                      camera, flush)
+    optimizer = None if args.no_paper_res else run_optimizer(args, g, torch, stream, scene, L)
     cascade = None if args.no_cascade else run_cascade(args, g, torch, stream)
     diff = None if args.no_diff else run_diff(args, g, torch, stream)
 
@@ -429,6 +430,7 @@ def run_gpu(args):
                                    / 1e12,
             "frame_setup_ms": mixed[2]["frame_setup"][0] / max(mixed[2]["frame_setup"][1], 1)},
         "paper_resolution": paper_res,
+        "position_optimizer": optimizer,
         "cascade_batched": cascade,
         "differentiation": diff,
         "cpu_baseline": cpu,
@@ -508,6 +510,31 @@ def run_paper_resolution(args, g, torch, stream, scene, L, pos, nrm, camera, flu
     return {"workload": "city, 8x8 irradiance / 16x16 visibility interiors, FP32 blend",
             "ms_per_step": ms, "grays_per_s": n_active * desc.rays_per_probe / (ms * 1e-3) / 1e9,
             "blend_ms": tm["blend"][0] / max(tm["blend"][1], 1), "active_probes": n_active}
+
+
+def run_optimizer(args, g, torch, stream, scene, L):
+    """Probe position optimizer (Sec. 5) on the city volume: the first frame
+    (every probe new: 5 optimizer iterations, then classification) with and
+    without it, and the probe states it leads to."""
+    out = {}
+    for iters in (0, 5):
+        times = []
+        for rep in range(3):
+            vol = g.Volume(synth.city_volume(optimizer_iters=iters))
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            vol.update(scene, L, 0, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        st = vol.states().cpu().numpy()
+        out[f"iters_{iters}"] = {"first_frame_ms": float(np.median(times)),
+                                 "vigilant": int((st == g.STATE_VIGILANT).sum()),
+                                 "off": int((st == g.STATE_OFF).sum()),
+                                 "moved": int((vol.offsets().abs().sum(1) > 0).sum().item())}
+    return out
 
 
 def run_diff(args, g, torch, stream):

@@ -186,6 +186,11 @@ typedef struct {
     int32_t dist_format;        /* DDGI_DIST_* */
     int32_t tracking;           /* cascades: 1 = camera-tracking window (Sec. 7.2) */
     uint64_t seed;              /* seed of the per-frame random rotation */
+    int32_t optimizer_iters;    /* probe position optimizer (Sec. 5): iterations run for
+                                   uninitialised probes before classification, 0..16
+                                   (0: off; the paper uses 5); single volumes only */
+    float   offset_limit;       /* largest probe offset per axis, fraction of the spacing,
+                                   [0, 0.5) (the paper leaves it open; 0.45) */
 } ddgi_volume_desc;
 
 /* Allocate a volume: zeroed atlases (Tab. "algtable": uniform
@@ -267,6 +272,8 @@ ddgi_status ddgi_query_glossy(ddgi_volume volume, const float* pos_dev, const fl
  *   which 0: irradiance atlas, [P][(irr_n+2)^2] texels in irr_format
  *   which 1: distance atlas,   [P][(dist_n+2)^2] texels in dist_format
  *   which 2: probe states,     [P] uint8
+ *   which 3: probe offsets,    [P][4] float (x, y, z, 0) from the grid point
+ *            (Sec. 5; zero unless the position optimizer is on)
  * bytes must equal the buffer's size.  ddgi_set_buffer copies the other way
  * (restoring a checkpoint or a shard exchanged between devices). */
 ddgi_status ddgi_get_buffer(ddgi_volume volume, int32_t which, void* dst_dev, size_t bytes,

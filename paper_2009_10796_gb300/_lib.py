@@ -36,7 +36,8 @@ class VolumeDesc(C.Structure):
                 ("self_shadow_bias", C.c_float), ("dist_cos_power", C.c_float), ("t_max", C.c_float),
                 ("thr_low", C.c_float), ("thr_high", C.c_float), ("thr_step", C.c_float),
                 ("state_machine", C.c_int32), ("irr_format", C.c_int32), ("dist_format", C.c_int32),
-                ("tracking", C.c_int32), ("seed", C.c_uint64)]
+                ("tracking", C.c_int32), ("seed", C.c_uint64), ("optimizer_iters", C.c_int32),
+                ("offset_limit", C.c_float)]
 
 
 class VolumeInfo(C.Structure):

@@ -150,6 +150,8 @@ def desc_struct(d) -> _lib.VolumeDesc:
     s.dist_format = int(getattr(d, "dist_format", _lib.DIST_FP32))
     s.tracking = int(getattr(d, "tracking", 0))
     s.seed = int(getattr(d, "seed", 0))
+    s.optimizer_iters = int(getattr(d, "optimizer_iters", 0))
+    s.offset_limit = float(getattr(d, "offset_limit", 0.45))
     return s
 
 
@@ -213,6 +215,10 @@ class Volume:
 
     def states(self, stream=None) -> torch.Tensor:
         return self._get(2, self.n_probes, stream)
+
+    def offsets(self, stream=None) -> torch.Tensor:
+        """Probe offsets from the grid [P, 3] (position optimizer, Sec. 5)."""
+        return self._get(3, self.n_probes * 16, stream).view(torch.float32).view(self.n_probes, 4)[:, :3]
 
     def irr_raw(self, stream=None) -> torch.Tensor:
         return self._get(0, self.info.irr_bytes, stream)

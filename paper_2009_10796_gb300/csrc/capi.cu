@@ -153,6 +153,10 @@ struct ddgi_volume_s {
     float* inv_dist_r = nullptr;
     int64_t updates = 0;
     int3 shift{0, 0, 0};
+    float4* offsets = nullptr;             // [P] probe offsets (position optimizer)
+    float4* opt_dirs = nullptr;            // [R] rays of an optimizer iteration
+    double* opt_dirs64 = nullptr;
+    bool uninit_possible = true;           // some probe may still be UNINIT
     bool timing = false;
     TimedStage stages[8];
 };
@@ -181,6 +185,9 @@ static VolView make_view(const ddgi_volume_s* v) {
     w.states = v->states;
     w.irr = v->irr;
     w.dist = v->dist;
+    // offsets only when the position optimizer is on: the query then reads them
+    w.offsets = d.optimizer_iters > 0 ? v->offsets : nullptr;
+    w.offset_limit = d.offset_limit;
     return w;
 }
 
@@ -440,6 +447,10 @@ static ddgi_status check_desc(const ddgi_volume_desc* d) {
         return fail(DDGI_ERR_INVALID_ARG, "negative cosine power or bias");
     if (d->irr_format < 0 || d->irr_format > 2 || d->dist_format < 0 || d->dist_format > 1)
         return fail(DDGI_ERR_INVALID_ARG, "unknown atlas format");
+    if (d->optimizer_iters < 0 || d->optimizer_iters > 16)
+        return fail(DDGI_ERR_INVALID_ARG, "optimizer_iters must be in [0, 16]");
+    if (!(d->offset_limit >= 0.0f && d->offset_limit < 0.5f))
+        return fail(DDGI_ERR_INVALID_ARG, "offset_limit must be in [0, 0.5)");
     return DDGI_OK;
 }
 
@@ -453,6 +464,7 @@ void ddgi_volume_destroy(ddgi_volume v) {
     for (void* p : v->snap_dist) cudaFree(p);
     cudaFree(v->g_irr); cudaFree(v->g_prev);
     cudaFree(v->pack_irr); cudaFree(v->pack_dist); cudaFree(v->inv_irr_r); cudaFree(v->inv_dist_r);
+    cudaFree(v->offsets); cudaFree(v->opt_dirs); cudaFree(v->opt_dirs64);
     for (auto& st : v->stages)
         for (auto& pr : st.pending) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     delete v;
@@ -492,6 +504,11 @@ ddgi_status ddgi_volume_create(const ddgi_volume_desc* desc, ddgi_volume* out) {
     A((void**)&v->records, sizeof(float4) * (size_t)v->P * v->R);
     A((void**)&v->dirs, sizeof(float4) * v->R);
     A((void**)&v->dirs64, sizeof(double) * 3 * v->R);
+    A((void**)&v->offsets, sizeof(float4) * (size_t)v->P);
+    if (desc->optimizer_iters > 0) {
+        A((void**)&v->opt_dirs, sizeof(float4) * v->R);
+        A((void**)&v->opt_dirs64, sizeof(double) * 3 * v->R);
+    }
     A((void**)&v->w_irr, sizeof(float) * desc->irr_n * desc->irr_n * (size_t)v->R);
     A((void**)&v->inv_s_irr, sizeof(float) * desc->irr_n * desc->irr_n);
     A((void**)&v->w_dist, sizeof(float) * desc->dist_n * desc->dist_n * (size_t)v->R);
@@ -512,6 +529,7 @@ ddgi_status ddgi_volume_create(const ddgi_volume_desc* desc, ddgi_volume* out) {
     if (e == cudaSuccess) e = cudaMemset(v->states, desc->state_machine ? DDGI_STATE_UNINIT : DDGI_STATE_VIGILANT, (size_t)v->P);
     if (e == cudaSuccess) e = cudaMemset(v->irr, 0, v->irr_bytes);
     if (e == cudaSuccess) e = cudaMemset(v->dist, 0, v->dist_bytes);
+    if (e == cudaSuccess) e = cudaMemset(v->offsets, 0, sizeof(float4) * (size_t)v->P);
     if (e == cudaSuccess) e = cudaMemset(v->counts, 0, sizeof(int32_t) * 4);
     if (e == cudaSuccess) e = cudaMemset(v->status, 0, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -610,13 +628,22 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
                                         v->inv_irr_r, v->inv_dist_r, st));
     }
     DDGI_CK(cudaMemsetAsync(v->counts, 0, sizeof(int32_t) * 2, st));
-    if (d.state_machine) {
+    // uninitialised probes (none after a full-range update, until states are
+    // set again): position optimizer iterations, then classification
+    if (d.state_machine && v->uninit_possible) {
         {
             StageTimer tm(v, 1, st);
             DDGI_CK(launch_build_list_range(v->states, (int)begin, (int)end, 0, v->lists, v->counts + 0, st));
         }
         StageTimer tm(v, 0, st);
+        for (int k = 0; k < d.optimizer_iters; ++k) {
+            // iteration k traces the rays of frame + k, as if spread over frames
+            DDGI_CK(launch_frame_dirs(frame_rotation(d.seed, params->frame + k), v->R, v->opt_dirs, v->opt_dirs64,
+                                      st));
+            DDGI_CK(launch_optimize(s->dev, view, v->opt_dirs, v->R, v->lists, v->counts + 0, sms * 8, st));
+        }
         DDGI_CK(launch_classify(s->dev, view, v->dirs, v->R, v->perm, v->lists, v->counts + 0, sms * 8, st));
+        if (begin == 0 && end == v->P) v->uninit_possible = false;
     }
     {
         StageTimer tm(v, 1, st);
@@ -719,7 +746,8 @@ static ddgi_status buffer_of(ddgi_volume v, int32_t which, void** p, size_t* byt
     if (which == 0) { *p = v->irr; *bytes = v->irr_bytes; }
     else if (which == 1) { *p = v->dist; *bytes = v->dist_bytes; }
     else if (which == 2) { *p = v->states; *bytes = (size_t)v->P; }
-    else return fail(DDGI_ERR_INVALID_ARG, "which must be 0, 1 or 2");
+    else if (which == 3) { *p = v->offsets; *bytes = sizeof(float4) * (size_t)v->P; }
+    else return fail(DDGI_ERR_INVALID_ARG, "which must be 0, 1, 2 or 3");
     return DDGI_OK;
 }
 
@@ -742,6 +770,7 @@ ddgi_status ddgi_set_buffer(ddgi_volume v, int32_t which, const void* src_dev, s
     if (s != DDGI_OK) return s;
     if (bytes != nb) return fail(DDGI_ERR_INVALID_ARG, "size mismatch: expected " + std::to_string(nb));
     DDGI_CK(cudaMemcpyAsync(p, src_dev, nb, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    if (which == 2) v->uninit_possible = true;   // restored states may hold UNINIT probes
     return DDGI_OK;
 }
 
@@ -1002,6 +1031,8 @@ ddgi_status ddgi_cascade_create(const ddgi_volume_desc* descs, int32_t n, ddgi_c
     for (int k = 0; k < n; ++k) {
         ddgi_status s = check_desc(&descs[k]);
         if (s != DDGI_OK) return s;
+        if (descs[k].optimizer_iters != 0)
+            return fail(DDGI_ERR_UNSUPPORTED, "cascades have no probe position optimizer");
         const ddgi_volume_desc &a = descs[0], &b = descs[k];
         if (b.rays_per_probe != a.rays_per_probe || b.irr_n != a.irr_n || b.dist_n != a.dist_n ||
             b.irr_format != a.irr_format || b.dist_format != a.dist_format || b.gamma != a.gamma ||

@@ -61,6 +61,8 @@ struct VolView {
     void*    dist;
     float3   blend_lo;      // cascade fall-off box (Sec. 7.3): outermost planes, or
     float3   blend_hi;      // camera-centred for a tracking window
+    float4*  offsets;       // [P] probe offsets from the grid (Sec. 5), or nullptr
+    float    offset_limit;  // largest offset per axis, fraction of the spacing
 };
 
 // Largest BVH leaf (triangles); the traversal packs a leaf's first triangle
@@ -150,6 +152,11 @@ cudaError_t launch_build_list_multi(const VolSet& vs, int total, int which, int3
                                     cudaStream_t st);
 // perm (may be NULL = identity): ray order of a probe's warps, a permutation
 // of [0, R) that groups nearby directions (ray_order_morton)
+// One position-optimizer iteration (Sec. 5) over the UNINIT list, rays `dirs`.
+cudaError_t launch_optimize(const DevScene& s, const VolView& v, const float4* dirs, int R, const int32_t* list,
+                            const int32_t* count, int grid, cudaStream_t st);
+// Frame ray directions only (float4 for the trace, double for the weights).
+cudaError_t launch_frame_dirs(const FrameRot& rot, int R, float4* dirs, double* dirs64, cudaStream_t st);
 cudaError_t launch_classify(const DevScene& s, const VolView& v, const float4* dirs, int R, const int32_t* perm,
                             const int32_t* list, const int32_t* count, int grid, cudaStream_t st);
 cudaError_t launch_classify_multi(const DevScene& s, const VolSet& vs, const float4* dirs, int R,

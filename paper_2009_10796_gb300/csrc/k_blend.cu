@@ -463,6 +463,11 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, B
     }
 }
 
+cudaError_t launch_frame_dirs(const FrameRot& rot, int R, float4* dirs, double* dirs64, cudaStream_t st) {
+    k_frame_dirs<false><<<(R + 31) / 32, 32, 0, st>>>(rot, nullptr, R, dirs, dirs64);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_frame_setup(const FrameRot& rot, int R, int irr_n, int dist_n, float cos_power,
                                float4* dirs, double* dirs64, float* w_irr, float* inv_s_irr, float* w_dist,
                                float* inv_s_dist, cudaStream_t st) {

@@ -410,6 +410,89 @@ __global__ void k_gbuffer(DevScene s, float3 cpos, float3 fwd, float3 right, flo
     }
 }
 
+// One iteration of the probe position optimizer (Sec. 5 and its listing),
+// one warp per UNINIT probe: the lanes trace the iteration's rays from the
+// probe's current position and reduce, as (t bits << 32 | ray) keys, the
+// closest backface, the closest front face and the farthest front face
+// (ties: smaller ray index for closest, larger for farthest); lane 0 moves
+// the offset:
+//   more than 25% backfaces: along t * w of the closest backface, by the
+//     largest scale keeping every component within +-limit (less 1 mm),
+//     only when that scale exceeds 1 (the move goes through the backface);
+//   otherwise, unless the farthest front face lies within 60 degrees of the
+//     closest: min(0.2, t) along the farthest front face, clamped to +-limit.
+__global__ void __launch_bounds__(256) k_optimize(DevScene s, VolView v, const float4* __restrict__ dirs, int R,
+                                                  const int32_t* __restrict__ list,
+                                                  const int32_t* __restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int n = *count;
+    for (int q = warp; q < n; q += nwarps) {
+        const int p = list[q];
+        const float3 o = probe_pos_phys(v, p);
+        int bf = 0;
+        unsigned long long cb = ~0ull, cf = ~0ull, ff = 0ull;
+        for (int i = lane; i < R; i += 32) {
+            float4 d4 = __ldg(dirs + i);
+            float3 d = f3(d4.x, d4.y, d4.z);
+            Hit h = traverse<false>(s, ray_pre(o, d));
+            if (h.orig < 0) continue;
+            const float4* T = s.tris + 3 * (int64_t)h.k;
+            float4 p0 = __ldg(T), p1 = __ldg(T + 1), p2 = __ldg(T + 2);
+            float3 ng = cross(f3(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z), f3(p2.x - p0.x, p2.y - p0.y, p2.z - p0.z));
+            const unsigned long long key = ((unsigned long long)__float_as_uint(h.t) << 32) | (unsigned)i;
+            if (dot(d, ng) > 0.0f) {
+                bf++;
+                cb = key < cb ? key : cb;
+            } else {
+                cf = key < cf ? key : cf;
+                ff = key > ff ? key : ff;
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            bf += __shfl_xor_sync(0xffffffffu, bf, off);
+            const unsigned long long a = __shfl_xor_sync(0xffffffffu, cb, off);
+            const unsigned long long b = __shfl_xor_sync(0xffffffffu, cf, off);
+            const unsigned long long c = __shfl_xor_sync(0xffffffffu, ff, off);
+            cb = a < cb ? a : cb;
+            cf = b < cf ? b : cf;
+            ff = c > ff ? c : ff;
+        }
+        if (lane != 0) continue;
+        const float4 c4 = v.offsets[p];
+        float3 cur = f3(c4.x, c4.y, c4.z);
+        const float3 lim = f3(v.offset_limit * v.spacing.x, v.offset_limit * v.spacing.y,
+                              v.offset_limit * v.spacing.z);
+        if (4 * bf > R) {
+            const float4 w = __ldg(dirs + (int)(cb & 0xffffffffu));
+            const float tb = __uint_as_float((unsigned)(cb >> 32));
+            const float3 vec = f3(tb * w.x, tb * w.y, tb * w.z);
+            const float sx = fmaxf((lim.x - cur.x) / vec.x, (-lim.x - cur.x) / vec.x);
+            const float sy = fmaxf((lim.y - cur.y) / vec.y, (-lim.y - cur.y) / vec.y);
+            const float sz = fmaxf((lim.z - cur.z) / vec.z, (-lim.z - cur.z) / vec.z);
+            const float scale = fminf(fminf(sx, sy), sz) - 1e-3f;
+            if (scale > 1.0f) cur = f3(cur.x + vec.x * scale, cur.y + vec.y * scale, cur.z + vec.z * scale);
+        } else if (ff != 0ull && cf != ~0ull) {
+            const float4 wf = __ldg(dirs + (int)(ff & 0xffffffffu));
+            const float4 wc = __ldg(dirs + (int)(cf & 0xffffffffu));
+            if (!(wf.x * wc.x + wf.y * wc.y + wf.z * wc.z > 0.5f)) {
+                const float step = fminf(0.2f, __uint_as_float((unsigned)(ff >> 32)));
+                cur = f3(fminf(fmaxf(cur.x + step * wf.x, -lim.x), lim.x),
+                         fminf(fmaxf(cur.y + step * wf.y, -lim.y), lim.y),
+                         fminf(fmaxf(cur.z + step * wf.z, -lim.z), lim.z));
+            }
+        }
+        v.offsets[p] = make_float4(cur.x, cur.y, cur.z, 0.0f);
+    }
+}
+
+cudaError_t launch_optimize(const DevScene& s, const VolView& v, const float4* dirs, int R, const int32_t* list,
+                            const int32_t* count, int grid, cudaStream_t st) {
+    k_optimize<<<grid, 256, 0, st>>>(s, v, dirs, R, list, count);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_classify(const DevScene& s, const VolView& v, const float4* dirs, int R, const int32_t* perm,
                             const int32_t* list, const int32_t* count, int grid, cudaStream_t st) {
     k_classify<false><<<grid, 256, 0, st>>>(s, single_set(v), dirs, R, perm, list, count);

@@ -117,6 +117,8 @@ extern "C" ddgi_status ddgi_update_noalloc(ddgi_scene scene, const ddgi_volume_d
         return set_error(DDGI_ERR_INVALID_ARG, "ddgi_update_noalloc: irr_n must be in [1, 8], dist_n in [1, 16]");
     if (d->irr_format < 0 || d->irr_format > 2 || d->dist_format < 0 || d->dist_format > 1)
         return set_error(DDGI_ERR_INVALID_ARG, "unknown atlas format");
+    if (d->optimizer_iters != 0)
+        return set_error(DDGI_ERR_UNSUPPORTED, "ddgi_update_noalloc: no probe position optimizer (no offset storage)");
     if (!(d->gamma > 0.0f) || !(d->hysteresis_irr >= 0.0f && d->hysteresis_irr <= 1.0f) ||
         !(d->hysteresis_vis >= 0.0f && d->hysteresis_vis <= 1.0f) || !(d->dist_cos_power >= 0.0f) ||
         !(d->self_shadow_bias >= 0.0f))

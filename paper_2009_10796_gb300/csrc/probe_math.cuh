@@ -69,12 +69,18 @@ __device__ __forceinline__ float3 probe_pos_logical(const VolView& v, int i, int
               v.origin.z + (float)k * v.spacing.z);
 }
 
+// World position of physical probe p: its grid point plus its offset (Sec. 5).
 __device__ __forceinline__ float3 probe_pos_phys(const VolView& v, int p) {
     int a = p % v.counts.x;
     int b = (p / v.counts.x) % v.counts.y;
     int c = p / (v.counts.x * v.counts.y);
-    return probe_pos_logical(v, wrap_sub(a, v.shift.x, v.counts.x), wrap_sub(b, v.shift.y, v.counts.y),
-                             wrap_sub(c, v.shift.z, v.counts.z));
+    float3 x = probe_pos_logical(v, wrap_sub(a, v.shift.x, v.counts.x), wrap_sub(b, v.shift.y, v.counts.y),
+                                 wrap_sub(c, v.shift.z, v.counts.z));
+    if (v.offsets) {
+        const float4 o = v.offsets[p];
+        x = f3(x.x + o.x, x.y + o.y, x.z + o.z);
+    }
+    return x;
 }
 
 __device__ __forceinline__ bool state_active(uint8_t s) {
@@ -307,6 +313,10 @@ __device__ __forceinline__ float3 query_M_look(const VolView& v, float3 x, float
         int p = probe_phys(v, base[0] + o0, base[1] + o1, base[2] + o2);
         if (!state_active(v.states[p])) continue;
         float3 xp = probe_pos_logical(v, base[0] + o0, base[1] + o1, base[2] + o2);
+        if (v.offsets) {   // the probe's own (moved) position; the cage stays on the grid
+            const float4 po = __ldg(v.offsets + p);
+            xp = f3(xp.x + po.x, xp.y + po.y, xp.z + po.z);
+        }
         float wt = (o0 ? fr[0] : 1.0f - fr[0]) * (o1 ? fr[1] : 1.0f - fr[1]) * (o2 ? fr[2] : 1.0f - fr[2]);
         float3 dp = xp - x;
         float dd = dot(dp, dp);

@@ -110,3 +110,16 @@ def test_optimizer_turns_a_buried_probe_on():
         assert (st[0] == oracle.OFF) == want_off, (iters, st[0], off[0])
         if iters:
             assert abs(off[0, 1]) > 0.1       # out of the slab
+
+
+def test_optimizer_reduces_off_probes_in_the_room():
+    """Moving buried probes out of the room's boxes turns some of them on."""
+    sc = synth.room_scene()
+    h = oracle.SceneHandle(sc)
+    n_off = []
+    for iters in (0, 5):
+        desc = synth.room_volume(optimizer_iters=iters)
+        st, irr, dist = oracle.new_state(desc)
+        oracle.update(h, synth.room_lights(), desc, 0, st, irr, dist, offsets=oracle.new_offsets(desc))
+        n_off.append(int((st == oracle.OFF).sum()))
+    assert n_off[1] < n_off[0], n_off
