@@ -28,7 +28,7 @@ _LIB_PATH = os.path.join(_HERE, "libddgi_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-UNINIT, OFF, SLEEPING, NEWLY_VIGILANT, VIGILANT = 0, 1, 2, 3, 4
+UNINIT, OFF, SLEEPING, NEWLY_VIGILANT, VIGILANT, NEWLY_AWAKE, AWAKE = 0, 1, 2, 3, 4, 5, 6
 
 _dp = C.POINTER(C.c_double)
 _i32p = C.POINTER(C.c_int32)
@@ -55,7 +55,8 @@ class OrVolume(C.Structure):
                 ("thr_low", C.c_double), ("thr_high", C.c_double), ("thr_step", C.c_double),
                 ("state_machine", C.c_int64), ("seed", C.c_uint64), ("shift", C.c_int64 * 3),
                 ("blend_lo", C.c_double * 3), ("blend_hi", C.c_double * 3),
-                ("offsets", C.POINTER(C.c_double)), ("opt_iters", C.c_int64), ("offset_limit", C.c_double)]
+                ("offsets", C.POINTER(C.c_double)), ("opt_iters", C.c_int64), ("offset_limit", C.c_double),
+                ("dyn_boxes", C.POINTER(C.c_double)), ("n_dyn", C.c_int64)]
 
 
 def build(force: bool = False, extra_flags=()) -> str:
@@ -188,10 +189,17 @@ def make_lights(lights) -> OrLights:
     return L
 
 
-def make_volume(desc, shift=(0, 0, 0), origin=None, blend_lo=None, blend_hi=None, offsets=None) -> OrVolume:
+def make_volume(desc, shift=(0, 0, 0), origin=None, blend_lo=None, blend_hi=None, offsets=None,
+                dyn_boxes=None) -> OrVolume:
     """`offsets`: float64 [P, 3] probe offsets (Sec. 5), written in place by the
-    position optimizer; the caller keeps it alive while the struct is used."""
+    position optimizer; `dyn_boxes`: float64 [n, 6] dynamic-object boxes (lo,
+    hi) that wake sleeping probes (Sec. 6.3).  The caller keeps both alive
+    while the struct is used."""
     v = OrVolume()
+    if dyn_boxes is not None and len(dyn_boxes):
+        assert dyn_boxes.dtype == np.float64 and dyn_boxes.flags.c_contiguous and dyn_boxes.shape[1] == 6
+        v.dyn_boxes = dyn_boxes.ctypes.data_as(C.POINTER(C.c_double))
+        v.n_dyn = len(dyn_boxes)
     if offsets is not None:
         assert offsets.dtype == np.float64 and offsets.flags.c_contiguous and offsets.shape == (desc.n_probes, 3)
         v.offsets = offsets.ctypes.data_as(C.POINTER(C.c_double))
@@ -344,14 +352,15 @@ def classify(scene_h, desc, frame, probe_ids, states, shift=(0, 0, 0), origin=No
 
 
 def update(scene_h, lights, desc, frame, states, irr, dist, subset=None, irr_scale=1.0,
-           vis_scale=1.0, want_rays=False, shift=(0, 0, 0), origin=None, offsets=None):
+           vis_scale=1.0, want_rays=False, shift=(0, 0, 0), origin=None, offsets=None, dyn_boxes=None):
     """One update frame, in place on (states, irr, dist) and, with the position
     optimizer on, on `offsets` [P, 3].  Returns per-ray records [n_list, R, 4]
     (r, g, b, d) when want_rays (NaN for inactive probes)."""
     assert states.dtype == np.uint8 and states.flags.c_contiguous
     assert irr.dtype == np.float64 and irr.flags.c_contiguous
     assert dist.dtype == np.float64 and dist.flags.c_contiguous
-    v = make_volume(desc, shift, origin, offsets=offsets)
+    boxes = None if dyn_boxes is None else np.ascontiguousarray(dyn_boxes, dtype=np.float64).reshape(-1, 6)
+    v = make_volume(desc, shift, origin, offsets=offsets, dyn_boxes=boxes)
     L = make_lights(lights)
     sub = None if subset is None else np.ascontiguousarray(subset, dtype=np.int64)
     n_list = desc.n_probes if sub is None else len(sub)

@@ -312,7 +312,14 @@ static double min_spacing(const or_volume* v) {
     return fmin(v->spacing[0], fmin(v->spacing[1], v->spacing[2]));
 }
 
-static int is_active(uint8_t s) { return s == OR_NEWLY_VIGILANT || s == OR_VIGILANT; }
+/* traced and updated: vigilant probes, and sleeping probes woken by a dynamic object */
+static int is_active(uint8_t s) {
+    return s == OR_NEWLY_VIGILANT || s == OR_VIGILANT || s == OR_NEWLY_AWAKE || s == OR_AWAKE;
+}
+static int is_newly(uint8_t s) { return s == OR_NEWLY_VIGILANT || s == OR_NEWLY_AWAKE; }
+static uint8_t advanced(uint8_t s) {
+    return s == OR_NEWLY_VIGILANT ? OR_VIGILANT : (s == OR_NEWLY_AWAKE ? OR_AWAKE : s);
+}
 
 static int64_t irr_tile_size(const or_volume* v) { return (v->irr_n + 2) * (v->irr_n + 2) * 3; }
 static int64_t dist_tile_size(const or_volume* v) { return (v->dist_n + 2) * (v->dist_n + 2) * 2; }
@@ -378,6 +385,35 @@ void or_optimize(const or_scene* s, const or_volume* v, int64_t frame, int64_t n
         }
     }
     free(dirs);
+}
+
+/* ------------------------------------------------------------------ */
+/* Dynamic objects (Sec. 6.3, second step of the initialisation listing) */
+/* ------------------------------------------------------------------ */
+/* Each dynamic object's box is extended on every side by one grid cell
+ * plus the largest self-shadow bias offset (0.75 D B); a SLEEPING probe
+ * inside an extended box becomes NEWLY_AWAKE, an AWAKE probe inside none
+ * goes back to SLEEPING.  Other states are untouched. */
+void or_wake(const or_volume* v, int64_t n, const int64_t* phys_ids, uint8_t* states) {
+    double ext[3];
+    double bias = 0.75 * min_spacing(v) * v->bias_B;
+    for (int a = 0; a < 3; ++a) ext[a] = v->spacing[a] + bias;
+    for (int64_t q = 0; q < n; ++q) {
+        int64_t p = phys_ids[q];
+        uint8_t s = states[p];
+        if (s != OR_SLEEPING && s != OR_AWAKE) continue;
+        double x[3];
+        probe_pos_phys(v, p, x);
+        int inside = 0;
+        for (int64_t b = 0; b < v->n_dyn && !inside; ++b) {
+            const double* bx = v->dyn_boxes + 6 * b;
+            inside = 1;
+            for (int a = 0; a < 3; ++a)
+                if (x[a] < bx[a] - ext[a] || x[a] > bx[3 + a] + ext[a]) inside = 0;
+        }
+        if (s == OR_SLEEPING && inside) states[p] = OR_NEWLY_AWAKE;
+        else if (s == OR_AWAKE && !inside) states[p] = OR_SLEEPING;
+    }
 }
 
 /* ------------------------------------------------------------------ */
@@ -739,6 +775,7 @@ void or_update(const or_scene* s, const or_lights* L, const or_volume* v, int64_
         if (nu) or_optimize(s, v, frame, nu, un);   /* no-op unless the optimizer is on */
         if (nu) or_classify(s, v, frame, nu, un, states, NULL, NULL);
         free(un);
+        or_wake(v, n, list, states);
     }
     /* 2. trace and shade every ray of every active probe against the old atlas */
     double* dirs = (double*)malloc(sizeof(double) * 3 * (size_t)R);
@@ -763,7 +800,7 @@ void or_update(const or_scene* s, const or_lights* L, const or_volume* v, int64_
     for (int64_t q = 0; q < n; ++q) {
         int64_t p = list[q];
         if (!is_active(states[p])) continue;
-        blend_probe(v, dirs, rays + q * R * 4, states[p] == OR_NEWLY_VIGILANT,
+        blend_probe(v, dirs, rays + q * R * 4, is_newly(states[p]),
                     irr_scale, vis_scale, irr + p * tsi, dist + p * tsd);
     }
     if (rays_out) {
@@ -773,7 +810,7 @@ void or_update(const or_scene* s, const or_lights* L, const or_volume* v, int64_
     }
     /* 4. state advance: Newly Vigilant -> Vigilant */
     for (int64_t q = 0; q < n; ++q)
-        if (states[list[q]] == OR_NEWLY_VIGILANT) states[list[q]] = OR_VIGILANT;
+        states[list[q]] = advanced(states[list[q]]);
     free(rays);
     free(dirs);
     free(list);
@@ -869,7 +906,7 @@ void or_update_cascade(const or_scene* s, const or_lights* L, int64_t n_vol, con
         for (int64_t q = 0; q < nl[k]; ++q) {
             int64_t p = lists[k][q];
             if (!is_active(states[k][p])) continue;
-            blend_probe(v, dirs, rays[k] + q * R * 4, states[k][p] == OR_NEWLY_VIGILANT, irr_scale, vis_scale,
+            blend_probe(v, dirs, rays[k] + q * R * 4, is_newly(states[k][p]), irr_scale, vis_scale,
                         irr[k] + p * irr_tile_size(v), dist[k] + p * dist_tile_size(v));
         }
         if (rays_out && rays_out[k])
@@ -877,7 +914,7 @@ void or_update_cascade(const or_scene* s, const or_lights* L, int64_t n_vol, con
                 if (is_active(states[k][lists[k][q]]))
                     memcpy(rays_out[k] + q * R * 4, rays[k] + q * R * 4, sizeof(double) * 4 * (size_t)R);
         for (int64_t q = 0; q < nl[k]; ++q)
-            if (states[k][lists[k][q]] == OR_NEWLY_VIGILANT) states[k][lists[k][q]] = OR_VIGILANT;
+            states[k][lists[k][q]] = advanced(states[k][lists[k][q]]);
         free(rays[k]);
         free(lists[k]);
     }

@@ -63,9 +63,12 @@ typedef struct {
     double* offsets;            /* [P][3] probe offsets from the grid (Sec. 5), or NULL */
     int64_t opt_iters;          /* position-optimizer iterations for uninitialised probes (0: off) */
     double  offset_limit;       /* largest offset per axis, as a fraction of the spacing */
+    const double* dyn_boxes;    /* [n_dyn][6] dynamic-object boxes (lo xyz, hi xyz), Sec. 6.3 */
+    int64_t n_dyn;
 } or_volume;
 
-enum { OR_UNINIT = 0, OR_OFF = 1, OR_SLEEPING = 2, OR_NEWLY_VIGILANT = 3, OR_VIGILANT = 4 };
+enum { OR_UNINIT = 0, OR_OFF = 1, OR_SLEEPING = 2, OR_NEWLY_VIGILANT = 3, OR_VIGILANT = 4,
+       OR_NEWLY_AWAKE = 5, OR_AWAKE = 6 };
 
 /* --- frame rays --- */
 uint64_t or_splitmix64_next(uint64_t* state);
@@ -91,6 +94,7 @@ int or_any_hit_shadow(const or_scene* s, const double o[3], const double d[3]);
 int64_t or_probe_phys(const or_volume* v, int64_t i, int64_t j, int64_t k);
 void or_probe_pos_logical(const or_volume* v, int64_t i, int64_t j, int64_t k, double x[3]);
 void or_optimize(const or_scene* s, const or_volume* v, int64_t frame, int64_t n, const int64_t* phys_ids);
+void or_wake(const or_volume* v, int64_t n, const int64_t* phys_ids, uint8_t* states);
 void or_classify(const or_scene* s, const or_volume* v, int64_t frame,
                  int64_t n, const int64_t* phys_ids, uint8_t* states,
                  int32_t* backface_count, double* dmin_front);
