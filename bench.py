@@ -374,6 +374,7 @@ def run_gpu(args):
     paper_res = None if args.no_paper_res else run_paper_resolution(args, g, torch, stream, scene, L, pos, nrm,
                                                                      camera, flush)
     optimizer = None if args.no_paper_res else run_optimizer(args, g, torch, stream, scene, L)
+    dynamic = None if args.no_paper_res else run_dynamic(args, g, torch, stream, scene, L, pos, nrm, camera, flush)
     cascade = None if args.no_cascade else run_cascade(args, g, torch, stream)
     diff = None if args.no_diff else run_diff(args, g, torch, stream)
 
@@ -431,6 +432,7 @@ def run_gpu(args):
             "frame_setup_ms": mixed[2]["frame_setup"][0] / max(mixed[2]["frame_setup"][1], 1)},
         "paper_resolution": paper_res,
         "position_optimizer": optimizer,
+        "dynamic_objects": dynamic,
         "cascade_batched": cascade,
         "differentiation": diff,
         "cpu_baseline": cpu,
@@ -537,6 +539,54 @@ def run_optimizer(args, g, torch, stream, scene, L):
     return out
 
 
+def run_dynamic(args, g, torch, stream, scene, L, pos, nrm, camera, flush):
+    """Dynamic objects (Sec. 6.3) in the city: 32 vehicle-sized boxes (4 x 1.5 x
+    2 m) flying straight lines over the streets at 5-30 m, where the sleeping
+    probes are, waking those near them; the same step as the headline (update
+    + 1080p query) with the boxes updated every frame."""
+    desc = synth.city_volume()
+    vol = g.Volume(desc)
+    out = torch.empty_like(pos)
+    rng = np.random.default_rng(4004)
+    lane = rng.integers(-7, 8, 32) * 4.0                 # street lines between the 4 m lots
+    start = rng.uniform(-30.0, 30.0, 32)
+    along_x = rng.integers(0, 2, 32).astype(bool)
+    height = rng.uniform(5.0, 30.0, 32)
+
+    def boxes(f):
+        s = (start + 0.5 * f + 30.0) % 60.0 - 30.0
+        c = np.stack([np.where(along_x, s, lane), height, np.where(along_x, lane, s)], 1)
+        h = np.where(along_x[:, None], [2.0, 0.75, 1.0], [1.0, 0.75, 2.0])
+        return np.concatenate([c - h, c + h], 1)
+
+    frame = 0
+    for _ in range(args.warmup):
+        vol.set_dynamic_boxes(boxes(frame))
+        vol.update(scene, L, frame, stream=stream)
+        vol.query(pos, nrm, camera, out, stream=stream)
+        frame += 1
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    awake = []
+    for k in range(args.steps):
+        vol.set_dynamic_boxes(boxes(frame))
+        flush.fill_(float(k))
+        evs[k][0].record(stream)
+        vol.update(scene, L, frame, stream=stream)
+        vol.query(pos, nrm, camera, out, stream=stream)
+        evs[k][1].record(stream)
+        frame += 1
+    torch.cuda.synchronize()
+    st = vol.states()
+    n_awake = int((st == g.STATE_AWAKE).sum().item())
+    n_active = int(((st == g.STATE_VIGILANT) | (st == g.STATE_AWAKE)).sum().item())
+    vol.poll_status()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    return {"workload": "city + 32 vehicle-sized boxes flying at 5-30 m, waking sleeping probes", "ms_per_step": ms,
+            "grays_per_s": n_active * desc.rays_per_probe / (ms * 1e-3) / 1e9, "awake_probes": n_awake,
+            "active_probes": n_active}
+
+
 def run_diff(args, g, torch, stream):
     """Differentiation: 16x8x16 probes (2,048, 128 rays) in a 192k-triangle
     interior with 64 emissive quads and 257 objects; two frames from a zero
@@ -593,7 +643,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the TF32 tensor-core blend timing")
     ap.add_argument("--no-cascade", action="store_true", help="skip the batched cascade workload")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation workload")
-    ap.add_argument("--no-paper-res", action="store_true", help="skip the paper-resolution tile variant")
+    ap.add_argument("--no-paper-res", action="store_true",
+                    help="skip the next-row lines (paper tile resolution, position optimizer, dynamic objects)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

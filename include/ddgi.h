@@ -57,7 +57,10 @@ enum {
     DDGI_STATE_OFF = 1,             /* inside static geometry: never traced (Sec. 6.1) */
     DDGI_STATE_SLEEPING = 2,        /* no surface within probe spacing (Sec. 6.2) */
     DDGI_STATE_NEWLY_VIGILANT = 3,  /* just classified; first update uses hysteresis 0 */
-    DDGI_STATE_VIGILANT = 4         /* traced and updated every frame */
+    DDGI_STATE_VIGILANT = 4,        /* traced and updated every frame */
+    DDGI_STATE_NEWLY_AWAKE = 5,     /* sleeping probe woken by a dynamic object (Sec. 6.3);
+                                       first update uses hysteresis 0 */
+    DDGI_STATE_AWAKE = 6            /* traced and updated while a dynamic object is near */
 };
 
 /* Atlas storage formats (precision variants; the paper does not fix one). */
@@ -243,6 +246,17 @@ ddgi_status ddgi_update(ddgi_volume volume, ddgi_scene scene, const ddgi_lights*
  * samples every probe of the volume's current atlas.  Running the shards of a
  * frame on copies of the same state and exchanging the updated ranges gives
  * the same atlas as one ddgi_update.  Errors: INVALID_ARG on a bad range. */
+/* Dynamic objects (Sec. 6.3): boxes_host [n][6] float (lo x, y, z, hi x,
+ * y, z), at most DDGI_MAX_DYNAMIC_BOXES; n = 0 clears them.  From the next
+ * update on, each update extends every box on each side by one probe
+ * spacing plus the largest self-shadow bias offset (0.75 D B), wakes the
+ * Sleeping probes inside an extended box (Newly Awake: traced and blended
+ * with hysteresis 0, then Awake) and puts Awake probes inside none back to
+ * Sleeping.  Needs the state machine; single volumes only (not cascades).
+ * Copies the boxes to the device synchronously.  Errors: INVALID_ARG. */
+#define DDGI_MAX_DYNAMIC_BOXES 1024
+ddgi_status ddgi_set_dynamic_boxes(ddgi_volume volume, const float* boxes_host, int32_t n);
+
 ddgi_status ddgi_update_range(ddgi_volume volume, ddgi_scene scene, const ddgi_lights* lights,
                               const ddgi_update_params* params, int64_t probe_begin, int64_t probe_end,
                               ddgi_stream stream);

@@ -18,6 +18,7 @@ _lib = None
 ERRORS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "NUMERIC", 6: "UNSUPPORTED"}
 
 STATE_UNINIT, STATE_OFF, STATE_SLEEPING, STATE_NEWLY_VIGILANT, STATE_VIGILANT = 0, 1, 2, 3, 4
+STATE_NEWLY_AWAKE, STATE_AWAKE = 5, 6
 IRR_FP32, IRR_FP16, IRR_RGB9E5 = 0, 1, 2
 DIST_FP32, DIST_FP16 = 0, 1
 BLEND_FP32, BLEND_TF32, BLEND_BF16 = 0, 1, 2
@@ -78,6 +79,7 @@ SIGNATURES = {
     "ddgi_update": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.POINTER(UpdateParams), _vp]),
     "ddgi_query": (C.c_int, [_vp, _vp, _vp, C.c_int64, F3, _vp, _vp]),
     "ddgi_query_glossy": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, _vp, _vp]),
+    "ddgi_set_dynamic_boxes": (C.c_int, [_vp, _vp, C.c_int32]),
     "ddgi_update_range": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.POINTER(UpdateParams), C.c_int64, C.c_int64,
                                     _vp]),
     "ddgi_get_buffer": (C.c_int, [_vp, C.c_int32, _vp, C.c_size_t, _vp]),

@@ -180,6 +180,12 @@ class Volume:
         L = lights if isinstance(lights, _lib.Lights) else lights_struct(lights)
         check(load().ddgi_update(self.handle, scene.handle, C.byref(L), C.byref(p), _stream(stream)))
 
+    def set_dynamic_boxes(self, boxes):
+        """Dynamic-object boxes [n, 6] (lo xyz, hi xyz) that wake sleeping probes
+        from the next update on (Sec. 6.3); an empty array clears them."""
+        b = _np(boxes, np.float32).reshape(-1, 6)
+        check(load().ddgi_set_dynamic_boxes(self.handle, b.ctypes.data if len(b) else None, len(b)))
+
     def update_range(self, scene: Scene, lights, frame: int, probe_begin: int, probe_end: int, irr_scale=1.0,
                      vis_scale=1.0, precision=_lib.BLEND_FP32, stream=None):
         """Update only probes [probe_begin, probe_end) (one shard of the grid)."""

@@ -157,6 +157,9 @@ struct ddgi_volume_s {
     float4* opt_dirs = nullptr;            // [R] rays of an optimizer iteration
     double* opt_dirs64 = nullptr;
     bool uninit_possible = true;           // some probe may still be UNINIT
+    float* dyn_boxes = nullptr;            // [DDGI_MAX_DYNAMIC_BOXES][6] extended boxes (device)
+    int32_t n_dyn = 0;
+    bool awake_possible = false;           // some probe may be Awake
     bool timing = false;
     TimedStage stages[8];
 };
@@ -464,7 +467,7 @@ void ddgi_volume_destroy(ddgi_volume v) {
     for (void* p : v->snap_dist) cudaFree(p);
     cudaFree(v->g_irr); cudaFree(v->g_prev);
     cudaFree(v->pack_irr); cudaFree(v->pack_dist); cudaFree(v->inv_irr_r); cudaFree(v->inv_dist_r);
-    cudaFree(v->offsets); cudaFree(v->opt_dirs); cudaFree(v->opt_dirs64);
+    cudaFree(v->offsets); cudaFree(v->opt_dirs); cudaFree(v->opt_dirs64); cudaFree(v->dyn_boxes);
     for (auto& st : v->stages)
         for (auto& pr : st.pending) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     delete v;
@@ -594,6 +597,28 @@ ddgi_status ddgi_update(ddgi_volume v, ddgi_scene s, const ddgi_lights* lights,
     return update_impl(v, s, lights, params, 0, v->P, stream);
 }
 
+ddgi_status ddgi_set_dynamic_boxes(ddgi_volume v, const float* boxes_host, int32_t n) {
+    if (!v) return fail(DDGI_ERR_INVALID_ARG, "volume is NULL");
+    if (n < 0 || n > DDGI_MAX_DYNAMIC_BOXES) return fail(DDGI_ERR_INVALID_ARG, "n must be in [0, DDGI_MAX_DYNAMIC_BOXES]");
+    if (n > 0 && !boxes_host) return fail(DDGI_ERR_INVALID_ARG, "boxes_host is NULL");
+    if (n > 0 && !v->desc.state_machine) return fail(DDGI_ERR_INVALID_ARG, "dynamic objects need the state machine");
+    const ddgi_volume_desc& d = v->desc;
+    const float bias = 0.75f * std::fmin(d.spacing[0], std::fmin(d.spacing[1], d.spacing[2])) * d.self_shadow_bias;
+    std::vector<float> ext((size_t)6 * n);
+    for (int32_t b = 0; b < n; ++b)
+        for (int a = 0; a < 3; ++a) {
+            const float lo = boxes_host[6 * b + a], hi = boxes_host[6 * b + 3 + a];
+            if (!std::isfinite(lo) || !std::isfinite(hi) || lo > hi)
+                return fail(DDGI_ERR_INVALID_ARG, "box with lo > hi or a non-finite bound");
+            ext[6 * b + a] = lo - (d.spacing[a] + bias);
+            ext[6 * b + 3 + a] = hi + (d.spacing[a] + bias);
+        }
+    if (!v->dyn_boxes) DDGI_CK(cudaMalloc(&v->dyn_boxes, sizeof(float) * 6 * DDGI_MAX_DYNAMIC_BOXES));
+    if (n > 0) DDGI_CK(cudaMemcpy(v->dyn_boxes, ext.data(), sizeof(float) * 6 * (size_t)n, cudaMemcpyHostToDevice));
+    v->n_dyn = n;
+    return DDGI_OK;
+}
+
 ddgi_status ddgi_update_range(ddgi_volume v, ddgi_scene s, const ddgi_lights* lights,
                               const ddgi_update_params* params, int64_t probe_begin, int64_t probe_end,
                               ddgi_stream stream) {
@@ -644,6 +669,13 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
         }
         DDGI_CK(launch_classify(s->dev, view, v->dirs, v->R, v->perm, v->lists, v->counts + 0, sms * 8, st));
         if (begin == 0 && end == v->P) v->uninit_possible = false;
+    }
+    // dynamic objects wake sleeping probes (and awake probes fall asleep
+    // again once none is near: one more pass after the boxes are cleared)
+    if (d.state_machine && (v->n_dyn > 0 || v->awake_possible)) {
+        StageTimer tm(v, 1, st);
+        DDGI_CK(launch_wake(view, v->dyn_boxes, v->n_dyn, (int)begin, (int)end, st));
+        v->awake_possible = v->n_dyn > 0;
     }
     {
         StageTimer tm(v, 1, st);

@@ -219,6 +219,8 @@ cudaError_t launch_blend_tc_set(const VolSet& vs, bool multi, const BlendParams&
 cudaError_t prepare_blend_tc_kernels();
 cudaError_t launch_query_glossy(const VolView& v, const float* pos, const float* nrm, const float* dirs, int64_t n,
                                 float* out, cudaStream_t st);
+// Dynamic-object wake-up over probes [begin, end); boxes [n][6] device, extended.
+cudaError_t launch_wake(const VolView& v, const float* boxes, int n_boxes, int begin, int end, cudaStream_t st);
 cudaError_t launch_query(const VolView& v, const float* pos, const float* nrm, int64_t n,
                          float3 camera, float* out, cudaStream_t st);
 cudaError_t launch_query_cascade(const VolSet& vs, const float* pos, const float* nrm, int64_t n, float3 camera,

@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256) k_blend_simt(VolSet vs, BlendParams bp,
             int e = active[g0 + threadIdx.x];
             s_probe[threadIdx.x] = e;
             s_newly[threadIdx.x] =
-                vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask] == DDGI_STATE_NEWLY_VIGILANT;
+                state_newly(vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask]);
         }
         for (int k = threadIdx.x; k < np * R; k += blockDim.x) {
             int pp = k / R, i = k - pp * R;
@@ -201,7 +201,10 @@ __global__ void __launch_bounds__(256) k_blend_simt(VolSet vs, BlendParams bp,
         __syncthreads();
         if (threadIdx.x < np && s_newly[threadIdx.x]) {
             const int e = s_probe[threadIdx.x];
-            vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask] = DDGI_STATE_VIGILANT;
+            {
+                uint8_t* sp = vol_of<MULTI>(vs, e >> kEntryShift).states + (e & kEntryMask);
+                *sp = state_advanced(*sp);
+            }
         }
         __syncthreads();
     }
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, B
             int e = active[g0 + threadIdx.x];
             s_probe[threadIdx.x] = e;
             s_newly[threadIdx.x] =
-                vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask] == DDGI_STATE_NEWLY_VIGILANT;
+                state_newly(vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask]);
         }
         // records -> planes, kRecBatch independent loads in flight per thread
         for (int k0 = threadIdx.x; k0 < PG * R; k0 += kRecBatch * blockDim.x) {
@@ -457,7 +460,10 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, B
         __syncthreads();
         if (threadIdx.x < np && s_newly[threadIdx.x]) {
             const int e = s_probe[threadIdx.x];
-            vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask] = DDGI_STATE_VIGILANT;
+            {
+                uint8_t* sp = vol_of<MULTI>(vs, e >> kEntryShift).states + (e & kEntryMask);
+                *sp = state_advanced(*sp);
+            }
         }
         __syncthreads();
     }

@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(VolSet vs, BlendParams bp, c
             int e = tid < np ? active[g0 + tid] : 0;
             s_probe[tid] = e;
             s_newly[tid] = tid < np &&
-                           vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask] == DDGI_STATE_NEWLY_VIGILANT;
+                           state_newly(vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask]);
         }
         for (int c = 0; c < nchunks; ++c) {
             const int s = c & 1;
@@ -414,7 +414,10 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(VolSet vs, BlendParams bp, c
         __syncthreads();
         if (tid < np && s_newly[tid]) {
             const int e = s_probe[tid];
-            vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask] = DDGI_STATE_VIGILANT;
+            {
+                uint8_t* sp = vol_of<MULTI>(vs, e >> kEntryShift).states + (e & kEntryMask);
+                *sp = state_advanced(*sp);
+            }
         }
         __syncthreads();
     }

@@ -76,6 +76,36 @@ __global__ void k_build_list(const uint8_t* __restrict__ states, int begin, int 
     }
 }
 
+// Dynamic-object wake-up (Sec. 6.3): probes [begin, end); a Sleeping probe
+// inside a box (already extended by one cell plus the self-shadow bias)
+// becomes Newly Awake, an Awake probe inside none goes back to Sleeping.
+__global__ void __launch_bounds__(256) k_wake(VolView v, const float* __restrict__ boxes, int n_boxes, int begin,
+                                              int end) {
+    extern __shared__ float sbox[];   // n_boxes x 6
+    for (int k = threadIdx.x; k < 6 * n_boxes; k += blockDim.x) sbox[k] = boxes[k];
+    __syncthreads();
+    for (int p = begin + blockIdx.x * blockDim.x + threadIdx.x; p < end; p += gridDim.x * blockDim.x) {
+        const uint8_t s = v.states[p];
+        if (s != DDGI_STATE_SLEEPING && s != DDGI_STATE_AWAKE) continue;
+        const float3 x = probe_pos_phys(v, p);
+        bool inside = false;
+        for (int b = 0; b < n_boxes && !inside; ++b) {
+            const float* bx = sbox + 6 * b;
+            inside = x.x >= bx[0] && x.y >= bx[1] && x.z >= bx[2] && x.x <= bx[3] && x.y <= bx[4] && x.z <= bx[5];
+        }
+        if (s == DDGI_STATE_SLEEPING && inside) v.states[p] = DDGI_STATE_NEWLY_AWAKE;
+        else if (s == DDGI_STATE_AWAKE && !inside) v.states[p] = DDGI_STATE_SLEEPING;
+    }
+}
+
+cudaError_t launch_wake(const VolView& v, const float* boxes, int n_boxes, int begin, int end, cudaStream_t st) {
+    if (end <= begin) return cudaSuccess;
+    int blocks = (end - begin + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_wake<<<blocks, 256, sizeof(float) * 6 * (size_t)n_boxes, st>>>(v, boxes, n_boxes, begin, end);
+    return cudaGetLastError();
+}
+
 // Cascade query (Sec. 7.3): one thread per point, volumes densest first.
 __global__ void __launch_bounds__(256) k_query_cascade(VolSet vs, const float* __restrict__ pos,
                                                        const float* __restrict__ nrm, int64_t n, float3 cam,

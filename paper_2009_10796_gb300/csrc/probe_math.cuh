@@ -83,8 +83,20 @@ __device__ __forceinline__ float3 probe_pos_phys(const VolView& v, int p) {
     return x;
 }
 
+// Traced, blended and used by the query: vigilant probes and sleeping probes
+// woken by a dynamic object (Sec. 6.3).
 __device__ __forceinline__ bool state_active(uint8_t s) {
-    return s == DDGI_STATE_NEWLY_VIGILANT || s == DDGI_STATE_VIGILANT;
+    return s == DDGI_STATE_NEWLY_VIGILANT || s == DDGI_STATE_VIGILANT || s == DDGI_STATE_NEWLY_AWAKE ||
+           s == DDGI_STATE_AWAKE;
+}
+// First update after becoming active: blended with hysteresis 0.
+__device__ __forceinline__ bool state_newly(uint8_t s) {
+    return s == DDGI_STATE_NEWLY_VIGILANT || s == DDGI_STATE_NEWLY_AWAKE;
+}
+// The state after a probe's update.
+__device__ __forceinline__ uint8_t state_advanced(uint8_t s) {
+    return s == DDGI_STATE_NEWLY_VIGILANT ? (uint8_t)DDGI_STATE_VIGILANT
+                                          : (s == DDGI_STATE_NEWLY_AWAKE ? (uint8_t)DDGI_STATE_AWAKE : s);
 }
 
 // Bilinear footprint in a bordered tile of n interior texels: the octahedral
