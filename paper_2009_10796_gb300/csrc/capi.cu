@@ -130,7 +130,8 @@ struct ddgi_volume_s {
     void* irr = nullptr;
     void* dist = nullptr;
     int32_t* lists = nullptr;      // [0, P): uninit list, [P, 2P): active list
-    int32_t* counts = nullptr;     // [0] uninit count, [1] active count
+    int32_t* counts = nullptr;     // [0] uninit count, [1] active count, [4..9] trace counters
+                                   // (shadow_count below), all cleared by one memset per frame
     uint32_t* status = nullptr;
     float4* records = nullptr;     // [P * R]
     float4* dirs = nullptr;        // [R]
@@ -462,7 +463,7 @@ void ddgi_volume_destroy(ddgi_volume v) {
     cudaFree(v->states); cudaFree(v->irr); cudaFree(v->dist); cudaFree(v->lists); cudaFree(v->counts);
     cudaFree(v->status); cudaFree(v->records); cudaFree(v->dirs); cudaFree(v->dirs64); cudaFree(v->w_irr);
     cudaFree(v->inv_s_irr); cudaFree(v->w_dist); cudaFree(v->inv_s_dist); cudaFree(v->stats);
-    cudaFree(v->shadow_list); cudaFree(v->hit_list); cudaFree(v->shadow_count); cudaFree(v->perm);
+    cudaFree(v->shadow_list); cudaFree(v->hit_list); cudaFree(v->perm);
     for (void* p : v->snap_irr) cudaFree(p);
     for (void* p : v->snap_dist) cudaFree(p);
     cudaFree(v->g_irr); cudaFree(v->g_prev);
@@ -502,7 +503,7 @@ ddgi_status ddgi_volume_create(const ddgi_volume_desc* desc, ddgi_volume* out) {
     A(&v->irr, v->irr_bytes);
     A(&v->dist, v->dist_bytes);
     A((void**)&v->lists, sizeof(int32_t) * 2 * (size_t)v->P);
-    A((void**)&v->counts, sizeof(int32_t) * 4);
+    A((void**)&v->counts, sizeof(int32_t) * kCounterInts);
     A((void**)&v->status, sizeof(uint32_t));
     A((void**)&v->records, sizeof(float4) * (size_t)v->P * v->R);
     A((void**)&v->dirs, sizeof(float4) * v->R);
@@ -519,7 +520,6 @@ ddgi_status ddgi_volume_create(const ddgi_volume_desc* desc, ddgi_volume* out) {
     A((void**)&v->stats, sizeof(unsigned long long) * 8);
     A((void**)&v->shadow_list, sizeof(int32_t) * (size_t)v->P * v->R);
     A((void**)&v->hit_list, sizeof(int32_t) * (size_t)v->P * v->R);
-    A((void**)&v->shadow_count, sizeof(int32_t) * 4);
     A((void**)&v->perm, sizeof(int32_t) * v->R);
     if (e == cudaSuccess) {
         std::vector<int32_t> perm = ray_order_morton(v->R);
@@ -533,7 +533,8 @@ ddgi_status ddgi_volume_create(const ddgi_volume_desc* desc, ddgi_volume* out) {
     if (e == cudaSuccess) e = cudaMemset(v->irr, 0, v->irr_bytes);
     if (e == cudaSuccess) e = cudaMemset(v->dist, 0, v->dist_bytes);
     if (e == cudaSuccess) e = cudaMemset(v->offsets, 0, sizeof(float4) * (size_t)v->P);
-    if (e == cudaSuccess) e = cudaMemset(v->counts, 0, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMemset(v->counts, 0, sizeof(int32_t) * kCounterInts);
+    v->shadow_count = v->counts + 4;
     if (e == cudaSuccess) e = cudaMemset(v->status, 0, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -652,7 +653,7 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
                                         params->blend_precision == DDGI_BLEND_BF16, v->pack_irr, v->pack_dist,
                                         v->inv_irr_r, v->inv_dist_r, st));
     }
-    DDGI_CK(cudaMemsetAsync(v->counts, 0, sizeof(int32_t) * 2, st));
+    DDGI_CK(cudaMemsetAsync(v->counts, 0, sizeof(int32_t) * kCounterInts, st));   // lists and trace counters
     // uninitialised probes (none after a full-range update, until states are
     // set again): position optimizer iterations, then classification
     if (d.state_machine && v->uninit_possible) {
@@ -939,7 +940,7 @@ namespace {
 void cascade_free(ddgi_cascade_s* c) {
     for (int k = 0; k < c->n; ++k) { cudaFree(c->states[k]); cudaFree(c->irr[k]); cudaFree(c->dist[k]); }
     cudaFree(c->lists); cudaFree(c->counts); cudaFree(c->status); cudaFree(c->records);
-    cudaFree(c->shadow_list); cudaFree(c->hit_list); cudaFree(c->shadow_count); cudaFree(c->perm); cudaFree(c->dirs);
+    cudaFree(c->shadow_list); cudaFree(c->hit_list); cudaFree(c->perm); cudaFree(c->dirs);
     cudaFree(c->dirs64);
     cudaFree(c->w_irr);
     cudaFree(c->inv_s_irr); cudaFree(c->w_dist); cudaFree(c->inv_s_dist); cudaFree(c->pack_irr);
@@ -1034,7 +1035,7 @@ ddgi_status cascade_enqueue(ddgi_cascade_s* c, const DevScene& sc, const Lights&
     if (tensor)
         DDGI_CK(launch_pack_weights(c->w_irr, c->w_dist, c->R, d0.irr_n, d0.dist_n, precision == DDGI_BLEND_BF16,
                                     c->pack_irr, c->pack_dist, c->inv_irr_r, c->inv_dist_r, st));
-    DDGI_CK(cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 2, st));
+    DDGI_CK(cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * kCounterInts, st));   // lists and trace counters
     DDGI_CK(launch_build_list_multi(vs, (int)c->total, 0, c->lists, c->counts + 0, st));
     DDGI_CK(launch_classify_multi(sc, vs, c->dirs, c->R, c->perm, c->lists, c->counts + 0, sms * 8, st));
     DDGI_CK(launch_build_list_multi(vs, (int)c->total, 1, c->lists + c->total, c->counts + 1, st));
@@ -1107,12 +1108,12 @@ ddgi_status ddgi_cascade_create(const ddgi_volume_desc* descs, int32_t n, ddgi_c
     }
     const ddgi_volume_desc& d0 = descs[0];
     A((void**)&c->lists, sizeof(int32_t) * 2 * (size_t)c->total);
-    A((void**)&c->counts, sizeof(int32_t) * 4);
+    A((void**)&c->counts, sizeof(int32_t) * kCounterInts);
+    c->shadow_count = c->counts + 4;
     A((void**)&c->status, sizeof(uint32_t));
     A((void**)&c->records, sizeof(float4) * (size_t)c->total * c->R);
     A((void**)&c->shadow_list, sizeof(int32_t) * (size_t)c->total * c->R);
     A((void**)&c->hit_list, sizeof(int32_t) * (size_t)c->total * c->R);
-    A((void**)&c->shadow_count, sizeof(int32_t) * 4);
     A((void**)&c->dirs, sizeof(float4) * c->R);
     A((void**)&c->dirs64, sizeof(double) * 3 * c->R);
     A((void**)&c->perm, sizeof(int32_t) * c->R);

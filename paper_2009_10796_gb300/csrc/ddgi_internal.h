@@ -165,11 +165,17 @@ cudaError_t launch_classify_multi(const DevScene& s, const VolSet& vs, const flo
 cudaError_t launch_trace_shade(const DevScene& s, const VolView& v, const Lights& L,
                                const float4* dirs, int R, const int32_t* active,
                                const int32_t* count, float4* records, int grid, cudaStream_t st);
+// Per-volume device counters, one block cleared by one memset per frame:
+// [0] uninitialised-list count, [1] active-list count, [4..9] the trace's
+// counters (shadow_count below).
+constexpr int kCounterInts = 10;
+
 // Wavefront trace: persistent primary pass (closest hits; final records of
 // misses and back faces; lists of shadow rays and of front hits), persistent
 // shadow pass, then shading of the front hits.  shadow_list and hit_list
-// hold one int32 per ray (active probes x R); shadow_count is 4 int32 of
-// device scratch, 8-byte aligned (shadow rays, front hits, 64-bit work counter).
+// hold one int32 per ray (active probes x R); shadow_count is 6 int32 of
+// device scratch, 8-byte aligned, zeroed by the caller: shadow rays, front
+// hits, the 64-bit work counters of the primary and the shadow pass.
 // marks: 4 events recorded around the three passes, or nullptr.
 cudaError_t launch_trace_wavefront(const DevScene& s, const VolView& v, const Lights& L, const float4* dirs,
                                    int R, const int32_t* perm, const int32_t* active, const int32_t* count,

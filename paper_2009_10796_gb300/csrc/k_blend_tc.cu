@@ -4,8 +4,8 @@
 // (Eq. 1) is a dense contraction per frame:
 //   irradiance  D_irr[t][(p,c)]  = sum_i W_irr[t][i]  * L[p][i][c]     c in {r, g, b}
 //   distance    D_dist[t][(p,c)] = sum_i W_dist[t][i] * X[p][i][c]     c in {d_hi, d_lo, d2_hi, d2_lo}
-// A persistent CTA (one per SM) takes groups of 32 active probes and walks the
-// rays in chunks of 32:
+// A persistent CTA (one per SM, 256 threads) takes groups of 32 active probes
+// and walks the rays in chunks of 32:
 //   * the weight tiles of the chunk (pre-packed by k_pack_weights in the
 //     operand layout) arrive by two bulk TMA copies, completion counted on an
 //     mbarrier;
@@ -41,7 +41,7 @@ namespace {
 
 constexpr int PG = 32;                       // probes per group
 constexpr int KC = 32;                       // rays per chunk
-constexpr int NT = 128;                      // threads per CTA
+constexpr int NT = 256;                      // threads per CTA: staging, TMEM readback, epilogue
 constexpr int IRR_N = 3 * PG;                // 96 accumulator columns
 constexpr int DIST_N = 4 * PG;               // 128 accumulator columns
 constexpr uint32_t COL_IRR = 0, COL_DIST0 = 128, COL_DIST1 = 256, TMEM_COLS = 512;
@@ -53,11 +53,16 @@ constexpr uint32_t OFF_A_DIST = OFF_A_IRR + A_IRR_MAX;
 constexpr uint32_t OFF_B_IRR = OFF_A_DIST + A_DIST_BYTES;
 constexpr uint32_t OFF_B_DIST = OFF_B_IRR + IRR_N * KC * 4;
 constexpr uint32_t STAGE_BYTES = OFF_B_DIST + DIST_N * KC * 4;   // 77,824 B
+// accumulator rows in shared memory for the epilogue, padded by one float so
+// a warp reading one column of consecutive rows hits distinct banks
+constexpr int DIRR_STRIDE = IRR_N + 1;
+constexpr int DDIST_STRIDE = DIST_N + 1;
 // two stages plus slack: an operand read of up to 256 rows from the last
-// tile, and the epilogue's accumulator copy (128 x 96 + 256 x 128 floats),
+// tile, and the epilogue's accumulator copy (128 x 97 + 256 x 129 floats),
 // both stay inside the allocation
 constexpr uint32_t SMEM_BYTES = 2 * STAGE_BYTES + 32768;
-constexpr uint32_t OFF_D_DIST = 128 * IRR_N * 4;
+constexpr uint32_t OFF_D_DIST = 128 * DIRR_STRIDE * 4;
+static_assert(OFF_D_DIST + 256 * DDIST_STRIDE * 4 <= SMEM_BYTES, "epilogue copy fits");
 
 constexpr uint32_t kWaitLimit = 1u << 22;
 
@@ -368,43 +373,50 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(VolSet vs, BlendParams bp, c
         abort = __syncthreads_or(abort);
         if (abort) break;
         tc_fence_after();
-        // accumulators -> shared memory (stage buffers are free now)
+        // accumulators -> shared memory (stage buffers are free now); warp w
+        // reads TMEM lanes 32 (w % 4) .. + 31, the two warps of a lane quarter
+        // splitting the columns
         float* Dirr = reinterpret_cast<float*>(smem);
         float* Ddist = reinterpret_cast<float*>(smem + OFF_D_DIST);
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        const int row = warp * 32 + lane;
-        if (warp * 32 < ti) {
-            for (int cb = 0; cb < IRR_N; cb += 16) {
+        const int quarter = warp & 3, half = warp >> 2;
+        const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+        const int row = quarter * 32 + lane;
+        if (quarter * 32 < ti) {
+            for (int cb = half * (IRR_N / 2); cb < (half + 1) * (IRR_N / 2); cb += 16) {
                 float r16[16];
                 tmem_ld16(tmem + lane_base + COL_IRR + cb, r16);
                 if (row < ti)
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) Dirr[row * IRR_N + cb + j] = r16[j];
+                    for (int j = 0; j < 16; ++j) Dirr[row * DIRR_STRIDE + cb + j] = r16[j];
             }
         }
         for (int m = 0; m < 2; ++m) {
-            if (m * 128 + warp * 32 >= td) continue;
+            if (m * 128 + quarter * 32 >= td) continue;
             const int drow = m * 128 + row;
-            for (int cb = 0; cb < DIST_N; cb += 16) {
+            for (int cb = half * (DIST_N / 2); cb < (half + 1) * (DIST_N / 2); cb += 16) {
                 float r16[16];
                 tmem_ld16(tmem + lane_base + (m ? COL_DIST1 : COL_DIST0) + cb, r16);
                 if (drow < td)
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) Ddist[drow * DIST_N + cb + j] = r16[j];
+                    for (int j = 0; j < 16; ++j) Ddist[drow * DDIST_STRIDE + cb + j] = r16[j];
             }
         }
         tc_fence_before();
         __syncthreads();
+        // epilogue: consecutive threads on consecutive texels of one probe,
+        // two texels in flight per thread
+#pragma unroll 2
         for (int q = tid; q < ti * np; q += NT) {
-            int t = q / np, pp = q - t * np;
-            const float* a = Dirr + t * IRR_N + 3 * pp;
+            const int pp = q / ti, t = q - pp * ti;
+            const float* a = Dirr + t * DIRR_STRIDE + 3 * pp;
             const int e = s_probe[pp];
             blend_irr_texel(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, t, a[0], a[1], a[2],
                             __ldg(inv_irr + t), s_newly[pp] != 0, status);
         }
+#pragma unroll 2
         for (int q = tid; q < td * np; q += NT) {
-            int t = q / np, pp = q - t * np;
-            const float* a = Ddist + t * DIST_N + 4 * pp;
+            const int pp = q / td, t = q - pp * td;
+            const float* a = Ddist + t * DDIST_STRIDE + 4 * pp;
             const int e = s_probe[pp];
             blend_dist_texel(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, t, a[0] + a[1], a[2] + a[3],
                              __ldg(inv_dist + t), s_newly[pp] != 0, status);

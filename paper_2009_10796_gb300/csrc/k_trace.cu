@@ -518,19 +518,18 @@ static cudaError_t trace_wavefront(const DevScene& s, const VolSet& vs, const Li
                                    const int32_t* perm, const int32_t* active, const int32_t* count,
                                    float4* records, int32_t* shadow_list, int32_t* hit_list, int32_t* shadow_count,
                                    int grid, cudaStream_t st, cudaEvent_t* marks) {
-    // shadow_count[0]: shadow rays; [1]: front hits; [2..3]: the 64-bit work
-    // counter of the persistent passes, zeroed before each
+    // shadow_count (zeroed by the caller): [0] shadow rays, [1] front hits,
+    // [2..3] and [4..5] the 64-bit work counters of the two persistent passes
     unsigned long long* next = reinterpret_cast<unsigned long long*>(shadow_count + 2);
-    cudaError_t e = cudaMemsetAsync(shadow_count, 0, 4 * sizeof(int32_t), st);
-    if (e != cudaSuccess) return e;
+    unsigned long long* next_shadow = reinterpret_cast<unsigned long long*>(shadow_count + 4);
+    cudaError_t e = cudaSuccess;
     if (marks && (e = cudaEventRecord(marks[0], st)) != cudaSuccess) return e;
     k_trace_primary<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, perm, active, count, records, shadow_list,
                                                   hit_list, shadow_count, next);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
     if (marks && (e = cudaEventRecord(marks[1], st)) != cudaSuccess) return e;
     k_trace_shadow<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, active, records, shadow_list, shadow_count,
-                                                 next);
+                                                 next_shadow);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (marks && (e = cudaEventRecord(marks[2], st)) != cudaSuccess) return e;
     k_shade<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, active, hit_list, shadow_count + 1, records);
@@ -545,14 +544,14 @@ cudaError_t launch_trace_count(const DevScene& s, const VolView& v, const Lights
                                unsigned long long* stats, int grid, cudaStream_t st) {
     const VolSet vs = single_set(v);
     unsigned long long* next = reinterpret_cast<unsigned long long*>(shadow_count + 2);
-    cudaError_t e = cudaMemsetAsync(shadow_count, 0, 4 * sizeof(int32_t), st);
+    unsigned long long* next_shadow = reinterpret_cast<unsigned long long*>(shadow_count + 4);
+    cudaError_t e = cudaMemsetAsync(shadow_count, 0, 6 * sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     k_trace_primary<false, true><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, perm, active, count, records,
                                                         shadow_list, hit_list, shadow_count, next, stats);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
     k_trace_shadow<false, true><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, active, records, shadow_list,
-                                                       shadow_count, next, stats);
+                                                       shadow_count, next_shadow, stats);
     return cudaGetLastError();
 }
 

@@ -224,25 +224,42 @@ __device__ __forceinline__ void store_dist(const VolView& v, int p, int x, int y
 
 // Bilinear samples at a footprint: one storage-format dispatch per sample,
 // then the four taps (rows y0, y0 + 1 of the bordered tile).
-__device__ __forceinline__ float3 bilerp3(const Footprint& f, float3 a, float3 b, float3 c, float3 d) {
-    float w00 = (1.0f - f.tx) * (1.0f - f.ty), w10 = f.tx * (1.0f - f.ty);
-    float w01 = (1.0f - f.tx) * f.ty, w11 = f.tx * f.ty;
-    return f3(w00 * a.x + w10 * b.x + w01 * c.x + w11 * d.x,
-              w00 * a.y + w10 * b.y + w01 * c.y + w11 * d.y,
-              w00 * a.z + w10 * b.z + w01 * c.z + w11 * d.z);
+struct Bilerp {
+    float w00, w10, w01, w11;
+};
+
+__device__ __forceinline__ Bilerp bilerp_weights(const Footprint& f) {
+    Bilerp b;
+    b.w00 = (1.0f - f.tx) * (1.0f - f.ty);
+    b.w10 = f.tx * (1.0f - f.ty);
+    b.w01 = (1.0f - f.tx) * f.ty;
+    b.w11 = f.tx * f.ty;
+    return b;
 }
 
-__device__ __forceinline__ float3 sample_irr_at(const VolView& v, int p, const Footprint& f) {
+__device__ __forceinline__ float3 bilerp3(const Bilerp& w, float3 a, float3 b, float3 c, float3 d) {
+    return f3(w.w00 * a.x + w.w10 * b.x + w.w01 * c.x + w.w11 * d.x,
+              w.w00 * a.y + w.w10 * b.y + w.w01 * c.y + w.w11 * d.y,
+              w.w00 * a.z + w.w10 * b.z + w.w01 * c.z + w.w11 * d.z);
+}
+
+// Irradiance at a footprint whose bilinear weights are already known (the
+// query reads every cage probe at the same footprint).
+__device__ __forceinline__ float3 sample_irr_at(const VolView& v, int p, const Footprint& f, const Bilerp& w) {
     const int row = v.irr_n + 2;
     const int64_t t = (int64_t)p * v.irr_tile + (int64_t)f.y0 * row + f.x0;
     if (v.irr_format == DDGI_IRR_FP32) {
         const float4* a = (const float4*)v.irr + t;
         const float4 q00 = __ldg(a), q10 = __ldg(a + 1), q01 = __ldg(a + row), q11 = __ldg(a + row + 1);
-        return bilerp3(f, f3(q00.x, q00.y, q00.z), f3(q10.x, q10.y, q10.z), f3(q01.x, q01.y, q01.z),
+        return bilerp3(w, f3(q00.x, q00.y, q00.z), f3(q10.x, q10.y, q10.z), f3(q01.x, q01.y, q01.z),
                        f3(q11.x, q11.y, q11.z));
     }
-    return bilerp3(f, load_irr(v, p, f.x0, f.y0), load_irr(v, p, f.x0 + 1, f.y0), load_irr(v, p, f.x0, f.y0 + 1),
+    return bilerp3(w, load_irr(v, p, f.x0, f.y0), load_irr(v, p, f.x0 + 1, f.y0), load_irr(v, p, f.x0, f.y0 + 1),
                    load_irr(v, p, f.x0 + 1, f.y0 + 1));
+}
+
+__device__ __forceinline__ float3 sample_irr_at(const VolView& v, int p, const Footprint& f) {
+    return sample_irr_at(v, p, f, bilerp_weights(f));
 }
 
 __device__ __forceinline__ float2 sample_dist_at(const VolView& v, int p, const Footprint& f) {
@@ -319,10 +336,15 @@ __device__ __forceinline__ float3 query_M_look(const VolView& v, float3 x, float
     float sumw = 0.0f;
     float3 acc = f3(0.0f, 0.0f, 0.0f);
     const Footprint fn = footprint(oct_encode(look), v.irr_n);   // irradiance lookup, the same for every probe
+    const Bilerp wn = bilerp_weights(fn);
+    // physical indices of the cage's two planes per axis
+    const int px0 = wrap_add(base[0], v.shift.x, cnt[0]), px1 = wrap_add(base[0] + 1, v.shift.x, cnt[0]);
+    const int py0 = wrap_add(base[1], v.shift.y, cnt[1]), py1 = wrap_add(base[1] + 1, v.shift.y, cnt[1]);
+    const int pz0 = wrap_add(base[2], v.shift.z, cnt[2]), pz1 = wrap_add(base[2] + 1, v.shift.z, cnt[2]);
 #pragma unroll 1
     for (int c = 0; c < 8; ++c) {
         int o0 = c & 1, o1 = (c >> 1) & 1, o2 = (c >> 2) & 1;
-        int p = probe_phys(v, base[0] + o0, base[1] + o1, base[2] + o2);
+        int p = (o0 ? px1 : px0) + cnt[0] * ((o1 ? py1 : py0) + cnt[1] * (o2 ? pz1 : pz0));
         if (!state_active(v.states[p])) continue;
         float3 xp = probe_pos_logical(v, base[0] + o0, base[1] + o1, base[2] + o2);
         if (v.offsets) {   // the probe's own (moved) position; the cage stays on the grid
@@ -349,7 +371,7 @@ __device__ __forceinline__ float3 query_M_look(const VolView& v, float3 x, float
             }
         }
         float w = wt * wb * fmaxf(wc, 1e-6f);
-        float3 e = sample_irr_at(v, p, fn);
+        float3 e = sample_irr_at(v, p, fn, wn);
         acc.x += w * gamma_decode_half_fast(e.x, v.half_gamma);
         acc.y += w * gamma_decode_half_fast(e.y, v.half_gamma);
         acc.z += w * gamma_decode_half_fast(e.z, v.half_gamma);
