@@ -305,29 +305,27 @@ def run_gpu(args):
     rays_per_step = n_active * R
     value = world * rays_per_step / (ms_max * 1e-3) / 1e9
 
-    # end to end through the public API with host buffers: pinned G-buffer in,
-    # irradiance out, every step
+    # end to end through the C-ABI frame call with host buffers: pinned
+    # G-buffer copied in (alongside the probe update), irradiance copied out
+    # (chunked behind the query), every step
     pos_h = pos.cpu().pin_memory()
     nrm_h = nrm.cpu().pin_memory()
     out_h = torch.empty_like(pos_h).pin_memory()
-    pos_d = torch.empty_like(pos)
-    nrm_d = torch.empty_like(nrm)
+    vol.frame_host(scene, L, frame, pos_h, nrm_h, camera, out_h, stream=stream)   # staging allocation
+    frame += 1
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for k in range(args.steps):
-        pos_d.copy_(pos_h, non_blocking=True)
-        nrm_d.copy_(nrm_h, non_blocking=True)
-        vol.update(scene, L, frame, stream=stream)
-        vol.query(pos_d, nrm_d, camera, out, stream=stream)
-        out_h.copy_(out, non_blocking=True)
+    eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for k in range(args.steps):   # L2 flushed between steps outside the events
+        flush.fill_(float(k))
+        eev[k][0].record(stream)
+        vol.frame_host(scene, L, frame, pos_h, nrm_h, camera, out_h, stream=stream)
+        eev[k][1].record(stream)
         frame += 1
-    e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
+    e2e_ms = float(np.mean([a.elapsed_time(b) for a, b in eev]))
     t = torch.tensor([e2e_ms], device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -390,7 +388,9 @@ def run_gpu(args):
                          f"query points "
                          f"({t_q:.2f} s), extrapolated to {n_act_cpu} active probes (oracle's own "
                          f"estimate) + {n_pix} pixels"}
-    launches_per_step = 10  # frame directions + weights, 2 list builds, classify, 3 trace passes, blend, query
+    # steady-state frame: directions + weights, 3 trace passes, blend, query (the
+    # active list is kept and classification skipped once no probe is uninitialised)
+    launches_per_step = 7
     line = {
         "metric": METRIC, "value": value, "unit": "Grays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",

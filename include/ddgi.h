@@ -271,6 +271,23 @@ ddgi_status ddgi_update_range(ddgi_volume volume, ddgi_scene scene, const ddgi_l
 ddgi_status ddgi_query(ddgi_volume volume, const float* pos_dev, const float* nrm_dev, int64_t n,
                        const float camera_pos[3], float* out_dev, ddgi_stream stream);
 
+/* One frame from host memory: ddgi_update (Sec. 2.3) then ddgi_query
+ * (Sec. 2.2) of n points whose G-buffer lives on the host.
+ *   pos_host, nrm_host [n][3] float, host; out_host [n][3] float, host.
+ * The input copy runs on an internal stream while the probe update runs on
+ * `stream`; the query then runs in chunks whose result copies overlap the
+ * next chunk's query.  Asynchronous like the other calls: out_host holds
+ * the irradiance once `stream` has completed the work enqueued here; the
+ * host arrays must stay valid and unchanged until then.  Page-locked host
+ * memory keeps the copies asynchronous; pageable memory works but
+ * serialises them.  The volume owns the device staging buffers (three of
+ * n*12 bytes); a call with a larger n than any before synchronises
+ * `stream` and reallocates them.  Errors: those of ddgi_update and
+ * ddgi_query, INVALID_ARG on a NULL host array with n > 0. */
+ddgi_status ddgi_frame_host(ddgi_volume volume, ddgi_scene scene, const ddgi_lights* lights,
+                            const ddgi_update_params* params, const float* pos_host, const float* nrm_host,
+                            int64_t n, const float camera_pos[3], float* out_host, ddgi_stream stream);
+
 /* Second-order glossy lookup (Sec. 4.4): the probes reused as prefiltered
  * radiance at reflection-ray hits.  pos_dev, nrm_dev: [n][3] float hit
  * points and unit normals; dir_dev: [n][3] float unit directions the hits

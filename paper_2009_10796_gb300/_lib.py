@@ -79,6 +79,8 @@ SIGNATURES = {
     "ddgi_update": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.POINTER(UpdateParams), _vp]),
     "ddgi_query": (C.c_int, [_vp, _vp, _vp, C.c_int64, F3, _vp, _vp]),
     "ddgi_query_glossy": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, _vp, _vp]),
+    "ddgi_frame_host": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.POINTER(UpdateParams), _vp, _vp, C.c_int64, F3,
+                                  _vp, _vp]),
     "ddgi_set_dynamic_boxes": (C.c_int, [_vp, _vp, C.c_int32]),
     "ddgi_update_range": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.POINTER(UpdateParams), C.c_int64, C.c_int64,
                                     _vp]),

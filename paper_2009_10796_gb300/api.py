@@ -203,6 +203,27 @@ class Volume:
                                 _stream(stream)))
         return out
 
+    def frame_host(self, scene: Scene, lights, frame: int, pos: torch.Tensor, nrm: torch.Tensor, camera,
+                   out: torch.Tensor = None, irr_scale=1.0, vis_scale=1.0, precision=_lib.BLEND_FP32,
+                   stream=None) -> torch.Tensor:
+        """One frame from host memory: the probe update, then the query of the
+        host G-buffer `pos`, `nrm` ([n, 3] float32 CPU tensors, best pinned)
+        into the host tensor `out`.  Asynchronous: `out` is complete once
+        `stream` has run the enqueued work (synchronise it before reading)."""
+        for t in (pos, nrm) + ((out,) if out is not None else ()):
+            if t.device.type != "cpu" or t.dtype != torch.float32 or not t.is_contiguous():
+                raise ValueError("frame_host takes contiguous float32 CPU tensors")
+        n = pos.shape[0]
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+        if any(t.dim() != 2 or t.shape != (n, 3) for t in (pos, nrm, out)):
+            raise ValueError("pos, nrm and out must be [n, 3]")
+        p = _lib.UpdateParams(int(frame), float(irr_scale), float(vis_scale), int(precision), 0)
+        L = lights if isinstance(lights, _lib.Lights) else lights_struct(lights)
+        check(load().ddgi_frame_host(self.handle, scene.handle, C.byref(L), C.byref(p), pos.data_ptr(),
+                                     nrm.data_ptr(), n, _f3(camera), out.data_ptr(), _stream(stream)))
+        return out
+
     def query_glossy(self, pos: torch.Tensor, nrm: torch.Tensor, dirs: torch.Tensor, out: torch.Tensor = None,
                      stream=None) -> torch.Tensor:
         """Prefiltered radiance M read in the mirror direction at reflection-ray

@@ -161,6 +161,13 @@ struct ddgi_volume_s {
     float* dyn_boxes = nullptr;            // [DDGI_MAX_DYNAMIC_BOXES][6] extended boxes (device)
     int32_t n_dyn = 0;
     bool awake_possible = false;           // some probe may be Awake
+    int64_t list_begin = -1, list_end = -1; // range of the active list built last, if still valid
+    // ddgi_frame_host: device staging of host G-buffers, copy streams, events
+    float* stage = nullptr;                // [3][stage_cap][3] float: positions, normals, results
+    int64_t stage_cap = 0;
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;
+    cudaEvent_t ev_entry = nullptr, ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_chunk[4] = {nullptr, nullptr, nullptr, nullptr};
     bool timing = false;
     TimedStage stages[8];
 };
@@ -469,6 +476,12 @@ void ddgi_volume_destroy(ddgi_volume v) {
     cudaFree(v->g_irr); cudaFree(v->g_prev);
     cudaFree(v->pack_irr); cudaFree(v->pack_dist); cudaFree(v->inv_irr_r); cudaFree(v->inv_dist_r);
     cudaFree(v->offsets); cudaFree(v->opt_dirs); cudaFree(v->opt_dirs64); cudaFree(v->dyn_boxes);
+    cudaFree(v->stage);
+    if (v->copy_in) cudaStreamDestroy(v->copy_in);
+    if (v->copy_out) cudaStreamDestroy(v->copy_out);
+    for (cudaEvent_t e : {v->ev_entry, v->ev_in, v->ev_out, v->ev_chunk[0], v->ev_chunk[1], v->ev_chunk[2],
+                          v->ev_chunk[3]})
+        if (e) cudaEventDestroy(e);
     for (auto& st : v->stages)
         for (auto& pr : st.pending) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     delete v;
@@ -653,7 +666,16 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
                                         params->blend_precision == DDGI_BLEND_BF16, v->pack_irr, v->pack_dist,
                                         v->inv_irr_r, v->inv_dist_r, st));
     }
-    DDGI_CK(cudaMemsetAsync(v->counts, 0, sizeof(int32_t) * kCounterInts, st));   // lists and trace counters
+    // the active list can be kept from the previous frame when no state can
+    // have changed in between: no uninitialised probe, no dynamic object
+    // waking or putting probes to sleep, same probe range
+    const bool keep_list = d.state_machine && !v->uninit_possible && v->n_dyn == 0 && !v->awake_possible &&
+                           v->list_begin == begin && v->list_end == end;
+    if (keep_list) {   // clear the trace counters only, keep the list counts
+        DDGI_CK(cudaMemsetAsync(v->counts + 4, 0, sizeof(int32_t) * (kCounterInts - 4), st));
+    } else {
+        DDGI_CK(cudaMemsetAsync(v->counts, 0, sizeof(int32_t) * kCounterInts, st));   // lists and trace counters
+    }
     // uninitialised probes (none after a full-range update, until states are
     // set again): position optimizer iterations, then classification
     if (d.state_machine && v->uninit_possible) {
@@ -678,9 +700,12 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
         DDGI_CK(launch_wake(view, v->dyn_boxes, v->n_dyn, (int)begin, (int)end, st));
         v->awake_possible = v->n_dyn > 0;
     }
-    {
+    if (!keep_list) {
         StageTimer tm(v, 1, st);
         DDGI_CK(launch_build_list_range(v->states, (int)begin, (int)end, 1, v->lists + v->P, v->counts + 1, st));
+        // reusable next frame only if nothing below changes which probes are active
+        v->list_begin = begin;
+        v->list_end = end;
     }
     {
         StageTimer tm(v, 2, st);
@@ -775,6 +800,66 @@ ddgi_status ddgi_query(ddgi_volume v, const float* pos_dev, const float* nrm_dev
     return DDGI_OK;
 }
 
+ddgi_status ddgi_frame_host(ddgi_volume v, ddgi_scene s, const ddgi_lights* lights,
+                            const ddgi_update_params* params, const float* pos_host, const float* nrm_host,
+                            int64_t n, const float camera_pos[3], float* out_host, ddgi_stream stream) {
+    if (!v || !camera_pos) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (n < 0) return fail(DDGI_ERR_INVALID_ARG, "n < 0");
+    if (n > 0 && (!pos_host || !nrm_host || !out_host)) return fail(DDGI_ERR_INVALID_ARG, "NULL host array");
+    cudaStream_t st = (cudaStream_t)stream;
+    constexpr int kChunks = 4;
+    if (!v->copy_in) {
+        DDGI_CK(cudaStreamCreateWithFlags(&v->copy_in, cudaStreamNonBlocking));
+        DDGI_CK(cudaStreamCreateWithFlags(&v->copy_out, cudaStreamNonBlocking));
+        for (cudaEvent_t* e : {&v->ev_entry, &v->ev_in, &v->ev_out, &v->ev_chunk[0], &v->ev_chunk[1],
+                               &v->ev_chunk[2], &v->ev_chunk[3]})
+            DDGI_CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+    if (n > v->stage_cap) {   // earlier frames may still read the old staging
+        DDGI_CK(cudaStreamSynchronize(st));
+        cudaFree(v->stage);
+        v->stage = nullptr;
+        v->stage_cap = 0;
+        DDGI_CK(cudaMalloc(&v->stage, sizeof(float) * 9 * (size_t)n));
+        v->stage_cap = n;
+    }
+    const size_t row = sizeof(float) * 3;
+    float* pos_d = v->stage;
+    float* nrm_d = v->stage + 3 * v->stage_cap;
+    float* out_d = v->stage + 6 * v->stage_cap;
+    // inputs: after everything enqueued on the stream so far (the previous
+    // frame's query read the staging), alongside the probe update
+    if (n > 0) {
+        DDGI_CK(cudaEventRecord(v->ev_entry, st));
+        DDGI_CK(cudaStreamWaitEvent(v->copy_in, v->ev_entry, 0));
+        DDGI_CK(cudaMemcpyAsync(pos_d, pos_host, row * (size_t)n, cudaMemcpyHostToDevice, v->copy_in));
+        DDGI_CK(cudaMemcpyAsync(nrm_d, nrm_host, row * (size_t)n, cudaMemcpyHostToDevice, v->copy_in));
+        DDGI_CK(cudaEventRecord(v->ev_in, v->copy_in));
+    }
+    ddgi_status r = update_impl(v, s, lights, params, 0, v->P, stream);
+    if (r != DDGI_OK || n == 0) {   // the stream still orders after the input copies
+        if (n > 0) DDGI_CK(cudaStreamWaitEvent(st, v->ev_in, 0));
+        return r;
+    }
+    DDGI_CK(cudaStreamWaitEvent(st, v->ev_in, 0));
+    // query in chunks; each chunk's result copy overlaps the next chunk's query
+    const float3 cam = make_float3(camera_pos[0], camera_pos[1], camera_pos[2]);
+    const VolView view = make_view(v);
+    const int64_t chunk = (n + kChunks - 1) / kChunks;
+    for (int c = 0; c < kChunks; ++c) {
+        const int64_t a = c * chunk, b = std::min(n, a + chunk);
+        if (a >= b) break;
+        DDGI_CK(launch_query(view, pos_d + 3 * a, nrm_d + 3 * a, b - a, cam, out_d + 3 * a, st));
+        DDGI_CK(cudaEventRecord(v->ev_chunk[c], st));
+        DDGI_CK(cudaStreamWaitEvent(v->copy_out, v->ev_chunk[c], 0));
+        DDGI_CK(cudaMemcpyAsync(out_host + 3 * a, out_d + 3 * a, row * (size_t)(b - a), cudaMemcpyDeviceToHost,
+                                v->copy_out));
+    }
+    DDGI_CK(cudaEventRecord(v->ev_out, v->copy_out));
+    DDGI_CK(cudaStreamWaitEvent(st, v->ev_out, 0));
+    return DDGI_OK;
+}
+
 static ddgi_status buffer_of(ddgi_volume v, int32_t which, void** p, size_t* bytes) {
     if (which == 0) { *p = v->irr; *bytes = v->irr_bytes; }
     else if (which == 1) { *p = v->dist; *bytes = v->dist_bytes; }
@@ -803,7 +888,10 @@ ddgi_status ddgi_set_buffer(ddgi_volume v, int32_t which, const void* src_dev, s
     if (s != DDGI_OK) return s;
     if (bytes != nb) return fail(DDGI_ERR_INVALID_ARG, "size mismatch: expected " + std::to_string(nb));
     DDGI_CK(cudaMemcpyAsync(p, src_dev, nb, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
-    if (which == 2) v->uninit_possible = true;   // restored states may hold UNINIT probes
+    if (which == 2) {   // restored states may hold UNINIT probes and change the active set
+        v->uninit_possible = true;
+        v->list_begin = v->list_end = -1;
+    }
     return DDGI_OK;
 }
 
@@ -1446,6 +1534,7 @@ ddgi_status ddgi_diff_forward(ddgi_volume v, ddgi_scene s, const ddgi_lights* li
     DDGI_CK(cudaMemsetAsync(v->irr, 0, v->irr_bytes, st));
     DDGI_CK(cudaMemsetAsync(v->dist, 0, v->dist_bytes, st));
     DDGI_CK(cudaMemsetAsync(v->states, DDGI_STATE_VIGILANT, (size_t)v->P, st));
+    v->list_begin = v->list_end = -1;   // every probe active now: rebuild the list
     DDGI_CK(cudaMemsetAsync(v->snap_irr[0], 0, v->irr_bytes, st));
     DDGI_CK(cudaMemsetAsync(v->snap_dist[0], 0, v->dist_bytes, st));
     for (int f = 0; f < n_frames; ++f) {
