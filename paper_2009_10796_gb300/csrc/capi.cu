@@ -179,6 +179,7 @@ static VolView make_view(const ddgi_volume_s* v) {
     w.spacing = make_float3(d.spacing[0], d.spacing[1], d.spacing[2]);
     w.inv_spacing = make_float3(1.0f / d.spacing[0], 1.0f / d.spacing[1], 1.0f / d.spacing[2]);
     w.counts = make_int3(d.counts[0], d.counts[1], d.counts[2]);
+    set_view_divisors(w);
     w.shift = v->shift;
     w.min_spacing = std::fmin(d.spacing[0], std::fmin(d.spacing[1], d.spacing[2]));
     w.bias = d.self_shadow_bias;
@@ -1072,6 +1073,7 @@ VolView cascade_view(const ddgi_cascade_s* c, int k, const float cam[3]) {
     w.spacing = make_float3(d.spacing[0], d.spacing[1], d.spacing[2]);
     w.inv_spacing = make_float3(1.0f / d.spacing[0], 1.0f / d.spacing[1], 1.0f / d.spacing[2]);
     w.counts = make_int3(d.counts[0], d.counts[1], d.counts[2]);
+    set_view_divisors(w);
     // reduced to [0, count): the device indexes with one conditional add / subtract
     w.shift = make_int3(((c->shift[k][0] % d.counts[0]) + d.counts[0]) % d.counts[0],
                         ((c->shift[k][1] % d.counts[1]) + d.counts[1]) % d.counts[1],

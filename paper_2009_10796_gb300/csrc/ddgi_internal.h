@@ -40,6 +40,28 @@ struct Lights {
 };
 
 // Volume view passed by value to kernels.
+// Division by an invariant divisor d >= 1 of dividends below 2^31
+// (Granlund and Montgomery, PLDI 1994, Sec. 4): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(m, n) + n) >> l; the
+// sum stays below 2^32 for such n.
+struct FastDiv {
+    uint32_t m;
+    int32_t l;
+};
+
+inline FastDiv make_fast_div(uint32_t d) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    FastDiv f;
+    f.m = (uint32_t)((((1ull << l) - d) << 32) / d + 1);
+    f.l = l;
+    return f;
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t fast_div(uint32_t n, FastDiv f) { return (__umulhi(f.m, n) + n) >> f.l; }
+#endif
+
 struct VolView {
     float3 origin;
     float3 spacing;
@@ -63,7 +85,13 @@ struct VolView {
     float3   blend_hi;      // camera-centred for a tracking window
     float4*  offsets;       // [P] probe offsets from the grid (Sec. 5), or nullptr
     float    offset_limit;  // largest offset per axis, fraction of the spacing
+    FastDiv  div_x, div_xy; // by counts.x and counts.x * counts.y (set_view_divisors)
 };
+
+inline void set_view_divisors(VolView& w) {
+    w.div_x = make_fast_div((uint32_t)w.counts.x);
+    w.div_xy = make_fast_div((uint32_t)w.counts.x * (uint32_t)w.counts.y);
+}
 
 // Largest BVH leaf (triangles); the traversal packs a leaf's first triangle
 // and count - 1 into one int (kLeafBits bits of count), so scenes stay below

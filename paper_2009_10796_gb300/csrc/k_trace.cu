@@ -149,6 +149,11 @@ __device__ __forceinline__ void hit_frame(const DevScene& s, int k, float3& ng) 
 constexpr int kRefillLanes = 32;
 
 // Hands idle lanes the next work items; returns the lane's item or -1.
+// Probe slot of work item (or record) idx = slot * R + ray.
+__device__ __forceinline__ int ray_slot(int64_t idx, int R, FastDiv dR) {
+    return idx <= INT32_MAX ? (int)fast_div((uint32_t)idx, dR) : (int)(idx / R);
+}
+
 __device__ __forceinline__ int64_t refill(unsigned long long* next, int64_t total, bool idle_lane,
                                           bool& exhausted) {
     const unsigned idle = __ballot_sync(0xffffffffu, idle_lane);
@@ -168,7 +173,7 @@ __device__ __forceinline__ int64_t refill(unsigned long long* next, int64_t tota
 // tests to stats[1], stats[2] (otherwise identical).
 template <bool MULTI, bool COUNT = false>
 __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Lights L,
-                                                       const float4* __restrict__ dirs, int R,
+                                                       const float4* __restrict__ dirs, int R, FastDiv dR,
                                                        const int32_t* __restrict__ perm,
                                                        const int32_t* __restrict__ active,
                                                        const int32_t* __restrict__ count,
@@ -196,7 +201,7 @@ __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Li
         if (item >= 0) {
             // work item -> (probe slot, ray): consecutive items take a compact
             // cone of directions; the record keeps its canonical ray index
-            int slot = (int)(item / R);
+            int slot = ray_slot(item, R, dR);
             int j = (int)(item - (int64_t)slot * R);
             int i = perm ? __ldg(perm + j) : j;
             rec = (int64_t)slot * R + i;
@@ -265,7 +270,7 @@ __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Li
 // COUNT: adds 4-wide node visits and triangle tests to stats[4], stats[5].
 template <bool MULTI, bool COUNT = false>
 __global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolSet vs, Lights L,
-                                                      const float4* __restrict__ dirs, int R,
+                                                      const float4* __restrict__ dirs, int R, FastDiv dR,
                                                       const int32_t* __restrict__ active,
                                                       float4* __restrict__ hits,
                                                       const int32_t* __restrict__ shadow_list,
@@ -286,7 +291,7 @@ __global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolSet vs, Lig
         int64_t item = refill(next, total, rec < 0, exhausted);
         if (item >= 0) {
             rec = __ldg(shadow_list + item);
-            int slot = (int)(rec / R);
+            int slot = ray_slot(rec, R, dR);
             int i = (int)(rec - (int64_t)slot * R);
             int e = __ldg(active + slot);
             float3 o = probe_pos_phys(vol_of<MULTI>(vs, e >> kEntryShift), e & kEntryMask);
@@ -318,13 +323,13 @@ __global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolSet vs, Lig
 // previous frame's probes), one thread per entry of the compacted hit list.
 template <bool MULTI>
 __global__ void __launch_bounds__(256, 4) k_shade(DevScene s, VolSet vs, Lights L, const float4* __restrict__ dirs,
-                                               int R, const int32_t* __restrict__ active,
+                                               int R, FastDiv dR, const int32_t* __restrict__ active,
                                                const int32_t* __restrict__ hit_list,
                                                const int32_t* __restrict__ hit_count, float4* records) {
     const int n_hits = *hit_count;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_hits; q += gridDim.x * blockDim.x) {
         const int64_t idx = __ldg(hit_list + q);
-        const int slot = (int)(idx / R);
+        const int slot = ray_slot(idx, R, dR);
         const int i = (int)(idx - (int64_t)slot * R);
         float4 d4 = __ldg(dirs + i);
         float3 d = f3(d4.x, d4.y, d4.z);
@@ -524,15 +529,16 @@ static cudaError_t trace_wavefront(const DevScene& s, const VolSet& vs, const Li
     unsigned long long* next_shadow = reinterpret_cast<unsigned long long*>(shadow_count + 4);
     cudaError_t e = cudaSuccess;
     if (marks && (e = cudaEventRecord(marks[0], st)) != cudaSuccess) return e;
-    k_trace_primary<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, perm, active, count, records, shadow_list,
+    const FastDiv dR = make_fast_div((uint32_t)R);
+    k_trace_primary<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, dR, perm, active, count, records, shadow_list,
                                                   hit_list, shadow_count, next);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (marks && (e = cudaEventRecord(marks[1], st)) != cudaSuccess) return e;
-    k_trace_shadow<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, active, records, shadow_list, shadow_count,
+    k_trace_shadow<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, dR, active, records, shadow_list, shadow_count,
                                                  next_shadow);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (marks && (e = cudaEventRecord(marks[2], st)) != cudaSuccess) return e;
-    k_shade<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, active, hit_list, shadow_count + 1, records);
+    k_shade<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, dR, active, hit_list, shadow_count + 1, records);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (marks && (e = cudaEventRecord(marks[3], st)) != cudaSuccess) return e;
     return cudaSuccess;
@@ -547,10 +553,11 @@ cudaError_t launch_trace_count(const DevScene& s, const VolView& v, const Lights
     unsigned long long* next_shadow = reinterpret_cast<unsigned long long*>(shadow_count + 4);
     cudaError_t e = cudaMemsetAsync(shadow_count, 0, 6 * sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
-    k_trace_primary<false, true><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, perm, active, count, records,
+    const FastDiv dR = make_fast_div((uint32_t)R);
+    k_trace_primary<false, true><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, dR, perm, active, count, records,
                                                         shadow_list, hit_list, shadow_count, next, stats);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_trace_shadow<false, true><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, active, records, shadow_list,
+    k_trace_shadow<false, true><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, dR, active, records, shadow_list,
                                                        shadow_count, next_shadow, stats);
     return cudaGetLastError();
 }

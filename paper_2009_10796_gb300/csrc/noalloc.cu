@@ -137,6 +137,7 @@ extern "C" ddgi_status ddgi_update_noalloc(ddgi_scene scene, const ddgi_volume_d
     v.spacing = make_float3(d->spacing[0], d->spacing[1], d->spacing[2]);
     v.inv_spacing = make_float3(1.0f / d->spacing[0], 1.0f / d->spacing[1], 1.0f / d->spacing[2]);
     v.counts = make_int3(d->counts[0], d->counts[1], d->counts[2]);
+    set_view_divisors(v);
     v.shift = make_int3(0, 0, 0);
     v.min_spacing = std::fmin(d->spacing[0], std::fmin(d->spacing[1], d->spacing[2]));
     v.bias = d->self_shadow_bias;

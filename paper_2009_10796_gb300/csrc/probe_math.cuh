@@ -71,9 +71,10 @@ __device__ __forceinline__ float3 probe_pos_logical(const VolView& v, int i, int
 
 // World position of physical probe p: its grid point plus its offset (Sec. 5).
 __device__ __forceinline__ float3 probe_pos_phys(const VolView& v, int p) {
-    int a = p % v.counts.x;
-    int b = (p / v.counts.x) % v.counts.y;
-    int c = p / (v.counts.x * v.counts.y);
+    const int q = (int)fast_div((uint32_t)p, v.div_x);   // p / counts.x
+    const int c = (int)fast_div((uint32_t)p, v.div_xy);  // p / (counts.x counts.y)
+    const int a = p - q * v.counts.x;
+    const int b = q - c * v.counts.y;
     float3 x = probe_pos_logical(v, wrap_sub(a, v.shift.x, v.counts.x), wrap_sub(b, v.shift.y, v.counts.y),
                                  wrap_sub(c, v.shift.z, v.counts.z));
     if (v.offsets) {
@@ -341,11 +342,19 @@ __device__ __forceinline__ float3 query_M_look(const VolView& v, float3 x, float
     const int px0 = wrap_add(base[0], v.shift.x, cnt[0]), px1 = wrap_add(base[0] + 1, v.shift.x, cnt[0]);
     const int py0 = wrap_add(base[1], v.shift.y, cnt[1]), py1 = wrap_add(base[1] + 1, v.shift.y, cnt[1]);
     const int pz0 = wrap_add(base[2], v.shift.z, cnt[2]), pz1 = wrap_add(base[2] + 1, v.shift.z, cnt[2]);
-#pragma unroll 1
+    // the eight states first, as independent loads, so the probe loop below
+    // does not wait on one state load per probe
+    unsigned act = 0;
+#pragma unroll
     for (int c = 0; c < 8; ++c) {
+        const int p = (c & 1 ? px1 : px0) + cnt[0] * ((c & 2 ? py1 : py0) + cnt[1] * (c & 4 ? pz1 : pz0));
+        act |= state_active(v.states[p]) ? 1u << c : 0u;
+    }
+#pragma unroll 1
+    for (; act != 0; act &= act - 1) {   // active probes in ascending c
+        const int c = __ffs(act) - 1;
         int o0 = c & 1, o1 = (c >> 1) & 1, o2 = (c >> 2) & 1;
         int p = (o0 ? px1 : px0) + cnt[0] * ((o1 ? py1 : py0) + cnt[1] * (o2 ? pz1 : pz0));
-        if (!state_active(v.states[p])) continue;
         float3 xp = probe_pos_logical(v, base[0] + o0, base[1] + o1, base[2] + o2);
         if (v.offsets) {   // the probe's own (moved) position; the cage stays on the grid
             const float4 po = __ldg(v.offsets + p);
