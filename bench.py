@@ -258,15 +258,19 @@ def run_gpu(args):
     R = desc.rays_per_probe
     stats = vol.trace_stats(scene, L)
 
-    def timed_steps(precision):
-        # device-timed steps; L2 flushed between steps outside the events
+    def timed_steps(precision, stages):
+        # device-timed steps; L2 flushed between steps outside the events.
+        # stages=False: events at the step boundaries only (the headline
+        # pass); stages=True: per-stage events inside the update and around
+        # the query as well (they cost about 20 us per step, so the headline
+        # pass runs without them)
         nonlocal frame
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
         qev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
         vol.read_timings()
-        vol.enable_timing(True)
+        vol.enable_timing(stages)
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -275,9 +279,11 @@ def run_gpu(args):
             flush.fill_(float(k))
             evs[k][0].record(stream)
             vol.update(scene, L, frame, precision=precision, stream=stream)
-            qev[k][0].record(stream)
+            if stages:
+                qev[k][0].record(stream)
             vol.query(pos, nrm, camera, out, stream=stream)
-            qev[k][1].record(stream)
+            if stages:
+                qev[k][1].record(stream)
             evs[k][1].record(stream)
             frame += 1
         torch.cuda.synchronize()
@@ -286,16 +292,21 @@ def run_gpu(args):
             dist.barrier()
         tm = vol.read_timings()
         vol.enable_timing(False)
-        return ([a.elapsed_time(b) for a, b in evs], [a.elapsed_time(b) for a, b in qev], tm, wall_s)
+        q = [a.elapsed_time(b) for a, b in qev] if stages else None
+        return [a.elapsed_time(b) for a, b in evs], q, tm, wall_s
 
     with ClockSampler(local) as clk:
         m0 = clk.mark()
-        step_ms, query_ms, timings, wall = timed_steps(g.BLEND_FP32)
+        step_ms, _, _, wall = timed_steps(g.BLEND_FP32, False)
         time.sleep(0.15)    # one sampling period, so a row taken during the region has landed
         clk.window = (m0, clk.mark())
+        # the same steps again with per-stage events: stage times, the query's
+        # time and the primary pass's launch duration for the roofline
+        _, query_ms, timings, _ = timed_steps(g.BLEND_FP32, True)
         mixed = None
         if not args.no_mixed:
-            m_step, m_query, m_tm, _ = timed_steps(g.BLEND_TF32)
+            m_step, _, _, _ = timed_steps(g.BLEND_TF32, False)
+            _, m_query, m_tm, _ = timed_steps(g.BLEND_TF32, True)
             mixed = (m_step, m_query, m_tm)
     ms = float(np.mean(step_ms))
     t = torch.tensor([ms], device=dev)
@@ -398,6 +409,9 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "probes": desc.n_probes, "active_probes": n_active,
                    "rays_per_probe": R, "query_pixels": n_pix,
                    "l2": "flushed between timed steps (256 MiB write outside the events)",
+                   "timing": "value: CUDA events at the step boundaries only; stage_ms, query and the "
+                             "roofline launch times: a second pass of the same steps with per-stage "
+                             "events on the update stream",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "update_ms_per_frame": ms - q_ms, "query_ms_1080p": q_ms, "glossy_query_ms_1080p": glossy_ms,
         "trace_grays_per_s": rays_per_step / (trace_ms_avg * 1e-3) / 1e9,

@@ -520,11 +520,11 @@ ddgi_status ddgi_volume_create(const ddgi_volume_desc* desc, ddgi_volume* out) {
     A((void**)&v->counts, sizeof(int32_t) * kCounterInts);
     A((void**)&v->status, sizeof(uint32_t));
     A((void**)&v->records, sizeof(float4) * (size_t)v->P * v->R);
-    A((void**)&v->dirs, sizeof(float4) * v->R);
+    A((void**)&v->dirs, sizeof(float4) * 3 * v->R);
     A((void**)&v->dirs64, sizeof(double) * 3 * v->R);
     A((void**)&v->offsets, sizeof(float4) * (size_t)v->P);
     if (desc->optimizer_iters > 0) {
-        A((void**)&v->opt_dirs, sizeof(float4) * v->R);
+        A((void**)&v->opt_dirs, sizeof(float4) * 3 * v->R);
         A((void**)&v->opt_dirs64, sizeof(double) * 3 * v->R);
     }
     A((void**)&v->w_irr, sizeof(float) * desc->irr_n * desc->irr_n * (size_t)v->R);
@@ -1204,7 +1204,7 @@ ddgi_status ddgi_cascade_create(const ddgi_volume_desc* descs, int32_t n, ddgi_c
     A((void**)&c->records, sizeof(float4) * (size_t)c->total * c->R);
     A((void**)&c->shadow_list, sizeof(int32_t) * (size_t)c->total * c->R);
     A((void**)&c->hit_list, sizeof(int32_t) * (size_t)c->total * c->R);
-    A((void**)&c->dirs, sizeof(float4) * c->R);
+    A((void**)&c->dirs, sizeof(float4) * 3 * c->R);
     A((void**)&c->dirs64, sizeof(double) * 3 * c->R);
     A((void**)&c->perm, sizeof(int32_t) * c->R);
     if (e == cudaSuccess) {

@@ -165,6 +165,8 @@ FrameRot frame_rotation(uint64_t seed, int64_t frame);
 // Kernel launchers (k_*.cu)
 // ---------------------------------------------------------------------------
 // Frame ray pattern and texel weights; dirs64 is [R][3] double scratch.
+// Per-frame direction buffers hold 3R float4: the R ray directions (w = 0),
+// then for ray i the two packed ray constants of dir_pre_pack at R + 2i.
 cudaError_t launch_frame_setup(const FrameRot& rot, int R, int irr_n, int dist_n, float cos_power,
                                float4* dirs, double* dirs64, float* w_irr, float* inv_s_irr, float* w_dist,
                                float* inv_s_dist, cudaStream_t st);

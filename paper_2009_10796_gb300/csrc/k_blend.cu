@@ -23,6 +23,7 @@
 // border copy of Sec. 7.1 fused into the blend).  The probe's state advances
 // Newly Vigilant -> Vigilant after its texels are written.
 #include "blend_epilogue.cuh"
+#include "traverse.cuh"
 
 namespace ddgi {
 
@@ -76,7 +77,12 @@ __global__ void __launch_bounds__(32) k_frame_dirs(FrameRot rot_arg, const Frame
     const FrameRot rot = ROT_DEV ? *rot_dev : rot_arg;
     double w[3];
     frame_dir(rot, i, R, w);
-    dirs[i] = make_float4((float)w[0], (float)w[1], (float)w[2], 0.0f);
+    const float3 d = f3((float)w[0], (float)w[1], (float)w[2]);
+    dirs[i] = make_float4(d.x, d.y, d.z, 0.0f);
+    float4 a, b;   // the ray constants of this direction, after the R directions
+    dir_pre_pack(d, a, b);
+    dirs[R + 2 * i] = a;
+    dirs[R + 2 * i + 1] = b;
     dirs64[3 * i] = w[0];
     dirs64[3 * i + 1] = w[1];
     dirs64[3 * i + 2] = w[2];

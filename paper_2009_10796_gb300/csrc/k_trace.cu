@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Li
             float3 o = probe_pos_phys(vol_of<MULTI>(vs, entry >> kEntryShift), entry & kEntryMask);
             float4 d4 = __ldg(dirs + i);
             d = f3(d4.x, d4.y, d4.z);
-            r = ray_pre(o, d);
+            r = ray_pre_packed(o, d, __ldg(dirs + R + 2 * i), __ldg(dirs + R + 2 * i + 1));
             ww_start(s, w, true);
         }
         if (__ballot_sync(0xffffffffu, rec >= 0) == 0) break;
@@ -282,7 +282,8 @@ __global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolSet vs, Lig
     const float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
     int64_t rec = -1;
     bool exhausted = false;
-    RayPre r = ray_pre(f3(0.0f, 0.0f, 0.0f), tol);
+    const RayPre r_sun = ray_pre(f3(0.0f, 0.0f, 0.0f), tol);   // every shadow ray runs towards the sun
+    RayPre r = r_sun;
     int stack[kStackSize4];
     WwLane<kStackSize4> w;
     w.stack = stack;
@@ -303,7 +304,8 @@ __global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolSet vs, Lig
             float3 nn = (1.0f / length(ng)) * ng;
             float3 x = o + hr.x * d;
             float off = 1e-4f * (1.0f + length(x));
-            r = ray_pre(x + off * nn, tol);
+            r = r_sun;
+            r.o = x + off * nn;
             ww_start(s, w, true);
         }
         if (__ballot_sync(0xffffffffu, rec >= 0) == 0) break;

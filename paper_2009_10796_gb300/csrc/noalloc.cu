@@ -25,7 +25,7 @@ constexpr int kNaMaxProbes = 32768;           // probes in the volume
 constexpr int64_t kNaMaxRecords = 1 << 20;    // probes x rays (16 MiB of ray records)
 
 static __device__ __align__(256) float4 g_na_records[kNaMaxRecords];
-static __device__ __align__(256) float4 g_na_dirs[kNaMaxRays];
+static __device__ __align__(256) float4 g_na_dirs[3 * kNaMaxRays];   // directions, then ray constants
 static __device__ __align__(256) double g_na_dirs64[3 * kNaMaxRays];
 static __device__ __align__(256) float g_na_w_irr[kNaMaxIrrTexels * kNaMaxRays];
 static __device__ __align__(256) float g_na_inv_s_irr[kNaMaxIrrTexels];

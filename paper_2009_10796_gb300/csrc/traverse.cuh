@@ -48,6 +48,33 @@ __device__ __forceinline__ RayPre ray_pre(float3 o, float3 d) {
     return r;
 }
 
+// The direction-only fields of RayPre packed into two float4 (idir, Sx;
+// Sy, Sz, kx | ky << 2 | kz << 4, oct), so rays sharing a direction (the
+// per-frame probe ray directions) take them from a table instead of six
+// divisions per ray.  ray_pre_packed(o, d, a, b) equals ray_pre(o, d)
+// field by field when (a, b) = dir_pre_pack(d).
+__device__ __forceinline__ void dir_pre_pack(float3 d, float4& a, float4& b) {
+    const RayPre r = ray_pre(f3(0.0f, 0.0f, 0.0f), d);
+    a = make_float4(r.idir.x, r.idir.y, r.idir.z, r.Sx);
+    b = make_float4(r.Sy, r.Sz, __int_as_float(r.kx | (r.ky << 2) | (r.kz << 4)), __int_as_float(r.oct));
+}
+
+__device__ __forceinline__ RayPre ray_pre_packed(float3 o, float3 d, float4 a, float4 b) {
+    RayPre r;
+    r.o = o;
+    r.d = d;
+    r.idir = f3(a.x, a.y, a.z);
+    r.Sx = a.w;
+    r.Sy = b.x;
+    r.Sz = b.y;
+    const int k = __float_as_int(b.z);
+    r.kx = k & 3;
+    r.ky = (k >> 2) & 3;
+    r.kz = (k >> 4) & 3;
+    r.oct = __float_as_int(b.w);
+    return r;
+}
+
 // Three-input minimum / maximum (one PTX instruction on sm_100 and later).
 __device__ __forceinline__ float fmin3f(float a, float b, float c) {
     float d;
