@@ -172,7 +172,7 @@ __device__ __forceinline__ int64_t refill(unsigned long long* next, int64_t tota
 // COUNT: measurement build that adds its 4-wide node visits and triangle
 // tests to stats[1], stats[2] (otherwise identical).
 template <bool MULTI, bool COUNT = false>
-__global__ void __launch_bounds__(256) k_trace_primary(DevScene s, VolSet vs, Lights L,
+__global__ void __launch_bounds__(256, 4) k_trace_primary(DevScene s, VolSet vs, Lights L,
                                                        const float4* __restrict__ dirs, int R, FastDiv dR,
                                                        const int32_t* __restrict__ perm,
                                                        const int32_t* __restrict__ active,
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolSet vs, Lig
             float3 x = o + hr.x * d;
             float off = 1e-4f * (1.0f + length(x));
             r = r_sun;
-            r.o = x + off * nn;
+            ray_set_origin(r, x + off * nn);
             ww_start(s, w, true);
         }
         if (__ballot_sync(0xffffffffu, rec >= 0) == 0) break;

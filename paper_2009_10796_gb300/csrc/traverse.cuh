@@ -15,12 +15,48 @@ namespace ddgi {
 
 constexpr int kStackSize = 64;
 
+// Two floats in one 64-bit register pair, for the packed FP32 pair
+// arithmetic of sm_100 and later (add / sub / mul .rn.f32x2: each half
+// rounded exactly as the scalar instruction would).
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
 struct RayPre {
     float3 o, d, idir;
     int kx, ky, kz;
     float Sx, Sy, Sz;
     int oct;    // bit a set: axis a runs toward -inf (its near slab plane is the box's hi)
+    uint64_t o2[3], i2[3];   // o and idir per axis, doubled for the packed box tests
 };
+
+__device__ __forceinline__ void ray_set_origin(RayPre& r, float3 o) {
+    r.o = o;
+    r.o2[0] = f2_pack(o.x, o.x);
+    r.o2[1] = f2_pack(o.y, o.y);
+    r.o2[2] = f2_pack(o.z, o.z);
+}
+
+__device__ __forceinline__ void ray_set_packed_idir(RayPre& r) {
+    r.i2[0] = f2_pack(r.idir.x, r.idir.x);
+    r.i2[1] = f2_pack(r.idir.y, r.idir.y);
+    r.i2[2] = f2_pack(r.idir.z, r.idir.z);
+}
 
 __device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
 
@@ -45,6 +81,8 @@ __device__ __forceinline__ RayPre ray_pre(float3 o, float3 d) {
                 1.0f / (fabsf(d.y) > eps ? d.y : copysignf(eps, d.y)),
                 1.0f / (fabsf(d.z) > eps ? d.z : copysignf(eps, d.z)));
     r.oct = (signbit(r.idir.x) ? 1 : 0) | (signbit(r.idir.y) ? 2 : 0) | (signbit(r.idir.z) ? 4 : 0);
+    ray_set_origin(r, o);
+    ray_set_packed_idir(r);
     return r;
 }
 
@@ -61,7 +99,6 @@ __device__ __forceinline__ void dir_pre_pack(float3 d, float4& a, float4& b) {
 
 __device__ __forceinline__ RayPre ray_pre_packed(float3 o, float3 d, float4 a, float4 b) {
     RayPre r;
-    r.o = o;
     r.d = d;
     r.idir = f3(a.x, a.y, a.z);
     r.Sx = a.w;
@@ -72,6 +109,8 @@ __device__ __forceinline__ RayPre ray_pre_packed(float3 o, float3 d, float4 a, f
     r.ky = (k >> 2) & 3;
     r.kz = (k >> 4) & 3;
     r.oct = __float_as_int(b.w);
+    ray_set_origin(r, o);
+    ray_set_packed_idir(r);
     return r;
 }
 
@@ -142,6 +181,40 @@ __device__ __forceinline__ float box_enter_oct(const RayPre& r, float nx, float 
     float tn = fmax3f((nx - r.o.x) * r.idir.x, (ny - r.o.y) * r.idir.y, fmaxf((nz - r.o.z) * r.idir.z, 0.0f));
     float tf = fmin3f((fx - r.o.x) * r.idir.x, (fy - r.o.y) * r.idir.y, fminf((fz - r.o.z) * r.idir.z, tmax));
     return tn <= tf * 1.0000005f ? tn : INFINITY;
+}
+
+// box_enter_oct for the four children of a 4-wide node at once: the slab
+// distances of children (0, 1) and (2, 3) in packed pairs, the same IEEE
+// operations lane by lane, so each k_c equals box_enter_oct's result.
+__device__ __forceinline__ void box4_enter_oct(const RayPre& r, float4 nx, float4 fx, float4 ny, float4 fy, float4 nz,
+                                               float4 fz, float tmax, float& k0, float& k1, float& k2, float& k3) {
+    float tnx[4], tfx[4], tny[4], tfy[4], tnz[4], tfz[4];
+    f2_unpack(f2_mul(f2_sub(f2_pack(nx.x, nx.y), r.o2[0]), r.i2[0]), tnx[0], tnx[1]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(nx.z, nx.w), r.o2[0]), r.i2[0]), tnx[2], tnx[3]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(fx.x, fx.y), r.o2[0]), r.i2[0]), tfx[0], tfx[1]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(fx.z, fx.w), r.o2[0]), r.i2[0]), tfx[2], tfx[3]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(ny.x, ny.y), r.o2[1]), r.i2[1]), tny[0], tny[1]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(ny.z, ny.w), r.o2[1]), r.i2[1]), tny[2], tny[3]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(fy.x, fy.y), r.o2[1]), r.i2[1]), tfy[0], tfy[1]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(fy.z, fy.w), r.o2[1]), r.i2[1]), tfy[2], tfy[3]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(nz.x, nz.y), r.o2[2]), r.i2[2]), tnz[0], tnz[1]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(nz.z, nz.w), r.o2[2]), r.i2[2]), tnz[2], tnz[3]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(fz.x, fz.y), r.o2[2]), r.i2[2]), tfz[0], tfz[1]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(fz.z, fz.w), r.o2[2]), r.i2[2]), tfz[2], tfz[3]);
+    float tn[4], tf[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        tn[c] = fmax3f(tnx[c], tny[c], fmaxf(tnz[c], 0.0f));
+        tf[c] = fmin3f(tfx[c], tfy[c], fminf(tfz[c], tmax));
+    }
+    const uint64_t widen = f2_pack(1.0000005f, 1.0000005f);
+    float w[4];
+    f2_unpack(f2_mul(f2_pack(tf[0], tf[1]), widen), w[0], w[1]);
+    f2_unpack(f2_mul(f2_pack(tf[2], tf[3]), widen), w[2], w[3]);
+    k0 = tn[0] <= w[0] ? tn[0] : INFINITY;
+    k1 = tn[1] <= w[1] ? tn[1] : INFINITY;
+    k2 = tn[2] <= w[2] ? tn[2] : INFINITY;
+    k3 = tn[3] <= w[3] ? tn[3] : INFINITY;
 }
 
 // Work counters of the measurement builds of the 4-wide walk.
@@ -367,10 +440,8 @@ __device__ __forceinline__ void ww4_round(const DevScene& s, const RayPre& r, Ww
             const float4 ny = __ldg(N + 2 + ay), fy = __ldg(N + 2 + (ay ^ 1));
             const float4 nz = __ldg(N + 4 + az), fz = __ldg(N + 4 + (az ^ 1));
             const int4 ref = __ldg(reinterpret_cast<const int4*>(N + 6));
-            float k0 = box_enter_oct(r, nx.x, fx.x, ny.x, fy.x, nz.x, fz.x, w.h.t);
-            float k1 = box_enter_oct(r, nx.y, fx.y, ny.y, fy.y, nz.y, fz.y, w.h.t);
-            float k2 = box_enter_oct(r, nx.z, fx.z, ny.z, fy.z, nz.z, fz.z, w.h.t);
-            float k3 = box_enter_oct(r, nx.w, fx.w, ny.w, fy.w, nz.w, fz.w, w.h.t);
+            float k0, k1, k2, k3;
+            box4_enter_oct(r, nx, fx, ny, fy, nz, fz, w.h.t, k0, k1, k2, k3);
             int v0 = ref.x, v1 = ref.y, v2 = ref.z, v3 = ref.w;
             if (!ANY) {
                 cx(k0, v0, k1, v1);
