@@ -22,21 +22,13 @@ __device__ __forceinline__ void for_border_copies(int x, int y, int n, F&& f) {
 }
 
 // Epilogues shared by the SIMT and tensor-core blends: one (texel, probe)
-// pair from its weighted sums and the texel's old value.  inv < 0 marks a
-// texel no ray reaches: it keeps its old value.
-__device__ __forceinline__ float3 irr_texel_old(const VolView& v, int p, int t) {
-    return load_irr<false>(v, p, 1 + t % v.irr_n, 1 + t / v.irr_n);
-}
-
-__device__ __forceinline__ float2 dist_texel_old(const VolView& v, int p, int t) {
-    return load_dist<false>(v, p, 1 + t % v.dist_n, 1 + t / v.dist_n);
-}
-
-__device__ __forceinline__ void blend_irr_texel_from(const VolView& v, const BlendParams& bp, int p, int t,
-                                                     float ar, float ag, float ab, float inv, bool newly,
-                                                     uint32_t* status, float3 old) {
-    const int ni = v.irr_n;
-    int x = 1 + t % ni, y = 1 + t / ni;
+// pair from its weighted sums and the texel's old value, the texel at tile
+// coordinates (x, y) (interior 1..n).  inv < 0 marks a texel no ray
+// reaches: it keeps its old value.
+__device__ __forceinline__ void blend_irr_texel_at(const VolView& v, const BlendParams& bp, int p, int x, int y,
+                                                   float ar, float ag, float ab, float inv, bool newly,
+                                                   uint32_t* status) {
+    const float3 old = load_irr<false>(v, p, x, y);
     float3 e = old;
     if (inv >= 0.0f) {
         float3 en = f3(powf(ar * inv, v.inv_gamma), powf(ag * inv, v.inv_gamma), powf(ab * inv, v.inv_gamma));
@@ -48,14 +40,12 @@ __device__ __forceinline__ void blend_irr_texel_from(const VolView& v, const Ble
         if (!(isfinite(e.x) && isfinite(e.y) && isfinite(e.z))) atomicOr(status, 1u);
     }
     store_irr(v, p, x, y, e);
-    for_border_copies(x, y, ni, [&](int bx, int by) { store_irr(v, p, bx, by, e); });
+    for_border_copies(x, y, v.irr_n, [&](int bx, int by) { store_irr(v, p, bx, by, e); });
 }
 
-__device__ __forceinline__ void blend_dist_texel_from(const VolView& v, const BlendParams& bp, int p, int t,
-                                                      float m1, float m2, float inv, bool newly,
-                                                      uint32_t* status, float2 old) {
-    const int nd = v.dist_n;
-    int x = 1 + t % nd, y = 1 + t / nd;
+__device__ __forceinline__ void blend_dist_texel_at(const VolView& v, const BlendParams& bp, int p, int x, int y,
+                                                    float m1, float m2, float inv, bool newly, uint32_t* status) {
+    const float2 old = load_dist<false>(v, p, x, y);
     float2 e = old;
     if (inv >= 0.0f) {
         float a = newly ? 0.0f : bp.hyst_vis;
@@ -63,19 +53,20 @@ __device__ __forceinline__ void blend_dist_texel_from(const VolView& v, const Bl
         if (!(isfinite(e.x) && isfinite(e.y))) atomicOr(status, 1u);
     }
     store_dist(v, p, x, y, e);
-    for_border_copies(x, y, nd, [&](int bx, int by) { store_dist(v, p, bx, by, e); });
+    for_border_copies(x, y, v.dist_n, [&](int bx, int by) { store_dist(v, p, bx, by, e); });
 }
 
+// The same by interior texel index t (row-major over the n x n interior).
 __device__ __forceinline__ void blend_irr_texel(const VolView& v, const BlendParams& bp, int p, int t,
                                                 float ar, float ag, float ab, float inv, bool newly,
                                                 uint32_t* status) {
-    blend_irr_texel_from(v, bp, p, t, ar, ag, ab, inv, newly, status, irr_texel_old(v, p, t));
+    blend_irr_texel_at(v, bp, p, 1 + t % v.irr_n, 1 + t / v.irr_n, ar, ag, ab, inv, newly, status);
 }
 
 __device__ __forceinline__ void blend_dist_texel(const VolView& v, const BlendParams& bp, int p, int t,
                                                  float m1, float m2, float inv, bool newly,
                                                  uint32_t* status) {
-    blend_dist_texel_from(v, bp, p, t, m1, m2, inv, newly, status, dist_texel_old(v, p, t));
+    blend_dist_texel_at(v, bp, p, 1 + t % v.dist_n, 1 + t / v.dist_n, m1, m2, inv, newly, status);
 }
 
 }  // namespace ddgi

@@ -140,6 +140,9 @@ struct BlendParams {
     float hyst_irr, hyst_vis;      // already scaled and clamped
     float thr_low, thr_high, thr_step;
     int32_t R;
+    // set by the tiled blend's launcher: by the texel counts n^2 and the
+    // tile widths n of irradiance and distance
+    FastDiv div_ti, div_td, div_ni, div_nd;
 };
 
 struct FrameRot { double m[9]; };

@@ -237,7 +237,7 @@ static TiledShape tiled_shape(int PG, int R, int irr_n, int dist_n) {
     t.dist_threads = (t.dist_units + 31) / 32 * 32;
     t.irr_units = t.nqi * (PG / 2);
     t.threads = t.dist_threads + (t.irr_units + 31) / 32 * 32;
-    t.smem = sizeof(float) * ((size_t)4 * PG * (R + 4) + (size_t)2 * 4 * (t.nqd + t.nqi) * kTileWS);
+    t.smem = sizeof(float) * ((size_t)4 * PG * R + (size_t)2 * 4 * (t.nqd + t.nqi) * kTileWS);
     // the epilogue reuses the same shared memory for the weighted sums
     const size_t sums = sizeof(float) * (size_t)PG * (2 * dist_n * dist_n + 3 * irr_n * irr_n);
     if (sums > t.smem) t.smem = sums;
@@ -254,14 +254,18 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// grid-stride over groups of PG active probes; blockDim = TiledShape::threads.
+// Each CTA takes an equal share of the active probes (at most PG per pass;
+// the grid is one wave of resident CTAs); blockDim = TiledShape::threads.
 // Requires R % 4 == 0.  Thread u < dist_units owns distance texels
 // tq + a * nqd (a < 4) of probes 4 pq .. 4 pq + 3; thread dist_threads + u'
 // (u' < irr_units) owns irradiance texels tq + a * nqi of probes 2 pq,
 // 2 pq + 1.  Striding the texels by nqd (not 4) puts a warp's weight rows on
-// distinct banks.  The next weight chunk is in flight (asynchronous copy)
-// while the current one is summed; the blend epilogue runs over the sums in
-// shared memory.
+// distinct banks.  The record planes are probe-interleaved ([ray][probe]),
+// so one shared load gives a ray's value for all of a thread's probes and
+// the probes pair up in packed FP32 FMAs (the same fused multiply-add per
+// texel, probe and ray, in ray order, as the scalar kernel).  The next
+// weight chunk is in flight (asynchronous copy) while the current one is
+// summed; the blend epilogue runs over the sums in shared memory.
 template <bool MULTI, int PG>
 __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, BlendParams bp,
                                                                     const float* __restrict__ w_irr,
@@ -277,17 +281,16 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, B
     __shared__ int s_probe[PG];
     __shared__ int s_newly[PG];
     const int R = bp.R;
-    const int RS = R + 4;
     const VolView& v0 = vol_of<MULTI>(vs, 0);   // cascades share R and tile sizes
     const int ni = v0.irr_n, nd = v0.dist_n;
     const int ti = ni * ni, td = nd * nd;
     const int nqi = (ti + 3) / 4, nqd = (td + 3) / 4;
     const int wrows = 4 * (nqd + nqi);          // distance rows, then irradiance rows
-    float* pr = sm;                              // [PG][RS] planes: radiance r, g, b and distance
-    float* pgc = pr + PG * RS;
-    float* pbc = pgc + PG * RS;
-    float* pdc = pbc + PG * RS;
-    float* wbuf = pdc + PG * RS;                 // 2 x [wrows][kTileWS] weight chunks
+    float* pr = sm;                              // [R][PG] planes: radiance r, g, b and distance
+    float* pgc = pr + PG * R;
+    float* pbc = pgc + PG * R;
+    float* pdc = pbc + PG * R;
+    float* wbuf = pdc + PG * R;                  // 2 x [wrows][kTileWS] weight chunks
     const int dist_units = nqd * (PG / 4), irr_units = nqi * (PG / 2);
     const int dist_threads = (dist_units + 31) / 32 * 32;
     const int u = threadIdx.x;
@@ -313,8 +316,10 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, B
         cp_async_commit();
     };
 
-    for (int g0 = blockIdx.x * PG; g0 < n_act; g0 += gridDim.x * PG) {
-        const int np = min(PG, n_act - g0);
+    const int per = min(PG, max(1, (n_act + (int)gridDim.x - 1) / (int)gridDim.x));
+    for (int g0 = blockIdx.x * per; g0 < n_act; g0 += gridDim.x * per) {
+        const int np = min(per, n_act - g0);
+        const bool live = is_dist ? 4 * pq < np : 2 * pq < np;   // some of the thread's probes hold records
         issue_chunk(0);   // overlaps the record staging below
         if (threadIdx.x < np) {
             int e = active[g0 + threadIdx.x];
@@ -322,19 +327,23 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, B
             s_newly[threadIdx.x] =
                 state_newly(vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask]);
         }
-        // records -> planes, kRecBatch independent loads in flight per thread
+        // records -> planes, kRecBatch independent loads in flight per thread.
+        // Item k is (ray pair, probe, ray within the pair): two threads read a
+        // probe's 32 contiguous bytes, a warp writes 32 consecutive plane floats.
         for (int k0 = threadIdx.x; k0 < PG * R; k0 += kRecBatch * blockDim.x) {
             float4 rec[kRecBatch];
 #pragma unroll
             for (int b = 0; b < kRecBatch; ++b) {
                 const int k = k0 + b * blockDim.x;
-                rec[b] = k < np * R ? records[(int64_t)g0 * R + k] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                const int q = k >> 1, pp = q % PG, ray = 2 * (q / PG) + (k & 1);
+                rec[b] = (k < PG * R && pp < np) ? records[(int64_t)(g0 + pp) * R + ray]
+                                                 : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             }
 #pragma unroll
             for (int b = 0; b < kRecBatch; ++b) {
                 const int k = k0 + b * blockDim.x;
                 if (k < PG * R) {
-                    const int pp = k / R, o = pp * RS + (k - pp * R);
+                    const int q = k >> 1, o = (2 * (q / PG) + (k & 1)) * PG + q % PG;
                     pr[o] = rec[b].x;
                     pgc[o] = rec[b].y;
                     pbc[o] = rec[b].z;
@@ -342,11 +351,12 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, B
                 }
             }
         }
-        // distance tile: sum w d at acc[a*4+b], sum w d^2 at acc[16+a*4+b];
-        // irradiance tile: r, g, b at acc[{0, 8, 16} + a*2+b]
-        float acc[32];
+        // distance tile: sum w d of probes (4 pq, 4 pq + 1) at acc[2 a], of
+        // (4 pq + 2, 4 pq + 3) at acc[2 a + 1], sum w d^2 at acc[8 + ...];
+        // irradiance tile: r, g, b of probes (2 pq, 2 pq + 1) at acc[{0, 4, 8} + a]
+        uint64_t acc[16];
 #pragma unroll
-        for (int k = 0; k < 32; ++k) acc[k] = 0.0f;
+        for (int k = 0; k < 16; ++k) acc[k] = 0ull;
         for (int c = 0; c < n_chunks; ++c) {
             if (c + 1 < n_chunks) {
                 issue_chunk(c + 1);
@@ -357,59 +367,49 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, B
             __syncthreads();   // chunk c (and, at c = 0, the planes) visible to all
             const float* wb = wbuf + (c & 1) * wrows * kTileWS;
             const int c0 = c * kTileKC, kc = min(kTileKC, R - c0);
-            if (is_dist) {
+            if (is_dist && live) {
                 for (int j = 0; j < kc; j += 4) {
-                    float4 w[4], d[4];
+                    float4 w[4];
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
                         w[a] = *reinterpret_cast<const float4*>(wb + (tq + a * nqd) * kTileWS + j);
 #pragma unroll
-                    for (int b = 0; b < 4; ++b)
-                        d[b] = *reinterpret_cast<const float4*>(pdc + (4 * pq + b) * RS + c0 + j);
-#pragma unroll
                     for (int ii = 0; ii < 4; ++ii) {
+                        const float4 dq = *reinterpret_cast<const float4*>(pdc + (c0 + j + ii) * PG + 4 * pq);
+                        const uint64_t d01 = f2_pack(dq.x, dq.y), d23 = f2_pack(dq.z, dq.w);
+                        const uint64_t q01 = f2_mul(d01, d01), q23 = f2_mul(d23, d23);
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            const float dv = ii == 0 ? d[b].x : ii == 1 ? d[b].y : ii == 2 ? d[b].z : d[b].w;
-                            const float d2 = dv * dv;
-#pragma unroll
-                            for (int a = 0; a < 4; ++a) {
-                                const float wv = ii == 0 ? w[a].x : ii == 1 ? w[a].y : ii == 2 ? w[a].z : w[a].w;
-                                acc[a * 4 + b] = fmaf(wv, dv, acc[a * 4 + b]);
-                                acc[16 + a * 4 + b] = fmaf(wv, d2, acc[16 + a * 4 + b]);
-                            }
+                        for (int a = 0; a < 4; ++a) {
+                            const float wv = ii == 0 ? w[a].x : ii == 1 ? w[a].y : ii == 2 ? w[a].z : w[a].w;
+                            const uint64_t w2 = f2_pack(wv, wv);
+                            acc[2 * a] = f2_fma(w2, d01, acc[2 * a]);
+                            acc[2 * a + 1] = f2_fma(w2, d23, acc[2 * a + 1]);
+                            acc[8 + 2 * a] = f2_fma(w2, q01, acc[8 + 2 * a]);
+                            acc[8 + 2 * a + 1] = f2_fma(w2, q23, acc[8 + 2 * a + 1]);
                         }
                     }
                 }
-            } else if (is_irr) {
+            } else if (is_irr && live) {
                 const float* wsi = wb + 4 * nqd * kTileWS;
                 for (int j = 0; j < kc; j += 4) {
-                    float4 w[4], cr[2], cg[2], cb[2];
+                    float4 w[4];
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
                         w[a] = *reinterpret_cast<const float4*>(wsi + (tq + a * nqi) * kTileWS + j);
 #pragma unroll
-                    for (int b = 0; b < 2; ++b) {
-                        const int o = (2 * pq + b) * RS + c0 + j;
-                        cr[b] = *reinterpret_cast<const float4*>(pr + o);
-                        cg[b] = *reinterpret_cast<const float4*>(pgc + o);
-                        cb[b] = *reinterpret_cast<const float4*>(pbc + o);
-                    }
-#pragma unroll
                     for (int ii = 0; ii < 4; ++ii) {
+                        const int o = (c0 + j + ii) * PG + 2 * pq;
+                        const float2 lr = *reinterpret_cast<const float2*>(pr + o);
+                        const float2 lg = *reinterpret_cast<const float2*>(pgc + o);
+                        const float2 lb = *reinterpret_cast<const float2*>(pbc + o);
+                        const uint64_t r2 = f2_pack(lr.x, lr.y), g2 = f2_pack(lg.x, lg.y), b2 = f2_pack(lb.x, lb.y);
 #pragma unroll
                         for (int a = 0; a < 4; ++a) {
                             const float wv = ii == 0 ? w[a].x : ii == 1 ? w[a].y : ii == 2 ? w[a].z : w[a].w;
-#pragma unroll
-                            for (int b = 0; b < 2; ++b) {
-                                const float4 r4 = cr[b], g4 = cg[b], b4 = cb[b];
-                                const float lr = ii == 0 ? r4.x : ii == 1 ? r4.y : ii == 2 ? r4.z : r4.w;
-                                const float lg = ii == 0 ? g4.x : ii == 1 ? g4.y : ii == 2 ? g4.z : g4.w;
-                                const float lb = ii == 0 ? b4.x : ii == 1 ? b4.y : ii == 2 ? b4.z : b4.w;
-                                acc[a * 2 + b] = fmaf(wv, lr, acc[a * 2 + b]);
-                                acc[8 + a * 2 + b] = fmaf(wv, lg, acc[8 + a * 2 + b]);
-                                acc[16 + a * 2 + b] = fmaf(wv, lb, acc[16 + a * 2 + b]);
-                            }
+                            const uint64_t w2 = f2_pack(wv, wv);
+                            acc[a] = f2_fma(w2, r2, acc[a]);
+                            acc[4 + a] = f2_fma(w2, g2, acc[4 + a]);
+                            acc[8 + a] = f2_fma(w2, b2, acc[8 + a]);
                         }
                     }
                 }
@@ -422,46 +422,58 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, B
         // loop, not once per unrolled output
         float* sum_d = sm;                    // [PG][td] x (m1, m2)
         float* sum_i = sm + 2 * PG * td;      // [PG][ti] x (r, g, b)
-        if (is_dist) {
+        if (is_dist && live) {
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 const int t = tq + a * nqd;
+                float m1[4], m2[4];
+                f2_unpack(acc[2 * a], m1[0], m1[1]);
+                f2_unpack(acc[2 * a + 1], m1[2], m1[3]);
+                f2_unpack(acc[8 + 2 * a], m2[0], m2[1]);
+                f2_unpack(acc[8 + 2 * a + 1], m2[2], m2[3]);
 #pragma unroll
                 for (int b = 0; b < 4; ++b)
                     if (t < td) {
                         const int o = (4 * pq + b) * td + t;
-                        sum_d[2 * o] = acc[a * 4 + b];
-                        sum_d[2 * o + 1] = acc[16 + a * 4 + b];
+                        sum_d[2 * o] = m1[b];
+                        sum_d[2 * o + 1] = m2[b];
                     }
             }
-        } else if (is_irr) {
+        } else if (is_irr && live) {
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 const int t = tq + a * nqi;
+                float cr[2], cg[2], cb[2];
+                f2_unpack(acc[a], cr[0], cr[1]);
+                f2_unpack(acc[4 + a], cg[0], cg[1]);
+                f2_unpack(acc[8 + a], cb[0], cb[1]);
 #pragma unroll
                 for (int b = 0; b < 2; ++b)
                     if (t < ti) {
                         const int o = (2 * pq + b) * ti + t;
-                        sum_i[3 * o] = acc[a * 2 + b];
-                        sum_i[3 * o + 1] = acc[8 + a * 2 + b];
-                        sum_i[3 * o + 2] = acc[16 + a * 2 + b];
+                        sum_i[3 * o] = cr[b];
+                        sum_i[3 * o + 1] = cg[b];
+                        sum_i[3 * o + 2] = cb[b];
                     }
             }
         }
         __syncthreads();
 #pragma unroll 2
         for (int o = threadIdx.x; o < np * td; o += blockDim.x) {
-            const int pp = o / td, t = o - pp * td;
+            const int pp = (int)fast_div((uint32_t)o, bp.div_td), t = o - pp * td;
+            const int y = (int)fast_div((uint32_t)t, bp.div_nd), x = t - y * nd;
             const int e = s_probe[pp];
-            blend_dist_texel(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, t, sum_d[2 * o],
-                             sum_d[2 * o + 1], __ldg(inv_s_dist + t), s_newly[pp] != 0, status);
+            blend_dist_texel_at(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, x + 1, y + 1,
+                                sum_d[2 * o], sum_d[2 * o + 1], __ldg(inv_s_dist + t), s_newly[pp] != 0, status);
         }
 #pragma unroll 2
         for (int o = threadIdx.x; o < np * ti; o += blockDim.x) {
-            const int pp = o / ti, t = o - pp * ti;
+            const int pp = (int)fast_div((uint32_t)o, bp.div_ti), t = o - pp * ti;
+            const int y = (int)fast_div((uint32_t)t, bp.div_ni), x = t - y * ni;
             const int e = s_probe[pp];
-            blend_irr_texel(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, t, sum_i[3 * o],
-                            sum_i[3 * o + 1], sum_i[3 * o + 2], __ldg(inv_s_irr + t), s_newly[pp] != 0, status);
+            blend_irr_texel_at(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, x + 1, y + 1,
+                               sum_i[3 * o], sum_i[3 * o + 1], sum_i[3 * o + 2], __ldg(inv_s_irr + t),
+                               s_newly[pp] != 0, status);
         }
         __syncthreads();
         if (threadIdx.x < np && s_newly[threadIdx.x]) {
@@ -555,7 +567,23 @@ static cudaError_t launch_tiled(const VolSet& vs, const BlendParams& bp, int irr
     cudaError_t e = opt_in_blend<MULTI, PG>();
     if (e != cudaSuccess) return e;
     const TiledShape ts = tiled_shape(PG, bp.R, irr_n, dist_n);
-    k_blend_tiled<MULTI, PG><<<grid, ts.threads, ts.smem, st>>>(vs, bp, w_irr, inv_s_irr, w_dist, inv_s_dist,
+    // one wave of resident CTAs; the kernel splits the active probes evenly
+    static int occ_threads = -1, occ = 0;
+    if (occ_threads != ts.threads) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_blend_tiled<MULTI, PG>, ts.threads, ts.smem);
+        if (e != cudaSuccess) return e;
+        occ_threads = ts.threads;
+    }
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    grid = sms * (occ > 0 ? occ : 1);
+    BlendParams bpt = bp;
+    bpt.div_ti = make_fast_div((uint32_t)(irr_n * irr_n));
+    bpt.div_td = make_fast_div((uint32_t)(dist_n * dist_n));
+    bpt.div_ni = make_fast_div((uint32_t)irr_n);
+    bpt.div_nd = make_fast_div((uint32_t)dist_n);
+    k_blend_tiled<MULTI, PG><<<grid, ts.threads, ts.smem, st>>>(vs, bpt, w_irr, inv_s_irr, w_dist, inv_s_dist,
                                                                 records, active, count, status);
     return cudaGetLastError();
 }

@@ -102,6 +102,34 @@ __device__ __forceinline__ uint8_t state_advanced(uint8_t s) {
 
 // Bilinear footprint in a bordered tile of n interior texels: the octahedral
 // coordinate [-1,1] spans texel positions [1, n+1]; texel k has its centre at k+0.5.
+// Two floats in one 64-bit register pair, for the packed FP32 pair
+// arithmetic of sm_100 and later (sub / mul / fma .rn.f32x2: each half
+// rounded exactly as the scalar instruction would).
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+// a * b + c, each half one fused multiply-add (as fmaf)
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 struct Footprint {
     int x0, y0;
     float tx, ty;
