@@ -135,7 +135,7 @@ struct ddgi_volume_s {
     uint32_t* status = nullptr;
     float4* records = nullptr;     // [P * R]
     float4* dirs = nullptr;        // [R]
-    double* dirs64 = nullptr;      // [R][3] the same in double precision (weights)
+    double* sf64 = nullptr;        // [R][3] unrotated ray pattern sf(i, R), double (frame setup)
     float* w_irr = nullptr;        // [irr_n^2][R]
     float* inv_s_irr = nullptr;
     float* w_dist = nullptr;       // [dist_n^2][R]
@@ -469,7 +469,7 @@ static ddgi_status check_desc(const ddgi_volume_desc* d) {
 void ddgi_volume_destroy(ddgi_volume v) {
     if (!v) return;
     cudaFree(v->states); cudaFree(v->irr); cudaFree(v->dist); cudaFree(v->lists); cudaFree(v->counts);
-    cudaFree(v->status); cudaFree(v->records); cudaFree(v->dirs); cudaFree(v->dirs64); cudaFree(v->w_irr);
+    cudaFree(v->status); cudaFree(v->records); cudaFree(v->dirs); cudaFree(v->sf64); cudaFree(v->w_irr);
     cudaFree(v->inv_s_irr); cudaFree(v->w_dist); cudaFree(v->inv_s_dist); cudaFree(v->stats);
     cudaFree(v->shadow_list); cudaFree(v->hit_list); cudaFree(v->perm);
     for (void* p : v->snap_irr) cudaFree(p);
@@ -521,7 +521,8 @@ ddgi_status ddgi_volume_create(const ddgi_volume_desc* desc, ddgi_volume* out) {
     A((void**)&v->status, sizeof(uint32_t));
     A((void**)&v->records, sizeof(float4) * (size_t)v->P * v->R);
     A((void**)&v->dirs, sizeof(float4) * 3 * v->R);
-    A((void**)&v->dirs64, sizeof(double) * 3 * v->R);
+    A((void**)&v->sf64, sizeof(double) * 3 * v->R);
+    if (e == cudaSuccess) e = launch_sf_table(v->R, v->sf64, 0);
     A((void**)&v->offsets, sizeof(float4) * (size_t)v->P);
     if (desc->optimizer_iters > 0) {
         A((void**)&v->opt_dirs, sizeof(float4) * 3 * v->R);
@@ -658,24 +659,22 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
     VolView view = make_view(v);
     int sms = sm_count();
     FrameRot rot = frame_rotation(d.seed, params->frame);
-    {
-        StageTimer tm(v, 4, st);
-        DDGI_CK(launch_frame_setup(rot, v->R, d.irr_n, d.dist_n, d.dist_cos_power, v->dirs, v->dirs64, v->w_irr,
-                                   v->inv_s_irr, v->w_dist, v->inv_s_dist, st));
-        if (tensor)
-            DDGI_CK(launch_pack_weights(v->w_irr, v->w_dist, v->R, d.irr_n, d.dist_n,
-                                        params->blend_precision == DDGI_BLEND_BF16, v->pack_irr, v->pack_dist,
-                                        v->inv_irr_r, v->inv_dist_r, st));
-    }
     // the active list can be kept from the previous frame when no state can
     // have changed in between: no uninitialised probe, no dynamic object
     // waking or putting probes to sleep, same probe range
     const bool keep_list = d.state_machine && !v->uninit_possible && v->n_dyn == 0 && !v->awake_possible &&
                            v->list_begin == begin && v->list_end == end;
-    if (keep_list) {   // clear the trace counters only, keep the list counts
-        DDGI_CK(cudaMemsetAsync(v->counts + 4, 0, sizeof(int32_t) * (kCounterInts - 4), st));
-    } else {
-        DDGI_CK(cudaMemsetAsync(v->counts, 0, sizeof(int32_t) * kCounterInts, st));   // lists and trace counters
+    {
+        StageTimer tm(v, 4, st);
+        // the setup launch also clears the trace counters, and the list counts
+        // unless the active list is kept (below)
+        DDGI_CK(launch_frame_setup(rot, v->R, d.irr_n, d.dist_n, d.dist_cos_power, v->sf64, v->dirs, v->w_irr,
+                                   v->inv_s_irr, v->w_dist, v->inv_s_dist, keep_list ? v->counts + 4 : v->counts,
+                                   keep_list ? kCounterInts - 4 : kCounterInts, st));
+        if (tensor)
+            DDGI_CK(launch_pack_weights(v->w_irr, v->w_dist, v->R, d.irr_n, d.dist_n,
+                                        params->blend_precision == DDGI_BLEND_BF16, v->pack_irr, v->pack_dist,
+                                        v->inv_irr_r, v->inv_dist_r, st));
     }
     // uninitialised probes (none after a full-range update, until states are
     // set again): position optimizer iterations, then classification
@@ -1008,7 +1007,7 @@ struct ddgi_cascade_s {
     int32_t* shadow_count = nullptr;
     int32_t* perm = nullptr;
     float4* dirs = nullptr;
-    double* dirs64 = nullptr;
+    double* sf64 = nullptr;   // [R][3] unrotated ray pattern, double
     float *w_irr = nullptr, *inv_s_irr = nullptr, *w_dist = nullptr, *inv_s_dist = nullptr;
     uint8_t *pack_irr = nullptr, *pack_dist = nullptr;
     float *inv_irr_r = nullptr, *inv_dist_r = nullptr;
@@ -1030,7 +1029,7 @@ void cascade_free(ddgi_cascade_s* c) {
     for (int k = 0; k < c->n; ++k) { cudaFree(c->states[k]); cudaFree(c->irr[k]); cudaFree(c->dist[k]); }
     cudaFree(c->lists); cudaFree(c->counts); cudaFree(c->status); cudaFree(c->records);
     cudaFree(c->shadow_list); cudaFree(c->hit_list); cudaFree(c->perm); cudaFree(c->dirs);
-    cudaFree(c->dirs64);
+    cudaFree(c->sf64);
     cudaFree(c->w_irr);
     cudaFree(c->inv_s_irr); cudaFree(c->w_dist); cudaFree(c->inv_s_dist); cudaFree(c->pack_irr);
     cudaFree(c->pack_dist); cudaFree(c->inv_irr_r); cudaFree(c->inv_dist_r); cudaFree(c->d_params);
@@ -1120,12 +1119,12 @@ ddgi_status cascade_enqueue(ddgi_cascade_s* c, const DevScene& sc, const Lights&
     vs.n = c->n;
     DDGI_CK(cudaMemcpyAsync(c->d_params, c->h_params[slot], sizeof(FrameParams), cudaMemcpyHostToDevice, st));
     DDGI_CK(launch_reset_planes(vs, c->d_params->planes, &c->d_params->n_planes, kMaxPlanes, st));
-    DDGI_CK(launch_frame_setup_dev(&c->d_params->rot, c->R, d0.irr_n, d0.dist_n, d0.dist_cos_power, c->dirs, c->dirs64,
-                                   c->w_irr, c->inv_s_irr, c->w_dist, c->inv_s_dist, st));
+    // frame setup; also clears the lists and trace counters
+    DDGI_CK(launch_frame_setup_dev(&c->d_params->rot, c->R, d0.irr_n, d0.dist_n, d0.dist_cos_power, c->sf64, c->dirs,
+                                   c->w_irr, c->inv_s_irr, c->w_dist, c->inv_s_dist, c->counts, kCounterInts, st));
     if (tensor)
         DDGI_CK(launch_pack_weights(c->w_irr, c->w_dist, c->R, d0.irr_n, d0.dist_n, precision == DDGI_BLEND_BF16,
                                     c->pack_irr, c->pack_dist, c->inv_irr_r, c->inv_dist_r, st));
-    DDGI_CK(cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * kCounterInts, st));   // lists and trace counters
     DDGI_CK(launch_build_list_multi(vs, (int)c->total, 0, c->lists, c->counts + 0, st));
     DDGI_CK(launch_classify_multi(sc, vs, c->dirs, c->R, c->perm, c->lists, c->counts + 0, sms * 8, st));
     DDGI_CK(launch_build_list_multi(vs, (int)c->total, 1, c->lists + c->total, c->counts + 1, st));
@@ -1205,7 +1204,8 @@ ddgi_status ddgi_cascade_create(const ddgi_volume_desc* descs, int32_t n, ddgi_c
     A((void**)&c->shadow_list, sizeof(int32_t) * (size_t)c->total * c->R);
     A((void**)&c->hit_list, sizeof(int32_t) * (size_t)c->total * c->R);
     A((void**)&c->dirs, sizeof(float4) * 3 * c->R);
-    A((void**)&c->dirs64, sizeof(double) * 3 * c->R);
+    A((void**)&c->sf64, sizeof(double) * 3 * c->R);
+    if (e == cudaSuccess) e = launch_sf_table(c->R, c->sf64, 0);
     A((void**)&c->perm, sizeof(int32_t) * c->R);
     if (e == cudaSuccess) {
         std::vector<int32_t> perm = ray_order_morton(c->R);
@@ -1586,8 +1586,8 @@ ddgi_status ddgi_diff_backward(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
     for (int f = n_frames - 1; f >= 0; --f) {
         DDGI_CK(launch_border_fold(g, (int)v->P, d.irr_n, st));
         FrameRot rot = frame_rotation(d.seed, first_frame + f);
-        DDGI_CK(launch_frame_setup(rot, v->R, d.irr_n, d.dist_n, d.dist_cos_power, v->dirs, v->dirs64, v->w_irr, v->inv_s_irr,
-                                   v->w_dist, v->inv_s_dist, st));
+        DDGI_CK(launch_frame_setup(rot, v->R, d.irr_n, d.dist_n, d.dist_cos_power, v->sf64, v->dirs, v->w_irr,
+                                   v->inv_s_irr, v->w_dist, v->inv_s_dist, nullptr, 0, st));
         DDGI_CK(launch_blend_adjoint(snap_view(f + 1), v->w_irr, v->inv_s_irr, g, (int)v->P, v->R, v->records, st));
         DDGI_CK(cudaMemsetAsync(gp, 0, gbytes, st));
         DDGI_CK(launch_shade_adjoint(s->dev, snap_view(f), L, v->dirs, (int)v->P, v->R, v->records, d_emit_dev,

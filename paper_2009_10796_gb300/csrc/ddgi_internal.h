@@ -167,15 +167,18 @@ FrameRot frame_rotation(uint64_t seed, int64_t frame);
 // ---------------------------------------------------------------------------
 // Kernel launchers (k_*.cu)
 // ---------------------------------------------------------------------------
-// Frame ray pattern and texel weights; dirs64 is [R][3] double scratch.
 // Per-frame direction buffers hold 3R float4: the R ray directions (w = 0),
 // then for ray i the two packed ray constants of dir_pre_pack at R + 2i.
+// Frame ray pattern and texel weights in one launch.  sf64: [R][3] double,
+// the unrotated pattern written once by launch_sf_table; the first n_zero
+// ints at zero (counters) are cleared by the same launch.
+cudaError_t launch_sf_table(int R, double* sf64, cudaStream_t st);
 cudaError_t launch_frame_setup(const FrameRot& rot, int R, int irr_n, int dist_n, float cos_power,
-                               float4* dirs, double* dirs64, float* w_irr, float* inv_s_irr, float* w_dist,
-                               float* inv_s_dist, cudaStream_t st);
+                               const double* sf64, float4* dirs, float* w_irr, float* inv_s_irr, float* w_dist,
+                               float* inv_s_dist, int32_t* zero, int n_zero, cudaStream_t st);
 cudaError_t launch_frame_setup_dev(const FrameRot* rot_dev, int R, int irr_n, int dist_n, float cos_power,
-                                   float4* dirs, double* dirs64, float* w_irr, float* inv_s_irr, float* w_dist,
-                                   float* inv_s_dist, cudaStream_t st);
+                                   const double* sf64, float4* dirs, float* w_irr, float* inv_s_irr, float* w_dist,
+                                   float* inv_s_dist, int32_t* zero, int n_zero, cudaStream_t st);
 cudaError_t launch_build_list(const uint8_t* states, int P, int which, int32_t* list,
                               int32_t* count, cudaStream_t st);
 // probes [begin, end) only (a shard of the grid)

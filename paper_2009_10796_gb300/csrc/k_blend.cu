@@ -1,6 +1,6 @@
 // Per-frame ray pattern and the probe blend (Sec. 2.3 Eq. 1, Sec. 4.2, 4.3, 7.1).
 //
-// k_frame_dirs and k_frame_weights compute, once per frame and shared by
+// k_frame_setup computes, once per frame and shared by
 // every probe, the ray directions w_i = R_t sf(i, R) and the texel weight
 // matrices
 //   W_irr[t][i]  = max(0, n_t . w_i)              (cosine weight)
@@ -43,10 +43,25 @@ __device__ void sf_dir(int i, int n, double v[3]) {
     v[2] = z;
 }
 
+__device__ __forceinline__ void rotate_dir(const FrameRot& rot, const double sv[3], double out[3]) {
+    for (int a = 0; a < 3; ++a) out[a] = rot.m[3 * a] * sv[0] + rot.m[3 * a + 1] * sv[1] + rot.m[3 * a + 2] * sv[2];
+}
+
 __device__ void frame_dir(const FrameRot& rot, int i, int n, double out[3]) {
     double sv[3];
     sf_dir(i, n, sv);
-    for (int a = 0; a < 3; ++a) out[a] = rot.m[3 * a] * sv[0] + rot.m[3 * a + 1] * sv[1] + rot.m[3 * a + 2] * sv[2];
+    rotate_dir(rot, sv, out);
+}
+
+// The float ray direction and its packed traversal constants in a
+// direction buffer of 3R float4 (directions, then two constants per ray).
+__device__ __forceinline__ void store_frame_dir(float4* dirs, int R, int i, const double w[3]) {
+    const float3 d = f3((float)w[0], (float)w[1], (float)w[2]);
+    dirs[i] = make_float4(d.x, d.y, d.z, 0.0f);
+    float4 a, b;
+    dir_pre_pack(d, a, b);
+    dirs[R + 2 * i] = a;
+    dirs[R + 2 * i + 1] = b;
 }
 
 __device__ void texel_dir(int t, int n, double v[3]) {
@@ -77,12 +92,7 @@ __global__ void __launch_bounds__(32) k_frame_dirs(FrameRot rot_arg, const Frame
     const FrameRot rot = ROT_DEV ? *rot_dev : rot_arg;
     double w[3];
     frame_dir(rot, i, R, w);
-    const float3 d = f3((float)w[0], (float)w[1], (float)w[2]);
-    dirs[i] = make_float4(d.x, d.y, d.z, 0.0f);
-    float4 a, b;   // the ray constants of this direction, after the R directions
-    dir_pre_pack(d, a, b);
-    dirs[R + 2 * i] = a;
-    dirs[R + 2 * i + 1] = b;
+    store_frame_dir(dirs, R, i, w);
     dirs64[3 * i] = w[0];
     dirs64[3 * i + 1] = w[1];
     dirs64[3 * i + 2] = w[2];
@@ -104,23 +114,52 @@ __device__ double cos_pow(double c, double p) {
     return pow(c, p);
 }
 
-// grid: irr_n^2 + dist_n^2 blocks; block b < irr_n^2 handles irradiance
-// texel b, the others distance texels; rays strided over the block.
-__global__ void __launch_bounds__(256) k_frame_weights(int R, int irr_n, int dist_n, double cos_power,
-                                                       const double* __restrict__ dirs64, float* w_irr,
-                                                       float* inv_s_irr, float* w_dist, float* inv_s_dist) {
+// The unrotated pattern sf(i, R) in double precision, once per volume.
+__global__ void k_sf_table(int R, double* sf64) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < R) sf_dir(i, R, sf64 + 3 * i);
+}
+
+// One launch of the whole frame setup.  Block b < irr_n^2 handles
+// irradiance texel b, the next dist_n^2 blocks the distance texels, rays
+// strided over the block: each rotates the pattern itself from the sf table
+// (the same double operations as k_frame_dirs, so the same directions),
+// writes its weight row and 1 / row sum.  The remaining blocks write the
+// frame's float directions and ray constants, and the first of them clears
+// n_zero counters.  No block waits on another.
+template <bool ROT_DEV>
+__global__ void __launch_bounds__(256) k_frame_setup(FrameRot rot_arg, const FrameRot* rot_dev, int R, int irr_n,
+                                                     int dist_n, double cos_power,
+                                                     const double* __restrict__ sf64, float4* dirs, float* w_irr,
+                                                     float* inv_s_irr, float* w_dist, float* inv_s_dist,
+                                                     int32_t* zero, int n_zero) {
     __shared__ double red[256];
     __shared__ double s_nt[3];
+    const FrameRot rot = ROT_DEV ? *rot_dev : rot_arg;
+    const int ti = irr_n * irr_n, nwb = ti + dist_n * dist_n;
+    if ((int)blockIdx.x >= nwb) {
+        if ((int)blockIdx.x == nwb && (int)threadIdx.x < n_zero) zero[threadIdx.x] = 0;
+        const int i = ((int)blockIdx.x - nwb) * blockDim.x + threadIdx.x;
+        if (i < R) {
+            const double sv[3] = {sf64[3 * i], sf64[3 * i + 1], sf64[3 * i + 2]};
+            double w[3];
+            rotate_dir(rot, sv, w);
+            store_frame_dir(dirs, R, i, w);
+        }
+        return;
+    }
     const int b = blockIdx.x;
-    const int ti = irr_n * irr_n;
     const bool is_irr = b < ti;
     const int t = is_irr ? b : b - ti;
-    if (threadIdx.x == 0) texel_dir(t, is_irr ? irr_n : dist_n, s_nt);   // once per block: FP64 is slow here
+    if (threadIdx.x == 0) texel_dir(t, is_irr ? irr_n : dist_n, s_nt);
     __syncthreads();
     const double nt[3] = {s_nt[0], s_nt[1], s_nt[2]};
     double acc = 0.0;
     for (int i = threadIdx.x; i < R; i += blockDim.x) {
-        double c = fmax(0.0, nt[0] * dirs64[3 * i] + nt[1] * dirs64[3 * i + 1] + nt[2] * dirs64[3 * i + 2]);
+        const double sv[3] = {sf64[3 * i], sf64[3 * i + 1], sf64[3 * i + 2]};
+        double w[3];
+        rotate_dir(rot, sv, w);
+        double c = fmax(0.0, nt[0] * w[0] + nt[1] * w[1] + nt[2] * w[2]);
         double wt = is_irr ? c : cos_pow(c, cos_power);
         acc += wt;
         if (is_irr) w_irr[(int64_t)t * R + i] = (float)wt;
@@ -492,25 +531,28 @@ cudaError_t launch_frame_dirs(const FrameRot& rot, int R, float4* dirs, double* 
     return cudaGetLastError();
 }
 
+cudaError_t launch_sf_table(int R, double* sf64, cudaStream_t st) {
+    k_sf_table<<<(R + 127) / 128, 128, 0, st>>>(R, sf64);
+    return cudaGetLastError();
+}
+
+static int frame_setup_grid(int R, int irr_n, int dist_n) { return irr_n * irr_n + dist_n * dist_n + (R + 255) / 256; }
+
 cudaError_t launch_frame_setup(const FrameRot& rot, int R, int irr_n, int dist_n, float cos_power,
-                               float4* dirs, double* dirs64, float* w_irr, float* inv_s_irr, float* w_dist,
-                               float* inv_s_dist, cudaStream_t st) {
-    k_frame_dirs<false><<<(R + 31) / 32, 32, 0, st>>>(rot, nullptr, R, dirs, dirs64);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_frame_weights<<<irr_n * irr_n + dist_n * dist_n, 256, 0, st>>>(R, irr_n, dist_n, (double)cos_power, dirs64,
-                                                                      w_irr, inv_s_irr, w_dist, inv_s_dist);
+                               const double* sf64, float4* dirs, float* w_irr, float* inv_s_irr, float* w_dist,
+                               float* inv_s_dist, int32_t* zero, int n_zero, cudaStream_t st) {
+    k_frame_setup<false><<<frame_setup_grid(R, irr_n, dist_n), 256, 0, st>>>(
+        rot, nullptr, R, irr_n, dist_n, (double)cos_power, sf64, dirs, w_irr, inv_s_irr, w_dist, inv_s_dist, zero,
+        n_zero);
     return cudaGetLastError();
 }
 
 cudaError_t launch_frame_setup_dev(const FrameRot* rot_dev, int R, int irr_n, int dist_n, float cos_power,
-                                   float4* dirs, double* dirs64, float* w_irr, float* inv_s_irr, float* w_dist,
-                                   float* inv_s_dist, cudaStream_t st) {
-    k_frame_dirs<true><<<(R + 31) / 32, 32, 0, st>>>(FrameRot{}, rot_dev, R, dirs, dirs64);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_frame_weights<<<irr_n * irr_n + dist_n * dist_n, 256, 0, st>>>(R, irr_n, dist_n, (double)cos_power, dirs64,
-                                                                      w_irr, inv_s_irr, w_dist, inv_s_dist);
+                                   const double* sf64, float4* dirs, float* w_irr, float* inv_s_irr, float* w_dist,
+                                   float* inv_s_dist, int32_t* zero, int n_zero, cudaStream_t st) {
+    k_frame_setup<true><<<frame_setup_grid(R, irr_n, dist_n), 256, 0, st>>>(
+        FrameRot{}, rot_dev, R, irr_n, dist_n, (double)cos_power, sf64, dirs, w_irr, inv_s_irr, w_dist, inv_s_dist,
+        zero, n_zero);
     return cudaGetLastError();
 }
 

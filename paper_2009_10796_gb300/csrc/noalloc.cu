@@ -26,7 +26,7 @@ constexpr int64_t kNaMaxRecords = 1 << 20;    // probes x rays (16 MiB of ray re
 
 static __device__ __align__(256) float4 g_na_records[kNaMaxRecords];
 static __device__ __align__(256) float4 g_na_dirs[3 * kNaMaxRays];   // directions, then ray constants
-static __device__ __align__(256) double g_na_dirs64[3 * kNaMaxRays];
+static __device__ __align__(256) double g_na_dirs64[3 * kNaMaxRays];   // unrotated ray pattern
 static __device__ __align__(256) float g_na_w_irr[kNaMaxIrrTexels * kNaMaxRays];
 static __device__ __align__(256) float g_na_inv_s_irr[kNaMaxIrrTexels];
 static __device__ __align__(256) float g_na_w_dist[kNaMaxDistTexels * kNaMaxRays];
@@ -181,11 +181,12 @@ extern "C" ddgi_status ddgi_update_noalloc(ddgi_scene scene, const ddgi_volume_d
     cudaStream_t st = (cudaStream_t)stream;
     int sms = sm_count();
     FrameRot rot = frame_rotation(d->seed, params->frame);
-    // the arrays keep the previous call's contents: counters and status start at zero
-    if ((e = cudaMemsetAsync(s.counts, 0, sizeof(int32_t) * 4, st)) != cudaSuccess) return na_fail(e, "clear counters");
+    // the arrays keep the previous call's contents: counters and status start
+    // at zero (the frame setup clears the counters)
     if ((e = cudaMemsetAsync(s.status, 0, sizeof(uint32_t) * 4, st)) != cudaSuccess) return na_fail(e, "clear status");
-    if ((e = launch_frame_setup(rot, R, d->irr_n, d->dist_n, d->dist_cos_power, s.dirs, s.dirs64, s.w_irr, s.inv_s_irr,
-                                s.w_dist, s.inv_s_dist, st)) != cudaSuccess)
+    if ((e = launch_sf_table(R, s.dirs64, st)) != cudaSuccess) return na_fail(e, "ray pattern");
+    if ((e = launch_frame_setup(rot, R, d->irr_n, d->dist_n, d->dist_cos_power, s.dirs64, s.dirs, s.w_irr,
+                                s.inv_s_irr, s.w_dist, s.inv_s_dist, s.counts, 4, st)) != cudaSuccess)
         return na_fail(e, "frame setup");
     if (d->state_machine) {
         if ((e = launch_build_list(states_dev, (int)P, 0, s.lists, s.counts + 0, st)) != cudaSuccess)
