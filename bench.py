@@ -399,9 +399,10 @@ def run_gpu(args):
                          f"query points "
                          f"({t_q:.2f} s), extrapolated to {n_act_cpu} active probes (oracle's own "
                          f"estimate) + {n_pix} pixels"}
-    # steady-state frame: directions + weights, 3 trace passes, blend, query (the
-    # active list is kept and classification skipped once no probe is uninitialised)
-    launches_per_step = 7
+    # steady-state frame: frame setup (directions, weights, counter clear), 3 trace
+    # passes, blend, query (the active list is kept and classification skipped
+    # once no probe is uninitialised)
+    launches_per_step = 6
     line = {
         "metric": METRIC, "value": value, "unit": "Grays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
