@@ -275,8 +275,10 @@ ddgi_status ddgi_query(ddgi_volume volume, const float* pos_dev, const float* nr
  * (Sec. 2.2) of n points whose G-buffer lives on the host.
  *   pos_host, nrm_host [n][3] float, host; out_host [n][3] float, host.
  * The input copy runs on an internal stream while the probe update runs on
- * `stream`; the query then runs in chunks whose result copies overlap the
- * next chunk's query.  Asynchronous like the other calls: out_host holds
+ * `stream`.  When out_host is page-locked and mapped for the device (as
+ * cudaHostAlloc memory is under unified addressing) the query writes it
+ * directly; otherwise the query runs in chunks whose result copies overlap
+ * the next chunk's query.  Asynchronous like the other calls: out_host holds
  * the irradiance once `stream` has completed the work enqueued here; the
  * host arrays must stay valid and unchanged until then.  Page-locked host
  * memory keeps the copies asynchronous; pageable memory works but

@@ -842,9 +842,18 @@ ddgi_status ddgi_frame_host(ddgi_volume v, ddgi_scene s, const ddgi_lights* ligh
         return r;
     }
     DDGI_CK(cudaStreamWaitEvent(st, v->ev_in, 0));
-    // query in chunks; each chunk's result copy overlaps the next chunk's query
     const float3 cam = make_float3(camera_pos[0], camera_pos[1], camera_pos[2]);
     const VolView view = make_view(v);
+    // page-locked, device-mapped result memory: the query writes it directly
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, out_host) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer != nullptr) {
+        DDGI_CK(launch_query(view, pos_d, nrm_d, n, cam, (float*)pa.devicePointer, st, true));
+        return DDGI_OK;
+    }
+    (void)cudaGetLastError();   // an unregistered pointer is not an error here
+    // otherwise the query runs in chunks; each chunk's result copy overlaps
+    // the next chunk's query
     const int64_t chunk = (n + kChunks - 1) / kChunks;
     for (int c = 0; c < kChunks; ++c) {
         const int64_t a = c * chunk, b = std::min(n, a + chunk);

@@ -264,7 +264,8 @@ cudaError_t launch_query_glossy(const VolView& v, const float* pos, const float*
 // Dynamic-object wake-up over probes [begin, end); boxes [n][6] device, extended.
 cudaError_t launch_wake(const VolView& v, const float* boxes, int n_boxes, int begin, int end, cudaStream_t st);
 cudaError_t launch_query(const VolView& v, const float* pos, const float* nrm, int64_t n,
-                         float3 camera, float* out, cudaStream_t st);
+                         float3 camera, float* out, cudaStream_t st,
+                         bool out_host = false);
 cudaError_t launch_query_cascade(const VolSet& vs, const float* pos, const float* nrm, int64_t n, float3 camera,
                                  float* out, cudaStream_t st);
 // Resets probe planes that a tracking window leapfrogged: planes[i] =

@@ -3,27 +3,55 @@
 
 namespace ddgi {
 
-// One thread per point; positions, normals and outputs are [n][3] floats, read
-// and written with unit-stride scalar accesses (coalesced per warp).
-__global__ void __launch_bounds__(256) k_query(VolView v, const float* __restrict__ pos,
-                                               const float* __restrict__ nrm, int64_t n, float3 cam,
-                                               float* __restrict__ out) {
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        float3 x = f3(__ldg(pos + 3 * q), __ldg(pos + 3 * q + 1), __ldg(pos + 3 * q + 2));
-        float3 nn = f3(__ldg(nrm + 3 * q), __ldg(nrm + 3 * q + 1), __ldg(nrm + 3 * q + 2));
+// One thread per point; positions and normals are [n][3] floats read with
+// unit-stride scalar loads (coalesced per warp).  STAGE_OUT: a block's
+// outputs are staged in shared memory and written as one contiguous run
+// (16-byte stores when the run is aligned), so each warp writes whole lines,
+// for page-locked host memory written across the host link; otherwise each
+// thread stores its own three floats (device memory).
+constexpr int kQueryThreads = 256;
+template <bool STAGE_OUT>
+__global__ void __launch_bounds__(kQueryThreads) k_query(VolView v, const float* __restrict__ pos,
+                                                         const float* __restrict__ nrm, int64_t n, float3 cam,
+                                                         float* __restrict__ out) {
+    __shared__ __align__(16) float s_out[3 * kQueryThreads];
+    for (int64_t q0 = (int64_t)blockIdx.x * kQueryThreads; q0 < n; q0 += (int64_t)gridDim.x * kQueryThreads) {
+        const int64_t q = q0 + threadIdx.x;
         float3 E = f3(0.0f, 0.0f, 0.0f);
-        if (nn.x != 0.0f || nn.y != 0.0f || nn.z != 0.0f) {
-            float3 wo = cam - x;
-            float l = length(wo);
-            wo = l < 1e-6f ? nn : (1.0f / l) * wo;
-            float3 M = query_M(v, x, nn, wo);
-            const float pi = 3.14159265358979323846f;
-            E = f3(pi * M.x, pi * M.y, pi * M.z);
+        if (q < n) {
+            float3 x = f3(__ldg(pos + 3 * q), __ldg(pos + 3 * q + 1), __ldg(pos + 3 * q + 2));
+            float3 nn = f3(__ldg(nrm + 3 * q), __ldg(nrm + 3 * q + 1), __ldg(nrm + 3 * q + 2));
+            if (nn.x != 0.0f || nn.y != 0.0f || nn.z != 0.0f) {
+                float3 wo = cam - x;
+                float l = length(wo);
+                wo = l < 1e-6f ? nn : (1.0f / l) * wo;
+                float3 M = query_M(v, x, nn, wo);
+                const float pi = 3.14159265358979323846f;
+                E = f3(pi * M.x, pi * M.y, pi * M.z);
+            }
         }
-        out[3 * q] = E.x;
-        out[3 * q + 1] = E.y;
-        out[3 * q + 2] = E.z;
+        if (!STAGE_OUT) {
+            if (q < n) {
+                out[3 * q] = E.x;
+                out[3 * q + 1] = E.y;
+                out[3 * q + 2] = E.z;
+            }
+            continue;
+        }
+        s_out[3 * threadIdx.x] = E.x;
+        s_out[3 * threadIdx.x + 1] = E.y;
+        s_out[3 * threadIdx.x + 2] = E.z;
+        __syncthreads();
+        const int nf = 3 * (int)min((int64_t)kQueryThreads, n - q0);   // floats of this block's run
+        float* dst = out + 3 * q0;
+        if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+            for (int i = threadIdx.x; i < nf / 4; i += kQueryThreads)
+                reinterpret_cast<float4*>(dst)[i] = reinterpret_cast<const float4*>(s_out)[i];
+            for (int i = (nf / 4) * 4 + threadIdx.x; i < nf; i += kQueryThreads) dst[i] = s_out[i];
+        } else {
+            for (int i = threadIdx.x; i < nf; i += kQueryThreads) dst[i] = s_out[i];
+        }
+        __syncthreads();
     }
 }
 
@@ -207,11 +235,14 @@ cudaError_t launch_reset_planes(const VolSet& vs, const int4* planes, const int3
 }
 
 cudaError_t launch_query(const VolView& v, const float* pos, const float* nrm, int64_t n, float3 camera,
-                         float* out, cudaStream_t st) {
+                         float* out, cudaStream_t st, bool out_host) {
     if (n == 0) return cudaSuccess;
-    int64_t blocks = (n + 255) / 256;
+    int64_t blocks = (n + kQueryThreads - 1) / kQueryThreads;
     int grid = (int)(blocks < 1048576 ? blocks : 1048576);
-    k_query<<<grid, 256, 0, st>>>(v, pos, nrm, n, camera, out);
+    if (out_host)
+        k_query<true><<<grid, kQueryThreads, 0, st>>>(v, pos, nrm, n, camera, out);
+    else
+        k_query<false><<<grid, kQueryThreads, 0, st>>>(v, pos, nrm, n, camera, out);
     return cudaGetLastError();
 }
 
