@@ -407,7 +407,9 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, B
             const float* wb = wbuf + (c & 1) * wrows * kTileWS;
             const int c0 = c * kTileKC, kc = min(kTileKC, R - c0);
             if (is_dist && live) {
-                for (int j = 0; j < kc; j += 4) {
+#pragma unroll
+                for (int j = 0; j < kTileKC; j += 4) {
+                    if (j >= kc) break;
                     float4 w[4];
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
@@ -430,7 +432,9 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, B
                 }
             } else if (is_irr && live) {
                 const float* wsi = wb + 4 * nqd * kTileWS;
-                for (int j = 0; j < kc; j += 4) {
+#pragma unroll
+                for (int j = 0; j < kTileKC; j += 4) {
+                    if (j >= kc) break;
                     float4 w[4];
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
