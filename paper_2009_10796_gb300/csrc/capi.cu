@@ -168,6 +168,9 @@ struct ddgi_volume_s {
     cudaStream_t copy_in = nullptr, copy_out = nullptr;
     cudaEvent_t ev_entry = nullptr, ev_in = nullptr, ev_out = nullptr;
     cudaEvent_t ev_chunk[4] = {nullptr, nullptr, nullptr, nullptr};
+    // the frame's texel weights run on a side stream, overlapping the trace
+    cudaStream_t setup_st = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_weights = nullptr;
     bool timing = false;
     TimedStage stages[8];
 };
@@ -478,6 +481,9 @@ void ddgi_volume_destroy(ddgi_volume v) {
     cudaFree(v->pack_irr); cudaFree(v->pack_dist); cudaFree(v->inv_irr_r); cudaFree(v->inv_dist_r);
     cudaFree(v->offsets); cudaFree(v->opt_dirs); cudaFree(v->opt_dirs64); cudaFree(v->dyn_boxes);
     cudaFree(v->stage);
+    if (v->setup_st) cudaStreamDestroy(v->setup_st);
+    if (v->ev_fork) cudaEventDestroy(v->ev_fork);
+    if (v->ev_weights) cudaEventDestroy(v->ev_weights);
     if (v->copy_in) cudaStreamDestroy(v->copy_in);
     if (v->copy_out) cudaStreamDestroy(v->copy_out);
     for (cudaEvent_t e : {v->ev_entry, v->ev_in, v->ev_out, v->ev_chunk[0], v->ev_chunk[1], v->ev_chunk[2],
@@ -666,15 +672,26 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
                            v->list_begin == begin && v->list_end == end;
     {
         StageTimer tm(v, 4, st);
-        // the setup launch also clears the trace counters, and the list counts
-        // unless the active list is kept (below)
-        DDGI_CK(launch_frame_setup(rot, v->R, d.irr_n, d.dist_n, d.dist_cos_power, v->sf64, v->dirs, v->w_irr,
-                                   v->inv_s_irr, v->w_dist, v->inv_s_dist, keep_list ? v->counts + 4 : v->counts,
-                                   keep_list ? kCounterInts - 4 : kCounterInts, st));
+        if (!v->setup_st) {
+            DDGI_CK(cudaStreamCreateWithFlags(&v->setup_st, cudaStreamNonBlocking));
+            DDGI_CK(cudaEventCreateWithFlags(&v->ev_fork, cudaEventDisableTiming));
+            DDGI_CK(cudaEventCreateWithFlags(&v->ev_weights, cudaEventDisableTiming));
+        }
+        // the texel weights (and their tensor-core packing) on the side stream,
+        // after all earlier work on the stream (the previous blend read them);
+        // the directions on the stream.  The directions launch also clears the
+        // trace counters, and the list counts unless the active list is kept.
+        DDGI_CK(cudaEventRecord(v->ev_fork, st));
+        DDGI_CK(cudaStreamWaitEvent(v->setup_st, v->ev_fork, 0));
+        DDGI_CK(launch_frame_setup_split(rot, v->R, d.irr_n, d.dist_n, d.dist_cos_power, v->sf64, v->dirs, v->w_irr,
+                                         v->inv_s_irr, v->w_dist, v->inv_s_dist,
+                                         keep_list ? v->counts + 4 : v->counts,
+                                         keep_list ? kCounterInts - 4 : kCounterInts, st, v->setup_st));
         if (tensor)
             DDGI_CK(launch_pack_weights(v->w_irr, v->w_dist, v->R, d.irr_n, d.dist_n,
                                         params->blend_precision == DDGI_BLEND_BF16, v->pack_irr, v->pack_dist,
-                                        v->inv_irr_r, v->inv_dist_r, st));
+                                        v->inv_irr_r, v->inv_dist_r, v->setup_st));
+        DDGI_CK(cudaEventRecord(v->ev_weights, v->setup_st));
     }
     // uninitialised probes (none after a full-range update, until states are
     // set again): position optimizer iterations, then classification
@@ -729,6 +746,7 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
     bp.thr_high = d.thr_high;
     bp.thr_step = d.thr_step;
     bp.R = v->R;
+    DDGI_CK(cudaStreamWaitEvent(st, v->ev_weights, 0));   // the frame's weights are ready
     {
         StageTimer tm(v, 3, st);
         if (tensor)

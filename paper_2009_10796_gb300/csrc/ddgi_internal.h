@@ -176,6 +176,12 @@ cudaError_t launch_sf_table(int R, double* sf64, cudaStream_t st);
 cudaError_t launch_frame_setup(const FrameRot& rot, int R, int irr_n, int dist_n, float cos_power,
                                const double* sf64, float4* dirs, float* w_irr, float* inv_s_irr, float* w_dist,
                                float* inv_s_dist, int32_t* zero, int n_zero, cudaStream_t st);
+// The same as two launches: the texel weights on st_weights, the directions
+// (and the counter clear) on st_dirs, so the weights can overlap the trace.
+cudaError_t launch_frame_setup_split(const FrameRot& rot, int R, int irr_n, int dist_n, float cos_power,
+                                     const double* sf64, float4* dirs, float* w_irr, float* inv_s_irr,
+                                     float* w_dist, float* inv_s_dist, int32_t* zero, int n_zero,
+                                     cudaStream_t st_dirs, cudaStream_t st_weights);
 cudaError_t launch_frame_setup_dev(const FrameRot* rot_dev, int R, int irr_n, int dist_n, float cos_power,
                                    const double* sf64, float4* dirs, float* w_irr, float* inv_s_irr, float* w_dist,
                                    float* inv_s_dist, int32_t* zero, int n_zero, cudaStream_t st);

@@ -132,14 +132,15 @@ __global__ void __launch_bounds__(256) k_frame_setup(FrameRot rot_arg, const Fra
                                                      int dist_n, double cos_power,
                                                      const double* __restrict__ sf64, float4* dirs, float* w_irr,
                                                      float* inv_s_irr, float* w_dist, float* inv_s_dist,
-                                                     int32_t* zero, int n_zero) {
+                                                     int32_t* zero, int n_zero, int first_block) {
     __shared__ double red[256];
     __shared__ double s_nt[3];
     const FrameRot rot = ROT_DEV ? *rot_dev : rot_arg;
     const int ti = irr_n * irr_n, nwb = ti + dist_n * dist_n;
-    if ((int)blockIdx.x >= nwb) {
-        if ((int)blockIdx.x == nwb && (int)threadIdx.x < n_zero) zero[threadIdx.x] = 0;
-        const int i = ((int)blockIdx.x - nwb) * blockDim.x + threadIdx.x;
+    const int blk = (int)blockIdx.x + first_block;   // a launch may cover a sub-range of the blocks
+    if (blk >= nwb) {
+        if (blk == nwb && (int)threadIdx.x < n_zero) zero[threadIdx.x] = 0;
+        const int i = (blk - nwb) * blockDim.x + threadIdx.x;
         if (i < R) {
             const double sv[3] = {sf64[3 * i], sf64[3 * i + 1], sf64[3 * i + 2]};
             double w[3];
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(256) k_frame_setup(FrameRot rot_arg, const Fra
         }
         return;
     }
-    const int b = blockIdx.x;
+    const int b = blk;
     const bool is_irr = b < ti;
     const int t = is_irr ? b : b - ti;
     if (threadIdx.x == 0) texel_dir(t, is_irr ? irr_n : dist_n, s_nt);
@@ -547,7 +548,22 @@ cudaError_t launch_frame_setup(const FrameRot& rot, int R, int irr_n, int dist_n
                                float* inv_s_dist, int32_t* zero, int n_zero, cudaStream_t st) {
     k_frame_setup<false><<<frame_setup_grid(R, irr_n, dist_n), 256, 0, st>>>(
         rot, nullptr, R, irr_n, dist_n, (double)cos_power, sf64, dirs, w_irr, inv_s_irr, w_dist, inv_s_dist, zero,
-        n_zero);
+        n_zero, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_frame_setup_split(const FrameRot& rot, int R, int irr_n, int dist_n, float cos_power,
+                                     const double* sf64, float4* dirs, float* w_irr, float* inv_s_irr,
+                                     float* w_dist, float* inv_s_dist, int32_t* zero, int n_zero,
+                                     cudaStream_t st_dirs, cudaStream_t st_weights) {
+    const int nwb = irr_n * irr_n + dist_n * dist_n;
+    k_frame_setup<false><<<nwb, 256, 0, st_weights>>>(rot, nullptr, R, irr_n, dist_n, (double)cos_power, sf64, dirs,
+                                                      w_irr, inv_s_irr, w_dist, inv_s_dist, zero, n_zero, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_frame_setup<false><<<(R + 255) / 256, 256, 0, st_dirs>>>(rot, nullptr, R, irr_n, dist_n, (double)cos_power,
+                                                                sf64, dirs, w_irr, inv_s_irr, w_dist, inv_s_dist,
+                                                                zero, n_zero, nwb);
     return cudaGetLastError();
 }
 
@@ -556,7 +572,7 @@ cudaError_t launch_frame_setup_dev(const FrameRot* rot_dev, int R, int irr_n, in
                                    float* inv_s_dist, int32_t* zero, int n_zero, cudaStream_t st) {
     k_frame_setup<true><<<frame_setup_grid(R, irr_n, dist_n), 256, 0, st>>>(
         FrameRot{}, rot_dev, R, irr_n, dist_n, (double)cos_power, sf64, dirs, w_irr, inv_s_irr, w_dist, inv_s_dist,
-        zero, n_zero);
+        zero, n_zero, 0);
     return cudaGetLastError();
 }
 
