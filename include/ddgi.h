@@ -194,6 +194,13 @@ typedef struct {
                                    (0: off; the paper uses 5); single volumes only */
     float   offset_limit;       /* largest probe offset per axis, fraction of the spacing,
                                    [0, 0.5) (the paper leaves it open; 0.45) */
+    int32_t converge_batches;   /* optional converge pass (Sec. 6.3): 0 = off; else 1..64
+                                   batches of R rays traced for Newly Vigilant / Newly
+                                   Awake probes, which take the encoded weighted
+                                   average over all of them (hysteresis 0) and become
+                                   Vigilant / Awake before the frame's update; batch b
+                                   uses the rotation of (seed + 0xD1B54A32D192ED03 (b+1),
+                                   frame); single volumes only */
 } ddgi_volume_desc;
 
 /* Allocate a volume: zeroed atlases (Tab. "algtable": uniform

@@ -56,7 +56,8 @@ class OrVolume(C.Structure):
                 ("state_machine", C.c_int64), ("seed", C.c_uint64), ("shift", C.c_int64 * 3),
                 ("blend_lo", C.c_double * 3), ("blend_hi", C.c_double * 3),
                 ("offsets", C.POINTER(C.c_double)), ("opt_iters", C.c_int64), ("offset_limit", C.c_double),
-                ("dyn_boxes", C.POINTER(C.c_double)), ("n_dyn", C.c_int64)]
+                ("dyn_boxes", C.POINTER(C.c_double)), ("n_dyn", C.c_int64),
+                ("converge_batches", C.c_int64)]
 
 
 def build(force: bool = False, extra_flags=()) -> str:
@@ -205,6 +206,7 @@ def make_volume(desc, shift=(0, 0, 0), origin=None, blend_lo=None, blend_hi=None
         v.offsets = offsets.ctypes.data_as(C.POINTER(C.c_double))
     v.opt_iters = int(getattr(desc, "optimizer_iters", 0))
     v.offset_limit = float(getattr(desc, "offset_limit", 0.45))
+    v.converge_batches = int(getattr(desc, "converge_batches", 0))
     org = desc.origin if origin is None else origin
     v.origin[:] = [float(x) for x in org]
     v.spacing[:] = [float(x) for x in desc.spacing]

@@ -755,6 +755,82 @@ static void blend_probe(const or_volume* v, const double* dirs, const double* ra
 }
 
 /* ------------------------------------------------------------------ */
+/* Optional converge pass for new probes (Sec. 6.3)                     */
+/* ------------------------------------------------------------------ */
+static void converge_probes(const or_scene* s, const or_lights* L, const or_volume* v, int64_t frame,
+                            int64_t nn, const int64_t* nl, uint8_t* states, double* irr, double* dist) {
+    const int64_t R = v->rays, B = v->converge_batches;
+    const int64_t ni = v->irr_n, nd = v->dist_n;
+    const int64_t tsi = irr_tile_size(v), tsd = dist_tile_size(v);
+    double* bdirs = (double*)malloc(sizeof(double) * 3 * (size_t)(B * R));
+    for (int64_t b = 0; b < B; ++b)
+        or_frame_dirs(v->seed + 0xD1B54A32D192ED03ULL * (uint64_t)(b + 1), frame, R, bdirs + 3 * b * R);
+    double* ni_t = (double*)malloc(sizeof(double) * (size_t)(nn * tsi));
+    double* nd_t = (double*)malloc(sizeof(double) * (size_t)(nn * tsd));
+    const uint8_t* st1[1] = { states };
+    const double* ir1[1] = { irr };
+    const double* di1[1] = { dist };
+    or_prev prev = { 1, v, st1, ir1, di1 };
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < nn; ++q) {
+        const int64_t p = nl[q];
+        double* ti = ni_t + q * tsi;
+        double* td = nd_t + q * tsd;
+        memcpy(ti, irr + p * tsi, sizeof(double) * (size_t)tsi);
+        memcpy(td, dist + p * tsd, sizeof(double) * (size_t)tsd);
+        double* num_i = (double*)calloc((size_t)(ni * ni * 4), sizeof(double));   /* r, g, b, sum w */
+        double* num_d = (double*)calloc((size_t)(nd * nd * 3), sizeof(double));   /* mu, mu2, sum w */
+        double x[3];
+        probe_pos_phys(v, p, x);
+        for (int64_t b = 0; b < B; ++b)
+            for (int64_t r = 0; r < R; ++r) {
+                const double* dir = bdirs + 3 * (b * R + r);
+                double ray[4];
+                shade_ray(s, L, v, &prev, x, dir, ray);
+                for (int64_t t = 0; t < ni * ni; ++t) {
+                    double nt[3];
+                    or_texel_dir(t % ni, t / ni, ni, nt);
+                    const double w = fmax(0.0, dot3(nt, dir));
+                    for (int k = 0; k < 3; ++k) num_i[4 * t + k] += w * ray[k];
+                    num_i[4 * t + 3] += w;
+                }
+                for (int64_t t = 0; t < nd * nd; ++t) {
+                    double nt[3];
+                    or_texel_dir(t % nd, t / nd, nd, nt);
+                    const double w = pow(fmax(0.0, dot3(nt, dir)), v->cos_power);
+                    num_d[3 * t] += w * ray[3];
+                    num_d[3 * t + 1] += w * ray[3] * ray[3];
+                    num_d[3 * t + 2] += w;
+                }
+            }
+        for (int64_t t = 0; t < ni * ni; ++t) {
+            if (!(num_i[4 * t + 3] > 0.0)) continue;   /* no ray in reach: keeps its value */
+            double* e = TILE(ti, ni + 2, 3, t % ni + 1, t / ni + 1);
+            for (int k = 0; k < 3; ++k) e[k] = pow(num_i[4 * t + k] / num_i[4 * t + 3], 1.0 / v->gamma);
+        }
+        for (int64_t t = 0; t < nd * nd; ++t) {
+            if (!(num_d[3 * t + 2] > 0.0)) continue;
+            double* e = TILE(td, nd + 2, 2, t % nd + 1, t / nd + 1);
+            e[0] = num_d[3 * t] / num_d[3 * t + 2];
+            e[1] = num_d[3 * t + 1] / num_d[3 * t + 2];
+        }
+        or_border_copy(ti, ni, 3);
+        or_border_copy(td, nd, 2);
+        free(num_i);
+        free(num_d);
+    }
+    for (int64_t q = 0; q < nn; ++q) {
+        const int64_t p = nl[q];
+        memcpy(irr + p * tsi, ni_t + q * tsi, sizeof(double) * (size_t)tsi);
+        memcpy(dist + p * tsd, nd_t + q * tsd, sizeof(double) * (size_t)tsd);
+        states[p] = advanced(states[p]);
+    }
+    free(ni_t);
+    free(nd_t);
+    free(bdirs);
+}
+
+/* ------------------------------------------------------------------ */
 /* One update frame over a probe subset (Sec. 2.3, Sec. 6.3 listing)    */
 /* ------------------------------------------------------------------ */
 void or_update(const or_scene* s, const or_lights* L, const or_volume* v, int64_t frame,
@@ -776,6 +852,19 @@ void or_update(const or_scene* s, const or_lights* L, const or_volume* v, int64_
         if (nu) or_classify(s, v, frame, nu, un, states, NULL, NULL);
         free(un);
         or_wake(v, n, list, states);
+    }
+    /* 1b. optional converge pass (Sec. 6.3): every Newly Vigilant / Newly Awake
+       probe traces converge_batches batches of R rays against the atlas as it
+       stands (batch b rotated by (seed + 0xD1B54A32D192ED03 (b+1), frame)),
+       takes per texel the weighted average over all of them, encoded, with
+       hysteresis 0, and becomes Vigilant / Awake.  The new texels are
+       committed after all of them are shaded. */
+    if (v->state_machine && v->converge_batches > 0) {
+        int64_t nn = 0;
+        int64_t* nl = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+        for (int64_t q = 0; q < n; ++q) if (is_newly(states[list[q]])) nl[nn++] = list[q];
+        if (nn) converge_probes(s, L, v, frame, nn, nl, states, irr, dist);
+        free(nl);
     }
     /* 2. trace and shade every ray of every active probe against the old atlas */
     double* dirs = (double*)malloc(sizeof(double) * 3 * (size_t)R);

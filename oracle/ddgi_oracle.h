@@ -65,6 +65,7 @@ typedef struct {
     double  offset_limit;       /* largest offset per axis, as a fraction of the spacing */
     const double* dyn_boxes;    /* [n_dyn][6] dynamic-object boxes (lo xyz, hi xyz), Sec. 6.3 */
     int64_t n_dyn;
+    int64_t converge_batches;   /* optional converge pass for new probes (Sec. 6.3), 0 = off */
 } or_volume;
 
 enum { OR_UNINIT = 0, OR_OFF = 1, OR_SLEEPING = 2, OR_NEWLY_VIGILANT = 3, OR_VIGILANT = 4,

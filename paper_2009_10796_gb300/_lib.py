@@ -38,7 +38,7 @@ class VolumeDesc(C.Structure):
                 ("thr_low", C.c_float), ("thr_high", C.c_float), ("thr_step", C.c_float),
                 ("state_machine", C.c_int32), ("irr_format", C.c_int32), ("dist_format", C.c_int32),
                 ("tracking", C.c_int32), ("seed", C.c_uint64), ("optimizer_iters", C.c_int32),
-                ("offset_limit", C.c_float)]
+                ("offset_limit", C.c_float), ("converge_batches", C.c_int32)]
 
 
 class VolumeInfo(C.Structure):

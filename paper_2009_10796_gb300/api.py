@@ -152,6 +152,7 @@ def desc_struct(d) -> _lib.VolumeDesc:
     s.seed = int(getattr(d, "seed", 0))
     s.optimizer_iters = int(getattr(d, "optimizer_iters", 0))
     s.offset_limit = float(getattr(d, "offset_limit", 0.45))
+    s.converge_batches = int(getattr(d, "converge_batches", 0))
     return s
 
 

@@ -126,6 +126,7 @@ class VolumeDesc:
     tracking: int = 0
     optimizer_iters: int = 0  # position-optimizer iterations for new probes (Sec. 5; the paper uses 5)
     offset_limit: float = 0.45  # largest probe offset per axis, fraction of the spacing
+    converge_batches: int = 0  # optional converge pass for new probes (Sec. 6.3), batches of R rays
 
     def resolved_t_max(self) -> float:
         if self.t_max >= 0:
