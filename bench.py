@@ -383,7 +383,12 @@ def run_gpu(args):
     paper_res = None if args.no_paper_res else run_paper_resolution(args, g, torch, stream, scene, L, pos, nrm,
                                                                      camera, flush)
     optimizer = None if args.no_paper_res else run_optimizer(args, g, torch, stream, scene, L)
-    dynamic = None if args.no_paper_res else run_dynamic(args, g, torch, stream, scene, L, pos, nrm, camera, flush)
+    dynamic = None
+    if not args.no_paper_res:
+        dynamic = run_dynamic(args, g, torch, stream, scene, L, pos, nrm, camera, flush)
+        # the same with the optional converge pass: 4 batches of R rays for every probe woken
+        dynamic["converge_pass"] = run_dynamic(args, g, torch, stream, scene, L, pos, nrm, camera, flush,
+                                               converge=4)
     cascade = None if args.no_cascade else run_cascade(args, g, torch, stream)
     diff = None if args.no_diff else run_diff(args, g, torch, stream)
 
@@ -554,12 +559,13 @@ def run_optimizer(args, g, torch, stream, scene, L):
     return out
 
 
-def run_dynamic(args, g, torch, stream, scene, L, pos, nrm, camera, flush):
+def run_dynamic(args, g, torch, stream, scene, L, pos, nrm, camera, flush, converge=0):
     """Dynamic objects (Sec. 6.3) in the city: 32 vehicle-sized boxes (4 x 1.5 x
     2 m) flying straight lines over the streets at 5-30 m, where the sleeping
     probes are, waking those near them; the same step as the headline (update
-    + 1080p query) with the boxes updated every frame."""
-    desc = synth.city_volume()
+    + 1080p query) with the boxes updated every frame.  converge: batches of
+    the optional converge pass for the probes woken each frame."""
+    desc = synth.city_volume(converge_batches=converge)
     vol = g.Volume(desc)
     out = torch.empty_like(pos)
     rng = np.random.default_rng(4004)
@@ -599,7 +605,7 @@ def run_dynamic(args, g, torch, stream, scene, L, pos, nrm, camera, flush):
     ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
     return {"workload": "city + 32 vehicle-sized boxes flying at 5-30 m, waking sleeping probes", "ms_per_step": ms,
             "grays_per_s": n_active * desc.rays_per_probe / (ms * 1e-3) / 1e9, "awake_probes": n_awake,
-            "active_probes": n_active}
+            "active_probes": n_active, "converge_batches": converge}
 
 
 def run_diff(args, g, torch, stream):

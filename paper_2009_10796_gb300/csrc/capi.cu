@@ -130,7 +130,7 @@ struct ddgi_volume_s {
     void* irr = nullptr;
     void* dist = nullptr;
     int32_t* lists = nullptr;      // [0, P): uninit list, [P, 2P): active list
-    int32_t* counts = nullptr;     // [0] uninit count, [1] active count, [4..9] trace counters
+    int32_t* counts = nullptr;     // [0] uninit count, [1] active count, [2] new-probe count, [4..9] trace counters
                                    // (shadow_count below), all cleared by one memset per frame
     uint32_t* status = nullptr;
     float4* records = nullptr;     // [P * R]
@@ -168,6 +168,12 @@ struct ddgi_volume_s {
     cudaStream_t copy_in = nullptr, copy_out = nullptr;
     cudaEvent_t ev_entry = nullptr, ev_in = nullptr, ev_out = nullptr;
     cudaEvent_t ev_chunk[4] = {nullptr, nullptr, nullptr, nullptr};
+    // optional converge pass (Sec. 6.3): its batch's frame tables and the sums
+    float4* conv_dirs = nullptr;
+    float *conv_w_irr = nullptr, *conv_inv_irr = nullptr, *conv_w_dist = nullptr, *conv_inv_dist = nullptr;
+    float4* conv_acc_irr = nullptr;
+    float2* conv_acc_dist = nullptr;
+    float* conv_den = nullptr;
     // the frame's texel weights run on a side stream, overlapping the trace
     cudaStream_t setup_st = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_weights = nullptr;
@@ -466,6 +472,8 @@ static ddgi_status check_desc(const ddgi_volume_desc* d) {
         return fail(DDGI_ERR_INVALID_ARG, "optimizer_iters must be in [0, 16]");
     if (!(d->offset_limit >= 0.0f && d->offset_limit < 0.5f))
         return fail(DDGI_ERR_INVALID_ARG, "offset_limit must be in [0, 0.5)");
+    if (d->converge_batches < 0 || d->converge_batches > 64)
+        return fail(DDGI_ERR_INVALID_ARG, "converge_batches must be in [0, 64]");
     return DDGI_OK;
 }
 
@@ -481,6 +489,8 @@ void ddgi_volume_destroy(ddgi_volume v) {
     cudaFree(v->pack_irr); cudaFree(v->pack_dist); cudaFree(v->inv_irr_r); cudaFree(v->inv_dist_r);
     cudaFree(v->offsets); cudaFree(v->opt_dirs); cudaFree(v->opt_dirs64); cudaFree(v->dyn_boxes);
     cudaFree(v->stage);
+    cudaFree(v->conv_dirs); cudaFree(v->conv_w_irr); cudaFree(v->conv_inv_irr); cudaFree(v->conv_w_dist);
+    cudaFree(v->conv_inv_dist); cudaFree(v->conv_acc_irr); cudaFree(v->conv_acc_dist); cudaFree(v->conv_den);
     if (v->setup_st) cudaStreamDestroy(v->setup_st);
     if (v->ev_fork) cudaEventDestroy(v->ev_fork);
     if (v->ev_weights) cudaEventDestroy(v->ev_weights);
@@ -533,6 +543,17 @@ ddgi_status ddgi_volume_create(const ddgi_volume_desc* desc, ddgi_volume* out) {
     if (desc->optimizer_iters > 0) {
         A((void**)&v->opt_dirs, sizeof(float4) * 3 * v->R);
         A((void**)&v->opt_dirs64, sizeof(double) * 3 * v->R);
+    }
+    if (desc->converge_batches > 0) {
+        const size_t ti = (size_t)desc->irr_n * desc->irr_n, td = (size_t)desc->dist_n * desc->dist_n;
+        A((void**)&v->conv_dirs, sizeof(float4) * 3 * v->R);
+        A((void**)&v->conv_w_irr, sizeof(float) * ti * (size_t)v->R);
+        A((void**)&v->conv_inv_irr, sizeof(float) * ti);
+        A((void**)&v->conv_w_dist, sizeof(float) * td * (size_t)v->R);
+        A((void**)&v->conv_inv_dist, sizeof(float) * td);
+        A((void**)&v->conv_acc_irr, sizeof(float4) * ti * (size_t)v->P);
+        A((void**)&v->conv_acc_dist, sizeof(float2) * td * (size_t)v->P);
+        A((void**)&v->conv_den, sizeof(float) * (ti + td));
     }
     A((void**)&v->w_irr, sizeof(float) * desc->irr_n * desc->irr_n * (size_t)v->R);
     A((void**)&v->inv_s_irr, sizeof(float) * desc->irr_n * desc->irr_n);
@@ -716,6 +737,31 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
         StageTimer tm(v, 1, st);
         DDGI_CK(launch_wake(view, v->dyn_boxes, v->n_dyn, (int)begin, (int)end, st));
         v->awake_possible = v->n_dyn > 0;
+    }
+    // optional converge pass (Sec. 6.3): new probes (only where states changed)
+    // trace converge_batches batches of R rays against the atlas as it stands,
+    // take the encoded weighted average over all of them and advance to
+    // Vigilant / Awake before the regular trace
+    if (d.state_machine && d.converge_batches > 0 && !keep_list) {
+        StageTimer tm(v, 1, st);
+        DDGI_CK(cudaMemsetAsync(v->counts + 2, 0, sizeof(int32_t), st));
+        DDGI_CK(launch_build_list_range(v->states, (int)begin, (int)end, 2, v->lists, v->counts + 2, st));
+        for (int b = 0; b < d.converge_batches; ++b) {
+            const FrameRot rb = frame_rotation(d.seed + 0xD1B54A32D192ED03ULL * (uint64_t)(b + 1), params->frame);
+            DDGI_CK(launch_frame_setup(rb, v->R, d.irr_n, d.dist_n, d.dist_cos_power, v->sf64, v->conv_dirs,
+                                       v->conv_w_irr, v->conv_inv_irr, v->conv_w_dist, v->conv_inv_dist,
+                                       v->counts + 4, kCounterInts - 4, st));
+            DDGI_CK(launch_trace_wavefront(s->dev, view, make_lights(lights), v->conv_dirs, v->R, v->perm, v->lists,
+                                           v->counts + 2, v->records, v->shadow_list, v->hit_list, v->shadow_count,
+                                           sms * 8, st, nullptr));
+            DDGI_CK(launch_converge_accum(v->R, d.irr_n, d.dist_n, v->conv_w_irr, v->conv_w_dist, v->records,
+                                          v->counts + 2, v->conv_acc_irr, v->conv_acc_dist, v->conv_den, b == 0,
+                                          sms * 8, st));
+        }
+        DDGI_CK(launch_converge_finish(view, v->lists, v->counts + 2, v->conv_acc_irr, v->conv_acc_dist,
+                                       v->conv_den, v->status, sms * 8, st));
+        // the regular trace starts its counters from zero
+        DDGI_CK(cudaMemsetAsync(v->counts + 4, 0, sizeof(int32_t) * (kCounterInts - 4), st));
     }
     if (!keep_list) {
         StageTimer tm(v, 1, st);
@@ -1182,6 +1228,8 @@ ddgi_status ddgi_cascade_create(const ddgi_volume_desc* descs, int32_t n, ddgi_c
         if (s != DDGI_OK) return s;
         if (descs[k].optimizer_iters != 0)
             return fail(DDGI_ERR_UNSUPPORTED, "cascades have no probe position optimizer");
+        if (descs[k].converge_batches != 0)
+            return fail(DDGI_ERR_UNSUPPORTED, "cascades have no converge pass");
         const ddgi_volume_desc &a = descs[0], &b = descs[k];
         if (b.rays_per_probe != a.rays_per_probe || b.irr_n != a.irr_n || b.dist_n != a.dist_n ||
             b.irr_format != a.irr_format || b.dist_format != a.dist_format || b.gamma != a.gamma ||

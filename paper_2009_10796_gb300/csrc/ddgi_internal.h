@@ -173,6 +173,15 @@ FrameRot frame_rotation(uint64_t seed, int64_t frame);
 // the unrotated pattern written once by launch_sf_table; the first n_zero
 // ints at zero (counters) are cleared by the same launch.
 cudaError_t launch_sf_table(int R, double* sf64, cudaStream_t st);
+// Optional converge pass for new probes (Sec. 6.3): one batch's weighted
+// sums per list slot (init: first batch), then the texels and state advance.
+// acc_irr [n][irr_n^2], acc_dist [n][dist_n^2], den [irr_n^2 + dist_n^2].
+cudaError_t launch_converge_accum(int R, int irr_n, int dist_n, const float* w_irr, const float* w_dist,
+                                  const float4* records, const int32_t* count, float4* acc_irr, float2* acc_dist,
+                                  float* den, bool init, int grid, cudaStream_t st);
+cudaError_t launch_converge_finish(const VolView& v, const int32_t* list, const int32_t* count,
+                                   const float4* acc_irr, const float2* acc_dist, const float* den, uint32_t* status,
+                                   int grid, cudaStream_t st);
 cudaError_t launch_frame_setup(const FrameRot& rot, int R, int irr_n, int dist_n, float cos_power,
                                const double* sf64, float4* dirs, float* w_irr, float* inv_s_irr, float* w_dist,
                                float* inv_s_dist, int32_t* zero, int n_zero, cudaStream_t st);

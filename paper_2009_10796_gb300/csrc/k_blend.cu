@@ -531,6 +531,118 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, B
     }
 }
 
+// Optional converge pass for new probes (Sec. 6.3).  k_converge_accum adds
+// one batch's weighted sums, per list slot q and texel t,
+//   acc_irr[q][t] += sum_i W_irr[t][i] (r, g, b)_i,  acc_dist[q][t] += sum_i W_dist[t][i] (d, d^2)_i,
+// and den[t] += sum_i W[t][i] (the same for every probe; written by the
+// block of slot 0); init starts the sums.  Block per slot, thread per texel
+// (irradiance texels first), the slot's R records staged in shared memory.
+__global__ void __launch_bounds__(1024) k_converge_accum(int R, int ti, int td, const float* __restrict__ w_irr,
+                                                        const float* __restrict__ w_dist,
+                                                        const float4* __restrict__ records,
+                                                        const int32_t* __restrict__ count, float4* acc_irr,
+                                                        float2* acc_dist, float* den, int init) {
+    extern __shared__ float4 s_rec[];
+    const int n = *count;
+    const int t = threadIdx.x;
+    for (int q = blockIdx.x; q < n; q += gridDim.x) {
+        __syncthreads();
+        for (int i = t; i < R; i += blockDim.x) s_rec[i] = records[(int64_t)q * R + i];
+        __syncthreads();
+        if (t < ti) {
+            const float* w = w_irr + (int64_t)t * R;
+            float r = 0.0f, g = 0.0f, b = 0.0f, sw = 0.0f;
+            for (int i = 0; i < R; ++i) {
+                const float wi = __ldg(w + i);
+                const float4 rec = s_rec[i];
+                r = fmaf(wi, rec.x, r);
+                g = fmaf(wi, rec.y, g);
+                b = fmaf(wi, rec.z, b);
+                sw += wi;
+            }
+            float4& a = acc_irr[(int64_t)q * ti + t];
+            a = init ? make_float4(r, g, b, 0.0f) : make_float4(a.x + r, a.y + g, a.z + b, 0.0f);
+            if (q == 0) den[t] = init ? sw : den[t] + sw;
+        } else if (t < ti + td) {
+            const int u = t - ti;
+            const float* w = w_dist + (int64_t)u * R;
+            float m1 = 0.0f, m2 = 0.0f, sw = 0.0f;
+            for (int i = 0; i < R; ++i) {
+                const float wi = __ldg(w + i);
+                const float d = s_rec[i].w;
+                m1 = fmaf(wi, d, m1);
+                m2 = fmaf(wi, d * d, m2);
+                sw += wi;
+            }
+            float2& a = acc_dist[(int64_t)q * td + u];
+            a = init ? make_float2(m1, m2) : make_float2(a.x + m1, a.y + m2);
+            if (q == 0) den[t] = init ? sw : den[t] + sw;
+        }
+    }
+}
+
+// The converge pass's texels: encoded ratio of sums (hysteresis 0), border
+// copies, then Newly Vigilant / Newly Awake -> Vigilant / Awake.  A texel no
+// ray reached (den = 0) keeps its value.
+__global__ void __launch_bounds__(1024) k_converge_finish(VolView v, const int32_t* __restrict__ list,
+                                                         const int32_t* __restrict__ count,
+                                                         const float4* __restrict__ acc_irr,
+                                                         const float2* __restrict__ acc_dist,
+                                                         const float* __restrict__ den, uint32_t* status) {
+    const int n = *count;
+    const int ti = v.irr_n * v.irr_n, td = v.dist_n * v.dist_n;
+    const int t = threadIdx.x;
+    for (int q = blockIdx.x; q < n; q += gridDim.x) {
+        const int p = list[q];
+        if (t < ti) {
+            const float sw = den[t];
+            if (sw > 0.0f) {
+                const float4 a = acc_irr[(int64_t)q * ti + t];
+                const float inv = 1.0f / sw;
+                const float3 e = f3(powf(a.x * inv, v.inv_gamma), powf(a.y * inv, v.inv_gamma),
+                                    powf(a.z * inv, v.inv_gamma));
+                if (!(isfinite(e.x) && isfinite(e.y) && isfinite(e.z))) atomicOr(status, 1u);
+                const int x = 1 + t % v.irr_n, y = 1 + t / v.irr_n;
+                store_irr(v, p, x, y, e);
+                for_border_copies(x, y, v.irr_n, [&](int bx, int by) { store_irr(v, p, bx, by, e); });
+            }
+        } else if (t < ti + td) {
+            const int u = t - ti;
+            const float sw = den[t];
+            if (sw > 0.0f) {
+                const float2 a = acc_dist[(int64_t)q * td + u];
+                const float inv = 1.0f / sw;
+                const float2 e = make_float2(a.x * inv, a.y * inv);
+                if (!(isfinite(e.x) && isfinite(e.y))) atomicOr(status, 1u);
+                const int x = 1 + u % v.dist_n, y = 1 + u / v.dist_n;
+                store_dist(v, p, x, y, e);
+                for_border_copies(x, y, v.dist_n, [&](int bx, int by) { store_dist(v, p, bx, by, e); });
+            }
+        }
+        if (t == 0) v.states[p] = state_advanced(v.states[p]);
+    }
+}
+
+cudaError_t launch_converge_accum(int R, int irr_n, int dist_n, const float* w_irr, const float* w_dist,
+                                  const float4* records, const int32_t* count, float4* acc_irr, float2* acc_dist,
+                                  float* den, bool init, int grid, cudaStream_t st) {
+    const int ti = irr_n * irr_n, td = dist_n * dist_n;
+    const int threads = (ti + td + 31) / 32 * 32;
+    if (threads > 1024) return cudaErrorInvalidValue;
+    k_converge_accum<<<grid, threads, sizeof(float4) * (size_t)R, st>>>(R, ti, td, w_irr, w_dist, records, count,
+                                                                         acc_irr, acc_dist, den, init ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_converge_finish(const VolView& v, const int32_t* list, const int32_t* count,
+                                   const float4* acc_irr, const float2* acc_dist, const float* den, uint32_t* status,
+                                   int grid, cudaStream_t st) {
+    const int threads = (v.irr_n * v.irr_n + v.dist_n * v.dist_n + 31) / 32 * 32;
+    if (threads > 1024) return cudaErrorInvalidValue;
+    k_converge_finish<<<grid, threads, 0, st>>>(v, list, count, acc_irr, acc_dist, den, status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_frame_dirs(const FrameRot& rot, int R, float4* dirs, double* dirs64, cudaStream_t st) {
     k_frame_dirs<false><<<(R + 31) / 32, 32, 0, st>>>(rot, nullptr, R, dirs, dirs64);
     return cudaGetLastError();

@@ -81,7 +81,8 @@ __global__ void __launch_bounds__(256) k_query_glossy(VolView v, const float* __
 }
 
 // Compacts probe indices whose state matches `which` (0: UNINIT, 1: active =
-// NEWLY_VIGILANT or VIGILANT) into list[], count[0] += matches.  Warp-
+// traced and blended, 2: newly = Newly Vigilant or Newly Awake) into list[],
+// count[0] += matches.  Warp-
 // aggregated atomics: one atomic per warp.  List order is not deterministic;
 // consumers carry the probe index with each entry.
 __global__ void k_build_list(const uint8_t* __restrict__ states, int begin, int end, int which, int32_t* list,
@@ -92,7 +93,7 @@ __global__ void k_build_list(const uint8_t* __restrict__ states, int begin, int 
         bool pred = false;
         if (p < end) {
             uint8_t s = states[p];
-            pred = which == 0 ? s == DDGI_STATE_UNINIT : state_active(s);
+            pred = which == 0 ? s == DDGI_STATE_UNINIT : (which == 2 ? state_newly(s) : state_active(s));
         }
         unsigned mask = __ballot_sync(0xffffffffu, pred);
         if (mask == 0) continue;

@@ -119,6 +119,8 @@ extern "C" ddgi_status ddgi_update_noalloc(ddgi_scene scene, const ddgi_volume_d
         return set_error(DDGI_ERR_INVALID_ARG, "unknown atlas format");
     if (d->optimizer_iters != 0)
         return set_error(DDGI_ERR_UNSUPPORTED, "ddgi_update_noalloc: no probe position optimizer (no offset storage)");
+    if (d->converge_batches != 0)
+        return set_error(DDGI_ERR_UNSUPPORTED, "ddgi_update_noalloc: no converge pass (no storage for its sums)");
     if (!(d->gamma > 0.0f) || !(d->hysteresis_irr >= 0.0f && d->hysteresis_irr <= 1.0f) ||
         !(d->hysteresis_vis >= 0.0f && d->hysteresis_vis <= 1.0f) || !(d->dist_cos_power >= 0.0f) ||
         !(d->self_shadow_bias >= 0.0f))
