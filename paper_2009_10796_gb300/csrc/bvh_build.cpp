@@ -289,6 +289,23 @@ void collapse_wide(const std::vector<float4>& n2, std::vector<float4>& n4, int32
 
 }  // namespace
 
+int64_t wide_stack_bound(const std::vector<float4>& n4) {
+    if (n4.empty()) return 0;
+    std::vector<int32_t> st{0};
+    int64_t deepest = 1;
+    while (!st.empty()) {
+        const int32_t ref = st.back();
+        st.pop_back();
+        if (ref < 0) continue;   // a leaf
+        int32_t kid[4];
+        std::memcpy(kid, &n4[8 * (size_t)ref + 6], sizeof(kid));
+        for (int c = 0; c < 4; ++c)
+            if (kid[c] != kRefDone) st.push_back(kid[c]);
+        deepest = std::max<int64_t>(deepest, (int64_t)st.size());
+    }
+    return deepest;
+}
+
 bool build_bvh(const float* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris,
                const int32_t* tri_flags, BvhHost& out, std::string& err) {
     out = BvhHost();

@@ -260,6 +260,9 @@ ddgi_status ddgi_scene_create(const float* verts, int64_t n_verts, const int32_t
     std::string err;
     if (!build_bvh(verts, n_verts, tris, n_tris, tri_flags.data(), bvh, err))
         return fail(DDGI_ERR_INVALID_ARG, err);
+    // the 4-wide walk pushes without a bound test; the collapse keeps its
+    // stack within kStackSize4 by construction, checked here
+    if (wide_stack_bound(bvh.nodes4) > kStackSize4) return fail(DDGI_ERR_INVALID_ARG, "BVH too deep for the traversal");
     std::vector<float4> alb((size_t)n_objects), em((size_t)(n_emitters > 0 ? n_emitters : 1));
     for (int32_t o = 0; o < n_objects; ++o) {
         float fb;

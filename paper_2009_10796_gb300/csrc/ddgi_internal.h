@@ -158,6 +158,9 @@ struct BvhHost {
 };
 
 // bvh_build.cpp
+// Deepest stack of a depth-first walk of the 4-wide form that pushes every
+// child: a bound on the traversal stack (pushes fewer children, keeps one).
+int64_t wide_stack_bound(const std::vector<float4>& n4);
 bool build_bvh(const float* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris,
                const int32_t* tri_flags, BvhHost& out, std::string& err);
 

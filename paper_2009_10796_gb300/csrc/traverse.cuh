@@ -428,9 +428,11 @@ __device__ __forceinline__ void ww4_round(const DevScene& s, const RayPre& r, Ww
                 cx(k1, v1, k3, v3);
                 cx(k1, v1, k2, v2);
             }
-            if (k3 != INFINITY && w.sp < kStackSize4) w.stack[w.sp++] = v3;
-            if (k2 != INFINITY && w.sp < kStackSize4) w.stack[w.sp++] = v2;
-            if (k1 != INFINITY && w.sp < kStackSize4) w.stack[w.sp++] = v1;
+            // no bound test: scene creation checks that the hierarchy keeps the
+            // stack within kStackSize4 (wide_stack_bound)
+            if (k3 != INFINITY) w.stack[w.sp++] = v3;
+            if (k2 != INFINITY) w.stack[w.sp++] = v2;
+            if (k1 != INFINITY) w.stack[w.sp++] = v1;
             w.node = k0 != INFINITY ? v0 : ww_pop(w);
             if (w.node < 0 && w.node != kDone && w.leaf == kNoLeaf) {
                 w.leaf = w.node;

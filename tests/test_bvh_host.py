@@ -79,3 +79,20 @@ def test_bad_index_rejected(g):
     t = np.array([[0, 1, 5]], np.int32)
     with pytest.raises(g.DDGIError):
         g.bvh_check(v, t)
+
+
+def test_deep_nested_scales_keep_the_stack_bound(g):
+    """Triangles at geometrically shrinking scales around one point drive the
+    SAH tree to its depth limits; the 4-wide walk's stack (which the trace
+    kernels push without a bound test) must stay within its fixed size."""
+    rng = np.random.default_rng(11)
+    tris, verts = [], []
+    for k in range(3000):
+        s = 0.97 ** k
+        c = rng.normal(0.0, 1.0, 3) * s
+        for q in range(3):
+            verts.append(c + rng.normal(0.0, 0.1, 3) * s)
+        tris.append([3 * k, 3 * k + 1, 3 * k + 2])
+    st = _check(g, np.asarray(verts, np.float32), np.asarray(tris, np.int32))
+    print(f"[bvh] nested: {st}")
+    assert st["depth"] > 20
