@@ -272,8 +272,9 @@ __device__ __forceinline__ Hit traverse(const DevScene& s, const RayPre& r) {
 // of once per node visit for whichever lane happened to reach a leaf.  The
 // closest hit (smallest t, ties to the smaller original index) does not
 // depend on the visiting order because box culling is conservative, so the
-// result equals traverse<false>'s; for ANY, occlusion is the same.
-// Every lane of the warp must call it (inactive lanes pass valid = false).
+// result equals traverse<false>'s; for ANY, occlusion is the same.  The walk
+// runs over the 4-wide form (ww4_round); every lane of the warp takes part
+// (inactive lanes start with valid = false).
 // Stack entries are node indices (>= 0) or leaf codes
 // ~((first << kLeafBits) | (count - 1)) (1..kMaxLeafTris triangles).
 constexpr int kNoLeaf = 0;              // "no parked leaf" (leaf codes are < 0)
@@ -309,44 +310,6 @@ __device__ __forceinline__ int ww_pop(WwLane<N>& w) { return w.sp > 0 ? w.stack[
 template <bool ANY, int N, bool COUNT = false>
 __device__ __forceinline__ void ww_leaves(const DevScene& s, const RayPre& r, WwLane<N>& w,
                                           TraceCount* tc = nullptr);
-
-// One round: descend internal nodes until no lane is still looking for a
-// leaf, then test every parked leaf (and leaves popped right after it).  A
-// lane's walk is over when node == kDone after the round.  Warp-cooperative.
-template <bool ANY>
-__device__ __forceinline__ void ww_round(const DevScene& s, const RayPre& r, WwLane<>& w) {
-    while (true) {
-        if (w.node >= 0) {
-            const float4* N = s.nodes + 4 * (int64_t)w.node;
-            float4 a = __ldg(N), b = __ldg(N + 1), z = __ldg(N + 2);
-            int4 m = __ldg(reinterpret_cast<const int4*>(N + 3));
-            float e0 = box_enter(r, a.x, a.y, a.z, a.w, z.x, z.y, w.h.t);
-            float e1 = box_enter(r, b.x, b.y, b.z, b.w, z.z, z.w, w.h.t);
-            int c0 = m.x >= 0 ? m.x : leaf_code(m.x, m.z);
-            int c1 = m.y >= 0 ? m.y : leaf_code(m.y, m.w);
-            // an empty slot (leaf of 0 triangles, inverted box) is never entered
-            bool h0 = e0 != INFINITY && (m.x >= 0 || m.z > 0);
-            bool h1 = e1 != INFINITY && (m.y >= 0 || m.w > 0);
-            if (h0 && h1) {
-                bool first0 = e0 <= e1;
-                if (w.sp < kStackSize) w.stack[w.sp++] = first0 ? c1 : c0;
-                w.node = first0 ? c0 : c1;
-            } else if (h0) {
-                w.node = c0;
-            } else if (h1) {
-                w.node = c1;
-            } else {
-                w.node = ww_pop(w);
-            }
-            if (w.node < 0 && w.node != kDone && w.leaf == kNoLeaf) {
-                w.leaf = w.node;
-                w.node = ww_pop(w);
-            }
-        }
-        if (__ballot_sync(0xffffffffu, w.node >= 0 && w.leaf == kNoLeaf) == 0) break;
-    }
-    ww_leaves<ANY>(s, r, w);
-}
 
 // Leaf phase of a round: test the parked leaf and the leaves popped right
 // after it.  COUNT adds triangle tests to *tc (measurement builds only).
@@ -442,18 +405,6 @@ __device__ __forceinline__ void ww4_round(const DevScene& s, const RayPre& r, Ww
         if (__ballot_sync(0xffffffffu, w.node >= 0 && w.leaf == kNoLeaf) == 0) break;
     }
     ww_leaves<ANY, kStackSize4, COUNT>(s, r, w, tc);
-}
-
-template <bool ANY>
-__device__ __forceinline__ Hit traverse_ww(const DevScene& s, const RayPre& r, bool valid) {
-    int stack[kStackSize];
-    WwLane<> w;
-    w.stack = stack;
-    ww_start(s, w, valid);
-    do {
-        ww_round<ANY>(s, r, w);
-    } while (__ballot_sync(0xffffffffu, w.node != kDone) != 0);
-    return w.h;
 }
 
 }  // namespace ddgi
