@@ -719,7 +719,9 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
     }
     // uninitialised probes (none after a full-range update, until states are
     // set again): position optimizer iterations, then classification
+    bool states_changed = false;   // classification or waking ran: new probes may exist
     if (d.state_machine && v->uninit_possible) {
+        states_changed = true;
         {
             StageTimer tm(v, 1, st);
             DDGI_CK(launch_build_list_range(v->states, (int)begin, (int)end, 0, v->lists, v->counts + 0, st));
@@ -737,15 +739,16 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
     // dynamic objects wake sleeping probes (and awake probes fall asleep
     // again once none is near: one more pass after the boxes are cleared)
     if (d.state_machine && (v->n_dyn > 0 || v->awake_possible)) {
+        states_changed = true;
         StageTimer tm(v, 1, st);
         DDGI_CK(launch_wake(view, v->dyn_boxes, v->n_dyn, (int)begin, (int)end, st));
         v->awake_possible = v->n_dyn > 0;
     }
-    // optional converge pass (Sec. 6.3): new probes (only where states changed)
+    // optional converge pass (Sec. 6.3): new probes (only when states changed)
     // trace converge_batches batches of R rays against the atlas as it stands,
     // take the encoded weighted average over all of them and advance to
     // Vigilant / Awake before the regular trace
-    if (d.state_machine && d.converge_batches > 0 && !keep_list) {
+    if (d.state_machine && d.converge_batches > 0 && states_changed) {
         StageTimer tm(v, 1, st);
         DDGI_CK(cudaMemsetAsync(v->counts + 2, 0, sizeof(int32_t), st));
         DDGI_CK(launch_build_list_range(v->states, (int)begin, (int)end, 2, v->lists, v->counts + 2, st));

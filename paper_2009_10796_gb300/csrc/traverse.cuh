@@ -20,21 +20,9 @@ struct RayPre {
     int kx, ky, kz;
     float Sx, Sy, Sz;
     int oct;    // bit a set: axis a runs toward -inf (its near slab plane is the box's hi)
-    uint64_t o2[3], i2[3];   // o and idir per axis, doubled for the packed box tests
 };
 
-__device__ __forceinline__ void ray_set_origin(RayPre& r, float3 o) {
-    r.o = o;
-    r.o2[0] = f2_pack(o.x, o.x);
-    r.o2[1] = f2_pack(o.y, o.y);
-    r.o2[2] = f2_pack(o.z, o.z);
-}
-
-__device__ __forceinline__ void ray_set_packed_idir(RayPre& r) {
-    r.i2[0] = f2_pack(r.idir.x, r.idir.x);
-    r.i2[1] = f2_pack(r.idir.y, r.idir.y);
-    r.i2[2] = f2_pack(r.idir.z, r.idir.z);
-}
+__device__ __forceinline__ void ray_set_origin(RayPre& r, float3 o) { r.o = o; }
 
 __device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
 
@@ -60,7 +48,6 @@ __device__ __forceinline__ RayPre ray_pre(float3 o, float3 d) {
                 1.0f / (fabsf(d.z) > eps ? d.z : copysignf(eps, d.z)));
     r.oct = (signbit(r.idir.x) ? 1 : 0) | (signbit(r.idir.y) ? 2 : 0) | (signbit(r.idir.z) ? 4 : 0);
     ray_set_origin(r, o);
-    ray_set_packed_idir(r);
     return r;
 }
 
@@ -88,7 +75,6 @@ __device__ __forceinline__ RayPre ray_pre_packed(float3 o, float3 d, float4 a, f
     r.kz = (k >> 4) & 3;
     r.oct = __float_as_int(b.w);
     ray_set_origin(r, o);
-    ray_set_packed_idir(r);
     return r;
 }
 
@@ -167,18 +153,23 @@ __device__ __forceinline__ float box_enter_oct(const RayPre& r, float nx, float 
 __device__ __forceinline__ void box4_enter_oct(const RayPre& r, float4 nx, float4 fx, float4 ny, float4 fy, float4 nz,
                                                float4 fz, float tmax, float& k0, float& k1, float& k2, float& k3) {
     float tnx[4], tfx[4], tny[4], tfy[4], tnz[4], tfz[4];
-    f2_unpack(f2_mul(f2_sub(f2_pack(nx.x, nx.y), r.o2[0]), r.i2[0]), tnx[0], tnx[1]);
-    f2_unpack(f2_mul(f2_sub(f2_pack(nx.z, nx.w), r.o2[0]), r.i2[0]), tnx[2], tnx[3]);
-    f2_unpack(f2_mul(f2_sub(f2_pack(fx.x, fx.y), r.o2[0]), r.i2[0]), tfx[0], tfx[1]);
-    f2_unpack(f2_mul(f2_sub(f2_pack(fx.z, fx.w), r.o2[0]), r.i2[0]), tfx[2], tfx[3]);
-    f2_unpack(f2_mul(f2_sub(f2_pack(ny.x, ny.y), r.o2[1]), r.i2[1]), tny[0], tny[1]);
-    f2_unpack(f2_mul(f2_sub(f2_pack(ny.z, ny.w), r.o2[1]), r.i2[1]), tny[2], tny[3]);
-    f2_unpack(f2_mul(f2_sub(f2_pack(fy.x, fy.y), r.o2[1]), r.i2[1]), tfy[0], tfy[1]);
-    f2_unpack(f2_mul(f2_sub(f2_pack(fy.z, fy.w), r.o2[1]), r.i2[1]), tfy[2], tfy[3]);
-    f2_unpack(f2_mul(f2_sub(f2_pack(nz.x, nz.y), r.o2[2]), r.i2[2]), tnz[0], tnz[1]);
-    f2_unpack(f2_mul(f2_sub(f2_pack(nz.z, nz.w), r.o2[2]), r.i2[2]), tnz[2], tnz[3]);
-    f2_unpack(f2_mul(f2_sub(f2_pack(fz.x, fz.y), r.o2[2]), r.i2[2]), tfz[0], tfz[1]);
-    f2_unpack(f2_mul(f2_sub(f2_pack(fz.z, fz.w), r.o2[2]), r.i2[2]), tfz[2], tfz[3]);
+    // the doubled operands are built per visit: holding them across the walk
+    // cost more in registers (spills) than the moves cost here
+    const uint64_t o2x = f2_pack(r.o.x, r.o.x), o2y = f2_pack(r.o.y, r.o.y), o2z = f2_pack(r.o.z, r.o.z);
+    const uint64_t i2x = f2_pack(r.idir.x, r.idir.x), i2y = f2_pack(r.idir.y, r.idir.y),
+                   i2z = f2_pack(r.idir.z, r.idir.z);
+    f2_unpack(f2_mul(f2_sub(f2_pack(nx.x, nx.y), o2x), i2x), tnx[0], tnx[1]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(nx.z, nx.w), o2x), i2x), tnx[2], tnx[3]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(fx.x, fx.y), o2x), i2x), tfx[0], tfx[1]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(fx.z, fx.w), o2x), i2x), tfx[2], tfx[3]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(ny.x, ny.y), o2y), i2y), tny[0], tny[1]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(ny.z, ny.w), o2y), i2y), tny[2], tny[3]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(fy.x, fy.y), o2y), i2y), tfy[0], tfy[1]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(fy.z, fy.w), o2y), i2y), tfy[2], tfy[3]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(nz.x, nz.y), o2z), i2z), tnz[0], tnz[1]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(nz.z, nz.w), o2z), i2z), tnz[2], tnz[3]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(fz.x, fz.y), o2z), i2z), tfz[0], tfz[1]);
+    f2_unpack(f2_mul(f2_sub(f2_pack(fz.z, fz.w), o2z), i2z), tfz[2], tfz[3]);
     float tn[4], tf[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
