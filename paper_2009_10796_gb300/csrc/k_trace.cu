@@ -345,7 +345,15 @@ __global__ void __launch_bounds__(256, 4) k_shade(DevScene s, VolSet vs, Lights 
         float3 o = probe_pos_phys(v, e & kEntryMask);
         float3 n = (1.0f / length(ng)) * ng;
         float3 x = o + t * d;
-        int orig = __float_as_int(__ldg(&s.tris[3 * (int64_t)k].w));
+        // the sun's cosine term (zero when the shadow ray was blocked) and the
+        // triangle's material index now; the previous frame's probes at the
+        // hit (the volume itself, or the whole cascade) next, with little
+        // else held across that query; the material terms after it
+        const float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
+        const float kk = hr.z != 0.0f ? dot(n, tol) * 0.318309886183790672f : 0.0f;   // 1/pi
+        const int orig = __float_as_int(__ldg(&s.tris[3 * (int64_t)k].w));
+        float3 M = MULTI ? cascade_M(vs.table, vs.n, x, n, f3(-d.x, -d.y, -d.z))
+                         : query_M(v, x, n, f3(-d.x, -d.y, -d.z));
         int2 at = __ldg(s.attr + orig);
         float4 rho = __ldg(s.albedo + at.x);
         float3 Le = f3(0.0f, 0.0f, 0.0f);
@@ -353,15 +361,7 @@ __global__ void __launch_bounds__(256, 4) k_shade(DevScene s, VolSet vs, Lights 
             float4 em = __ldg(s.emit + at.y);
             Le = f3(em.x, em.y, em.z);
         }
-        float3 direct = f3(0.0f, 0.0f, 0.0f);
-        if (hr.z != 0.0f) {
-            float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
-            float kk = dot(n, tol) * 0.318309886183790672f;   // 1/pi
-            direct = f3(L.sun_irr.x * kk, L.sun_irr.y * kk, L.sun_irr.z * kk);
-        }
-        // the previous frame's probes at the hit: the volume itself, or the whole cascade
-        float3 M = MULTI ? cascade_M(vs.table, vs.n, x, n, f3(-d.x, -d.y, -d.z))
-                         : query_M(v, x, n, f3(-d.x, -d.y, -d.z));
+        const float3 direct = f3(L.sun_irr.x * kk, L.sun_irr.y * kk, L.sun_irr.z * kk);
         records[idx] = make_float4(Le.x + rho.x * (direct.x + M.x), Le.y + rho.y * (direct.y + M.y),
                                    Le.z + rho.z * (direct.z + M.z), fminf(t, v.t_max));
     }
