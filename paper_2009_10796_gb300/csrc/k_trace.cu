@@ -172,7 +172,7 @@ __device__ __forceinline__ int64_t refill(unsigned long long* next, int64_t tota
 // COUNT: measurement build that adds its 4-wide node visits and triangle
 // tests to stats[1], stats[2] (otherwise identical).
 template <bool MULTI, bool COUNT = false>
-__global__ void __launch_bounds__(256, 4) k_trace_primary(DevScene s, VolSet vs, Lights L,
+__global__ void __launch_bounds__(256, 5) k_trace_primary(DevScene s, VolSet vs, Lights L,
                                                        const float4* __restrict__ dirs, int R, FastDiv dR,
                                                        const int32_t* __restrict__ perm,
                                                        const int32_t* __restrict__ active,
@@ -190,8 +190,7 @@ __global__ void __launch_bounds__(256, 4) k_trace_primary(DevScene s, VolSet vs,
     int64_t rec = -1;   // record index of the lane's ray, -1 when idle
     int entry = 0;      // its probe's list entry
     bool exhausted = false;
-    float3 d = f3(0.0f, 0.0f, 1.0f);
-    RayPre r = ray_pre(f3(0.0f, 0.0f, 0.0f), d);
+    RayPre r = ray_pre(f3(0.0f, 0.0f, 0.0f), f3(0.0f, 0.0f, 1.0f));   // the lane's ray (r.d its direction)
     int stack[kStackSize4];
     WwLane<kStackSize4> w;
     w.stack = stack;
@@ -207,9 +206,8 @@ __global__ void __launch_bounds__(256, 4) k_trace_primary(DevScene s, VolSet vs,
             rec = (int64_t)slot * R + i;
             entry = __ldg(active + slot);
             float3 o = probe_pos_phys(vol_of<MULTI>(vs, entry >> kEntryShift), entry & kEntryMask);
-            float4 d4 = __ldg(dirs + i);
-            d = f3(d4.x, d4.y, d4.z);
-            r = ray_pre_packed(o, d, __ldg(dirs + R + 2 * i), __ldg(dirs + R + 2 * i + 1));
+            const float4 d4 = __ldg(dirs + i);
+            r = ray_pre_packed(o, f3(d4.x, d4.y, d4.z), __ldg(dirs + R + 2 * i), __ldg(dirs + R + 2 * i + 1));
             ww_start(s, w, true);
         }
         if (__ballot_sync(0xffffffffu, rec >= 0) == 0) break;
@@ -223,13 +221,13 @@ __global__ void __launch_bounds__(256, 4) k_trace_primary(DevScene s, VolSet vs,
             const float t_max = vol_of<MULTI>(vs, entry >> kEntryShift).t_max;
             float4 out;
             if (h.orig < 0) {
-                float c = dot(d, L.sky_up);
+                float c = dot(r.d, L.sky_up);
                 out = make_float4(L.sky_a.x + L.sky_b.x * c, L.sky_a.y + L.sky_b.y * c, L.sky_a.z + L.sky_b.z * c,
                                   t_max);
             } else {
                 float3 ng;
                 hit_frame(s, h.k, ng);
-                if (dot(d, ng) > 0.0f) {
+                if (dot(r.d, ng) > 0.0f) {
                     out = make_float4(0.0f, 0.0f, 0.0f, fminf(0.2f * h.t, t_max));
                 } else {
                     front = true;
