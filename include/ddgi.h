@@ -206,7 +206,8 @@ typedef struct {
 /* Allocate a volume: zeroed atlases (Tab. "algtable": uniform
  * initialisation to 0), all probes UNINIT (VIGILANT when state_machine is
  * 0), plus the per-frame ray buffer [P*R] of 16-byte records.  Synchronises
- * the device once.  Errors: INVALID_ARG, OOM. */
+ * the device once.  Errors: INVALID_ARG (a field out of range, or P*R of
+ * 2^31 or more: the ray lists index rays with 32-bit ints), OOM. */
 ddgi_status ddgi_volume_create(const ddgi_volume_desc* desc, ddgi_volume* out);
 void ddgi_volume_destroy(ddgi_volume volume);
 

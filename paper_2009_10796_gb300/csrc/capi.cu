@@ -477,6 +477,8 @@ static ddgi_status check_desc(const ddgi_volume_desc* d) {
         return fail(DDGI_ERR_INVALID_ARG, "offset_limit must be in [0, 0.5)");
     if (d->converge_batches < 0 || d->converge_batches > 64)
         return fail(DDGI_ERR_INVALID_ARG, "converge_batches must be in [0, 64]");
+    if ((int64_t)d->counts[0] * d->counts[1] * d->counts[2] * d->rays_per_probe >= (1LL << 31))
+        return fail(DDGI_ERR_INVALID_ARG, "probes x rays_per_probe must stay below 2^31");
     return DDGI_OK;
 }
 
@@ -1229,9 +1231,12 @@ ddgi_status ddgi_cascade_create(const ddgi_volume_desc* descs, int32_t n, ddgi_c
     if (!out) return fail(DDGI_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!descs || n < 1 || n > kMaxVolumes) return fail(DDGI_ERR_INVALID_ARG, "need 1..8 volume descriptors");
+    int64_t all_rays = 0;   // the lists index rays of all volumes with 32-bit ints
     for (int k = 0; k < n; ++k) {
         ddgi_status s = check_desc(&descs[k]);
         if (s != DDGI_OK) return s;
+        all_rays += (int64_t)descs[k].counts[0] * descs[k].counts[1] * descs[k].counts[2] * descs[k].rays_per_probe;
+        if (all_rays >= (1LL << 31)) return fail(DDGI_ERR_INVALID_ARG, "probes x rays_per_probe must stay below 2^31");
         if (descs[k].optimizer_iters != 0)
             return fail(DDGI_ERR_UNSUPPORTED, "cascades have no probe position optimizer");
         if (descs[k].converge_batches != 0)

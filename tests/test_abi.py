@@ -101,3 +101,21 @@ def test_struct_layouts_match_header(tmp_path):
         assert got[(cname, "size")] == C.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_descriptor_limits_without_gpu(lib):
+    """Descriptor checks run before any device call: the ray lists index
+    rays with 32-bit ints (probes x rays below 2^31), converge batches and
+    optimizer iterations have ranges."""
+    import ctypes as C
+    import paper_2009_10796_gb300 as g
+    import synth
+    from paper_2009_10796_gb300 import api
+    L = g.load()
+    out = C.c_void_p()
+    for kw, msg in [(dict(counts=(2048, 1024, 32), rays_per_probe=64), b"2^31"),
+                    (dict(converge_batches=65), b"converge_batches"),
+                    (dict(optimizer_iters=17), b"optimizer_iters")]:
+        d = api.desc_struct(synth.room_volume(**kw))
+        assert L.ddgi_volume_create(C.byref(d), C.byref(out)) == 1
+        assert msg in L.ddgi_last_error(), (kw, L.ddgi_last_error())
