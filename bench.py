@@ -46,7 +46,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one k_trace_primary launch on this workload,
 # from the ncu capture in profiles/trace_passes_city.md; set to None whenever
 # the kernel changes until it is captured again
-PRIMARY_TRAFFIC_BYTES = None   # DRAM read + write of one k_trace_primary launch (ncu); None until re-captured
+PRIMARY_TRAFFIC_BYTES = 3_437_824 + 1_157_120   # DRAM read + write of one k_trace_primary launch (ncu)
 
 
 def peaks():
