@@ -155,8 +155,7 @@ struct ddgi_volume_s {
     int64_t updates = 0;
     int3 shift{0, 0, 0};
     float4* offsets = nullptr;             // [P] probe offsets (position optimizer)
-    float4* opt_dirs = nullptr;            // [R] rays of an optimizer iteration
-    double* opt_dirs64 = nullptr;
+    float4* opt_dirs = nullptr;            // [3R] rays (and their constants) of an optimizer iteration
     bool uninit_possible = true;           // some probe may still be UNINIT
     float* dyn_boxes = nullptr;            // [DDGI_MAX_DYNAMIC_BOXES][6] extended boxes (device)
     int32_t n_dyn = 0;
@@ -492,7 +491,7 @@ void ddgi_volume_destroy(ddgi_volume v) {
     for (void* p : v->snap_dist) cudaFree(p);
     cudaFree(v->g_irr); cudaFree(v->g_prev);
     cudaFree(v->pack_irr); cudaFree(v->pack_dist); cudaFree(v->inv_irr_r); cudaFree(v->inv_dist_r);
-    cudaFree(v->offsets); cudaFree(v->opt_dirs); cudaFree(v->opt_dirs64); cudaFree(v->dyn_boxes);
+    cudaFree(v->offsets); cudaFree(v->opt_dirs); cudaFree(v->dyn_boxes);
     cudaFree(v->stage);
     cudaFree(v->conv_dirs); cudaFree(v->conv_w_irr); cudaFree(v->conv_inv_irr); cudaFree(v->conv_w_dist);
     cudaFree(v->conv_inv_dist); cudaFree(v->conv_acc_irr); cudaFree(v->conv_acc_dist); cudaFree(v->conv_den);
@@ -547,7 +546,6 @@ ddgi_status ddgi_volume_create(const ddgi_volume_desc* desc, ddgi_volume* out) {
     A((void**)&v->offsets, sizeof(float4) * (size_t)v->P);
     if (desc->optimizer_iters > 0) {
         A((void**)&v->opt_dirs, sizeof(float4) * 3 * v->R);
-        A((void**)&v->opt_dirs64, sizeof(double) * 3 * v->R);
     }
     if (desc->converge_batches > 0) {
         const size_t ti = (size_t)desc->irr_n * desc->irr_n, td = (size_t)desc->dist_n * desc->dist_n;
@@ -731,8 +729,8 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
         StageTimer tm(v, 0, st);
         for (int k = 0; k < d.optimizer_iters; ++k) {
             // iteration k traces the rays of frame + k, as if spread over frames
-            DDGI_CK(launch_frame_dirs(frame_rotation(d.seed, params->frame + k), v->R, v->opt_dirs, v->opt_dirs64,
-                                      st));
+            DDGI_CK(launch_frame_dirs(frame_rotation(d.seed, params->frame + k), v->R, d.irr_n, d.dist_n, v->sf64,
+                                      v->opt_dirs, st));
             DDGI_CK(launch_optimize(s->dev, view, v->opt_dirs, v->R, v->lists, v->counts + 0, sms * 8, st));
         }
         DDGI_CK(launch_classify(s->dev, view, v->dirs, v->R, v->perm, v->lists, v->counts + 0, sms * 8, st));

@@ -210,7 +210,9 @@ cudaError_t launch_build_list_multi(const VolSet& vs, int total, int which, int3
 cudaError_t launch_optimize(const DevScene& s, const VolView& v, const float4* dirs, int R, const int32_t* list,
                             const int32_t* count, int grid, cudaStream_t st);
 // Frame ray directions only (float4 for the trace, double for the weights).
-cudaError_t launch_frame_dirs(const FrameRot& rot, int R, float4* dirs, double* dirs64, cudaStream_t st);
+// The frame directions and ray constants alone (position-optimizer rays).
+cudaError_t launch_frame_dirs(const FrameRot& rot, int R, int irr_n, int dist_n, const double* sf64, float4* dirs,
+                              cudaStream_t st);
 cudaError_t launch_classify(const DevScene& s, const VolView& v, const float4* dirs, int R, const int32_t* perm,
                             const int32_t* list, const int32_t* count, int grid, cudaStream_t st);
 cudaError_t launch_classify_multi(const DevScene& s, const VolSet& vs, const float4* dirs, int R,

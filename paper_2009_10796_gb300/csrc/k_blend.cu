@@ -47,12 +47,6 @@ __device__ __forceinline__ void rotate_dir(const FrameRot& rot, const double sv[
     for (int a = 0; a < 3; ++a) out[a] = rot.m[3 * a] * sv[0] + rot.m[3 * a + 1] * sv[1] + rot.m[3 * a + 2] * sv[2];
 }
 
-__device__ void frame_dir(const FrameRot& rot, int i, int n, double out[3]) {
-    double sv[3];
-    sf_dir(i, n, sv);
-    rotate_dir(rot, sv, out);
-}
-
 // The float ray direction and its packed traversal constants in a
 // direction buffer of 3R float4 (directions, then two constants per ray).
 __device__ __forceinline__ void store_frame_dir(float4* dirs, int R, int i, const double w[3]) {
@@ -80,24 +74,6 @@ __device__ void texel_dir(int t, int n, double v[3]) {
 
 }  // namespace
 
-// The frame's ray directions, once per ray: w_i = R_t sf(i, R) in double
-// precision, rounded to float for the trace and kept in double for the
-// weights.  ROT_DEV: the rotation is read from device memory (per-frame
-// parameters written before a captured graph replays).
-template <bool ROT_DEV>
-__global__ void __launch_bounds__(32) k_frame_dirs(FrameRot rot_arg, const FrameRot* rot_dev, int R, float4* dirs,
-                                                   double* dirs64) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= R) return;
-    const FrameRot rot = ROT_DEV ? *rot_dev : rot_arg;
-    double w[3];
-    frame_dir(rot, i, R, w);
-    store_frame_dir(dirs, R, i, w);
-    dirs64[3 * i] = w[0];
-    dirs64[3 * i + 1] = w[1];
-    dirs64[3 * i + 2] = w[2];
-}
-
 // c^p for c >= 0: repeated squaring when p is a small whole number (the
 // usual power-cosine exponent), pow otherwise.
 __device__ double cos_pow(double c, double p) {
@@ -123,10 +99,11 @@ __global__ void k_sf_table(int R, double* sf64) {
 // One launch of the whole frame setup.  Block b < irr_n^2 handles
 // irradiance texel b, the next dist_n^2 blocks the distance texels, rays
 // strided over the block: each rotates the pattern itself from the sf table
-// (the same double operations as k_frame_dirs, so the same directions),
-// writes its weight row and 1 / row sum.  The remaining blocks write the
-// frame's float directions and ray constants, and the first of them clears
-// n_zero counters.  No block waits on another.
+// (the same double operations as the direction blocks, so the same
+// directions), writes its weight row and 1 / row sum.  The remaining blocks
+// write the frame's float directions and ray constants, and the first of
+// them clears n_zero counters.  No block waits on another; a launch may
+// cover a sub-range of the blocks (first_block).
 template <bool ROT_DEV>
 __global__ void __launch_bounds__(256) k_frame_setup(FrameRot rot_arg, const FrameRot* rot_dev, int R, int irr_n,
                                                      int dist_n, double cos_power,
@@ -643,8 +620,12 @@ cudaError_t launch_converge_finish(const VolView& v, const int32_t* list, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_frame_dirs(const FrameRot& rot, int R, float4* dirs, double* dirs64, cudaStream_t st) {
-    k_frame_dirs<false><<<(R + 31) / 32, 32, 0, st>>>(rot, nullptr, R, dirs, dirs64);
+cudaError_t launch_frame_dirs(const FrameRot& rot, int R, int irr_n, int dist_n, const double* sf64, float4* dirs,
+                              cudaStream_t st) {
+    // the direction blocks of k_frame_setup alone
+    k_frame_setup<false><<<(R + 255) / 256, 256, 0, st>>>(rot, nullptr, R, irr_n, dist_n, 0.0, sf64, dirs, nullptr,
+                                                           nullptr, nullptr, nullptr, nullptr, 0,
+                                                           irr_n * irr_n + dist_n * dist_n);
     return cudaGetLastError();
 }
 

@@ -26,7 +26,7 @@ constexpr int64_t kNaMaxRecords = 1 << 20;    // probes x rays (16 MiB of ray re
 
 static __device__ __align__(256) float4 g_na_records[kNaMaxRecords];
 static __device__ __align__(256) float4 g_na_dirs[3 * kNaMaxRays];   // directions, then ray constants
-static __device__ __align__(256) double g_na_dirs64[3 * kNaMaxRays];   // unrotated ray pattern
+static __device__ __align__(256) double g_na_sf64[3 * kNaMaxRays];   // unrotated ray pattern
 static __device__ __align__(256) float g_na_w_irr[kNaMaxIrrTexels * kNaMaxRays];
 static __device__ __align__(256) float g_na_inv_s_irr[kNaMaxIrrTexels];
 static __device__ __align__(256) float g_na_w_dist[kNaMaxDistTexels * kNaMaxRays];
@@ -38,7 +38,7 @@ static __device__ __align__(256) uint32_t g_na_status[4];
 struct NaScratch {
     float4* records;
     float4* dirs;
-    double* dirs64;
+    double* sf64;
     float* w_irr;
     float* inv_s_irr;
     float* w_dist;
@@ -66,7 +66,7 @@ cudaError_t scratch_for_current_device(NaScratch* out) {
         NaScratch s{};
         if ((e = cudaGetSymbolAddress((void**)&s.records, g_na_records)) != cudaSuccess) return e;
         if ((e = cudaGetSymbolAddress((void**)&s.dirs, g_na_dirs)) != cudaSuccess) return e;
-        if ((e = cudaGetSymbolAddress((void**)&s.dirs64, g_na_dirs64)) != cudaSuccess) return e;
+        if ((e = cudaGetSymbolAddress((void**)&s.sf64, g_na_sf64)) != cudaSuccess) return e;
         if ((e = cudaGetSymbolAddress((void**)&s.w_irr, g_na_w_irr)) != cudaSuccess) return e;
         if ((e = cudaGetSymbolAddress((void**)&s.inv_s_irr, g_na_inv_s_irr)) != cudaSuccess) return e;
         if ((e = cudaGetSymbolAddress((void**)&s.w_dist, g_na_w_dist)) != cudaSuccess) return e;
@@ -186,8 +186,8 @@ extern "C" ddgi_status ddgi_update_noalloc(ddgi_scene scene, const ddgi_volume_d
     // the arrays keep the previous call's contents: counters and status start
     // at zero (the frame setup clears the counters)
     if ((e = cudaMemsetAsync(s.status, 0, sizeof(uint32_t) * 4, st)) != cudaSuccess) return na_fail(e, "clear status");
-    if ((e = launch_sf_table(R, s.dirs64, st)) != cudaSuccess) return na_fail(e, "ray pattern");
-    if ((e = launch_frame_setup(rot, R, d->irr_n, d->dist_n, d->dist_cos_power, s.dirs64, s.dirs, s.w_irr,
+    if ((e = launch_sf_table(R, s.sf64, st)) != cudaSuccess) return na_fail(e, "ray pattern");
+    if ((e = launch_frame_setup(rot, R, d->irr_n, d->dist_n, d->dist_cos_power, s.sf64, s.dirs, s.w_irr,
                                 s.inv_s_irr, s.w_dist, s.inv_s_dist, s.counts, 4, st)) != cudaSuccess)
         return na_fail(e, "frame setup");
     if (d->state_machine) {
