@@ -188,25 +188,31 @@ __global__ void k_build_list_multi(VolSet vs, int total, int which, int32_t* lis
 }
 
 // Tracking-window reset (Sec. 7.2): every probe of a leapfrogged plane gets
-// zero texels and state UNINIT.  One block per plane.
+// zero texels and state UNINIT.  The blocks share each plane's probes; a
+// block zeroes one probe's tiles with consecutive 4-byte stores (every atlas
+// format encodes 0 as zero bits).
 __global__ void k_reset_planes(VolSet vs, const int4* __restrict__ planes, const int32_t* __restrict__ count) {
-    if ((int)blockIdx.x >= *count) return;
-    int4 pl = planes[blockIdx.x];          // (volume, axis, physical plane, 0)
-    const VolView& v = vs.table[pl.x];
-    int cnt[3] = {v.counts.x, v.counts.y, v.counts.z};
-    int a = pl.y, b = (a + 1) % 3, c = (a + 2) % 3;
-    int n_probes = cnt[b] * cnt[c];
-    int ti = v.irr_tile, td = v.dist_tile;
-    for (int q = threadIdx.x; q < n_probes; q += blockDim.x) {
-        int ijk[3];
-        ijk[a] = pl.z;
-        ijk[b] = q % cnt[b];
-        ijk[c] = q / cnt[b];
-        int p = ijk[0] + cnt[0] * (ijk[1] + cnt[1] * ijk[2]);
-        v.states[p] = DDGI_STATE_UNINIT;
-        for (int k = 0; k < ti; ++k) store_irr(v, p, k % (v.irr_n + 2), k / (v.irr_n + 2), f3(0.0f, 0.0f, 0.0f));
-        for (int k = 0; k < td; ++k)
-            store_dist(v, p, k % (v.dist_n + 2), k / (v.dist_n + 2), make_float2(0.0f, 0.0f));
+    const int n_planes = *count;
+    for (int k = 0; k < n_planes; ++k) {
+        const int4 pl = planes[k];          // (volume, axis, physical plane, 0)
+        const VolView& v = vs.table[pl.x];
+        const int cnt[3] = {v.counts.x, v.counts.y, v.counts.z};
+        const int a = pl.y, b = (a + 1) % 3, c = (a + 2) % 3;
+        const int n_probes = cnt[b] * cnt[c];
+        const int irr_words = v.irr_tile * (v.irr_format == DDGI_IRR_FP32 ? 4 : (v.irr_format == DDGI_IRR_FP16 ? 2 : 1));
+        const int dist_words = v.dist_tile * (v.dist_format == DDGI_DIST_FP32 ? 2 : 1);
+        for (int q = blockIdx.x; q < n_probes; q += gridDim.x) {
+            int ijk[3];
+            ijk[a] = pl.z;
+            ijk[b] = q % cnt[b];
+            ijk[c] = q / cnt[b];
+            const int p = ijk[0] + cnt[0] * (ijk[1] + cnt[1] * ijk[2]);
+            if (threadIdx.x == 0) v.states[p] = DDGI_STATE_UNINIT;
+            uint32_t* ti = reinterpret_cast<uint32_t*>(v.irr) + (int64_t)p * irr_words;
+            uint32_t* td = reinterpret_cast<uint32_t*>(v.dist) + (int64_t)p * dist_words;
+            for (int i = threadIdx.x; i < irr_words; i += blockDim.x) ti[i] = 0u;
+            for (int i = threadIdx.x; i < dist_words; i += blockDim.x) td[i] = 0u;
+        }
     }
 }
 
@@ -231,7 +237,11 @@ cudaError_t launch_build_list_multi(const VolSet& vs, int total, int which, int3
 cudaError_t launch_reset_planes(const VolSet& vs, const int4* planes, const int32_t* count, int max_planes,
                                 cudaStream_t st) {
     if (max_planes <= 0) return cudaSuccess;
-    k_reset_planes<<<max_planes, 256, 0, st>>>(vs, planes, count);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    k_reset_planes<<<2 * sms, 256, 0, st>>>(vs, planes, count);
     return cudaGetLastError();
 }
 

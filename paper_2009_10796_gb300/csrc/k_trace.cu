@@ -21,6 +21,9 @@ __global__ void __launch_bounds__(256) k_classify(DevScene s, VolSet vs, const f
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int n = *count;
+    int stack[kStackSize4];
+    WwLane<kStackSize4> w;
+    w.stack = stack;
     for (int q = warp; q < n; q += nwarps) {
         int e = list[q];
         const VolView& v = vol_of<MULTI>(vs, e >> kEntryShift);
@@ -28,13 +31,21 @@ __global__ void __launch_bounds__(256) k_classify(DevScene s, VolSet vs, const f
         float3 o = probe_pos_phys(v, p);
         int bf = 0;
         float dmin = INFINITY;
-        for (int j = lane; j < R; j += 32) {
-            const int i = perm ? __ldg(perm + j) : j;
-            float4 d4 = __ldg(dirs + i);
-            float3 d = f3(d4.x, d4.y, d4.z);
-            RayPre r = ray_pre(o, d);
-            Hit h = traverse<false>(s, r);
-            if (h.orig >= 0) {
+        // the warp's lanes take 32 rays at a time through the warp-cooperative
+        // 4-wide walk (lanes past R take part without a ray)
+        for (int j0 = 0; j0 < R; j0 += 32) {
+            const int j = j0 + lane;
+            const bool valid = j < R;
+            const int i = valid ? (perm ? __ldg(perm + j) : j) : 0;
+            const float4 d4 = __ldg(dirs + i);
+            const float3 d = f3(d4.x, d4.y, d4.z);
+            const RayPre r = ray_pre_packed(o, d, __ldg(dirs + R + 2 * i), __ldg(dirs + R + 2 * i + 1));
+            ww_start(s, w, valid);
+            do {
+                ww4_round<false>(s, r, w);
+            } while (__ballot_sync(0xffffffffu, w.node != kDone) != 0);
+            const Hit& h = w.h;
+            if (valid && h.orig >= 0) {
                 const float4* T = s.tris + 3 * (int64_t)h.k;
                 float4 p0 = __ldg(T), p1 = __ldg(T + 1), p2 = __ldg(T + 2);
                 float3 ng = cross(f3(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z),
