@@ -444,16 +444,30 @@ __global__ void __launch_bounds__(256) k_optimize(DevScene s, VolView v, const f
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int n = *count;
+    const DevScene& sc = s;
+    int stack[kStackSize4];
+    WwLane<kStackSize4> w;
+    w.stack = stack;
     for (int q = warp; q < n; q += nwarps) {
         const int p = list[q];
         const float3 o = probe_pos_phys(v, p);
         int bf = 0;
         unsigned long long cb = ~0ull, cf = ~0ull, ff = 0ull;
-        for (int i = lane; i < R; i += 32) {
-            float4 d4 = __ldg(dirs + i);
-            float3 d = f3(d4.x, d4.y, d4.z);
-            Hit h = traverse<false>(s, ray_pre(o, d));
-            if (h.orig < 0) continue;
+        // 32 rays at a time through the warp-cooperative 4-wide walk (lanes
+        // past R take part without a ray)
+        for (int i0 = 0; i0 < R; i0 += 32) {
+            const int i = i0 + lane;
+            const bool valid = i < R;
+            const int ii = valid ? i : 0;
+            const float4 d4 = __ldg(dirs + ii);
+            const float3 d = f3(d4.x, d4.y, d4.z);
+            const RayPre r = ray_pre_packed(o, d, __ldg(dirs + R + 2 * ii), __ldg(dirs + R + 2 * ii + 1));
+            ww_start(sc, w, valid);
+            do {
+                ww4_round<false>(sc, r, w);
+            } while (__ballot_sync(0xffffffffu, w.node != kDone) != 0);
+            const Hit h = w.h;
+            if (!valid || h.orig < 0) continue;
             const float4* T = s.tris + 3 * (int64_t)h.k;
             float4 p0 = __ldg(T), p1 = __ldg(T + 1), p2 = __ldg(T + 2);
             float3 ng = cross(f3(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z), f3(p2.x - p0.x, p2.y - p0.y, p2.z - p0.z));
