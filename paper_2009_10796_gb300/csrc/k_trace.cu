@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(256) k_classify(DevScene s, VolSet vs, const f
 }
 
 // Fused trace + shade, one thread per probe ray (the allocation-free
-// update's path: it needs no shadow or hit lists).
+// update's path: it needs no shadow or hit lists); rays and shadow rays go
+// through the warp-cooperative 4-wide walk.
 __global__ void __launch_bounds__(128) k_trace_shade(DevScene s, VolView v, Lights L,
                                                      const float4* __restrict__ dirs, int R,
                                                      const int32_t* __restrict__ active,
@@ -77,54 +78,77 @@ __global__ void __launch_bounds__(128) k_trace_shade(DevScene s, VolView v, Ligh
                                                      float4* __restrict__ records) {
     const int64_t total = (int64_t)(*count) * R;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
-        int slot = (int)(idx / R);
-        int i = (int)(idx - (int64_t)slot * R);
+    const int lane = threadIdx.x & 31;
+    const float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
+    const RayPre r_sun = ray_pre(f3(0.0f, 0.0f, 0.0f), tol);
+    int stack[kStackSize4];
+    WwLane<kStackSize4> w;
+    w.stack = stack;
+    // warp-uniform loop: each warp takes 32 consecutive rays through the
+    // warp-cooperative 4-wide walk, then their shadow rays the same way
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
+        const int64_t idx = base + lane;
+        const bool valid = idx < total;
+        const int64_t id = valid ? idx : 0;
+        int slot = (int)(id / R);
+        int i = (int)(id - (int64_t)slot * R);
         int p = __ldg(active + slot);
         float3 o = probe_pos_phys(v, p);
         float4 d4 = __ldg(dirs + i);
         float3 d = f3(d4.x, d4.y, d4.z);
-        RayPre r = ray_pre(o, d);
-        Hit h = traverse<false>(s, r);
+        const RayPre r = ray_pre_packed(o, d, __ldg(dirs + R + 2 * i), __ldg(dirs + R + 2 * i + 1));
+        ww_start(s, w, valid);
+        do {
+            ww4_round<false>(s, r, w);
+        } while (__ballot_sync(0xffffffffu, w.node != kDone) != 0);
+        const Hit h = w.h;
+        // the shadow ray of a sunlit front hit
+        float3 n = f3(0.0f, 0.0f, 1.0f), x = o;
+        float cosl = 0.0f;
+        bool front = false;
+        float3 ng = f3(0.0f, 0.0f, 1.0f);
+        if (valid && h.orig >= 0) {
+            const float4* T = s.tris + 3 * (int64_t)h.k;
+            float4 p0 = __ldg(T), p1 = __ldg(T + 1), p2 = __ldg(T + 2);
+            ng = cross(f3(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z), f3(p2.x - p0.x, p2.y - p0.y, p2.z - p0.z));
+            front = !(dot(d, ng) > 0.0f);
+            n = (1.0f / length(ng)) * ng;
+            x = o + h.t * d;
+            cosl = dot(n, tol);
+        }
+        const bool shadow = front && L.sun_on && cosl > 0.0f;
+        RayPre sr = r_sun;
+        if (shadow) ray_set_origin(sr, x + (1e-4f * (1.0f + length(x))) * n);
+        ww_start(s, w, shadow);
+        do {
+            ww4_round<true>(s, sr, w);
+        } while (__ballot_sync(0xffffffffu, w.node != kDone) != 0);
+        const bool lit = shadow && w.h.orig < 0;
+        if (!valid) continue;
         float4 rec;
         if (h.orig < 0) {
             float c = dot(d, L.sky_up);
             rec = make_float4(L.sky_a.x + L.sky_b.x * c, L.sky_a.y + L.sky_b.y * c,
                               L.sky_a.z + L.sky_b.z * c, v.t_max);
+        } else if (!front) {
+            // back face: radiance 0, depth shortened by 80% (Sec. 4.1)
+            rec = make_float4(0.0f, 0.0f, 0.0f, fminf(0.2f * h.t, v.t_max));
         } else {
-            const float4* T = s.tris + 3 * (int64_t)h.k;
-            float4 p0 = __ldg(T), p1 = __ldg(T + 1), p2 = __ldg(T + 2);
-            float3 ng = cross(f3(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z),
-                              f3(p2.x - p0.x, p2.y - p0.y, p2.z - p0.z));
-            if (dot(d, ng) > 0.0f) {
-                // back face: radiance 0, depth shortened by 80% (Sec. 4.1)
-                rec = make_float4(0.0f, 0.0f, 0.0f, fminf(0.2f * h.t, v.t_max));
-            } else {
-                float3 n = (1.0f / length(ng)) * ng;
-                float3 x = o + h.t * d;
-                int2 at = __ldg(s.attr + h.orig);
-                float4 rho = __ldg(s.albedo + at.x);
-                float3 Le = f3(0.0f, 0.0f, 0.0f);
-                if (at.y >= 0) {
-                    float4 e = __ldg(s.emit + at.y);
-                    Le = f3(e.x, e.y, e.z);
-                }
-                float3 direct = f3(0.0f, 0.0f, 0.0f);
-                float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
-                float cosl = dot(n, tol);
-                if (L.sun_on && cosl > 0.0f) {
-                    float off = 1e-4f * (1.0f + length(x));
-                    RayPre sr = ray_pre(x + off * n, tol);
-                    Hit sh = traverse<true>(s, sr);
-                    if (sh.orig < 0) {
-                        float k = cosl * 0.318309886183790672f;   // 1/pi
-                        direct = f3(L.sun_irr.x * k, L.sun_irr.y * k, L.sun_irr.z * k);
-                    }
-                }
-                float3 M = query_M(v, x, n, f3(-d.x, -d.y, -d.z));
-                rec = make_float4(Le.x + rho.x * (direct.x + M.x), Le.y + rho.y * (direct.y + M.y),
-                                  Le.z + rho.z * (direct.z + M.z), fminf(h.t, v.t_max));
+            int2 at = __ldg(s.attr + h.orig);
+            float4 rho = __ldg(s.albedo + at.x);
+            float3 Le = f3(0.0f, 0.0f, 0.0f);
+            if (at.y >= 0) {
+                float4 e = __ldg(s.emit + at.y);
+                Le = f3(e.x, e.y, e.z);
             }
+            float3 direct = f3(0.0f, 0.0f, 0.0f);
+            if (lit) {
+                float k = cosl * 0.318309886183790672f;   // 1/pi
+                direct = f3(L.sun_irr.x * k, L.sun_irr.y * k, L.sun_irr.z * k);
+            }
+            float3 M = query_M(v, x, n, f3(-d.x, -d.y, -d.z));
+            rec = make_float4(Le.x + rho.x * (direct.x + M.x), Le.y + rho.y * (direct.y + M.y),
+                              Le.z + rho.z * (direct.z + M.z), fminf(h.t, v.t_max));
         }
         records[idx] = rec;
     }
