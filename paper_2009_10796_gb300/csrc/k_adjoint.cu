@@ -172,22 +172,53 @@ __global__ void k_blend_adjoint(VolView v_after, const float* __restrict__ w_irr
 __global__ void k_shade_adjoint(DevScene s, VolView v_before, Lights L, const float4* __restrict__ dirs, int P,
                                 int R, const float4* __restrict__ gL, float* d_emit, float* d_albedo,
                                 float* g_prev, int with_prev) {
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)P * R;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        float4 g4 = gL[idx];
-        if (g4.x == 0.0f && g4.y == 0.0f && g4.z == 0.0f) continue;
-        int p = (int)(idx / R), i = (int)(idx - (int64_t)p * R);
+    const int64_t total = (int64_t)P * R;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
+    const RayPre r_sun = ray_pre(f3(0.0f, 0.0f, 0.0f), tol);
+    int stack[kStackSize4];
+    WwLane<kStackSize4> w;
+    w.stack = stack;
+    // warp-uniform loop: 32 rays per warp through the warp-cooperative 4-wide
+    // walk (rays without a gradient take part without tracing), then their
+    // shadow rays the same way
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
+        const int64_t idx = base + lane;
+        const float4 g4 = idx < total ? gL[idx] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const bool valid = g4.x != 0.0f || g4.y != 0.0f || g4.z != 0.0f;
+        const int64_t id = valid ? idx : 0;
+        int p = (int)(id / R), i = (int)(id - (int64_t)p * R);
         float3 o = probe_pos_phys(v_before, p);
         float4 d4 = __ldg(dirs + i);
         float3 d = f3(d4.x, d4.y, d4.z);
-        Hit h = traverse<false>(s, ray_pre(o, d));
-        if (h.orig < 0) continue;
-        const float4* T = s.tris + 3 * (int64_t)h.k;
-        float4 p0 = __ldg(T), p1 = __ldg(T + 1), p2 = __ldg(T + 2);
-        float3 ng = cross(f3(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z), f3(p2.x - p0.x, p2.y - p0.y, p2.z - p0.z));
-        if (dot(d, ng) > 0.0f) continue;   // back faces carry no radiance
-        float3 n = (1.0f / length(ng)) * ng;
-        float3 x = o + h.t * d;
+        const RayPre r = ray_pre_packed(o, d, __ldg(dirs + R + 2 * i), __ldg(dirs + R + 2 * i + 1));
+        ww_start(s, w, valid);
+        do {
+            ww4_round<false>(s, r, w);
+        } while (__ballot_sync(0xffffffffu, w.node != kDone) != 0);
+        const Hit h = w.h;
+        bool front = false;
+        float3 n = f3(0.0f, 0.0f, 1.0f), x = o;
+        float cosl = 0.0f;
+        if (valid && h.orig >= 0) {
+            const float4* T = s.tris + 3 * (int64_t)h.k;
+            float4 p0 = __ldg(T), p1 = __ldg(T + 1), p2 = __ldg(T + 2);
+            float3 ng = cross(f3(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z), f3(p2.x - p0.x, p2.y - p0.y, p2.z - p0.z));
+            front = !(dot(d, ng) > 0.0f);   // back faces carry no radiance
+            n = (1.0f / length(ng)) * ng;
+            x = o + h.t * d;
+            cosl = dot(n, tol);
+        }
+        const bool shadow = front && L.sun_on && cosl > 0.0f;
+        RayPre sr = r_sun;
+        if (shadow) ray_set_origin(sr, x + (1e-4f * (1.0f + length(x))) * n);
+        ww_start(s, w, shadow);
+        do {
+            ww4_round<true>(s, sr, w);
+        } while (__ballot_sync(0xffffffffu, w.node != kDone) != 0);
+        const bool lit = shadow && w.h.orig < 0;
+        if (!front) continue;
         int2 at = __ldg(s.attr + h.orig);
         if (at.y >= 0) {
             atomicAdd(d_emit + 3 * at.y + 0, g4.x);
@@ -195,15 +226,9 @@ __global__ void k_shade_adjoint(DevScene s, VolView v_before, Lights L, const fl
             atomicAdd(d_emit + 3 * at.y + 2, g4.z);
         }
         float3 direct = f3(0.0f, 0.0f, 0.0f);
-        float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
-        float cosl = dot(n, tol);
-        if (L.sun_on && cosl > 0.0f) {
-            float off = 1e-4f * (1.0f + length(x));
-            Hit sh = traverse<true>(s, ray_pre(x + off * n, tol));
-            if (sh.orig < 0) {
-                float kk = cosl * 0.318309886183790672f;
-                direct = f3(L.sun_irr.x * kk, L.sun_irr.y * kk, L.sun_irr.z * kk);
-            }
+        if (lit) {
+            float kk = cosl * 0.318309886183790672f;
+            direct = f3(L.sun_irr.x * kk, L.sun_irr.y * kk, L.sun_irr.z * kk);
         }
         float3 wo = f3(-d.x, -d.y, -d.z);
         float3 M = query_M(v_before, x, n, wo);
