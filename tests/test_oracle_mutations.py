@@ -10,6 +10,7 @@ import os
 import pytest
 
 import oracle
+import test_oracle_converge as conv
 import test_oracle_pins as pins
 
 BATTERY = [
@@ -34,6 +35,9 @@ BATTERY = [
     pins.test_states_hand_built,
     pins.test_states_backface_fraction_threshold,
     pins.test_cascade_weights_nested,
+    conv.test_converge_uniform_sky_exact_and_states,
+    conv.test_converge_batches_are_distinct_rotations,
+    conv.test_converge_enclosing_sphere_moments,
 ]
 
 MUTATIONS = {
@@ -63,6 +67,10 @@ MUTATIONS = {
     "distance_square_moment": ("mu2 += w * dd * dd;", "mu2 += w * dd;"),
     "tie_break": ("if (tri_intersect(s, k, o, d, &tk, &bk) && tk < best)",
                   "if (tri_intersect(s, k, o, d, &tk, &bk) && tk > 0.0 && (bi < 0 || tk > best))"),
+    "converge_one_rotation": ("0xD1B54A32D192ED03ULL * (uint64_t)(b + 1)", "0xD1B54A32D192ED03ULL * (uint64_t)1"),
+    "converge_unencoded": ("e[k] = pow(num_i[4 * t + k] / num_i[4 * t + 3], 1.0 / v->gamma);",
+                           "e[k] = num_i[4 * t + k] / num_i[4 * t + 3];"),
+    "converge_no_advance": ("states[p] = advanced(states[p]);", "(void)0;"),
 }
 
 
