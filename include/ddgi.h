@@ -406,6 +406,16 @@ ddgi_status ddgi_cascade_get_buffer(ddgi_cascade cascade, int32_t vol, int32_t w
                                     size_t bytes, ddgi_stream stream);
 ddgi_status ddgi_cascade_get_window(ddgi_cascade cascade, int32_t vol, double origin[3], int32_t shift[3]);
 
+/* Ray records of the last cascade update (Sec. 2.3 per-ray radiance and
+ * distance, every volume's active probes in one list): records_dev
+ * [total_probes * R][4] float (r, g, b, d) in active-list order,
+ * entries_dev [total_probes] int32 with entry = (volume index << 24) | the
+ * probe's stored index in that volume, and the active count written to
+ * *n_active (host; synchronises the stream).  INVALID_ARG before the first
+ * update or on a NULL argument. */
+ddgi_status ddgi_cascade_get_ray_records(ddgi_cascade cascade, float* records_dev, int32_t* entries_dev,
+                                         int64_t* n_active, ddgi_stream stream);
+
 /* Launch shapes: trace kernels' blocks per SM (1..32) and the SIMT blend's
  * probes per CTA (4, 8 or 16).  ddgi_cascade_autotune times the update under
  * each candidate and keeps the fastest, caching the choice in a JSON file at

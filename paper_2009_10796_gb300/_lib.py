@@ -99,6 +99,7 @@ SIGNATURES = {
     "ddgi_cascade_query": (C.c_int, [_vp, _vp, _vp, C.c_int64, F3, _vp, _vp]),
     "ddgi_cascade_get_buffer": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.c_size_t, _vp]),
     "ddgi_cascade_get_window": (C.c_int, [_vp, C.c_int32, C.c_double * 3, C.c_int32 * 3]),
+    "ddgi_cascade_get_ray_records": (C.c_int, [_vp, _vp, _vp, C.POINTER(C.c_int64), _vp]),
     "ddgi_cascade_set_tuning": (C.c_int, [_vp, C.c_int32, C.c_int32]),
     "ddgi_cascade_get_tuning": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "ddgi_cascade_autotune": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.POINTER(CascadeParams), C.c_char_p,

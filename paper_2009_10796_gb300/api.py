@@ -419,6 +419,19 @@ class Cascade:
         check(load().ddgi_cascade_get_window(self.handle, k, o, sh))
         return list(o), list(sh)
 
+    def ray_records(self, stream=None):
+        """(records [n_active, R, 4], volume index [n_active], stored probe
+        index [n_active]) of the last update, in active-list order."""
+        total = sum(d.counts[0] * d.counts[1] * d.counts[2] for d in self.descs)
+        R = self.descs[0].rays_per_probe
+        rec = torch.empty((total * R, 4), dtype=torch.float32, device="cuda")
+        ent = torch.empty(total, dtype=torch.int32, device="cuda")
+        n = C.c_int64()
+        check(load().ddgi_cascade_get_ray_records(self.handle, _ptr(rec), _ptr(ent), C.byref(n), _stream(stream)))
+        k = n.value
+        ent = ent[:k]
+        return rec[: k * R].view(k, R, 4), ent >> 24, ent & ((1 << 24) - 1)
+
     def set_tuning(self, trace_blocks_per_sm, blend_probes_per_cta):
         check(load().ddgi_cascade_set_tuning(self.handle, int(trace_blocks_per_sm), int(blend_probes_per_cta)))
 

@@ -1429,6 +1429,24 @@ ddgi_status ddgi_cascade_get_buffer(ddgi_cascade c, int32_t vol, int32_t which, 
     return DDGI_OK;
 }
 
+ddgi_status ddgi_cascade_get_ray_records(ddgi_cascade c, float* records_dev, int32_t* entries_dev,
+                                         int64_t* n_active, ddgi_stream stream) {
+    if (!c || !records_dev || !entries_dev || !n_active) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (c->updates == 0) return fail(DDGI_ERR_INVALID_ARG, "no update has run on this cascade");
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t cnt = 0;
+    DDGI_CK(cudaMemcpyAsync(&cnt, c->counts + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    DDGI_CK(cudaStreamSynchronize(st));
+    *n_active = cnt;
+    if (cnt > 0) {
+        DDGI_CK(cudaMemcpyAsync(records_dev, c->records, sizeof(float4) * (size_t)cnt * c->R,
+                                cudaMemcpyDeviceToDevice, st));
+        DDGI_CK(cudaMemcpyAsync(entries_dev, c->lists + c->total, sizeof(int32_t) * (size_t)cnt,
+                                cudaMemcpyDeviceToDevice, st));
+    }
+    return DDGI_OK;
+}
+
 ddgi_status ddgi_cascade_get_window(ddgi_cascade c, int32_t vol, double origin[3], int32_t shift[3]) {
     if (!c || !origin || !shift) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
     if (vol < 0 || vol >= c->n) return fail(DDGI_ERR_INVALID_ARG, "volume index out of range");

@@ -1,6 +1,7 @@
 """Cascades with a camera-tracking window (Sec. 7.2, 7.3) against the oracle."""
 import json
 import os
+import types
 
 import numpy as np
 import pytest
@@ -8,7 +9,7 @@ import torch
 
 import oracle
 import synth
-from parity import REL, rel_err, to_dev
+from parity import REL, compare_rays, rel_err, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -115,3 +116,87 @@ def test_cascade_autotune_and_cache(g, tmp_path):
     assert D.tuning() == t
     with pytest.raises(g.DDGIError):
         D.set_tuning(0, 8)
+
+
+def test_terrain_cascades_full_size_frame0_sampled(g):
+    """The batched-cascade workload at full size and in the bench's launch
+    configuration (four 32^3 tracking volumes at 1 / 2 / 4 / 8 m, 288 rays,
+    1,048,568 triangles, the frame as one CUDA graph, 8 trace blocks per SM,
+    16 probes per blend CTA), frame 0: for a seeded sample of probes of every
+    volume the states are bit-exact and the per-ray records and texels match
+    the oracle's one-step update of that sample (rays that graze an edge
+    within FP32 rounding are counted and their probes skipped); then the
+    cascade query at seeded surface points around the camera, across the
+    fall-off between volumes, matches the oracle's query over the GPU's own
+    atlases."""
+    sc = synth.terrain_scene()
+    L = synth.city_lights()
+    descs = synth.terrain_cascades()
+    S = g.Scene.from_arrays(sc)
+    C = g.Cascade(descs)
+    C.set_tuning(8, 16)
+    cam = synth.terrain_camera_path(0)
+    C.update(S, L, 0, cam, use_graph=True)
+    torch.cuda.synchronize()
+    C.poll_status()
+    rec, vol_of, probe_of = C.ray_records()
+    rec = rec.cpu().numpy().astype(np.float64)
+    vol_of = vol_of.cpu().numpy()
+    probe_of = probe_of.cpu().numpy()
+    gst = [C.states(k).cpu().numpy() for k in range(C.n)]
+    gi = [C.irr_atlas(k).cpu().numpy().astype(np.float64) for k in range(C.n)]
+    gd = [C.dist_atlas(k).cpu().numpy().astype(np.float64) for k in range(C.n)]
+
+    vols = [oracle.make_volume(d) for d in descs]
+    ost = [oracle.new_state(d) for d in descs]
+    for k, d in enumerate(descs):
+        oracle.tracking_scroll(vols[k], cam, *ost[k])
+        lo, hi = _track_box(d, cam)
+        vols[k].blend_lo[:] = list(lo)
+        vols[k].blend_hi[:] = list(hi)
+        origin, shift = C.window(k)
+        assert np.allclose(origin, list(vols[k].origin), atol=1e-12)
+        assert np.array_equal(np.mod(shift, d.counts), np.mod(list(vols[k].shift), d.counts))
+    rng = np.random.default_rng(2025)
+    subsets = []
+    for k, d in enumerate(descs):
+        act = probe_of[vol_of == k]
+        assert len(act) > 0, f"volume {k} has no active probe"
+        pick = np.concatenate([rng.choice(d.n_probes, 2, replace=False), rng.choice(act, 2, replace=False)])
+        subsets.append(np.unique(pick).astype(np.int64))
+    rays = oracle.update_cascade(oracle.SceneHandle(sc), L, vols, 0, [o[0] for o in ost], [o[1] for o in ost],
+                                 [o[2] for o in ost], subsets=subsets, want_rays=True)
+    where = {(int(v), int(p)): i for i, (v, p) in enumerate(zip(vol_of, probe_of))}
+    flagged = checked = 0
+    worst_i = worst_d = 0.0
+    for k in range(C.n):
+        st, irr, dist = ost[k]
+        sub = subsets[k]
+        assert np.array_equal(gst[k][sub], st[sub]), f"sampled states differ, volume {k}"
+        for q, p in enumerate(sub):
+            if st[p] != oracle.VIGILANT:
+                continue
+            bad, _ = compare_rays(rec[where[(k, int(p))]][None], np.array([0]), rays[k][q][None])
+            flagged += int(bad.sum())
+            if bad.any():
+                continue
+            checked += 1
+            worst_i = max(worst_i, float(rel_err(gi[k][p], irr[p]).max()))
+            worst_d = max(worst_d, float(rel_err(gd[k][p], dist[p]).max()))
+    print(f"[terrain cascade] sampled {sum(len(x) for x in subsets)} probes, {checked} active compared, "
+          f"flagged rays {flagged}, irr max rel {worst_i:.2e}, dist max rel {worst_d:.2e}")
+    assert checked >= 6 and flagged <= 2
+    assert worst_i <= REL and worst_d <= REL
+
+    # query around the camera: the densest window's fall-off and the next volume
+    lo = cam - np.array([22.0, 40.0, 22.0])
+    hi = cam + np.array([22.0, 10.0, 22.0])
+    ctr = sc.verts[sc.tris].mean(axis=1)
+    near = np.all((ctr >= lo) & (ctr <= hi), axis=1)
+    pts, nrm = synth.surface_points(types.SimpleNamespace(verts=sc.verts, tris=sc.tris[near]), 4096, seed=3004)
+    pts, nrm = synth.f32(pts), synth.f32(nrm)   # the oracle sees the GPU's FP32 inputs
+    E_ref = oracle.query_cascade(vols, gst, gi, gd, pts, nrm, cam)
+    E = C.query(to_dev(pts), to_dev(nrm), cam).cpu().numpy()
+    e = rel_err(E, E_ref).max(-1)
+    print(f"[terrain cascade] query {len(e)} points, max rel {e.max():.2e}, over 1e-4: {int((e > REL).sum())}")
+    assert np.mean(e <= REL) >= 0.999
