@@ -82,3 +82,58 @@ def test_adam_recovers_materials(g):
     print(f"[adjoint] adam: loss {losses[0]:.3e} -> {losses[-1]:.3e}, emitter error "
           f"{float((emit - true_em).abs().max()):.3f}")
     assert losses[-1] < 0.01 * losses[0]
+
+
+def test_interior_full_size_gradient_properties(g):
+    """The differentiation workload at full size and as the bench runs it
+    (2,048 probes x 128 rays, 192,140 triangles, 257 objects, 64 emitters, 1M
+    query points, two frames from a zero atlas, gamma 1, no sun or sky), with
+    checks that hold at any size, for the loss sum(G * E), G > 0:
+    (1) lit by its emitters alone, E is positively homogeneous of degree 1 in
+    the emitter radiances (frame-0 texels, the frame-1 bounce through them,
+    the frame-1 texels and the query all scale with them; no weight depends
+    on radiance), so Euler's theorem gives, per channel c,
+    sum_k L_e[k, c] dloss/dL_e[k, c] = sum_i G[i, c] E[i, c];
+    (2) E is smooth in the albedos (they enter affinely before the query), so
+    the albedo gradient along a positive seeded direction matches the central
+    difference of the forward, summed in FP64."""
+    sc, truth_alb, truth_em = synth.interior_scene()
+    L = synth.Lights()
+    S = g.Scene.from_arrays(sc)
+    V = g.Volume(synth.interior_volume())
+    pts, nrm = synth.surface_points(sc, 1_000_000, seed=3005)
+    P = to_dev(pts)
+    N_ = to_dev(nrm)
+    cam = np.array([0.0, 10.0, 0.0])
+    rng = synth.Rng(4006)
+    G = rng.uniform(3 * len(pts), 0.5, 1.5).reshape(-1, 3)
+    Gd = to_dev(G)
+    albedo = torch.tensor(truth_alb, dtype=torch.float32, device="cuda", requires_grad=True)
+    emit = torch.tensor(truth_em, dtype=torch.float32, device="cuda", requires_grad=True)
+    E = g.IrradianceField.apply(albedo, emit, V, S, L, P, N_, cam, 0, 2)
+    (E * Gd).sum().backward()
+    E = E.detach().cpu().numpy().astype(np.float64)
+    g_em = emit.grad.cpu().numpy().astype(np.float64)
+    g_al = albedo.grad.cpu().numpy().astype(np.float64)
+    Gf = Gd.cpu().numpy().astype(np.float64)
+    lhs = (truth_em.astype(np.float32).astype(np.float64) * g_em).sum(0)
+    rhs = (Gf * E).sum(0)
+    e_euler = np.abs(lhs - rhs) / np.abs(rhs)
+    print(f"[adjoint full size] Euler: lhs {lhs}, rhs {rhs}, rel {e_euler.max():.2e}")
+    assert np.all(rhs > 0) and e_euler.max() <= 1e-3
+
+    delta = rng.uniform(truth_alb.size, 0.0, 1.0).reshape(truth_alb.shape)
+    h = 0.01
+
+    def loss(a):
+        with torch.no_grad():
+            Ea = g.IrradianceField.apply(torch.tensor(a, dtype=torch.float32, device="cuda"), emit.detach(), V, S,
+                                         L, P, N_, cam, 0, 2)
+        return float((Gf * Ea.cpu().numpy().astype(np.float64)).sum())
+
+    a0 = truth_alb.astype(np.float32).astype(np.float64)
+    fd = (loss(a0 + h * delta) - loss(a0 - h * delta)) / (2 * h)
+    ad = float((g_al * delta.astype(np.float32).astype(np.float64)).sum())
+    e_fd = abs(ad - fd) / abs(fd)
+    print(f"[adjoint full size] albedo direction: adjoint {ad:.6e}, central difference {fd:.6e}, rel {e_fd:.2e}")
+    assert fd > 0 and e_fd <= 1e-3
