@@ -88,3 +88,52 @@ def run_oracle(sc, lights, desc, frames, subset=None):
     for f in frames:
         rays.append(oracle.update(h, lights, desc, f, st, irr, dist, subset=subset, want_rays=True))
     return st, irr, dist, rays
+
+
+def lit_query_sample(sc, desc, seed, n_cells=4, per_cell=16, min_active=2, batch=16):
+    """Seeded surface points for a volume query that the oracle can check
+    with a one-step update of few probes.  Cells are taken in order of how
+    many points they hold; in batches, the oracle classifies (frame 0) the
+    eight cage probes of each, and the first `n_cells` cells with at least
+    `min_active` active cage probes are kept (in the dense city most surface
+    points lie inside other boxes, where every cage probe is Off), so the
+    query has light to interpolate; `per_cell` points each.  Returns
+    (points, normals, the 4x4x4 probes around every kept cell), points and
+    normals rounded to FP32."""
+    lo = np.asarray(desc.origin) + 1.0
+    hi = np.asarray(desc.origin) + (np.asarray(desc.counts) - 1) * np.asarray(desc.spacing) - 1.0
+    pts, nrm = synth.surface_points(sc, 20000, seed=seed, region_lo=lo, region_hi=hi)
+    cell = np.floor((pts - np.asarray(desc.origin)) / np.asarray(desc.spacing)).astype(int)
+    cx, cy, cz = desc.counts
+    key = cell[:, 0] + cx * (cell[:, 1] + cy * cell[:, 2])
+    uniq, counts = np.unique(key, return_counts=True)
+    order = uniq[np.argsort(-counts, kind="stable")]
+    corners = np.array([[a & 1, (a >> 1) & 1, (a >> 2) & 1] for a in range(8)])
+    h = oracle.SceneHandle(sc)
+    st, _, _ = oracle.new_state(desc)
+    kept = []
+    for b0 in range(0, len(order), batch):
+        cand = order[b0:b0 + batch]
+        cages = []
+        for c in cand:
+            base = np.array([c % cx, (c // cx) % cy, c // (cx * cy)])
+            q = base + corners
+            cages.append(q[:, 0] + cx * (q[:, 1] + cy * q[:, 2]))
+        ids = np.unique(np.concatenate(cages))
+        ids = ids[st[ids] == oracle.UNINIT]
+        if len(ids):
+            oracle.classify(h, desc, 0, ids, st)
+        active = (st == oracle.NEWLY_VIGILANT) | (st == oracle.VIGILANT)
+        kept += [c for c, cage in zip(cand, cages) if active[cage].sum() >= min_active]
+        if len(kept) >= n_cells:
+            break
+    kept = kept[:n_cells]
+    assert len(kept) == n_cells, "too few lit cells"
+    sel = np.concatenate([np.nonzero(key == c)[0][:per_cell] for c in kept])
+    need = set()
+    for c in cell[sel]:
+        for i in range(max(0, c[0] - 1), min(cx, c[0] + 3)):
+            for j in range(max(0, c[1] - 1), min(cy, c[1] + 3)):
+                for k in range(max(0, c[2] - 1), min(cz, c[2] + 3)):
+                    need.add(i + cx * (j + cy * k))
+    return synth.f32(pts[sel]), synth.f32(nrm[sel]), np.array(sorted(need))

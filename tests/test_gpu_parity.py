@@ -5,7 +5,7 @@ import torch
 
 import oracle
 import synth
-from parity import (REL, compare_rays, gpu_rays_by_probe, masked_texels, rel_err, run_oracle,
+from parity import (REL, compare_rays, gpu_rays_by_probe, lit_query_sample, masked_texels, rel_err, run_oracle,
                     to_dev)
 
 pytestmark = pytest.mark.gpu
@@ -230,33 +230,17 @@ def test_city_frame0_sampled_probes(g, city):
 
 def test_city_query_sampled_points(g, city):
     sc, desc, L, S, V = city
-    lo = np.asarray(desc.origin) + 1.0
-    hi = np.asarray(desc.origin) + (np.asarray(desc.counts) - 1) * np.asarray(desc.spacing) - 1.0
-    pts, nrm = synth.surface_points(sc, 20000, seed=3002, region_lo=lo, region_hi=hi)
-    cell = np.floor((pts - np.asarray(desc.origin)) / np.asarray(desc.spacing)).astype(int)
-    key = cell[:, 0] + 1000 * (cell[:, 1] + 1000 * cell[:, 2])
-    uniq, counts = np.unique(key, return_counts=True)
-    chosen = uniq[np.argsort(-counts)[:4]]
-    sel = np.concatenate([np.nonzero(key == c)[0][:16] for c in chosen])
-    pts, nrm = pts[sel], nrm[sel]
+    pts, nrm, subset = lit_query_sample(sc, desc, 3002)
     cam = np.array([0.0, 12.0, -28.0])
-    cx, cy, cz = desc.counts
-    need = set()
-    # the biased point can leave the cell by less than one spacing: update the
-    # 4x4x4 probes around each chosen cell
-    for c in cell[sel]:
-        for i in range(max(0, c[0] - 1), min(cx, c[0] + 3)):
-            for j in range(max(0, c[1] - 1), min(cy, c[1] + 3)):
-                for k in range(max(0, c[2] - 1), min(cz, c[2] + 3)):
-                    need.add(i + cx * (j + cy * k))
-    subset = np.array(sorted(need))
     st, irr, dist = oracle.new_state(desc)
     oracle.update(oracle.SceneHandle(sc), L, desc, 0, st, irr, dist, subset=subset)
     E_ref = oracle.query(desc, st, irr, dist, pts, nrm, cam)
     E = V.query(to_dev(pts), to_dev(nrm), cam).cpu().numpy()
     e = rel_err(E, E_ref).max(-1)
-    _report("city query", points=len(pts), probes=len(subset), max_rel=float(e.max()),
+    lit = float(np.mean(np.any(E_ref > 0, axis=1)))
+    _report("city query", points=len(pts), probes=len(subset), lit=lit, max_rel=float(e.max()),
             over=int((e > REL).sum()))
+    assert lit >= 0.9
     assert np.mean(e <= REL) >= 0.95
     assert np.median(e) <= REL
 

@@ -11,7 +11,7 @@ import torch
 
 import oracle
 import synth
-from parity import REL, rel_err, run_oracle, to_dev
+from parity import REL, compare_rays, gpu_rays_by_probe, lit_query_sample, rel_err, run_oracle, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -172,3 +172,93 @@ def test_tensor_core_blend_matches_fp32_at_scale(g, mode):
         assert ei.max() <= 1e-3
     else:
         assert ei.max() <= 2e-3 and np.quantile(ei, 0.999) <= 1e-3
+
+
+# ------------------------------------------- city scale against the oracle
+
+@pytest.fixture(scope="module")
+def city_ref(g):
+    """The 16,384-probe city workload at frame 0: the oracle's one-step update
+    of a seeded probe sample (24 seeded + 12 active probes) and of the 4x4x4
+    probes around four lit query cells (seeded surface points)."""
+    sc = synth.city_scene()
+    desc = synth.city_volume()
+    L = synth.city_lights()
+    S = g.Scene.from_arrays(sc)
+    A = g.Volume(desc)
+    A.update(S, L, 0)
+    torch.cuda.synchronize()
+    states = A.states().cpu().numpy()
+    rec, ids = gpu_rays_by_probe(A)
+    rng = np.random.default_rng(124)
+    act = np.nonzero(states == oracle.VIGILANT)[0]
+    sample = np.unique(np.concatenate([rng.choice(desc.n_probes, 24, replace=False),
+                                       rng.choice(act, 12, replace=False)]))
+    pts, nrm, cages = lit_query_sample(sc, desc, 3012)
+    subset = np.union1d(sample, cages)
+    st, irr, dist = oracle.new_state(desc)
+    rays = oracle.update(oracle.SceneHandle(sc), L, desc, 0, st, irr, dist, subset=subset, want_rays=True)
+    assert np.array_equal(states[subset], st[subset]), "sampled states differ"
+    # frame-0 rays do not depend on the atlas formats: probes with a ray that
+    # grazes an edge within FP32 rounding are left out of every comparison
+    pos_of = {int(p): k for k, p in enumerate(ids)}
+    row = {int(p): q for q, p in enumerate(subset)}
+    clean = []
+    for p in sample:
+        if st[p] != oracle.VIGILANT:
+            continue
+        bad, _ = compare_rays(rec[pos_of[int(p)]][None], np.array([0]), rays[row[int(p)]][None])
+        if not bad.any():
+            clean.append(int(p))
+    cam = np.array([0.0, 12.0, -28.0])
+    E_ref = oracle.query(desc, st, irr, dist, pts, nrm, cam)
+    return sc, desc, L, S, np.array(clean), irr, dist, pts, nrm, cam, E_ref
+
+
+# (atlas formats, blend precision, stored-domain bounds for irradiance and
+# distance texels, median bound for queries); the query raises the stored
+# value to the power gamma / 2 and squares the normalised sum, so it carries
+# 5x the stored relative error: its bound is 5x the irradiance texels' bound
+_CITY_VARIANTS = {
+    "fp16_storage": ("IRR_FP16", "DIST_FP16", "BLEND_FP32", 2.0 ** -11 + REL, 2.0 ** -11 + REL,
+                     5 * (2.0 ** -11 + REL)),
+    "rgb9e5_storage": ("IRR_RGB9E5", "DIST_FP32", "BLEND_FP32", None, REL, 5 * 2.0 ** -9),
+    "tf32_blend": ("IRR_FP32", "DIST_FP32", "BLEND_TF32", 1e-3, 1e-3, 5e-3),
+    "bf16_blend": ("IRR_FP32", "DIST_FP32", "BLEND_BF16", 2e-3, 1e-3, 1e-2),
+}
+
+
+@pytest.mark.parametrize("variant", sorted(_CITY_VARIANTS))
+def test_city_precision_variants_against_oracle(g, city_ref, variant):
+    """The precision configuration: the 16,384-probe city volume with reduced
+    atlas storage or the tensor-core blend; per-texel error of the sampled
+    active probes and per-pixel query error against the FP64 oracle."""
+    sc, desc, L, S, clean, irr, dist, pts, nrm, cam, E_ref = city_ref
+    fi, fd, prec, tol_i, tol_d, tol_q = _CITY_VARIANTS[variant]
+    V = g.Volume(desc, irr_format=getattr(g, fi), dist_format=getattr(g, fd))
+    V.update(S, L, 0, precision=getattr(g, prec))
+    torch.cuda.synchronize()
+    assert len(clean) >= 6
+    if fi == "IRR_RGB9E5":
+        gi = _decode_rgb9e5(V.irr_atlas().cpu().numpy())[clean]
+        ref = irr[clean]
+        mx = np.abs(ref).max(-1, keepdims=True)
+        bound = 2.0 ** -9 * mx + REL * np.maximum(mx, 1e-3 * np.abs(ref).max())
+        ei = float(np.max(np.abs(gi - ref) / np.maximum(bound, 1e-30)))
+        ok_i = ei <= 1.0
+        what_i = f"err / bound {ei:.3f}"
+    else:
+        gi = V.irr_atlas().cpu().numpy().astype(np.float64)[clean]
+        ei = max(float(rel_err(gi[k], irr[p]).max()) for k, p in enumerate(clean))
+        ok_i = ei <= tol_i
+        what_i = f"max rel {ei:.2e}"
+    gd = V.dist_atlas().cpu().numpy().astype(np.float64)[clean]
+    ed = max(float(rel_err(gd[k], dist[p]).max()) for k, p in enumerate(clean))
+    E = V.query(to_dev(pts), to_dev(nrm), cam).cpu().numpy()
+    eq = rel_err(E, E_ref).max(-1)
+    lit = float(np.mean(np.any(E_ref > 0, axis=1)))
+    print(f"[precision city] {variant}: {len(clean)} probes, irr {what_i}, dist max rel {ed:.2e}; "
+          f"{len(eq)} queries ({lit:.0%} lit), median rel {np.median(eq):.2e}, max {eq.max():.2e}")
+    assert ok_i and ed <= tol_d
+    assert lit >= 0.9
+    assert np.median(eq) <= tol_q
