@@ -1209,7 +1209,7 @@ ddgi_status cascade_enqueue(ddgi_cascade_s* c, const DevScene& sc, const Lights&
     DDGI_CK(launch_build_list_multi(vs, (int)c->total, 1, c->lists + c->total, c->counts + 1, st));
     DDGI_CK(launch_trace_wavefront_multi(sc, vs, L, c->dirs, c->R, c->perm, c->lists + c->total, c->counts + 1,
                                          c->records, c->shadow_list, c->hit_list, c->shadow_count, sms * c->trace_mult,
-                                         st));
+                                         st, query_fast_view(c->h_params[slot]->views[0])));
     if (tensor)
         DDGI_CK(launch_blend_tc_set(vs, true, bp, precision == DDGI_BLEND_BF16, c->pack_irr, c->pack_dist,
                                     c->inv_irr_r, c->inv_dist_r, c->records, c->lists + c->total, c->counts + 1,

@@ -93,6 +93,14 @@ inline void set_view_divisors(VolView& w) {
     w.div_xy = make_fast_div((uint32_t)w.counts.x * (uint32_t)w.counts.y);
 }
 
+// Views the specialised (FAST) probe query serves: FP32 atlases, gamma 5 and
+// no probe offsets; its kernels skip the per-probe format, gamma and offset
+// tests and otherwise compute the same operations in the same order.
+inline bool query_fast_view(const VolView& w) {
+    return w.irr_format == DDGI_IRR_FP32 && w.dist_format == DDGI_DIST_FP32 && w.half_gamma == 2.5f &&
+           w.offsets == nullptr;
+}
+
 // Largest BVH leaf (triangles); the traversal packs a leaf's first triangle
 // and count - 1 into one int (kLeafBits bits of count), so scenes stay below
 // 2^(31 - kLeafBits) triangles.
@@ -247,7 +255,8 @@ cudaError_t launch_trace_count(const DevScene& s, const VolView& v, const Lights
 cudaError_t launch_trace_wavefront_multi(const DevScene& s, const VolSet& vs, const Lights& L,
                                          const float4* dirs, int R, const int32_t* perm, const int32_t* active,
                                          const int32_t* count, float4* records, int32_t* shadow_list,
-                                         int32_t* hit_list, int32_t* shadow_count, int grid, cudaStream_t st);
+                                         int32_t* hit_list, int32_t* shadow_count, int grid, cudaStream_t st,
+                                         bool fast_query);
 // Morton order of the octahedral positions of the unrotated spherical-
 // Fibonacci directions (host; a rotation keeps neighbouring directions together)
 std::vector<int32_t> ray_order_morton(int R);

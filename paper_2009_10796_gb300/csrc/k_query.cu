@@ -10,7 +10,7 @@ namespace ddgi {
 // for page-locked host memory written across the host link; otherwise each
 // thread stores its own three floats (device memory).
 constexpr int kQueryThreads = 256;
-template <bool STAGE_OUT>
+template <bool STAGE_OUT, bool FAST>
 __global__ void __launch_bounds__(kQueryThreads) k_query(VolView v, const float* __restrict__ pos,
                                                          const float* __restrict__ nrm, int64_t n, float3 cam,
                                                          float* __restrict__ out) {
@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(VolView v, const float*
                 float3 wo = cam - x;
                 float l = length(wo);
                 wo = l < 1e-6f ? nn : (1.0f / l) * wo;
-                float3 M = query_M(v, x, nn, wo);
+                float3 M = query_M<FAST>(v, x, nn, wo);
                 const float pi = 3.14159265358979323846f;
                 E = f3(pi * M.x, pi * M.y, pi * M.z);
             }
@@ -250,10 +250,15 @@ cudaError_t launch_query(const VolView& v, const float* pos, const float* nrm, i
     if (n == 0) return cudaSuccess;
     int64_t blocks = (n + kQueryThreads - 1) / kQueryThreads;
     int grid = (int)(blocks < 1048576 ? blocks : 1048576);
-    if (out_host)
-        k_query<true><<<grid, kQueryThreads, 0, st>>>(v, pos, nrm, n, camera, out);
+    const bool fast = query_fast_view(v);
+    if (out_host && fast)
+        k_query<true, true><<<grid, kQueryThreads, 0, st>>>(v, pos, nrm, n, camera, out);
+    else if (out_host)
+        k_query<true, false><<<grid, kQueryThreads, 0, st>>>(v, pos, nrm, n, camera, out);
+    else if (fast)
+        k_query<false, true><<<grid, kQueryThreads, 0, st>>>(v, pos, nrm, n, camera, out);
     else
-        k_query<false><<<grid, kQueryThreads, 0, st>>>(v, pos, nrm, n, camera, out);
+        k_query<false, false><<<grid, kQueryThreads, 0, st>>>(v, pos, nrm, n, camera, out);
     return cudaGetLastError();
 }
 

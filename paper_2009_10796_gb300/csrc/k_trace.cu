@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolSet vs, Lig
 
 // Shading of the front hits (Sec. 2.3 ray radiance, multi-bounce through the
 // previous frame's probes), one thread per entry of the compacted hit list.
-template <bool MULTI>
+template <bool MULTI, bool FAST>
 __global__ void __launch_bounds__(256, 4) k_shade(DevScene s, VolSet vs, Lights L, const float4* __restrict__ dirs,
                                                int R, FastDiv dR, const int32_t* __restrict__ active,
                                                const int32_t* __restrict__ hit_list,
@@ -385,8 +385,8 @@ __global__ void __launch_bounds__(256, 4) k_shade(DevScene s, VolSet vs, Lights 
         const float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
         const float kk = hr.z != 0.0f ? dot(n, tol) * 0.318309886183790672f : 0.0f;   // 1/pi
         const int orig = __float_as_int(__ldg(&s.tris[3 * (int64_t)k].w));
-        float3 M = MULTI ? cascade_M(vs.table, vs.n, x, n, f3(-d.x, -d.y, -d.z))
-                         : query_M(v, x, n, f3(-d.x, -d.y, -d.z));
+        float3 M = MULTI ? cascade_M<FAST>(vs.table, vs.n, x, n, f3(-d.x, -d.y, -d.z))
+                         : query_M<FAST>(v, x, n, f3(-d.x, -d.y, -d.z));
         int2 at = __ldg(s.attr + orig);
         float4 rho = __ldg(s.albedo + at.x);
         float3 Le = f3(0.0f, 0.0f, 0.0f);
@@ -571,7 +571,7 @@ template <bool MULTI>
 static cudaError_t trace_wavefront(const DevScene& s, const VolSet& vs, const Lights& L, const float4* dirs, int R,
                                    const int32_t* perm, const int32_t* active, const int32_t* count,
                                    float4* records, int32_t* shadow_list, int32_t* hit_list, int32_t* shadow_count,
-                                   int grid, cudaStream_t st, cudaEvent_t* marks) {
+                                   int grid, cudaStream_t st, cudaEvent_t* marks, bool fast_query) {
     // shadow_count (zeroed by the caller): [0] shadow rays, [1] front hits,
     // [2..3] and [4..5] the 64-bit work counters of the two persistent passes
     unsigned long long* next = reinterpret_cast<unsigned long long*>(shadow_count + 2);
@@ -587,7 +587,12 @@ static cudaError_t trace_wavefront(const DevScene& s, const VolSet& vs, const Li
                                                  next_shadow);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (marks && (e = cudaEventRecord(marks[2], st)) != cudaSuccess) return e;
-    k_shade<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, dR, active, hit_list, shadow_count + 1, records);
+    if (fast_query)
+        k_shade<MULTI, true><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, dR, active, hit_list, shadow_count + 1,
+                                                   records);
+    else
+        k_shade<MULTI, false><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, dR, active, hit_list, shadow_count + 1,
+                                                    records);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (marks && (e = cudaEventRecord(marks[3], st)) != cudaSuccess) return e;
     return cudaSuccess;
@@ -616,15 +621,16 @@ cudaError_t launch_trace_wavefront(const DevScene& s, const VolView& v, const Li
                                    float4* records, int32_t* shadow_list, int32_t* hit_list, int32_t* shadow_count,
                                    int grid, cudaStream_t st, cudaEvent_t* marks) {
     return trace_wavefront<false>(s, single_set(v), L, dirs, R, perm, active, count, records, shadow_list, hit_list,
-                                  shadow_count, grid, st, marks);
+                                  shadow_count, grid, st, marks, query_fast_view(v));
 }
 
 cudaError_t launch_trace_wavefront_multi(const DevScene& s, const VolSet& vs, const Lights& L,
                                          const float4* dirs, int R, const int32_t* perm, const int32_t* active,
                                          const int32_t* count, float4* records, int32_t* shadow_list,
-                                         int32_t* hit_list, int32_t* shadow_count, int grid, cudaStream_t st) {
+                                         int32_t* hit_list, int32_t* shadow_count, int grid, cudaStream_t st,
+                                         bool fast_query) {
     return trace_wavefront<true>(s, vs, L, dirs, R, perm, active, count, records, shadow_list, hit_list,
-                                 shadow_count, grid, st, nullptr);
+                                 shadow_count, grid, st, nullptr, fast_query);
 }
 
 cudaError_t launch_trace_rays(const DevScene& s, const float* orig, const float* dir, int64_t n,

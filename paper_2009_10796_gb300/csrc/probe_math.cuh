@@ -287,6 +287,15 @@ __device__ __forceinline__ float3 sample_irr_at(const VolView& v, int p, const F
                    load_irr(v, p, f.x0 + 1, f.y0 + 1));
 }
 
+// FP32-only forms of the two samplers above (the same loads and arithmetic).
+__device__ __forceinline__ float3 sample_irr_fp32(const VolView& v, int p, const Footprint& f, const Bilerp& w) {
+    const int row = v.irr_n + 2;
+    const float4* a = (const float4*)v.irr + ((int64_t)p * v.irr_tile + (int64_t)f.y0 * row + f.x0);
+    const float4 q00 = __ldg(a), q10 = __ldg(a + 1), q01 = __ldg(a + row), q11 = __ldg(a + row + 1);
+    return bilerp3(w, f3(q00.x, q00.y, q00.z), f3(q10.x, q10.y, q10.z), f3(q01.x, q01.y, q01.z),
+                   f3(q11.x, q11.y, q11.z));
+}
+
 __device__ __forceinline__ float3 sample_irr_at(const VolView& v, int p, const Footprint& f) {
     return sample_irr_at(v, p, f, bilerp_weights(f));
 }
@@ -306,6 +315,16 @@ __device__ __forceinline__ float2 sample_dist_at(const VolView& v, int p, const 
         c = load_dist(v, p, f.x0, f.y0 + 1);
         d = load_dist(v, p, f.x0 + 1, f.y0 + 1);
     }
+    float w00 = (1.0f - f.tx) * (1.0f - f.ty), w10 = f.tx * (1.0f - f.ty);
+    float w01 = (1.0f - f.tx) * f.ty, w11 = f.tx * f.ty;
+    return make_float2(w00 * a.x + w10 * b.x + w01 * c.x + w11 * d.x,
+                       w00 * a.y + w10 * b.y + w01 * c.y + w11 * d.y);
+}
+
+__device__ __forceinline__ float2 sample_dist_fp32(const VolView& v, int p, const Footprint& f) {
+    const int row = v.dist_n + 2;
+    const float2* q = (const float2*)v.dist + (int64_t)p * v.dist_tile + (int64_t)f.y0 * row + f.x0;
+    const float2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + row), d = __ldg(q + row + 1);
     float w00 = (1.0f - f.tx) * (1.0f - f.ty), w10 = f.tx * (1.0f - f.ty);
     float w01 = (1.0f - f.tx) * f.ty, w11 = f.tx * f.ty;
     return make_float2(w00 * a.x + w10 * b.x + w01 * c.x + w11 * d.x,
@@ -338,6 +357,13 @@ __device__ __forceinline__ float gamma_decode_half_fast(float e, float half_gamm
     return powf(e, half_gamma);
 }
 
+// gamma_decode_half_fast for gamma 5 (half_gamma 2.5), without the test.
+__device__ __forceinline__ float gamma_decode_g5_fast(float e) {
+    e = fmaxf(e, 0.0f);
+    const float sq = e > 0.0f ? e * rsqrtf(e) : 0.0f;
+    return e * e * sq;
+}
+
 // Cosine-weighted mean radiance M at x with normal n, the self-shadow bias
 // using w_o (Sec. 4.1 equation), the 8-probe cage (Sec. 2.2): trilinear,
 // backface ((1 + n.w_p)/2)^2 + 0.2, Chebyshev visibility, weight floor
@@ -347,6 +373,10 @@ __device__ __forceinline__ float gamma_decode_half_fast(float e, float half_gamm
 // `look` is the direction the irradiance tiles are read in: n for the
 // irradiance query, the mirror direction for a second-order glossy lookup
 // (Sec. 4.4); the bias and the backface weights use n either way.
+// FAST: the view is known to hold FP32 atlases, gamma 5 and no probe
+// offsets (query_fast_view), so the format, gamma and offset tests drop out
+// of the probe loop; the arithmetic and its order are the same.
+template <bool FAST = false>
 __device__ __forceinline__ float3 query_M_look(const VolView& v, float3 x, float3 n, float3 wo, float3 look) {
     float k = 0.75f * v.min_spacing * v.bias;
     float3 xb = f3(x.x + (0.2f * n.x + 0.8f * wo.x) * k, x.y + (0.2f * n.y + 0.8f * wo.y) * k,
@@ -384,7 +414,7 @@ __device__ __forceinline__ float3 query_M_look(const VolView& v, float3 x, float
         int o0 = c & 1, o1 = (c >> 1) & 1, o2 = (c >> 2) & 1;
         int p = (o0 ? px1 : px0) + cnt[0] * ((o1 ? py1 : py0) + cnt[1] * (o2 ? pz1 : pz0));
         float3 xp = probe_pos_logical(v, base[0] + o0, base[1] + o1, base[2] + o2);
-        if (v.offsets) {   // the probe's own (moved) position; the cage stays on the grid
+        if (!FAST && v.offsets) {   // the probe's own (moved) position; the cage stays on the grid
             const float4 po = __ldg(v.offsets + p);
             xp = f3(xp.x + po.x, xp.y + po.y, xp.z + po.z);
         }
@@ -400,7 +430,8 @@ __device__ __forceinline__ float3 query_M_look(const VolView& v, float3 x, float
         if (rr > 0.0f) {
             float ir = rsqrtf(rr);
             float r = rr * ir;
-            float2 mom = sample_dist_at(v, p, footprint(oct_encode_fast(ir * pv), v.dist_n));
+            const Footprint fd = footprint(oct_encode_fast(ir * pv), v.dist_n);
+            float2 mom = FAST ? sample_dist_fp32(v, p, fd) : sample_dist_at(v, p, fd);
             if (r > mom.x) {
                 float var = fmaxf(mom.y - mom.x * mom.x, 0.0f);
                 float dr = r - mom.x;
@@ -408,10 +439,10 @@ __device__ __forceinline__ float3 query_M_look(const VolView& v, float3 x, float
             }
         }
         float w = wt * wb * fmaxf(wc, 1e-6f);
-        float3 e = sample_irr_at(v, p, fn, wn);
-        acc.x += w * gamma_decode_half_fast(e.x, v.half_gamma);
-        acc.y += w * gamma_decode_half_fast(e.y, v.half_gamma);
-        acc.z += w * gamma_decode_half_fast(e.z, v.half_gamma);
+        float3 e = FAST ? sample_irr_fp32(v, p, fn, wn) : sample_irr_at(v, p, fn, wn);
+        acc.x += w * (FAST ? gamma_decode_g5_fast(e.x) : gamma_decode_half_fast(e.x, v.half_gamma));
+        acc.y += w * (FAST ? gamma_decode_g5_fast(e.y) : gamma_decode_half_fast(e.y, v.half_gamma));
+        acc.z += w * (FAST ? gamma_decode_g5_fast(e.z) : gamma_decode_half_fast(e.z, v.half_gamma));
         sumw += w;
     }
     if (!(sumw > 0.0f)) return f3(0.0f, 0.0f, 0.0f);
@@ -420,8 +451,9 @@ __device__ __forceinline__ float3 query_M_look(const VolView& v, float3 x, float
     return f3(a.x * a.x, a.y * a.y, a.z * a.z);
 }
 
+template <bool FAST = false>
 __device__ __forceinline__ float3 query_M(const VolView& v, float3 x, float3 n, float3 wo) {
-    return query_M_look(v, x, n, wo, n);
+    return query_M_look<FAST>(v, x, n, wo, n);
 }
 
 // Cascade value M at x (Sec. 7.3): volumes densest first; each volume's
@@ -435,6 +467,7 @@ __device__ __forceinline__ float volume_weight(const VolView& v, float3 x) {
     return wx * wy * wz;
 }
 
+template <bool FAST = false>
 __device__ __forceinline__ float3 cascade_M(const VolView* vols, int n, float3 x, float3 nrm, float3 wo) {
     float sum = 0.0f;
     float3 acc = f3(0.0f, 0.0f, 0.0f);
@@ -442,7 +475,7 @@ __device__ __forceinline__ float3 cascade_M(const VolView* vols, int n, float3 x
         const VolView& v = vols[k];
         float take = fminf(volume_weight(v, x), 1.0f - sum);
         if (!(take > 0.0f)) continue;
-        float3 M = query_M(v, x, nrm, wo);
+        float3 M = query_M<FAST>(v, x, nrm, wo);
         acc = acc + take * M;
         sum += take;
         if (sum >= 1.0f) break;
