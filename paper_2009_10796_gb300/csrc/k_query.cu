@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(VolView v, const float*
 // Second-order glossy lookup (Sec. 4.4): one thread per reflection-ray hit;
 // dirs are the unit directions the hits were reached along.  Output is the
 // prefiltered radiance M read in the mirror direction (no factor pi).
+template <bool FAST>
 __global__ void __launch_bounds__(256) k_query_glossy(VolView v, const float* __restrict__ pos,
                                                       const float* __restrict__ nrm, const float* __restrict__ dirs,
                                                       int64_t n, float* __restrict__ out) {
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(256) k_query_glossy(VolView v, const float* __
             float3 r = d - (2.0f * dn) * nn;
             float lr = length(r);
             if (lr > 0.0f) r = (1.0f / lr) * r;
-            M = query_M_look(v, x, nn, f3(-d.x, -d.y, -d.z), r);
+            M = query_M_look<FAST>(v, x, nn, f3(-d.x, -d.y, -d.z), r);
         }
         out[3 * q] = M.x;
         out[3 * q + 1] = M.y;
@@ -267,7 +268,10 @@ cudaError_t launch_query_glossy(const VolView& v, const float* pos, const float*
     if (n == 0) return cudaSuccess;
     int64_t blocks = (n + 255) / 256;
     int grid = (int)(blocks < 1048576 ? blocks : 1048576);
-    k_query_glossy<<<grid, 256, 0, st>>>(v, pos, nrm, dirs, n, out);
+    if (query_fast_view(v))
+        k_query_glossy<true><<<grid, 256, 0, st>>>(v, pos, nrm, dirs, n, out);
+    else
+        k_query_glossy<false><<<grid, 256, 0, st>>>(v, pos, nrm, dirs, n, out);
     return cudaGetLastError();
 }
 
