@@ -147,6 +147,13 @@ def test_odd_sizes_parity(g):
     ed = rel_err(V.dist_atlas().cpu().numpy(), dist).max(-1)
     _report("odd sizes", irr_max=float(ei.max()), dist_max=float(ed.max()))
     assert np.mean(ei <= REL) >= 0.99 and np.mean(ed <= REL) >= 0.99
+    # gamma 2 takes the query's general form (the specialised one serves gamma 5)
+    pos, nrm, cam = synth.room_queries(n=2048)
+    E_ref = oracle.query(desc, st, irr, dist, pos, nrm, cam)
+    E = V.query(to_dev(pos), to_dev(nrm), cam).cpu().numpy()
+    eq = rel_err(E, E_ref).max(-1)
+    _report("odd sizes query", n=len(eq), max_rel=float(eq.max()), over=int((eq > REL).sum()))
+    assert np.mean(eq <= REL) >= 0.99
 
 
 def test_empty_scene_uniform_sky(g):
