@@ -67,18 +67,35 @@ def border_sources(n):
     return tile[..., 0].astype(np.int64)
 
 
+LISTED_WEIGHT = 1e-7
+
+
 def masked_texels(desc, seed, frame, bad, ids):
-    """Boolean masks [P, N, N] of texels influenced (> 1e-3 of their weight) by flagged rays."""
+    """Boolean masks [P, N, N] of the texels a flagged ray reaches: its share
+    of the texel's normalised weights is above LISTED_WEIGHT.  A listed ray
+    can move a texel it reaches by its whole record difference times that
+    share (a distance texel's power-cosine weights make shares of 1e-4 .. 1e-3
+    common), so the threshold is small enough that whatever is left moves by
+    far less than the parity tolerance."""
     P = desc.n_probes
     wi, wd = texel_weights(desc, seed, frame)
     mi = np.zeros((P, desc.irr_n ** 2), dtype=bool)
     md = np.zeros((P, desc.dist_n ** 2), dtype=bool)
     for k in np.nonzero(bad.any(axis=1))[0]:
         rays = np.nonzero(bad[k])[0]
-        mi[ids[k]] |= wi[:, rays].sum(1) > 1e-3
-        md[ids[k]] |= wd[:, rays].sum(1) > 1e-3
+        mi[ids[k]] |= wi[:, rays].sum(1) > LISTED_WEIGHT
+        md[ids[k]] |= wd[:, rays].sum(1) > LISTED_WEIGHT
     si, sd = border_sources(desc.irr_n), border_sources(desc.dist_n)
     return mi[:, si], md[:, sd]
+
+
+def patched(ref, gpu, mask):
+    """The oracle's atlas with the listed texels (mask [P, N, N]) taken from
+    the GPU's: a query of it differs from the GPU's only by the query's own
+    arithmetic and by texels that met the tolerance."""
+    out = np.array(ref, dtype=np.float64, copy=True)
+    out[mask] = np.asarray(gpu, dtype=np.float64)[mask]
+    return out
 
 
 def run_oracle(sc, lights, desc, frames, subset=None):
@@ -137,3 +154,47 @@ def lit_query_sample(sc, desc, seed, n_cells=4, per_cell=16, min_active=2, batch
                 for k in range(max(0, c[2] - 1), min(cz, c[2] + 3)):
                     need.add(i + cx * (j + cy * k))
     return synth.f32(pts[sel]), synth.f32(nrm[sel]), np.array(sorted(need))
+
+
+def probe_positions(desc, ids):
+    """Grid positions [n, 3] of probes (row-major x fastest, no offsets)."""
+    ids = np.asarray(ids, dtype=np.int64)
+    cx, cy, _ = desc.counts
+    ijk = np.stack([ids % cx, (ids // cx) % cy, ids // (cx * cy)], 1)
+    return np.asarray(desc.origin, dtype=np.float64) + ijk * np.asarray(desc.spacing, dtype=np.float64)
+
+
+def near_probes(desc, pos, probe_ids, cells=2.0):
+    """Points within `cells` spacings (per axis) of any of the probes: the
+    points whose query can read a texel of those probes."""
+    pos = np.asarray(pos, dtype=np.float64)
+    out = np.zeros(len(pos), dtype=bool)
+    sp = np.asarray(desc.spacing, dtype=np.float64)
+    for x in probe_positions(desc, probe_ids):
+        out |= np.all(np.abs(pos - x) <= cells * sp, axis=1)
+    return out
+
+
+def flagged_probes(bad, ids):
+    """Probe ids with at least one flagged ray."""
+    return np.asarray(ids)[np.nonzero(np.asarray(bad).any(axis=1))[0]]
+
+
+def fp32_neighbourhood_spread(fn, pos, nrm, floor_scale):
+    """For each point, the largest change of the oracle's result fn(pos, nrm)
+    over the 26 neighbouring FP32 positions (one ulp per axis), relative to
+    the scale rel_err uses (max(|ref|, floor_scale)).  Where this exceeds the
+    parity tolerance the FP32 input does not fix the result to that
+    tolerance: rounding at the input's scale alone moves it further."""
+    pos = np.asarray(pos, dtype=np.float64)
+    nrm = np.asarray(nrm, dtype=np.float64)
+    nb = np.array([[a, b, c] for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1) if (a, b, c) != (0, 0, 0)],
+                  dtype=np.float64)
+    p32 = pos.astype(np.float32)
+    ulp = np.abs(np.nextafter(p32, np.float32(np.inf)) - p32).astype(np.float64)
+    P = (pos[:, None, :] + nb[None] * ulp[:, None, :]).reshape(-1, 3)
+    N_ = np.repeat(nrm, len(nb), axis=0)
+    E0 = fn(pos, nrm)
+    En = fn(P, N_).reshape(len(pos), len(nb), -1)
+    scale = np.maximum(np.abs(E0), floor_scale)
+    return (np.abs(En - E0[:, None, :]) / scale[:, None, :]).max(axis=(1, 2))

@@ -7,7 +7,7 @@ import torch
 
 import oracle
 import synth
-from parity import rel_err, to_dev
+from parity import REL, compare_rays, gpu_rays_by_probe, masked_texels, patched, rel_err, run_oracle, to_dev
 from test_oracle_adjoint import _scene
 
 pytestmark = pytest.mark.gpu
@@ -38,22 +38,60 @@ def _setup(gamma):
 
 @pytest.mark.parametrize("gamma", [1.0, 5.0])
 def test_adjoint_matches_oracle_gradient(g, gamma):
+    """The differentiable forward (two updates from a zero atlas, hysteresis 0,
+    then the query) and its adjoint against the oracle.  The forward's
+    updates are replayed through the plain update and compared ray by ray;
+    rays whose FP32 and FP64 hits differ (an edge grazed within rounding) are
+    listed with the texels they reach (weight > 1e-3 of the texel's row) and
+    the query points near those probes; everything else meets 1e-4."""
     sc, L, desc, pos, nrm, G, cam = _setup(gamma)
     E_ref, g_em_ref, g_al_ref = oracle.diff(oracle.SceneHandle(sc), L, desc, pos, nrm, cam, G)
+    st_o, irr_o, dist_o, rays_o = run_oracle(sc, L, desc, [0, 1])
     S = g.Scene.from_arrays(sc)
+    W = g.Volume(desc)
+    mi = np.zeros(irr_o.shape[:3], dtype=bool)
+    md = np.zeros(dist_o.shape[:3], dtype=bool)
+    flagged = 0
+    for k, f in enumerate([0, 1]):
+        W.update(S, L, f)
+        rec, ids = gpu_rays_by_probe(W)
+        bad, err = compare_rays(rec, ids, rays_o[k])
+        a, b = masked_texels(desc, desc.seed, f, bad, ids)
+        mi |= a
+        md |= b
+        flagged += int(bad.sum())
+        if bad.any():
+            print(f"[adjoint] gamma {gamma} frame {f}: listed rays (probe, ray): "
+                  f"{[(int(ids[i]), int(r)) for i, r in zip(*np.nonzero(bad))][:12]}")
     V = g.Volume(desc)
     albedo = torch.tensor(sc.object_albedo, dtype=torch.float32, device="cuda", requires_grad=True)
     emit = torch.tensor(sc.emitter_radiance, dtype=torch.float32, device="cuda", requires_grad=True)
     P, N_ = to_dev(pos), to_dev(nrm)
     E = g.IrradianceField.apply(albedo, emit, V, S, L, P, N_, cam, 0, 2)
+    # the differentiable forward runs the same updates: its atlas is the plain update's, bit for bit
+    assert torch.equal(V.irr_raw(), W.irr_raw()) and torch.equal(V.dist_raw(), W.dist_raw())
     (E * to_dev(G)).sum().backward()
-    e = rel_err(E.detach().cpu().numpy(), E_ref).max()
+    gi = V.irr_atlas().cpu().numpy().astype(np.float64)
+    gd = V.dist_atlas().cpu().numpy().astype(np.float64)
+    ei = rel_err(gi, irr_o).max(-1)
+    ed = rel_err(gd, dist_o).max(-1)
+    # end to end: the oracle's query of its own atlas with the listed texels
+    # taken from the GPU's (the rest of the forward must then meet 1e-4)
+    E_gpu = E.detach().cpu().numpy()
+    E_patch = oracle.query(desc, st_o, patched(irr_o, gi, mi), patched(dist_o, gd, md), pos, nrm, cam)
+    e = rel_err(E_gpu, E_patch).max(-1)
+    e_all = rel_err(E_gpu, E_ref).max(-1)
+    E_own = oracle.query(desc, V.states().cpu().numpy(), gi, gd, pos, nrm, cam)
+    e_own = rel_err(E_gpu, E_own).max(-1)
     ea = rel_err(albedo.grad.cpu().numpy(), g_al_ref).max()
     ee = rel_err(emit.grad.cpu().numpy(), g_em_ref).max()
-    print(f"[adjoint] gamma {gamma}: forward max rel {e:.2e}, albedo grad {ea:.2e}, emitter grad {ee:.2e}")
-    # the forward is the FP32 update + query; with 32 rays per probe the query's
-    # Chebyshev variance (mu2 - mu^2 of a few rays) cancels most in FP32
-    assert e <= 1e-3
+    print(f"[adjoint] gamma {gamma}: listed rays {flagged} of {2 * desc.n_probes * desc.rays_per_probe}, masked "
+          f"texels {int(mi.sum())} + {int(md.sum())}; texels irr {ei[~mi].max():.2e}, dist {ed[~md].max():.2e}; "
+          f"forward: against the listed-texel-patched oracle atlas {e.max():.2e} (unpatched {e_all.max():.2e}), "
+          f"on the GPU's own atlas {e_own.max():.2e}; albedo grad {ea:.2e}, emitter grad {ee:.2e}")
+    assert flagged <= max(2, int(1e-3 * 2 * desc.n_probes * desc.rays_per_probe))
+    assert ei[~mi].max() <= REL and ed[~md].max() <= REL
+    assert e.max() <= REL and e_own.max() <= REL
     assert ea <= 1e-3 and ee <= 1e-3
 
 

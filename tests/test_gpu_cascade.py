@@ -9,7 +9,7 @@ import torch
 
 import oracle
 import synth
-from parity import REL, compare_rays, rel_err, to_dev
+from parity import REL, compare_rays, fp32_neighbourhood_spread, rel_err, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -70,7 +70,7 @@ def test_cascade_tracking_update_and_query_parity(g):
             ed = rel_err(C.dist_atlas(k).cpu().numpy(), dist).max(-1)
             print(f"[cascade] frame {f} volume {k}: shift {shift if k == 0 else '-'}, irr max rel "
                   f"{ei.max():.2e}, dist max rel {ed.max():.2e}")
-            assert np.mean(ei <= REL) >= 0.999 and np.mean(ed <= REL) >= 0.999
+            assert ei.max() <= REL and ed.max() <= REL
     C.poll_status()
     pos, nrm, _ = synth.room_queries(n=4096)
     cam = _camera(frames[-1])
@@ -78,7 +78,7 @@ def test_cascade_tracking_update_and_query_parity(g):
     E = C.query(to_dev(pos), to_dev(nrm), cam).cpu().numpy()
     e = rel_err(E, E_ref).max(-1)
     print(f"[cascade] query max rel {e.max():.2e}, over 1e-4: {int((e > REL).sum())}")
-    assert np.mean(e <= REL) >= 0.999
+    assert e.max() <= REL
 
 
 def test_cascade_graph_replay_matches_eager(g):
@@ -160,7 +160,7 @@ def test_terrain_cascades_full_size_frame0_sampled(g):
     rng = np.random.default_rng(2025)
     subsets = []
     for k, d in enumerate(descs):
-        act = probe_of[vol_of == k]
+        act = np.sort(probe_of[vol_of == k])   # the list's order depends on the GPU's schedule
         assert len(act) > 0, f"volume {k} has no active probe"
         pick = np.concatenate([rng.choice(d.n_probes, 2, replace=False), rng.choice(act, 2, replace=False)])
         subsets.append(np.unique(pick).astype(np.int64))
@@ -179,6 +179,9 @@ def test_terrain_cascades_full_size_frame0_sampled(g):
             bad, _ = compare_rays(rec[where[(k, int(p))]][None], np.array([0]), rays[k][q][None])
             flagged += int(bad.sum())
             if bad.any():
+                for r in np.nonzero(bad[0])[0]:
+                    print(f"[terrain cascade] listed ray: volume {k} probe {int(p)} ray {int(r)}: gpu "
+                          f"{rec[where[(k, int(p))]][r].tolist()}, oracle {rays[k][q][r].tolist()}")
                 continue
             checked += 1
             worst_i = max(worst_i, float(rel_err(gi[k][p], irr[p]).max()))
@@ -199,4 +202,18 @@ def test_terrain_cascades_full_size_frame0_sampled(g):
     E = C.query(to_dev(pts), to_dev(nrm), cam).cpu().numpy()
     e = rel_err(E, E_ref).max(-1)
     print(f"[terrain cascade] query {len(e)} points, max rel {e.max():.2e}, over 1e-4: {int((e > REL).sum())}")
-    assert np.mean(e <= REL) >= 0.999
+    # points where the oracle's own result moves by more than the tolerance
+    # between neighbouring FP32 positions are listed: there the FP32 inputs
+    # do not fix the result to 1e-4 (a Chebyshev test with r close to mu and
+    # a small sigma), and the GPU must stay within 1e-4 plus twice that spread
+    spread = fp32_neighbourhood_spread(lambda P, N_: oracle.query_cascade(vols, gst, gi, gd, P, N_, cam), pts, nrm,
+                                       1e-3 * np.abs(E_ref).max())
+    listed = spread > REL
+    for i in np.nonzero(listed | (e > REL))[0]:
+        print(f"[terrain cascade] listed point {int(i)} at {pts[i].tolist()}: rel {e[i]:.2e}, oracle 1-ulp "
+              f"neighbourhood spread {spread[i]:.2e}, gpu {E[i].tolist()}, oracle {E_ref[i].tolist()}")
+    print(f"[terrain cascade] listed {int(listed.sum())} of {len(e)} points; max rel on the rest "
+          f"{e[~listed].max():.2e}")
+    assert listed.mean() <= 1e-3
+    assert e[~listed].max() <= REL
+    assert np.all(e[listed] <= REL + 2.0 * spread[listed])

@@ -51,12 +51,13 @@ def test_converge_pass_parity(g, dynamic):
     ei = rel_err(V.irr_atlas().cpu().numpy(), irr).max(-1)
     ed = rel_err(V.dist_atlas().cpu().numpy(), dist).max(-1)
     print(f"[converge] irr max {ei.max():.2e}, dist max {ed.max():.2e}")
-    assert np.mean(ei <= REL) >= 0.999 and np.mean(ed <= REL) >= 0.999
+    assert ei.max() <= REL and ed.max() <= REL
     pos, nrm, cam = synth.room_queries(n=2048)
     want = oracle.query(desc, st, irr, dist, pos, nrm, cam)
     got = V.query(to_dev(pos), to_dev(nrm), cam).cpu().numpy()
     eq = rel_err(got, want).max(-1)
-    assert np.mean(eq <= REL) >= 0.999
+    print(f"[converge] query max {eq.max():.2e}")
+    assert eq.max() <= REL
 
 
 def test_converge_changes_the_first_frame(g):

@@ -49,7 +49,7 @@ def test_dynamic_wakeup_parity(g):
     ei = rel_err(V.irr_atlas().cpu().numpy(), irr).max(-1)
     ed = rel_err(V.dist_atlas().cpu().numpy(), dist).max(-1)
     print(f"[dynamic] awake probe-frames {awake_seen}; irr max {ei.max():.2e}, dist max {ed.max():.2e}")
-    assert np.mean(ei <= REL) >= 0.999 and np.mean(ed <= REL) >= 0.999
+    assert ei.max() <= REL and ed.max() <= REL
 
 
 def test_dynamic_boxes_validation(g):

@@ -9,7 +9,7 @@ import torch
 
 import oracle
 import synth
-from parity import REL, rel_err, to_dev
+from parity import REL, patched, rel_err, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -59,13 +59,24 @@ def test_optimizer_offsets_states_and_texels(g, case):
     ei = rel_err(gi, irr).max(-1)[~bad]
     ed = rel_err(gd, dist).max(-1)[~bad]
     print(f"[optimizer] texels: irr max {ei.max():.2e}, dist max {ed.max():.2e}")
-    assert np.mean(ei <= REL) >= 0.999 and np.mean(ed <= REL) >= 0.999
+    assert ei.max() <= REL and ed.max() <= REL
+    # end to end, with the probes the two sides moved differently (listed
+    # above) taken from the GPU (offset, state, tiles); and the query kernel
+    # alone against the oracle's query of the GPU's own atlas, states and offsets
     pos, nrm, cam = synth.room_queries()
-    E_ref = oracle.query(desc, st, irr, dist, pos, nrm, cam, offsets=off)
+    st_p = np.where(bad, gs, st).astype(np.uint8)
+    off_p = np.ascontiguousarray(np.where(bad[:, None], go, off))
+    E_ref = oracle.query(desc, st_p, patched(irr, gi, np.broadcast_to(bad[:, None, None], gi.shape[:3])),
+                         patched(dist, gd, np.broadcast_to(bad[:, None, None], gd.shape[:3])), pos, nrm, cam,
+                         offsets=off_p)
     E = V.query(to_dev(pos), to_dev(nrm), cam).cpu().numpy()
     e = rel_err(E, E_ref).max(-1)
-    print(f"[optimizer] query: median {np.median(e):.2e}, within 1e-4: {np.mean(e <= REL):.4f}")
-    assert np.mean(e <= REL) >= 0.98
+    E_own = oracle.query(desc, gs, gi.astype(np.float64), gd.astype(np.float64), pos, nrm, cam,
+                         offsets=np.ascontiguousarray(go))
+    e_own = rel_err(E, E_own).max(-1)
+    print(f"[optimizer] query: max {e.max():.2e} ({int(bad.sum())} listed probes from the GPU); against the "
+          f"GPU's own atlas max {e_own.max():.2e}")
+    assert e.max() <= REL and e_own.max() <= REL
 
 
 def test_optimizer_off_matches_plain_update(g):

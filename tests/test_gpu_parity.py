@@ -5,8 +5,8 @@ import torch
 
 import oracle
 import synth
-from parity import (REL, compare_rays, gpu_rays_by_probe, lit_query_sample, masked_texels, rel_err, run_oracle,
-                    to_dev)
+from parity import (REL, compare_rays, gpu_rays_by_probe, lit_query_sample, masked_texels, patched, rel_err,
+                    run_oracle, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -100,14 +100,17 @@ def test_room_update_and_query_parity(g):
     _report("room texels", irr_max=float(ei[~mi].max()), dist_max=float(ed[~md].max()),
             masked_irr=int(mi.sum()), masked_dist=int(md.sum()))
     assert ei[~mi].max() <= REL and ed[~md].max() <= REL
-    # query at 4096 seeded points
+    # query at 4096 seeded points: end to end against the oracle's atlas
+    # (with the listed texels, if any, taken from the GPU's), and the query
+    # kernel alone against the oracle's query of the GPU's own atlas
     pos, nrm, cam = synth.room_queries()
-    E_ref = oracle.query(desc, st, irr, dist, pos, nrm, cam)
+    E_ref = oracle.query(desc, st, patched(irr, gi, mi), patched(dist, gd, md), pos, nrm, cam)
     E = V.query(to_dev(pos), to_dev(nrm), cam).cpu().numpy()
     e = rel_err(E, E_ref).max(-1)
-    _report("room query", n=len(e), max_rel=float(e.max()), over=int((e > REL).sum()))
-    assert np.mean(e <= REL) >= 0.999
-    assert e.max() <= 1e-2
+    E_own = oracle.query(desc, states, gi.astype(np.float64), gd.astype(np.float64), pos, nrm, cam)
+    e_own = rel_err(E, E_own).max(-1)
+    _report("room query", n=len(e), max_rel=float(e.max()), own_atlas_max_rel=float(e_own.max()))
+    assert e.max() <= REL and e_own.max() <= REL
 
 
 def test_room_multiframe_hysteresis_parity(g):
@@ -116,19 +119,24 @@ def test_room_multiframe_hysteresis_parity(g):
     sc, V, (st, irr, dist, rays), per_frame = _room_case(g, desc, frames)
     assert np.array_equal(V.states().cpu().numpy(), st)
     flagged = 0
+    mi = np.zeros(V.irr_atlas().shape[:3], dtype=bool)
+    md = np.zeros(V.dist_atlas().shape[:3], dtype=bool)
     for k, f in enumerate(frames):
         rec, ids = per_frame[k]
-        bad, err = compare_rays(rec, ids, rays[k], rtol=5e-4)
+        bad, err = compare_rays(rec, ids, rays[k])
         flagged += int(bad.sum())
+        a, b = masked_texels(desc, desc.seed, f, bad, ids)
+        mi |= a
+        md |= b
         _report(f"multiframe rays f{f}", flagged=int(bad.sum()), max_rel=float(err[~bad].max()))
     assert flagged <= 8
     gi = V.irr_atlas().cpu().numpy()
     gd = V.dist_atlas().cpu().numpy()
     ei = rel_err(gi, irr).max(-1)
     ed = rel_err(gd, dist).max(-1)
-    _report("multiframe texels", irr_max=float(ei.max()), dist_max=float(ed.max()),
-            irr_over=int((ei > REL).sum()), dist_over=int((ed > REL).sum()))
-    assert np.mean(ei <= REL) >= 0.999 and np.mean(ed <= REL) >= 0.999
+    _report("multiframe texels", irr_max=float(ei[~mi].max()), dist_max=float(ed[~md].max()),
+            masked_irr=int(mi.sum()), masked_dist=int(md.sum()))
+    assert ei[~mi].max() <= REL and ed[~md].max() <= REL
 
 
 def test_odd_sizes_parity(g):
@@ -146,14 +154,14 @@ def test_odd_sizes_parity(g):
     ei = rel_err(V.irr_atlas().cpu().numpy(), irr).max(-1)
     ed = rel_err(V.dist_atlas().cpu().numpy(), dist).max(-1)
     _report("odd sizes", irr_max=float(ei.max()), dist_max=float(ed.max()))
-    assert np.mean(ei <= REL) >= 0.99 and np.mean(ed <= REL) >= 0.99
+    assert ei.max() <= REL and ed.max() <= REL
     # gamma 2 takes the query's general form (the specialised one serves gamma 5)
     pos, nrm, cam = synth.room_queries(n=2048)
     E_ref = oracle.query(desc, st, irr, dist, pos, nrm, cam)
     E = V.query(to_dev(pos), to_dev(nrm), cam).cpu().numpy()
     eq = rel_err(E, E_ref).max(-1)
     _report("odd sizes query", n=len(eq), max_rel=float(eq.max()), over=int((eq > REL).sum()))
-    assert np.mean(eq <= REL) >= 0.99
+    assert eq.max() <= REL
 
 
 def test_empty_scene_uniform_sky(g):
@@ -248,8 +256,83 @@ def test_city_query_sampled_points(g, city):
     _report("city query", points=len(pts), probes=len(subset), lit=lit, max_rel=float(e.max()),
             over=int((e > REL).sum()))
     assert lit >= 0.9
-    assert np.mean(e <= REL) >= 0.95
-    assert np.median(e) <= REL
+    assert e.max() <= REL
+
+
+@pytest.fixture(scope="module")
+def city_steady(g):
+    """The benchmark's city volume run for 60 frames (hysteresis 0.97, per-frame
+    rotation, multi-bounce through the previous atlas, per-texel thresholds),
+    keeping, at frames 5 and 59, the GPU's state before the update (the
+    previous atlas the oracle's one-step update starts from) and after it."""
+    sc = synth.city_scene()
+    desc = synth.city_volume()
+    L = synth.city_lights()
+    S = g.Scene.from_arrays(sc)
+    V = g.Volume(desc)
+    snaps = {}
+    for f in range(60):
+        if f in (5, 59):
+            prev = (V.states().cpu().numpy(), np.ascontiguousarray(V.irr_atlas().cpu().numpy(), dtype=np.float64),
+                    np.ascontiguousarray(V.dist_atlas().cpu().numpy(), dtype=np.float64))
+        V.update(S, L, f)
+        if f in (5, 59):
+            rec, ids = V.ray_records()
+            snaps[f] = dict(prev=prev, rec=rec.cpu().numpy(), ids=ids.cpu().numpy().astype(np.int64),
+                            states=V.states().cpu().numpy(), irr=V.irr_atlas().cpu().numpy(),
+                            dist=V.dist_atlas().cpu().numpy())
+    torch.cuda.synchronize()
+    V.poll_status()
+    return sc, desc, L, S, V, snaps
+
+
+@pytest.mark.parametrize("frame", [5, 59])
+def test_city_steady_state_one_step(g, city_steady, frame):
+    """Steady-state frames of the benchmark workload: the oracle's one-step
+    update of 64 seeded active probes, started from the GPU's own previous
+    atlas and states, against the GPU's update of the same frame: per-ray
+    records (shading reads the lit previous atlas), texels (hysteresis 0.97
+    and the per-texel thresholds of Sec. 4.3), states."""
+    sc, desc, L, S, V, snaps = city_steady
+    sn = snaps[frame]
+    st0, irr0, dist0 = sn["prev"]
+    act = np.nonzero(st0 == oracle.VIGILANT)[0]
+    sample = np.sort(np.random.default_rng(500 + frame).choice(act, 64, replace=False))
+    st, irr, dist = st0.copy(), irr0.copy(), dist0.copy()
+    rays = oracle.update(oracle.SceneHandle(sc), L, desc, frame, st, irr, dist, subset=sample, want_rays=True)
+    assert np.array_equal(sn["states"], np.where(np.isin(np.arange(desc.n_probes), sample), st, sn["states"]))
+    pos_of = {int(p): k for k, p in enumerate(sn["ids"])}
+    rec = sn["rec"][[pos_of[int(p)] for p in sample]].astype(np.float64)
+    bad, err = compare_rays(rec, np.arange(len(sample)), rays)
+    mi, md = masked_texels(desc, desc.seed, frame, bad, sample)
+    ei = rel_err(sn["irr"][sample], irr[sample]).max(-1)
+    ed = rel_err(sn["dist"][sample], dist[sample]).max(-1)
+    mi, md = mi[sample], md[sample]
+    _report(f"city one-step f{frame}", probes=len(sample), rays=bad.size, flagged=int(bad.sum()),
+            ray_max_rel=float(err[~bad].max()), irr_max=float(ei[~mi].max()), dist_max=float(ed[~md].max()),
+            masked_irr=int(mi.sum()), masked_dist=int(md.sum()))
+    assert bad.sum() <= max(2, int(1e-4 * bad.size))
+    assert ei[~mi].max() <= REL and ed[~md].max() <= REL
+
+
+def test_city_full_1080p_query_own_atlas(g, city_steady):
+    """The benchmark's query, every pixel of the 1920x1080 G-buffer, at frame 59,
+    against the oracle's query of the GPU's own atlas and states."""
+    sc, desc, L, S, V, snaps = city_steady
+    cam = synth.city_camera()
+    pos, nrm = S.raycast_gbuffer(cam.position, cam.forward, cam.up, cam.vfov_deg, cam.width, cam.height)
+    E = V.query(pos, nrm, cam.position).cpu().numpy()
+    st = V.states().cpu().numpy()
+    gi = np.ascontiguousarray(V.irr_atlas().cpu().numpy(), dtype=np.float64)
+    gd = np.ascontiguousarray(V.dist_atlas().cpu().numpy(), dtype=np.float64)
+    P = pos.cpu().numpy().astype(np.float64)
+    N_ = nrm.cpu().numpy().astype(np.float64)
+    E_ref = oracle.query(desc, st, gi, gd, P, N_, cam.position)
+    e = rel_err(E, E_ref).max(-1)
+    worst = np.argsort(-e)[:5]
+    _report("city 1080p query", pixels=len(e), lit=float(np.mean(np.any(E_ref > 0, 1))), max_rel=float(e.max()),
+            over=int((e > REL).sum()), worst=[(int(i), float(e[i])) for i in worst])
+    assert e.max() <= REL
 
 
 def test_room_glossy_lookup_parity(g):
@@ -262,5 +345,8 @@ def test_room_glossy_lookup_parity(g):
     M_ref = oracle.query_glossy(desc, st, irr, dist, pos, nrm, dirs)
     M = V.query_glossy(to_dev(pos), to_dev(nrm), to_dev(dirs)).cpu().numpy()
     e = rel_err(M, M_ref).max(-1)
-    _report("room glossy", n=len(e), max_rel=float(e.max()), over=int((e > REL).sum()))
-    assert np.mean(e <= REL) >= 0.999 and e.max() <= 1e-2
+    M_own = oracle.query_glossy(desc, V.states().cpu().numpy(), V.irr_atlas().cpu().numpy().astype(np.float64),
+                                V.dist_atlas().cpu().numpy().astype(np.float64), pos, nrm, dirs)
+    e_own = rel_err(M, M_own).max(-1)
+    _report("room glossy", n=len(e), max_rel=float(e.max()), own_atlas_max_rel=float(e_own.max()))
+    assert e.max() <= REL and e_own.max() <= REL
