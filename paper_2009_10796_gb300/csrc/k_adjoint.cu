@@ -19,11 +19,9 @@ namespace ddgi {
 // a_pc = b_pc^(gamma/2), b the bilinear sample of probe p's tile in
 // direction n.  Scatters dM into g_irr (float [P][tile][3]).
 __device__ void query_M_adjoint(const VolView& v, float3 x, float3 n, float3 wo, float3 dM, float* g_irr) {
-    float k = 0.75f * v.min_spacing * v.bias;
-    float3 xb = f3(x.x + (0.2f * n.x + 0.8f * wo.x) * k, x.y + (0.2f * n.y + 0.8f * wo.y) * k,
-                   x.z + (0.2f * n.z + 0.8f * wo.z) * k);
-    float g[3] = {(xb.x - v.origin.x) / v.spacing.x, (xb.y - v.origin.y) / v.spacing.y,
-                  (xb.z - v.origin.z) / v.spacing.z};
+    const LocalPoint q = local_point(v, x, n, wo);
+    float g[3] = {(q.hi.x + q.lb.x) / v.spacing.x, (q.hi.y + q.lb.y) / v.spacing.y,
+                  (q.hi.z + q.lb.z) / v.spacing.z};
     int cnt[3] = {v.counts.x, v.counts.y, v.counts.z};
     int base[3];
     float fr[3];
@@ -45,14 +43,14 @@ __device__ void query_M_adjoint(const VolView& v, float3 x, float3 n, float3 wo,
         p8[c] = p;
         w8[c] = 0.0f;
         if (!state_active(v.states[p])) continue;
-        float3 xp = probe_pos_logical(v, base[0] + o0, base[1] + o1, base[2] + o2);
+        const float3 a = local_to_probe(v, q, base[0] + o0, base[1] + o1, base[2] + o2);
         float wt = (o0 ? fr[0] : 1.0f - fr[0]) * (o1 ? fr[1] : 1.0f - fr[1]) * (o2 ? fr[2] : 1.0f - fr[2]);
-        float3 dp = xp - x;
+        float3 dp = f3(-(a.x + q.lo.x), -(a.y + q.lo.y), -(a.z + q.lo.z));   // probe - x
         float ldp = length(dp);
         float cw = ldp > 0.0f ? dot(n, dp) / ldp : 1.0f;
         float hb = (1.0f + cw) * 0.5f;
         float wb = hb * hb + 0.2f;
-        float3 pv = xb - xp;
+        float3 pv = a + q.lb;                                                // biased point - probe
         float r = length(pv);
         float wc = 1.0f;
         if (r > 0.0f) {

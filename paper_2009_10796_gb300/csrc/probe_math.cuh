@@ -364,6 +364,43 @@ __device__ __forceinline__ float gamma_decode_g5_fast(float e) {
     return e * e * sq;
 }
 
+// a - b for FP32 a, b as the unevaluated sum hi + lo, exactly (Knuth's
+// TwoSum applied to a and -b, round-to-nearest); the intrinsics keep each
+// step as written.
+__device__ __forceinline__ void two_diff(float a, float b, float& hi, float& lo) {
+    hi = __fsub_rn(a, b);
+    const float bb = __fsub_rn(hi, a);
+    lo = __fadd_rn(__fsub_rn(a, __fsub_rn(hi, bb)), __fsub_rn(-b, bb));
+}
+
+// A query point in the volume's own frame: x - origin = hi + lo exactly, and
+// lb = lo + the self-shadow bias vector (Sec. 4.1), so the biased point is
+// origin + hi + lb.  Probe-to-point vectors formed from these carry rounding
+// errors relative to their own length, not to |x|: far from the world
+// origin, 2^-24 |x| approaches the standard deviation the Chebyshev test
+// divides by, and the weight then follows the rounding of x instead of x.
+struct LocalPoint {
+    float3 hi, lo, lb;
+};
+
+__device__ __forceinline__ LocalPoint local_point(const VolView& v, float3 x, float3 n, float3 wo) {
+    const float k = 0.75f * v.min_spacing * v.bias;
+    LocalPoint q;
+    two_diff(x.x, v.origin.x, q.hi.x, q.lo.x);
+    two_diff(x.y, v.origin.y, q.hi.y, q.lo.y);
+    two_diff(x.z, v.origin.z, q.hi.z, q.lo.z);
+    q.lb = f3(q.lo.x + (0.2f * n.x + 0.8f * wo.x) * k, q.lo.y + (0.2f * n.y + 0.8f * wo.y) * k,
+              q.lo.z + (0.2f * n.z + 0.8f * wo.z) * k);
+    return q;
+}
+
+// x - x_p for the grid point (i, j, k) of the cage: the high part of the
+// difference (one rounding, relative to |x - x_p|); add q.lo for the
+// unbiased point, q.lb for the biased one.
+__device__ __forceinline__ float3 local_to_probe(const VolView& v, const LocalPoint& q, int i, int j, int k) {
+    return f3(q.hi.x - (float)i * v.spacing.x, q.hi.y - (float)j * v.spacing.y, q.hi.z - (float)k * v.spacing.z);
+}
+
 // Cosine-weighted mean radiance M at x with normal n, the self-shadow bias
 // using w_o (Sec. 4.1 equation), the 8-probe cage (Sec. 2.2): trilinear,
 // backface ((1 + n.w_p)/2)^2 + 0.2, Chebyshev visibility, weight floor
@@ -378,11 +415,9 @@ __device__ __forceinline__ float gamma_decode_g5_fast(float e) {
 // of the probe loop; the arithmetic and its order are the same.
 template <bool FAST = false>
 __device__ __forceinline__ float3 query_M_look(const VolView& v, float3 x, float3 n, float3 wo, float3 look) {
-    float k = 0.75f * v.min_spacing * v.bias;
-    float3 xb = f3(x.x + (0.2f * n.x + 0.8f * wo.x) * k, x.y + (0.2f * n.y + 0.8f * wo.y) * k,
-                   x.z + (0.2f * n.z + 0.8f * wo.z) * k);
-    float g[3] = {(xb.x - v.origin.x) / v.spacing.x, (xb.y - v.origin.y) / v.spacing.y,
-                  (xb.z - v.origin.z) / v.spacing.z};
+    const LocalPoint q = local_point(v, x, n, wo);
+    float g[3] = {(q.hi.x + q.lb.x) / v.spacing.x, (q.hi.y + q.lb.y) / v.spacing.y,
+                  (q.hi.z + q.lb.z) / v.spacing.z};
     int cnt[3] = {v.counts.x, v.counts.y, v.counts.z};
     int base[3];
     float fr[3];
@@ -413,18 +448,18 @@ __device__ __forceinline__ float3 query_M_look(const VolView& v, float3 x, float
         const int c = __ffs(act) - 1;
         int o0 = c & 1, o1 = (c >> 1) & 1, o2 = (c >> 2) & 1;
         int p = (o0 ? px1 : px0) + cnt[0] * ((o1 ? py1 : py0) + cnt[1] * (o2 ? pz1 : pz0));
-        float3 xp = probe_pos_logical(v, base[0] + o0, base[1] + o1, base[2] + o2);
+        float3 a = local_to_probe(v, q, base[0] + o0, base[1] + o1, base[2] + o2);
         if (!FAST && v.offsets) {   // the probe's own (moved) position; the cage stays on the grid
             const float4 po = __ldg(v.offsets + p);
-            xp = f3(xp.x + po.x, xp.y + po.y, xp.z + po.z);
+            a = f3(a.x - po.x, a.y - po.y, a.z - po.z);
         }
         float wt = (o0 ? fr[0] : 1.0f - fr[0]) * (o1 ? fr[1] : 1.0f - fr[1]) * (o2 ? fr[2] : 1.0f - fr[2]);
-        float3 dp = xp - x;
+        float3 dp = f3(-(a.x + q.lo.x), -(a.y + q.lo.y), -(a.z + q.lo.z));   // probe - x
         float dd = dot(dp, dp);
         float cw = dd > 0.0f ? dot(n, dp) * rsqrtf(dd) : 1.0f;
         float hb = (1.0f + cw) * 0.5f;
         float wb = hb * hb + 0.2f;
-        float3 pv = xb - xp;
+        float3 pv = a + q.lb;                                                // biased point - probe
         float rr = dot(pv, pv);
         float wc = 1.0f;
         if (rr > 0.0f) {
