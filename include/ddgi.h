@@ -485,15 +485,27 @@ ddgi_status ddgi_diff_backward(ddgi_volume volume, ddgi_scene scene, const ddgi_
  * probe and 1048576 probes x rays; irr_n <= 8, dist_n <= 16; FP32 blend only
  * (UNSUPPORTED otherwise).
  *
- * The first call on a device looks up the arrays' device addresses with
- * that device current; make that first call before any stream capture.
+ * The first call on a device loads the library's module there, which is when
+ * the driver sets the arrays up, and looks up their device addresses with
+ * that device current.  Make that first call as a warm-up, before the
+ * region in which the caller may not allocate begins and before any stream
+ * capture; later calls allocate nothing.
  * Every call shares the arrays and overwrites the previous call's contents
  * (the counters it needs zeroed are cleared by each call), so calls whose
- * work overlaps on the GPU, on any streams, race: serialise them. */
+ * work overlaps on the GPU, on any streams, race: serialise them.
+ * Device-side errors (a non-finite texel) are not returned by the call; they
+ * accumulate in a status word read by ddgi_update_noalloc_poll_status. */
 ddgi_status ddgi_update_noalloc(ddgi_scene scene, const ddgi_volume_desc* desc,
                                 const ddgi_lights* lights, const ddgi_update_params* params,
                                 uint8_t* states_dev, void* irr_dev, void* dist_dev,
                                 ddgi_stream stream);
+
+/* Status of the ddgi_update_noalloc calls on the current device since the
+ * last poll (no counterpart in the paper): reads and clears the device status
+ * word those calls share, synchronising `stream`.  NUMERIC when a blend wrote
+ * a non-finite texel, TIMEOUT when a bounded device wait gave up, OK
+ * otherwise (also before any call on this device).  Allocates nothing. */
+ddgi_status ddgi_update_noalloc_poll_status(ddgi_stream stream);
 
 #ifdef __cplusplus
 }

@@ -93,6 +93,7 @@ SIGNATURES = {
     "ddgi_trace_stats": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.c_uint64 * 7, _vp]),
     "ddgi_update_noalloc": (C.c_int, [_vp, C.POINTER(VolumeDesc), C.POINTER(Lights),
                                       C.POINTER(UpdateParams), _vp, _vp, _vp, _vp]),
+    "ddgi_update_noalloc_poll_status": (C.c_int, [_vp]),
     "ddgi_cascade_create": (C.c_int, [C.POINTER(VolumeDesc), C.c_int32, C.POINTER(_vp)]),
     "ddgi_cascade_destroy": (None, [_vp]),
     "ddgi_cascade_update": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.POINTER(CascadeParams), _vp]),

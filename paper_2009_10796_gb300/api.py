@@ -355,6 +355,13 @@ def update_noalloc(scene: Scene, desc, lights, frame: int, states: torch.Tensor,
                                      _ptr(irr), _ptr(dist), _stream(stream)))
 
 
+def update_noalloc_poll_status(stream=None):
+    """Raise DDGIError if an update_noalloc call on the current device flagged
+    a device-side error since the last poll (reads and clears the shared
+    status word; synchronises the stream)."""
+    check(load().ddgi_update_noalloc_poll_status(_stream(stream)))
+
+
 class Cascade:
     """Nested probe volumes updated together (densest first), optionally
     camera-tracking windows; see ddgi_cascade_* in include/ddgi.h."""

@@ -9,7 +9,10 @@
 // weight tables, probe lists, counters, ray records) lives in the file-scope
 // device arrays below, whose sizes fix the largest volume this entry point
 // accepts.  Every GPU that loads the library holds these arrays (about 17 MiB)
-// until the process exits.
+// until the process exits; they come into being when this file's module is
+// loaded on a device, which the first call on that device triggers.
+// Device-side errors (a non-finite texel) accumulate in a status word of the
+// same kind until ddgi_update_noalloc_poll_status reads and clears it.
 #include <cmath>
 #include <mutex>
 
@@ -183,9 +186,8 @@ extern "C" ddgi_status ddgi_update_noalloc(ddgi_scene scene, const ddgi_volume_d
     cudaStream_t st = (cudaStream_t)stream;
     int sms = sm_count();
     FrameRot rot = frame_rotation(d->seed, params->frame);
-    // the arrays keep the previous call's contents: counters and status start
-    // at zero (the frame setup clears the counters)
-    if ((e = cudaMemsetAsync(s.status, 0, sizeof(uint32_t) * 4, st)) != cudaSuccess) return na_fail(e, "clear status");
+    // the arrays keep the previous call's contents: the frame setup clears the
+    // counters; the status word keeps its flags until it is polled
     if ((e = launch_sf_table(R, s.sf64, st)) != cudaSuccess) return na_fail(e, "ray pattern");
     if ((e = launch_frame_setup(rot, R, d->irr_n, d->dist_n, d->dist_cos_power, s.sf64, s.dirs, s.w_irr,
                                 s.inv_s_irr, s.w_dist, s.inv_s_dist, s.counts, 4, st)) != cudaSuccess)
@@ -204,5 +206,27 @@ extern "C" ddgi_status ddgi_update_noalloc(ddgi_scene scene, const ddgi_volume_d
     if ((e = launch_blend(v, bp, s.w_irr, s.inv_s_irr, s.w_dist, s.inv_s_dist, s.records, s.lists + P,
                           s.counts + 1, s.status, sms * 4, st)) != cudaSuccess)
         return na_fail(e, "blend");
+    return DDGI_OK;
+}
+
+extern "C" ddgi_status ddgi_update_noalloc_poll_status(ddgi_stream stream) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return na_fail(e, "current device");
+    if (dev < 0 || dev >= kNaMaxDevices) return set_error(DDGI_ERR_INVALID_ARG, "device index out of range");
+    NaScratch s;
+    {
+        std::lock_guard<std::mutex> lock(g_na_mutex);
+        if (!g_na_ready[dev]) return DDGI_OK;   // no call on this device yet: nothing was flagged
+        s = g_na_scratch[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t w = 0;
+    if ((e = cudaMemcpyAsync(&w, s.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return na_fail(e, "read status");
+    if ((e = cudaMemsetAsync(s.status, 0, sizeof(uint32_t), st)) != cudaSuccess) return na_fail(e, "clear status");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return na_fail(e, "synchronise");
+    if (w & 2u) return set_error(DDGI_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (w & 1u) return set_error(DDGI_ERR_NUMERIC, "non-finite texel value produced");
     return DDGI_OK;
 }
