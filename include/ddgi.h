@@ -13,9 +13,10 @@
  *     ddgi_last_error() returns a message for the calling thread, and no
  *     output buffer has been written unless stated.
  *   - Pointers named *_dev are CUDA device pointers owned by the caller,
- *     contiguous, 4-byte aligned (16-byte aligned where stated).  Pointers
- *     without the suffix are host pointers; the library copies what it needs
- *     before returning.
+ *     contiguous and 16-byte aligned (the base of any cudaMalloc or torch
+ *     allocation is); a misaligned one gives DDGI_ERR_INVALID_ARG before any
+ *     work is enqueued.  Pointers without the suffix are host pointers; the
+ *     library copies what it needs before returning.
  *   - Device work is enqueued asynchronously on the stream passed as
  *     ddgi_stream (a cudaStream_t; NULL is the legacy default stream).  No
  *     call synchronises the device unless its comment says so.
@@ -322,6 +323,28 @@ ddgi_status ddgi_get_buffer(ddgi_volume volume, int32_t which, void* dst_dev, si
 ddgi_status ddgi_set_buffer(ddgi_volume volume, int32_t which, const void* src_dev, size_t bytes,
                             ddgi_stream stream);
 
+/* Save and restore a volume's state (no counterpart in the paper, which
+ * keeps probes for the lifetime of a level; a checkpoint of the Sec. 6 states
+ * and the Sec. 2.1 atlases): a versioned host blob holding a header (magic
+ * "DDGIVOL1", format version 1, the volume's descriptor, the section sizes,
+ * the update count, an FNV-1a checksum of the payload), then the states
+ * [P] uint8, the irradiance and distance atlases and the probe offsets
+ * [P][4] float exactly as stored on the device.
+ * ddgi_volume_save: host_buf NULL writes the size needed to *bytes and does
+ * nothing else; otherwise *bytes is the buffer's capacity (INVALID_ARG, with
+ * *bytes set to the size needed, if it is too small) and becomes the bytes
+ * written.  Synchronises the stream.
+ * ddgi_volume_load: the blob must come from a volume whose probe counts,
+ * origin, spacing, tile sizes, storage formats and gamma equal this one's
+ * (the fields that fix what the stored bytes mean; hysteresis, seed, rays and
+ * the other update parameters may differ) and pass its checksum; otherwise
+ * INVALID_ARG (UNSUPPORTED for another format version) and the volume is
+ * unchanged.  Synchronises the stream; the next update rebuilds its probe
+ * lists from the loaded states.  An update after a load continues exactly
+ * as it would have on the saved volume. */
+ddgi_status ddgi_volume_save(ddgi_volume volume, void* host_buf, size_t* bytes, ddgi_stream stream);
+ddgi_status ddgi_volume_load(ddgi_volume volume, const void* host_buf, size_t bytes, ddgi_stream stream);
+
 /* Ray records of the last update: records_dev [P*R][4] float (r, g, b, d)
  * in active-list order, probe_ids_dev [P] int32 (the active list), and the
  * active count written to *n_active (host; synchronises the stream). */
@@ -461,6 +484,25 @@ ddgi_status ddgi_diff_backward(ddgi_volume volume, ddgi_scene scene, const ddgi_
                                int64_t n, const float camera_pos[3], const float* dE_dev, float* d_albedo_dev,
                                float* d_emit_dev, ddgi_stream stream);
 
+/* Texel half of the adjoint (the query of Sec. 2.2 with the gamma decode of
+ * Sec. 4.2, differentiated): given dE_dev [n][3] = dLoss/dE at the n points
+ * of a ddgi_query with the same pos_dev, nrm_dev and camera_pos on the
+ * volume's current atlases, writes g_irr_dev [P][(irr_n+2)^2][3] float =
+ * dLoss/d(stored irradiance texel value), bordered tiles in the atlas's
+ * texel order, for every texel (overwritten; zero where no point reads it).
+ * The values are the gamma-encoded ones the atlas stores, decoded from its
+ * storage format.  E depends on irradiance texels only through the bilinear
+ * samples and the decode; its trilinear, backface and Chebyshev weights do
+ * not involve them, so this is the exact gradient (distance texels are not
+ * differentiated).  fold_borders != 0 adds each border texel's gradient to
+ * the interior texel it copies (Sec. 7.1 border copy) and leaves the border
+ * entries zero: the gradient with respect to the interior texels as free
+ * parameters.  Float atomics: the summation order, and so the last bits,
+ * can differ between calls.  Errors: INVALID_ARG, CUDA. */
+ddgi_status ddgi_query_backward(ddgi_volume volume, const float* pos_dev, const float* nrm_dev, int64_t n,
+                                const float camera_pos[3], const float* dE_dev, int32_t fold_borders,
+                                float* g_irr_dev, ddgi_stream stream);
+
 /* ------------------------------------------------------------------ */
 /* Allocation-free update                                              */
 /* ------------------------------------------------------------------ */
@@ -475,8 +517,7 @@ ddgi_status ddgi_diff_backward(ddgi_volume volume, ddgi_scene scene, const ddgi_
  * whose state the caller owns: states_dev [P] uint8, irr_dev and dist_dev the
  * atlases in the layout and formats of `desc` (what ddgi_get_buffer returns
  * for a volume made from the same descriptor; start from zeroed atlases and
- * states UNINIT, or VIGILANT with the state machine off); irr_dev 16-byte
- * and dist_dev 8-byte aligned.  The call allocates
+ * states UNINIT, or VIGILANT with the state machine off).  The call allocates
  * nothing: its scratch (ray pattern, weight tables, probe lists, counters,
  * ray records) lives in fixed arrays of the library, about 17 MiB that every
  * GPU loading the library holds until the process exits.

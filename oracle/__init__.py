@@ -134,6 +134,8 @@ def _declare(lib):
                                      _dp, _dp]
     lib.or_diff.argtypes = [C.POINTER(OrScene), C.POINTER(OrLights), C.POINTER(OrVolume), C.c_int64,
                             C.c_int64, C.c_int64, _dp, _dp, _dp, _dp, _dp, _dp, _dp, C.c_int64, C.c_int64]
+    lib.or_query_texel_grad.argtypes = [C.POINTER(OrVolume), _u8p, _dp, _dp, C.c_int64, _dp, _dp, _dp, _dp,
+                                        C.c_int, _dp]
     lib.or_tracking_scroll.argtypes = [C.POINTER(OrVolume), _dp, _u8p, _dp, _dp]
     lib.or_tracking_scroll.restype = C.c_int64
     lib.or_update_cascade.argtypes = [C.POINTER(OrScene), C.POINTER(OrLights), C.c_int64,
@@ -385,6 +387,23 @@ def query(desc, states, irr, dist, pos, nrm, camera, want_weights=False, shift=(
     lib().or_query(C.byref(v), _ptr(states, _u8p), _ptr(_f64(irr), _dp), _ptr(_f64(dist), _dp),
                    n, _ptr(pos, _dp), _ptr(nrm, _dp), _ptr(cam, _dp), _ptr(out, _dp), _ptr(w, _dp))
     return (out, w) if want_weights else out
+
+
+def query_texel_grad(desc, states, irr, dist, pos, nrm, camera, dE, fold=False, offsets=None):
+    """Gradient of sum(dE * E), E = query(...), with respect to every stored
+    irradiance texel [P, n+2, n+2, 3] (exact: the query's weights do not
+    involve irradiance texels); fold adds border gradients to the interior
+    texels they copy and zeroes the borders."""
+    pos = _f64(pos, (-1, 3))
+    nrm = _f64(nrm, (-1, 3))
+    dE = _f64(dE, (-1, 3))
+    cam = _f64(camera, (3,))
+    g = np.zeros((desc.n_probes, desc.irr_n + 2, desc.irr_n + 2, 3))
+    v = make_volume(desc, offsets=offsets)
+    lib().or_query_texel_grad(C.byref(v), _ptr(states, _u8p), _ptr(_f64(irr), _dp), _ptr(_f64(dist), _dp), len(pos),
+                              _ptr(pos, _dp), _ptr(nrm, _dp), _ptr(cam, _dp), _ptr(dE, _dp), int(bool(fold)),
+                              _ptr(g, _dp))
+    return g
 
 
 def query_glossy(desc, states, irr, dist, pos, nrm, dirs, shift=(0, 0, 0), origin=None, offsets=None):

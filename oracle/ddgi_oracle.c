@@ -1099,6 +1099,34 @@ static void border_fold(double* g_tile, int64_t n, int64_t C) {
                 for (int64_t c = 0; c < C; ++c) TILE(g_tile, N, C, x, y)[c] = 0.0;
 }
 
+/* Texel half of the adjoint: the gradient of sum_q dE_q . E_q, E the query
+ * of Sec. 2.2 at n points (E = pi M, as or_query), with respect to every
+ * stored irradiance texel value (bordered tiles, the gamma-encoded values
+ * the atlas holds): g_irr [P][(irr_n+2)^2][3], overwritten.  The trilinear,
+ * backface and Chebyshev weights do not involve irradiance texels, so this
+ * is the exact gradient.  fold != 0 adds each border texel's gradient to the
+ * interior texel it copies (Sec. 7.1) and zeroes the border entries. */
+void or_query_texel_grad(const or_volume* v, const uint8_t* states, const double* irr, const double* dist,
+                         int64_t n, const double* pos, const double* nrm, const double camera[3],
+                         const double* dE, int fold, double* g_irr) {
+    int64_t P = v->counts[0] * v->counts[1] * v->counts[2], tsi = irr_tile_size(v);
+    memset(g_irr, 0, sizeof(double) * (size_t)(P * tsi));
+    for (int64_t q = 0; q < n; ++q) {
+        const double* x = pos + 3*q;
+        const double* nn = nrm + 3*q;
+        if (nn[0] == 0.0 && nn[1] == 0.0 && nn[2] == 0.0) continue;   /* no surface: E = 0 */
+        double wo[3];
+        sub3(camera, x, wo);
+        double l = len3(wo);
+        if (l < 1e-6) { wo[0] = nn[0]; wo[1] = nn[1]; wo[2] = nn[2]; }
+        else { wo[0] /= l; wo[1] /= l; wo[2] /= l; }
+        double dM[3] = { M_PI * dE[3*q], M_PI * dE[3*q + 1], M_PI * dE[3*q + 2] };
+        query_M_adjoint(v, states, irr, dist, x, nn, wo, dM, g_irr);
+    }
+    if (fold)
+        for (int64_t p = 0; p < P; ++p) border_fold(g_irr + p * tsi, v->irr_n, 3);
+}
+
 /* Forward: n_frames updates (state machine off: every probe traces) from a
  * zero atlas with hysteresis 0, then E at the query points.  Backward: the
  * gradient of sum(dE * E) with respect to emitter radiance [n_em][3] and

@@ -119,6 +119,9 @@ void or_update_cascade(const or_scene* s, const or_lights* L, int64_t n_vol, con
                        uint8_t* const* states, double* const* irr, double* const* dist,
                        const int64_t* n_subset, const int64_t* const* subsets, double* const* rays_out);
 
+void or_query_texel_grad(const or_volume* v, const uint8_t* states, const double* irr, const double* dist,
+                         int64_t n, const double* pos, const double* nrm, const double camera[3],
+                         const double* dE, int fold, double* g_irr);
 void or_diff(const or_scene* s, const or_lights* L, const or_volume* v, int64_t first_frame, int64_t n_frames,
              int64_t n, const double* pos, const double* nrm, const double camera[3], const double* dE,
              double* E_out, double* d_emit, double* d_albedo, int64_t n_emitters, int64_t n_objects);

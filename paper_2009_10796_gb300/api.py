@@ -312,6 +312,31 @@ class Volume:
                                         _ptr(d_em), _stream(stream)))
         return d_alb, d_em[:n_emitters]
 
+    def query_backward(self, pos, nrm, camera, dE, fold_borders=False, stream=None):
+        """dLoss/d(stored irradiance texels) [P, n+2, n+2, 3] float32 of a query
+        at (pos, nrm, camera) on the current atlases, given dE = dLoss/dE [n, 3]
+        (ddgi_query_backward); fold_borders adds border gradients to the
+        interior texels they copy."""
+        N = self.desc.irr_n + 2
+        g = torch.empty((self.n_probes, N, N, 3), dtype=torch.float32, device=pos.device)
+        dE = dE.float().contiguous()
+        check(load().ddgi_query_backward(self.handle, _ptr(pos), _ptr(nrm), pos.shape[0], _f3(camera), _ptr(dE),
+                                         int(bool(fold_borders)), _ptr(g), _stream(stream)))
+        return g
+
+    def save(self, stream=None) -> bytes:
+        """The volume's states, atlases and offsets as a versioned blob (ddgi_volume_save)."""
+        n = C.c_size_t(0)
+        check(load().ddgi_volume_save(self.handle, None, C.byref(n), _stream(stream)))
+        buf = C.create_string_buffer(n.value)
+        check(load().ddgi_volume_save(self.handle, buf, C.byref(n), _stream(stream)))
+        return buf.raw[: n.value]
+
+    def load(self, blob: bytes, stream=None):
+        """Restore a blob from `save` of a volume with the same layout (ddgi_volume_load)."""
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        check(load().ddgi_volume_load(self.handle, buf, len(blob), _stream(stream)))
+
     def enable_timing(self, on=True):
         check(load().ddgi_enable_timing(self.handle, int(bool(on))))
 
@@ -470,6 +495,30 @@ class Cascade:
             self.close()
         except Exception:
             pass
+
+
+class ProbeQuery(torch.autograd.Function):
+    """E = query(irradiance atlas) at fixed points: the volume's query with the
+    FP32 irradiance atlas given as a tensor [P, n+2, n+2, 4] (rgb + the unused
+    lane, the stored layout), differentiable with respect to it through
+    ddgi_query_backward (the unused lane gets zero gradient).  The forward
+    copies the atlas into the volume.
+
+    Usage: ProbeQuery.apply(irr_atlas, volume, pos, nrm, camera)."""
+
+    @staticmethod
+    def forward(ctx, irr_atlas, volume, pos, nrm, camera):
+        if volume.desc.irr_format != _lib.IRR_FP32:
+            raise ValueError("ProbeQuery needs an FP32 irradiance atlas")
+        volume.set_buffer(0, irr_atlas.detach().contiguous())
+        ctx.args = (volume, pos, nrm, camera)
+        return volume.query(pos, nrm, camera)
+
+    @staticmethod
+    def backward(ctx, dE):
+        volume, pos, nrm, camera = ctx.args
+        g = volume.query_backward(pos, nrm, camera, dE)
+        return torch.nn.functional.pad(g, (0, 1)), None, None, None, None
 
 
 class IrradianceField(torch.autograd.Function):

@@ -212,6 +212,10 @@ static VolView make_view(const ddgi_volume_s* v) {
 }
 
 static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+// Caller-owned device buffers start on 16-byte boundaries (the base of any
+// cudaMalloc or torch allocation does); NULL passes, callers check it apart.
+static bool dev16(const void* p) { return aligned(p, 16); }
+static const char* kMisaligned = "device buffers must be 16-byte aligned";
 
 extern "C" {
 
@@ -415,9 +419,9 @@ ddgi_status ddgi_trace(ddgi_scene s, const float* orig_dev, const float* dir_dev
     if (n < 0) return fail(DDGI_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return DDGI_OK;
     if (!orig_dev || !dir_dev || !t_dev || !tri_dev) return fail(DDGI_ERR_INVALID_ARG, "NULL buffer");
-    if (!aligned(orig_dev, 4) || !aligned(dir_dev, 4) || !aligned(t_dev, 4) || !aligned(tri_dev, 4) ||
-        !aligned(backface_dev, 4))
-        return fail(DDGI_ERR_INVALID_ARG, "misaligned buffer");
+    if (!dev16(orig_dev) || !dev16(dir_dev) || !dev16(t_dev) || !dev16(tri_dev) ||
+        !dev16(backface_dev))
+        return fail(DDGI_ERR_INVALID_ARG, kMisaligned);
     DDGI_CK(launch_trace_rays(s->dev, orig_dev, dir_dev, n, t_dev, tri_dev, backface_dev, (cudaStream_t)stream));
     return DDGI_OK;
 }
@@ -428,7 +432,7 @@ ddgi_status ddgi_raycast_gbuffer(ddgi_scene s, const float cam_pos[3], const flo
     if (!s || !cam_pos || !cam_fwd || !cam_up) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
     if (width <= 0 || height <= 0 || !(vfov_deg > 0.0f && vfov_deg < 180.0f))
         return fail(DDGI_ERR_INVALID_ARG, "bad image size or field of view");
-    if (!pos_dev || !nrm_dev || !aligned(pos_dev, 4) || !aligned(nrm_dev, 4))
+    if (!pos_dev || !nrm_dev || !dev16(pos_dev) || !dev16(nrm_dev))
         return fail(DDGI_ERR_INVALID_ARG, "bad output buffer");
     double f[3] = {cam_fwd[0], cam_fwd[1], cam_fwd[2]}, u[3] = {cam_up[0], cam_up[1], cam_up[2]};
     double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
@@ -850,8 +854,8 @@ ddgi_status ddgi_query_glossy(ddgi_volume v, const float* pos_dev, const float* 
     if (!v) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
     if (n < 0) return fail(DDGI_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return DDGI_OK;
-    if (!pos_dev || !nrm_dev || !dir_dev || !out_dev || !aligned(pos_dev, 4) || !aligned(nrm_dev, 4) ||
-        !aligned(dir_dev, 4) || !aligned(out_dev, 4))
+    if (!pos_dev || !nrm_dev || !dir_dev || !out_dev || !dev16(pos_dev) || !dev16(nrm_dev) ||
+        !dev16(dir_dev) || !dev16(out_dev))
         return fail(DDGI_ERR_INVALID_ARG, "bad buffer");
     DDGI_CK(launch_query_glossy(make_view(v), pos_dev, nrm_dev, dir_dev, n, out_dev, (cudaStream_t)stream));
     return DDGI_OK;
@@ -862,7 +866,7 @@ ddgi_status ddgi_query(ddgi_volume v, const float* pos_dev, const float* nrm_dev
     if (!v || !camera_pos) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
     if (n < 0) return fail(DDGI_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return DDGI_OK;
-    if (!pos_dev || !nrm_dev || !out_dev || !aligned(pos_dev, 4) || !aligned(nrm_dev, 4) || !aligned(out_dev, 4))
+    if (!pos_dev || !nrm_dev || !out_dev || !dev16(pos_dev) || !dev16(nrm_dev) || !dev16(out_dev))
         return fail(DDGI_ERR_INVALID_ARG, "bad buffer");
     DDGI_CK(launch_query(make_view(v), pos_dev, nrm_dev, n,
                          make_float3(camera_pos[0], camera_pos[1], camera_pos[2]), out_dev,
@@ -950,6 +954,7 @@ static ddgi_status buffer_of(ddgi_volume v, int32_t which, void** p, size_t* byt
 
 ddgi_status ddgi_get_buffer(ddgi_volume v, int32_t which, void* dst_dev, size_t bytes, ddgi_stream stream) {
     if (!v || !dst_dev) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (!dev16(dst_dev)) return fail(DDGI_ERR_INVALID_ARG, kMisaligned);
     void* p;
     size_t nb;
     ddgi_status s = buffer_of(v, which, &p, &nb);
@@ -961,14 +966,16 @@ ddgi_status ddgi_get_buffer(ddgi_volume v, int32_t which, void* dst_dev, size_t 
 
 ddgi_status ddgi_set_buffer(ddgi_volume v, int32_t which, const void* src_dev, size_t bytes, ddgi_stream stream) {
     if (!v || !src_dev) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (!dev16(src_dev)) return fail(DDGI_ERR_INVALID_ARG, kMisaligned);
     void* p;
     size_t nb;
     ddgi_status s = buffer_of(v, which, &p, &nb);
     if (s != DDGI_OK) return s;
     if (bytes != nb) return fail(DDGI_ERR_INVALID_ARG, "size mismatch: expected " + std::to_string(nb));
     DDGI_CK(cudaMemcpyAsync(p, src_dev, nb, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
-    if (which == 2) {   // restored states may hold UNINIT probes and change the active set
+    if (which == 2) {   // restored states may hold UNINIT or Awake probes and change the active set
         v->uninit_possible = true;
+        v->awake_possible = true;
         v->list_begin = v->list_end = -1;
     }
     return DDGI_OK;
@@ -977,6 +984,7 @@ ddgi_status ddgi_set_buffer(ddgi_volume v, int32_t which, const void* src_dev, s
 ddgi_status ddgi_get_ray_records(ddgi_volume v, float* records_dev, int32_t* probe_ids_dev, int64_t* n_active,
                                  ddgi_stream stream) {
     if (!v || !records_dev || !probe_ids_dev || !n_active) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (!dev16(records_dev) || !dev16(probe_ids_dev)) return fail(DDGI_ERR_INVALID_ARG, kMisaligned);
     cudaStream_t st = (cudaStream_t)stream;
     int32_t cnt = 0;
     DDGI_CK(cudaMemcpyAsync(&cnt, v->counts + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -1404,7 +1412,7 @@ ddgi_status ddgi_cascade_query(ddgi_cascade c, const float* pos_dev, const float
     if (c->updates == 0) return fail(DDGI_ERR_INVALID_ARG, "no cascade update has run");
     if (n < 0) return fail(DDGI_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return DDGI_OK;
-    if (!pos_dev || !nrm_dev || !out_dev || !aligned(pos_dev, 4) || !aligned(nrm_dev, 4) || !aligned(out_dev, 4))
+    if (!pos_dev || !nrm_dev || !out_dev || !dev16(pos_dev) || !dev16(nrm_dev) || !dev16(out_dev))
         return fail(DDGI_ERR_INVALID_ARG, "bad buffer");
     VolSet vs{};
     vs.table = c->d_params->views;
@@ -1417,6 +1425,7 @@ ddgi_status ddgi_cascade_query(ddgi_cascade c, const float* pos_dev, const float
 ddgi_status ddgi_cascade_get_buffer(ddgi_cascade c, int32_t vol, int32_t which, void* dst_dev, size_t bytes,
                                     ddgi_stream stream) {
     if (!c || !dst_dev) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (!dev16(dst_dev)) return fail(DDGI_ERR_INVALID_ARG, kMisaligned);
     if (vol < 0 || vol >= c->n) return fail(DDGI_ERR_INVALID_ARG, "volume index out of range");
     void* p;
     size_t nb;
@@ -1432,6 +1441,7 @@ ddgi_status ddgi_cascade_get_buffer(ddgi_cascade c, int32_t vol, int32_t which, 
 ddgi_status ddgi_cascade_get_ray_records(ddgi_cascade c, float* records_dev, int32_t* entries_dev,
                                          int64_t* n_active, ddgi_stream stream) {
     if (!c || !records_dev || !entries_dev || !n_active) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (!dev16(records_dev) || !dev16(entries_dev)) return fail(DDGI_ERR_INVALID_ARG, kMisaligned);
     if (c->updates == 0) return fail(DDGI_ERR_INVALID_ARG, "no update has run on this cascade");
     cudaStream_t st = (cudaStream_t)stream;
     int32_t cnt = 0;
@@ -1615,7 +1625,7 @@ extern "C" {
 ddgi_status ddgi_scene_set_materials(ddgi_scene s, const float* albedo_dev, const float* emit_dev,
                                      ddgi_stream stream) {
     if (!s) return fail(DDGI_ERR_INVALID_ARG, "scene is NULL");
-    if (!aligned(albedo_dev, 4) || !aligned(emit_dev, 4)) return fail(DDGI_ERR_INVALID_ARG, "misaligned buffer");
+    if (!dev16(albedo_dev) || !dev16(emit_dev)) return fail(DDGI_ERR_INVALID_ARG, kMisaligned);
     DDGI_CK(launch_set_materials(s->albedo, albedo_dev ? s->n_objects : 0, albedo_dev, s->emit,
                                  emit_dev ? s->n_emitters : 0, emit_dev, (cudaStream_t)stream));
     return DDGI_OK;
@@ -1625,6 +1635,7 @@ ddgi_status ddgi_diff_forward(ddgi_volume v, ddgi_scene s, const ddgi_lights* li
                               int32_t n_frames, const float* pos_dev, const float* nrm_dev, int64_t n,
                               const float camera_pos[3], float* out_dev, ddgi_stream stream) {
     if (!v || !s || !lights || !camera_pos) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (!dev16(pos_dev) || !dev16(nrm_dev) || !dev16(out_dev)) return fail(DDGI_ERR_INVALID_ARG, kMisaligned);
     ddgi_status r = diff_check(v, n_frames);
     if (r != DDGI_OK) return r;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1662,6 +1673,8 @@ ddgi_status ddgi_diff_backward(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
     if (!v || !s || !lights || !camera_pos || !d_albedo_dev) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
     if (s->n_emitters > 0 && !d_emit_dev) return fail(DDGI_ERR_INVALID_ARG, "NULL emitter gradient");
     if (n > 0 && (!pos_dev || !nrm_dev || !dE_dev)) return fail(DDGI_ERR_INVALID_ARG, "NULL buffer");
+    if (!dev16(pos_dev) || !dev16(nrm_dev) || !dev16(dE_dev) || !dev16(d_albedo_dev) || !dev16(d_emit_dev))
+        return fail(DDGI_ERR_INVALID_ARG, kMisaligned);
     ddgi_status r = diff_check(v, n_frames);
     if (r != DDGI_OK) return r;
     if ((int)v->snap_irr.size() < n_frames + 1)
@@ -1698,6 +1711,153 @@ ddgi_status ddgi_diff_backward(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
         g = gp;
         gp = t;
     }
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_query_backward(ddgi_volume v, const float* pos_dev, const float* nrm_dev, int64_t n,
+                                const float camera_pos[3], const float* dE_dev, int32_t fold_borders,
+                                float* g_irr_dev, ddgi_stream stream) {
+    if (!v || !camera_pos || !g_irr_dev) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (n < 0) return fail(DDGI_ERR_INVALID_ARG, "n < 0");
+    if (n > 0 && (!pos_dev || !nrm_dev || !dE_dev)) return fail(DDGI_ERR_INVALID_ARG, "NULL buffer");
+    if (!dev16(pos_dev) || !dev16(nrm_dev) || !dev16(dE_dev) || !dev16(g_irr_dev))
+        return fail(DDGI_ERR_INVALID_ARG, kMisaligned);
+    const ddgi_volume_desc& d = v->desc;
+    const int N = d.irr_n + 2;
+    cudaStream_t st = (cudaStream_t)stream;
+    DDGI_CK(cudaMemsetAsync(g_irr_dev, 0, sizeof(float) * 3 * (size_t)N * N * (size_t)v->P, st));
+    if (n > 0)
+        DDGI_CK(launch_query_adjoint(make_view(v), pos_dev, nrm_dev, n,
+                                     make_float3(camera_pos[0], camera_pos[1], camera_pos[2]), dE_dev, g_irr_dev,
+                                     st));
+    if (fold_borders) DDGI_CK(launch_border_fold(g_irr_dev, (int)v->P, d.irr_n, st));
+    return DDGI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Volume save / load: a versioned host blob (header, then states, atlases and
+// probe offsets as stored on the device), guarded by an FNV-1a checksum.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr char kBlobMagic[8] = {'D', 'D', 'G', 'I', 'V', 'O', 'L', '1'};
+constexpr uint32_t kBlobVersion = 1;
+
+struct BlobHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t header_bytes;          // sizeof(BlobHeader)
+    uint32_t desc_bytes;            // sizeof(ddgi_volume_desc)
+    uint32_t reserved;
+    ddgi_volume_desc desc;          // the descriptor of the saved volume
+    int64_t n_probes;
+    int64_t states_bytes, irr_bytes, dist_bytes, offsets_bytes;
+    int64_t updates;                // updates run on the volume before the save
+    uint64_t checksum;              // FNV-1a over the payload that follows the header
+};
+
+uint64_t fnv1a(const uint8_t* p, size_t n, uint64_t h = 1469598103934665603ull) {
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+size_t blob_bytes(const ddgi_volume_s* v) {
+    return sizeof(BlobHeader) + (size_t)v->P + v->irr_bytes + v->dist_bytes + sizeof(float4) * (size_t)v->P;
+}
+
+// The descriptor fields that fix what the stored bytes mean: the grid and
+// its placement, tile sizes, storage formats and the gamma encoding.
+bool blob_compatible(const ddgi_volume_desc& a, const ddgi_volume_desc& b, std::string* why) {
+    for (int k = 0; k < 3; ++k) {
+        if (a.counts[k] != b.counts[k]) { *why = "probe counts differ"; return false; }
+        if (a.origin[k] != b.origin[k] || a.spacing[k] != b.spacing[k]) { *why = "grid placement differs"; return false; }
+    }
+    if (a.irr_n != b.irr_n || a.dist_n != b.dist_n) { *why = "tile sizes differ"; return false; }
+    if (a.irr_format != b.irr_format || a.dist_format != b.dist_format) { *why = "storage formats differ"; return false; }
+    if (a.gamma != b.gamma) { *why = "gamma encodings differ"; return false; }
+    return true;
+}
+
+}  // namespace
+
+ddgi_status ddgi_volume_save(ddgi_volume v, void* host_buf, size_t* bytes, ddgi_stream stream) {
+    if (!v || !bytes) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    const size_t need = blob_bytes(v);
+    if (!host_buf) {
+        *bytes = need;
+        return DDGI_OK;
+    }
+    if (*bytes < need) {
+        *bytes = need;
+        return fail(DDGI_ERR_INVALID_ARG, "buffer too small: " + std::to_string(need) + " bytes needed");
+    }
+    BlobHeader h{};
+    std::memcpy(h.magic, kBlobMagic, sizeof(kBlobMagic));
+    h.version = kBlobVersion;
+    h.header_bytes = sizeof(BlobHeader);
+    h.desc_bytes = sizeof(ddgi_volume_desc);
+    h.desc = v->desc;
+    h.n_probes = v->P;
+    h.states_bytes = v->P;
+    h.irr_bytes = (int64_t)v->irr_bytes;
+    h.dist_bytes = (int64_t)v->dist_bytes;
+    h.offsets_bytes = (int64_t)(sizeof(float4) * (size_t)v->P);
+    h.updates = v->updates;
+    uint8_t* out = (uint8_t*)host_buf + sizeof(BlobHeader);
+    cudaStream_t st = (cudaStream_t)stream;
+    uint8_t* q = out;
+    DDGI_CK(cudaMemcpyAsync(q, v->states, (size_t)h.states_bytes, cudaMemcpyDeviceToHost, st));
+    q += h.states_bytes;
+    DDGI_CK(cudaMemcpyAsync(q, v->irr, (size_t)h.irr_bytes, cudaMemcpyDeviceToHost, st));
+    q += h.irr_bytes;
+    DDGI_CK(cudaMemcpyAsync(q, v->dist, (size_t)h.dist_bytes, cudaMemcpyDeviceToHost, st));
+    q += h.dist_bytes;
+    DDGI_CK(cudaMemcpyAsync(q, v->offsets, (size_t)h.offsets_bytes, cudaMemcpyDeviceToHost, st));
+    DDGI_CK(cudaStreamSynchronize(st));
+    h.checksum = fnv1a(out, need - sizeof(BlobHeader));
+    std::memcpy(host_buf, &h, sizeof(BlobHeader));
+    *bytes = need;
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_volume_load(ddgi_volume v, const void* host_buf, size_t bytes, ddgi_stream stream) {
+    if (!v || !host_buf) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (bytes < sizeof(BlobHeader)) return fail(DDGI_ERR_INVALID_ARG, "blob shorter than its header");
+    BlobHeader h;
+    std::memcpy(&h, host_buf, sizeof(BlobHeader));
+    if (std::memcmp(h.magic, kBlobMagic, sizeof(kBlobMagic)) != 0) return fail(DDGI_ERR_INVALID_ARG, "not a volume blob");
+    if (h.version != kBlobVersion) return fail(DDGI_ERR_UNSUPPORTED, "blob version " + std::to_string(h.version));
+    if (h.header_bytes != sizeof(BlobHeader) || h.desc_bytes != sizeof(ddgi_volume_desc))
+        return fail(DDGI_ERR_INVALID_ARG, "blob header layout differs from this library's");
+    std::string why;
+    if (!blob_compatible(h.desc, v->desc, &why)) return fail(DDGI_ERR_INVALID_ARG, "blob does not fit the volume: " + why);
+    if (h.n_probes != v->P || h.states_bytes != v->P || h.irr_bytes != (int64_t)v->irr_bytes ||
+        h.dist_bytes != (int64_t)v->dist_bytes || h.offsets_bytes != (int64_t)(sizeof(float4) * (size_t)v->P))
+        return fail(DDGI_ERR_INVALID_ARG, "blob sizes do not fit the volume");
+    const size_t need = blob_bytes(v);
+    if (bytes != need) return fail(DDGI_ERR_INVALID_ARG, "blob size " + std::to_string(bytes) + ", expected " +
+                                                             std::to_string(need));
+    const uint8_t* in = (const uint8_t*)host_buf + sizeof(BlobHeader);
+    if (fnv1a(in, need - sizeof(BlobHeader)) != h.checksum) return fail(DDGI_ERR_INVALID_ARG, "blob checksum mismatch");
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint8_t* q = in;
+    DDGI_CK(cudaMemcpyAsync(v->states, q, (size_t)h.states_bytes, cudaMemcpyHostToDevice, st));
+    q += h.states_bytes;
+    DDGI_CK(cudaMemcpyAsync(v->irr, q, (size_t)h.irr_bytes, cudaMemcpyHostToDevice, st));
+    q += h.irr_bytes;
+    DDGI_CK(cudaMemcpyAsync(v->dist, q, (size_t)h.dist_bytes, cudaMemcpyHostToDevice, st));
+    q += h.dist_bytes;
+    DDGI_CK(cudaMemcpyAsync(v->offsets, q, (size_t)h.offsets_bytes, cudaMemcpyHostToDevice, st));
+    // the host buffer may be released once the call returns
+    DDGI_CK(cudaStreamSynchronize(st));
+    v->updates = h.updates;
+    v->uninit_possible = true;      // the loaded states decide; the next update rebuilds its lists
+    v->awake_possible = true;
+    v->list_begin = v->list_end = -1;
     return DDGI_OK;
 }
 

@@ -43,7 +43,11 @@ __device__ void query_M_adjoint(const VolView& v, float3 x, float3 n, float3 wo,
         p8[c] = p;
         w8[c] = 0.0f;
         if (!state_active(v.states[p])) continue;
-        const float3 a = local_to_probe(v, q, base[0] + o0, base[1] + o1, base[2] + o2);
+        float3 a = local_to_probe(v, q, base[0] + o0, base[1] + o1, base[2] + o2);
+        if (v.offsets) {   // the probe's own (moved) position; the cage stays on the grid
+            const float4 po = v.offsets[p];
+            a = f3(a.x - po.x, a.y - po.y, a.z - po.z);
+        }
         float wt = (o0 ? fr[0] : 1.0f - fr[0]) * (o1 ? fr[1] : 1.0f - fr[1]) * (o2 ? fr[2] : 1.0f - fr[2]);
         float3 dp = f3(-(a.x + q.lo.x), -(a.y + q.lo.y), -(a.z + q.lo.z));   // probe - x
         float ldp = length(dp);

@@ -100,8 +100,8 @@ extern "C" ddgi_status ddgi_update_noalloc(ddgi_scene scene, const ddgi_volume_d
     const DevScene* sv = scene_device_view(scene);
     if (!sv || !d || !lights || !params || !states_dev || !irr_dev || !dist_dev)
         return set_error(DDGI_ERR_INVALID_ARG, "NULL argument");
-    if (((uintptr_t)irr_dev % 16) != 0 || ((uintptr_t)dist_dev % 8) != 0)
-        return set_error(DDGI_ERR_INVALID_ARG, "irradiance atlas must be 16-byte, distance atlas 8-byte aligned");
+    if (((uintptr_t)states_dev % 16) != 0 || ((uintptr_t)irr_dev % 16) != 0 || ((uintptr_t)dist_dev % 16) != 0)
+        return set_error(DDGI_ERR_INVALID_ARG, "device buffers must be 16-byte aligned");
     for (int a = 0; a < 3; ++a) {
         if (d->counts[a] < 2) return set_error(DDGI_ERR_INVALID_ARG, "counts must be >= 2");
         if (!(d->spacing[a] > 0.0f) || !std::isfinite(d->spacing[a]) || !std::isfinite(d->origin[a]))

@@ -12,6 +12,7 @@ import pytest
 import oracle
 import test_oracle_converge as conv
 import test_oracle_pins as pins
+import test_oracle_texel_grad as tgrad
 
 BATTERY = [
     lambda: pins.test_spherical_fibonacci_structure(64),
@@ -38,6 +39,8 @@ BATTERY = [
     conv.test_converge_uniform_sky_exact_and_states,
     conv.test_converge_batches_are_distinct_rotations,
     conv.test_converge_enclosing_sphere_moments,
+    lambda: tgrad.test_texel_gradient_matches_central_differences(5.0),
+    tgrad.test_texel_gradient_fold_is_the_interior_gradient,
 ]
 
 MUTATIONS = {
@@ -71,6 +74,12 @@ MUTATIONS = {
     "converge_unencoded": ("e[k] = pow(num_i[4 * t + k] / num_i[4 * t + 3], 1.0 / v->gamma);",
                            "e[k] = num_i[4 * t + k] / num_i[4 * t + 3];"),
     "converge_no_advance": ("states[p] = advanced(states[p]);", "(void)0;"),
+    "texel_grad_gamma_chain": ("double db = da * 0.5 * v->gamma * pow(b[k], 0.5 * v->gamma - 1.0);",
+                               "double db = da * 0.5 * v->gamma;"),
+    "texel_grad_bilinear_swapped": ("g_irr[p * tsi + (by[j] * N + bx[j]) * 3 + k] += db * bw[j];",
+                                    "g_irr[p * tsi + (by[j] * N + bx[j]) * 3 + k] += db * bw[3 - j];"),
+    "texel_grad_fold_corner": ("TILE(g_tile, N, C, n, n)[c] += TILE(g_tile, N, C, 0, 0)[c];",
+                               "TILE(g_tile, N, C, 1, 1)[c] += TILE(g_tile, N, C, 0, 0)[c];"),
 }
 
 
