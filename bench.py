@@ -43,6 +43,11 @@ OPS_PER_WIDE_NODE = 4 * 25 + 5 * 5
 OPS_PER_WIDE_NODE_ANY = 4 * 25
 OPS_PER_TRI = 30
 L2_FLUSH_BYTES = 256 << 20
+TC_BLEND_DOC = {
+    "tf32": "tcgen05 tensor cores: TF32 irradiance, FP32-accurate distance moments (B-side hi/lo split)",
+    "bf16": "tcgen05 tensor cores: BF16 irradiance, FP32-accurate distance moments",
+    "tf32x3": "tcgen05 tensor cores, FP32-accurate: weights and values split hi + lo in TF32, three products",
+}
 # DRAM bytes (read + write) of one k_trace_primary launch on this workload,
 # from the ncu capture in profiles/trace_passes_city.md; set to None whenever
 # the kernel changes until it is captured again
@@ -303,11 +308,13 @@ def run_gpu(args):
         # the same steps again with per-stage events: stage times, the query's
         # time and the primary pass's launch duration for the roofline
         _, query_ms, timings, _ = timed_steps(g.BLEND_FP32, True)
-        mixed = None
+        # the same step with the blend on tensor cores, per precision
+        mixed = {}
         if not args.no_mixed:
-            m_step, _, _, _ = timed_steps(g.BLEND_TF32, False)
-            _, m_query, m_tm, _ = timed_steps(g.BLEND_TF32, True)
-            mixed = (m_step, m_query, m_tm)
+            for name, prec in (("tf32", g.BLEND_TF32), ("bf16", g.BLEND_BF16), ("tf32x3", g.BLEND_TF32X3)):
+                m_step, _, _, _ = timed_steps(prec, False)
+                _, m_query, m_tm, _ = timed_steps(prec, True)
+                mixed[name] = (m_step, m_query, m_tm)
     ms = float(np.mean(step_ms))
     t = torch.tensor([ms], device=dev)
     if world > 1:
@@ -440,16 +447,14 @@ def run_gpu(args):
                            "frac": blend_bytes / (blend_ms * 1e-3) / 1e9 / hbm},
         "roofline_query": {"bound": "hbm", "achieved": q_bytes / (q_ms * 1e-3) / 1e9, "peak": hbm,
                            "unit": "GB/s", "frac": q_bytes / (q_ms * 1e-3) / 1e9 / hbm},
-        "mixed_tf32": None if mixed is None else {
-            "blend": "TF32 irradiance / FP32-accurate distance moments on tcgen05 tensor cores",
-            "ms_per_step": float(np.mean(mixed[0])),
-            "value": rays_per_step / (float(np.mean(mixed[0])) * 1e-3) / 1e9,
-            "blend_ms": mixed[2]["blend"][0] / max(mixed[2]["blend"][1], 1),
-            "blend_hbm_frac": blend_bytes / (mixed[2]["blend"][0] / max(mixed[2]["blend"][1], 1) * 1e-3)
-                              / 1e9 / hbm,
-            "blend_tensor_tflops": blend_flops / (mixed[2]["blend"][0] / max(mixed[2]["blend"][1], 1) * 1e-3)
-                                   / 1e12,
-            "frame_setup_ms": mixed[2]["frame_setup"][0] / max(mixed[2]["frame_setup"][1], 1)},
+        "tensor_blend": {name: {
+            "blend": TC_BLEND_DOC[name],
+            "ms_per_step": float(np.mean(m[0])),
+            "value": rays_per_step / (float(np.mean(m[0])) * 1e-3) / 1e9,
+            "blend_ms": m[2]["blend"][0] / max(m[2]["blend"][1], 1),
+            "blend_hbm_frac": blend_bytes / (m[2]["blend"][0] / max(m[2]["blend"][1], 1) * 1e-3) / 1e9 / hbm,
+            "frame_setup_ms": m[2]["frame_setup"][0] / max(m[2]["frame_setup"][1], 1)}
+            for name, m in mixed.items()},
         "paper_resolution": paper_res,
         "position_optimizer": optimizer,
         "dynamic_objects": dynamic,

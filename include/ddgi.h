@@ -77,7 +77,9 @@ enum {
 enum {
     DDGI_BLEND_FP32 = 0,    /* SIMT float32 */
     DDGI_BLEND_TF32 = 1,    /* tensor cores, TF32 operands, FP32 accumulate */
-    DDGI_BLEND_BF16 = 2     /* tensor cores, BF16 operands, FP32 accumulate */
+    DDGI_BLEND_BF16 = 2,    /* tensor cores, BF16 operands, FP32 accumulate */
+    DDGI_BLEND_TF32X3 = 3   /* tensor cores, FP32-accurate: weights and values split into TF32
+                               high and low parts, hi.hi + hi.lo + lo.hi accumulated in FP32 */
 };
 
 const char* ddgi_last_error(void);

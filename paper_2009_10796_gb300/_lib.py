@@ -21,7 +21,7 @@ STATE_UNINIT, STATE_OFF, STATE_SLEEPING, STATE_NEWLY_VIGILANT, STATE_VIGILANT = 
 STATE_NEWLY_AWAKE, STATE_AWAKE = 5, 6
 IRR_FP32, IRR_FP16, IRR_RGB9E5 = 0, 1, 2
 DIST_FP32, DIST_FP16 = 0, 1
-BLEND_FP32, BLEND_TF32, BLEND_BF16 = 0, 1, 2
+BLEND_FP32, BLEND_TF32, BLEND_BF16, BLEND_TF32X3 = 0, 1, 2, 3
 
 F3 = C.c_float * 3
 

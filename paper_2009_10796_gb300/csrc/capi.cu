@@ -148,8 +148,7 @@ struct ddgi_volume_s {
     std::vector<void*> snap_irr, snap_dist;   // differentiable forward: atlas after each frame
     float* g_irr = nullptr;                // adjoint: texel gradients of two frames
     float* g_prev = nullptr;
-    uint8_t* pack_irr = nullptr;           // tensor-core blend: weight tiles in operand layout
-    uint8_t* pack_dist = nullptr;
+    uint8_t* pack_w = nullptr;             // tensor-core blend: weight tiles in operand layout
     float* inv_irr_r = nullptr;            // 1 / sum of the rounded weights
     float* inv_dist_r = nullptr;
     int64_t updates = 0;
@@ -432,8 +431,8 @@ ddgi_status ddgi_raycast_gbuffer(ddgi_scene s, const float cam_pos[3], const flo
     if (!s || !cam_pos || !cam_fwd || !cam_up) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
     if (width <= 0 || height <= 0 || !(vfov_deg > 0.0f && vfov_deg < 180.0f))
         return fail(DDGI_ERR_INVALID_ARG, "bad image size or field of view");
-    if (!pos_dev || !nrm_dev || !dev16(pos_dev) || !dev16(nrm_dev))
-        return fail(DDGI_ERR_INVALID_ARG, "bad output buffer");
+    if (!pos_dev || !nrm_dev) return fail(DDGI_ERR_INVALID_ARG, "NULL output buffer");
+    if (!dev16(pos_dev) || !dev16(nrm_dev)) return fail(DDGI_ERR_INVALID_ARG, kMisaligned);
     double f[3] = {cam_fwd[0], cam_fwd[1], cam_fwd[2]}, u[3] = {cam_up[0], cam_up[1], cam_up[2]};
     double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
     for (double& c : f) c /= fl;
@@ -494,7 +493,7 @@ void ddgi_volume_destroy(ddgi_volume v) {
     for (void* p : v->snap_irr) cudaFree(p);
     for (void* p : v->snap_dist) cudaFree(p);
     cudaFree(v->g_irr); cudaFree(v->g_prev);
-    cudaFree(v->pack_irr); cudaFree(v->pack_dist); cudaFree(v->inv_irr_r); cudaFree(v->inv_dist_r);
+    cudaFree(v->pack_w); cudaFree(v->inv_irr_r); cudaFree(v->inv_dist_r);
     cudaFree(v->offsets); cudaFree(v->opt_dirs); cudaFree(v->dyn_boxes);
     cudaFree(v->stage);
     cudaFree(v->conv_dirs); cudaFree(v->conv_w_irr); cudaFree(v->conv_inv_irr); cudaFree(v->conv_w_dist);
@@ -574,8 +573,7 @@ ddgi_status ddgi_volume_create(const ddgi_volume_desc* desc, ddgi_volume* out) {
         std::vector<int32_t> perm = ray_order_morton(v->R);
         e = cudaMemcpy(v->perm, perm.data(), sizeof(int32_t) * v->R, cudaMemcpyHostToDevice);
     }
-    A((void**)&v->pack_irr, tc_pack_irr_bytes(v->R));
-    A((void**)&v->pack_dist, tc_pack_dist_bytes(v->R));
+    A((void**)&v->pack_w, tc_pack_bytes(v->R));
     A((void**)&v->inv_irr_r, sizeof(float) * 128);
     A((void**)&v->inv_dist_r, sizeof(float) * 256);
     if (e == cudaSuccess) e = cudaMemset(v->states, desc->state_machine ? DDGI_STATE_UNINIT : DDGI_STATE_VIGILANT, (size_t)v->P);
@@ -683,7 +681,7 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
     if (!v || !s || !lights || !params) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
     if (!(params->irr_hyst_scale >= 0.0f) || !(params->vis_hyst_scale >= 0.0f))
         return fail(DDGI_ERR_INVALID_ARG, "negative hysteresis scale");
-    if (params->blend_precision < DDGI_BLEND_FP32 || params->blend_precision > DDGI_BLEND_BF16)
+    if (params->blend_precision < DDGI_BLEND_FP32 || params->blend_precision > DDGI_BLEND_TF32X3)
         return fail(DDGI_ERR_INVALID_ARG, "unknown blend precision");
     const bool tensor = params->blend_precision != DDGI_BLEND_FP32;
     if (tensor && !tc_blend_supported(v->desc.irr_n, v->desc.dist_n))
@@ -716,9 +714,8 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
                                          keep_list ? v->counts + 4 : v->counts,
                                          keep_list ? kCounterInts - 4 : kCounterInts, st, v->setup_st));
         if (tensor)
-            DDGI_CK(launch_pack_weights(v->w_irr, v->w_dist, v->R, d.irr_n, d.dist_n,
-                                        params->blend_precision == DDGI_BLEND_BF16, v->pack_irr, v->pack_dist,
-                                        v->inv_irr_r, v->inv_dist_r, v->setup_st));
+            DDGI_CK(launch_pack_weights(v->w_irr, v->w_dist, v->R, d.irr_n, d.dist_n, params->blend_precision,
+                                        v->pack_w, v->inv_irr_r, v->inv_dist_r, v->setup_st));
         DDGI_CK(cudaEventRecord(v->ev_weights, v->setup_st));
     }
     // uninitialised probes (none after a full-range update, until states are
@@ -806,9 +803,8 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
     {
         StageTimer tm(v, 3, st);
         if (tensor)
-            DDGI_CK(launch_blend_tc(view, bp, params->blend_precision == DDGI_BLEND_BF16, v->pack_irr, v->pack_dist,
-                                    v->inv_irr_r, v->inv_dist_r, v->records, v->lists + v->P, v->counts + 1,
-                                    v->status, sms, st));
+            DDGI_CK(launch_blend_tc(view, bp, params->blend_precision, v->pack_w, v->inv_irr_r, v->inv_dist_r,
+                                    v->records, v->lists + v->P, v->counts + 1, v->status, sms, st));
         else
             DDGI_CK(launch_blend(view, bp, v->w_irr, v->inv_s_irr, v->w_dist, v->inv_s_dist, v->records,
                                  v->lists + v->P, v->counts + 1, v->status, sms * 4, st));
@@ -854,9 +850,9 @@ ddgi_status ddgi_query_glossy(ddgi_volume v, const float* pos_dev, const float* 
     if (!v) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
     if (n < 0) return fail(DDGI_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return DDGI_OK;
-    if (!pos_dev || !nrm_dev || !dir_dev || !out_dev || !dev16(pos_dev) || !dev16(nrm_dev) ||
-        !dev16(dir_dev) || !dev16(out_dev))
-        return fail(DDGI_ERR_INVALID_ARG, "bad buffer");
+    if (!pos_dev || !nrm_dev || !dir_dev || !out_dev) return fail(DDGI_ERR_INVALID_ARG, "NULL buffer");
+    if (!dev16(pos_dev) || !dev16(nrm_dev) || !dev16(dir_dev) || !dev16(out_dev))
+        return fail(DDGI_ERR_INVALID_ARG, kMisaligned);
     DDGI_CK(launch_query_glossy(make_view(v), pos_dev, nrm_dev, dir_dev, n, out_dev, (cudaStream_t)stream));
     return DDGI_OK;
 }
@@ -866,8 +862,8 @@ ddgi_status ddgi_query(ddgi_volume v, const float* pos_dev, const float* nrm_dev
     if (!v || !camera_pos) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
     if (n < 0) return fail(DDGI_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return DDGI_OK;
-    if (!pos_dev || !nrm_dev || !out_dev || !dev16(pos_dev) || !dev16(nrm_dev) || !dev16(out_dev))
-        return fail(DDGI_ERR_INVALID_ARG, "bad buffer");
+    if (!pos_dev || !nrm_dev || !out_dev) return fail(DDGI_ERR_INVALID_ARG, "NULL buffer");
+    if (!dev16(pos_dev) || !dev16(nrm_dev) || !dev16(out_dev)) return fail(DDGI_ERR_INVALID_ARG, kMisaligned);
     DDGI_CK(launch_query(make_view(v), pos_dev, nrm_dev, n,
                          make_float3(camera_pos[0], camera_pos[1], camera_pos[2]), out_dev,
                          (cudaStream_t)stream));
@@ -1096,7 +1092,7 @@ struct ddgi_cascade_s {
     float4* dirs = nullptr;
     double* sf64 = nullptr;   // [R][3] unrotated ray pattern, double
     float *w_irr = nullptr, *inv_s_irr = nullptr, *w_dist = nullptr, *inv_s_dist = nullptr;
-    uint8_t *pack_irr = nullptr, *pack_dist = nullptr;
+    uint8_t* pack_w = nullptr;
     float *inv_irr_r = nullptr, *inv_dist_r = nullptr;
     FrameParams* d_params = nullptr;
     FrameParams* h_params[2]{};
@@ -1118,8 +1114,8 @@ void cascade_free(ddgi_cascade_s* c) {
     cudaFree(c->shadow_list); cudaFree(c->hit_list); cudaFree(c->perm); cudaFree(c->dirs);
     cudaFree(c->sf64);
     cudaFree(c->w_irr);
-    cudaFree(c->inv_s_irr); cudaFree(c->w_dist); cudaFree(c->inv_s_dist); cudaFree(c->pack_irr);
-    cudaFree(c->pack_dist); cudaFree(c->inv_irr_r); cudaFree(c->inv_dist_r); cudaFree(c->d_params);
+    cudaFree(c->inv_s_irr); cudaFree(c->w_dist); cudaFree(c->inv_s_dist); cudaFree(c->pack_w);
+    cudaFree(c->inv_irr_r); cudaFree(c->inv_dist_r); cudaFree(c->d_params);
     for (int s = 0; s < 2; ++s) {
         if (c->h_params[s]) cudaFreeHost(c->h_params[s]);
         if (c->slot_done[s]) cudaEventDestroy(c->slot_done[s]);
@@ -1210,8 +1206,8 @@ ddgi_status cascade_enqueue(ddgi_cascade_s* c, const DevScene& sc, const Lights&
     DDGI_CK(launch_frame_setup_dev(&c->d_params->rot, c->R, d0.irr_n, d0.dist_n, d0.dist_cos_power, c->sf64, c->dirs,
                                    c->w_irr, c->inv_s_irr, c->w_dist, c->inv_s_dist, c->counts, kCounterInts, st));
     if (tensor)
-        DDGI_CK(launch_pack_weights(c->w_irr, c->w_dist, c->R, d0.irr_n, d0.dist_n, precision == DDGI_BLEND_BF16,
-                                    c->pack_irr, c->pack_dist, c->inv_irr_r, c->inv_dist_r, st));
+        DDGI_CK(launch_pack_weights(c->w_irr, c->w_dist, c->R, d0.irr_n, d0.dist_n, precision, c->pack_w,
+                                    c->inv_irr_r, c->inv_dist_r, st));
     DDGI_CK(launch_build_list_multi(vs, (int)c->total, 0, c->lists, c->counts + 0, st));
     DDGI_CK(launch_classify_multi(sc, vs, c->dirs, c->R, c->perm, c->lists, c->counts + 0, sms * 8, st));
     DDGI_CK(launch_build_list_multi(vs, (int)c->total, 1, c->lists + c->total, c->counts + 1, st));
@@ -1219,9 +1215,8 @@ ddgi_status cascade_enqueue(ddgi_cascade_s* c, const DevScene& sc, const Lights&
                                          c->records, c->shadow_list, c->hit_list, c->shadow_count, sms * c->trace_mult,
                                          st, query_fast_view(c->h_params[slot]->views[0])));
     if (tensor)
-        DDGI_CK(launch_blend_tc_set(vs, true, bp, precision == DDGI_BLEND_BF16, c->pack_irr, c->pack_dist,
-                                    c->inv_irr_r, c->inv_dist_r, c->records, c->lists + c->total, c->counts + 1,
-                                    c->status, sms, st));
+        DDGI_CK(launch_blend_tc_set(vs, true, bp, precision, d0.irr_n, d0.dist_n, c->pack_w, c->inv_irr_r,
+                                    c->inv_dist_r, c->records, c->lists + c->total, c->counts + 1, c->status, sms, st));
     else
         DDGI_CK(launch_blend_set(vs, true, bp, d0.irr_n, d0.dist_n, c->w_irr, c->inv_s_irr, c->w_dist, c->inv_s_dist,
                                  c->records,
@@ -1307,8 +1302,7 @@ ddgi_status ddgi_cascade_create(const ddgi_volume_desc* descs, int32_t n, ddgi_c
     A((void**)&c->inv_s_irr, sizeof(float) * d0.irr_n * d0.irr_n);
     A((void**)&c->w_dist, sizeof(float) * d0.dist_n * d0.dist_n * (size_t)c->R);
     A((void**)&c->inv_s_dist, sizeof(float) * d0.dist_n * d0.dist_n);
-    A((void**)&c->pack_irr, tc_pack_irr_bytes(c->R));
-    A((void**)&c->pack_dist, tc_pack_dist_bytes(c->R));
+    A((void**)&c->pack_w, tc_pack_bytes(c->R));
     A((void**)&c->inv_irr_r, sizeof(float) * 128);
     A((void**)&c->inv_dist_r, sizeof(float) * 256);
     A((void**)&c->d_params, sizeof(FrameParams));
@@ -1341,7 +1335,7 @@ ddgi_status ddgi_cascade_update(ddgi_cascade c, ddgi_scene s, const ddgi_lights*
     if (!c || !s || !lights || !params) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
     if (!(params->irr_hyst_scale >= 0.0f) || !(params->vis_hyst_scale >= 0.0f))
         return fail(DDGI_ERR_INVALID_ARG, "negative hysteresis scale");
-    if (params->blend_precision < DDGI_BLEND_FP32 || params->blend_precision > DDGI_BLEND_BF16)
+    if (params->blend_precision < DDGI_BLEND_FP32 || params->blend_precision > DDGI_BLEND_TF32X3)
         return fail(DDGI_ERR_INVALID_ARG, "unknown blend precision");
     if (params->blend_precision != DDGI_BLEND_FP32 && !tc_blend_supported(c->desc[0].irr_n, c->desc[0].dist_n))
         return fail(DDGI_ERR_UNSUPPORTED, "tensor-core blend needs irr_n^2 <= 128 and dist_n^2 <= 256");
@@ -1412,8 +1406,8 @@ ddgi_status ddgi_cascade_query(ddgi_cascade c, const float* pos_dev, const float
     if (c->updates == 0) return fail(DDGI_ERR_INVALID_ARG, "no cascade update has run");
     if (n < 0) return fail(DDGI_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return DDGI_OK;
-    if (!pos_dev || !nrm_dev || !out_dev || !dev16(pos_dev) || !dev16(nrm_dev) || !dev16(out_dev))
-        return fail(DDGI_ERR_INVALID_ARG, "bad buffer");
+    if (!pos_dev || !nrm_dev || !out_dev) return fail(DDGI_ERR_INVALID_ARG, "NULL buffer");
+    if (!dev16(pos_dev) || !dev16(nrm_dev) || !dev16(out_dev)) return fail(DDGI_ERR_INVALID_ARG, kMisaligned);
     VolSet vs{};
     vs.table = c->d_params->views;
     vs.n = c->n;

@@ -273,20 +273,20 @@ cudaError_t launch_blend_set(const VolSet& vs, bool multi, const BlendParams& bp
                              uint32_t* status, int grid, int probes_per_cta, cudaStream_t st);
 cudaError_t prepare_blend_kernels(int R);
 // tensor-core blend (k_blend_tc.cu)
+// (precision: DDGI_BLEND_TF32, _BF16 or _TF32X3; one packed weight buffer
+// of tc_pack_bytes(R), written per frame by launch_pack_weights)
 int tc_blend_chunks(int R);
-size_t tc_pack_irr_bytes(int R);
-size_t tc_pack_dist_bytes(int R);
+size_t tc_pack_bytes(int R);
 bool tc_blend_supported(int irr_n, int dist_n);
-cudaError_t launch_pack_weights(const float* w_irr, const float* w_dist, int R, int irr_n, int dist_n, int irr_bf16,
-                                uint8_t* a_irr, uint8_t* a_dist, float* inv_irr, float* inv_dist, cudaStream_t st);
-cudaError_t launch_blend_tc(const VolView& v, const BlendParams& bp, int bf16, const uint8_t* a_irr,
-                            const uint8_t* a_dist, const float* inv_irr, const float* inv_dist,
-                            const float4* records, const int32_t* active, const int32_t* count, uint32_t* status,
-                            int grid, cudaStream_t st);
-cudaError_t launch_blend_tc_set(const VolSet& vs, bool multi, const BlendParams& bp, int bf16,
-                                const uint8_t* a_irr, const uint8_t* a_dist, const float* inv_irr,
-                                const float* inv_dist, const float4* records, const int32_t* active,
-                                const int32_t* count, uint32_t* status, int grid, cudaStream_t st);
+cudaError_t launch_pack_weights(const float* w_irr, const float* w_dist, int R, int irr_n, int dist_n, int precision,
+                                uint8_t* pack, float* inv_irr, float* inv_dist, cudaStream_t st);
+cudaError_t launch_blend_tc(const VolView& v, const BlendParams& bp, int precision, const uint8_t* pack,
+                            const float* inv_irr, const float* inv_dist, const float4* records, const int32_t* active,
+                            const int32_t* count, uint32_t* status, int grid, cudaStream_t st);
+cudaError_t launch_blend_tc_set(const VolSet& vs, bool multi, const BlendParams& bp, int precision, int irr_n,
+                                int dist_n, const uint8_t* pack, const float* inv_irr, const float* inv_dist,
+                                const float4* records, const int32_t* active, const int32_t* count, uint32_t* status,
+                                int grid, cudaStream_t st);
 cudaError_t prepare_blend_tc_kernels();
 cudaError_t launch_query_glossy(const VolView& v, const float* pos, const float* nrm, const float* dirs, int64_t n,
                                 float* out, cudaStream_t st);

@@ -2,31 +2,46 @@
 //
 // With one ray pattern per frame shared by every probe, the blend of Sec. 2.3
 // (Eq. 1) is a dense contraction per frame:
-//   irradiance  D_irr[t][(p,c)]  = sum_i W_irr[t][i]  * L[p][i][c]     c in {r, g, b}
-//   distance    D_dist[t][(p,c)] = sum_i W_dist[t][i] * X[p][i][c]     c in {d_hi, d_lo, d2_hi, d2_lo}
-// A persistent CTA (one per SM, 256 threads) takes groups of 32 active probes
-// and walks the rays in chunks of 32:
-//   * the weight tiles of the chunk (pre-packed by k_pack_weights in the
-//     operand layout) arrive by two bulk TMA copies, completion counted on an
+//   irradiance  D_irr[t][(c,p)]  = sum_i W_irr[t][i]  * L[p][i][c]     c in {r, g, b}
+//   distance    D_dist[t][(c,p)] = sum_i W_dist[t][i] * X[p][i][c]     c in {d_hi, d2_hi, d_lo, d2_lo}
+// texels t on the MMA's M side (one 128-row tile of irradiance texels, two of
+// distance texels), probes and channels on N, rays on K.
+//
+// Work split.  One persistent CTA per SM takes an equal, contiguous share of
+// the active list and blends it in rounds of up to PG probes; each round
+// walks the rays in chunks of KC.  Per chunk:
+//   * warp 0 issues bulk copies (TMA, 1D) of the chunk's pre-packed weight
+//     tiles (k_pack_weights: the MMA A operands, L2 resident, shared by all
+//     probes) and of every probe's KC raw ray records (KC x 16 contiguous
+//     bytes each) into one stage of a ring (3 stages for X3, 5 otherwise),
+//     issued ring depth - 1 chunks ahead, completion counted on the stage's
 //     mbarrier;
-//   * the threads stage the chunk's ray records as the B operands;
-//   * one thread issues the MMAs (irradiance M=128 N=96; distance two M=128
-//     tiles, N=128) accumulating in TMEM and commits them to a second mbarrier
-//     that frees the stage (two stages, so staging overlaps the MMAs).
-// The accumulators are read back with tcgen05.ld into shared memory and the
-// epilogue of the SIMT blend finishes each texel (normalise, gamma, per-texel
-// hysteresis, lerp, border copy).
+//   * all threads convert the stage's raw records in shared memory into the
+//     B operands (channel planes, hi / lo splits) of a double-buffered B tile;
+//   * one thread issues the chunk's MMAs into TMEM and commits them to the
+//     stage's second mbarrier, which frees the stage and the B tile.
+// The round's old atlas tiles are prefetched into L2 at its start.  Its
+// epilogue reads the accumulators straight from TMEM (thread = texel row,
+// the two warps of a TMEM lane quarter splitting the probes), loads the old
+// texels of all its probes before computing any, and finishes each texel as
+// the SIMT blend does (normalise, gamma, per-texel hysteresis, lerp, border
+// copies, Sec. 4.2, 4.3, 7.1).  mbarrier parities follow from a chunk
+// counter that runs across rounds.
 //
-// Precision.  Irradiance runs in TF32 or BF16 (one pass).  The distance
-// moments keep FP32 accuracy: d and d^2 enter as hi + lo TF32 pairs (the hi part
-// truncated to TF32, the lo part the exact FP32 remainder) and accumulate in
-// FP32; the weights are TF32, and both moments are normalised by the sum of the
-// same rounded weights, so mu2 - mu^2 remains the variance of one weighted
-// distribution.
+// Precision modes.
+//   TF32: irradiance with TF32 operands; the distance moments keep FP32
+//         accuracy with d and d^2 split into a TF32 high part and the FP32
+//         remainder on the B side; TF32 weights, normalised by the sum of
+//         the same rounded weights (so mu2 - mu^2 stays the variance of one
+//         weighted distribution).
+//   BF16: irradiance with BF16 operands; distance as TF32.
+//   X3:   every contraction FP32-accurate: weights and values both split
+//         into TF32 high and low parts, the three products hi.hi + hi.lo +
+//         lo.hi accumulated in FP32 (the lo.lo term is below 2^-22 of the
+//         product); normalised by the sum of hi + lo.
 //
-// Operand layout: K-major, no swizzle: 8-row x 16-byte core matrices, K chunks
-// of a row group adjacent (LBO = 128 B), row groups after all of a tile's K
-// chunks (SBO = 32 * element size * 8 B).
+// Operand layout: K-major, no swizzle: 8-row x 16-byte core matrices, the K
+// core matrices of a row group adjacent (LBO = 128 B), row groups SBO apart.
 //
 // Every wait on an mbarrier is bounded; when one gives up the kernel sets bit
 // 2 of the status word, drains what it issued (bounded again), frees its TMEM
@@ -39,32 +54,52 @@ namespace ddgi {
 
 namespace {
 
-constexpr int PG = 32;                       // probes per group
-constexpr int KC = 32;                       // rays per chunk
-constexpr int NT = 256;                      // threads per CTA: staging, TMEM readback, epilogue
-constexpr int IRR_N = 3 * PG;                // 96 accumulator columns
-constexpr int DIST_N = 4 * PG;               // 128 accumulator columns
-constexpr uint32_t COL_IRR = 0, COL_DIST0 = 128, COL_DIST1 = 256, TMEM_COLS = 512;
-
-constexpr uint32_t A_IRR_MAX = 128 * KC * 4;          // 16 KB (BF16 uses half)
-constexpr uint32_t A_DIST_BYTES = 256 * KC * 4;       // 32 KB
-constexpr uint32_t OFF_A_IRR = 0;
-constexpr uint32_t OFF_A_DIST = OFF_A_IRR + A_IRR_MAX;
-constexpr uint32_t OFF_B_IRR = OFF_A_DIST + A_DIST_BYTES;
-constexpr uint32_t OFF_B_DIST = OFF_B_IRR + IRR_N * KC * 4;
-constexpr uint32_t STAGE_BYTES = OFF_B_DIST + DIST_N * KC * 4;   // 77,824 B
-// accumulator rows in shared memory for the epilogue, padded by one float so
-// a warp reading one column of consecutive rows hits distinct banks
-constexpr int DIRR_STRIDE = IRR_N + 1;
-constexpr int DDIST_STRIDE = DIST_N + 1;
-// two stages plus slack: an operand read of up to 256 rows from the last
-// tile, and the epilogue's accumulator copy (128 x 97 + 256 x 129 floats),
-// both stay inside the allocation
-constexpr uint32_t SMEM_BYTES = 2 * STAGE_BYTES + 32768;
-constexpr uint32_t OFF_D_DIST = 128 * DIRR_STRIDE * 4;
-static_assert(OFF_D_DIST + 256 * DDIST_STRIDE * 4 <= SMEM_BYTES, "epilogue copy fits");
-
+constexpr int PG = 32;                       // probes per round at most (MMA N columns per channel)
+constexpr int KC = 16;                       // rays per chunk
+constexpr int kMaxNS = 5;                    // weight ring stages, at most
+constexpr int NCW = 8;                       // converter warps
+constexpr int NCT = NCW * 32;                // converter threads: one per (probe slot, ray pair) of a chunk
+constexpr int NT = NCT + 32;                 // plus the control warp (weight copies, MMAs)
+constexpr int NR = 4;                        // raw record ring depth (per-thread asynchronous copies)
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t COL_IRR = 0, COL_DIST0 = 192, COL_DIST1 = 320;
 constexpr uint32_t kWaitLimit = 1u << 22;
+static_assert(NCT == PG * KC / 2, "one converter thread per (probe slot, ray pair)");
+
+enum : int { kTF32 = 0, kBF16 = 1, kX3 = 2 };
+
+// Shared-memory layout and operand shapes of one precision mode: the weight
+// ring (ns stages of one packed chunk), the raw record ring (NR stages, probe
+// rows padded so a warp's 16-byte reads of consecutive probes hit distinct
+// banks), two B tiles.
+template <int MODE>
+struct Tc {
+    static constexpr uint32_t es_irr = MODE == kBF16 ? 2u : 4u;          // irradiance operand element size
+    static constexpr uint32_t irr_hi_bytes = 128 * KC * es_irr;
+    static constexpr uint32_t irr_bytes = MODE == kX3 ? 2 * irr_hi_bytes : irr_hi_bytes;
+    static constexpr uint32_t dist_hi_bytes = 256 * KC * 4;
+    static constexpr uint32_t off_irr_lo = irr_hi_bytes;
+    static constexpr uint32_t off_dist_hi = irr_bytes;
+    static constexpr uint32_t off_dist_lo = irr_bytes + dist_hi_bytes;
+    static constexpr uint32_t a_bytes = irr_bytes + (MODE == kX3 ? 2u : 1u) * dist_hi_bytes;   // one packed chunk
+    static constexpr int ns = MODE == kX3 ? 3 : 5;                       // weight ring depth
+    static constexpr uint32_t raw_stride = KC * 16 + 16;                 // probes 68 words apart
+    static constexpr uint32_t raw_bytes = PG * raw_stride;
+    static constexpr int irr_rows = MODE == kX3 ? 6 * PG : 3 * PG;      // irradiance B rows (MMA N)
+    static constexpr uint32_t b_irr_bytes = irr_rows * KC * es_irr;
+    static constexpr uint32_t b_dist_bytes = 4 * PG * KC * 4;
+    static constexpr uint32_t b_bytes = b_irr_bytes + b_dist_bytes;
+    static constexpr uint32_t off_raw = ns * a_bytes;
+    static constexpr uint32_t off_b = off_raw + NR * raw_bytes;
+    static constexpr uint32_t smem_bytes = off_b + 2 * b_bytes;
+    static constexpr uint32_t sbo_irr = KC * es_irr * 8;
+    static constexpr uint32_t sbo4 = KC * 4 * 8;
+    static constexpr int ksteps_irr = MODE == kBF16 ? KC / 16 : KC / 8;
+    static constexpr int ksteps_dist = KC / 8;
+    static_assert(a_bytes % 1024 == 0 && off_b % 16 == 0 && b_bytes % 16 == 0, "operand alignment");
+    static_assert(smem_bytes <= 227 * 1024, "fits the shared-memory opt-in");
+    static_assert(COL_IRR + irr_rows <= COL_DIST0 && COL_DIST1 + 4 * PG <= TMEM_COLS, "TMEM columns");
+};
 
 __device__ __forceinline__ uint32_t canon(uint32_t row, uint32_t kbyte, uint32_t sbo) {
     return (row >> 3) * sbo + (kbyte >> 4) * 128u + (row & 7u) * 16u + (kbyte & 15u);
@@ -99,6 +134,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Waits for the completion of the phase with this parity, a bounded number
+// of polls; false when it gave up.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     for (uint32_t it = 0; it < kWaitLimit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
@@ -155,20 +192,46 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* out) {
     for (int j = 0; j < 16; ++j) out[j] = __uint_as_float(r[j]);
 }
 
+// Per-thread asynchronous global -> shared copies (16 or 4 bytes; 16-byte
+// copies of invalid sources zero-fill and read nothing).
+__device__ __forceinline__ void cpa16(void* dst, const void* src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ float comp4(float4 v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : v.z); }
+
+// Bytes of one stored texel (DDGI_IRR_* / DDGI_DIST_* formats).
+__device__ __forceinline__ int irr_texel_bytes(int fmt) {
+    return fmt == DDGI_IRR_FP32 ? 16 : (fmt == DDGI_IRR_FP16 ? 8 : 4);
+}
+__device__ __forceinline__ int dist_texel_bytes(int fmt) { return fmt == DDGI_DIST_FP32 ? 8 : 4; }
 
 }  // namespace
 
-// Weight tiles of one frame in the MMA operand layout, chunk after chunk:
-// irradiance rows (128 per chunk) in TF32 (truncated) or BF16 (rounded),
-// distance rows (256 per chunk) in TF32; rows past the texel count and rays
-// past R are zero.  inv_* are 1 / (sum of the rounded weights) per texel, -1 when
-// no ray reaches the texel.  Blocks [0,128) pack irradiance rows, [128,384) distance.
+// Weight tiles of one frame in the MMA operand layout, one block of
+// Tc<MODE>::a_bytes per chunk of KC rays: irradiance rows (128) high part
+// (TF32 truncated, or BF16 rounded), [X3: the TF32 remainder], distance rows
+// (256) TF32 high part, [X3: remainder].  Rows past the texel count and rays
+// past R are zero.  inv_* are 1 / (sum of the weights as the MMAs see them)
+// per texel, -1 when no ray reaches the texel.  Blocks [0,128) pack
+// irradiance rows, [128,384) distance rows.
+template <int MODE>
 __global__ void __launch_bounds__(128) k_pack_weights(const float* __restrict__ w_irr,
                                                       const float* __restrict__ w_dist, int R, int ti, int td,
-                                                      int nchunks, int irr_bf16, uint8_t* __restrict__ a_irr,
-                                                      uint8_t* __restrict__ a_dist, float* __restrict__ inv_irr,
-                                                      float* __restrict__ inv_dist) {
+                                                      int nchunks, uint8_t* __restrict__ pack,
+                                                      float* __restrict__ inv_irr, float* __restrict__ inv_dist) {
+    using C = Tc<MODE>;
     __shared__ double red[128];
     const int b = blockIdx.x;
     const bool is_irr = b < 128;
@@ -179,16 +242,24 @@ __global__ void __launch_bounds__(128) k_pack_weights(const float* __restrict__ 
     for (int k = threadIdx.x; k < KP; k += blockDim.x) {
         float w = 0.0f;
         if (row < valid && k < R) w = is_irr ? w_irr[(int64_t)row * R + k] : w_dist[(int64_t)row * R + k];
-        int c = k / KC, kk = k - c * KC;
-        if (is_irr && irr_bf16) {
-            __nv_bfloat16 h = __float2bfloat16_rn(w);
+        const int c = k / KC, kk = k - c * KC;
+        uint8_t* chunk = pack + (size_t)c * C::a_bytes;
+        if (is_irr && MODE == kBF16) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(w);
             acc += (double)__bfloat162float(h);
-            *reinterpret_cast<__nv_bfloat16*>(a_irr + (size_t)c * (128 * KC * 2) + canon(row, kk * 2, KC * 2 * 8)) = h;
-        } else {
-            float wt = tf32_trunc(w);
-            acc += (double)wt;
-            uint8_t* base = is_irr ? a_irr + (size_t)c * (128 * KC * 4) : a_dist + (size_t)c * (256 * KC * 4);
-            *reinterpret_cast<float*>(base + canon(row, kk * 4, KC * 4 * 8)) = wt;
+            *reinterpret_cast<__nv_bfloat16*>(chunk + canon(row, kk * 2, C::sbo_irr)) = h;
+            continue;
+        }
+        const float hi = tf32_trunc(w);
+        const float lo = tf32_trunc(w - hi);
+        const uint32_t off_hi = is_irr ? canon(row, kk * 4, C::sbo_irr) : C::off_dist_hi + canon(row, kk * 4, C::sbo4);
+        *reinterpret_cast<float*>(chunk + off_hi) = hi;
+        acc += (double)hi;
+        if (MODE == kX3) {
+            const uint32_t off_lo =
+                is_irr ? C::off_irr_lo + canon(row, kk * 4, C::sbo_irr) : C::off_dist_lo + canon(row, kk * 4, C::sbo4);
+            *reinterpret_cast<float*>(chunk + off_lo) = lo;
+            acc += (double)lo;
         }
     }
     red[threadIdx.x] = acc;
@@ -204,33 +275,39 @@ __global__ void __launch_bounds__(128) k_pack_weights(const float* __restrict__ 
     }
 }
 
-template <bool BF16, bool MULTI>
-__global__ void __launch_bounds__(NT, 1) k_blend_tc(VolSet vs, BlendParams bp, const uint8_t* __restrict__ a_irr_pack,
-                                                    const uint8_t* __restrict__ a_dist_pack, int nchunks,
-                                                    const float* __restrict__ inv_irr,
+template <int MODE, bool MULTI>
+__global__ void __launch_bounds__(NT, 1) k_blend_tc(VolSet vs, BlendParams bp, const uint8_t* __restrict__ pack,
+                                                    int nchunks, const float* __restrict__ inv_irr,
                                                     const float* __restrict__ inv_dist,
                                                     const float4* __restrict__ records,
                                                     const int32_t* __restrict__ active,
                                                     const int32_t* __restrict__ count, uint32_t* status) {
+    using C = Tc<MODE>;
+    constexpr int NS = C::ns;
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t full_bar[2];
-    __shared__ __align__(8) uint64_t empty_bar[2];
+    __shared__ __align__(8) uint64_t afull[kMaxNS];     // a weight chunk landed
+    __shared__ __align__(8) uint64_t mma_bar[kMaxNS];   // a chunk's MMAs are done: its weight stage and B tile are free
+    __shared__ __align__(8) uint64_t bfull[2];          // the converters filled a B tile
     __shared__ uint32_t tmem_slot;
+    __shared__ int s_abort;
     __shared__ int s_probe[PG];
     __shared__ int s_newly[PG];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool control = warp == NCW;
     const int R = bp.R;
-    const VolView& v0 = vol_of<MULTI>(vs, 0);   // cascades share R and tile sizes
-    const int ti = v0.irr_n * v0.irr_n, td = v0.dist_n * v0.dist_n;
-    constexpr uint32_t es_irr = BF16 ? 2u : 4u;
-    constexpr uint32_t sbo_irr = KC * es_irr * 8;
-    constexpr uint32_t sbo4 = KC * 4 * 8;
-    constexpr uint32_t a_irr_bytes = 128 * KC * es_irr;
-    constexpr uint32_t idesc_irr = make_idesc(BF16 ? 1u : 2u, 128, IRR_N);
-    constexpr uint32_t idesc_dist = make_idesc(2u, 128, DIST_N);
-    constexpr int ksteps_irr = BF16 ? KC / 16 : KC / 8;
-    constexpr int ksteps_dist = KC / 8;
+    const VolView& v0 = vol_of<MULTI>(vs, 0);   // cascades share R, tile sizes, formats and gamma
+    const int ni = v0.irr_n, nd = v0.dist_n;
+    const int ti = ni * ni, td = nd * nd;
+    const bool two_dist_tiles = td > 128;
+    // epilogue layout (the whole dynamic shared memory, free by then): the
+    // summed accumulators S [texel][channel * PG + probe] (rows padded by one
+    // float), then the round's old tiles T, irradiance then distance
+    constexpr int SI = 3 * PG + 1, SD = 2 * PG + 1;
+    const uint32_t s_bytes = ((uint32_t)(ti * SI + td * SD) * 4u + 15u) & ~15u;
+    const uint32_t tile_i = (uint32_t)(v0.irr_tile * irr_texel_bytes(v0.irr_format));
+    const uint32_t tile_d = (uint32_t)(v0.dist_tile * dist_texel_bytes(v0.dist_format));
+    const int pgr = min(PG, (int)((C::smem_bytes - s_bytes) / (tile_i + tile_d)));   // probes per round
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -239,10 +316,13 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(VolSet vs, BlendParams bp, c
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(&full_bar[0], 1);
-        mbar_init(&full_bar[1], 1);
-        mbar_init(&empty_bar[0], 1);
-        mbar_init(&empty_bar[1], 1);
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&afull[s], 1);
+            mbar_init(&mma_bar[s], 1);
+        }
+        mbar_init(&bfull[0], NCT);
+        mbar_init(&bfull[1], NCT);
+        s_abort = pgr < 1;   // tiles too large for the epilogue (the launcher rejects them first)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -252,197 +332,346 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(VolSet vs, BlendParams bp, c
     const uint32_t tmem = tmem_slot;
     const uint32_t sbase = smem_u32(smem);
 
-    uint32_t full_phase[2] = {0u, 0u}, empty_phase[2] = {0u, 0u};
-    bool empty_pending[2] = {false, false};   // every thread: MMAs committed on this stage, not yet waited
-    bool tma_pending[2] = {false, false};     // thread 0: bulk copies issued, not yet waited
-    bool committed[2] = {false, false};       // thread 0: MMAs committed, completion not yet seen
-    bool abort = false;
     const int n_act = *count;
+    const int per = (n_act + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int lo = (int)blockIdx.x * per, hi = min(n_act, lo + per);
 
-    for (int g0 = blockIdx.x * PG; g0 < n_act; g0 += gridDim.x * PG) {
-        const int np = min(PG, n_act - g0);
-        if (tid < PG) {
-            int e = tid < np ? active[g0 + tid] : 0;
-            s_probe[tid] = e;
-            s_newly[tid] = tid < np &&
-                           state_newly(vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask]);
+    // global chunk index g across rounds: weight stage g % NS, raw stage
+    // g % NR, B tile g & 1, mbarrier parities from the use counts; the
+    // control lane keeps what it issued for the drain after an abort
+    uint32_t gc = 0;
+    int64_t a_issued = -1, a_waited = -1, committed = -1;
+    bool abort = false;
+    const int cp = tid % PG, cpair = tid / PG;   // converter: probe slot, ray pair (rays 2 cpair, 2 cpair + 1)
+
+    auto issue_a = [&](int c, uint32_t g) {   // control lane: weight chunk c
+        const int s = (int)(g % NS);
+        mbar_expect_tx(&afull[s], C::a_bytes);
+        bulk_g2s(sbase + (uint32_t)s * C::a_bytes, pack + (size_t)c * C::a_bytes, C::a_bytes, &afull[s]);
+        a_issued = (int64_t)g;
+    };
+    auto issue_raw = [&](int c, int g0, int np, uint32_t g) {   // converter: its 32 bytes of chunk c
+        if (c < nchunks && cp < np) {
+            const int k = c * KC + 2 * cpair;
+            uint8_t* dst = smem + C::off_raw + (g % NR) * C::raw_bytes + cp * C::raw_stride + cpair * 32;
+            const float4* src = records + (int64_t)(g0 + cp) * R + k;
+            cpa16(dst, k < R ? (const void*)src : (const void*)records, k < R);
+            cpa16(dst + 16, k + 1 < R ? (const void*)(src + 1) : (const void*)records, k + 1 < R);
         }
-        for (int c = 0; c < nchunks; ++c) {
-            const int s = c & 1;
-            abort = __syncthreads_or(abort);
-            if (abort) break;
-            if (empty_pending[s]) {
-                if (!mbar_wait(&empty_bar[s], empty_phase[s])) abort = true;
-                else committed[s] = false;
-                empty_phase[s] ^= 1u;
-                empty_pending[s] = false;
-            }
-            abort = __syncthreads_or(abort);
-            if (abort) break;
-            uint8_t* stage = smem + s * STAGE_BYTES;
-            const uint32_t sstage = sbase + s * STAGE_BYTES;
-            if (tid == 0) {
-                mbar_expect_tx(&full_bar[s], a_irr_bytes + A_DIST_BYTES);
-                bulk_g2s(sstage + OFF_A_IRR, a_irr_pack + (size_t)c * a_irr_bytes, a_irr_bytes, &full_bar[s]);
-                bulk_g2s(sstage + OFF_A_DIST, a_dist_pack + (size_t)c * A_DIST_BYTES, A_DIST_BYTES, &full_bar[s]);
-                tma_pending[s] = true;
-            }
-            // ray records of the chunk -> B operands; a thread takes 4 rays of one probe
-            for (int item = tid; item < PG * (KC / 4); item += NT) {
-                const int pp = item % PG, q = item / PG;
-                float4 rr[4];
+        cpa_commit();   // one group per chunk (empty past the round's chunks)
+    };
+
+    for (int g0 = lo; g0 < hi && !s_abort; g0 += max(pgr, 1)) {
+        const int np = min(pgr, hi - g0);
+        if (tid < PG) {
+            const int e = tid < np ? active[g0 + tid] : 0;
+            s_probe[tid] = e;
+            s_newly[tid] = tid < np && state_newly(vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask]);
+        }
+        __syncthreads();
+        if (control) {
+            // weight copies NS - 1 chunks ahead; per chunk: wait for its
+            // weights and its B tile, issue the MMAs, commit
+            if (lane == 0) {
+                for (int c = 0; c < min(NS - 1, nchunks); ++c) issue_a(c, gc + c);
+                for (int c = 0; c < nchunks; ++c) {
+                    const uint32_t g = gc + c;
+                    const int s = (int)(g % NS), b = (int)(g & 1u);
+                    bool ok = mbar_wait(&afull[s], (g / NS) & 1u);
+                    if (ok) a_waited = (int64_t)g;
+                    ok = ok && mbar_wait(&bfull[b], (g >> 1) & 1u);
+                    if (!ok) {
+                        abort = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    // descriptors of the stage's and the B tile's bases; an
+                    // operand at byte offset o adds o >> 4 to the address field
+                    const uint64_t dA = smem_desc(sbase + (uint32_t)s * C::a_bytes, 128, C::sbo_irr);
+                    const uint64_t dA4 = smem_desc(sbase + (uint32_t)s * C::a_bytes, 128, C::sbo4);
+                    const uint64_t dB = smem_desc(sbase + C::off_b + (uint32_t)b * C::b_bytes, 128, C::sbo_irr);
+                    const uint64_t dB4 = smem_desc(sbase + C::off_b + (uint32_t)b * C::b_bytes, 128, C::sbo4);
+                    constexpr uint32_t id_irr = make_idesc(MODE == kBF16 ? 1u : 2u, 128, C::irr_rows);
+                    constexpr uint32_t id_irr_lo = make_idesc(2u, 128, 3 * PG);
+                    constexpr uint32_t id_dist = make_idesc(2u, 128, 4 * PG);
+                    constexpr uint32_t id_dist_lo = make_idesc(2u, 128, 2 * PG);
+                    const uint32_t first = c > 0 ? 1u : 0u;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    int k = c * KC + 4 * q + j;
-                    rr[j] = (pp < np && k < R) ? __ldg(records + (int64_t)(g0 + pp) * R + k)
-                                               : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                }
+                    for (int k = 0; k < C::ksteps_irr; ++k) {
+                        const uint64_t bdesc = dB + (uint64_t)(k * 256 >> 4);
+                        mma<MODE == kBF16>(tmem + COL_IRR, dA + (uint64_t)(k * 256 >> 4), bdesc, id_irr,
+                                           k > 0 ? 1u : first);
+                        if (MODE == kX3)
+                            mma<false>(tmem + COL_IRR, dA + (uint64_t)((C::off_irr_lo + k * 256) >> 4), bdesc,
+                                       id_irr_lo, 1u);
+                    }
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    uint8_t* dst = stage + OFF_B_IRR + canon(3 * pp + ch, 4 * q * es_irr, sbo_irr);
-                    if (BF16) {
-                        __nv_bfloat162 lo = __floats2bfloat162_rn(comp4(rr[0], ch), comp4(rr[1], ch));
-                        __nv_bfloat162 hi = __floats2bfloat162_rn(comp4(rr[2], ch), comp4(rr[3], ch));
-                        uint2 w;
-                        w.x = *reinterpret_cast<uint32_t*>(&lo);
-                        w.y = *reinterpret_cast<uint32_t*>(&hi);
-                        *reinterpret_cast<uint2*>(dst) = w;
-                    } else {
-                        *reinterpret_cast<float4*>(dst) =
-                            make_float4(comp4(rr[0], ch), comp4(rr[1], ch), comp4(rr[2], ch), comp4(rr[3], ch));
+                    for (int m = 0; m < 2; ++m) {
+                        if (m == 1 && !two_dist_tiles) break;
+#pragma unroll
+                        for (int k = 0; k < C::ksteps_dist; ++k) {
+                            const uint64_t bdesc = dB4 + (uint64_t)((C::b_irr_bytes + k * 256) >> 4);
+                            const uint32_t col = m ? COL_DIST1 : COL_DIST0;
+                            mma<false>(tmem + col, dA4 + (uint64_t)((C::off_dist_hi + m * 8192 + k * 256) >> 4), bdesc,
+                                       id_dist, k > 0 ? 1u : first);
+                            if (MODE == kX3)
+                                mma<false>(tmem + col, dA4 + (uint64_t)((C::off_dist_lo + m * 8192 + k * 256) >> 4),
+                                           bdesc, id_dist_lo, 1u);
+                        }
+                    }
+                    mma_commit(&mma_bar[s]);
+                    committed = (int64_t)g;
+                    // chunk c + NS - 1 into the stage of chunk c - 1 once its MMAs are done
+                    if (c + NS - 1 < nchunks) {
+                        if (c >= 1 && !mbar_wait(&mma_bar[(g - 1) % NS], ((g - 1) / NS) & 1u)) {
+                            abort = true;
+                            break;
+                        }
+                        issue_a(c + NS - 1, g + NS - 1);
                     }
                 }
-                float dh[4], dl[4], qh[4], ql[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float d = rr[j].w, d2 = d * d;
-                    dh[j] = tf32_trunc(d);
-                    dl[j] = d - dh[j];
-                    qh[j] = tf32_trunc(d2);
-                    ql[j] = d2 - qh[j];
-                }
-                *reinterpret_cast<float4*>(stage + OFF_B_DIST + canon(4 * pp + 0, 16 * q, sbo4)) =
-                    make_float4(dh[0], dh[1], dh[2], dh[3]);
-                *reinterpret_cast<float4*>(stage + OFF_B_DIST + canon(4 * pp + 1, 16 * q, sbo4)) =
-                    make_float4(dl[0], dl[1], dl[2], dl[3]);
-                *reinterpret_cast<float4*>(stage + OFF_B_DIST + canon(4 * pp + 2, 16 * q, sbo4)) =
-                    make_float4(qh[0], qh[1], qh[2], qh[3]);
-                *reinterpret_cast<float4*>(stage + OFF_B_DIST + canon(4 * pp + 3, 16 * q, sbo4)) =
-                    make_float4(ql[0], ql[1], ql[2], ql[3]);
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
-                bool ok = mbar_wait(&full_bar[s], full_phase[s]);
-                full_phase[s] ^= 1u;
-                tma_pending[s] = false;
-                if (!ok) {
+        } else {
+            // converters: own records of chunk c (asynchronous copies NR - 1
+            // chunks ahead) -> B tile, once that tile's MMAs two chunks back are done
+            for (int c = 0; c < NR - 1; ++c) issue_raw(c, g0, np, gc + c);
+            for (int c = 0; c < nchunks; ++c) {
+                const uint32_t g = gc + c;
+                const int b = (int)(g & 1u);
+                cpa_wait<NR - 2>();
+                if (c >= 2 && !mbar_wait(&mma_bar[(g - 2) % NS], ((g - 2) / NS) & 1u)) {
                     abort = true;
-                } else {
-                    tc_fence_after();
+                    break;
+                }
+                float4 r0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), r1 = r0;
+                if (cp < np) {
+                    const uint8_t* raw = smem + C::off_raw + (g % NR) * C::raw_bytes + cp * C::raw_stride + cpair * 32;
+                    r0 = *reinterpret_cast<const float4*>(raw);
+                    r1 = *reinterpret_cast<const float4*>(raw + 16);
+                }
+                uint8_t* B = smem + C::off_b + (uint32_t)b * C::b_bytes;
 #pragma unroll
-                    for (int k = 0; k < ksteps_irr; ++k)
-                        mma<BF16>(tmem + COL_IRR, smem_desc(sstage + OFF_A_IRR + k * 256, 128, sbo_irr),
-                                  smem_desc(sstage + OFF_B_IRR + k * 256, 128, sbo_irr), idesc_irr,
-                                  (c > 0 || k > 0) ? 1u : 0u);
+                for (int ch = 0; ch < 3; ++ch) {
+                    const float x0 = comp4(r0, ch), x1 = comp4(r1, ch);
+                    if (MODE == kBF16) {
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+                        *reinterpret_cast<__nv_bfloat162*>(B + canon(ch * PG + cp, 4 * cpair, C::sbo_irr)) = h2;
+                    } else if (MODE == kX3) {
+                        const float2 h = make_float2(tf32_trunc(x0), tf32_trunc(x1));
+                        *reinterpret_cast<float2*>(B + canon(ch * PG + cp, 8 * cpair, C::sbo_irr)) = h;
+                        *reinterpret_cast<float2*>(B + canon((3 + ch) * PG + cp, 8 * cpair, C::sbo_irr)) =
+                            make_float2(x0 - h.x, x1 - h.y);
+                    } else {
+                        *reinterpret_cast<float2*>(B + canon(ch * PG + cp, 8 * cpair, C::sbo_irr)) =
+                            make_float2(x0, x1);
+                    }
+                }
+                {
+                    const float d0 = r0.w, d1 = r1.w, q0 = d0 * d0, q1 = d1 * d1;
+                    const float dh0 = tf32_trunc(d0), dh1 = tf32_trunc(d1), qh0 = tf32_trunc(q0), qh1 = tf32_trunc(q1);
+                    uint8_t* Bd = B + C::b_irr_bytes;
+                    *reinterpret_cast<float2*>(Bd + canon(cp, 8 * cpair, C::sbo4)) = make_float2(dh0, dh1);
+                    *reinterpret_cast<float2*>(Bd + canon(PG + cp, 8 * cpair, C::sbo4)) = make_float2(qh0, qh1);
+                    *reinterpret_cast<float2*>(Bd + canon(2 * PG + cp, 8 * cpair, C::sbo4)) =
+                        make_float2(d0 - dh0, d1 - dh1);
+                    *reinterpret_cast<float2*>(Bd + canon(3 * PG + cp, 8 * cpair, C::sbo4)) =
+                        make_float2(q0 - qh0, q1 - qh1);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&bfull[b]);
+                issue_raw(c + NR - 1, g0, np, g + NR - 1);
+            }
+            cpa_wait<0>();   // no copy lands after this thread moves on
+        }
+        if (abort) s_abort = 1;
+        __syncthreads();
+        if (s_abort) break;
+        // the last chunk's commit covers every MMA of the round
+        if (!mbar_wait(&mma_bar[(gc + nchunks - 1) % NS], ((gc + nchunks - 1) / NS) & 1u)) s_abort = 1;
+        __syncthreads();
+        if (s_abort) break;
+        tc_fence_after();
+
+        // epilogue: the round's old tiles -> T (asynchronous copies, whole
+        // tiles); the accumulators, split parts added, -> S (converter warps:
+        // warp w reads TMEM lanes 32 (w % 4) .. + 31, the columns of probes
+        // 16 (w / 4) .. + 15); new texels and their border copies written in
+        // T in place; T -> the atlases with coalesced 16-byte stores
+        float* S = reinterpret_cast<float*>(smem);
+        float* Sd = S + ti * SI;
+        uint8_t* Ti = smem + s_bytes;
+        uint8_t* Td = Ti + np * tile_i;
+        const bool g16 = (tile_i % 16u) == 0 && (tile_d % 16u) == 0;
+        {
+            const int gran = g16 ? 16 : 4;
+            const int ui = (int)tile_i / gran, ud = (int)tile_d / gran;
+            for (int k = tid; k < np * (ui + ud); k += NT) {
+                const int pp = k / (ui + ud), u = k - pp * (ui + ud);
+                const int e = s_probe[pp];
+                const VolView& v = vol_of<MULTI>(vs, e >> kEntryShift);
+                const int64_t pb = e & kEntryMask;
+                const uint8_t* src = u < ui ? (const uint8_t*)v.irr + pb * tile_i + gran * u
+                                            : (const uint8_t*)v.dist + pb * tile_d + gran * (u - ui);
+                uint8_t* dst = u < ui ? Ti + pp * tile_i + gran * u : Td + pp * tile_d + gran * (u - ui);
+                if (g16) cpa16(dst, src, true);
+                else cpa4(dst, src);
+            }
+            cpa_commit();
+        }
+        if (!control) {
+            const int quarter = warp & 3, half = warp >> 2;
+            const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+            const int row = quarter * 32 + lane;
+            if (quarter * 32 < ti) {
 #pragma unroll
-                    for (int m = 0; m < 2; ++m)
+                for (int ch = 0; ch < 3; ++ch) {
+                    float a[16];
+                    tmem_ld16(tmem + lane_base + COL_IRR + ch * PG + 16 * half, a);
+                    if constexpr (MODE == kX3) {
+                        float l[16];
+                        tmem_ld16(tmem + lane_base + COL_IRR + (3 + ch) * PG + 16 * half, l);
 #pragma unroll
-                        for (int k = 0; k < ksteps_dist; ++k)
-                            mma<false>(tmem + (m ? COL_DIST1 : COL_DIST0),
-                                       smem_desc(sstage + OFF_A_DIST + m * 16384 + k * 256, 128, sbo4),
-                                       smem_desc(sstage + OFF_B_DIST + k * 256, 128, sbo4), idesc_dist,
-                                       (c > 0 || k > 0) ? 1u : 0u);
-                    mma_commit(&empty_bar[s]);
-                    committed[s] = true;
+                        for (int j = 0; j < 16; ++j) a[j] += l[j];
+                    }
+                    if (row < ti)
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) S[row * SI + ch * PG + 16 * half + j] = a[j];
                 }
             }
-            empty_pending[s] = true;
-        }
-        abort = __syncthreads_or(abort);
-        if (abort) break;
-        // all MMAs of the group complete before the accumulators are read
-        for (int s = 0; s < 2; ++s) {
-            if (empty_pending[s]) {
-                if (!mbar_wait(&empty_bar[s], empty_phase[s])) abort = true;
-                else committed[s] = false;
-                empty_phase[s] ^= 1u;
-                empty_pending[s] = false;
-            }
-        }
-        abort = __syncthreads_or(abort);
-        if (abort) break;
-        tc_fence_after();
-        // accumulators -> shared memory (stage buffers are free now); warp w
-        // reads TMEM lanes 32 (w % 4) .. + 31, the two warps of a lane quarter
-        // splitting the columns
-        float* Dirr = reinterpret_cast<float*>(smem);
-        float* Ddist = reinterpret_cast<float*>(smem + OFF_D_DIST);
-        const int quarter = warp & 3, half = warp >> 2;
-        const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-        const int row = quarter * 32 + lane;
-        if (quarter * 32 < ti) {
-            for (int cb = half * (IRR_N / 2); cb < (half + 1) * (IRR_N / 2); cb += 16) {
-                float r16[16];
-                tmem_ld16(tmem + lane_base + COL_IRR + cb, r16);
-                if (row < ti)
+#pragma unroll 1
+            for (int m = 0; m < 2; ++m) {
+                if (m * 128 + quarter * 32 >= td) continue;
+                float d[4][16];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) Dirr[row * DIRR_STRIDE + cb + j] = r16[j];
-            }
-        }
-        for (int m = 0; m < 2; ++m) {
-            if (m * 128 + quarter * 32 >= td) continue;
-            const int drow = m * 128 + row;
-            for (int cb = half * (DIST_N / 2); cb < (half + 1) * (DIST_N / 2); cb += 16) {
-                float r16[16];
-                tmem_ld16(tmem + lane_base + (m ? COL_DIST1 : COL_DIST0) + cb, r16);
-                if (drow < td)
+                for (int gi = 0; gi < 4; ++gi)
+                    tmem_ld16(tmem + lane_base + (m ? COL_DIST1 : COL_DIST0) + gi * PG + 16 * half, d[gi]);
+                const int t = m * 128 + row;
+                if (t < td)
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) Ddist[drow * DDIST_STRIDE + cb + j] = r16[j];
+                    for (int j = 0; j < 16; ++j) {
+                        Sd[t * SD + 16 * half + j] = d[0][j] + d[2][j];        // sum w d   (hi + lo parts)
+                        Sd[t * SD + PG + 16 * half + j] = d[1][j] + d[3][j];   // sum w d^2
+                    }
             }
         }
-        tc_fence_before();
+        cpa_wait<0>();
         __syncthreads();
-        // epilogue: consecutive threads on consecutive texels of one probe,
-        // two texels in flight per thread
-#pragma unroll 2
-        for (int q = tid; q < ti * np; q += NT) {
-            const int pp = q / ti, t = q - pp * ti;
-            const float* a = Dirr + t * DIRR_STRIDE + 3 * pp;
-            const int e = s_probe[pp];
-            blend_irr_texel(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, t, a[0], a[1], a[2],
-                            __ldg(inv_irr + t), s_newly[pp] != 0, status);
-        }
-#pragma unroll 2
-        for (int q = tid; q < td * np; q += NT) {
-            const int pp = q / td, t = q - pp * td;
-            const float* a = Ddist + t * DDIST_STRIDE + 4 * pp;
-            const int e = s_probe[pp];
-            blend_dist_texel(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, t, a[0] + a[1], a[2] + a[3],
-                             __ldg(inv_dist + t), s_newly[pp] != 0, status);
-        }
-        // the next group's bulk copies (async proxy) overwrite what these reads used
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        {
+            VolView vt = v0;   // the round's tiles in T, probe index = round slot
+            vt.irr = Ti;
+            vt.dist = Td;
+            if (v0.irr_format == DDGI_IRR_FP32 && v0.dist_format == DDGI_DIST_FP32) {
+                // FP32 atlases (the default): typed shared-memory tiles
+                float4* Ti4 = reinterpret_cast<float4*>(Ti);
+                float2* Td2 = reinterpret_cast<float2*>(Td);
+                const int wi = ni + 2, wd = nd + 2;
+                for (int q = tid; q < np * ti; q += NT) {
+                    const int pp = (int)fast_div((uint32_t)q, bp.div_ti), t = q - pp * ti;
+                    const int yy = (int)fast_div((uint32_t)t, bp.div_ni), x = 1 + t - yy * ni, y = 1 + yy;
+                    float4* tile = Ti4 + pp * v0.irr_tile;
+                    const float4 o = tile[y * wi + x];
+                    const float* a = S + t * SI + pp;
+                    const float3 e = blend_irr_value_fast(v0, bp, f3(o.x, o.y, o.z), a[0], a[PG], a[2 * PG],
+                                                          __ldg(inv_irr + t), s_newly[pp] != 0, status);
+                    const float4 e4 = make_float4(e.x, e.y, e.z, 0.0f);
+                    tile[y * wi + x] = e4;
+                    for_border_copies(x, y, ni, [&](int bx, int by) { tile[by * wi + bx] = e4; });
+                }
+                for (int q = tid; q < np * td; q += NT) {
+                    const int pp = (int)fast_div((uint32_t)q, bp.div_td), t = q - pp * td;
+                    const int yy = (int)fast_div((uint32_t)t, bp.div_nd), x = 1 + t - yy * nd, y = 1 + yy;
+                    float2* tile = Td2 + pp * v0.dist_tile;
+                    const float* a = Sd + t * SD + pp;
+                    const float2 e = blend_dist_value(bp, tile[y * wd + x], a[0], a[PG], __ldg(inv_dist + t),
+                                                      s_newly[pp] != 0, status);
+                    tile[y * wd + x] = e;
+                    for_border_copies(x, y, nd, [&](int bx, int by) { tile[by * wd + bx] = e; });
+                }
+            } else {
+                // batches of independent items per thread: all their shared-memory
+                // loads first, then the blends and stores
+                constexpr int kUI = 2, kUD = 4;
+                for (int q0 = tid; q0 < np * ti; q0 += kUI * NT) {
+                    float3 old[kUI], sum[kUI];
+                    int pi[kUI], xi[kUI], yi[kUI], tt[kUI];
+    #pragma unroll
+                    for (int u = 0; u < kUI; ++u) {
+                        const int q = min(q0 + u * NT, np * ti - 1);
+                        pi[u] = (int)fast_div((uint32_t)q, bp.div_ti);
+                        tt[u] = q - pi[u] * ti;
+                        const int yy = (int)fast_div((uint32_t)tt[u], bp.div_ni);
+                        xi[u] = 1 + tt[u] - yy * ni;
+                        yi[u] = 1 + yy;
+                        const float* a = S + tt[u] * SI + pi[u];
+                        sum[u] = f3(a[0], a[PG], a[2 * PG]);
+                        old[u] = load_irr<false>(vt, pi[u], xi[u], yi[u]);
+                    }
+    #pragma unroll
+                    for (int u = 0; u < kUI; ++u)
+                        if (q0 + u * NT < np * ti)
+                            store_irr_with_borders(vt, pi[u], xi[u], yi[u],
+                                                   blend_irr_value_fast(vt, bp, old[u], sum[u].x, sum[u].y, sum[u].z,
+                                                                        __ldg(inv_irr + tt[u]), s_newly[pi[u]] != 0,
+                                                                        status));
+                }
+                for (int q0 = tid; q0 < np * td; q0 += kUD * NT) {
+                    float2 old[kUD], mom[kUD];
+                    int pi[kUD], xi[kUD], yi[kUD], tt[kUD];
+    #pragma unroll
+                    for (int u = 0; u < kUD; ++u) {
+                        const int q = min(q0 + u * NT, np * td - 1);
+                        pi[u] = (int)fast_div((uint32_t)q, bp.div_td);
+                        tt[u] = q - pi[u] * td;
+                        const int yy = (int)fast_div((uint32_t)tt[u], bp.div_nd);
+                        xi[u] = 1 + tt[u] - yy * nd;
+                        yi[u] = 1 + yy;
+                        const float* a = Sd + tt[u] * SD + pi[u];
+                        mom[u] = make_float2(a[0], a[PG]);
+                        old[u] = load_dist<false>(vt, pi[u], xi[u], yi[u]);
+                    }
+    #pragma unroll
+                    for (int u = 0; u < kUD; ++u)
+                        if (q0 + u * NT < np * td)
+                            store_dist_with_borders(vt, pi[u], xi[u], yi[u],
+                                                    blend_dist_value(bp, old[u], mom[u].x, mom[u].y,
+                                                                     __ldg(inv_dist + tt[u]), s_newly[pi[u]] != 0,
+                                                                     status));
+                }
+            }
+            }
         __syncthreads();
+        {
+            const int gran = g16 ? 16 : 4;
+            const int ui = (int)tile_i / gran, ud = (int)tile_d / gran;
+            for (int k = tid; k < np * (ui + ud); k += NT) {
+                const int pp = k / (ui + ud), u = k - pp * (ui + ud);
+                const int e = s_probe[pp];
+                const VolView& v = vol_of<MULTI>(vs, e >> kEntryShift);
+                const int64_t pb = e & kEntryMask;
+                uint8_t* dst = u < ui ? (uint8_t*)v.irr + pb * tile_i + gran * u
+                                      : (uint8_t*)v.dist + pb * tile_d + gran * (u - ui);
+                const uint8_t* src = u < ui ? Ti + pp * tile_i + gran * u : Td + pp * tile_d + gran * (u - ui);
+                if (g16) *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
+                else *reinterpret_cast<uint32_t*>(dst) = *reinterpret_cast<const uint32_t*>(src);
+            }
+        }
         if (tid < np && s_newly[tid]) {
             const int e = s_probe[tid];
-            {
-                uint8_t* sp = vol_of<MULTI>(vs, e >> kEntryShift).states + (e & kEntryMask);
-                *sp = state_advanced(*sp);
-            }
+            uint8_t* sp = vol_of<MULTI>(vs, e >> kEntryShift).states + (e & kEntryMask);
+            *sp = state_advanced(*sp);
         }
+        // the next round's weight copies (async proxy) overwrite what these accesses used
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        gc += (uint32_t)nchunks;
         __syncthreads();
     }
-    if (abort) {
-        // a wait gave up: report, then drain (bounded) what this CTA issued
-        if (tid == 0) {
-            atomicOr(status, 2u);
-            for (int s = 0; s < 2; ++s) {
-                if (tma_pending[s]) mbar_wait(&full_bar[s], full_phase[s]);
-                if (committed[s]) mbar_wait(&empty_bar[s], empty_phase[s]);
-            }
-        }
+    if (s_abort && control && lane == 0 && pgr >= 1) {
+        // a wait gave up: report, then drain (bounded) the copies and MMAs this CTA issued
+        atomicOr(status, 2u);
+        for (int64_t g = a_waited + 1; g <= a_issued; ++g) mbar_wait(&afull[g % NS], (uint32_t)(g / NS) & 1u);
+        if (committed >= 0) mbar_wait(&mma_bar[committed % NS], (uint32_t)(committed / NS) & 1u);
     }
+    if (pgr < 1 && tid == 0) atomicOr(status, 2u);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -451,65 +680,91 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(VolSet vs, BlendParams bp, c
 }
 
 int tc_blend_chunks(int R) { return (R + KC - 1) / KC; }
-size_t tc_pack_irr_bytes(int R) { return (size_t)tc_blend_chunks(R) * A_IRR_MAX; }
-size_t tc_pack_dist_bytes(int R) { return (size_t)tc_blend_chunks(R) * A_DIST_BYTES; }
+size_t tc_pack_bytes(int R) { return (size_t)tc_blend_chunks(R) * Tc<kX3>::a_bytes; }
 bool tc_blend_supported(int irr_n, int dist_n) { return irr_n * irr_n <= 128 && dist_n * dist_n <= 256; }
 
-cudaError_t launch_pack_weights(const float* w_irr, const float* w_dist, int R, int irr_n, int dist_n, int irr_bf16,
-                                uint8_t* a_irr, uint8_t* a_dist, float* inv_irr, float* inv_dist, cudaStream_t st) {
-    k_pack_weights<<<384, 128, 0, st>>>(w_irr, w_dist, R, irr_n * irr_n, dist_n * dist_n, tc_blend_chunks(R),
-                                        irr_bf16, a_irr, a_dist, inv_irr, inv_dist);
+// Tensor-core mode of a blend precision (DDGI_BLEND_*).
+static int tc_mode(int precision) {
+    return precision == DDGI_BLEND_BF16 ? kBF16 : (precision == DDGI_BLEND_TF32X3 ? kX3 : kTF32);
+}
+
+cudaError_t launch_pack_weights(const float* w_irr, const float* w_dist, int R, int irr_n, int dist_n, int precision,
+                                uint8_t* pack, float* inv_irr, float* inv_dist, cudaStream_t st) {
+    const int ti = irr_n * irr_n, td = dist_n * dist_n, nch = tc_blend_chunks(R);
+    switch (tc_mode(precision)) {
+        case kBF16:
+            k_pack_weights<kBF16><<<384, 128, 0, st>>>(w_irr, w_dist, R, ti, td, nch, pack, inv_irr, inv_dist);
+            break;
+        case kX3:
+            k_pack_weights<kX3><<<384, 128, 0, st>>>(w_irr, w_dist, R, ti, td, nch, pack, inv_irr, inv_dist);
+            break;
+        default:
+            k_pack_weights<kTF32><<<384, 128, 0, st>>>(w_irr, w_dist, R, ti, td, nch, pack, inv_irr, inv_dist);
+    }
     return cudaGetLastError();
 }
 
-template <bool BF16, bool MULTI>
-static cudaError_t blend_tc(const VolSet& vs, const BlendParams& bp, const uint8_t* a_irr, const uint8_t* a_dist,
-                            const float* inv_irr, const float* inv_dist, const float4* records,
-                            const int32_t* active, const int32_t* count, uint32_t* status, int grid,
-                            cudaStream_t st) {
+template <int MODE, bool MULTI>
+static cudaError_t blend_tc(const VolSet& vs, const BlendParams& bp_in, int irr_n, int dist_n, const uint8_t* pack,
+                            const float* inv_irr,
+                            const float* inv_dist, const float4* records, const int32_t* active, const int32_t* count,
+                            uint32_t* status, int grid, cudaStream_t st) {
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_blend_tc<BF16, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)SMEM_BYTES);
+        cudaError_t e = cudaFuncSetAttribute(k_blend_tc<MODE, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Tc<MODE>::smem_bytes);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_blend_tc<BF16, MULTI><<<grid, NT, SMEM_BYTES, st>>>(vs, bp, a_irr, a_dist, tc_blend_chunks(bp.R), inv_irr,
-                                                          inv_dist, records, active, count, status);
+    BlendParams bp = bp_in;   // the epilogue's divisors: texel counts and tile widths
+    bp.div_ti = make_fast_div((uint32_t)(irr_n * irr_n));
+    bp.div_td = make_fast_div((uint32_t)(dist_n * dist_n));
+    bp.div_ni = make_fast_div((uint32_t)irr_n);
+    bp.div_nd = make_fast_div((uint32_t)dist_n);
+    k_blend_tc<MODE, MULTI><<<grid, NT, Tc<MODE>::smem_bytes, st>>>(vs, bp, pack, tc_blend_chunks(bp.R), inv_irr,
+                                                                     inv_dist, records, active, count, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_blend_tc_set(const VolSet& vs, bool multi, const BlendParams& bp, int bf16,
-                                const uint8_t* a_irr, const uint8_t* a_dist, const float* inv_irr,
-                                const float* inv_dist, const float4* records, const int32_t* active,
-                                const int32_t* count, uint32_t* status, int grid, cudaStream_t st) {
-    if (bf16 && multi)
-        return blend_tc<true, true>(vs, bp, a_irr, a_dist, inv_irr, inv_dist, records, active, count, status, grid, st);
-    if (bf16)
-        return blend_tc<true, false>(vs, bp, a_irr, a_dist, inv_irr, inv_dist, records, active, count, status, grid, st);
-    if (multi)
-        return blend_tc<false, true>(vs, bp, a_irr, a_dist, inv_irr, inv_dist, records, active, count, status, grid, st);
-    return blend_tc<false, false>(vs, bp, a_irr, a_dist, inv_irr, inv_dist, records, active, count, status, grid, st);
+cudaError_t launch_blend_tc_set(const VolSet& vs, bool multi, const BlendParams& bp, int precision, int irr_n,
+                                int dist_n, const uint8_t* pack, const float* inv_irr, const float* inv_dist,
+                                const float4* records, const int32_t* active, const int32_t* count, uint32_t* status,
+                                int grid, cudaStream_t st) {
+#define DDGI_TC_CASE(M, MU)                                                                                          \
+    if (tc_mode(precision) == M && multi == MU)                                                                     \
+        return blend_tc<M, MU>(vs, bp, irr_n, dist_n, pack, inv_irr, inv_dist, records, active, count, status, grid,  \
+                               st);
+    DDGI_TC_CASE(kTF32, false)
+    DDGI_TC_CASE(kTF32, true)
+    DDGI_TC_CASE(kBF16, false)
+    DDGI_TC_CASE(kBF16, true)
+    DDGI_TC_CASE(kX3, false)
+    DDGI_TC_CASE(kX3, true)
+#undef DDGI_TC_CASE
+    return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_blend_tc(const VolView& v, const BlendParams& bp, int bf16, const uint8_t* a_irr,
-                            const uint8_t* a_dist, const float* inv_irr, const float* inv_dist,
-                            const float4* records, const int32_t* active, const int32_t* count, uint32_t* status,
-                            int grid, cudaStream_t st) {
-    return launch_blend_tc_set(single_set(v), false, bp, bf16, a_irr, a_dist, inv_irr, inv_dist, records, active,
-                               count, status, grid, st);
+cudaError_t launch_blend_tc(const VolView& v, const BlendParams& bp, int precision, const uint8_t* pack,
+                            const float* inv_irr, const float* inv_dist, const float4* records, const int32_t* active,
+                            const int32_t* count, uint32_t* status, int grid, cudaStream_t st) {
+    return launch_blend_tc_set(single_set(v), false, bp, precision, v.irr_n, v.dist_n, pack, inv_irr, inv_dist,
+                               records, active, count, status, grid, st);
 }
 
 // Shared-memory opt-in of every tensor-core blend instantiation (outside any stream capture).
 cudaError_t prepare_blend_tc_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(k_blend_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SMEM_BYTES);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_blend_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_blend_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_blend_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    cudaError_t e = cudaSuccess;
+#define DDGI_TC_OPT(M, MU)                                                                                           \
+    if (e == cudaSuccess)                                                                                          \
+        e = cudaFuncSetAttribute(k_blend_tc<M, MU>, cudaFuncAttributeMaxDynamicSharedMemorySize,                   \
+                                 (int)Tc<M>::smem_bytes);
+    DDGI_TC_OPT(kTF32, false)
+    DDGI_TC_OPT(kTF32, true)
+    DDGI_TC_OPT(kBF16, false)
+    DDGI_TC_OPT(kBF16, true)
+    DDGI_TC_OPT(kX3, false)
+    DDGI_TC_OPT(kX3, true)
+#undef DDGI_TC_OPT
     return e;
 }
 
