@@ -249,9 +249,41 @@ def run_gpu(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     camera = cam.position
 
+    # several GPUs (torchrun): the update is sharded by z-slabs of probes,
+    # the updated slabs all-gathered into every GPU's own atlases (NCCL, one
+    # collective per buffer, persistent buffers), the query sharded by pixels
+    # over the replicated atlases; --replicas runs independent copies instead
+    sharded = world > 1 and not args.replicas
+    if sharded:
+        from paper_2009_10796_gb300 import shard
+        ranges = shard.slabs(desc.counts, world)
+        slab = ranges[rank]
+        info = vol.info
+        nb = [info.irr_bytes // desc.n_probes, info.dist_bytes // desc.n_probes, 1]
+        bufs = [torch.empty(info.irr_bytes, dtype=torch.uint8, device=dev),
+                torch.empty(info.dist_bytes, dtype=torch.uint8, device=dev),
+                torch.empty(desc.n_probes, dtype=torch.uint8, device=dev)]
+        exchange = shard.SlabExchange(nb, ranges, rank, dev)
+        cut = [4 * ((n_pix * r // world) // 4) for r in range(world)] + [n_pix]   # 16-byte aligned pixel shards
+        pix = slice(cut[rank], cut[rank + 1])
+    else:
+        pix = slice(0, n_pix)
+    pos_q, nrm_q, out_q = pos[pix], nrm[pix], out[pix]
+
+    def update(frame, precision=g.BLEND_FP32):
+        if not sharded:
+            vol.update(scene, L, frame, precision=precision, stream=stream)
+            return
+        vol.update_range(scene, L, frame, slab[0], slab[1], precision=precision, stream=stream)
+        for k, b in enumerate(bufs):
+            vol.copy_buffer(k, b, stream=stream)
+        exchange(bufs)
+        for k, b in enumerate(bufs):
+            vol.set_buffer(k, b, stream=stream)
+
     def step(frame):
-        vol.update(scene, L, frame, stream=stream)
-        vol.query(pos, nrm, camera, out, stream=stream)
+        update(frame)
+        vol.query(pos_q, nrm_q, camera, out_q, stream=stream)
 
     frame = 0
     for _ in range(args.warmup):
@@ -259,7 +291,11 @@ def run_gpu(args):
         frame += 1
     torch.cuda.synchronize()
     vol.poll_status()
-    n_active = int((vol.states() == g.STATE_VIGILANT).sum().item())
+    states_now = vol.states()
+    n_active = int((states_now == g.STATE_VIGILANT).sum().item())
+    # this GPU's share (the slab it traces and blends, sharded; else all)
+    lo_p, hi_p = slab if sharded else (0, desc.n_probes)
+    n_active_local = int((states_now[lo_p:hi_p] == g.STATE_VIGILANT).sum().item())
     R = desc.rays_per_probe
     stats = vol.trace_stats(scene, L)
 
@@ -283,10 +319,10 @@ def run_gpu(args):
         for k in range(args.steps):
             flush.fill_(float(k))
             evs[k][0].record(stream)
-            vol.update(scene, L, frame, precision=precision, stream=stream)
+            update(frame, precision)
             if stages:
                 qev[k][0].record(stream)
-            vol.query(pos, nrm, camera, out, stream=stream)
+            vol.query(pos_q, nrm_q, camera, out_q, stream=stream)
             if stages:
                 qev[k][1].record(stream)
             evs[k][1].record(stream)
@@ -321,16 +357,20 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
     rays_per_step = n_active * R
-    value = world * rays_per_step / (ms_max * 1e-3) / 1e9
+    # rays of the whole job per step: N replicas each trace the volume; N
+    # shards together trace it once
+    job_rays = (1 if sharded else world) * rays_per_step
+    value = job_rays / (ms_max * 1e-3) / 1e9
 
     # end to end through the C-ABI frame call with host buffers: pinned
     # G-buffer copied in (alongside the probe update), irradiance copied out
     # (chunked behind the query), every step
-    pos_h = pos.cpu().pin_memory()
-    nrm_h = nrm.cpu().pin_memory()
+    pos_h = pos_q.cpu().pin_memory()
+    nrm_h = nrm_q.cpu().pin_memory()
     out_h = torch.empty_like(pos_h).pin_memory()
-    vol.frame_host(scene, L, frame, pos_h, nrm_h, camera, out_h, stream=stream)   # staging allocation
-    frame += 1
+    if not sharded:
+        vol.frame_host(scene, L, frame, pos_h, nrm_h, camera, out_h, stream=stream)   # staging allocation
+        frame += 1
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -339,7 +379,13 @@ def run_gpu(args):
     for k in range(args.steps):   # L2 flushed between steps outside the events
         flush.fill_(float(k))
         eev[k][0].record(stream)
-        vol.frame_host(scene, L, frame, pos_h, nrm_h, camera, out_h, stream=stream)
+        if sharded:   # the rank's pixel shard in from host memory, its irradiance back out
+            pos_q.copy_(pos_h, non_blocking=True)
+            nrm_q.copy_(nrm_h, non_blocking=True)
+            step(frame)
+            out_h.copy_(out_q, non_blocking=True)
+        else:
+            vol.frame_host(scene, L, frame, pos_h, nrm_h, camera, out_h, stream=stream)
         eev[k][1].record(stream)
         frame += 1
     torch.cuda.synchronize()
@@ -347,7 +393,7 @@ def run_gpu(args):
     t = torch.tensor([e2e_ms], device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * rays_per_step / (float(t.item()) * 1e-3) / 1e9
+    e2e_value = job_rays / (float(t.item()) * 1e-3) / 1e9
     vol.poll_status()
 
     # roofline of the dominant kernel, the primary trace pass: its counted FP32
@@ -365,10 +411,9 @@ def run_gpu(args):
     achieved = prim_ops / (prim_ms * 1e-3) / 1e12
     shadow_achieved = shadow_ops / (shadow_ms * 1e-3) / 1e12
     blend_ms = timings["blend"][0] / max(timings["blend"][1], 1)
-    blend_bytes = n_active * (R * 16 + 2000 + 2816)      # records in, old interior in, tiles out
-    blend_flops = n_active * 2 * R * (36 * 3 + 196 * 2)    # the contraction of Eq. 1 (irr + distance moments)
+    blend_bytes = n_active_local * (R * 16 + 2000 + 2816)      # records in, old interior in, tiles out
     q_ms = float(np.mean(query_ms))
-    q_bytes = n_pix * 36                                  # positions + normals in, irradiance out
+    q_bytes = pos_q.shape[0] * 36                         # positions + normals in, irradiance out
     hbm = pk.get("hbm_gbs", 6800.0)
 
     # second-order glossy lookups (Sec. 4.4) at the G-buffer points, the camera
@@ -387,6 +432,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     glossy_ms = float(np.mean([a.elapsed_time(b) for a, b in gev]))
 
+    precision = None if args.no_mixed else run_precision(args, g, torch, stream, scene, L, sc, pos, nrm, camera,
+                                                         flush)
     paper_res = None if args.no_paper_res else run_paper_resolution(args, g, torch, stream, scene, L, pos, nrm,
                                                                      camera, flush)
     optimizer = None if args.no_paper_res else run_optimizer(args, g, torch, stream, scene, L)
@@ -417,7 +464,8 @@ def run_gpu(args):
     launches_per_step = 6
     line = {
         "metric": METRIC, "value": value, "unit": "Grays/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "strong" if sharded else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "probes": desc.n_probes, "active_probes": n_active,
                    "rays_per_probe": R, "query_pixels": n_pix,
@@ -425,9 +473,10 @@ def run_gpu(args):
                    "timing": "value: CUDA events at the step boundaries only; stage_ms, query and the "
                              "roofline launch times: a second pass of the same steps with per-stage "
                              "events on the update stream",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": ("sharded: z-slabs of probes, NCCL all-gather of the updated slabs, "
+                                   "pixel-sharded query" if sharded else ("replicas" if world > 1 else "single GPU"))},
         "update_ms_per_frame": ms - q_ms, "query_ms_1080p": q_ms, "glossy_query_ms_1080p": glossy_ms,
-        "trace_grays_per_s": rays_per_step / (trace_ms_avg * 1e-3) / 1e9,
+        "trace_grays_per_s": n_active_local * R / (trace_ms_avg * 1e-3) / 1e9,
         "stage_ms": {k: v[0] / max(v[1], 1) for k, v in timings.items()},
         "wall_ms_per_step": 1e3 * wall / args.steps,
         "trace_work_per_ray": {"wide_nodes": stats["nodes"] / max(stats["rays"], 1),
@@ -455,14 +504,15 @@ def run_gpu(args):
             "blend_hbm_frac": blend_bytes / (m[2]["blend"][0] / max(m[2]["blend"][1], 1) * 1e-3) / 1e9 / hbm,
             "frame_setup_ms": m[2]["frame_setup"][0] / max(m[2]["frame_setup"][1], 1)}
             for name, m in mixed.items()},
+        "precision_forms": precision,
         "paper_resolution": paper_res,
         "position_optimizer": optimizer,
         "dynamic_objects": dynamic,
         "cascade_batched": cascade,
         "differentiation": diff,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": "Grays/s", "h2d_bytes_per_step": 2 * n_pix * 12,
-                "d2h_bytes_per_step": n_pix * 12},
+        "e2e": {"value": e2e_value, "unit": "Grays/s", "h2d_bytes_per_step": 2 * pos_q.shape[0] * 12,
+                "d2h_bytes_per_step": pos_q.shape[0] * 12},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
     }
@@ -499,11 +549,156 @@ def run_cascade(args, g, torch, stream):
     C.poll_status()
     ms = e0.elapsed_time(e1) / args.steps
     rays = sum(active) * descs[0].rays_per_probe
+    forms = run_cascade_forms(args, g, torch, stream, scene, L, descs, C.tuning())
     return {"workload": "terrain + buildings, 1,048,568 tris; 4 tracking cascades of 32^3 probes at 1/2/4/8 m; "
                         "288 rays/probe; camera 0.6 m/frame",
             "ms_per_frame": ms, "grays_per_s": rays / (ms * 1e-3) / 1e9, "active_probes": active,
             "graph": True, "tuning": {"trace_blocks_per_sm": C.tuning()[0], "blend_probes_per_cta": C.tuning()[1],
-                                      "from_cache": from_cache}}
+                                      "from_cache": from_cache},
+            "forms": forms}
+
+
+def _rel_err(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = np.maximum(np.abs(ref), 1e-3 * max(np.abs(ref).max(), 1e-30))
+    return np.abs(got - ref) / scale
+
+
+def _decoded_irr(g, V):
+    """Stored irradiance texels as float64 [P, n+2, n+2, 3], any storage format."""
+    a = V.irr_atlas().cpu().numpy()
+    if V.desc.irr_format != g.IRR_RGB9E5:
+        return a.astype(np.float64)
+    w = a.astype(np.int64)
+    sc = np.exp2((w >> 27) - 24.0)
+    return np.stack([(w & 511) * sc, ((w >> 9) & 511) * sc, ((w >> 18) & 511) * sc], -1)
+
+
+# precision configurations of the city step: irradiance and distance storage
+# formats, blend arithmetic
+PRECISION_FORMS = {
+    "fp32": ("IRR_FP32", "DIST_FP32", "BLEND_FP32"),
+    "fp16_atlases": ("IRR_FP16", "DIST_FP16", "BLEND_FP32"),
+    "rgb9e5_irradiance": ("IRR_RGB9E5", "DIST_FP32", "BLEND_FP32"),
+    "tf32_blend": ("IRR_FP32", "DIST_FP32", "BLEND_TF32"),
+    "bf16_blend": ("IRR_FP32", "DIST_FP32", "BLEND_BF16"),
+    "tf32x3_blend": ("IRR_FP32", "DIST_FP32", "BLEND_TF32X3"),
+    "mixed_tf32_fp16": ("IRR_FP16", "DIST_FP32", "BLEND_TF32"),
+    "mixed_bf16_rgb9e5": ("IRR_RGB9E5", "DIST_FP32", "BLEND_BF16"),
+}
+
+
+def run_precision(args, g, torch, stream, scene, L, sc, pos, nrm, camera, flush):
+    """The city step (update + 1080p query) in each precision configuration:
+    ms per step, blend and query times, the blend's HBM fraction (algorithmic
+    bytes at the stored texel sizes), and the texel error against the FP64
+    oracle at frame 0 (the oracle's one-step update of 12 seeded active
+    probes; max relative error in the stored, gamma-encoded domain)."""
+    import oracle
+    desc = synth.city_volume()
+    R = desc.rays_per_probe
+    ref = g.Volume(desc)
+    ref.update(scene, L, 0, stream=stream)
+    torch.cuda.synchronize()
+    act = np.nonzero(ref.states().cpu().numpy() == g.STATE_VIGILANT)[0]
+    sample = np.sort(np.random.default_rng(77).choice(act, 12, replace=False))
+    st, irr, dist = oracle.new_state(desc)
+    oracle.update(oracle.SceneHandle(sc), L, desc, 0, st, irr, dist, subset=sample)
+    pk, _ = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    ti, td = desc.irr_n ** 2, desc.dist_n ** 2
+    tile_i, tile_d = (desc.irr_n + 2) ** 2, (desc.dist_n + 2) ** 2
+    out = {}
+    for name, (fi, fd, fb) in PRECISION_FORMS.items():
+        prec = getattr(g, fb)
+        V = g.Volume(desc, irr_format=getattr(g, fi), dist_format=getattr(g, fd))
+        V.update(scene, L, 0, precision=prec, stream=stream)
+        torch.cuda.synchronize()
+        ei = float(_rel_err(_decoded_irr(g, V)[sample], irr[sample]).max())
+        ed = float(_rel_err(V.dist_atlas().cpu().numpy()[sample], dist[sample]).max())
+        res = torch.empty_like(pos)
+        frame = 1
+        for _ in range(args.warmup):
+            V.update(scene, L, frame, precision=prec, stream=stream)
+            V.query(pos, nrm, camera, res, stream=stream)
+            frame += 1
+        torch.cuda.synchronize()
+        n_active = int((V.states() == g.STATE_VIGILANT).sum().item())
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        V.read_timings()
+        V.enable_timing(True)
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            V.update(scene, L, frame, precision=prec, stream=stream)
+            V.query(pos, nrm, camera, res, stream=stream)
+            ev[k][1].record(stream)
+            frame += 1
+        torch.cuda.synchronize()
+        tm = V.read_timings()
+        V.enable_timing(False)
+        V.poll_status()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        blend_ms = tm["blend"][0] / max(tm["blend"][1], 1)
+        ib = {"IRR_FP32": 12, "IRR_FP16": 8, "IRR_RGB9E5": 4}[fi]    # algorithmic bytes per texel
+        db = {"DIST_FP32": 8, "DIST_FP16": 4}[fd]
+        blend_bytes = n_active * (R * 16 + ti * ib + td * db + tile_i * ib + tile_d * db)
+        out[name] = {"irr_format": fi, "dist_format": fd, "blend": fb, "ms_per_step": ms,
+                     "value": n_active * R / (ms * 1e-3) / 1e9, "blend_ms": blend_ms,
+                     "blend_hbm_frac": blend_bytes / (blend_ms * 1e-3) / 1e9 / hbm,
+                     "texel_max_rel_err_vs_oracle": {"irradiance": ei, "distance": ed},
+                     "oracle_sample": "12 seeded active probes, frame 0, one-step FP64 update"}
+    return out
+
+
+def run_cascade_forms(args, g, torch, stream, scene, L, descs, tuning):
+    """The batched cascade frame in other forms, for the batching and
+    precision gains: TF32 and BF16 tensor-core blends (graph), the same
+    launch sequence eager (no graph), and unbatched: each volume its own
+    one-volume cascade with its own launch sequence (graph; hit shading then
+    samples that volume only)."""
+    out = {}
+
+    def timed(cascades, precision, use_graph):
+        frame = 1
+        for _ in range(args.warmup):
+            for C in cascades:
+                C.update(scene, L, frame, synth.terrain_camera_path(frame), precision=precision, use_graph=use_graph,
+                         stream=stream)
+            frame += 1
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            for C in cascades:
+                C.update(scene, L, frame, synth.terrain_camera_path(frame), precision=precision, use_graph=use_graph,
+                         stream=stream)
+            frame += 1
+        e1.record(stream)
+        torch.cuda.synchronize()
+        for C in cascades:
+            C.poll_status()
+        active = sum(int((C.states(k) == g.STATE_VIGILANT).sum().item()) for C in cascades for k in range(C.n))
+        ms = e0.elapsed_time(e1) / args.steps
+        return {"ms_per_frame": ms, "grays_per_s": active * descs[0].rays_per_probe / (ms * 1e-3) / 1e9,
+                "active_probes": active}
+
+    for name, prec in (("tf32_blend", g.BLEND_TF32), ("bf16_blend", g.BLEND_BF16), ("tf32x3_blend", g.BLEND_TF32X3)):
+        C = g.Cascade(descs)
+        C.set_tuning(*tuning)
+        out[name] = timed([C], prec, True)
+    C = g.Cascade(descs)
+    C.set_tuning(*tuning)
+    out["fp32_eager"] = timed([C], g.BLEND_FP32, False)
+    singles = []
+    for d in descs:
+        C1 = g.Cascade([d])
+        C1.set_tuning(*tuning)
+        singles.append(C1)
+    out["fp32_unbatched"] = timed(singles, g.BLEND_FP32, True)
+    return out
 
 
 def run_paper_resolution(args, g, torch, stream, scene, L, pos, nrm, camera, flush):
@@ -676,7 +871,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the TF32 tensor-core blend timing")
+    ap.add_argument("--replicas", action="store_true",
+                    help="several GPUs: independent replicas instead of the sharded update")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the tensor-core blend timings and the precision configurations")
     ap.add_argument("--no-cascade", action="store_true", help="skip the batched cascade workload")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation workload")
     ap.add_argument("--no-paper-res", action="store_true",
@@ -684,6 +882,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        # several GPUs: the headline step only (the other workloads are single-GPU measurements)
+        args.no_mixed = args.no_cascade = args.no_diff = args.no_paper_res = True
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -271,6 +271,11 @@ class Volume:
             return raw.view(torch.float32).view(self.n_probes, n, n, 2)
         return raw.view(torch.float16).view(self.n_probes, n, n, 2).float()
 
+    def copy_buffer(self, which: int, dst: torch.Tensor, stream=None):
+        """Copy buffer `which` (ddgi_get_buffer) into the caller's device tensor."""
+        check(load().ddgi_get_buffer(self.handle, which, _ptr(dst), dst.numel() * dst.element_size(),
+                                     _stream(stream)))
+
     def set_buffer(self, which: int, src: torch.Tensor, stream=None):
         check(load().ddgi_set_buffer(self.handle, which, _ptr(src), src.numel() * src.element_size(),
                                      _stream(stream)))

@@ -6,6 +6,7 @@ import os
 import socket
 
 import numpy as np
+import pytest
 import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
@@ -24,7 +25,7 @@ def _as_bytes(a):
     return torch.from_numpy(a.reshape(-1).view(np.uint8))
 
 
-def _rank(rank, world, port, out_path):
+def _rank(rank, world, port, out_path, persistent=False):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
@@ -38,10 +39,18 @@ def _rank(rank, world, port, out_path):
     ranges = shard.slabs(desc.counts, world)
     P = desc.n_probes
     nb = [irr.nbytes // P, dist_.nbytes // P, 1]
+    ex = shard.SlabExchange(nb, ranges, rank, "cpu") if persistent else None
+    bufs = [_as_bytes(irr), _as_bytes(dist_), _as_bytes(st)]
+    kept = [t.data_ptr() for t in ex.send + ex.recv] if persistent else []
     for frame in range(3):
         b, e = ranges[rank]
         oracle.update(h, L, desc, frame, st, irr, dist_, subset=np.arange(b, e))
-        shard.exchange([_as_bytes(irr), _as_bytes(dist_), _as_bytes(st)], nb, ranges, rank)
+        if persistent:
+            ex(bufs)
+        else:
+            shard.exchange(bufs, nb, ranges, rank)
+    if persistent:   # the same send and receive buffers every frame
+        assert [t.data_ptr() for t in ex.send + ex.recv] == kept
     if rank == 0:
         np.savez(out_path, st=st, irr=irr, dist=dist_)
     dist.barrier()
@@ -57,9 +66,12 @@ def test_slabs_partition_the_grid():
         assert all((e - b) % (counts[0] * counts[1]) == 0 for b, e in r)
 
 
-def test_two_gloo_ranks_match_unsharded_update(tmp_path):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_two_gloo_ranks_match_unsharded_update(tmp_path, persistent):
+    """Both the one-shot exchange and SlabExchange (persistent buffers, one
+    all_gather_into_tensor per buffer) reproduce the unsharded update."""
     out = str(tmp_path / "sharded.npz")
-    mp.start_processes(_rank, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
+    mp.start_processes(_rank, args=(2, _free_port(), out, persistent), nprocs=2, join=True, start_method="spawn")
     got = np.load(out)
     sc = synth.room_scene(n_boxes=10)
     L = synth.room_lights()
