@@ -486,6 +486,33 @@ ddgi_status ddgi_diff_backward(ddgi_volume volume, ddgi_scene scene, const ddgi_
                                int64_t n, const float camera_pos[3], const float* dE_dev, float* d_albedo_dev,
                                float* d_emit_dev, ddgi_stream stream);
 
+/* FP64 instantiation of the differentiable forward and of its reverse pass
+ * (the computation of ddgi_diff_forward / ddgi_diff_backward: Sec. 2.3 hit
+ * shading, Eq. 1 blend with the gamma encoding of Sec. 4.2, the Sec. 7.1
+ * border copy and the Sec. 2.2 query), with every quantity that depends on
+ * the parameters in double precision and the parameters given as double
+ * device arrays: albedo_dev [n_objects][3], emit_dev [n_emitters][3]
+ * (NULL when the scene has no emitter); out_dev [n][3] double gets E.  Hits
+ * and shadow rays keep the FP32 traversal: geometry is a constant of the
+ * parameters, so central differences of this forward check the reverse
+ * pass's arithmetic in FP64.  The reverse pass (after a forward with the
+ * same frames) takes dE_dev [n][3] double and writes d_albedo_dev
+ * [n_objects][3] and d_emit_dev [n_emitters][3] double (overwritten).
+ * Needs the volume of ddgi_diff_forward (hysteresis 0, state machine off,
+ * FP32 atlases) without the position optimizer.  The volume keeps the
+ * double atlases of every frame (allocated by the first call).  Meant for
+ * checking gradients on small volumes; the FP32 calls are the fast path.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+ddgi_status ddgi_diff_forward_f64(ddgi_volume volume, ddgi_scene scene, const ddgi_lights* lights,
+                                  int64_t first_frame, int32_t n_frames, const double* albedo_dev,
+                                  const double* emit_dev, const float* pos_dev, const float* nrm_dev, int64_t n,
+                                  const float camera_pos[3], double* out_dev, ddgi_stream stream);
+ddgi_status ddgi_diff_backward_f64(ddgi_volume volume, ddgi_scene scene, const ddgi_lights* lights,
+                                   int64_t first_frame, int32_t n_frames, const double* albedo_dev,
+                                   const float* pos_dev, const float* nrm_dev, int64_t n, const float camera_pos[3],
+                                   const double* dE_dev, double* d_albedo_dev, double* d_emit_dev,
+                                   ddgi_stream stream);
+
 /* Texel half of the adjoint (the query of Sec. 2.2 with the gamma decode of
  * Sec. 4.2, differentiated): given dE_dev [n][3] = dLoss/dE at the n points
  * of a ddgi_query with the same pos_dev, nrm_dev and camera_pos on the

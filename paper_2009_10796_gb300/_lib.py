@@ -97,6 +97,10 @@ SIGNATURES = {
     "ddgi_volume_save": (C.c_int, [_vp, _vp, C.POINTER(C.c_size_t), _vp]),
     "ddgi_volume_load": (C.c_int, [_vp, _vp, C.c_size_t, _vp]),
     "ddgi_query_backward": (C.c_int, [_vp, _vp, _vp, C.c_int64, F3, _vp, C.c_int32, _vp, _vp]),
+    "ddgi_diff_forward_f64": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.c_int64, C.c_int32, _vp, _vp, _vp, _vp,
+                                        C.c_int64, F3, _vp, _vp]),
+    "ddgi_diff_backward_f64": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.c_int64, C.c_int32, _vp, _vp, _vp,
+                                         C.c_int64, F3, _vp, _vp, _vp, _vp]),
     "ddgi_cascade_create": (C.c_int, [C.POINTER(VolumeDesc), C.c_int32, C.POINTER(_vp)]),
     "ddgi_cascade_destroy": (None, [_vp]),
     "ddgi_cascade_update": (C.c_int, [_vp, _vp, C.POINTER(Lights), C.POINTER(CascadeParams), _vp]),

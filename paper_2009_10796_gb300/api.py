@@ -317,6 +317,31 @@ class Volume:
                                         _ptr(d_em), _stream(stream)))
         return d_alb, d_em[:n_emitters]
 
+    def diff_forward_f64(self, scene: Scene, lights, albedo, emit, pos, nrm, camera, first_frame=0, n_frames=2,
+                         stream=None):
+        """E [n, 3] float64 of the FP64 differentiable forward (ddgi_diff_forward_f64)
+        for albedo [O, 3] and emitter radiance [E, 3] float64 device tensors."""
+        out = torch.empty((pos.shape[0], 3), dtype=torch.float64, device=pos.device)
+        L = lights if isinstance(lights, _lib.Lights) else lights_struct(lights)
+        check(load().ddgi_diff_forward_f64(self.handle, scene.handle, C.byref(L), int(first_frame), int(n_frames),
+                                           _ptr(albedo.contiguous()), _ptr(emit.contiguous()) if emit.numel() else None,
+                                           _ptr(pos), _ptr(nrm), pos.shape[0], _f3(camera), _ptr(out),
+                                           _stream(stream)))
+        return out
+
+    def diff_backward_f64(self, scene: Scene, lights, albedo, pos, nrm, camera, dE, n_emitters, first_frame=0,
+                          n_frames=2, stream=None):
+        """(dLoss/d albedo, dLoss/d emitter radiance) float64 of the FP64 reverse
+        pass (ddgi_diff_backward_f64) for dE = dLoss/dE [n, 3] float64."""
+        d_alb = torch.empty((albedo.shape[0], 3), dtype=torch.float64, device=pos.device)
+        d_em = torch.empty((max(n_emitters, 1), 3), dtype=torch.float64, device=pos.device)
+        L = lights if isinstance(lights, _lib.Lights) else lights_struct(lights)
+        check(load().ddgi_diff_backward_f64(self.handle, scene.handle, C.byref(L), int(first_frame), int(n_frames),
+                                            _ptr(albedo.contiguous()), _ptr(pos), _ptr(nrm), pos.shape[0],
+                                            _f3(camera), _ptr(dE.double().contiguous()), _ptr(d_alb), _ptr(d_em),
+                                            _stream(stream)))
+        return d_alb, d_em[:n_emitters]
+
     def query_backward(self, pos, nrm, camera, dE, fold_borders=False, stream=None):
         """dLoss/d(stored irradiance texels) [P, n+2, n+2, 3] float32 of a query
         at (pos, nrm, camera) on the current atlases, given dE = dLoss/dE [n, 3]

@@ -146,6 +146,10 @@ struct ddgi_volume_s {
     int32_t* shadow_count = nullptr;
     int32_t* perm = nullptr;               // [R] ray order within a probe's warps
     std::vector<void*> snap_irr, snap_dist;   // differentiable forward: atlas after each frame
+    // its FP64 instantiation: atlases after each frame, ray records, texel
+    // gradients of two frames, per-ray radiance gradients, weight row sums
+    std::vector<double*> snap64_irr, snap64_dist;
+    double *rec64 = nullptr, *g64 = nullptr, *g64_prev = nullptr, *gL64 = nullptr, *sw64 = nullptr;
     float* g_irr = nullptr;                // adjoint: texel gradients of two frames
     float* g_prev = nullptr;
     uint8_t* pack_w = nullptr;             // tensor-core blend: weight tiles in operand layout
@@ -495,6 +499,9 @@ void ddgi_volume_destroy(ddgi_volume v) {
     cudaFree(v->g_irr); cudaFree(v->g_prev);
     cudaFree(v->pack_w); cudaFree(v->inv_irr_r); cudaFree(v->inv_dist_r);
     cudaFree(v->offsets); cudaFree(v->opt_dirs); cudaFree(v->dyn_boxes);
+    for (double* q : v->snap64_irr) cudaFree(q);
+    for (double* q : v->snap64_dist) cudaFree(q);
+    cudaFree(v->rec64); cudaFree(v->g64); cudaFree(v->g64_prev); cudaFree(v->gL64); cudaFree(v->sw64);
     cudaFree(v->stage);
     cudaFree(v->conv_dirs); cudaFree(v->conv_w_irr); cudaFree(v->conv_inv_irr); cudaFree(v->conv_w_dist);
     cudaFree(v->conv_inv_dist); cudaFree(v->conv_acc_irr); cudaFree(v->conv_acc_dist); cudaFree(v->conv_den);
@@ -1704,6 +1711,118 @@ ddgi_status ddgi_diff_backward(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
         float* t = g;
         g = gp;
         gp = t;
+    }
+    return DDGI_OK;
+}
+
+static Diff64Volume diff64_volume(const ddgi_volume_s* v) {
+    const ddgi_volume_desc& d = v->desc;
+    Diff64Volume dv{};
+    for (int a = 0; a < 3; ++a) {
+        dv.origin[a] = d.origin[a];
+        dv.spacing[a] = d.spacing[a];
+        dv.counts[a] = d.counts[a];
+    }
+    dv.R = v->R;
+    dv.irr_n = d.irr_n;
+    dv.dist_n = d.dist_n;
+    dv.bias = d.self_shadow_bias;
+    dv.gamma = d.gamma;
+    dv.t_max = v->t_max;
+    dv.cos_power = d.dist_cos_power;
+    return dv;
+}
+
+static size_t irr64_bytes(const ddgi_volume_s* v) {
+    return sizeof(double) * 3 * (size_t)(v->desc.irr_n + 2) * (v->desc.irr_n + 2) * (size_t)v->P;
+}
+static size_t dist64_bytes(const ddgi_volume_s* v) {
+    return sizeof(double) * 2 * (size_t)(v->desc.dist_n + 2) * (v->desc.dist_n + 2) * (size_t)v->P;
+}
+
+ddgi_status ddgi_diff_forward_f64(ddgi_volume v, ddgi_scene s, const ddgi_lights* lights, int64_t first_frame,
+                                  int32_t n_frames, const double* albedo_dev, const double* emit_dev,
+                                  const float* pos_dev, const float* nrm_dev, int64_t n, const float camera_pos[3],
+                                  double* out_dev, ddgi_stream stream) {
+    if (!v || !s || !lights || !camera_pos || !albedo_dev) return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (s->n_emitters > 0 && !emit_dev) return fail(DDGI_ERR_INVALID_ARG, "NULL emitter radiance");
+    if (n < 0) return fail(DDGI_ERR_INVALID_ARG, "n < 0");
+    if (n > 0 && (!pos_dev || !nrm_dev || !out_dev)) return fail(DDGI_ERR_INVALID_ARG, "NULL buffer");
+    if (!dev16(albedo_dev) || !dev16(emit_dev) || !dev16(pos_dev) || !dev16(nrm_dev) || !dev16(out_dev))
+        return fail(DDGI_ERR_INVALID_ARG, kMisaligned);
+    if (v->desc.optimizer_iters != 0) return fail(DDGI_ERR_UNSUPPORTED, "no probe offsets in the FP64 path");
+    ddgi_status r = diff_check(v, n_frames);
+    if (r != DDGI_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    while ((int)v->snap64_irr.size() < n_frames + 1) {
+        double *a = nullptr, *b = nullptr;
+        DDGI_CK(cudaMalloc(&a, irr64_bytes(v)));
+        DDGI_CK(cudaMalloc(&b, dist64_bytes(v)));
+        v->snap64_irr.push_back(a);
+        v->snap64_dist.push_back(b);
+    }
+    if (!v->rec64) DDGI_CK(cudaMalloc(&v->rec64, sizeof(double) * 4 * (size_t)v->P * v->R));
+    const Diff64Volume dv = diff64_volume(v);
+    const ddgi_volume_desc& d = v->desc;
+    const Lights L = make_lights(lights);
+    DDGI_CK(cudaMemsetAsync(v->snap64_irr[0], 0, irr64_bytes(v), st));
+    DDGI_CK(cudaMemsetAsync(v->snap64_dist[0], 0, dist64_bytes(v), st));
+    for (int f = 0; f < n_frames; ++f) {
+        DDGI_CK(launch_frame_dirs(frame_rotation(d.seed, first_frame + f), v->R, d.irr_n, d.dist_n, v->sf64, v->dirs,
+                                  st));
+        // a texel no ray reaches keeps its value: start from the previous atlas
+        DDGI_CK(cudaMemcpyAsync(v->snap64_irr[f + 1], v->snap64_irr[f], irr64_bytes(v), cudaMemcpyDeviceToDevice, st));
+        DDGI_CK(cudaMemcpyAsync(v->snap64_dist[f + 1], v->snap64_dist[f], dist64_bytes(v), cudaMemcpyDeviceToDevice,
+                                st));
+        DDGI_CK(launch_diff64_frame(dv, s->dev, L, v->dirs, albedo_dev, emit_dev, v->snap64_irr[f],
+                                    v->snap64_dist[f], f > 0, v->rec64, v->snap64_irr[f + 1], v->snap64_dist[f + 1],
+                                    st));
+    }
+    return launch_diff64_query(dv, v->snap64_irr[n_frames], v->snap64_dist[n_frames], pos_dev, nrm_dev, n,
+                               make_float3(camera_pos[0], camera_pos[1], camera_pos[2]), out_dev, st) == cudaSuccess
+               ? DDGI_OK
+               : fail(DDGI_ERR_CUDA, "FP64 query launch failed");
+}
+
+ddgi_status ddgi_diff_backward_f64(ddgi_volume v, ddgi_scene s, const ddgi_lights* lights, int64_t first_frame,
+                                   int32_t n_frames, const double* albedo_dev, const float* pos_dev,
+                                   const float* nrm_dev, int64_t n, const float camera_pos[3], const double* dE_dev,
+                                   double* d_albedo_dev, double* d_emit_dev, ddgi_stream stream) {
+    if (!v || !s || !lights || !camera_pos || !albedo_dev || !d_albedo_dev)
+        return fail(DDGI_ERR_INVALID_ARG, "NULL argument");
+    if (s->n_emitters > 0 && !d_emit_dev) return fail(DDGI_ERR_INVALID_ARG, "NULL emitter gradient");
+    if (n > 0 && (!pos_dev || !nrm_dev || !dE_dev)) return fail(DDGI_ERR_INVALID_ARG, "NULL buffer");
+    if (!dev16(albedo_dev) || !dev16(pos_dev) || !dev16(nrm_dev) || !dev16(dE_dev) || !dev16(d_albedo_dev) ||
+        !dev16(d_emit_dev))
+        return fail(DDGI_ERR_INVALID_ARG, kMisaligned);
+    ddgi_status r = diff_check(v, n_frames);
+    if (r != DDGI_OK) return r;
+    if ((int)v->snap64_irr.size() < n_frames + 1 || !v->rec64)
+        return fail(DDGI_ERR_INVALID_ARG, "ddgi_diff_forward_f64 with these frames has not run");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!v->g64) DDGI_CK(cudaMalloc(&v->g64, irr64_bytes(v)));
+    if (!v->g64_prev) DDGI_CK(cudaMalloc(&v->g64_prev, irr64_bytes(v)));
+    if (!v->gL64) DDGI_CK(cudaMalloc(&v->gL64, sizeof(double) * 4 * (size_t)v->P * v->R));
+    if (!v->sw64) DDGI_CK(cudaMalloc(&v->sw64, sizeof(double) * 128));
+    const Diff64Volume dv = diff64_volume(v);
+    const ddgi_volume_desc& d = v->desc;
+    const Lights L = make_lights(lights);
+    DDGI_CK(cudaMemsetAsync(v->g64, 0, irr64_bytes(v), st));
+    DDGI_CK(cudaMemsetAsync(d_albedo_dev, 0, sizeof(double) * 3 * (size_t)s->n_objects, st));
+    if (s->n_emitters > 0) DDGI_CK(cudaMemsetAsync(d_emit_dev, 0, sizeof(double) * 3 * (size_t)s->n_emitters, st));
+    const float3 cam = make_float3(camera_pos[0], camera_pos[1], camera_pos[2]);
+    DDGI_CK(launch_diff64_query_adjoint(dv, v->snap64_irr[n_frames], v->snap64_dist[n_frames], pos_dev, nrm_dev, n,
+                                        cam, dE_dev, v->g64, st));
+    double* g = v->g64;
+    double* gp = v->g64_prev;
+    for (int f = n_frames - 1; f >= 0; --f) {
+        DDGI_CK(launch_frame_dirs(frame_rotation(d.seed, first_frame + f), v->R, d.irr_n, d.dist_n, v->sf64, v->dirs,
+                                  st));
+        DDGI_CK(cudaMemsetAsync(gp, 0, irr64_bytes(v), st));
+        DDGI_CK(launch_diff64_frame_adjoint(dv, s->dev, L, v->dirs, albedo_dev, v->snap64_irr[f], v->snap64_dist[f],
+                                            v->snap64_irr[f + 1], f > 0, v->sw64, g, v->gL64, d_emit_dev,
+                                            d_albedo_dev, gp, st));
+        std::swap(g, gp);
     }
     return DDGI_OK;
 }

@@ -288,6 +288,29 @@ cudaError_t launch_blend_tc_set(const VolSet& vs, bool multi, const BlendParams&
                                 const float4* records, const int32_t* active, const int32_t* count, uint32_t* status,
                                 int grid, cudaStream_t st);
 cudaError_t prepare_blend_tc_kernels();
+// FP64 differentiable path (k_diff64.cu): the volume's grid and parameters
+// in double; atlases [P][(n+2)^2][3] / [P][(m+2)^2][2] and ray records
+// [P*R][4] in double.
+struct Diff64Volume {
+    double origin[3], spacing[3];
+    int counts[3];
+    int R, irr_n, dist_n;
+    double bias, gamma, t_max, cos_power;
+};
+cudaError_t launch_diff64_frame(const Diff64Volume& dv, const DevScene& s, const Lights& L, const float4* dirs,
+                                const double* albedo, const double* emit, const double* irr_prev,
+                                const double* dist_prev, int with_prev, double* rec, double* irr_out,
+                                double* dist_out, cudaStream_t st);
+cudaError_t launch_diff64_query(const Diff64Volume& dv, const double* irr, const double* dist, const float* pos,
+                                const float* nrm, int64_t n, float3 cam, double* out, cudaStream_t st);
+cudaError_t launch_diff64_query_adjoint(const Diff64Volume& dv, const double* irr, const double* dist,
+                                        const float* pos, const float* nrm, int64_t n, float3 cam, const double* dE,
+                                        double* g_irr, cudaStream_t st);
+cudaError_t launch_diff64_frame_adjoint(const Diff64Volume& dv, const DevScene& s, const Lights& L,
+                                        const float4* dirs, const double* albedo, const double* irr_before,
+                                        const double* dist_before, const double* irr_after, int with_prev,
+                                        double* sw_irr, double* g_irr, double* gL, double* d_emit, double* d_albedo,
+                                        double* g_prev, cudaStream_t st);
 cudaError_t launch_query_glossy(const VolView& v, const float* pos, const float* nrm, const float* dirs, int64_t n,
                                 float* out, cudaStream_t st);
 // Dynamic-object wake-up over probes [begin, end); boxes [n][6] device, extended.
