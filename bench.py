@@ -51,7 +51,39 @@ TC_BLEND_DOC = {
 # DRAM bytes (read + write) of one k_trace_primary launch on this workload,
 # from the ncu capture in profiles/trace_passes_city.md; set to None whenever
 # the kernel changes until it is captured again
-PRIMARY_TRAFFIC_BYTES = 3_437_824 + 1_157_120   # DRAM read + write of one k_trace_primary launch (ncu)
+PRIMARY_TRAFFIC_BYTES = 3_510_272 + 1_194_752   # DRAM read + write of one k_trace_primary launch (ncu)
+# The traversal's cache roofline: bytes one 4-wide node visit reads (the six
+# slab planes and the child references, 7 of the node's 8 float4) and one
+# triangle test reads (3 float4), against the L2 read rate measured in the
+# same run over L2-resident buffers of these sizes
+BYTES_PER_WIDE_NODE = 7 * 16
+BYTES_PER_TRI = 3 * 16
+L2_PROBE_BYTES = (16 << 20, 32 << 20)
+# L2 bytes (lts__t_bytes) of one k_trace_primary launch on this workload,
+# from the same ncu capture rules as PRIMARY_TRAFFIC_BYTES
+PRIMARY_L2_BYTES = 309_296_832
+
+
+def l2_read_rate(g, torch, stream, passes=16, reps=5):
+    """L2 read rate (GB/s): the largest over L2_PROBE_BYTES of bytes x passes
+    / event time of ddgi_measure_l2_read, after one untimed call that makes
+    the buffer resident."""
+    sink = torch.zeros(1, dtype=torch.int32, device="cuda")
+    best = 0.0
+    with torch.cuda.stream(stream):
+        for nbytes in L2_PROBE_BYTES:
+            buf = torch.randint(-(1 << 31), (1 << 31) - 1, (nbytes // 4,), dtype=torch.int32, device="cuda")
+            g.measure_l2_read(buf, 2, sink, stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                g.measure_l2_read(buf, passes, sink, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = max(best, nbytes * passes * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+            del buf
+    return best
 
 
 def peaks():
@@ -410,6 +442,8 @@ def run_gpu(args):
     peak_tops = sm_count * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     achieved = prim_ops / (prim_ms * 1e-3) / 1e12
     shadow_achieved = shadow_ops / (shadow_ms * 1e-3) / 1e12
+    prim_l2_bytes = BYTES_PER_WIDE_NODE * stats["nodes"] + BYTES_PER_TRI * stats["tris"]
+    l2_peak = l2_read_rate(g, torch, stream)
     blend_ms = timings["blend"][0] / max(timings["blend"][1], 1)
     blend_bytes = n_active_local * (R * 16 + 2000 + 2816)      # records in, old interior in, tiles out
     q_ms = float(np.mean(query_ms))
@@ -487,7 +521,17 @@ def run_gpu(args):
                      "peak": peak_tops, "unit": "TFLOP/s", "frac": achieved / peak_tops,
                      "traffic": PRIMARY_TRAFFIC_BYTES,
                      "peak_kind": f"FP32 lanes x max SM clock ({pk_kind} clock)",
-                     "ops_per_launch": prim_ops, "launch_ms": prim_ms},
+                     "ops_per_launch": prim_ops, "launch_ms": prim_ms,
+                     "l2": {"bound": "l2", "achieved": prim_l2_bytes / (prim_ms * 1e-3) / 1e9, "peak": l2_peak,
+                            "unit": "GB/s", "frac": prim_l2_bytes / (prim_ms * 1e-3) / 1e9 / l2_peak,
+                            "traffic": PRIMARY_L2_BYTES, "bytes_per_launch": prim_l2_bytes,
+                            "traffic_frac": (PRIMARY_L2_BYTES / (prim_ms * 1e-3) / 1e9 / l2_peak
+                                             if PRIMARY_L2_BYTES else None),
+                            "peak_kind": "measured in this run: ddgi_measure_l2_read, L1-bypassing 16-byte "
+                                         "loads over an L2-resident buffer",
+                            "bytes_kind": "node visits x 112 B + triangle tests x 48 B (counting build); "
+                                          "traffic: lts__t_bytes of one launch (ncu), most node bytes "
+                                          "being L1 hits"}},
         "roofline_shadow": {"bound": "alu", "kernel": "k_trace_shadow", "achieved": shadow_achieved,
                             "peak": peak_tops, "unit": "TFLOP/s", "frac": shadow_achieved / peak_tops,
                             "launch_ms": shadow_ms},

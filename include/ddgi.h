@@ -577,6 +577,21 @@ ddgi_status ddgi_update_noalloc(ddgi_scene scene, const ddgi_volume_desc* desc,
  * otherwise (also before any call on this device).  Allocates nothing. */
 ddgi_status ddgi_update_noalloc_poll_status(ddgi_stream stream);
 
+/* Measurement helper (no counterpart in the paper): the denominator of the
+ * ray traversal's cache roofline.  Enqueues on `stream` one kernel that reads
+ * the `bytes` at buf_dev `passes` times with 16-byte loads that skip L1, so
+ * each load is an L2 request; with bytes well below the L2 capacity and one
+ * untimed call first, the data comes from L2, and bytes * passes divided by
+ * the call's event-timed duration is the device's L2 read rate.
+ * buf_dev: caller-owned device buffer, 16-byte aligned, bytes a positive
+ * multiple of 16 (its contents are only read).  sink_dev: one caller-owned
+ * device uint32, 4-byte aligned, that the kernel may increment (it keeps the
+ * loads from being optimised away).  passes >= 1.  INVALID_ARG for a NULL,
+ * misaligned or zero-sized argument; CUDA when the launch fails.  Allocates
+ * nothing. */
+ddgi_status ddgi_measure_l2_read(const void* buf_dev, size_t bytes, int32_t passes, uint32_t* sink_dev,
+                                 ddgi_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,4 +9,4 @@ from ._lib import (BLEND_BF16, BLEND_FP32, BLEND_TF32, BLEND_TF32X3, DIST_FP16, 
                    IRR_FP32, IRR_RGB9E5, STATE_AWAKE, STATE_NEWLY_AWAKE, STATE_NEWLY_VIGILANT, STATE_OFF, STATE_SLEEPING,
                    STATE_UNINIT, STATE_VIGILANT, DDGIError, load)
 from .api import (Cascade, IrradianceField, ProbeQuery, Scene, Volume, bvh_check, lights_struct, trace,  # noqa: F401
-                  update_noalloc, update_noalloc_poll_status)
+                  update_noalloc, update_noalloc_poll_status, measure_l2_read)

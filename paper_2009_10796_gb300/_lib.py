@@ -94,6 +94,7 @@ SIGNATURES = {
     "ddgi_update_noalloc": (C.c_int, [_vp, C.POINTER(VolumeDesc), C.POINTER(Lights),
                                       C.POINTER(UpdateParams), _vp, _vp, _vp, _vp]),
     "ddgi_update_noalloc_poll_status": (C.c_int, [_vp]),
+    "ddgi_measure_l2_read": (C.c_int, [_vp, C.c_size_t, C.c_int32, _vp, _vp]),
     "ddgi_volume_save": (C.c_int, [_vp, _vp, C.POINTER(C.c_size_t), _vp]),
     "ddgi_volume_load": (C.c_int, [_vp, _vp, C.c_size_t, _vp]),
     "ddgi_query_backward": (C.c_int, [_vp, _vp, _vp, C.c_int64, F3, _vp, C.c_int32, _vp, _vp]),

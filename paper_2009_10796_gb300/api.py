@@ -417,6 +417,15 @@ def update_noalloc_poll_status(stream=None):
     check(load().ddgi_update_noalloc_poll_status(_stream(stream)))
 
 
+def measure_l2_read(buf, passes, sink, stream=None):
+    """Enqueue one read of the device tensor `buf` (16-byte aligned, a
+    multiple of 16 bytes) `passes` times through L2 (ddgi_measure_l2_read);
+    `sink` is a one-element int32 device tensor.  Time it with events on
+    `stream` after an untimed call."""
+    check(load().ddgi_measure_l2_read(_ptr(buf), C.c_size_t(buf.numel() * buf.element_size()), int(passes),
+                                      _ptr(sink), _stream(stream)))
+
+
 class Cascade:
     """Nested probe volumes updated together (densest first), optionally
     camera-tracking windows; see ddgi_cascade_* in include/ddgi.h."""

@@ -7,26 +7,30 @@
 // texels t on the MMA's M side (one 128-row tile of irradiance texels, two of
 // distance texels), probes and channels on N, rays on K.
 //
-// Work split.  One persistent CTA per SM takes an equal, contiguous share of
-// the active list and blends it in rounds of up to PG probes; each round
-// walks the rays in chunks of KC.  Per chunk:
-//   * warp 0 issues bulk copies (TMA, 1D) of the chunk's pre-packed weight
-//     tiles (k_pack_weights: the MMA A operands, L2 resident, shared by all
-//     probes) and of every probe's KC raw ray records (KC x 16 contiguous
-//     bytes each) into one stage of a ring (3 stages for X3, 5 otherwise),
-//     issued ring depth - 1 chunks ahead, completion counted on the stage's
-//     mbarrier;
-//   * all threads convert the stage's raw records in shared memory into the
-//     B operands (channel planes, hi / lo splits) of a double-buffered B tile;
-//   * one thread issues the chunk's MMAs into TMEM and commits them to the
-//     stage's second mbarrier, which frees the stage and the B tile.
-// The round's old atlas tiles are prefetched into L2 at its start.  Its
-// epilogue reads the accumulators straight from TMEM (thread = texel row,
-// the two warps of a TMEM lane quarter splitting the probes), loads the old
-// texels of all its probes before computing any, and finishes each texel as
-// the SIMT blend does (normalise, gamma, per-texel hysteresis, lerp, border
-// copies, Sec. 4.2, 4.3, 7.1).  mbarrier parities follow from a chunk
-// counter that runs across rounds.
+// Work split.  One persistent CTA of 288 threads per SM takes an equal,
+// contiguous share of the active list and blends it in rounds of up to PG
+// probes; each round walks the rays in chunks of KC.  The warps specialise:
+//   * the control warp (warp 8, its lane 0) copies each chunk's pre-packed
+//     weight tiles (k_pack_weights: the MMA A operands, L2 resident, shared
+//     by all probes) into a ring of stages (3 for X3, 5 otherwise) with 1D
+//     bulk copies issued ring depth - 1 chunks ahead, completion counted on
+//     the stage's mbarrier; per chunk it waits for the weights and for the
+//     chunk's B tile, issues the MMAs into TMEM from descriptors built once
+//     per chunk, and commits them to the stage's second mbarrier, which
+//     frees the weight stage and the B tile;
+//   * the eight converter warps, one thread per (probe slot, ray pair):
+//     each fetches its 32 bytes of ray records with its own asynchronous
+//     copies NR - 1 chunks ahead, converts them into B operands (channel-
+//     major rows, hi / lo splits) of a double-buffered B tile once the MMAs
+//     that last read that tile are done, and arrives on the tile's mbarrier.
+// The round's epilogue copies the old atlas tiles of its probes into shared
+// memory; the converter warps move the accumulators from TMEM into a
+// staging array (warp w: TMEM lanes 32 (w % 4) .. + 31, the columns of
+// probes 16 (w / 4) .. + 15); then every thread finishes texels as the SIMT
+// blend does (normalise, gamma, per-texel hysteresis, lerp, border copies,
+// Sec. 4.2, 4.3, 7.1) in the staged tiles, which go back to the atlases with
+// coalesced 16-byte stores.  mbarrier parities follow from a chunk counter
+// that runs across rounds.
 //
 // Precision modes.
 //   TF32: irradiance with TF32 operands; the distance moments keep FP32

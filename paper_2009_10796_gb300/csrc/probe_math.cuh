@@ -287,15 +287,6 @@ __device__ __forceinline__ float3 sample_irr_at(const VolView& v, int p, const F
                    load_irr(v, p, f.x0 + 1, f.y0 + 1));
 }
 
-// FP32-only forms of the two samplers above (the same loads and arithmetic).
-__device__ __forceinline__ float3 sample_irr_fp32(const VolView& v, int p, const Footprint& f, const Bilerp& w) {
-    const int row = v.irr_n + 2;
-    const float4* a = (const float4*)v.irr + ((int64_t)p * v.irr_tile + (int64_t)f.y0 * row + f.x0);
-    const float4 q00 = __ldg(a), q10 = __ldg(a + 1), q01 = __ldg(a + row), q11 = __ldg(a + row + 1);
-    return bilerp3(w, f3(q00.x, q00.y, q00.z), f3(q10.x, q10.y, q10.z), f3(q01.x, q01.y, q01.z),
-                   f3(q11.x, q11.y, q11.z));
-}
-
 __device__ __forceinline__ float3 sample_irr_at(const VolView& v, int p, const Footprint& f) {
     return sample_irr_at(v, p, f, bilerp_weights(f));
 }
@@ -321,6 +312,7 @@ __device__ __forceinline__ float2 sample_dist_at(const VolView& v, int p, const 
                        w00 * a.y + w10 * b.y + w01 * c.y + w11 * d.y);
 }
 
+// FP32-only form of sample_dist_at (the same loads and arithmetic).
 __device__ __forceinline__ float2 sample_dist_fp32(const VolView& v, int p, const Footprint& f) {
     const int row = v.dist_n + 2;
     const float2* q = (const float2*)v.dist + (int64_t)p * v.dist_tile + (int64_t)f.y0 * row + f.x0;
@@ -357,12 +349,6 @@ __device__ __forceinline__ float gamma_decode_half_fast(float e, float half_gamm
     return powf(e, half_gamma);
 }
 
-// gamma_decode_half_fast for gamma 5 (half_gamma 2.5), without the test.
-__device__ __forceinline__ float gamma_decode_g5_fast(float e) {
-    e = fmaxf(e, 0.0f);
-    const float sq = e > 0.0f ? e * rsqrtf(e) : 0.0f;
-    return e * e * sq;
-}
 
 // a - b for FP32 a, b as the unevaluated sum hi + lo, exactly (Knuth's
 // TwoSum applied to a and -b, round-to-nearest); the intrinsics keep each
@@ -401,6 +387,111 @@ __device__ __forceinline__ float3 local_to_probe(const VolView& v, const LocalPo
     return f3(q.hi.x - (float)i * v.spacing.x, q.hi.y - (float)j * v.spacing.y, q.hi.z - (float)k * v.spacing.z);
 }
 
+// x^2.5 of a red / green pair of gamma-encoded values (gamma 5): e^2 times
+// e * rsqrt(e), the squares and products as packed FP32 pairs.  The floor
+// 1e-30 stands in for the zero test of gamma_decode_half_fast: below it both
+// give 0 in FP32 (x^2.5 < 1e-75), above it they are the same operations.
+__device__ __forceinline__ uint64_t gamma_decode_g5_pair(float er, float eg) {
+    er = fmaxf(er, 1e-30f);
+    eg = fmaxf(eg, 1e-30f);
+    const uint64_t E = f2_pack(er, eg);
+    const uint64_t S = f2_mul(E, f2_pack(rsqrtf(er), rsqrtf(eg)));
+    return f2_mul(f2_mul(E, E), S);
+}
+
+// The specialised query of query_M_look<true> (FP32 atlases, gamma 5, no
+// probe offsets; query_fast_view): the same operations in the same order,
+// except the decode's zero test (gamma_decode_g5_pair), with the eight cage
+// corners unrolled, so each corner's probe index, grid offset and
+// trilinear factor are registers rather than per-probe selects, and the red
+// and green channels of the irradiance taps and their decode carried as
+// packed FP32 pairs (the blue channel scalar).
+__device__ __forceinline__ float3 query_M_look_fast(const VolView& v, float3 x, float3 n, float3 wo, float3 look) {
+    const LocalPoint q = local_point(v, x, n, wo);
+    const float g[3] = {(q.hi.x + q.lb.x) / v.spacing.x, (q.hi.y + q.lb.y) / v.spacing.y,
+                        (q.hi.z + q.lb.z) / v.spacing.z};
+    const int cnt[3] = {v.counts.x, v.counts.y, v.counts.z};
+    int base[3];
+    float fr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float b = floorf(g[a]);
+        b = fminf(fmaxf(b, 0.0f), (float)(cnt[a] - 2));
+        base[a] = (int)b;
+        fr[a] = fminf(fmaxf(g[a] - b, 0.0f), 1.0f);
+    }
+    const Footprint fn = footprint(oct_encode(look), v.irr_n);
+    const Bilerp wn = bilerp_weights(fn);
+    const uint64_t W00 = f2_pack(wn.w00, wn.w00), W10 = f2_pack(wn.w10, wn.w10);
+    const uint64_t W01 = f2_pack(wn.w01, wn.w01), W11 = f2_pack(wn.w11, wn.w11);
+    const int irow = v.irr_n + 2;
+    const int64_t itap = (int64_t)fn.y0 * irow + fn.x0;
+    // per axis, the cage's two planes: physical index, x - x_p (high part)
+    // and trilinear factor
+    const int px[2] = {wrap_add(base[0], v.shift.x, cnt[0]), wrap_add(base[0] + 1, v.shift.x, cnt[0])};
+    const int py[2] = {wrap_add(base[1], v.shift.y, cnt[1]), wrap_add(base[1] + 1, v.shift.y, cnt[1])};
+    const int pz[2] = {wrap_add(base[2], v.shift.z, cnt[2]), wrap_add(base[2] + 1, v.shift.z, cnt[2])};
+    const float ax[2] = {q.hi.x - (float)base[0] * v.spacing.x, q.hi.x - (float)(base[0] + 1) * v.spacing.x};
+    const float ay[2] = {q.hi.y - (float)base[1] * v.spacing.y, q.hi.y - (float)(base[1] + 1) * v.spacing.y};
+    const float az[2] = {q.hi.z - (float)base[2] * v.spacing.z, q.hi.z - (float)(base[2] + 1) * v.spacing.z};
+    const float tx[2] = {1.0f - fr[0], fr[0]}, ty[2] = {1.0f - fr[1], fr[1]}, tz[2] = {1.0f - fr[2], fr[2]};
+    int pc[8];
+    unsigned act = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        pc[c] = px[c & 1] + cnt[0] * (py[(c >> 1) & 1] + cnt[1] * pz[c >> 2]);
+        act |= state_active(v.states[pc[c]]) ? 1u << c : 0u;
+    }
+    float sumw = 0.0f;
+    float3 acc = f3(0.0f, 0.0f, 0.0f);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        if (!(act & (1u << c))) continue;
+        const int o0 = c & 1, o1 = (c >> 1) & 1, o2 = c >> 2;
+        const float3 a = f3(ax[o0], ay[o1], az[o2]);
+        const float wt = tx[o0] * ty[o1] * tz[o2];
+        const float3 dp = f3(-(a.x + q.lo.x), -(a.y + q.lo.y), -(a.z + q.lo.z));   // probe - x
+        const float dd = dot(dp, dp);
+        const float cw = dd > 0.0f ? dot(n, dp) * rsqrtf(dd) : 1.0f;
+        const float hb = (1.0f + cw) * 0.5f;
+        const float wb = hb * hb + 0.2f;
+        const float3 pv = a + q.lb;                                                // biased point - probe
+        const float rr = dot(pv, pv);
+        float wc = 1.0f;
+        if (rr > 0.0f) {
+            const float ir = rsqrtf(rr);
+            const float r = rr * ir;
+            const float2 mom = sample_dist_fp32(v, pc[c], footprint(oct_encode_fast(ir * pv), v.dist_n));
+            if (r > mom.x) {
+                const float var = fmaxf(mom.y - mom.x * mom.x, 0.0f);
+                const float dr = r - mom.x;
+                wc = __fdividef(var, var + dr * dr);
+            }
+        }
+        const float w = wt * wb * fmaxf(wc, 1e-6f);
+        const float4* ia = (const float4*)v.irr + ((int64_t)pc[c] * v.irr_tile + itap);
+        const float4 q00 = __ldg(ia), q10 = __ldg(ia + 1), q01 = __ldg(ia + irow), q11 = __ldg(ia + irow + 1);
+        uint64_t rg = f2_mul(W00, f2_pack(q00.x, q00.y));
+        rg = f2_fma(W10, f2_pack(q10.x, q10.y), rg);
+        rg = f2_fma(W01, f2_pack(q01.x, q01.y), rg);
+        rg = f2_fma(W11, f2_pack(q11.x, q11.y), rg);
+        const float eb = wn.w00 * q00.z + wn.w10 * q10.z + wn.w01 * q01.z + wn.w11 * q11.z;
+        float er, eg;
+        f2_unpack(rg, er, eg);
+        float dr_, dg_;
+        f2_unpack(gamma_decode_g5_pair(er, eg), dr_, dg_);
+        const float ebc = fmaxf(eb, 1e-30f);
+        acc.x += w * dr_;
+        acc.y += w * dg_;
+        acc.z += w * (ebc * ebc * (ebc * rsqrtf(ebc)));
+        sumw += w;
+    }
+    if (!(sumw > 0.0f)) return f3(0.0f, 0.0f, 0.0f);
+    const float inv = 1.0f / sumw;
+    const float3 m = inv * acc;
+    return f3(m.x * m.x, m.y * m.y, m.z * m.z);
+}
+
 // Cosine-weighted mean radiance M at x with normal n, the self-shadow bias
 // using w_o (Sec. 4.1 equation), the 8-probe cage (Sec. 2.2): trilinear,
 // backface ((1 + n.w_p)/2)^2 + 0.2, Chebyshev visibility, weight floor
@@ -411,10 +502,10 @@ __device__ __forceinline__ float3 local_to_probe(const VolView& v, const LocalPo
 // irradiance query, the mirror direction for a second-order glossy lookup
 // (Sec. 4.4); the bias and the backface weights use n either way.
 // FAST: the view is known to hold FP32 atlases, gamma 5 and no probe
-// offsets (query_fast_view), so the format, gamma and offset tests drop out
-// of the probe loop; the arithmetic and its order are the same.
+// offsets (query_fast_view); query_M_look_fast serves it.
 template <bool FAST = false>
 __device__ __forceinline__ float3 query_M_look(const VolView& v, float3 x, float3 n, float3 wo, float3 look) {
+    if constexpr (FAST) return query_M_look_fast(v, x, n, wo, look);
     const LocalPoint q = local_point(v, x, n, wo);
     float g[3] = {(q.hi.x + q.lb.x) / v.spacing.x, (q.hi.y + q.lb.y) / v.spacing.y,
                   (q.hi.z + q.lb.z) / v.spacing.z};
@@ -449,7 +540,7 @@ __device__ __forceinline__ float3 query_M_look(const VolView& v, float3 x, float
         int o0 = c & 1, o1 = (c >> 1) & 1, o2 = (c >> 2) & 1;
         int p = (o0 ? px1 : px0) + cnt[0] * ((o1 ? py1 : py0) + cnt[1] * (o2 ? pz1 : pz0));
         float3 a = local_to_probe(v, q, base[0] + o0, base[1] + o1, base[2] + o2);
-        if (!FAST && v.offsets) {   // the probe's own (moved) position; the cage stays on the grid
+        if (v.offsets) {   // the probe's own (moved) position; the cage stays on the grid
             const float4 po = __ldg(v.offsets + p);
             a = f3(a.x - po.x, a.y - po.y, a.z - po.z);
         }
@@ -466,7 +557,7 @@ __device__ __forceinline__ float3 query_M_look(const VolView& v, float3 x, float
             float ir = rsqrtf(rr);
             float r = rr * ir;
             const Footprint fd = footprint(oct_encode_fast(ir * pv), v.dist_n);
-            float2 mom = FAST ? sample_dist_fp32(v, p, fd) : sample_dist_at(v, p, fd);
+            float2 mom = sample_dist_at(v, p, fd);
             if (r > mom.x) {
                 float var = fmaxf(mom.y - mom.x * mom.x, 0.0f);
                 float dr = r - mom.x;
@@ -474,10 +565,10 @@ __device__ __forceinline__ float3 query_M_look(const VolView& v, float3 x, float
             }
         }
         float w = wt * wb * fmaxf(wc, 1e-6f);
-        float3 e = FAST ? sample_irr_fp32(v, p, fn, wn) : sample_irr_at(v, p, fn, wn);
-        acc.x += w * (FAST ? gamma_decode_g5_fast(e.x) : gamma_decode_half_fast(e.x, v.half_gamma));
-        acc.y += w * (FAST ? gamma_decode_g5_fast(e.y) : gamma_decode_half_fast(e.y, v.half_gamma));
-        acc.z += w * (FAST ? gamma_decode_g5_fast(e.z) : gamma_decode_half_fast(e.z, v.half_gamma));
+        float3 e = sample_irr_at(v, p, fn, wn);
+        acc.x += w * gamma_decode_half_fast(e.x, v.half_gamma);
+        acc.y += w * gamma_decode_half_fast(e.y, v.half_gamma);
+        acc.z += w * gamma_decode_half_fast(e.z, v.half_gamma);
         sumw += w;
     }
     if (!(sumw > 0.0f)) return f3(0.0f, 0.0f, 0.0f);

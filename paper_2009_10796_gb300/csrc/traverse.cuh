@@ -1,5 +1,10 @@
-// BVH2 traversal with the watertight ray/triangle test of Woop, Benthin and
-// Wald ("Watertight Ray/Triangle Intersection", JCGT 2013).  The edge
+// Ray traversal of the scene's hierarchy in its two forms: the 4-wide
+// nodes that the probe-ray passes walk warp-cooperatively (the while-while
+// scheme of Aila and Laine, HPG 2009, over four child boxes per node), and
+// the binary nodes that the one-ray-per-thread paths (G-buffer, raw ray
+// queries, allocation-free update, adjoint) walk.  Triangles are tested with
+// the watertight ray/triangle test of Woop, Benthin and Wald ("Watertight
+// Ray/Triangle Intersection", JCGT 2013).  The edge
 // functions are evaluated with explicitly rounded products and differences
 // (no fused multiply-add), so a shared edge gives bitwise-negated values in
 // its two triangles and rays cannot slip between them.  Box tests are made

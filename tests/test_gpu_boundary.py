@@ -136,3 +136,24 @@ def test_probe_query_autograd(g):
     G = V.query_backward(P, N_, cam, to_dev(dE))
     assert torch.all(atlas.grad[..., 3] == 0)
     assert torch.allclose(atlas.grad[..., :3], G, rtol=1e-5, atol=1e-7 * float(G.abs().max()))
+
+
+def test_measure_l2_read(g):
+    """The L2 read-rate helper runs on a resident buffer, reports a rate
+    between the HBM copy rate's order and a bound no cache reaches, and
+    rejects misaligned or odd-sized buffers before launching."""
+    buf = torch.arange(4 << 20, dtype=torch.int32, device="cuda")     # 16 MiB
+    sink = torch.zeros(1, dtype=torch.int32, device="cuda")
+    g.measure_l2_read(buf, 2, sink)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    g.measure_l2_read(buf, 8, sink)
+    e1.record()
+    torch.cuda.synchronize()
+    gbs = buf.numel() * 4 * 8 / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    print(f"[l2 read] {gbs:.0f} GB/s")
+    assert 1000.0 < gbs < 200000.0
+    with pytest.raises(g.DDGIError, match="16-byte"):
+        g.measure_l2_read(buf[1:5], 1, sink)
+    with pytest.raises(g.DDGIError, match="multiple of 16"):
+        g.measure_l2_read(buf[:3], 1, sink)
