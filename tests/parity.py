@@ -5,9 +5,14 @@ Tolerances (FP32 device arithmetic against the FP64 oracle):
   * states and hit/miss: bit-exact, except rays whose FP32 and FP64 results
     legitimately differ (grazing a triangle edge or silhouette within float
     rounding); those are counted, reported and must stay rare.
-  * texels and query outputs: |gpu - oracle| <= 1e-4 * max(|oracle|, 1e-3 * max|oracle|);
-    texels touched with weight > 1e-3 of their row by a flagged ray are
-    listed and excluded.
+  * texels and query outputs: |gpu - oracle| <= 1e-4 * max(|oracle|, 1e-3 * max|oracle|)
+    at every element; texels in which a flagged ray's share of the normalised
+    weight exceeds LISTED_WEIGHT are listed and excluded, and queries that
+    read them compare against the oracle's atlas patched with the GPU's
+    listed texels (`patched`) and on the GPU's own atlas;
+  * query points where the oracle itself moves by more than the bound when
+    the point moves by one FP32 ulp (`fp32_neighbourhood_spread`) are listed
+    and held to the bound plus twice that spread.
 """
 from __future__ import annotations
 
