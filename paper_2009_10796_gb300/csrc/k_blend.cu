@@ -22,6 +22,8 @@
 // writes the texel plus the border texels that copy it (the octahedral
 // border copy of Sec. 7.1 fused into the blend).  The probe's state advances
 // Newly Vigilant -> Vigilant after its texels are written.
+#include <algorithm>
+
 #include "blend_epilogue.cuh"
 #include "traverse.cuh"
 
@@ -156,8 +158,10 @@ __global__ void __launch_bounds__(256) k_frame_setup(FrameRot rot_arg, const Fra
     }
 }
 
+// Groups of `group` <= kProbes probes per CTA (fewer than kProbes when the
+// group's records would not fit in shared memory at large R).
 template <bool MULTI, int kProbes>
-__global__ void __launch_bounds__(256) k_blend_simt(VolSet vs, BlendParams bp,
+__global__ void __launch_bounds__(256) k_blend_simt(VolSet vs, BlendParams bp, int group,
                                                     const float* __restrict__ w_irr,
                                                     const float* __restrict__ inv_s_irr,
                                                     const float* __restrict__ w_dist,
@@ -166,7 +170,7 @@ __global__ void __launch_bounds__(256) k_blend_simt(VolSet vs, BlendParams bp,
                                                     const int32_t* __restrict__ active,
                                                     const int32_t* __restrict__ count,
                                                     uint32_t* status) {
-    extern __shared__ float4 srec[];   // kProbes x (R + 1) records
+    extern __shared__ float4 srec[];   // group x (R + 1) records
     __shared__ int s_probe[kProbes];
     __shared__ int s_newly[kProbes];
     const int R = bp.R;
@@ -175,8 +179,8 @@ __global__ void __launch_bounds__(256) k_blend_simt(VolSet vs, BlendParams bp,
     const VolView& v0 = vol_of<MULTI>(vs, 0);   // cascades share R and tile sizes
     const int ni = v0.irr_n, nd = v0.dist_n;
     const int ti = ni * ni, td = nd * nd;
-    for (int g0 = blockIdx.x * kProbes; g0 < n_act; g0 += gridDim.x * kProbes) {
-        const int np = min(kProbes, n_act - g0);
+    for (int g0 = blockIdx.x * group; g0 < n_act; g0 += gridDim.x * group) {
+        const int np = min(group, n_act - g0);
         if (threadIdx.x < np) {
             int e = active[g0 + threadIdx.x];
             s_probe[threadIdx.x] = e;
@@ -763,9 +767,13 @@ static cudaError_t blend_simt(const VolSet& vs, const BlendParams& bp, int irr_n
                                       count, status, grid * (PGS / 4), st);
     cudaError_t e = opt_in_blend<MULTI, PGS>();
     if (e != cudaSuccess) return e;
-    size_t smem = (size_t)PGS * (bp.R + 1) * sizeof(float4);
-    k_blend_simt<MULTI, PGS><<<grid, 256, smem, st>>>(vs, bp, w_irr, inv_s_irr, w_dist, inv_s_dist, records,
-                                                      active, count, status);
+    // as many probes per CTA as fit (R <= 1024 leaves room for at least 13)
+    const size_t per_probe = (size_t)(bp.R + 1) * sizeof(float4);
+    const int group = (int)std::min<size_t>(PGS, ((size_t)smem_optin() - 1024) / per_probe);
+    if (group < 1) return cudaErrorInvalidValue;
+    k_blend_simt<MULTI, PGS><<<grid, 256, (size_t)group * per_probe, st>>>(vs, bp, group, w_irr, inv_s_irr, w_dist,
+                                                                            inv_s_dist, records, active, count,
+                                                                            status);
     return cudaGetLastError();
 }
 

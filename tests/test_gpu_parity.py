@@ -164,6 +164,35 @@ def test_odd_sizes_parity(g):
     assert eq.max() <= REL
 
 
+@pytest.mark.parametrize("case", ["max_tiles", "max_rays_tf32x3"])
+def test_maximum_sizes_parity(g, case):
+    """The largest rays per probe (1024) and tiles (32 x 32 irradiance, 64 x
+    64 distance interiors) a volume accepts: tiles too large for the
+    register-tiled blend take the row kernel, whose probe group shrinks to
+    fit its shared memory at this R; the 3xTF32 tensor-core blend at R = 1024
+    walks 64 ray chunks per probe group."""
+    sc = synth.room_scene(n_boxes=6)
+    tiles = dict(irr_n=32, dist_n=64) if case == "max_tiles" else dict(irr_n=6, dist_n=14)
+    desc = synth.VolumeDesc(origin=(2.0, 2.5, 1.5), spacing=(5.0, 4.0, 3.0), counts=(2, 2, 3),
+                            rays_per_probe=1024, hysteresis_irr=0.5, hysteresis_vis=0.5, state_machine=0,
+                            seed=41, **tiles)
+    prec = g.BLEND_FP32 if case == "max_tiles" else g.BLEND_TF32X3
+    L = synth.room_lights()
+    st, irr, dist, rays = run_oracle(sc, L, desc, [2, 3])
+    S = g.Scene.from_arrays(sc)
+    V = g.Volume(desc)
+    V.update(S, L, 2, precision=prec)
+    V.update(S, L, 3, precision=prec)
+    assert np.array_equal(V.states().cpu().numpy(), st)
+    ei = rel_err(V.irr_atlas().cpu().numpy(), irr).max(-1)
+    ed = rel_err(V.dist_atlas().cpu().numpy(), dist).max(-1)
+    pos, nrm, cam = synth.room_queries(n=2048)
+    E_ref = oracle.query(desc, st, irr, dist, pos, nrm, cam)
+    eq = rel_err(V.query(to_dev(pos), to_dev(nrm), cam).cpu().numpy(), E_ref).max(-1)
+    _report(f"maximum sizes {case}", irr_max=float(ei.max()), dist_max=float(ed.max()), query_max=float(eq.max()))
+    assert ei.max() <= REL and ed.max() <= REL and eq.max() <= REL
+
+
 def test_empty_scene_uniform_sky(g):
     a = np.array([0.3, 1.7, 0.05])
     L = synth.Lights(sky_a=a)
