@@ -446,6 +446,7 @@ def run_gpu(args):
     l2_peak = l2_read_rate(g, torch, stream)
     blend_ms = timings["blend"][0] / max(timings["blend"][1], 1)
     blend_bytes = n_active_local * (R * 16 + 2000 + 2816)      # records in, old interior in, tiles out
+    blend_flop = 2 * n_active_local * R * (desc.irr_n ** 2 * 3 + desc.dist_n ** 2 * 2)
     q_ms = float(np.mean(query_ms))
     q_bytes = pos_q.shape[0] * 36                         # positions + normals in, irradiance out
     hbm = pk.get("hbm_gbs", 6800.0)
@@ -492,10 +493,11 @@ def run_gpu(args):
                          f"query points "
                          f"({t_q:.2f} s), extrapolated to {n_act_cpu} active probes (oracle's own "
                          f"estimate) + {n_pix} pixels"}
-    # steady-state frame: frame setup (directions, weights, counter clear), 3 trace
+    # steady-state frame: frame setup in two launches (directions and counter
+    # clear on the update stream, texel weights on a side stream), 3 trace
     # passes, blend, query (the active list is kept and classification skipped
-    # once no probe is uninitialised)
-    launches_per_step = 6
+    # once no probe is uninitialised): 7 launches, as the ncu launch list shows
+    launches_per_step = 7
     line = {
         "metric": METRIC, "value": value, "unit": "Grays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
@@ -537,7 +539,11 @@ def run_gpu(args):
                             "launch_ms": shadow_ms},
         "roofline_blend": {"bound": "hbm", "achieved": blend_bytes / (blend_ms * 1e-3) / 1e9,
                            "peak": hbm, "unit": "GB/s",
-                           "frac": blend_bytes / (blend_ms * 1e-3) / 1e9 / hbm},
+                           "frac": blend_bytes / (blend_ms * 1e-3) / 1e9 / hbm,
+                           # the FP32 multiply-adds of the contraction, R x (36 x 3 + 196 x 2) per
+                           # probe, against 152 SMs x 128 lanes x 2 FLOP x the maximum SM clock
+                           "fp32": {"achieved": blend_flop / (blend_ms * 1e-3) / 1e12, "peak": 2 * peak_tops,
+                                    "unit": "TFLOP/s", "frac": blend_flop / (blend_ms * 1e-3) / 1e12 / (2 * peak_tops)}},
         "roofline_query": {"bound": "hbm", "achieved": q_bytes / (q_ms * 1e-3) / 1e9, "peak": hbm,
                            "unit": "GB/s", "frac": q_bytes / (q_ms * 1e-3) / 1e9 / hbm},
         "tensor_blend": {name: {

@@ -69,6 +69,25 @@ __device__ __forceinline__ float2 blend_dist_value(const BlendParams& bp, float2
     return e;
 }
 
+// Bytes of one stored texel (DDGI_IRR_* / DDGI_DIST_* formats).
+__device__ __forceinline__ int irr_texel_bytes(int fmt) {
+    return fmt == DDGI_IRR_FP32 ? 16 : (fmt == DDGI_IRR_FP16 ? 8 : 4);
+}
+__device__ __forceinline__ int dist_texel_bytes(int fmt) { return fmt == DDGI_DIST_FP32 ? 8 : 4; }
+
+// Requests probe p's two bordered tiles into L2 (one prefetch per 128-byte
+// line, the last byte's line included), for a blend that reads them later.
+__device__ __forceinline__ void prefetch_tiles_l2(const VolView& v, int p) {
+    const int64_t bi = (int64_t)v.irr_tile * irr_texel_bytes(v.irr_format);
+    const int64_t bd = (int64_t)v.dist_tile * dist_texel_bytes(v.dist_format);
+    const char* a = (const char*)v.irr + p * bi;
+    const char* d = (const char*)v.dist + p * bd;
+    for (int64_t o = 0; o < bi; o += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(a + o));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a + bi - 1));
+    for (int64_t o = 0; o < bd; o += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(d + o));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(d + bd - 1));
+}
+
 // A texel and the border texels that copy it (Sec. 7.1).
 __device__ __forceinline__ void store_irr_with_borders(const VolView& v, int p, int x, int y, float3 e) {
     store_irr(v, p, x, y, e);

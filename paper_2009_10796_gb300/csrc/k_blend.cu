@@ -259,8 +259,10 @@ static TiledShape tiled_shape(int PG, int R, int irr_n, int dist_n) {
     t.irr_units = t.nqi * (PG / 2);
     t.threads = t.dist_threads + (t.irr_units + 31) / 32 * 32;
     t.smem = sizeof(float) * ((size_t)4 * PG * R + (size_t)2 * 4 * (t.nqd + t.nqi) * kTileWS);
-    // the epilogue reuses the same shared memory for the weighted sums
-    const size_t sums = sizeof(float) * (size_t)PG * (2 * dist_n * dist_n + 3 * irr_n * irr_n);
+    // the epilogue reuses the same shared memory for the weighted sums and
+    // the frame's inverse weight sums
+    const size_t sums = sizeof(float) * ((size_t)PG * (2 * dist_n * dist_n + 3 * irr_n * irr_n) +
+                                         dist_n * dist_n + irr_n * irr_n);
     if (sums > t.smem) t.smem = sums;
     return t;
 }
@@ -345,8 +347,11 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, B
         if (threadIdx.x < np) {
             int e = active[g0 + threadIdx.x];
             s_probe[threadIdx.x] = e;
-            s_newly[threadIdx.x] =
-                state_newly(vol_of<MULTI>(vs, e >> kEntryShift).states[e & kEntryMask]);
+            const VolView& v = vol_of<MULTI>(vs, e >> kEntryShift);
+            s_newly[threadIdx.x] = state_newly(v.states[e & kEntryMask]);
+            // the probe's old tiles into L2 while the group is summed (the
+            // epilogue then reads them from L2)
+            prefetch_tiles_l2(v, e & kEntryMask);
         }
         // records -> planes, kRecBatch independent loads in flight per thread.
         // Item k is (ray pair, probe, ray within the pair): two threads read a
@@ -482,23 +487,69 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, B
                     }
             }
         }
+        float* inv_d = sum_i + 3 * PG * ti;   // [td], then [ti]
+        float* inv_i = inv_d + td;
+        for (int k = threadIdx.x; k < td; k += blockDim.x) inv_d[k] = __ldg(inv_s_dist + k);
+        for (int k = threadIdx.x; k < ti; k += blockDim.x) inv_i[k] = __ldg(inv_s_irr + k);
         __syncthreads();
-#pragma unroll 2
-        for (int o = threadIdx.x; o < np * td; o += blockDim.x) {
-            const int pp = (int)fast_div((uint32_t)o, bp.div_td), t = o - pp * td;
-            const int y = (int)fast_div((uint32_t)t, bp.div_nd), x = t - y * nd;
-            const int e = s_probe[pp];
-            blend_dist_texel_at(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, x + 1, y + 1,
-                                sum_d[2 * o], sum_d[2 * o + 1], __ldg(inv_s_dist + t), s_newly[pp] != 0, status);
+        // texels in batches per thread: every load of a batch (old texel,
+        // sums, inverse sum) first, then the blends and stores, so a thread
+        // has several independent texels in flight; the items of a batch are
+        // distinct texels and touch disjoint memory
+        constexpr int kBD = 4, kBI = 2;
+        for (int o0 = threadIdx.x; o0 < np * td; o0 += kBD * blockDim.x) {
+            float2 old[kBD];
+            float m1[kBD], m2[kBD], inv[kBD];
+            int pp[kBD], xs[kBD], ys[kBD];
+#pragma unroll
+            for (int u = 0; u < kBD; ++u) {
+                const int o = min(o0 + u * (int)blockDim.x, np * td - 1);
+                pp[u] = (int)fast_div((uint32_t)o, bp.div_td);
+                const int t = o - pp[u] * td;
+                const int y = (int)fast_div((uint32_t)t, bp.div_nd);
+                xs[u] = 1 + t - y * nd;
+                ys[u] = 1 + y;
+                const int e = s_probe[pp[u]];
+                old[u] = load_dist<false>(vol_of<MULTI>(vs, e >> kEntryShift), e & kEntryMask, xs[u], ys[u]);
+                m1[u] = sum_d[2 * o];
+                m2[u] = sum_d[2 * o + 1];
+                inv[u] = inv_d[t];
+            }
+#pragma unroll
+            for (int u = 0; u < kBD; ++u) {
+                if (o0 + u * (int)blockDim.x >= np * td) break;
+                const int e = s_probe[pp[u]];
+                store_dist_with_borders(vol_of<MULTI>(vs, e >> kEntryShift), e & kEntryMask, xs[u], ys[u],
+                                        blend_dist_value(bp, old[u], m1[u], m2[u], inv[u], s_newly[pp[u]] != 0,
+                                                         status));
+            }
         }
-#pragma unroll 2
-        for (int o = threadIdx.x; o < np * ti; o += blockDim.x) {
-            const int pp = (int)fast_div((uint32_t)o, bp.div_ti), t = o - pp * ti;
-            const int y = (int)fast_div((uint32_t)t, bp.div_ni), x = t - y * ni;
-            const int e = s_probe[pp];
-            blend_irr_texel_at(vol_of<MULTI>(vs, e >> kEntryShift), bp, e & kEntryMask, x + 1, y + 1,
-                               sum_i[3 * o], sum_i[3 * o + 1], sum_i[3 * o + 2], __ldg(inv_s_irr + t),
-                               s_newly[pp] != 0, status);
+        for (int o0 = threadIdx.x; o0 < np * ti; o0 += kBI * blockDim.x) {
+            float3 old[kBI], sum[kBI];
+            float inv[kBI];
+            int pp[kBI], xs[kBI], ys[kBI];
+#pragma unroll
+            for (int u = 0; u < kBI; ++u) {
+                const int o = min(o0 + u * (int)blockDim.x, np * ti - 1);
+                pp[u] = (int)fast_div((uint32_t)o, bp.div_ti);
+                const int t = o - pp[u] * ti;
+                const int y = (int)fast_div((uint32_t)t, bp.div_ni);
+                xs[u] = 1 + t - y * ni;
+                ys[u] = 1 + y;
+                const int e = s_probe[pp[u]];
+                old[u] = load_irr<false>(vol_of<MULTI>(vs, e >> kEntryShift), e & kEntryMask, xs[u], ys[u]);
+                sum[u] = f3(sum_i[3 * o], sum_i[3 * o + 1], sum_i[3 * o + 2]);
+                inv[u] = inv_i[t];
+            }
+#pragma unroll
+            for (int u = 0; u < kBI; ++u) {
+                if (o0 + u * (int)blockDim.x >= np * ti) break;
+                const int e = s_probe[pp[u]];
+                const VolView& v = vol_of<MULTI>(vs, e >> kEntryShift);
+                store_irr_with_borders(v, e & kEntryMask, xs[u], ys[u],
+                                       blend_irr_value(v, bp, old[u], sum[u].x, sum[u].y, sum[u].z, inv[u],
+                                                       s_newly[pp[u]] != 0, status));
+            }
         }
         __syncthreads();
         if (threadIdx.x < np && s_newly[threadIdx.x]) {

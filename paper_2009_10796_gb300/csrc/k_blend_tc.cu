@@ -215,12 +215,6 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 __device__ __forceinline__ float comp4(float4 v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : v.z); }
 
-// Bytes of one stored texel (DDGI_IRR_* / DDGI_DIST_* formats).
-__device__ __forceinline__ int irr_texel_bytes(int fmt) {
-    return fmt == DDGI_IRR_FP32 ? 16 : (fmt == DDGI_IRR_FP16 ? 8 : 4);
-}
-__device__ __forceinline__ int dist_texel_bytes(int fmt) { return fmt == DDGI_DIST_FP32 ? 8 : 4; }
-
 }  // namespace
 
 // Weight tiles of one frame in the MMA operand layout, one block of
