@@ -709,9 +709,12 @@ cudaError_t launch_frame_setup_split(const FrameRot& rot, int R, int irr_n, int 
                                                       w_irr, inv_s_irr, w_dist, inv_s_dist, zero, n_zero, 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_frame_setup<false><<<(R + 255) / 256, 256, 0, st_dirs>>>(rot, nullptr, R, irr_n, dist_n, (double)cos_power,
-                                                                sf64, dirs, w_irr, inv_s_irr, w_dist, inv_s_dist,
-                                                                zero, n_zero, nwb);
+    // the directions in blocks of 64 rays, so the FP64 rotations of the
+    // frame's rays spread over several SMs' double-precision units
+    if (n_zero > 64) return cudaErrorInvalidValue;
+    k_frame_setup<false><<<(R + 63) / 64, 64, 0, st_dirs>>>(rot, nullptr, R, irr_n, dist_n, (double)cos_power, sf64,
+                                                              dirs, w_irr, inv_s_irr, w_dist, inv_s_dist, zero, n_zero,
+                                                              nwb);
     return cudaGetLastError();
 }
 
