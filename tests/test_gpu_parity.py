@@ -193,6 +193,32 @@ def test_maximum_sizes_parity(g, case):
     assert ei.max() <= REL and ed.max() <= REL and eq.max() <= REL
 
 
+@pytest.mark.parametrize("prec", ["BLEND_FP32", "BLEND_TF32"])
+def test_no_active_probe(g, prec):
+    """Degenerate volume: every probe inside one solid box sees only back
+    faces, so classification turns all of them Off (Sec. 6.1) and the active
+    list is empty; every later pass, the blend (SIMT or tensor-core) included,
+    runs on zero probes, the atlases stay zero, and a query whose cage holds
+    no active probe returns 0 (as the oracle does)."""
+    sc = synth.solid_box((-1.0, -1.0, -1.0), (9.0, 9.0, 9.0))
+    desc = synth.VolumeDesc(origin=(1.0, 1.0, 1.0), spacing=(2.0, 2.0, 2.0), counts=(4, 4, 4), rays_per_probe=64,
+                            hysteresis_irr=0.9, hysteresis_vis=0.9, seed=17)
+    L = synth.room_lights()
+    st, irr, dist, _ = run_oracle(sc, L, desc, [0, 1])
+    assert np.all(st == g.STATE_OFF)
+    V = g.Volume(desc)
+    S = g.Scene.from_arrays(sc)
+    for f in range(3):
+        V.update(S, L, f, precision=getattr(g, prec))
+    torch.cuda.synchronize()
+    V.poll_status()
+    assert np.array_equal(V.states().cpu().numpy(), st)
+    assert not V.irr_atlas().any() and not V.dist_atlas().any()
+    pos, nrm, cam = synth.room_queries(n=256)
+    E = V.query(to_dev(pos), to_dev(nrm), cam).cpu().numpy()
+    assert np.all(E == 0.0) and np.all(oracle.query(desc, st, irr, dist, pos, nrm, cam) == 0.0)
+
+
 def test_empty_scene_uniform_sky(g):
     a = np.array([0.3, 1.7, 0.05])
     L = synth.Lights(sky_a=a)
