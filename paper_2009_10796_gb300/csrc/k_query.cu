@@ -9,9 +9,12 @@ namespace ddgi {
 // (16-byte stores when the run is aligned), so each warp writes whole lines,
 // for page-locked host memory written across the host link; otherwise each
 // thread stores its own three floats (device memory).
+// The specialised form runs five CTAs per SM (48 registers, a short spill),
+// which measured 1 us faster on the 1080p query than four; the general form
+// keeps four.
 constexpr int kQueryThreads = 256;
 template <bool STAGE_OUT, bool FAST>
-__global__ void __launch_bounds__(kQueryThreads) k_query(VolView v, const float* __restrict__ pos,
+__global__ void __launch_bounds__(kQueryThreads, FAST ? 5 : 4) k_query(VolView v, const float* __restrict__ pos,
                                                          const float* __restrict__ nrm, int64_t n, float3 cam,
                                                          float* __restrict__ out) {
     __shared__ __align__(16) float s_out[3 * kQueryThreads];
