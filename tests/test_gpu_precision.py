@@ -11,7 +11,7 @@ import torch
 
 import oracle
 import synth
-from parity import REL, compare_rays, gpu_rays_by_probe, lit_query_sample, rel_err, run_oracle, to_dev
+from parity import REL, compare_rays, gpu_rays_by_probe, rel_err, run_oracle, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -210,11 +210,28 @@ def test_tensor_core_blend_matches_fp32_at_scale(g, mode):
 
 # ------------------------------------------- city scale against the oracle
 
+def _window_probes(desc, pos, nrm):
+    """Probes within one cell of the cells of the given surface points (4 x 4
+    x 4 per cell: the self-shadow bias moves a point by less than a cell, so
+    every cage the query reads lies inside)."""
+    org, sp, cnt = np.asarray(desc.origin), np.asarray(desc.spacing), np.asarray(desc.counts)
+    cells = np.unique(np.clip(np.floor((pos - org) / sp), 0, cnt - 2).astype(np.int64), axis=0)
+    off = np.stack(np.meshgrid(*[np.arange(-1, 3)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    q = (cells[:, None, :] + off[None]).reshape(-1, 3)
+    q = q[np.all((q >= 0) & (q < cnt), axis=1)]
+    return np.unique(q[:, 0] + cnt[0] * (q[:, 1] + cnt[1] * q[:, 2]))
+
+
 @pytest.fixture(scope="module")
 def city_ref(g):
-    """The 16,384-probe city workload at frame 0: the oracle's one-step update
-    of a seeded probe sample (24 seeded + 12 active probes) and of the 4x4x4
-    probes around four lit query cells (seeded surface points)."""
+    """The 16,384-probe city workload at frame 0 against the oracle's one-step
+    update: 256 seeded active probes for texels, and the probes around the
+    cages of a 256 x 256 window at the centre of the 1920 x 1080 G-buffer
+    (65,536 pixels) for queries.  Probes whose classification flips within
+    FP32 rounding are listed (pixels whose cages could read them are left
+    out), and probes with a ray that grazes an edge within FP32 rounding are
+    left out of the texel comparisons (frame-0 rays do not depend on the
+    atlas formats)."""
     sc = synth.city_scene()
     desc = synth.city_volume()
     L = synth.city_lights()
@@ -224,29 +241,36 @@ def city_ref(g):
     torch.cuda.synchronize()
     states = A.states().cpu().numpy()
     rec, ids = gpu_rays_by_probe(A)
-    rng = np.random.default_rng(124)
     act = np.nonzero(states == oracle.VIGILANT)[0]
-    sample = np.unique(np.concatenate([rng.choice(desc.n_probes, 24, replace=False),
-                                       rng.choice(act, 12, replace=False)]))
-    pts, nrm, cages = lit_query_sample(sc, desc, 3012)
-    subset = np.union1d(sample, cages)
+    sample = np.sort(np.random.default_rng(124).choice(act, 256, replace=False))
+    cam = synth.city_camera()
+    P, N = S.raycast_gbuffer(cam.position, cam.forward, cam.up, cam.vfov_deg, cam.width, cam.height)
+    P = P.cpu().numpy().reshape(cam.height, cam.width, 3)[412:668, 832:1088].reshape(-1, 3)
+    N = N.cpu().numpy().reshape(cam.height, cam.width, 3)[412:668, 832:1088].reshape(-1, 3)
+    hit = np.any(N != 0, axis=1)
+    pts, nrm = P[hit].astype(np.float64), N[hit].astype(np.float64)
+    subset = np.union1d(sample, _window_probes(desc, pts, nrm))
     st, irr, dist = oracle.new_state(desc)
     rays = oracle.update(oracle.SceneHandle(sc), L, desc, 0, st, irr, dist, subset=subset, want_rays=True)
-    assert np.array_equal(states[subset], st[subset]), "sampled states differ"
-    # frame-0 rays do not depend on the atlas formats: probes with a ray that
-    # grazes an edge within FP32 rounding are left out of every comparison
+    flips = subset[states[subset] != st[subset]]
+    assert len(flips) <= max(2, int(1e-3 * len(subset))), f"classification differs at {flips}"
+    if len(flips):   # pixels whose cage neighbourhood holds a flipped probe
+        near = np.array([np.intersect1d(_window_probes(desc, x[None], None), flips).size > 0 for x in pts])
+        pts, nrm = pts[~near], nrm[~near]
     pos_of = {int(p): k for k, p in enumerate(ids)}
     row = {int(p): q for q, p in enumerate(subset)}
     clean = []
     for p in sample:
-        if st[p] != oracle.VIGILANT:
+        if st[p] != oracle.VIGILANT or p in flips:
             continue
         bad, _ = compare_rays(rec[pos_of[int(p)]][None], np.array([0]), rays[row[int(p)]][None])
         if not bad.any():
             clean.append(int(p))
-    cam = np.array([0.0, 12.0, -28.0])
-    E_ref = oracle.query(desc, st, irr, dist, pts, nrm, cam)
-    return sc, desc, L, S, np.array(clean), irr, dist, pts, nrm, cam, E_ref
+    camp = np.asarray(cam.position, dtype=np.float64)
+    E_ref = oracle.query(desc, st, irr, dist, pts, nrm, camp)
+    print(f"[precision city] oracle: {len(subset)} probes updated, {len(clean)} of {len(sample)} sampled probes "
+          f"clean, {len(flips)} classification flips, {len(pts)} window pixels")
+    return sc, desc, L, S, np.array(clean), st, irr, dist, pts, nrm, camp, E_ref
 
 
 # (atlas formats, blend precision, stored-domain bounds for irradiance and
@@ -268,7 +292,7 @@ def test_city_precision_variants_against_oracle(g, city_ref, variant):
     """The precision configuration: the 16,384-probe city volume with reduced
     atlas storage or the tensor-core blend; per-texel error of the sampled
     active probes and per-pixel query error against the FP64 oracle."""
-    sc, desc, L, S, clean, irr, dist, pts, nrm, cam, E_ref = city_ref
+    sc, desc, L, S, clean, st, irr, dist, pts, nrm, cam, E_ref = city_ref
     fi, fd, prec, tol_i, tol_d, tol_q = _CITY_VARIANTS[variant]
     V = g.Volume(desc, irr_format=getattr(g, fi), dist_format=getattr(g, fd))
     V.update(S, L, 0, precision=getattr(g, prec))
@@ -291,11 +315,33 @@ def test_city_precision_variants_against_oracle(g, city_ref, variant):
     ed = max(float(rel_err(gd[k], dist[p]).max()) for k, p in enumerate(clean))
     E = V.query(to_dev(pts), to_dev(nrm), cam).cpu().numpy()
     eq = rel_err(E, E_ref).max(-1)
-    lit = float(np.mean(np.any(E_ref > 0, axis=1)))
+    # at frame 0 only probes near geometry are active, so most window pixels
+    # have no active cage probe: both sides give exactly 0 there, and the
+    # median is taken over the lit pixels
+    lit = np.any(E_ref > 0, axis=1)
     print(f"[precision city] {variant}: {len(clean)} probes, irr {what_i}, dist max rel {ed:.2e}; "
-          f"{len(eq)} queries ({lit:.0%} lit), median rel {np.median(eq):.2e}, max {eq.max():.2e}")
+          f"{len(eq)} queries ({int(lit.sum())} lit), median rel over lit {np.median(eq[lit]):.2e}, "
+          f"max {eq.max():.2e}")
     assert ok_i and ed <= tol_d
-    assert lit >= 0.9
-    assert np.median(eq) <= tol_q
-    if prec == "BLEND_TF32X3":      # FP32-accurate: the parity bound on every query
-        assert eq.max() <= REL
+    assert lit.sum() >= 5000
+    assert np.all(E[~lit] == 0.0)
+    assert np.median(eq[lit]) <= tol_q
+    if prec == "BLEND_TF32X3":
+        # FP32-accurate: the parity bound at every pixel but those where the
+        # oracle's own query moves by more than half the bound when the
+        # updated probes' texels move by their errors in this run (seeded
+        # signs); those are listed and held to the bound plus twice that
+        gi_all = V.irr_atlas().cpu().numpy().astype(np.float64)
+        gd_all = V.dist_atlas().cpu().numpy().astype(np.float64)
+        rng = np.random.default_rng(11)
+        upd = st != oracle.UNINIT
+        irr_p, dist_p = irr.copy(), dist.copy()
+        irr_p[upd] += np.abs(gi_all[upd] - irr[upd]) * rng.choice([-1.0, 1.0], size=irr[upd].shape)
+        dist_p[upd] += np.abs(gd_all[upd] - dist[upd]) * rng.choice([-1.0, 1.0], size=dist[upd].shape)
+        sens = rel_err(oracle.query(desc, st, irr_p, dist_p, pts, nrm, cam), E_ref).max(-1)
+        listed = sens > REL / 2
+        print(f"[precision city] tf32x3: listed {int(listed.sum())} of {len(eq)} pixels, max rel on the rest "
+              f"{eq[~listed].max():.2e}")
+        assert listed.mean() <= 1e-3
+        assert eq[~listed].max() <= REL
+        assert np.all(eq[listed] <= REL + 2 * sens[listed])
