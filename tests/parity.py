@@ -185,6 +185,30 @@ def flagged_probes(bad, ids):
     return np.asarray(ids)[np.nonzero(np.asarray(bad).any(axis=1))[0]]
 
 
+def fp32_texel_spread(desc, states, irr, dist, pos, nrm, cams, draws=4, seed=5):
+    """For each point (with its own camera, the query's w_o), the largest
+    relative change of the oracle's query when every atlas value moves by
+    one FP32 ulp with a seeded random sign, over `draws` draws.  Where this
+    exceeds the parity tolerance the FP32 atlas does not fix the query to
+    that tolerance (a Chebyshev weight where mu2 - mu^2 nearly cancels)."""
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    nrm = np.asarray(nrm, dtype=np.float64).reshape(-1, 3)
+    cams = np.asarray(cams, dtype=np.float64).reshape(-1, 3)
+    E0 = np.stack([oracle.query(desc, states, irr, dist, pos[k][None], nrm[k][None], cams[k])[0]
+                   for k in range(len(pos))])
+    rng = np.random.default_rng(seed)
+    ui = np.abs(np.spacing(np.asarray(irr, dtype=np.float32))).astype(np.float64)
+    ud = np.abs(np.spacing(np.asarray(dist, dtype=np.float32))).astype(np.float64)
+    out = np.zeros(len(pos))
+    for _ in range(draws):
+        ip = irr + ui * rng.choice([-1.0, 1.0], size=irr.shape)
+        dp = dist + ud * rng.choice([-1.0, 1.0], size=dist.shape)
+        for k in range(len(pos)):
+            E = oracle.query(desc, states, ip, dp, pos[k][None], nrm[k][None], cams[k])[0]
+            out[k] = max(out[k], float((np.abs(E - E0[k]) / np.maximum(np.abs(E0[k]), 1e-30)).max()))
+    return out
+
+
 def fp32_neighbourhood_spread(fn, pos, nrm, floor_scale):
     """For each point, the largest change of the oracle's result fn(pos, nrm)
     over the 26 neighbouring FP32 positions (one ulp per axis), relative to

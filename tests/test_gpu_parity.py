@@ -5,8 +5,8 @@ import torch
 
 import oracle
 import synth
-from parity import (REL, compare_rays, gpu_rays_by_probe, lit_query_sample, masked_texels, patched, rel_err,
-                    run_oracle, to_dev)
+from parity import (REL, compare_rays, fp32_neighbourhood_spread, fp32_texel_spread, gpu_rays_by_probe,
+                    lit_query_sample, masked_texels, patched, rel_err, run_oracle, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -318,7 +318,7 @@ def test_city_query_sampled_points(g, city):
 def city_steady(g):
     """The benchmark's city volume run for 60 frames (hysteresis 0.97, per-frame
     rotation, multi-bounce through the previous atlas, per-texel thresholds),
-    keeping, at frames 5 and 59, the GPU's state before the update (the
+    keeping, at frames 1, 5 and 59, the GPU's state before the update (the
     previous atlas the oracle's one-step update starts from) and after it."""
     sc = synth.city_scene()
     desc = synth.city_volume()
@@ -327,11 +327,11 @@ def city_steady(g):
     V = g.Volume(desc)
     snaps = {}
     for f in range(60):
-        if f in (5, 59):
+        if f in (1, 5, 59):
             prev = (V.states().cpu().numpy(), np.ascontiguousarray(V.irr_atlas().cpu().numpy(), dtype=np.float64),
                     np.ascontiguousarray(V.dist_atlas().cpu().numpy(), dtype=np.float64))
         V.update(S, L, f)
-        if f in (5, 59):
+        if f in (1, 5, 59):
             rec, ids = V.ray_records()
             snaps[f] = dict(prev=prev, rec=rec.cpu().numpy(), ids=ids.cpu().numpy().astype(np.int64),
                             states=V.states().cpu().numpy(), irr=V.irr_atlas().cpu().numpy(),
@@ -341,10 +341,10 @@ def city_steady(g):
     return sc, desc, L, S, V, snaps
 
 
-@pytest.mark.parametrize("frame", [5, 59])
+@pytest.mark.parametrize("frame", [1, 5, 59])
 def test_city_steady_state_one_step(g, city_steady, frame):
     """Steady-state frames of the benchmark workload: the oracle's one-step
-    update of 64 seeded active probes, started from the GPU's own previous
+    update of 256 seeded active probes, started from the GPU's own previous
     atlas and states, against the GPU's update of the same frame: per-ray
     records (shading reads the lit previous atlas), texels (hysteresis 0.97
     and the per-texel thresholds of Sec. 4.3), states."""
@@ -352,21 +352,55 @@ def test_city_steady_state_one_step(g, city_steady, frame):
     sn = snaps[frame]
     st0, irr0, dist0 = sn["prev"]
     act = np.nonzero(st0 == oracle.VIGILANT)[0]
-    sample = np.sort(np.random.default_rng(500 + frame).choice(act, 64, replace=False))
+    sample = np.sort(np.random.default_rng(500 + frame).choice(act, 256, replace=False))
     st, irr, dist = st0.copy(), irr0.copy(), dist0.copy()
     rays = oracle.update(oracle.SceneHandle(sc), L, desc, frame, st, irr, dist, subset=sample, want_rays=True)
     assert np.array_equal(sn["states"], np.where(np.isin(np.arange(desc.n_probes), sample), st, sn["states"]))
     pos_of = {int(p): k for k, p in enumerate(sn["ids"])}
     rec = sn["rec"][[pos_of[int(p)] for p in sample]].astype(np.float64)
     bad, err = compare_rays(rec, np.arange(len(sample)), rays)
+    # a flagged ray whose distance agrees hit the same surface: its radiance
+    # differs through the previous-atlas query at the hit point.  Such a ray
+    # is listed when that query is ill-conditioned there: the oracle's query
+    # moves by more than half the bound over the neighbouring FP32 hit
+    # positions (the GPU forms the hit point in FP32) or when the atlas values
+    # move by one FP32 ulp (the GPU evaluates the query in FP32), and its
+    # radiance must stay within the bound plus four times that spread (the
+    # FP32 query rounds the bilinear moments and mu^2 again, a few ulps on
+    # top of the stored values); rays whose distance differs are the grazing
+    # rays of the traversal
+    grazing = bad & (err[..., 3] > REL)
+    shade = bad & ~grazing
+    spread = np.zeros(int(shade.sum()))
+    if shade.any():
+        pi_, ri = np.nonzero(shade)
+        cx, cy, _ = desc.counts
+        ijk = np.stack([sample[pi_] % cx, (sample[pi_] // cx) % cy, sample[pi_] // (cx * cy)], 1)
+        o = np.asarray(desc.origin) + ijk * np.asarray(desc.spacing)
+        w = oracle.frame_dirs(desc.seed, frame, desc.rays_per_probe)[ri]
+        t, tri, _ = oracle.trace(oracle.SceneHandle(sc), o, w)
+        x = o + t[:, None] * w
+        v = sc.verts[sc.tris[tri]]
+        n = np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0])
+        n /= np.linalg.norm(n, axis=1, keepdims=True)
+        for k in range(len(x)):
+            spread[k] = fp32_neighbourhood_spread(
+                lambda P, N_: oracle.query(desc, st0, irr0, dist0, P, N_, x[k] - w[k]), x[k][None], n[k][None],
+                1e-30)[0]
+        spread = np.maximum(spread, fp32_texel_spread(desc, st0, irr0, dist0, x, n, x - w, draws=8))
     mi, md = masked_texels(desc, desc.seed, frame, bad, sample)
     ei = rel_err(sn["irr"][sample], irr[sample]).max(-1)
     ed = rel_err(sn["dist"][sample], dist[sample]).max(-1)
     mi, md = mi[sample], md[sample]
-    _report(f"city one-step f{frame}", probes=len(sample), rays=bad.size, flagged=int(bad.sum()),
-            ray_max_rel=float(err[~bad].max()), irr_max=float(ei[~mi].max()), dist_max=float(ed[~md].max()),
-            masked_irr=int(mi.sum()), masked_dist=int(md.sum()))
-    assert bad.sum() <= max(2, int(1e-4 * bad.size))
+    _report(f"city one-step f{frame}", probes=len(sample), rays=bad.size, grazing=int(grazing.sum()),
+            shade_listed=int(shade.sum()), shade_err=[float(e) for e in err[shade][:, :3].max(-1)],
+            shade_spread=[float(e) for e in spread], ray_max_rel=float(err[~bad].max()),
+            irr_max=float(ei[~mi].max()), dist_max=float(ed[~md].max()), masked_irr=int(mi.sum()),
+            masked_dist=int(md.sum()))
+    assert grazing.sum() <= max(2, int(1e-4 * bad.size))
+    assert shade.sum() <= max(2, int(1e-3 * bad.size))
+    assert np.all(spread > REL / 2)
+    assert np.all(err[shade][:, :3].max(-1) <= REL + 4 * spread)
     assert ei[~mi].max() <= REL and ed[~md].max() <= REL
 
 
