@@ -185,20 +185,22 @@ def flagged_probes(bad, ids):
     return np.asarray(ids)[np.nonzero(np.asarray(bad).any(axis=1))[0]]
 
 
-def fp32_texel_spread(desc, states, irr, dist, pos, nrm, cams, draws=4, seed=5):
+def fp32_texel_spread(desc, states, irr, dist, pos, nrm, cams, draws=4, seed=5, ulps=4):
     """For each point (with its own camera, the query's w_o), the largest
     relative change of the oracle's query when every atlas value moves by
-    one FP32 ulp with a seeded random sign, over `draws` draws.  Where this
-    exceeds the parity tolerance the FP32 atlas does not fix the query to
-    that tolerance (a Chebyshev weight where mu2 - mu^2 nearly cancels)."""
+    `ulps` FP32 ulps with a seeded random sign, over `draws` draws: the size
+    of the rounding an FP32 evaluation adds to its inputs (the bilinear
+    moments, mu^2).  Where this exceeds the parity tolerance the FP32
+    evaluation cannot fix the query to that tolerance (a Chebyshev weight
+    where mu2 - mu^2 nearly cancels)."""
     pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
     nrm = np.asarray(nrm, dtype=np.float64).reshape(-1, 3)
     cams = np.asarray(cams, dtype=np.float64).reshape(-1, 3)
     E0 = np.stack([oracle.query(desc, states, irr, dist, pos[k][None], nrm[k][None], cams[k])[0]
                    for k in range(len(pos))])
     rng = np.random.default_rng(seed)
-    ui = np.abs(np.spacing(np.asarray(irr, dtype=np.float32))).astype(np.float64)
-    ud = np.abs(np.spacing(np.asarray(dist, dtype=np.float32))).astype(np.float64)
+    ui = ulps * np.abs(np.spacing(np.asarray(irr, dtype=np.float32))).astype(np.float64)
+    ud = ulps * np.abs(np.spacing(np.asarray(dist, dtype=np.float32))).astype(np.float64)
     out = np.zeros(len(pos))
     for _ in range(draws):
         ip = irr + ui * rng.choice([-1.0, 1.0], size=irr.shape)
@@ -209,11 +211,11 @@ def fp32_texel_spread(desc, states, irr, dist, pos, nrm, cams, draws=4, seed=5):
     return out
 
 
-def fp32_neighbourhood_spread(fn, pos, nrm, floor_scale):
+def fp32_neighbourhood_spread(fn, pos, nrm, floor_scale, ulps=1):
     """For each point, the largest change of the oracle's result fn(pos, nrm)
-    over the 26 neighbouring FP32 positions (one ulp per axis), relative to
-    the scale rel_err uses (max(|ref|, floor_scale)).  Where this exceeds the
-    parity tolerance the FP32 input does not fix the result to that
+    over the 26 neighbouring FP32 positions (`ulps` ulps per axis), relative
+    to the scale rel_err uses (max(|ref|, floor_scale)).  Where this exceeds
+    the parity tolerance the FP32 input does not fix the result to that
     tolerance: rounding at the input's scale alone moves it further."""
     pos = np.asarray(pos, dtype=np.float64)
     nrm = np.asarray(nrm, dtype=np.float64)
@@ -221,7 +223,7 @@ def fp32_neighbourhood_spread(fn, pos, nrm, floor_scale):
                   dtype=np.float64)
     p32 = pos.astype(np.float32)
     ulp = np.abs(np.nextafter(p32, np.float32(np.inf)) - p32).astype(np.float64)
-    P = (pos[:, None, :] + nb[None] * ulp[:, None, :]).reshape(-1, 3)
+    P = (pos[:, None, :] + ulps * nb[None] * ulp[:, None, :]).reshape(-1, 3)
     N_ = np.repeat(nrm, len(nb), axis=0)
     E0 = fn(pos, nrm)
     En = fn(P, N_).reshape(len(pos), len(nb), -1)

@@ -217,3 +217,140 @@ def test_terrain_cascades_full_size_frame0_sampled(g):
     assert listed.mean() <= 1e-3
     assert e[~listed].max() <= REL
     assert np.all(e[listed] <= REL + 2.0 * spread[listed])
+
+
+def test_terrain_cascades_full_size_scrolled_one_step(g):
+    """The batched-cascade workload at full size after its windows have
+    scrolled (frames 3 and 8, the camera moving 0.6 m per frame): starting
+    from the GPU's own cascade state before the frame, the oracle scrolls the
+    windows to the frame's camera (planes that leapfrog are reset) and makes
+    one update step for a seeded sample of 6 active probes per volume, hit
+    shading reading every volume's previous atlas; the sampled probes' states,
+    per-ray records and texels must match the GPU's frame.  Probes with a
+    flagged ray are skipped: rays that graze an edge within FP32 rounding are
+    counted, and rays whose radiance differs at an ill-conditioned hit-point
+    query are listed and bounded by their sensitivity."""
+    sc = synth.terrain_scene()
+    L = synth.city_lights()
+    descs = synth.terrain_cascades()
+    S = g.Scene.from_arrays(sc)
+    C = g.Cascade(descs)
+    C.set_tuning(8, 16)
+    h = oracle.SceneHandle(sc)
+    vols = [oracle.make_volume(d) for d in descs]
+    shadow = [oracle.new_state(d) for d in descs]   # state arrays the replayed scrolls run on between test frames
+    rng = np.random.default_rng(2026)
+    compared = 0
+    for f in range(9):
+        cam = synth.terrain_camera_path(f)
+        test = f in (3, 8)
+        if test:
+            prev = [(C.states(k).cpu().numpy().copy(), C.irr_atlas(k).cpu().numpy().astype(np.float64),
+                     C.dist_atlas(k).cpu().numpy().astype(np.float64)) for k in range(C.n)]
+        C.update(S, L, f, cam, use_graph=True)
+        torch.cuda.synchronize()
+        C.poll_status()
+        for k, d in enumerate(descs):
+            oracle.tracking_scroll(vols[k], cam, *(prev[k] if test else shadow[k]))
+            lo, hi = _track_box(d, cam)
+            vols[k].blend_lo[:] = list(lo)
+            vols[k].blend_hi[:] = list(hi)
+            origin, shift = C.window(k)
+            assert np.allclose(origin, list(vols[k].origin), atol=1e-12)
+            assert np.array_equal(np.mod(shift, d.counts), np.mod(list(vols[k].shift), d.counts))
+        if not test:
+            continue
+        rec, vol_of, probe_of = C.ray_records()
+        rec = rec.cpu().numpy().astype(np.float64)
+        vol_of = vol_of.cpu().numpy()
+        probe_of = probe_of.cpu().numpy()
+        subsets = []
+        for k in range(C.n):
+            act = np.sort(probe_of[vol_of == k])
+            subsets.append(np.sort(rng.choice(act, min(6, len(act)), replace=False)).astype(np.int64))
+        pre = [(a.copy(), b.copy(), c.copy()) for a, b, c in prev]
+        rays = oracle.update_cascade(h, L, vols, f, [p[0] for p in prev], [p[1] for p in prev], [p[2] for p in prev],
+                                     subsets=subsets, want_rays=True)
+        where = {(int(v), int(p)): i for i, (v, p) in enumerate(zip(vol_of, probe_of))}
+        grazing = checked = 0
+        worst_r = worst_i = worst_d = 0.0
+        shading = {}   # (volume, probe) -> (subset row, flagged rays, their errors)
+        for k in range(C.n):
+            st, irr, dist = prev[k]
+            gst = C.states(k).cpu().numpy()
+            gi = C.irr_atlas(k).cpu().numpy().astype(np.float64)
+            gd = C.dist_atlas(k).cpu().numpy().astype(np.float64)
+            sub = subsets[k]
+            assert np.array_equal(gst[sub], st[sub]), f"sampled states differ, volume {k}, frame {f}"
+            for q, p in enumerate(sub):
+                bad, err = compare_rays(rec[where[(k, int(p))]][None], np.array([0]), rays[k][q][None])
+                if bad.any():
+                    graze = bad & (err[..., 3] > REL)
+                    grazing += int(graze.sum())
+                    if not graze.any():
+                        shading[(k, int(p))] = (q, np.nonzero(bad[0])[0], err[0][bad[0]][:, :3].max(-1))
+                    continue
+                checked += 1
+                worst_r = max(worst_r, float(err.max()))
+                worst_i = max(worst_i, float(rel_err(gi[p], irr[p]).max()))
+                worst_d = max(worst_d, float(rel_err(gd[p], dist[p]).max()))
+        # a flagged ray whose distance agrees hit the same surface, and its
+        # radiance differs through the cascade query of the previous atlases
+        # at the hit: it is listed where that query is ill-conditioned, i.e.
+        # where the oracle's record moves by more than half the bound when
+        # every previous atlas value moves by four FP32 ulps (the rounding an
+        # FP32 query adds to the bilinear moments and mu^2; four seeded sign
+        # draws) or where the oracle's cascade query moves by that much when
+        # the hit position moves by four FP32 ulps over its 26 neighbours (the
+        # GPU forms the hit point as o + t w in FP32; the volumes' fall-off
+        # weights and the stop once they reach 1 depend on it), and it must
+        # stay within the bound plus twice that
+        if shading:
+            sens = {key: np.zeros(len(v[1])) for key, v in shading.items()}
+            draw_sub = [np.array(sorted(p for (kk, p) in shading if kk == k), dtype=np.int64) for k in range(C.n)]
+            prng = np.random.default_rng(31)
+            for _ in range(4):
+                pert = []
+                for a, b, c in pre:
+                    ub = 4 * np.abs(np.spacing(b.astype(np.float32))).astype(np.float64)
+                    uc = 4 * np.abs(np.spacing(c.astype(np.float32))).astype(np.float64)
+                    pert.append((a.copy(), b + ub * prng.choice([-1.0, 1.0], size=b.shape),
+                                 c + uc * prng.choice([-1.0, 1.0], size=c.shape)))
+                pr = oracle.update_cascade(h, L, vols, f, [x[0] for x in pert], [x[1] for x in pert],
+                                           [x[2] for x in pert], subsets=draw_sub, want_rays=True)
+                for (k, p), (q, rr, _) in shading.items():
+                    j = int(np.nonzero(draw_sub[k] == p)[0][0])
+                    ref = rays[k][q][rr, :3]
+                    chg = np.abs(pr[k][j][rr, :3] - ref) / np.maximum(np.abs(ref), 1e-30)
+                    sens[(k, p)] = np.maximum(sens[(k, p)], chg.max(-1))
+            dirs = oracle.frame_dirs(descs[0].seed, f, descs[0].rays_per_probe)
+            for (k, p), (q, rr, _) in shading.items():
+                cnt = np.asarray(descs[k].counts)
+                phys = np.array([p % cnt[0], (p // cnt[0]) % cnt[1], p // (cnt[0] * cnt[1])])
+                origin, shift = C.window(k)
+                o = np.asarray(origin) + np.mod(phys - np.asarray(shift), cnt) * np.asarray(descs[k].spacing)
+                for j, r in enumerate(rr):
+                    w = dirs[r]
+                    t, tri, _ = oracle.trace(h, o[None], w[None])
+                    x = o + t[0] * w
+                    v = sc.verts[sc.tris[tri[0]]]
+                    n = np.cross(v[1] - v[0], v[2] - v[0])
+                    n /= np.linalg.norm(n)
+                    sp_ = fp32_neighbourhood_spread(
+                        lambda P, N_: oracle.query_cascade(vols, [a for a, _, _ in pre], [b for _, b, _ in pre],
+                                                           [c for _, _, c in pre], P, N_, x - w),
+                        x[None], n[None], 1e-30, ulps=4)[0]
+                    sens[(k, p)][j] = max(sens[(k, p)][j], sp_)
+            for key, (q, rr, e) in shading.items():
+                print(f"[terrain cascade] frame {f}: listed shading rays of volume {key[0]} probe {key[1]}: "
+                      f"errors {[float(x) for x in e]}, sensitivities {[float(x) for x in sens[key]]}")
+                assert np.all(sens[key] > REL / 2)
+                assert np.all(e <= REL + 2 * sens[key])
+        n_shade = sum(len(v[1]) for v in shading.values())
+        print(f"[terrain cascade] frame {f}: {sum(len(s) for s in subsets)} sampled active probes, {checked} "
+              f"compared, grazing rays {grazing}, listed shading rays {n_shade}, records max rel {worst_r:.2e}, "
+              f"irr {worst_i:.2e}, dist {worst_d:.2e}")
+        assert checked >= 16 and grazing <= 3 and n_shade <= 0.005 * sum(len(s) for s in subsets) * descs[0].rays_per_probe
+        assert worst_r <= REL and worst_i <= REL and worst_d <= REL
+        compared += checked
+    assert compared >= 32
