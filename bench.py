@@ -64,6 +64,13 @@ L2_PROBE_BYTES = (16 << 20, 32 << 20)
 PRIMARY_L2_BYTES = 309_296_832
 
 
+def workload_config(desc, n_pix):
+    """The workload and timing protocol both arms report (identical in the
+    GPU arm's line and the reference arm's)."""
+    return {"workload": WORKLOAD, "probes": desc.n_probes, "rays_per_probe": desc.rays_per_probe,
+            "query_pixels": n_pix, "l2": "flushed between timed steps (256 MiB write outside the events)"}
+
+
 def l2_read_rate(g, torch, stream, passes=16, reps=5):
     """L2 read rate (GB/s): the largest over L2_PROBE_BYTES of bytes x passes
     / event time of ddgi_measure_l2_read, after one untimed call that makes
@@ -242,7 +249,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Grays/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "cpu"},
+        "data": "synthetic", "config": workload_config(desc, n_pix),
+        "active_probes": n_active, "parallelism": "host cores (FP64 oracle)",
         "cpu_baseline": {"value": value, "unit": "Grays/s", "cores": cores(), "kind": "oracle",
                          "sample": f"{n_ps} active probes (one update) + {n_qs} query points per "
                                    f"step, extrapolated to {n_active} active probes (oracle's own "
@@ -503,14 +511,13 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "strong" if sharded else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "probes": desc.n_probes, "active_probes": n_active,
-                   "rays_per_probe": R, "query_pixels": n_pix,
-                   "l2": "flushed between timed steps (256 MiB write outside the events)",
-                   "timing": "value: CUDA events at the step boundaries only; stage_ms, query and the "
-                             "roofline launch times: a second pass of the same steps with per-stage "
-                             "events on the update stream",
-                   "parallelism": ("sharded: z-slabs of probes, NCCL all-gather of the updated slabs, "
-                                   "pixel-sharded query" if sharded else ("replicas" if world > 1 else "single GPU"))},
+        "config": workload_config(desc, n_pix),
+        "active_probes": n_active,
+        "timing": "value: CUDA events at the step boundaries only; stage_ms, query and the "
+                  "roofline launch times: a second pass of the same steps with per-stage "
+                  "events on the update stream",
+        "parallelism": ("sharded: z-slabs of probes, NCCL all-gather of the updated slabs, "
+                        "pixel-sharded query" if sharded else ("replicas" if world > 1 else "single GPU")),
         "update_ms_per_frame": ms - q_ms, "query_ms_1080p": q_ms, "glossy_query_ms_1080p": glossy_ms,
         "trace_grays_per_s": n_active_local * R / (trace_ms_avg * 1e-3) / 1e9,
         "stage_ms": {k: v[0] / max(v[1], 1) for k, v in timings.items()},
