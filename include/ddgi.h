@@ -21,7 +21,9 @@
  *     ddgi_stream (a cudaStream_t; NULL is the legacy default stream).  No
  *     call synchronises the device unless its comment says so.
  *   - The library owns scenes and volumes (opaque handles).  A handle may be
- *     used from one host thread at a time.
+ *     used from one host thread at a time; different handles may be used
+ *     from several host threads at once, on one device or several (the
+ *     library's own once-per-device kernel setup is guarded).
  *   - Vectors are float32 [n][3] arrays unless stated.  Triangles are wound
  *     counter-clockwise seen from their front side.
  *   - Stored irradiance is the cosine-weighted mean radiance M; queries

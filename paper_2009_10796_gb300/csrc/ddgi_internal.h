@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -116,6 +117,28 @@ constexpr int kRefDone = (int)0x80000000;
 constexpr int kWideFullDepth = 20;
 constexpr int kStackSize4 = 128;
 static_assert(3 * kWideFullDepth + 63 <= kStackSize4, "4-wide traversal stack bound");
+
+// Host-side, once-per-device setup of a kernel (shared-memory opt-in and
+// the like), safe when several host threads launch at once: f() runs under
+// the flags' mutex until it succeeds once on the current device.
+constexpr int kMaxHostDevices = 64;
+struct DeviceOnce {
+    std::mutex m;
+    bool done[kMaxHostDevices] = {};
+};
+
+template <typename F>
+inline cudaError_t once_per_device(DeviceOnce& once, F&& f) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxHostDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(once.m);
+    if (once.done[dev]) return cudaSuccess;
+    e = f();
+    if (e == cudaSuccess) once.done[dev] = true;
+    return e;
+}
 
 // Volumes a kernel works on: one view by value (a single volume) or a device
 // table of up to kMaxVolumes views (a cascade).  Probe lists hold entries

@@ -728,39 +728,38 @@ cudaError_t launch_frame_setup_dev(const FrameRot* rot_dev, int R, int irr_n, in
 }
 
 // Sets the kernel's dynamic shared-memory cap to the device's opt-in maximum
-// less its static shared memory, once per process (host-side attribute; must
+// less its static shared memory, once per device (host-side attribute; must
 // not run under stream capture).
 template <typename K>
-static cudaError_t allow_max_smem(K kernel, bool& done) {
-    if (done) return cudaSuccess;
-    int dev = 0, optin = 0;
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 optin - (int)fa.sharedSizeBytes);
-    if (e == cudaSuccess) done = true;
-    return e;
+static cudaError_t allow_max_smem(K kernel, DeviceOnce& once) {
+    return once_per_device(once, [&]() {
+        int dev = 0, optin = 0;
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - (int)fa.sharedSizeBytes);
+        return e;
+    });
 }
 
+// The current device's opt-in shared memory per block (48 KB if it cannot
+// be read).
 static int smem_optin() {
-    static int optin = 0;
-    if (optin == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-            optin = 48 * 1024;
-    }
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        optin = 48 * 1024;
     return optin;
 }
 
 // Opts both blend kernels of one instantiation into the maximum dynamic
-// shared memory, once per process.
+// shared memory, once per device.
 template <bool MULTI, int PGS>
 static cudaError_t opt_in_blend() {
-    static bool tiled = false, rows = false;
+    static DeviceOnce tiled, rows;
     cudaError_t e = allow_max_smem(k_blend_tiled<MULTI, PGS>, tiled);
     if (e == cudaSuccess) e = allow_max_smem(k_blend_simt<MULTI, PGS>, rows);
     return e;
@@ -781,13 +780,10 @@ static cudaError_t launch_tiled(const VolSet& vs, const BlendParams& bp, int irr
     if (e != cudaSuccess) return e;
     const TiledShape ts = tiled_shape(PG, bp.R, irr_n, dist_n);
     // one wave of resident CTAs; the kernel splits the active probes evenly
-    static int occ_threads = -1, occ = 0;
-    if (occ_threads != ts.threads) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_blend_tiled<MULTI, PG>, ts.threads, ts.smem);
-        if (e != cudaSuccess) return e;
-        occ_threads = ts.threads;
-    }
-    int dev = 0, sms = 0;
+    int occ = 0, dev = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_blend_tiled<MULTI, PG>, ts.threads, ts.smem)) !=
+        cudaSuccess)
+        return e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     grid = sms * (occ > 0 ? occ : 1);

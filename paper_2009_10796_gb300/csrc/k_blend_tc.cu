@@ -707,13 +707,12 @@ static cudaError_t blend_tc(const VolSet& vs, const BlendParams& bp_in, int irr_
                             const float* inv_irr,
                             const float* inv_dist, const float4* records, const int32_t* active, const int32_t* count,
                             uint32_t* status, int grid, cudaStream_t st) {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_blend_tc<MODE, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)Tc<MODE>::smem_bytes);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static DeviceOnce configured;
+    cudaError_t e = once_per_device(configured, [] {
+        return cudaFuncSetAttribute(k_blend_tc<MODE, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)Tc<MODE>::smem_bytes);
+    });
+    if (e != cudaSuccess) return e;
     BlendParams bp = bp_in;   // the epilogue's divisors: texel counts and tile widths
     bp.div_ti = make_fast_div((uint32_t)(irr_n * irr_n));
     bp.div_td = make_fast_div((uint32_t)(dist_n * dist_n));
