@@ -62,6 +62,13 @@ L2_PROBE_BYTES = (16 << 20, 32 << 20)
 # L2 bytes (lts__t_bytes) of one k_trace_primary launch on this workload,
 # from the same ncu capture rules as PRIMARY_TRAFFIC_BYTES
 PRIMARY_L2_BYTES = 309_296_832
+# Warp instructions of one launch (smsp__inst_executed.sum, ncu) of the
+# primary pass and of the 1080p query on this workload: their issue rate
+# against the SMs' peak (four schedulers each issuing one warp instruction
+# per clock) is the bound these issue-limited kernels meet first; set to
+# None whenever the kernel changes until it is captured again
+PRIMARY_WARP_INSTR = 139_814_805
+QUERY_WARP_INSTR = 65_485_903
 
 
 def workload_config(desc, n_pix):
@@ -451,6 +458,14 @@ def run_gpu(args):
     achieved = prim_ops / (prim_ms * 1e-3) / 1e12
     shadow_achieved = shadow_ops / (shadow_ms * 1e-3) / 1e12
     prim_l2_bytes = BYTES_PER_WIDE_NODE * stats["nodes"] + BYTES_PER_TRI * stats["tris"]
+    issue_peak = sm_count * 4 * pk.get("sm_max_mhz", 2070.0) * 1e6   # warp instructions per second
+
+    def issue(instr, launch_ms):
+        if not instr:
+            return None
+        rate = instr / (launch_ms * 1e-3)
+        return {"bound": "issue", "achieved": rate / 1e12, "peak": issue_peak / 1e12,
+                "unit": "T warp-instr/s", "frac": rate / issue_peak, "instructions_per_launch": instr}
     l2_peak = l2_read_rate(g, torch, stream)
     blend_ms = timings["blend"][0] / max(timings["blend"][1], 1)
     blend_bytes = n_active_local * (R * 16 + 2000 + 2816)      # records in, old interior in, tiles out
@@ -540,7 +555,8 @@ def run_gpu(args):
                                          "loads over an L2-resident buffer",
                             "bytes_kind": "node visits x 112 B + triangle tests x 48 B (counting build); "
                                           "traffic: lts__t_bytes of one launch (ncu), most node bytes "
-                                          "being L1 hits"}},
+                                          "being L1 hits"},
+                     "issue": issue(PRIMARY_WARP_INSTR, prim_ms)},
         "roofline_shadow": {"bound": "alu", "kernel": "k_trace_shadow", "achieved": shadow_achieved,
                             "peak": peak_tops, "unit": "TFLOP/s", "frac": shadow_achieved / peak_tops,
                             "launch_ms": shadow_ms},
@@ -552,7 +568,8 @@ def run_gpu(args):
                            "fp32": {"achieved": blend_flop / (blend_ms * 1e-3) / 1e12, "peak": 2 * peak_tops,
                                     "unit": "TFLOP/s", "frac": blend_flop / (blend_ms * 1e-3) / 1e12 / (2 * peak_tops)}},
         "roofline_query": {"bound": "hbm", "achieved": q_bytes / (q_ms * 1e-3) / 1e9, "peak": hbm,
-                           "unit": "GB/s", "frac": q_bytes / (q_ms * 1e-3) / 1e9 / hbm},
+                           "unit": "GB/s", "frac": q_bytes / (q_ms * 1e-3) / 1e9 / hbm,
+                           "issue": issue(QUERY_WARP_INSTR, q_ms)},
         "tensor_blend": {name: {
             "blend": TC_BLEND_DOC[name],
             "ms_per_step": float(np.mean(m[0])),
