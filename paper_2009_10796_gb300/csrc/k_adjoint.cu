@@ -179,8 +179,8 @@ __global__ void k_shade_adjoint(DevScene s, VolView v_before, Lights L, const fl
     const int lane = threadIdx.x & 31;
     const float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
     const RayPre r_sun = ray_pre(f3(0.0f, 0.0f, 0.0f), tol);
-    int stack[kStackSize4];
-    WwLane<kStackSize4> w;
+    int2 stack[kStackSize4];
+    WwLane<kStackSize4, int2> w;
     w.stack = stack;
     // warp-uniform loop: 32 rays per warp through the warp-cooperative 4-wide
     // walk (rays without a gradient take part without tracing), then their

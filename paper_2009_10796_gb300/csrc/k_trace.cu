@@ -21,8 +21,8 @@ __global__ void __launch_bounds__(256) k_classify(DevScene s, VolSet vs, const f
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int n = *count;
-    int stack[kStackSize4];
-    WwLane<kStackSize4> w;
+    int2 stack[kStackSize4];
+    WwLane<kStackSize4, int2> w;
     w.stack = stack;
     for (int q = warp; q < n; q += nwarps) {
         int e = list[q];
@@ -81,8 +81,8 @@ __global__ void __launch_bounds__(128) k_trace_shade(DevScene s, VolView v, Ligh
     const int lane = threadIdx.x & 31;
     const float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
     const RayPre r_sun = ray_pre(f3(0.0f, 0.0f, 0.0f), tol);
-    int stack[kStackSize4];
-    WwLane<kStackSize4> w;
+    int2 stack[kStackSize4];
+    WwLane<kStackSize4, int2> w;
     w.stack = stack;
     // warp-uniform loop: each warp takes 32 consecutive rays through the
     // warp-cooperative 4-wide walk, then their shadow rays the same way
@@ -226,8 +226,8 @@ __global__ void __launch_bounds__(256, 5) k_trace_primary(DevScene s, VolSet vs,
     int entry = 0;      // its probe's list entry
     bool exhausted = false;
     RayPre r = ray_pre(f3(0.0f, 0.0f, 0.0f), f3(0.0f, 0.0f, 1.0f));   // the lane's ray (r.d its direction)
-    int stack[kStackSize4];
-    WwLane<kStackSize4> w;
+    int2 stack[kStackSize4];
+    WwLane<kStackSize4, int2> w;
     w.stack = stack;
     ww_start(s, w, false);
     while (true) {
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolSet vs, Lig
     bool exhausted = false;
     const RayPre r_sun = ray_pre(f3(0.0f, 0.0f, 0.0f), tol);   // every shadow ray runs towards the sun
     RayPre r = r_sun;
-    int stack[kStackSize4];
+    int stack[kStackSize4];   // any-hit walk: plain references (no hit distance to prune by)
     WwLane<kStackSize4> w;
     w.stack = stack;
     ww_start(s, w, false);
@@ -469,8 +469,8 @@ __global__ void __launch_bounds__(256) k_optimize(DevScene s, VolView v, const f
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int n = *count;
     const DevScene& sc = s;
-    int stack[kStackSize4];
-    WwLane<kStackSize4> w;
+    int2 stack[kStackSize4];
+    WwLane<kStackSize4, int2> w;
     w.stack = stack;
     for (int q = warp; q < n; q += nwarps) {
         const int p = list[q];

@@ -278,20 +278,41 @@ constexpr int kDone = kRefDone;         // empty-stack sentinel, below every lea
 
 __device__ __forceinline__ int leaf_code(int child, int cnt) { return ~(((~child) << kLeafBits) | (cnt - 1)); }
 
+// Stack entries of the walk: a node or leaf reference alone (int; any-hit
+// walks), or the reference with the entry distance of its box (int2;
+// closest-hit walks).  A popped int2 entry whose box starts beyond the
+// closest hit found since it was pushed is dropped without a visit: no
+// triangle in that box can be closer.  An entry at exactly the hit distance
+// is kept (the tie rule may still prefer a triangle in it).
+template <typename E>
+struct StackOps;
+template <>
+struct StackOps<int> {
+    static __device__ __forceinline__ int make(int ref, float) { return ref; }
+    static __device__ __forceinline__ bool live(int, float) { return true; }
+    static __device__ __forceinline__ int ref(int e) { return e; }
+};
+template <>
+struct StackOps<int2> {
+    static __device__ __forceinline__ int2 make(int ref, float k) { return make_int2(ref, __float_as_int(k)); }
+    static __device__ __forceinline__ bool live(int2 e, float t) { return __int_as_float(e.y) <= t; }
+    static __device__ __forceinline__ int ref(int2 e) { return e.x; }
+};
+
 // Per-lane state of the warp-cooperative walk.  The stack array lives
 // apart from the scalar fields (a pointer to the caller's local array), so
 // the fields stay in registers while only the array goes to local memory.
-template <int N = kStackSize>
+template <int N = kStackSize, typename E = int>
 struct WwLane {
-    int* stack;   // N entries
+    E* stack;   // N entries
     int sp;
     int node;   // next internal node, a leaf code taken from the stack, or kDone
     int leaf;   // parked leaf code or kNoLeaf
     Hit h;
 };
 
-template <int N>
-__device__ __forceinline__ void ww_start(const DevScene& s, WwLane<N>& w, bool valid) {
+template <int N, typename E>
+__device__ __forceinline__ void ww_start(const DevScene& s, WwLane<N, E>& w, bool valid) {
     w.sp = 0;
     w.node = (valid && s.n_nodes > 0) ? 0 : kDone;
     w.leaf = kNoLeaf;
@@ -300,17 +321,25 @@ __device__ __forceinline__ void ww_start(const DevScene& s, WwLane<N>& w, bool v
     w.h.k = -1;
 }
 
-template <int N>
-__device__ __forceinline__ int ww_pop(WwLane<N>& w) { return w.sp > 0 ? w.stack[--w.sp] : kDone; }
+// The next live stack entry (entries whose box starts beyond the current
+// hit are dropped), or kDone.
+template <int N, typename E>
+__device__ __forceinline__ int ww_pop(WwLane<N, E>& w) {
+    while (w.sp > 0) {
+        const E e = w.stack[--w.sp];
+        if (StackOps<E>::live(e, w.h.t)) return StackOps<E>::ref(e);
+    }
+    return kDone;
+}
 
-template <bool ANY, int N, bool COUNT = false>
-__device__ __forceinline__ void ww_leaves(const DevScene& s, const RayPre& r, WwLane<N>& w,
+template <bool ANY, int N, bool COUNT = false, typename E = int>
+__device__ __forceinline__ void ww_leaves(const DevScene& s, const RayPre& r, WwLane<N, E>& w,
                                           TraceCount* tc = nullptr);
 
 // Leaf phase of a round: test the parked leaf and the leaves popped right
 // after it.  COUNT adds triangle tests to *tc (measurement builds only).
-template <bool ANY, int N, bool COUNT>
-__device__ __forceinline__ void ww_leaves(const DevScene& s, const RayPre& r, WwLane<N>& w, TraceCount* tc) {
+template <bool ANY, int N, bool COUNT, typename E>
+__device__ __forceinline__ void ww_leaves(const DevScene& s, const RayPre& r, WwLane<N, E>& w, TraceCount* tc) {
     while (w.leaf != kNoLeaf) {
         int code = ~w.leaf;
         int first = code >> kLeafBits, cnt = (code & ((1 << kLeafBits) - 1)) + 1;
@@ -363,8 +392,8 @@ __device__ __forceinline__ void cx(float& ka, int& va, float& kb, int& vb) {
 // farthest first (closest-hit rays; shadow rays push in slot order, any hit
 // ends them).  Leaves found among the children are parked or pushed as leaf
 // codes exactly as in the binary walk.
-template <bool ANY, bool COUNT = false>
-__device__ __forceinline__ void ww4_round(const DevScene& s, const RayPre& r, WwLane<kStackSize4>& w,
+template <bool ANY, bool COUNT = false, typename E = int>
+__device__ __forceinline__ void ww4_round(const DevScene& s, const RayPre& r, WwLane<kStackSize4, E>& w,
                                           TraceCount* tc = nullptr) {
     while (true) {
         if (w.node >= 0) {
@@ -389,9 +418,9 @@ __device__ __forceinline__ void ww4_round(const DevScene& s, const RayPre& r, Ww
             }
             // no bound test: scene creation checks that the hierarchy keeps the
             // stack within kStackSize4 (wide_stack_bound)
-            if (k3 != INFINITY) w.stack[w.sp++] = v3;
-            if (k2 != INFINITY) w.stack[w.sp++] = v2;
-            if (k1 != INFINITY) w.stack[w.sp++] = v1;
+            if (k3 != INFINITY) w.stack[w.sp++] = StackOps<E>::make(v3, k3);
+            if (k2 != INFINITY) w.stack[w.sp++] = StackOps<E>::make(v2, k2);
+            if (k1 != INFINITY) w.stack[w.sp++] = StackOps<E>::make(v1, k1);
             w.node = k0 != INFINITY ? v0 : ww_pop(w);
             if (w.node < 0 && w.node != kDone && w.leaf == kNoLeaf) {
                 w.leaf = w.node;
@@ -400,7 +429,7 @@ __device__ __forceinline__ void ww4_round(const DevScene& s, const RayPre& r, Ww
         }
         if (__ballot_sync(0xffffffffu, w.node >= 0 && w.leaf == kNoLeaf) == 0) break;
     }
-    ww_leaves<ANY, kStackSize4, COUNT>(s, r, w, tc);
+    ww_leaves<ANY, kStackSize4, COUNT, E>(s, r, w, tc);
 }
 
 }  // namespace ddgi
