@@ -13,6 +13,7 @@
 #pragma once
 
 #include <cfloat>
+#include <type_traits>
 
 #include "probe_math.cuh"
 
@@ -197,6 +198,27 @@ struct TraceCount {
     uint32_t tris = 0;    // triangle tests
 };
 
+// Traversal stack entries: a node or leaf reference alone (int; any-hit
+// walks), or the reference with the entry distance of its box (int2;
+// closest-hit walks).  A popped int2 entry whose box starts beyond the
+// closest hit found since it was pushed is dropped without a visit: no
+// triangle in that box can be closer.  An entry at exactly the hit distance
+// is kept (the tie rule may still prefer a triangle in it).
+template <typename E>
+struct StackOps;
+template <>
+struct StackOps<int> {
+    static __device__ __forceinline__ int make(int ref, float) { return ref; }
+    static __device__ __forceinline__ bool live(int, float) { return true; }
+    static __device__ __forceinline__ int ref(int e) { return e; }
+};
+template <>
+struct StackOps<int2> {
+    static __device__ __forceinline__ int2 make(int ref, float k) { return make_int2(ref, __float_as_int(k)); }
+    static __device__ __forceinline__ bool live(int2 e, float t) { return __int_as_float(e.y) <= t; }
+    static __device__ __forceinline__ int ref(int2 e) { return e.x; }
+};
+
 // Closest hit (ANY = false) or any hit among shadow casters (ANY = true)
 // over the binary hierarchy, one ray per thread.
 template <bool ANY>
@@ -206,7 +228,8 @@ __device__ __forceinline__ Hit traverse(const DevScene& s, const RayPre& r) {
     h.orig = -1;
     h.k = -1;
     if (s.n_nodes == 0) return h;
-    int stack[kStackSize];
+    using E = typename std::conditional<ANY, int, int2>::type;
+    E stack[kStackSize];
     int sp = 0;
     int node = 0;
     while (true) {
@@ -246,15 +269,25 @@ __device__ __forceinline__ Hit traverse(const DevScene& s, const RayPre& r) {
         if (h0 && h1) {
             bool first0 = e0 <= e1;
             int nearc = first0 ? m.x : m.y, farc = first0 ? m.y : m.x;
-            if (sp < kStackSize) stack[sp++] = farc;
+            if (sp < kStackSize) stack[sp++] = StackOps<E>::make(farc, first0 ? e1 : e0);
             node = nearc;
         } else if (h0) {
             node = m.x;
         } else if (h1) {
             node = m.y;
         } else {
-            if (sp == 0) break;
-            node = stack[--sp];
+            // the next live entry (entries whose box starts beyond the
+            // closest hit found since they were pushed are dropped)
+            bool more = false;
+            while (sp > 0) {
+                const E e = stack[--sp];
+                if (StackOps<E>::live(e, h.t)) {
+                    node = StackOps<E>::ref(e);
+                    more = true;
+                    break;
+                }
+            }
+            if (!more) break;
         }
     }
     return h;
@@ -277,27 +310,6 @@ constexpr int kNoLeaf = 0;              // "no parked leaf" (leaf codes are < 0)
 constexpr int kDone = kRefDone;         // empty-stack sentinel, below every leaf code
 
 __device__ __forceinline__ int leaf_code(int child, int cnt) { return ~(((~child) << kLeafBits) | (cnt - 1)); }
-
-// Stack entries of the walk: a node or leaf reference alone (int; any-hit
-// walks), or the reference with the entry distance of its box (int2;
-// closest-hit walks).  A popped int2 entry whose box starts beyond the
-// closest hit found since it was pushed is dropped without a visit: no
-// triangle in that box can be closer.  An entry at exactly the hit distance
-// is kept (the tie rule may still prefer a triangle in it).
-template <typename E>
-struct StackOps;
-template <>
-struct StackOps<int> {
-    static __device__ __forceinline__ int make(int ref, float) { return ref; }
-    static __device__ __forceinline__ bool live(int, float) { return true; }
-    static __device__ __forceinline__ int ref(int e) { return e; }
-};
-template <>
-struct StackOps<int2> {
-    static __device__ __forceinline__ int2 make(int ref, float k) { return make_int2(ref, __float_as_int(k)); }
-    static __device__ __forceinline__ bool live(int2 e, float t) { return __int_as_float(e.y) <= t; }
-    static __device__ __forceinline__ int ref(int2 e) { return e.x; }
-};
 
 // Per-lane state of the warp-cooperative walk.  The stack array lives
 // apart from the scalar fields (a pointer to the caller's local array), so
