@@ -35,12 +35,11 @@ import synth  # noqa: E402
 METRIC = "probe-update ms/frame & Grays/s at 16k probes; query ms at 1080p vs FP32 plain"
 WORKLOAD = ("city 32x16x32 probes @ 2 m, 196,610 tris, 256 rays/probe, hysteresis 0.97, "
             "multi-bounce, state machine on, 1920x1080 G-buffer query")
-# FP32 lane operations counted per unit of work of the trace passes (see the
-# design notes): a child-box slab test is 25, a 4-wide node visit tests four
-# boxes and, for closest-hit rays, orders them with 5 compare-exchanges of 5
-# operations; a watertight triangle test is 30.
+# FP32 lane operations counted per unit of work of the trace passes: a
+# child-box slab test is 25, a 4-wide node visit tests four boxes and orders
+# them nearest first with 5 compare-exchanges of 5 operations (closest-hit
+# and shadow rays alike); a watertight triangle test is 30.
 OPS_PER_WIDE_NODE = 4 * 25 + 5 * 5
-OPS_PER_WIDE_NODE_ANY = 4 * 25
 OPS_PER_TRI = 30
 L2_FLUSH_BYTES = 256 << 20
 TC_BLEND_DOC = {
@@ -452,7 +451,7 @@ def run_gpu(args):
     prim_ms = timings["trace_primary"][0] / max(timings["trace_primary"][1], 1)
     shadow_ms = timings["trace_shadow"][0] / max(timings["trace_shadow"][1], 1)
     prim_ops = OPS_PER_WIDE_NODE * stats["nodes"] + OPS_PER_TRI * stats["tris"]
-    shadow_ops = OPS_PER_WIDE_NODE_ANY * stats["shadow_nodes"] + OPS_PER_TRI * stats["shadow_tris"]
+    shadow_ops = OPS_PER_WIDE_NODE * stats["shadow_nodes"] + OPS_PER_TRI * stats["shadow_tris"]
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_tops = sm_count * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     achieved = prim_ops / (prim_ms * 1e-3) / 1e12

@@ -18,7 +18,7 @@
  *   query            Sec. 2.2 (8-probe cage), Sec. 4.1 (self-shadow bias Eq.),
  *                    Sec. 4.2 (gamma decode), Sec. 7.3 (volume blending)
  *
- * Readings where the paper is silent (each is listed in the design notes):
+ * Readings where the paper is silent:
  *   - Eq. 1 is read as a normalised average (the text calls it an average).
  *   - stored irradiance is the cosine-weighted mean radiance M; queries
  *     return E = pi * M, hit shading uses rho * M.

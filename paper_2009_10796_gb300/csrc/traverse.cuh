@@ -401,9 +401,9 @@ __device__ __forceinline__ void cx(float& ka, int& va, float& kb, int& vb) {
 
 // The same round over the 4-wide hierarchy: a node tests its four child
 // boxes, descends into the nearest hit child and pushes the other hits
-// farthest first (closest-hit rays; shadow rays push in slot order, any hit
-// ends them).  Leaves found among the children are parked or pushed as leaf
-// codes exactly as in the binary walk.
+// farthest first (for shadow rays too: near occluders are found first, and
+// any hit ends them).  Leaves found among the children are parked or pushed
+// as leaf codes exactly as in the binary walk.
 template <bool ANY, bool COUNT = false, typename E = int>
 __device__ __forceinline__ void ww4_round(const DevScene& s, const RayPre& r, WwLane<kStackSize4, E>& w,
                                           TraceCount* tc = nullptr) {
@@ -421,13 +421,11 @@ __device__ __forceinline__ void ww4_round(const DevScene& s, const RayPre& r, Ww
             float k0, k1, k2, k3;
             box4_enter_oct(r, nx, fx, ny, fy, nz, fz, w.h.t, k0, k1, k2, k3);
             int v0 = ref.x, v1 = ref.y, v2 = ref.z, v3 = ref.w;
-            if (!ANY) {
-                cx(k0, v0, k1, v1);
-                cx(k2, v2, k3, v3);
-                cx(k0, v0, k2, v2);
-                cx(k1, v1, k3, v3);
-                cx(k1, v1, k2, v2);
-            }
+            cx(k0, v0, k1, v1);
+            cx(k2, v2, k3, v3);
+            cx(k0, v0, k2, v2);
+            cx(k1, v1, k3, v3);
+            cx(k1, v1, k2, v2);
             // no bound test: scene creation checks that the hierarchy keeps the
             // stack within kStackSize4 (wide_stack_bound)
             if (k3 != INFINITY) w.stack[w.sp++] = StackOps<E>::make(v3, k3);

@@ -3,7 +3,7 @@
 Each test checks the oracle against something other than itself: published
 test vectors, closed forms, exact rational arithmetic, invariants or values
 worked by hand.  Every piece of oracle arithmetic is reached by at least one
-of them (see the design notes' pin table).
+of them.
 """
 from fractions import Fraction
 
