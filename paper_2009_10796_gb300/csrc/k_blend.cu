@@ -112,6 +112,8 @@ __global__ void __launch_bounds__(256) k_frame_setup(FrameRot rot_arg, const Fra
                                                      const double* __restrict__ sf64, float4* dirs, float* w_irr,
                                                      float* inv_s_irr, float* w_dist, float* inv_s_dist,
                                                      int32_t* zero, int n_zero, int first_block) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double red[256];
     __shared__ double s_nt[3];
     const FrameRot rot = ROT_DEV ? *rot_dev : rot_arg;
@@ -300,6 +302,8 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_blend_tiled(VolSet vs, B
                                                                     const int32_t* __restrict__ count,
                                                                     uint32_t* status) {
     static_assert(PG % 4 == 0, "probe groups come in quads");
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) float sm[];
     __shared__ int s_probe[PG];
     __shared__ int s_newly[PG];
@@ -712,10 +716,8 @@ cudaError_t launch_frame_setup_split(const FrameRot& rot, int R, int irr_n, int 
     // the directions in blocks of 64 rays, so the FP64 rotations of the
     // frame's rays spread over several SMs' double-precision units
     if (n_zero > 64) return cudaErrorInvalidValue;
-    k_frame_setup<false><<<(R + 63) / 64, 64, 0, st_dirs>>>(rot, nullptr, R, irr_n, dist_n, (double)cos_power, sf64,
-                                                              dirs, w_irr, inv_s_irr, w_dist, inv_s_dist, zero, n_zero,
-                                                              nwb);
-    return cudaGetLastError();
+    return launch_pdl(k_frame_setup<false>, (R + 63) / 64, 64, 0, st_dirs, rot, nullptr, R, irr_n, dist_n,
+                      (double)cos_power, sf64, dirs, w_irr, inv_s_irr, w_dist, inv_s_dist, zero, n_zero, nwb);
 }
 
 cudaError_t launch_frame_setup_dev(const FrameRot* rot_dev, int R, int irr_n, int dist_n, float cos_power,

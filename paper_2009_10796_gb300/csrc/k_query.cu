@@ -17,6 +17,8 @@ template <bool STAGE_OUT, bool FAST>
 __global__ void __launch_bounds__(kQueryThreads, FAST ? 5 : 4) k_query(VolView v, const float* __restrict__ pos,
                                                          const float* __restrict__ nrm, int64_t n, float3 cam,
                                                          float* __restrict__ out) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ __align__(16) float s_out[3 * kQueryThreads];
     for (int64_t q0 = (int64_t)blockIdx.x * kQueryThreads; q0 < n; q0 += (int64_t)gridDim.x * kQueryThreads) {
         const int64_t q = q0 + threadIdx.x;
@@ -255,15 +257,10 @@ cudaError_t launch_query(const VolView& v, const float* pos, const float* nrm, i
     int64_t blocks = (n + kQueryThreads - 1) / kQueryThreads;
     int grid = (int)(blocks < 1048576 ? blocks : 1048576);
     const bool fast = query_fast_view(v);
-    if (out_host && fast)
-        k_query<true, true><<<grid, kQueryThreads, 0, st>>>(v, pos, nrm, n, camera, out);
-    else if (out_host)
-        k_query<true, false><<<grid, kQueryThreads, 0, st>>>(v, pos, nrm, n, camera, out);
-    else if (fast)
-        k_query<false, true><<<grid, kQueryThreads, 0, st>>>(v, pos, nrm, n, camera, out);
-    else
-        k_query<false, false><<<grid, kQueryThreads, 0, st>>>(v, pos, nrm, n, camera, out);
-    return cudaGetLastError();
+    if (out_host && fast) return launch_pdl(k_query<true, true>, grid, kQueryThreads, 0, st, v, pos, nrm, n, camera, out);
+    if (out_host) return launch_pdl(k_query<true, false>, grid, kQueryThreads, 0, st, v, pos, nrm, n, camera, out);
+    if (fast) return launch_pdl(k_query<false, true>, grid, kQueryThreads, 0, st, v, pos, nrm, n, camera, out);
+    return launch_pdl(k_query<false, false>, grid, kQueryThreads, 0, st, v, pos, nrm, n, camera, out);
 }
 
 cudaError_t launch_query_glossy(const VolView& v, const float* pos, const float* nrm, const float* dirs, int64_t n,

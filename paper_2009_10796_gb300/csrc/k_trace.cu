@@ -218,6 +218,8 @@ __global__ void __launch_bounds__(256, 5) k_trace_primary(DevScene s, VolSet vs,
                                                        int32_t* shadow_count,
                                                        unsigned long long* next,
                                                        unsigned long long* stats = nullptr) {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31;
     const int64_t total = (int64_t)(*count) * R;
     TraceCount tc;
@@ -310,6 +312,8 @@ __global__ void __launch_bounds__(256) k_trace_shadow(DevScene s, VolSet vs, Lig
                                                       const int32_t* __restrict__ shadow_count,
                                                       unsigned long long* next,
                                                       unsigned long long* stats = nullptr) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t total = *shadow_count;
     TraceCount tc;
     const float3 tol = f3(-L.sun_dir.x, -L.sun_dir.y, -L.sun_dir.z);
@@ -361,6 +365,8 @@ __global__ void __launch_bounds__(256, 4) k_shade(DevScene s, VolSet vs, Lights 
                                                int R, FastDiv dR, const int32_t* __restrict__ active,
                                                const int32_t* __restrict__ hit_list,
                                                const int32_t* __restrict__ hit_count, float4* records) {
+    pdl_wait();
+    pdl_trigger();
     const int n_hits = *hit_count;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_hits; q += gridDim.x * blockDim.x) {
         const int64_t idx = __ldg(hit_list + q);
@@ -579,21 +585,19 @@ static cudaError_t trace_wavefront(const DevScene& s, const VolSet& vs, const Li
     cudaError_t e = cudaSuccess;
     if (marks && (e = cudaEventRecord(marks[0], st)) != cudaSuccess) return e;
     const FastDiv dR = make_fast_div((uint32_t)R);
-    k_trace_primary<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, dR, perm, active, count, records, shadow_list,
-                                                  hit_list, shadow_count, next);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_pdl(k_trace_primary<MULTI>, grid, 256, 0, st, s, vs, L, dirs, R, dR, perm, active, count, records,
+                        shadow_list, hit_list, shadow_count, next, nullptr)) != cudaSuccess)
+        return e;
     if (marks && (e = cudaEventRecord(marks[1], st)) != cudaSuccess) return e;
-    k_trace_shadow<MULTI><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, dR, active, records, shadow_list, shadow_count,
-                                                 next_shadow);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_pdl(k_trace_shadow<MULTI>, grid, 256, 0, st, s, vs, L, dirs, R, dR, active, records, shadow_list,
+                        shadow_count, next_shadow, nullptr)) != cudaSuccess)
+        return e;
     if (marks && (e = cudaEventRecord(marks[2], st)) != cudaSuccess) return e;
-    if (fast_query)
-        k_shade<MULTI, true><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, dR, active, hit_list, shadow_count + 1,
-                                                   records);
-    else
-        k_shade<MULTI, false><<<grid, 256, 0, st>>>(s, vs, L, dirs, R, dR, active, hit_list, shadow_count + 1,
-                                                    records);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = fast_query ? launch_pdl(k_shade<MULTI, true>, grid, 256, 0, st, s, vs, L, dirs, R, dR, active, hit_list,
+                                shadow_count + 1, records)
+                   : launch_pdl(k_shade<MULTI, false>, grid, 256, 0, st, s, vs, L, dirs, R, dR, active, hit_list,
+                                shadow_count + 1, records);
+    if (e != cudaSuccess) return e;
     if (marks && (e = cudaEventRecord(marks[3], st)) != cudaSuccess) return e;
     return cudaSuccess;
 }

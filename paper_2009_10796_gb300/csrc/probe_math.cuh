@@ -7,6 +7,7 @@
 #include <cuda_fp16.h>
 
 #include "ddgi_internal.h"
+#include "pdl.cuh"
 
 namespace ddgi {
 
