@@ -50,7 +50,7 @@ TC_BLEND_DOC = {
 # DRAM bytes (read + write) of one k_trace_primary launch on this workload,
 # from the ncu capture in profiles/trace_passes_city.md; set to None whenever
 # the kernel changes until it is captured again
-PRIMARY_TRAFFIC_BYTES = 7_147_264 + 3_417_088   # DRAM read + write of one k_trace_primary launch (ncu)
+PRIMARY_TRAFFIC_BYTES = 7_106_560 + 3_401_728   # DRAM read + write of one k_trace_primary launch (ncu)
 # The traversal's cache roofline: bytes one 4-wide node visit reads (the six
 # slab planes and the child references, 7 of the node's 8 float4) and one
 # triangle test reads (3 float4), against the L2 read rate measured in the
@@ -60,14 +60,14 @@ BYTES_PER_TRI = 3 * 16
 L2_PROBE_BYTES = (16 << 20, 32 << 20)
 # L2 bytes (lts__t_bytes) of one k_trace_primary launch on this workload,
 # from the same ncu capture rules as PRIMARY_TRAFFIC_BYTES
-PRIMARY_L2_BYTES = 421_719_456
+PRIMARY_L2_BYTES = 420_674_752
 # Warp instructions of one launch (smsp__inst_executed.sum, ncu) of the
 # primary pass and of the 1080p query on this workload: their issue rate
 # against the SMs' peak (four schedulers each issuing one warp instruction
 # per clock) is the bound these issue-limited kernels meet first; set to
 # None whenever the kernel changes until it is captured again
 PRIMARY_WARP_INSTR = 109_074_897
-QUERY_WARP_INSTR = 65_485_903
+QUERY_WARP_INSTR = 65_615_503
 
 
 def workload_config(desc, n_pix):
