@@ -7,17 +7,25 @@
 // launched this way calls pdl_wait() before it touches device memory; the
 // kernels call pdl_trigger() right after it, which lets the next kernel's
 // blocks be scheduled once all of this kernel's blocks have started.  On a
-// kernel launched the ordinary way both are no-ops in effect.
+// kernel launched the ordinary way both are no-ops in effect.  DDGI_NO_PDL=1
+// in the environment (read at each launch) makes launch_pdl an ordinary
+// launch.
 #pragma once
 
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <utility>
 
 namespace ddgi {
 
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+inline bool pdl_enabled() {
+    const char* e = std::getenv("DDGI_NO_PDL");
+    return !(e && e[0] == '1');
+}
 
 template <typename... K, typename... A>
 inline cudaError_t launch_pdl(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
@@ -31,7 +39,7 @@ inline cudaError_t launch_pdl(void (*kernel)(K...), dim3 grid, dim3 block, size_
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
 }
 

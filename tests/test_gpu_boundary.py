@@ -157,3 +157,42 @@ def test_measure_l2_read(g):
         g.measure_l2_read(buf[1:5], 1, sink)
     with pytest.raises(g.DDGIError, match="multiple of 16"):
         g.measure_l2_read(buf[:3], 1, sink)
+
+
+def test_overlapped_launches_match_ordinary_launches(g, monkeypatch):
+    """The frame's kernels as programmatic dependent launches (the default)
+    give the same bits as ordinary launches (DDGI_NO_PDL=1): a volume's states,
+    atlases and query after four updates, and a tracking cascade replayed as a
+    CUDA graph."""
+    sc = synth.room_scene(n_boxes=12)
+    L = synth.room_lights()
+    S = g.Scene.from_arrays(sc)
+    desc = synth.room_volume(hysteresis_irr=0.9, hysteresis_vis=0.8)
+    pos, nrm, _ = synth.room_queries(n=4096)
+    P, N_ = to_dev(pos), to_dev(nrm)
+    cam = np.array([2.0, 1.5, 2.5])
+    common = dict(rays_per_probe=32, hysteresis_irr=0.5, hysteresis_vis=0.5, seed=4242)
+    fine = synth.VolumeDesc(origin=(2.0, 2.0, 2.0), spacing=(0.75, 0.75, 0.75), counts=(6, 6, 6), tracking=1,
+                            **common)
+    coarse = synth.VolumeDesc(origin=(0.625, 0.625, 0.625), spacing=(1.25, 1.25, 1.25), counts=(8, 8, 8),
+                              **common)
+
+    def run(ordinary):
+        if ordinary:
+            monkeypatch.setenv("DDGI_NO_PDL", "1")
+        else:
+            monkeypatch.delenv("DDGI_NO_PDL", raising=False)
+        V = g.Volume(desc)
+        C = g.Cascade([fine, coarse])
+        for f in range(4):
+            V.update(S, L, f)
+            C.update(S, L, f, synth.f32([3.0 + 0.55 * f, 4.0, 5.0 - 0.2 * f]), use_graph=True)
+        E = V.query(P, N_, cam)
+        torch.cuda.synchronize()
+        return _raw(V) + [E] + [C.states(k) for k in range(2)] + [C.buffer(k, b) for k in range(2) for b in (0, 1)]
+
+    overlapped = run(False)
+    ordinary = run(True)
+    monkeypatch.delenv("DDGI_NO_PDL", raising=False)
+    for a, b in zip(overlapped, ordinary):
+        assert torch.equal(a, b)
