@@ -28,6 +28,11 @@
  *     counter-clockwise seen from their front side.
  *   - Stored irradiance is the cosine-weighted mean radiance M; queries
  *     return irradiance E = pi * M.
+ *   - Consecutive kernels of an update and a query are programmatic
+ *     dependent launches (each may be scheduled before its predecessor on
+ *     the stream has finished, and waits for it on the device).  With
+ *     DDGI_NO_PDL=1 in the environment (read at each launch) they are
+ *     ordinary launches; the results are the same bit for bit.
  */
 #ifndef DDGI_H
 #define DDGI_H
