@@ -143,6 +143,7 @@ struct ddgi_volume_s {
     unsigned long long* stats = nullptr;   // [8] trace work counters
     int32_t* shadow_list = nullptr;        // [P * R] rays needing a shadow ray
     int32_t* hit_list = nullptr;           // [P * R] rays with a front hit to shade
+    int4* class_scratch = nullptr;         // [P] classification sums (zeroed between uses)
     int32_t* shadow_count = nullptr;
     int32_t* perm = nullptr;               // [R] ray order within a probe's warps
     std::vector<void*> snap_irr, snap_dist;   // differentiable forward: atlas after each frame
@@ -493,7 +494,7 @@ void ddgi_volume_destroy(ddgi_volume v) {
     cudaFree(v->states); cudaFree(v->irr); cudaFree(v->dist); cudaFree(v->lists); cudaFree(v->counts);
     cudaFree(v->status); cudaFree(v->records); cudaFree(v->dirs); cudaFree(v->sf64); cudaFree(v->w_irr);
     cudaFree(v->inv_s_irr); cudaFree(v->w_dist); cudaFree(v->inv_s_dist); cudaFree(v->stats);
-    cudaFree(v->shadow_list); cudaFree(v->hit_list); cudaFree(v->perm);
+    cudaFree(v->shadow_list); cudaFree(v->hit_list); cudaFree(v->class_scratch); cudaFree(v->perm);
     for (void* p : v->snap_irr) cudaFree(p);
     for (void* p : v->snap_dist) cudaFree(p);
     cudaFree(v->g_irr); cudaFree(v->g_prev);
@@ -575,6 +576,8 @@ ddgi_status ddgi_volume_create(const ddgi_volume_desc* desc, ddgi_volume* out) {
     A((void**)&v->stats, sizeof(unsigned long long) * 8);
     A((void**)&v->shadow_list, sizeof(int32_t) * (size_t)v->P * v->R);
     A((void**)&v->hit_list, sizeof(int32_t) * (size_t)v->P * v->R);
+    A((void**)&v->class_scratch, sizeof(int4) * (size_t)v->P);
+    if (e == cudaSuccess) e = cudaMemset(v->class_scratch, 0, sizeof(int4) * (size_t)v->P);
     A((void**)&v->perm, sizeof(int32_t) * v->R);
     if (e == cudaSuccess) {
         std::vector<int32_t> perm = ray_order_morton(v->R);
@@ -741,7 +744,8 @@ static ddgi_status update_impl(ddgi_volume v, ddgi_scene s, const ddgi_lights* l
                                       v->opt_dirs, st));
             DDGI_CK(launch_optimize(s->dev, view, v->opt_dirs, v->R, v->lists, v->counts + 0, sms * 8, st));
         }
-        DDGI_CK(launch_classify(s->dev, view, v->dirs, v->R, v->perm, v->lists, v->counts + 0, sms * 8, st));
+        DDGI_CK(launch_classify(s->dev, view, v->dirs, v->R, v->perm, v->lists, v->counts + 0, v->class_scratch,
+                                sms * 8, st));
         if (begin == 0 && end == v->P) v->uninit_possible = false;
     }
     // dynamic objects wake sleeping probes (and awake probes fall asleep
@@ -1094,6 +1098,7 @@ struct ddgi_cascade_s {
     float4* records = nullptr;
     int32_t* shadow_list = nullptr;
     int32_t* hit_list = nullptr;
+    int4* class_scratch = nullptr;   // [total] classification sums (zeroed between uses)
     int32_t* shadow_count = nullptr;
     int32_t* perm = nullptr;
     float4* dirs = nullptr;
@@ -1118,7 +1123,7 @@ namespace {
 void cascade_free(ddgi_cascade_s* c) {
     for (int k = 0; k < c->n; ++k) { cudaFree(c->states[k]); cudaFree(c->irr[k]); cudaFree(c->dist[k]); }
     cudaFree(c->lists); cudaFree(c->counts); cudaFree(c->status); cudaFree(c->records);
-    cudaFree(c->shadow_list); cudaFree(c->hit_list); cudaFree(c->perm); cudaFree(c->dirs);
+    cudaFree(c->shadow_list); cudaFree(c->hit_list); cudaFree(c->class_scratch); cudaFree(c->perm); cudaFree(c->dirs);
     cudaFree(c->sf64);
     cudaFree(c->w_irr);
     cudaFree(c->inv_s_irr); cudaFree(c->w_dist); cudaFree(c->inv_s_dist); cudaFree(c->pack_w);
@@ -1216,7 +1221,8 @@ ddgi_status cascade_enqueue(ddgi_cascade_s* c, const DevScene& sc, const Lights&
         DDGI_CK(launch_pack_weights(c->w_irr, c->w_dist, c->R, d0.irr_n, d0.dist_n, precision, c->pack_w,
                                     c->inv_irr_r, c->inv_dist_r, st));
     DDGI_CK(launch_build_list_multi(vs, (int)c->total, 0, c->lists, c->counts + 0, st));
-    DDGI_CK(launch_classify_multi(sc, vs, c->dirs, c->R, c->perm, c->lists, c->counts + 0, sms * 8, st));
+    DDGI_CK(launch_classify_multi(sc, vs, c->dirs, c->R, c->perm, c->lists, c->counts + 0, c->class_scratch,
+                                  sms * 8, st));
     DDGI_CK(launch_build_list_multi(vs, (int)c->total, 1, c->lists + c->total, c->counts + 1, st));
     DDGI_CK(launch_trace_wavefront_multi(sc, vs, L, c->dirs, c->R, c->perm, c->lists + c->total, c->counts + 1,
                                          c->records, c->shadow_list, c->hit_list, c->shadow_count, sms * c->trace_mult,
@@ -1297,6 +1303,8 @@ ddgi_status ddgi_cascade_create(const ddgi_volume_desc* descs, int32_t n, ddgi_c
     A((void**)&c->records, sizeof(float4) * (size_t)c->total * c->R);
     A((void**)&c->shadow_list, sizeof(int32_t) * (size_t)c->total * c->R);
     A((void**)&c->hit_list, sizeof(int32_t) * (size_t)c->total * c->R);
+    A((void**)&c->class_scratch, sizeof(int4) * (size_t)c->total);
+    if (e == cudaSuccess) e = cudaMemset(c->class_scratch, 0, sizeof(int4) * (size_t)c->total);
     A((void**)&c->dirs, sizeof(float4) * 3 * c->R);
     A((void**)&c->sf64, sizeof(double) * 3 * c->R);
     if (e == cudaSuccess) e = launch_sf_table(c->R, c->sf64, 0);

@@ -244,11 +244,14 @@ cudaError_t launch_optimize(const DevScene& s, const VolView& v, const float4* d
 // The frame directions and ray constants alone (position-optimizer rays).
 cudaError_t launch_frame_dirs(const FrameRot& rot, int R, int irr_n, int dist_n, const double* sf64, float4* dirs,
                               cudaStream_t st);
+// Classification of the listed (uninitialised) probes.  scratch: one zeroed
+// int4 per list entry, left zeroed (batch-split kernel), or nullptr (one
+// warp per probe, no scratch: the allocation-free update).
 cudaError_t launch_classify(const DevScene& s, const VolView& v, const float4* dirs, int R, const int32_t* perm,
-                            const int32_t* list, const int32_t* count, int grid, cudaStream_t st);
+                            const int32_t* list, const int32_t* count, int4* scratch, int grid, cudaStream_t st);
 cudaError_t launch_classify_multi(const DevScene& s, const VolSet& vs, const float4* dirs, int R,
-                                  const int32_t* perm, const int32_t* list, const int32_t* count, int grid,
-                                  cudaStream_t st);
+                                  const int32_t* perm, const int32_t* list, const int32_t* count, int4* scratch,
+                                  int grid, cudaStream_t st);
 cudaError_t launch_trace_shade(const DevScene& s, const VolView& v, const Lights& L,
                                const float4* dirs, int R, const int32_t* active,
                                const int32_t* count, float4* records, int grid, cudaStream_t st);

@@ -68,6 +68,77 @@ __global__ void __launch_bounds__(256) k_classify(DevScene s, VolSet vs, const f
     }
 }
 
+// Classification in 32-ray batches: one work item per (list entry, batch),
+// so the R rays of the few probes a frame classifies (the planes a tracking
+// window scrolls in) spread over all warps instead of R / 32 sequential
+// batches in one warp each.  A batch adds its backface count and maxes its
+// nearest front-face distance (as 0x7f800000 - bits, so a zeroed word
+// stands for +inf) into the entry's scratch, then counts itself done; the
+// warp that completes an entry's last batch sets the state as k_classify
+// does and zeroes the scratch for the next classification.  Counts and
+// minima do not depend on the order the batches run in, so the states are
+// k_classify's.  scratch: one zeroed int4 per list entry.
+template <bool MULTI>
+__global__ void __launch_bounds__(256) k_classify_split(DevScene s, VolSet vs, const float4* __restrict__ dirs,
+                                                        int R, const int32_t* __restrict__ perm,
+                                                        const int32_t* __restrict__ list,
+                                                        const int32_t* __restrict__ count, int4* scratch) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nb = (R + 31) / 32;
+    const int64_t items = (int64_t)(*count) * nb;
+    int2 stack[kStackSize4];
+    WwLane<kStackSize4, int2> w;
+    w.stack = stack;
+    for (int64_t it = warp; it < items; it += nwarps) {
+        const int q = (int)(it / nb), b = (int)(it - (int64_t)q * nb);
+        const int e = list[q];
+        const VolView& v = vol_of<MULTI>(vs, e >> kEntryShift);
+        const int p = e & kEntryMask;
+        const float3 o = probe_pos_phys(v, p);
+        const int j = 32 * b + lane;
+        const bool valid = j < R;
+        const int i = valid ? (perm ? __ldg(perm + j) : j) : 0;
+        const float4 d4 = __ldg(dirs + i);
+        const float3 d = f3(d4.x, d4.y, d4.z);
+        const RayPre r = ray_pre_packed(o, d, __ldg(dirs + R + 2 * i), __ldg(dirs + R + 2 * i + 1));
+        ww_start(s, w, valid);
+        do {
+            ww4_round<false>(s, r, w);
+        } while (__ballot_sync(0xffffffffu, w.node != kDone) != 0);
+        const Hit& h = w.h;
+        bool back = false;
+        float dmin = INFINITY;
+        if (valid && h.orig >= 0) {
+            const float4* T = s.tris + 3 * (int64_t)h.k;
+            float4 p0 = __ldg(T), p1 = __ldg(T + 1), p2 = __ldg(T + 2);
+            float3 ng = cross(f3(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z), f3(p2.x - p0.x, p2.y - p0.y, p2.z - p0.z));
+            if (dot(d, ng) > 0.0f) back = true;
+            else dmin = h.t;
+        }
+        const int bf = __popc(__ballot_sync(0xffffffffu, back));
+        for (int off = 16; off > 0; off >>= 1) dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, off));
+        if (lane == 0) {
+            int4* sc = scratch + q;
+            if (bf) atomicAdd(&sc->x, bf);
+            atomicMax(&sc->y, 0x7f800000 - __float_as_int(dmin));
+            __threadfence();   // this batch's sums before its done count
+            if (atomicAdd(&sc->z, 1) == nb - 1) {
+                __threadfence();
+                const int bft = atomicAdd(&sc->x, 0);
+                const float dm = __int_as_float(0x7f800000 - atomicAdd(&sc->y, 0));
+                uint8_t st;
+                if (4 * bft > R) st = DDGI_STATE_OFF;
+                else if (dm < v.min_spacing) st = DDGI_STATE_NEWLY_VIGILANT;
+                else st = DDGI_STATE_SLEEPING;
+                v.states[p] = st;
+                *sc = make_int4(0, 0, 0, 0);   // no other batch of this entry is left
+            }
+        }
+    }
+}
+
 // Fused trace + shade, one thread per probe ray (the allocation-free
 // update's path: it needs no shadow or hit lists); rays and shadow rays go
 // through the warp-cooperative 4-wide walk.
@@ -554,15 +625,21 @@ cudaError_t launch_optimize(const DevScene& s, const VolView& v, const float4* d
 }
 
 cudaError_t launch_classify(const DevScene& s, const VolView& v, const float4* dirs, int R, const int32_t* perm,
-                            const int32_t* list, const int32_t* count, int grid, cudaStream_t st) {
-    k_classify<false><<<grid, 256, 0, st>>>(s, single_set(v), dirs, R, perm, list, count);
+                            const int32_t* list, const int32_t* count, int4* scratch, int grid, cudaStream_t st) {
+    if (scratch)
+        k_classify_split<false><<<grid, 256, 0, st>>>(s, single_set(v), dirs, R, perm, list, count, scratch);
+    else
+        k_classify<false><<<grid, 256, 0, st>>>(s, single_set(v), dirs, R, perm, list, count);
     return cudaGetLastError();
 }
 
 cudaError_t launch_classify_multi(const DevScene& s, const VolSet& vs, const float4* dirs, int R,
-                                  const int32_t* perm, const int32_t* list, const int32_t* count, int grid,
-                                  cudaStream_t st) {
-    k_classify<true><<<grid, 256, 0, st>>>(s, vs, dirs, R, perm, list, count);
+                                  const int32_t* perm, const int32_t* list, const int32_t* count, int4* scratch,
+                                  int grid, cudaStream_t st) {
+    if (scratch)
+        k_classify_split<true><<<grid, 256, 0, st>>>(s, vs, dirs, R, perm, list, count, scratch);
+    else
+        k_classify<true><<<grid, 256, 0, st>>>(s, vs, dirs, R, perm, list, count);
     return cudaGetLastError();
 }
 

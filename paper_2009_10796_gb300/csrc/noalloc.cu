@@ -195,7 +195,7 @@ extern "C" ddgi_status ddgi_update_noalloc(ddgi_scene scene, const ddgi_volume_d
     if (d->state_machine) {
         if ((e = launch_build_list(states_dev, (int)P, 0, s.lists, s.counts + 0, st)) != cudaSuccess)
             return na_fail(e, "uninitialised list");
-        if ((e = launch_classify(*sv, v, s.dirs, R, nullptr, s.lists, s.counts + 0, sms * 8, st)) != cudaSuccess)
+        if ((e = launch_classify(*sv, v, s.dirs, R, nullptr, s.lists, s.counts + 0, nullptr, sms * 8, st)) != cudaSuccess)
             return na_fail(e, "classify");
     }
     if ((e = launch_build_list(states_dev, (int)P, 1, s.lists + P, s.counts + 1, st)) != cudaSuccess)
