@@ -284,11 +284,10 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool vali
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+// every group but the kTileNS - 1 most recent complete
 __device__ __forceinline__ void cp_async_wait_ahead() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(kTileNS - 1) : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Each CTA takes an equal share of the active probes (at most PG per pass;
 // the grid is one wave of resident CTAs); blockDim = TiledShape::threads.
